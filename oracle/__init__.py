@@ -1,0 +1,257 @@
+"""CPU FP64 oracle for the Stokes boundary-integral hot path.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import this package:
+only the tests, the smoke check (`__graft_entry__.smoke`) and the CPU-baseline
+leg of `bench.py` use it.  It shares no code with the CUDA library; the only
+module both sides use is the seeded input generator
+(`paper_2310_00889_gb300.inputs`), which holds none of the method's arithmetic.
+
+Contents
+  * pair sums (C, `stokes_oracle.c`): single layer, double layer, combined field,
+    sparse correction apply, the combined-field operator K = diag I + D + eta S + E
+    (paper Sec. 3.2.1 Eq. nystrom-no-correction / nystrom-correction,
+    Eqs. stokes-sl / stokes-dl / stokes-bie-new);
+  * `dense_operator`: the same kernels written a second time with numpy, as an
+    explicit 3N x 3N matrix, for tiny systems;
+  * `gmres`: restarted GMRES(m) with classical Gram--Schmidt applied twice and
+    Givens rotations (the paper uses unpreconditioned GMRES, Sec. 4, without
+    giving restart or orthogonalisation details);
+  * `eta_slender`: the slender-body mixing parameter 1 / (2 eps log(1/eps))
+    (Sec. 4.1, Laplace and Stokes slender combined-field formulations).
+
+Every pin of these functions lives in tests/test_oracle_*.py.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "stokes_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_d = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_i64 = ctypes.c_int64
+
+
+def build(force=False) -> str:
+    """Compile the C oracle with gcc (OpenMP) into oracle/liboracle.so."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp.%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            lib.oracle_stokes_combined.argtypes = [_i64, _d, _d, _d, _d, _i64, _d,
+                                                   ctypes.c_double, ctypes.c_double, _d]
+            lib.oracle_csr_apply.argtypes = [_i64, _i64p, _i64p, _d, _d, _d]
+            lib.oracle_stokes_matvec.argtypes = [_i64, _d, _d, _d, ctypes.c_double,
+                                                 ctypes.c_double, _i64, _i64p, _i64p, _d,
+                                                 _d, _d]
+            lib.oracle_num_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(_d) if a is not None else None
+
+
+def _c(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+def combined(src, nrm, w, sigma, trg, alpha, beta):
+    """u = sum_s [alpha S + beta D](x_t - y_s) w_s sigma_s over y_s != x_t; returns (3, nt)."""
+    lib = _load()
+    src = _c(src)
+    ns = src.shape[1]
+    trg = _c(trg)
+    nt = trg.shape[1]
+    w = _c(w, (ns,))
+    sigma = _c(sigma, (3, ns))
+    nrm = _c(nrm, (3, ns)) if nrm is not None else None
+    if beta != 0.0 and nrm is None:
+        raise ValueError("double layer needs normals")
+    u = np.empty((3, nt))
+    lib.oracle_stokes_combined(ns, _p(src), _p(nrm), _p(w), _p(sigma), nt, _p(trg),
+                               float(alpha), float(beta), _p(u))
+    return u
+
+
+def sl(src, w, sigma, trg):
+    """Single-layer potential S[sigma] (paper Eq. stokes-sl), uncorrected Nystrom sum."""
+    return combined(src, None, w, sigma, trg, 1.0, 0.0)
+
+
+def dl(src, nrm, w, sigma, trg):
+    """Double-layer potential D[sigma] (paper Eq. stokes-dl, sign reading in stokes_oracle.c)."""
+    return combined(src, nrm, w, sigma, trg, 0.0, 1.0)
+
+
+class CSR:
+    """Sparse correction matrix E with component-major (c * n + node) rows and columns."""
+
+    def __init__(self, rowptr, col, val, nrows, ncols):
+        self.rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        self.col = np.ascontiguousarray(col, dtype=np.int64)
+        self.val = np.ascontiguousarray(val, dtype=np.float64)
+        self.nrows, self.ncols = int(nrows), int(ncols)
+
+    @property
+    def nnz(self):
+        return int(self.val.shape[0])
+
+
+def csr_apply(E: CSR, x, y):
+    """y += E x (in place on a float64 contiguous y)."""
+    lib = _load()
+    x = _c(x).reshape(-1)
+    assert y.dtype == np.float64 and y.flags.c_contiguous
+    lib.oracle_csr_apply(E.nrows, E.rowptr.ctypes.data_as(_i64p), E.col.ctypes.data_as(_i64p),
+                         _p(E.val), _p(x), _p(y))
+    return y
+
+
+def matvec(src, nrm, w, eta, sigma, diag=0.5, E: CSR | None = None):
+    """K sigma = diag sigma + (D + eta S)[sigma] + E sigma on the nodes (paper Eq. stokes-bie-new)."""
+    lib = _load()
+    src = _c(src)
+    n = src.shape[1]
+    nrm = _c(nrm, (3, n))
+    w = _c(w, (n,))
+    sigma = _c(sigma, (3, n))
+    out = np.empty((3, n))
+    if E is not None and E.nnz > 0:
+        lib.oracle_stokes_matvec(n, _p(src), _p(nrm), _p(w), float(eta), float(diag), E.nnz,
+                                 E.rowptr.ctypes.data_as(_i64p), E.col.ctypes.data_as(_i64p),
+                                 _p(E.val), _p(sigma), _p(out))
+    else:
+        lib.oracle_stokes_matvec(n, _p(src), _p(nrm), _p(w), float(eta), float(diag), 0, None,
+                                 None, None, _p(sigma), _p(out))
+    return out
+
+
+def dense_operator(src, nrm, w, trg, alpha, beta):
+    """Explicit matrix A (3 nt x 3 ns, component-major) with A sigma = combined(...).
+
+    Written independently of the C code with numpy broadcasting, for tiny inputs only.
+    """
+    src, trg = np.asarray(src, float), np.asarray(trg, float)
+    r = trg[:, :, None] - src[:, None, :]                      # (3, nt, ns)
+    r2 = np.sum(r * r, axis=0)
+    same = r2 == 0.0
+    with np.errstate(divide="ignore", invalid="ignore"):
+        rl = np.sqrt(r2)
+        inv1 = np.where(same, 0.0, 1.0 / rl)
+        inv3 = inv1 ** 3
+        inv5 = inv1 ** 5
+    nt, ns = r2.shape
+    A = np.zeros((3, nt, 3, ns))
+    eye = np.eye(3)
+    for i in range(3):
+        for j in range(3):
+            blk = np.zeros((nt, ns))
+            if alpha != 0.0:
+                blk += alpha / (8.0 * np.pi) * (eye[i, j] * inv1 + r[i] * r[j] * inv3)
+            if beta != 0.0:
+                rdn = np.sum(r * np.asarray(nrm, float)[:, None, :], axis=0)
+                blk += beta * 3.0 / (4.0 * np.pi) * rdn * r[i] * r[j] * inv5
+            A[i, :, j, :] = blk * np.asarray(w, float)[None, :]
+    return A.reshape(3 * nt, 3 * ns)
+
+
+def eta_slender(eps):
+    """Slender-body mixing parameter eta = 1 / (2 eps log(1/eps)), natural log (paper Sec. 4.1)."""
+    eps = np.asarray(eps, dtype=np.float64)
+    return 1.0 / (2.0 * eps * np.log(1.0 / eps))
+
+
+def gmres(apply, b, x0=None, tol=1e-10, restart=100, max_iter=2000, true_residual=None):
+    """Restarted GMRES(m) for A x = b, FP64.
+
+    Arnoldi with classical Gram--Schmidt applied twice, Givens rotations on the
+    Hessenberg matrix, x0 = 0 unless given.  A cycle ends when the Givens
+    residual estimate drops to tol * ||b|| or after `restart` steps; the true
+    residual ||b - A x|| is then recomputed and the solve stops when it is at most
+    tol * ||b||.  Returns (x, info) with info = dict(iters, cycles, rel_res, hist).
+    """
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    n = b.size
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64).reshape(-1)
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return np.zeros(n), dict(iters=0, cycles=0, rel_res=0.0, hist=[0.0])
+    resid = true_residual or (lambda xx: b - apply(xx))
+    r = resid(x)
+    beta = np.linalg.norm(r)
+    hist = [beta / bnorm]
+    iters, cycles = 0, 0
+    while hist[-1] > tol and iters < max_iter:
+        m = min(restart, max_iter - iters)
+        V = np.zeros((m + 1, n))
+        H = np.zeros((m + 1, m))
+        cs, sn = np.zeros(m), np.zeros(m)
+        g = np.zeros(m + 1)
+        g[0] = beta
+        V[0] = r / beta
+        k = 0
+        for j in range(m):
+            wv = apply(V[j])
+            h = V[:j + 1] @ wv
+            wv = wv - V[:j + 1].T @ h
+            h2 = V[:j + 1] @ wv
+            wv = wv - V[:j + 1].T @ h2
+            h = h + h2
+            hn = np.linalg.norm(wv)
+            H[:j + 1, j] = h
+            H[j + 1, j] = hn
+            for i in range(j):                                   # previous rotations
+                a, c = H[i, j], H[i + 1, j]
+                H[i, j] = cs[i] * a + sn[i] * c
+                H[i + 1, j] = -sn[i] * a + cs[i] * c
+            a, c = H[j, j], H[j + 1, j]
+            den = np.hypot(a, c)
+            cs[j], sn[j] = (1.0, 0.0) if den == 0.0 else (a / den, c / den)
+            H[j, j] = cs[j] * a + sn[j] * c
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            k = j + 1
+            iters += 1
+            if abs(g[j + 1]) <= tol * bnorm or hn == 0.0:
+                break
+            V[j + 1] = wv / hn
+        y = np.zeros(k)
+        for i in range(k - 1, -1, -1):                           # back substitution
+            y[i] = (g[i] - H[i, i + 1:k] @ y[i + 1:k]) / H[i, i]
+        x = x + V[:k].T @ y
+        r = resid(x)
+        beta = np.linalg.norm(r)
+        hist.append(beta / bnorm)
+        cycles += 1
+        if beta == 0.0:
+            break
+    return x, dict(iters=iters, cycles=cycles, rel_res=hist[-1], hist=hist)

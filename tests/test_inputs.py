@@ -1,0 +1,82 @@
+"""Checks of the seeded input generator (no GPU): node counts, weights, normals, frames.
+
+Quadrature weights w = J w_GL 2 pi / N_theta (paper Sec. 3.2.1): the trapezoid rule in
+theta integrates the curvature factor (1 - eps kappa cos theta) exactly, so the weights of
+a constant-radius tube sum to the exact lateral area to rounding.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2310_00889_gb300 import inputs as I
+
+
+def test_straight_pipe_area_and_count():
+    s = I.straight_pipe(1.0, 4.0, 4, 8, 16)
+    assert s.size == 512
+    assert abs(s.w.sum() - 8 * math.pi) < 1e-12
+
+
+def test_arc_area_pappus():
+    s = I.arc_pipe(5.0, 0.5 * math.pi, 1.0, 32, 8, 64)
+    assert s.size == 16384
+    assert abs(s.w.sum() - 5 * math.pi ** 2) < 1e-11      # 2 pi R * Rc * angle
+
+
+def test_torus_and_sphere_area():
+    t = I.torus(1.0, 0.25, 16, 8, 32)
+    assert abs(t.w.sum() - 4 * math.pi ** 2 * 0.25) < 1e-12
+    sp = I.sphere(0.7, (0.1, 0.2, 0.3), 20, 30)
+    assert sp.size == 600
+    assert abs(sp.w.sum() - 4 * math.pi * 0.49) < 1e-12
+
+
+def test_helix_area():
+    h = I.helix_pipe(3.0, 2.0, 4.0, 1.0, 64, 8, 32)
+    length = 4 * math.sqrt((6 * math.pi) ** 2 + 2.0 ** 2)
+    assert abs(h.w.sum() - 2 * math.pi * length) < 1e-9
+
+
+def test_caps_area_and_normals():
+    cp = I.capped_straight_pipe(1.0, 4.0, 4, 8, 16, 8)
+    for nm, a, b in cp.parts:
+        if nm.startswith("cap"):
+            assert abs(cp.w[a:b].sum() - math.pi) < 1e-13
+    n0 = cp.n[:, [a for nm, a, b in cp.parts if nm == "cap0"][0]]
+    n1 = cp.n[:, [a for nm, a, b in cp.parts if nm == "cap1"][0]]
+    assert np.allclose(n0, [0, 0, -1]) and np.allclose(n1, [0, 0, 1])
+
+
+@pytest.mark.parametrize("maker", [lambda: I.straight_pipe(), lambda: I.arc_pipe(panels=4),
+                                   lambda: I.helix_pipe(panels=16), lambda: I.torus(),
+                                   lambda: I.random_loop(panels=16)])
+def test_normals_unit_and_outward(maker):
+    s = maker()
+    assert np.allclose(np.linalg.norm(s.n, axis=0), 1.0, atol=1e-12)
+    assert np.all(s.w > 0)
+
+
+def test_random_loop_frame_and_radius():
+    s = I.random_loop(seed=1, panels=64, ns=8, nth=16)
+    assert s.size == 64 * 8 * 16
+    # the generator re-orthonormalises e1; radius in [0.005, 0.015]: nodes lie on circles of
+    # that radius around the centreline, so every theta ring has the right mean distance
+    ring = s.x.reshape(3, 64 * 8, 16)
+    centre = ring.mean(axis=2, keepdims=True)
+    rad = np.linalg.norm(ring - centre, axis=0)
+    assert rad.min() > 0.0049 and rad.max() < 0.0151
+
+
+def test_config_sizes_and_seeds():
+    c1 = I.config1()
+    assert c1["surf"].size == 512 and c1["trg"].shape == (3, 768)
+    assert np.array_equal(c1["sigma"], I.config1()["sigma"])
+    c2 = I.config2(panels=4)
+    assert c2["surf"].size == 4 * 8 * 64 + 2 * 16 * 64
+    rhs = c2["rhs"]
+    assert np.all(rhs[:, :4 * 8 * 64] == 0) and np.abs(rhs).max() <= 1.0
+    c4 = I.config4(nseg=6)
+    for seg in c4["segments"]:
+        wall = seg["surf"].parts[0]
+        assert (wall[2] - wall[1]) % 256 == 0
