@@ -1,0 +1,406 @@
+#!/usr/bin/env python
+"""Benchmark of the Stokes boundary-integral hot path on one GB300 (or N replicas).
+
+Workload (curved pipe): quarter-circle arc of centreline radius 5, tube radius 1,
+32 panels x 8 Gauss-Legendre x 64 trapezoid = 16384 wall nodes plus two 16 x 64 end
+caps (18432 nodes, 55296 unknowns); combined-field operator K = I/2 + D + eta S with
+eta = 1/(2 eps log(1/eps)), eps = 1/5 (paper Eq. stokes-bie-new, uncorrected Nystrom
+sums); Dirichlet data: parabolic profile on the caps, zero on the wall.
+
+One step = one GMRES solve of K x = u0 to a 1e-10 FP64 relative residual from x0 = 0:
+compensated-FP32 pair sums inside the Krylov iterations, FP64 residual refinement,
+each Arnoldi step replayed by a CUDA-graph while node.  Inputs are resident in HBM
+before the timed region; the operator (geometry packing, tile-shape autotuning) is
+built once before it.  The L2 cache is flushed (256 MiB write) between steps, outside
+the timed intervals.
+
+metric: pair interactions per second over the whole solve (every FP32 and FP64 operator
+apply counted, N^2 pairs each), with the solve time (ms_per_step) and the plain-FP64
+GMRES solve time of the same system reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "pair interactions/s and GMRES solve time at 1e-10 residual, FP32-mixed vs plain FP64"
+UNIT = "pairs/s"
+FLOPS_PER_PAIR = {"sl": 28, "dl": 29, "cf": 37}   # FP32 flops per pair (FMA = 2), see the design doc
+WORKLOAD = "curved_pipe_arc90_Rc5_R1_16384wall_2048cap_gmres_ir_1e-10"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="sbq", choices=["sbq", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="CPU work bound of the oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-reps", type=int, default=20)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clk", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            if self.uuid and parts[1] != self.uuid:
+                continue
+            rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i] == "Active"})
+        loaded = [v for v in sm if mx and v > 0.3 * max(mx)] or sm
+        return {"sm_mhz": float(np.median(loaded)) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def gpu_uuid():
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_rate(seconds, rows_per_call=1024):
+    """FP64 CPU oracle on the same operator: rows of K sigma evaluated in blocks of
+    `rows_per_call` targets until `seconds` of CPU work have passed; pairs/s."""
+    import oracle
+    from paper_2310_00889_gb300 import inputs as I
+    oracle.build()
+    c = I.config2()
+    s = c["surf"]
+    eta = 1.0 / (2 * 0.2 * np.log(5.0))
+    sig = I.density(s.size, seed=12)
+    pairs, t0, k = 0.0, time.perf_counter(), 0
+    while True:
+        a = (k * rows_per_call) % s.size
+        b = min(s.size, a + rows_per_call)
+        oracle.combined(s.x, s.n, s.w, sig, s.x[:, a:b], eta, 1.0)
+        pairs += float(b - a) * s.size
+        k += 1
+        dt = time.perf_counter() - t0
+        if dt >= seconds:
+            break
+    return pairs / dt, oracle.num_threads(), dict(rows=int(pairs / s.size), seconds=dt)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2310_00889_gb300 import inputs as I
+    oracle.build()
+    c = I.config2()
+    s = c["surf"]
+    eta = 1.0 / (2 * 0.2 * np.log(5.0))
+    sig = I.density(s.size, seed=12)
+    rows = 2048
+
+    def step(k):
+        a = (k * rows) % s.size
+        oracle.combined(s.x, s.n, s.w, sig, s.x[:, a:a + rows], eta, 1.0)
+
+    for k in range(args.warmup):
+        step(k)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        step(args.warmup + k)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = rows * s.size / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nodes": s.size,
+                   "sample": "%d operator rows x %d sources per step" % (rows, s.size)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": "%d rows of the combined-field operator per step" % rows},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_2310_00889_gb300 import build as b
+    b.build()
+    from paper_2310_00889_gb300 import inputs as I
+    from paper_2310_00889_gb300 import sbq
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    c = I.config2()
+    s = c["surf"]
+    n = s.size
+    eta = sbq.slender_eta(c["slenderness"])
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+    src, nrm, w, rhs = t(s.x), t(s.n), t(s.w), t(c["rhs"])
+    stream = torch.cuda.current_stream()
+
+    t_setup = time.perf_counter()
+    op = sbq.StokesOp(src, nrm, w, eta)
+    op.autotune("fp32c")
+    op.autotune("fp64")
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t_setup) * 1e3
+    opts = dict(tol=1e-10, restart=100, inner_prec="fp32c", inner_tol=1e-5, max_outer=30,
+                use_graph=True)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    for _ in range(args.warmup):
+        x, rep = op.solve(rhs, **opts)
+    if rep["status"] != 0 or rep["rel_res"] > 1e-10:
+        raise RuntimeError("mixed solve did not converge: %s" % rep)
+
+    sampler = ClockSampler(gpu_uuid())
+    sampler.start()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    times, reps = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x, rep = op.solve(rhs, **opts)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        reps.append(rep)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = float(np.mean(times))
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    rep = reps[-1]
+    for r in reps:
+        if r["status"] != 0 or r["rel_res"] > 1e-10:
+            raise RuntimeError("a timed solve missed the tolerance: %s" % r)
+    pairs_step = float(rep["matvecs_fp64"] + rep["matvecs_low"]) * n * n
+    value = world * pairs_step / (ms * 1e-3)
+    kpm32 = op.stats("fp32c")["kernels_per_matvec"]
+    launches = rep["kernel_launches"] * args.steps
+
+    # plain FP64 GMRES solve of the same system (the comparison the metric names)
+    fp64_times = []
+    for k in range(2):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record(stream)
+        x64, rep64 = op.solve(rhs, tol=1e-10, restart=100, inner_prec="fp64", use_graph=True)
+        e1.record(stream)
+        e1.synchronize()
+        fp64_times.append(e0.elapsed_time(e1))
+    fp64_ms = float(np.min(fp64_times[1:] or fp64_times))
+    xdiff = float((x - x64).abs().max() / x64.abs().max())
+
+    # the dominant kernel on its own: compensated-FP32 combined-field pair sum, same launch
+    # configuration as inside the solve, CUDA events on the launching stream
+    sig = t(I.density(n, seed=12))
+    out = torch.empty_like(sig)
+
+    def time_matvec(prec, reps_):
+        for _ in range(2):
+            op.matvec(sig, prec=prec, out=out)
+        tl = []
+        for _ in range(reps_):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            op.matvec(sig, prec=prec, out=out)
+            e1.record(stream)
+            e1.synchronize()
+            tl.append(e0.elapsed_time(e1))
+        return float(np.mean(tl))
+
+    k32c = time_matvec("fp32c", args.kernel_reps)
+    k32 = time_matvec("fp32", args.kernel_reps)
+    k64 = time_matvec("fp64", max(3, args.kernel_reps // 4))
+    info = sbq.device_info()
+    sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        try:
+            sm_max = float(json.load(open(peaks_path)).get("sm_max_mhz", sm_max))
+        except Exception:
+            pass
+    peak = info["sms"] * info["fp32_lanes_per_sm"] * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
+    achieved = FLOPS_PER_PAIR["cf"] * float(n) * n / (k32c * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "pairsum_f32_kernel<combined field, compensated>",
+                "flops_per_pair": FLOPS_PER_PAIR["cf"], "pairs_per_launch": float(n) * n,
+                "launch_ms": k32c,
+                "peak_basis": "%d SMs x %d FP32 lanes x 2 x %.0f MHz (sm_max_mhz)" % (
+                    info["sms"], info["fp32_lanes_per_sm"], sm_max)}
+    if clocks and clocks.get("sm_mhz"):
+        roofline["frac_at_sampled_clock"] = achieved / (peak * clocks["sm_mhz"] / sm_max)
+
+    # end to end through the public API from pinned host buffers
+    hsrc, hnrm, hw, hrhs = (torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
+                            for a in (s.x, s.n, s.w, c["rhs"]))
+    e2e_times = []
+    for k in range(max(2, min(args.steps, 3)) + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xh, reph = sbq.solve_from_host(hsrc, hnrm, hw, hrhs, eta, tol=1e-10, inner_prec="fp32c",
+                                       restart=100, inner_tol=1e-5, max_outer=30, device=dev)
+        torch.cuda.synchronize()
+        if k > 0:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_s = float(np.mean(e2e_times))
+    pairs_e2e = float(reph["matvecs_fp64"] + reph["matvecs_low"]) * n * n
+    h2d = sum(a.numel() * a.element_size() for a in (hsrc, hnrm, hw, hrhs))
+    d2h = xh.numel() * xh.element_size()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, cores, smp = oracle_rate(args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "FP64 oracle rows of the same combined-field operator, %d target rows x "
+                         "%d sources in %.1f s" % (smp["rows"], n, smp["seconds"])}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nodes": n, "unknowns": 3 * n, "eta": eta,
+                       "tol": 1e-10, "inner": "fp32 compensated, FP64 refinement",
+                       "restart": 100, "graph": True,
+                       "l2": "flushed between steps (256 MiB write, outside the timed intervals)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "solve": {"mixed_ms": ms, "fp64_ms": fp64_ms, "speedup_vs_fp64": fp64_ms / ms,
+                      "mixed_iters": rep["iters"], "mixed_refinements": rep["outer_iters"],
+                      "mixed_matvecs_fp32c": rep["matvecs_low"],
+                      "mixed_matvecs_fp64": rep["matvecs_fp64"], "mixed_rel_res": rep["rel_res"],
+                      "fp64_iters": rep64["iters"], "fp64_rel_res": rep64["rel_res"],
+                      "x_rel_diff_mixed_vs_fp64": xdiff},
+            "kernels": {"fp32c_matvec_ms": k32c, "fp32_matvec_ms": k32, "fp64_matvec_ms": k64,
+                        "fp32c_pairs_per_s": n * n / (k32c * 1e-3),
+                        "fp32_pairs_per_s": n * n / (k32 * 1e-3),
+                        "fp64_pairs_per_s": n * n / (k64 * 1e-3),
+                        "tune_fp32c": op.tune("fp32c"), "tune_fp64": op.tune("fp64"),
+                        "kernels_per_matvec_fp32c": kpm32},
+            "setup_ms": setup_ms,
+            "clocks": clocks,
+            "e2e": {"value": pairs_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3,
+                    "includes": "H2D of geometry and data, operator build, graph capture, "
+                                "solve, D2H of the solution"},
+            "gpu_launches": launches,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    op.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,211 @@
+/*
+ * sbq.h — C ABI of the GB300 (sm_103a) Stokes boundary-integral hot path.
+ *
+ * The library evaluates the uncorrected Nystrom sums of the Stokes single- and
+ * double-layer velocity potentials between surface quadrature nodes and target
+ * points (Malhotra & Barnett, arXiv 2310.00889, Sec. 3.2.1,
+ * Eq. nystrom-no-correction), the combined-field operator
+ * K = diag I + D + eta S (+ sparse correction E, Eq. nystrom-correction) of the
+ * slender-body BIE (Sec. 4.1, Eq. stokes-bie-new), and solves K sigma = u0 with
+ * GMRES (plain FP64, or FP32 / compensated-FP32 inner solves with FP64
+ * iterative refinement).
+ *
+ * Kernels (viscosity 1, r = x - y, n = outward unit normal at the source y):
+ *   S(r)    = (1/8pi) (I/|r| + r r^T / |r|^3)                     Eq. stokes-sl
+ *   D(r; n) = (3/4pi) (r . n) r r^T / |r|^5                       Eq. stokes-dl
+ * The double-layer sign is the one for which the paper's identities hold:
+ * int D[e] = -e inside a closed surface, (I/2 + D) v = 0 for rigid motions
+ * (Prop. p:null), u = S[T] - D[u] inside (Appendix A).  The formula printed in
+ * Eq. stokes-dl carries the opposite sign for r = x - y.
+ *
+ * Conventions for every function:
+ *  - Arrays are FP64, structure-of-arrays: a point set of n points is 3*n
+ *    doubles x[0..n), y[0..n), z[0..n); densities and velocities likewise.
+ *  - Pointers are DEVICE pointers unless a comment says otherwise.  Inputs are
+ *    only read; outputs are overwritten.  The caller owns every buffer it passes.
+ *  - Handles (plans, operators) are owned by the library: create them with the
+ *    create calls and free them with sbq_destroy().
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  All device work
+ *    is enqueued on it; apply/matvec calls return without synchronising.
+ *  - Every function returns an sbq_status; nothing is thrown across the ABI.  On
+ *    failure sbq_last_error() (per host thread) describes the reason.
+ *  - A source whose coordinates equal a target's exactly is skipped (the
+ *    punctured sum; the correction E adds the true singular part).  The FP32
+ *    paths skip a pair whose FP32 difference is zero: they require distinct
+ *    points to differ at FP32 resolution relative to their tile, and pair
+ *    distances above ~1e-7 in the units of the input.
+ */
+#ifndef SBQ_H
+#define SBQ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SBQ_API __attribute__((visibility("default")))
+
+typedef enum {
+    SBQ_OK = 0,
+    SBQ_EINVAL = 1,       /* bad argument (null pointer, negative size, bad enum) */
+    SBQ_ECUDA = 2,        /* a CUDA runtime call or kernel launch failed */
+    SBQ_ENOCONV = 3,      /* GMRES hit its iteration cap above the tolerance */
+    SBQ_EBREAKDOWN = 4,   /* GMRES breakdown without convergence */
+    SBQ_ENONFINITE = 5,   /* a NaN or Inf appeared (input or residual) */
+    SBQ_ETIMEOUT = 6,     /* a device-side bounded wait expired (copy never landed) */
+    SBQ_ENOMEM = 7        /* device allocation failed */
+} sbq_status;
+
+typedef enum {
+    SBQ_FP64 = 0,         /* FP64 pair arithmetic and accumulation */
+    SBQ_FP32 = 1,         /* FP32 pair arithmetic, plain FP32 accumulation per work item */
+    SBQ_FP32_COMP = 2     /* FP32 pair arithmetic, TwoSum-compensated (hi, lo) accumulation */
+} sbq_prec;
+
+/* Tile shape of the pair-sum kernels.  targets per CTA = 32 * warps * r. */
+typedef struct {
+    int r;             /* targets per thread held in registers: FP32 {2,4,8}, FP64 {1,2} */
+    int warps;         /* warps per CTA: {2,4,8} (FP32), 4 (FP64) */
+    int chunk_tiles;   /* source tiles per work item; 0 = chosen from the SM count */
+} sbq_tune;
+
+/* GMRES options (Sec. 4: unpreconditioned GMRES; restart and orthogonalisation
+ * are not specified by the paper: restarted GMRES(m), classical Gram-Schmidt
+ * applied twice, Givens rotations, FP64 throughout except the inner operator). */
+typedef struct {
+    double tol;        /* stop when ||b - K x||_2 <= tol * ||b||_2 (FP64 true residual) */
+    int restart;       /* Krylov vectors per cycle m, 1..256 */
+    int max_iter;      /* cap on Arnoldi steps (summed over cycles and refinement steps) */
+    int inner_prec;    /* SBQ_FP64: plain FP64 GMRES.  SBQ_FP32 / SBQ_FP32_COMP: the inner
+                          GMRES applies K in that precision and an FP64 residual
+                          b - K x refines x (iterative refinement) */
+    double inner_tol;  /* relative tolerance of each inner solve (refinement only) */
+    int max_outer;     /* cap on refinement steps */
+    int use_graph;     /* 1: each Arnoldi step runs inside one CUDA graph whose while
+                          node repeats it on the device until the cycle ends */
+} sbq_gmres_opts;
+
+#define SBQ_HIST 64
+typedef struct {
+    int status;               /* sbq_status of the solve */
+    int iters;                /* Arnoldi steps in total */
+    int outer_iters;          /* refinement steps (mixed) or restart cycles (FP64) */
+    int matvecs_fp64;         /* FP64 operator applications */
+    int matvecs_low;          /* FP32 / compensated-FP32 operator applications */
+    int graph_used;           /* 1 if the Arnoldi steps ran inside a CUDA graph */
+    int kernel_launches;      /* kernels of this library executed by the solve (graph
+                                 replays included) */
+    double rel_res;           /* final FP64 true relative residual ||b - K x|| / ||b|| */
+    int n_hist;               /* entries used in rel_res_hist */
+    double rel_res_hist[SBQ_HIST]; /* FP64 true relative residual after each refinement
+                                      step / restart cycle, starting with x0 */
+    double time_ms;           /* wall time of the solve on the host clock */
+} sbq_gmres_report;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+SBQ_API int sbq_version(void);
+
+/* Description of the last error on this host thread ("" if none). */
+SBQ_API const char *sbq_last_error(void);
+
+/* Number of SMs of the current device and FP32 lanes per SM used for peaks. */
+SBQ_API int sbq_device_info(int *num_sms, int *fp32_lanes_per_sm, int *cc_major, int *cc_minor);
+
+/*
+ * Single-layer velocity u(x_t) = sum_{s: y_s != x_t} S(x_t - y_s) w_s sigma_s
+ * (Eq. stokes-sl discretised by Eq. nystrom-no-correction).
+ *   ns, src[3*ns], w[ns], sigma[3*ns]  sources: positions, quadrature weights, density
+ *   nt, trg[3*nt]                      targets
+ *   u[3*nt]                            output velocity (overwritten)
+ *   prec                               sbq_prec
+ * Scratch memory is taken from the device's stream-ordered pool on `stream`.
+ * Errors: SBQ_EINVAL for negative sizes, NULL pointers with a non-zero size or an
+ * unknown prec; SBQ_ECUDA / SBQ_ENOMEM from the runtime.
+ */
+SBQ_API int stokes_sl_apply(int64_t ns, const double *src, const double *w, const double *sigma,
+                            int64_t nt, const double *trg, double *u, int prec, void *stream);
+
+/* Double-layer velocity u = sum D(x_t - y_s; n_s) w_s sigma_s (Eq. stokes-dl), nrm[3*ns]
+ * unit outward normals.  Other arguments and errors as stokes_sl_apply. */
+SBQ_API int stokes_dl_apply(int64_t ns, const double *src, const double *nrm, const double *w,
+                            const double *sigma, int64_t nt, const double *trg, double *u,
+                            int prec, void *stream);
+
+/* Combined field u = sum [alpha S + beta D] w_s sigma_s in one pass (the representation
+ * of Eq. stokes-bie-rep-new is alpha = eta, beta = 1).  nrm may be NULL if beta == 0. */
+SBQ_API int stokes_combined_apply(int64_t ns, const double *src, const double *nrm,
+                                  const double *w, const double *sigma, int64_t nt,
+                                  const double *trg, double alpha, double beta, double *u,
+                                  int prec, void *stream);
+
+/*
+ * Work-list plan for a batch of independent segments (surfaces).  Segment i owns
+ * sources [seg_src_off[i], seg_src_off[i+1]) and targets [seg_trg_off[i],
+ * seg_trg_off[i+1]) of the global arrays (HOST int64 arrays of nseg+1 prefix
+ * offsets starting at 0).  Targets of a segment only see that segment's sources:
+ * the operator is block-diagonal.  All pair sums of an operator built on the plan
+ * run as ONE persistent launch over a (target tile, source-tile chunk) work-list
+ * sorted by cost, followed by a fixed-order reduction of chunk partials.
+ *   tune  HOST pointer or NULL; NULL lets stokes_op_create's autotuner choose.
+ * Errors: SBQ_EINVAL for nseg < 1 or non-monotone offsets.
+ */
+SBQ_API int batch_plan(int nseg, const int64_t *seg_src_off, const int64_t *seg_trg_off,
+                       const sbq_tune *tune, void **plan_out);
+
+/*
+ * Combined-field operator on the surface nodes (targets = sources):
+ *   K sigma = diag sigma + (D + eta S)[sigma] + E sigma           Eq. stokes-bie-new
+ * with the uncorrected pair sums and an optional sparse correction E (FP64 CSR over
+ * component-major indices c*n + node; rowptr[3n+1], col[nnz], val[nnz] device
+ * arrays; nnz = 0 and NULLs for none).  src, nrm, w: device arrays (copied into
+ * library-owned packed tiles; the caller may free them after the call).  plan:
+ * NULL for one segment, else a batch_plan handle (its offsets must cover n; the
+ * operator keeps its own copy of the plan).  The tile shape is autotuned on first
+ * use per precision unless the plan fixes it.  The operator owns all workspace of
+ * matvec and gmres_solve, so neither allocates.
+ */
+SBQ_API int stokes_op_create(int64_t n, const double *src, const double *nrm, const double *w,
+                             double eta, double diag, int64_t nnz, const int64_t *rowptr,
+                             const int64_t *col, const double *val, const void *plan,
+                             void **op_out);
+
+/* out = K sigma (device arrays of 3*n doubles) in precision prec, on `stream`. */
+SBQ_API int stokes_matvec(const void *op, const double *sigma, double *out, int prec,
+                          void *stream);
+
+/*
+ * Solve K x = rhs (device arrays of 3*n doubles).  x holds x0 on entry and the
+ * solution on exit.  o and rep are HOST pointers (rep may be NULL).  Returns
+ * SBQ_OK on convergence, SBQ_ENOCONV when max_iter / max_outer is reached first
+ * (x then holds the best iterate), SBQ_ENONFINITE if a residual is not finite.
+ * Synchronises `stream` (it reads residual norms back once per cycle).
+ */
+SBQ_API int gmres_solve(const void *op, const double *rhs, double *x, const sbq_gmres_opts *o,
+                        sbq_gmres_report *rep, void *stream);
+
+/* Autotune the tile shape of op for precision prec by timing candidate shapes on the
+ * operator's own data; the winner is stored in op and in a process-wide cache keyed
+ * by problem shape, and copied to *out if out is not NULL. */
+SBQ_API int sbq_autotune(void *op, int prec, sbq_tune *out, void *stream);
+
+/* Tile shape currently used by op for precision prec (HOST out pointer). */
+SBQ_API int sbq_op_tune(const void *op, int prec, sbq_tune *out);
+
+/* Launch statistics of the last matvec of op in precision prec: number of kernels
+ * launched and the number of pair interactions evaluated (HOST out pointers). */
+SBQ_API int sbq_op_stats(const void *op, int prec, int *kernels_per_matvec,
+                         double *pairs_per_matvec);
+
+/* Synchronise `stream` and report (then clear) the device error word set by bounded
+ * waits inside kernels: SBQ_ETIMEOUT if a wait expired since the last check. */
+SBQ_API int sbq_check_device(void *stream);
+
+/* Free a plan or operator handle (NULL is ignored). */
+SBQ_API void sbq_destroy(void *handle);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SBQ_H */

@@ -1,0 +1,355 @@
+// extern "C" entry points of libsbq (declared in include/sbq.h): argument checks,
+// handle management, dispatch to the engine.
+#include "engine.h"
+
+#include <cmath>
+#include <new>
+
+namespace sbq {
+const char *last_error_cstr();
+int gmres_solve_impl(Op *op, const double *b, double *x, const sbq_gmres_opts &o,
+                     sbq_gmres_report &rep, cudaStream_t s);
+int op_autotune(Op *op, int prec, cudaStream_t s);
+}  // namespace sbq
+
+using namespace sbq;
+
+namespace {
+
+bool prec_ok(int prec) { return prec == SBQ_FP64 || prec == SBQ_FP32 || prec == SBQ_FP32_COMP; }
+
+int fail(int code, const std::string &msg)
+{
+    set_error(msg);
+    return code;
+}
+
+// Generic apply: u = alpha S[sigma] + beta D[sigma] at the targets.
+int apply_generic(int64_t ns, const double *src, const double *nrm, const double *w,
+                  const double *sigma, int64_t nt, const double *trg, double alpha, double beta,
+                  double *u, int prec, void *stream)
+{
+    clear_error();
+    if (ns < 0 || nt < 0)
+        return fail(SBQ_EINVAL, "negative size");
+    if (!prec_ok(prec))
+        return fail(SBQ_EINVAL, "unknown precision");
+    if (!std::isfinite(alpha) || !std::isfinite(beta))
+        return fail(SBQ_EINVAL, "non-finite prefactor");
+    if (nt > 0 && (!trg || !u))
+        return fail(SBQ_EINVAL, "null target or output pointer");
+    if (ns > 0 && nt > 0 && (!src || !w || !sigma))
+        return fail(SBQ_EINVAL, "null source, weight or density pointer");
+    if (ns > 0 && nt > 0 && beta != 0.0 && !nrm)
+        return fail(SBQ_EINVAL, "double layer needs normals");
+    if (ns > (1LL << 31) || nt > (1LL << 31))
+        return fail(SBQ_EINVAL, "size above 2^31");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (nt == 0)
+        return SBQ_OK;
+    if (ns == 0 || (alpha == 0.0 && beta == 0.0)) {
+        SBQ_CUDA(cudaMemsetAsync(u, 0, 3 * static_cast<size_t>(nt) * sizeof(double), s));
+        return SBQ_OK;
+    }
+    int kind;
+    double scale, kappa;
+    kind_and_scale(alpha, beta, &kind, &scale, &kappa);
+    const int layout = (prec == SBQ_FP64) ? SBQ_FP64 : SBQ_FP32;
+    AsyncAllocScope scope(s);
+    SrcPack sp;
+    TrgSet ts;
+    std::vector<int64_t> soff = {0, ns}, toff = {0, nt};
+    SBQ_TRY(build_src_pack(sp, layout, soff, src, kind == KIND_SL ? nullptr : nrm, ns, s));
+    SBQ_TRY(build_trg_set(ts, kind, prec, default_tune(prec, nt), sp, toff, trg, nt, soff, s));
+    SBQ_TRY(run_pairsum(kind, prec, sp, ts, w, sigma, ns, trg, nt, u, scale, kappa, 0.0, nullptr, s));
+    return SBQ_OK;
+}
+
+Op *as_op(const void *h)
+{
+    Op *op = static_cast<Op *>(const_cast<void *>(h));
+    if (!op || op->magic != OP_MAGIC)
+        return nullptr;
+    return op;
+}
+
+}  // namespace
+
+extern "C" {
+
+SBQ_API int sbq_version(void) { return 100; }
+
+SBQ_API const char *sbq_last_error(void) { return last_error_cstr(); }
+
+SBQ_API int sbq_device_info(int *num_sms, int *fp32_lanes_per_sm, int *cc_major, int *cc_minor)
+{
+    clear_error();
+    int dev = 0;
+    SBQ_CUDA(cudaGetDevice(&dev));
+    const DeviceProps &p = device_props();
+    if (num_sms)
+        *num_sms = p.sms;
+    if (fp32_lanes_per_sm)
+        *fp32_lanes_per_sm = 128;   // FP32 lanes per SM on sm_100-class parts
+    if (cc_major)
+        *cc_major = p.cc_major;
+    if (cc_minor)
+        *cc_minor = p.cc_minor;
+    return SBQ_OK;
+}
+
+SBQ_API int stokes_sl_apply(int64_t ns, const double *src, const double *w, const double *sigma,
+                            int64_t nt, const double *trg, double *u, int prec, void *stream)
+{
+    return apply_generic(ns, src, nullptr, w, sigma, nt, trg, 1.0, 0.0, u, prec, stream);
+}
+
+SBQ_API int stokes_dl_apply(int64_t ns, const double *src, const double *nrm, const double *w,
+                            const double *sigma, int64_t nt, const double *trg, double *u,
+                            int prec, void *stream)
+{
+    return apply_generic(ns, src, nrm, w, sigma, nt, trg, 0.0, 1.0, u, prec, stream);
+}
+
+SBQ_API int stokes_combined_apply(int64_t ns, const double *src, const double *nrm,
+                                  const double *w, const double *sigma, int64_t nt,
+                                  const double *trg, double alpha, double beta, double *u,
+                                  int prec, void *stream)
+{
+    return apply_generic(ns, src, nrm, w, sigma, nt, trg, alpha, beta, u, prec, stream);
+}
+
+SBQ_API int batch_plan(int nseg, const int64_t *seg_src_off, const int64_t *seg_trg_off,
+                       const sbq_tune *tune, void **plan_out)
+{
+    clear_error();
+    if (!plan_out)
+        return fail(SBQ_EINVAL, "null plan_out");
+    *plan_out = nullptr;
+    if (nseg < 1 || !seg_src_off || !seg_trg_off)
+        return fail(SBQ_EINVAL, "nseg < 1 or null offsets");
+    if (seg_src_off[0] != 0 || seg_trg_off[0] != 0)
+        return fail(SBQ_EINVAL, "offsets must start at 0");
+    for (int i = 0; i < nseg; ++i)
+        if (seg_src_off[i + 1] < seg_src_off[i] || seg_trg_off[i + 1] < seg_trg_off[i])
+            return fail(SBQ_EINVAL, "offsets must be non-decreasing");
+    if (tune && tune->r != 0 && !pairsum_shape_supported(SBQ_FP32, tune->r, tune->warps))
+        return fail(SBQ_EINVAL, "unsupported tile shape");
+    PlanH *p = new (std::nothrow) PlanH();
+    if (!p)
+        return fail(SBQ_ENOMEM, "out of host memory");
+    p->nseg = nseg;
+    p->src_off.assign(seg_src_off, seg_src_off + nseg + 1);
+    p->trg_off.assign(seg_trg_off, seg_trg_off + nseg + 1);
+    if (tune && tune->r != 0) {
+        p->has_tune = true;
+        p->tune = *tune;
+    }
+    *plan_out = p;
+    return SBQ_OK;
+}
+
+SBQ_API int stokes_op_create(int64_t n, const double *src, const double *nrm, const double *w,
+                             double eta, double diag, int64_t nnz, const int64_t *rowptr,
+                             const int64_t *col, const double *val, const void *plan,
+                             void **op_out)
+{
+    clear_error();
+    if (!op_out)
+        return fail(SBQ_EINVAL, "null op_out");
+    *op_out = nullptr;
+    if (n < 0 || nnz < 0)
+        return fail(SBQ_EINVAL, "negative size");
+    if (n > (1LL << 31) / 3)
+        return fail(SBQ_EINVAL, "n above 2^31 / 3");
+    if (n > 0 && (!src || !nrm || !w))
+        return fail(SBQ_EINVAL, "null source, normal or weight pointer");
+    if (nnz > 0 && (!rowptr || !col || !val))
+        return fail(SBQ_EINVAL, "null CSR pointer");
+    if (!std::isfinite(eta) || !std::isfinite(diag))
+        return fail(SBQ_EINVAL, "non-finite eta or diag");
+    const PlanH *pl = static_cast<const PlanH *>(plan);
+    if (pl && pl->magic != PLAN_MAGIC)
+        return fail(SBQ_EINVAL, "plan is not a batch_plan handle");
+    if (pl) {
+        if (pl->src_off.back() != n || pl->trg_off.back() != n)
+            return fail(SBQ_EINVAL, "plan offsets do not cover the n nodes");
+        for (int i = 0; i <= pl->nseg; ++i)
+            if (pl->src_off[i] != pl->trg_off[i])
+                return fail(SBQ_EINVAL, "operator plans need equal source and target offsets");
+    }
+    Op *op = new (std::nothrow) Op();
+    if (!op)
+        return fail(SBQ_ENOMEM, "out of host memory");
+    auto bail = [&](int st) {
+        delete op;
+        return st;
+    };
+    cudaGetDevice(&op->device);
+    op->n = n;
+    op->eta = eta;
+    op->diag = diag;
+    op->nnz = nnz;
+    if (pl)
+        op->plan = *pl;
+    else {
+        op->plan.nseg = 1;
+        op->plan.src_off = {0, n};
+        op->plan.trg_off = {0, n};
+    }
+    const size_t vb = 3 * static_cast<size_t>(n) * sizeof(double);
+    int st = SBQ_OK;
+    if ((st = op->src.alloc(vb)) != SBQ_OK) return bail(st);
+    if ((st = op->nrm.alloc(vb)) != SBQ_OK) return bail(st);
+    if ((st = op->w.alloc(static_cast<size_t>(n) * sizeof(double))) != SBQ_OK) return bail(st);
+    if (n > 0) {
+        cudaError_t e = cudaMemcpy(op->src.p, src, vb, cudaMemcpyDeviceToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(op->nrm.p, nrm, vb, cudaMemcpyDeviceToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(op->w.p, w, static_cast<size_t>(n) * sizeof(double),
+                           cudaMemcpyDeviceToDevice);
+        if (e != cudaSuccess) return bail(cuda_status(e, "cudaMemcpy (operator geometry)"));
+    }
+    if (nnz > 0) {
+        if ((st = op->rowptr.alloc((3 * static_cast<size_t>(n) + 1) * sizeof(int64_t))) != SBQ_OK)
+            return bail(st);
+        if ((st = op->col.alloc(static_cast<size_t>(nnz) * sizeof(int64_t))) != SBQ_OK) return bail(st);
+        if ((st = op->val.alloc(static_cast<size_t>(nnz) * sizeof(double))) != SBQ_OK) return bail(st);
+        cudaError_t e = cudaMemcpy(op->rowptr.p, rowptr, (3 * n + 1) * sizeof(int64_t),
+                                   cudaMemcpyDeviceToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(op->col.p, col, nnz * sizeof(int64_t), cudaMemcpyDeviceToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(op->val.p, val, nnz * sizeof(double), cudaMemcpyDeviceToDevice);
+        if (e != cudaSuccess) return bail(cuda_status(e, "cudaMemcpy (correction)"));
+    }
+    cudaStream_t s = nullptr;
+    if ((st = build_src_pack(op->sp32, SBQ_FP32, op->plan.src_off, op->src.as<double>(),
+                             op->nrm.as<double>(), n, s)) != SBQ_OK)
+        return bail(st);
+    if ((st = build_src_pack(op->sp64, SBQ_FP64, op->plan.src_off, op->src.as<double>(),
+                             op->nrm.as<double>(), n, s)) != SBQ_OK)
+        return bail(st);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return bail(cuda_status(e, "stokes_op_create"));
+    *op_out = op;
+    return SBQ_OK;
+}
+
+SBQ_API int stokes_matvec(const void *oph, const double *sigma, double *out, int prec, void *stream)
+{
+    clear_error();
+    Op *op = as_op(oph);
+    if (!op)
+        return fail(SBQ_EINVAL, "not an operator handle");
+    if (!prec_ok(prec))
+        return fail(SBQ_EINVAL, "unknown precision");
+    if (op->n > 0 && (!sigma || !out))
+        return fail(SBQ_EINVAL, "null density or output pointer");
+    std::lock_guard<std::mutex> lk(op->mu);
+    return op_matvec(op, sigma, out, prec, static_cast<cudaStream_t>(stream));
+}
+
+SBQ_API int gmres_solve(const void *oph, const double *rhs, double *x, const sbq_gmres_opts *o,
+                        sbq_gmres_report *rep, void *stream)
+{
+    clear_error();
+    Op *op = as_op(oph);
+    if (!op)
+        return fail(SBQ_EINVAL, "not an operator handle");
+    if (!o)
+        return fail(SBQ_EINVAL, "null options");
+    if (op->n > 0 && (!rhs || !x))
+        return fail(SBQ_EINVAL, "null rhs or solution pointer");
+    if (!(o->tol > 0.0) || o->restart < 1 || o->restart > 256 || o->max_iter < 1 ||
+        !prec_ok(o->inner_prec))
+        return fail(SBQ_EINVAL, "bad GMRES options (tol > 0, 1 <= restart <= 256, max_iter >= 1)");
+    if (o->inner_prec != SBQ_FP64 && (!(o->inner_tol > 0.0) || o->inner_tol >= 1.0 || o->max_outer < 1))
+        return fail(SBQ_EINVAL, "bad refinement options (0 < inner_tol < 1, max_outer >= 1)");
+    sbq_gmres_report local{};
+    sbq_gmres_report &r = rep ? *rep : local;
+    if (op->n == 0) {
+        r = sbq_gmres_report{};
+        return SBQ_OK;
+    }
+    std::lock_guard<std::mutex> lk(op->mu);
+    const int st = gmres_solve_impl(op, rhs, x, *o, r, static_cast<cudaStream_t>(stream));
+    r.status = st;
+    return st;
+}
+
+SBQ_API int sbq_autotune(void *oph, int prec, sbq_tune *out, void *stream)
+{
+    clear_error();
+    Op *op = as_op(oph);
+    if (!op)
+        return fail(SBQ_EINVAL, "not an operator handle");
+    if (!prec_ok(prec))
+        return fail(SBQ_EINVAL, "unknown precision");
+    std::lock_guard<std::mutex> lk(op->mu);
+    if (op->n > 0)
+        SBQ_TRY(op_autotune(op, prec, static_cast<cudaStream_t>(stream)));
+    if (out && op->ts[prec])
+        *out = op->ts[prec]->tune;
+    return SBQ_OK;
+}
+
+SBQ_API int sbq_op_tune(const void *oph, int prec, sbq_tune *out)
+{
+    clear_error();
+    Op *op = as_op(oph);
+    if (!op || !out || !prec_ok(prec))
+        return fail(SBQ_EINVAL, "bad arguments");
+    if (!op->ts[prec])
+        return fail(SBQ_EINVAL, "no tile shape chosen yet for this precision");
+    *out = op->ts[prec]->tune;
+    return SBQ_OK;
+}
+
+SBQ_API int sbq_op_stats(const void *oph, int prec, int *kernels_per_matvec, double *pairs_per_matvec)
+{
+    clear_error();
+    Op *op = as_op(oph);
+    if (!op || !prec_ok(prec))
+        return fail(SBQ_EINVAL, "bad arguments");
+    if (kernels_per_matvec)
+        *kernels_per_matvec = op_kernels_per_matvec(op, prec);
+    if (pairs_per_matvec)
+        *pairs_per_matvec = op->ts[prec] ? op->ts[prec]->pairs : 0.0;
+    return SBQ_OK;
+}
+
+SBQ_API int sbq_check_device(void *stream)
+{
+    clear_error();
+    SBQ_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    int *err = device_error_word();
+    if (!err)
+        return fail(SBQ_ENOMEM, "cannot allocate the device error word");
+    int h = 0;
+    SBQ_CUDA(cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h != 0) {
+        SBQ_CUDA(cudaMemset(err, 0, sizeof(int)));
+        if (h & DEV_ERR_TIMEOUT)
+            return fail(SBQ_ETIMEOUT, "a device-side bounded wait expired");
+    }
+    return SBQ_OK;
+}
+
+SBQ_API void sbq_destroy(void *handle)
+{
+    if (!handle)
+        return;
+    const uint32_t magic = *static_cast<const uint32_t *>(handle);
+    if (magic == OP_MAGIC) {
+        Op *op = static_cast<Op *>(handle);
+        op->magic = 0;
+        delete op;
+    } else if (magic == PLAN_MAGIC) {
+        PlanH *p = static_cast<PlanH *>(handle);
+        p->magic = 0;
+        delete p;
+    }
+}
+
+}  // extern "C"

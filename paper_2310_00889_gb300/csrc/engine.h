@@ -1,0 +1,107 @@
+// Host-side engine of libsbq: tile tables, work lists, operator handles.
+#pragma once
+
+#include "sbq_common.cuh"
+
+#include <memory>
+#include <mutex>
+
+namespace sbq {
+
+constexpr uint32_t PLAN_MAGIC = 0x53425150u;   // "SBQP"
+constexpr uint32_t OP_MAGIC = 0x5342514fu;     // "SBQO"
+
+// Device buffer owned by the engine (cudaMalloc / cudaFree).
+// Allocations made while an AsyncAllocScope is alive on this host thread are stream
+// ordered (cudaMallocAsync / cudaFreeAsync on that stream); others use cudaMalloc.
+struct AsyncAllocScope {
+    explicit AsyncAllocScope(cudaStream_t s);
+    ~AsyncAllocScope();
+    cudaStream_t prev;
+    bool prev_on;
+};
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    bool async = false;
+    cudaStream_t stream = nullptr;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    int alloc(size_t n);
+    void release();
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+struct PlanH {
+    uint32_t magic = PLAN_MAGIC;
+    int nseg = 0;
+    std::vector<int64_t> src_off, trg_off;
+    bool has_tune = false;
+    sbq_tune tune{};
+};
+
+// Source tiles of one precision layout (FP32: TS_F32 float4 x3; FP64: TS_F64 doubles x9).
+struct SrcPack {
+    int layout = -1;            // SBQ_FP32 (shared by FP32 and FP32_COMP) or SBQ_FP64
+    int TS = 0;
+    int n_stiles = 0;
+    std::vector<int> seg_tile_begin, seg_tile_count;
+    DevBuf stiles, spack;
+};
+
+// Target tiles + work list for one tile shape.
+struct TrgSet {
+    sbq_tune tune{};
+    int TT = 0;
+    int n_ttiles = 0;
+    int n_items = 0;
+    int grid = 0;
+    bool needs_reduce = false;
+    double pairs = 0.0;         // pair interactions per apply (valid members only)
+    DevBuf ttiles, tpack, items, partial, counter;
+};
+
+struct Op {
+    uint32_t magic = OP_MAGIC;
+    int device = 0;
+    long long n = 0;
+    double eta = 0.0, diag = 0.5;
+    long long nnz = 0;
+    DevBuf src, nrm, w;                // library copies (SoA)
+    DevBuf rowptr, col, val;           // CSR correction
+    PlanH plan;                        // segments (one segment if none given)
+    SrcPack sp32, sp64;
+    std::unique_ptr<TrgSet> ts[3];     // per sbq_prec
+    bool tuned[3] = {false, false, false};
+    std::mutex mu;
+    struct GmresWS *gm = nullptr;      // solver workspace (gmres.cu)
+    ~Op();
+};
+
+// Segment layout helpers.
+int build_src_pack(SrcPack &sp, int layout, const std::vector<int64_t> &src_off, const double *src,
+                   const double *nrm, long long ns, cudaStream_t s);
+int build_trg_set(TrgSet &ts, int kind, int prec, const sbq_tune &tune, const SrcPack &sp,
+                  const std::vector<int64_t> &trg_off, const double *trg, long long nt,
+                  const std::vector<int64_t> &src_off, cudaStream_t s);
+
+// One pair-sum apply: out = scale * sum(...) [+ diag * diag_sigma].
+int run_pairsum(int kind, int prec, const SrcPack &sp, const TrgSet &ts, const double *w,
+                const double *sigma, long long ns, const double *trg, long long nt, double *out,
+                double scale, double kappa, double diag, const double *diag_sigma, cudaStream_t s);
+
+// Operator pieces used by the solver.
+int op_matvec(Op *op, const double *sigma, double *out, int prec, cudaStream_t s);
+int op_ensure_tuned(Op *op, int prec, cudaStream_t s);
+int op_kernels_per_matvec(const Op *op, int prec);
+
+// Kind and prefactors of alpha S + beta D.
+void kind_and_scale(double alpha, double beta, int *kind, double *scale, double *kappa);
+
+sbq_tune default_tune(int prec, long long nt);
+int gmres_destroy(struct GmresWS *ws);
+
+}  // namespace sbq

@@ -1,0 +1,327 @@
+// Packing, reduction and sparse-correction kernels of the pair-sum engine.
+//
+//  * source geometry pack (once per operator): positions relative to the tile centre
+//    (FP32) or absolute (FP64), unit normals, padding of ragged tiles, tile radius;
+//  * density pack (every apply): q = w sigma, the quadrature weight of paper
+//    Eq. nystrom-no-correction folded into the density;
+//  * target pack (FP32, once per tile shape): positions relative to the target tile
+//    centre;
+//  * fixed-order reduction of chunk partials with the prefactor and the diagonal term
+//    diag * sigma of K = I/2 + D + eta S (Eq. stokes-bie-new);
+//  * CSR apply y += E x of the local correction (Eq. nystrom-correction).
+#include "sbq_common.cuh"
+
+namespace sbq {
+
+namespace {
+
+// Block-wide max of a non-negative double (blockDim.x a multiple of 32, <= 1024).
+__device__ double block_max(double v, double *red)
+{
+    for (int o = 16; o > 0; o >>= 1)
+        v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0)
+        red[warp] = v;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    v = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+    if (warp == 0)
+        for (int o = 16; o > 0; o >>= 1)
+            v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;   // valid in thread 0
+}
+
+// Radius rounded up so that the FP32 value bounds every FP64 distance.
+__device__ float radius_up(double d2max)
+{
+    const double r = sqrt(d2max) * (1.0 + 1.0e-6) + 1.0e-300;
+    return __double2float_ru(r);
+}
+
+__global__ void pack_src_geom_f32(const double *__restrict__ src, const double *__restrict__ nrm,
+                                  long long ns, TileInfo *stiles, float4 *spack)
+{
+    constexpr int TS = TS_F32;
+    __shared__ double red[32];
+    const int k = blockIdx.x, j = threadIdx.x;
+    const long long begin = stiles[k].begin;
+    const int count = stiles[k].count;
+    const long long c = begin + min(TS / 2, count - 1);
+    const double cx = src[c], cy = src[ns + c], cz = src[2 * ns + c];
+    float4 *tile = spack + static_cast<size_t>(k) * 3 * TS;
+    double d2 = 0.0;
+    if (j < count) {
+        const long long s = begin + j;
+        const double dx = src[s] - cx, dy = src[ns + s] - cy, dz = src[2 * ns + s] - cz;
+        tile[j] = make_float4(static_cast<float>(dx), static_cast<float>(dy),
+                              static_cast<float>(dz), 0.0f);
+        tile[2 * TS + j] = nrm ? make_float4(static_cast<float>(nrm[s]),
+                                             static_cast<float>(nrm[ns + s]),
+                                             static_cast<float>(nrm[2 * ns + s]), 0.0f)
+                               : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        d2 = dx * dx + dy * dy + dz * dz;
+    } else {
+        tile[j] = make_float4(PAD_POS_F32, PAD_POS_F32, PAD_POS_F32, 0.0f);
+        tile[TS + j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        tile[2 * TS + j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    const double m = block_max(d2, red);
+    if (j == 0) {
+        stiles[k].cx = cx;
+        stiles[k].cy = cy;
+        stiles[k].cz = cz;
+        stiles[k].rad = radius_up(m);
+    }
+}
+
+__global__ void pack_src_geom_f64(const double *__restrict__ src, const double *__restrict__ nrm,
+                                  long long ns, TileInfo *stiles, double *spack)
+{
+    constexpr int TS = TS_F64;
+    __shared__ double red[32];
+    const int k = blockIdx.x, j = threadIdx.x;
+    const long long begin = stiles[k].begin;
+    const int count = stiles[k].count;
+    const long long c = begin + min(TS / 2, count - 1);
+    const double cx = src[c], cy = src[ns + c], cz = src[2 * ns + c];
+    double *tile = spack + static_cast<size_t>(k) * 9 * TS;
+    double d2 = 0.0;
+    if (j < count) {
+        const long long s = begin + j;
+        tile[j] = src[s];
+        tile[TS + j] = src[ns + s];
+        tile[2 * TS + j] = src[2 * ns + s];
+        tile[6 * TS + j] = nrm ? nrm[s] : 0.0;
+        tile[7 * TS + j] = nrm ? nrm[ns + s] : 0.0;
+        tile[8 * TS + j] = nrm ? nrm[2 * ns + s] : 0.0;
+        const double dx = src[s] - cx, dy = src[ns + s] - cy, dz = src[2 * ns + s] - cz;
+        d2 = dx * dx + dy * dy + dz * dz;
+    } else {
+        tile[j] = tile[TS + j] = tile[2 * TS + j] = PAD_POS_F64;
+        tile[3 * TS + j] = tile[4 * TS + j] = tile[5 * TS + j] = 0.0;
+        tile[6 * TS + j] = tile[7 * TS + j] = tile[8 * TS + j] = 0.0;
+    }
+    const double m = block_max(d2, red);
+    if (j == 0) {
+        stiles[k].cx = cx;
+        stiles[k].cy = cy;
+        stiles[k].cz = cz;
+        stiles[k].rad = radius_up(m);
+    }
+}
+
+__global__ void pack_src_q_f32(const double *__restrict__ w, const double *__restrict__ sigma,
+                               long long ns, const TileInfo *__restrict__ stiles, float4 *spack,
+                               int *counter)
+{
+    constexpr int TS = TS_F32;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && counter)
+        *counter = 0;
+    const int k = blockIdx.x, j = threadIdx.x;
+    const long long begin = stiles[k].begin;
+    const int count = stiles[k].count;
+    float4 q = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (j < count) {
+        const long long s = begin + j;
+        const double ww = w[s];
+        q = make_float4(static_cast<float>(ww * sigma[s]), static_cast<float>(ww * sigma[ns + s]),
+                        static_cast<float>(ww * sigma[2 * ns + s]), 0.0f);
+    }
+    spack[static_cast<size_t>(k) * 3 * TS + TS + j] = q;
+}
+
+__global__ void pack_src_q_f64(const double *__restrict__ w, const double *__restrict__ sigma,
+                               long long ns, const TileInfo *__restrict__ stiles, double *spack,
+                               int *counter)
+{
+    constexpr int TS = TS_F64;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && counter)
+        *counter = 0;
+    const int k = blockIdx.x, j = threadIdx.x;
+    const long long begin = stiles[k].begin;
+    const int count = stiles[k].count;
+    double *tile = spack + static_cast<size_t>(k) * 9 * TS;
+    double qx = 0.0, qy = 0.0, qz = 0.0;
+    if (j < count) {
+        const long long s = begin + j;
+        const double ww = w[s];
+        qx = ww * sigma[s];
+        qy = ww * sigma[ns + s];
+        qz = ww * sigma[2 * ns + s];
+    }
+    tile[3 * TS + j] = qx;
+    tile[4 * TS + j] = qy;
+    tile[5 * TS + j] = qz;
+}
+
+__global__ void pack_trg_f32(const double *__restrict__ trg, long long nt, TileInfo *ttiles, int TT,
+                             float4 *tpack)
+{
+    __shared__ double red[32];
+    const int k = blockIdx.x;
+    const long long begin = ttiles[k].begin;
+    const int count = ttiles[k].count;
+    const long long c = begin + min(TT / 2, count - 1);
+    const double cx = trg[c], cy = trg[nt + c], cz = trg[2 * nt + c];
+    double d2 = 0.0;
+    for (int j = threadIdx.x; j < TT; j += blockDim.x) {
+        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (j < count) {
+            const long long t = begin + j;
+            const double dx = trg[t] - cx, dy = trg[nt + t] - cy, dz = trg[2 * nt + t] - cz;
+            v = make_float4(static_cast<float>(dx), static_cast<float>(dy), static_cast<float>(dz),
+                            0.0f);
+            d2 = fmax(d2, dx * dx + dy * dy + dz * dz);
+        }
+        tpack[static_cast<size_t>(k) * TT + j] = v;
+    }
+    const double m = block_max(d2, red);
+    if (threadIdx.x == 0) {
+        ttiles[k].cx = cx;
+        ttiles[k].cy = cy;
+        ttiles[k].cz = cz;
+        ttiles[k].rad = radius_up(m);
+    }
+}
+
+__global__ void reduce_partials_kernel(const TileInfo *__restrict__ ttiles, int TT,
+                                       const double *__restrict__ partial, long long nt,
+                                       double *out, double scale, double diag,
+                                       const double *__restrict__ diag_sigma)
+{
+    const TileInfo ti = ttiles[blockIdx.x];
+    if (ti.slot_begin < 0)
+        return;
+    for (int loc = threadIdx.x; loc < ti.count; loc += blockDim.x) {
+        const long long t = ti.begin + loc;
+        for (int c = 0; c < 3; ++c) {
+            double s = 0.0;
+            for (int q = 0; q < ti.slot_count; ++q)
+                s += partial[(static_cast<size_t>(ti.slot_begin + q) * 3 + c) * TT + loc];
+            double o = scale * s;
+            if (diag_sigma)
+                o += diag * diag_sigma[c * nt + t];
+            out[c * nt + t] = o;
+        }
+    }
+}
+
+__global__ void csr_apply_kernel(long long nrows, const int64_t *__restrict__ rowptr,
+                                 const int64_t *__restrict__ col, const double *__restrict__ val,
+                                 const double *__restrict__ x, double *y)
+{
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < nrows;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        double acc = 0.0;
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k)
+            acc += val[k] * x[col[k]];
+        y[i] += acc;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_pack_src_geom(int prec, const double *src, const double *nrm, long long ns,
+                                 TileInfo *stiles, int n_stiles, void *spack, cudaStream_t s)
+{
+    if (n_stiles <= 0)
+        return cudaSuccess;
+    if (prec == SBQ_FP64)
+        pack_src_geom_f64<<<n_stiles, TS_F64, 0, s>>>(src, nrm, ns, stiles,
+                                                       static_cast<double *>(spack));
+    else
+        pack_src_geom_f32<<<n_stiles, TS_F32, 0, s>>>(src, nrm, ns, stiles,
+                                                       static_cast<float4 *>(spack));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_src_q(int prec, const double *w, const double *sigma, long long ns,
+                              const TileInfo *stiles, int n_stiles, void *spack, int *counter,
+                              cudaStream_t s)
+{
+    if (n_stiles <= 0)
+        return cudaSuccess;
+    if (prec == SBQ_FP64)
+        pack_src_q_f64<<<n_stiles, TS_F64, 0, s>>>(w, sigma, ns, stiles,
+                                                    static_cast<double *>(spack), counter);
+    else
+        pack_src_q_f32<<<n_stiles, TS_F32, 0, s>>>(w, sigma, ns, stiles,
+                                                    static_cast<float4 *>(spack), counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_trg(const double *trg, long long nt, TileInfo *ttiles, int n_ttiles, int TT,
+                            float4 *tpack, cudaStream_t s)
+{
+    if (n_ttiles <= 0)
+        return cudaSuccess;
+    pack_trg_f32<<<n_ttiles, 256, 0, s>>>(trg, nt, ttiles, TT, tpack);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_partials(const TileInfo *ttiles, int n_ttiles, int TT,
+                                   const double *partial, long long nt, double *out, double scale,
+                                   double diag, const double *diag_sigma, cudaStream_t s)
+{
+    if (n_ttiles <= 0)
+        return cudaSuccess;
+    reduce_partials_kernel<<<n_ttiles, 256, 0, s>>>(ttiles, TT, partial, nt, out, scale, diag,
+                                                     diag_sigma);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_csr_apply(long long nrows, const int64_t *rowptr, const int64_t *col,
+                             const double *val, const double *x, double *y, cudaStream_t s)
+{
+    if (nrows <= 0)
+        return cudaSuccess;
+    long long blocks = (nrows + 255) / 256;
+    if (blocks > 4096)
+        blocks = 4096;
+    csr_apply_kernel<<<static_cast<int>(blocks), 256, 0, s>>>(nrows, rowptr, col, val, x, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pairsum_sl(int, int, int, int, const PairsumParams &, cudaStream_t);
+cudaError_t launch_pairsum_dl(int, int, int, int, const PairsumParams &, cudaStream_t);
+cudaError_t launch_pairsum_cf(int, int, int, int, const PairsumParams &, cudaStream_t);
+int occupancy_pairsum_sl(int, int, int);
+int occupancy_pairsum_dl(int, int, int);
+int occupancy_pairsum_cf(int, int, int);
+
+cudaError_t launch_pairsum(int kind, int prec, int R, int W, int grid, const PairsumParams &p,
+                           cudaStream_t s)
+{
+    switch (kind) {
+    case KIND_SL: return launch_pairsum_sl(prec, R, W, grid, p, s);
+    case KIND_DL: return launch_pairsum_dl(prec, R, W, grid, p, s);
+    case KIND_CF: return launch_pairsum_cf(prec, R, W, grid, p, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+int pairsum_blocks_per_sm(int kind, int prec, int R, int W)
+{
+    switch (kind) {
+    case KIND_SL: return occupancy_pairsum_sl(prec, R, W);
+    case KIND_DL: return occupancy_pairsum_dl(prec, R, W);
+    case KIND_CF: return occupancy_pairsum_cf(prec, R, W);
+    default: return 0;
+    }
+}
+
+bool pairsum_shape_supported(int prec, int R, int W)
+{
+    if (prec == SBQ_FP64)
+        return W == 4 && (R == 1 || R == 2);
+    return (W == 4 && (R == 2 || R == 4 || R == 8)) || (W == 8 && R == 4);
+}
+
+size_t pairsum_smem_bytes(int prec)
+{
+    return prec == SBQ_FP64 ? 2 * 9 * TS_F64 * sizeof(double) : 2 * 3 * TS_F32 * sizeof(float4);
+}
+
+}  // namespace sbq

@@ -1,0 +1,484 @@
+// Pair-sum kernels: the uncorrected Nystrom sum of paper Eq. nystrom-no-correction for
+// the Stokes single layer (Eq. stokes-sl), double layer (Eq. stokes-dl, sign such that
+// int D[e] = -e inside) and their combination eta S + D (Eq. stokes-bie-new).
+//
+// Work decomposition (both precisions): a persistent grid claims work items
+// {target tile, first source tile, end source tile, partial slot} from a list with an
+// atomic counter.  A target tile holds TT = 32 * W * R targets; thread (warp w, lane l)
+// keeps targets w*32*R + r*32 + l (r < R) in registers.  Source tiles stream through
+// a two-stage shared-memory ring filled by one bulk async copy per tile (TMA engine)
+// that completes on an mbarrier; every thread reads each source by broadcast and
+// applies it to its R targets.  An item writes its sums straight to the output when it
+// covers the whole source range of its target tile, else to its partial slot, which a
+// fixed-order reduction adds up later (deterministic results).
+//
+// FP32 path: targets and sources are stored relative to their tile centre (FP64
+// subtraction, then rounding), and per (target tile, source tile) the FP64 offset of
+// the two centres is rounded once and added to the targets.  Pairs whose tiles cannot
+// contain coincident points skip the r^2 == 0 test.  The compensated variant sums runs
+// of COMP_RUN sources in FP32 and merges each run into a (hi, lo) pair with TwoSum.
+#pragma once
+
+#include "sbq_common.cuh"
+
+namespace sbq {
+
+// Per-pair arithmetic, FP32.  Accumulates (folded prefactors, see the launcher):
+//   SL: ri q + (r.q) ri^3 r
+//   DL: (r.q)(r.n) ri^5 r
+//   CF: ri q + (r.q) ri^3 (1 + kappa (r.n) ri^2) r
+template <int KIND, bool CHECK>
+__device__ __forceinline__ void pair_f32(float xh, float yh, float zh, const float4 &P,
+                                         const float4 &Q, const float4 &N, float kappa, float &ax,
+                                         float &ay, float &az)
+{
+    const float dx = xh - P.x, dy = yh - P.y, dz = zh - P.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    float ri = rsqrtf(r2);
+    if (CHECK)
+        ri = (r2 > 0.0f) ? ri : 0.0f;
+    const float rq = fmaf(dx, Q.x, fmaf(dy, Q.y, dz * Q.z));
+    const float ri2 = ri * ri;
+    if (KIND == KIND_SL) {
+        const float b = (rq * ri2) * ri;
+        ax = fmaf(ri, Q.x, ax);
+        ay = fmaf(ri, Q.y, ay);
+        az = fmaf(ri, Q.z, az);
+        ax = fmaf(b, dx, ax);
+        ay = fmaf(b, dy, ay);
+        az = fmaf(b, dz, az);
+    } else if (KIND == KIND_DL) {
+        const float rn = fmaf(dx, N.x, fmaf(dy, N.y, dz * N.z));
+        const float b = ((rq * ri2) * (rn * ri2)) * ri;
+        ax = fmaf(b, dx, ax);
+        ay = fmaf(b, dy, ay);
+        az = fmaf(b, dz, az);
+    } else {
+        const float rn = fmaf(dx, N.x, fmaf(dy, N.y, dz * N.z));
+        const float g = fmaf(kappa, rn * ri2, 1.0f);
+        const float b = (rq * ri2) * (ri * g);
+        ax = fmaf(ri, Q.x, ax);
+        ay = fmaf(ri, Q.y, ay);
+        az = fmaf(ri, Q.z, az);
+        ax = fmaf(b, dx, ax);
+        ay = fmaf(b, dy, ay);
+        az = fmaf(b, dz, az);
+    }
+}
+
+// Error-free transformation a + b = s + e (Knuth's TwoSum); folds e into lo.
+__device__ __forceinline__ void two_sum_merge(float &hi, float &lo, float b)
+{
+    const float s = hi + b;
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) + (b - bb);
+    hi = s;
+    lo += e;
+}
+
+template <int KIND, int R, bool CHECK, bool COMP>
+__device__ __forceinline__ void tile_f32(const float4 *__restrict__ sp, const float (&xh)[R],
+                                         const float (&yh)[R], const float (&zh)[R], float kappa,
+                                         float (&ax)[R], float (&ay)[R], float (&az)[R],
+                                         float (&hx)[R], float (&hy)[R], float (&hz)[R],
+                                         float (&lx)[R], float (&ly)[R], float (&lz)[R])
+{
+    constexpr int TS = TS_F32;
+    constexpr int RUN = COMP ? COMP_RUN : TS;
+#pragma unroll 1
+    for (int j0 = 0; j0 < TS; j0 += RUN) {
+#pragma unroll 4
+        for (int j = j0; j < j0 + RUN; ++j) {
+            const float4 P = sp[j];
+            const float4 Q = sp[TS + j];
+            float4 N;
+            if (KIND != KIND_SL)
+                N = sp[2 * TS + j];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                pair_f32<KIND, CHECK>(xh[r], yh[r], zh[r], P, Q, N, kappa, ax[r], ay[r], az[r]);
+        }
+        if (COMP) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                two_sum_merge(hx[r], lx[r], ax[r]);
+                two_sum_merge(hy[r], ly[r], ay[r]);
+                two_sum_merge(hz[r], lz[r], az[r]);
+                ax[r] = ay[r] = az[r] = 0.0f;
+            }
+        }
+    }
+}
+
+template <int KIND, int R, int W, bool COMP>
+__global__ void __launch_bounds__(W * 32) pairsum_f32_kernel(const PairsumParams p)
+{
+    constexpr int NT = W * 32;
+    constexpr int TT = NT * R;
+    constexpr int TS = TS_F32;
+    constexpr int NF = (KIND == KIND_SL) ? 2 : 3;
+    constexpr uint32_t TILE_BYTES = NF * TS * sizeof(float4);
+    constexpr int STAGE = 3 * TS;   // float4 per stage (and per packed tile)
+
+    extern __shared__ __align__(128) float4 sbuf[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int4 s_item;
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const float4 *__restrict__ spack = static_cast<const float4 *>(p.spack);
+    const float kappa = static_cast<float>(p.kappa);
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    uint32_t g = 0;   // source tiles consumed by this CTA (ring position)
+    for (;;) {
+        if (tid == 0) {
+            const int i = atomicAdd(p.counter, 1);
+            s_item = (i < p.n_items) ? p.items[i] : make_int4(-1, 0, 0, 0);
+        }
+        __syncthreads();
+        const int4 it = s_item;
+        if (it.x < 0)
+            break;
+        const TileInfo tt = p.ttiles[it.x];
+
+        float tx[R], ty[R], tz[R];
+        const float4 *tp = p.tpack + static_cast<size_t>(it.x) * TT + warp * 32 * R + lane;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float4 v = tp[r * 32];
+            tx[r] = v.x;
+            ty[r] = v.y;
+            tz[r] = v.z;
+        }
+        float ax[R], ay[R], az[R], hx[R], hy[R], hz[R], lx[R], ly[R], lz[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            ax[r] = ay[r] = az[r] = 0.0f;
+            hx[r] = hy[r] = hz[r] = 0.0f;
+            lx[r] = ly[r] = lz[r] = 0.0f;
+        }
+
+        const int nk = it.z - it.y;
+        if (tid == 0) {
+            const int st = g & 1;
+            mbar_arrive_expect_tx(&bar[st], TILE_BYTES);
+            bulk_copy_g2s(sbuf + st * STAGE, spack + static_cast<size_t>(it.y) * STAGE, TILE_BYTES,
+                          &bar[st]);
+        }
+        for (int k = 0; k < nk; ++k) {
+            const uint32_t gk = g + k;
+            const int st = gk & 1;
+            if (tid == 0 && k + 1 < nk) {
+                const int sn = (gk + 1) & 1;
+                mbar_arrive_expect_tx(&bar[sn], TILE_BYTES);
+                bulk_copy_g2s(sbuf + sn * STAGE, spack + static_cast<size_t>(it.y + k + 1) * STAGE,
+                              TILE_BYTES, &bar[sn]);
+            }
+            const bool timed_out = !mbar_wait_bounded(&bar[st], (gk >> 1) & 1);
+            if (__syncthreads_or(timed_out)) {
+                // The copy never landed: flag it, give the copies in flight a bounded
+                // chance to land, and leave without touching the output.
+                if (tid == 0)
+                    atomicOr(p.err, DEV_ERR_TIMEOUT);
+                mbar_wait_bounded(&bar[st], (gk >> 1) & 1, 100000000ull);
+                if (k + 1 < nk)
+                    mbar_wait_bounded(&bar[(gk + 1) & 1], ((gk + 1) >> 1) & 1, 100000000ull);
+                return;
+            }
+            const TileInfo si = p.stiles[it.y + k];
+            const double ddx = tt.cx - si.cx, ddy = tt.cy - si.cy, ddz = tt.cz - si.cz;
+            const double dist = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
+            const double lim = static_cast<double>(tt.rad) + static_cast<double>(si.rad);
+            const bool near = (dist - lim) <= 1.0e-5 * (dist + lim) + 1.0e-30;
+            const float sx = static_cast<float>(ddx), sy = static_cast<float>(ddy),
+                        sz = static_cast<float>(ddz);
+            float xh[R], yh[R], zh[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                xh[r] = tx[r] + sx;
+                yh[r] = ty[r] + sy;
+                zh[r] = tz[r] + sz;
+            }
+            const float4 *sp = sbuf + st * STAGE;
+            if (near)
+                tile_f32<KIND, R, true, COMP>(sp, xh, yh, zh, kappa, ax, ay, az, hx, hy, hz, lx, ly,
+                                              lz);
+            else
+                tile_f32<KIND, R, false, COMP>(sp, xh, yh, zh, kappa, ax, ay, az, hx, hy, hz, lx,
+                                               ly, lz);
+            __syncthreads();   // stage st may be refilled from here on
+        }
+        g += nk;
+
+        // Epilogue: FP64 totals, direct output or chunk partial.
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int loc = warp * 32 * R + r * 32 + lane;
+            double sx_, sy_, sz_;
+            if (COMP) {
+                sx_ = static_cast<double>(hx[r]) + static_cast<double>(lx[r]);
+                sy_ = static_cast<double>(hy[r]) + static_cast<double>(ly[r]);
+                sz_ = static_cast<double>(hz[r]) + static_cast<double>(lz[r]);
+            } else {
+                sx_ = ax[r];
+                sy_ = ay[r];
+                sz_ = az[r];
+            }
+            if (it.w < 0) {
+                if (loc < tt.count) {
+                    const long long t = tt.begin + loc;
+                    double ox = p.scale * sx_, oy = p.scale * sy_, oz = p.scale * sz_;
+                    if (p.diag_sigma) {
+                        ox += p.diag * p.diag_sigma[t];
+                        oy += p.diag * p.diag_sigma[p.nt + t];
+                        oz += p.diag * p.diag_sigma[2 * p.nt + t];
+                    }
+                    p.out[t] = ox;
+                    p.out[p.nt + t] = oy;
+                    p.out[2 * p.nt + t] = oz;
+                }
+            } else {
+                double *pp = p.partial + static_cast<size_t>(it.w) * 3 * TT + loc;
+                pp[0] = sx_;
+                pp[TT] = sy_;
+                pp[2 * TT] = sz_;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64
+// ---------------------------------------------------------------------------
+template <int KIND>
+__device__ __forceinline__ void pair_f64(double x, double y, double z, const double *__restrict__ s,
+                                         int j, double kappa, double &ax, double &ay, double &az)
+{
+    constexpr int TS = TS_F64;
+    const double dx = x - s[j], dy = y - s[TS + j], dz = z - s[2 * TS + j];
+    const double qx = s[3 * TS + j], qy = s[4 * TS + j], qz = s[5 * TS + j];
+    const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+    const double ri = (r2 > 0.0) ? rsqrt(r2) : 0.0;
+    const double rq = fma(dx, qx, fma(dy, qy, dz * qz));
+    const double ri2 = ri * ri;
+    if (KIND == KIND_SL) {
+        const double b = (rq * ri2) * ri;
+        ax = fma(ri, qx, ax);
+        ay = fma(ri, qy, ay);
+        az = fma(ri, qz, az);
+        ax = fma(b, dx, ax);
+        ay = fma(b, dy, ay);
+        az = fma(b, dz, az);
+    } else {
+        const double rn = fma(dx, s[6 * TS + j], fma(dy, s[7 * TS + j], dz * s[8 * TS + j]));
+        if (KIND == KIND_DL) {
+            const double b = ((rq * ri2) * (rn * ri2)) * ri;
+            ax = fma(b, dx, ax);
+            ay = fma(b, dy, ay);
+            az = fma(b, dz, az);
+        } else {
+            const double gg = fma(kappa, rn * ri2, 1.0);
+            const double b = (rq * ri2) * (ri * gg);
+            ax = fma(ri, qx, ax);
+            ay = fma(ri, qy, ay);
+            az = fma(ri, qz, az);
+            ax = fma(b, dx, ax);
+            ay = fma(b, dy, ay);
+            az = fma(b, dz, az);
+        }
+    }
+}
+
+template <int KIND, int R, int W>
+__global__ void __launch_bounds__(W * 32) pairsum_f64_kernel(const PairsumParams p)
+{
+    constexpr int NT = W * 32;
+    constexpr int TT = NT * R;
+    constexpr int TS = TS_F64;
+    constexpr int NF = (KIND == KIND_SL) ? 6 : 9;
+    constexpr uint32_t TILE_BYTES = NF * TS * sizeof(double);
+    constexpr int STAGE = 9 * TS;   // doubles per stage (and per packed tile)
+
+    extern __shared__ __align__(128) double dbuf[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int4 s_item;
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const double *__restrict__ spack = static_cast<const double *>(p.spack);
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    uint32_t g = 0;
+    for (;;) {
+        if (tid == 0) {
+            const int i = atomicAdd(p.counter, 1);
+            s_item = (i < p.n_items) ? p.items[i] : make_int4(-1, 0, 0, 0);
+        }
+        __syncthreads();
+        const int4 it = s_item;
+        if (it.x < 0)
+            break;
+        const TileInfo tt = p.ttiles[it.x];
+
+        double tx[R], ty[R], tz[R], ax[R], ay[R], az[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int loc = warp * 32 * R + r * 32 + lane;
+            const long long t = tt.begin + (loc < tt.count ? loc : 0);
+            tx[r] = p.trg[t];
+            ty[r] = p.trg[p.nt + t];
+            tz[r] = p.trg[2 * p.nt + t];
+            ax[r] = ay[r] = az[r] = 0.0;
+        }
+
+        const int nk = it.z - it.y;
+        if (tid == 0) {
+            const int st = g & 1;
+            mbar_arrive_expect_tx(&bar[st], TILE_BYTES);
+            bulk_copy_g2s(dbuf + st * STAGE, spack + static_cast<size_t>(it.y) * STAGE, TILE_BYTES,
+                          &bar[st]);
+        }
+        for (int k = 0; k < nk; ++k) {
+            const uint32_t gk = g + k;
+            const int st = gk & 1;
+            if (tid == 0 && k + 1 < nk) {
+                const int sn = (gk + 1) & 1;
+                mbar_arrive_expect_tx(&bar[sn], TILE_BYTES);
+                bulk_copy_g2s(dbuf + sn * STAGE, spack + static_cast<size_t>(it.y + k + 1) * STAGE,
+                              TILE_BYTES, &bar[sn]);
+            }
+            const bool timed_out = !mbar_wait_bounded(&bar[st], (gk >> 1) & 1);
+            if (__syncthreads_or(timed_out)) {
+                if (tid == 0)
+                    atomicOr(p.err, DEV_ERR_TIMEOUT);
+                mbar_wait_bounded(&bar[st], (gk >> 1) & 1, 100000000ull);
+                if (k + 1 < nk)
+                    mbar_wait_bounded(&bar[(gk + 1) & 1], ((gk + 1) >> 1) & 1, 100000000ull);
+                return;
+            }
+            const double *sp = dbuf + st * STAGE;
+#pragma unroll 2
+            for (int j = 0; j < TS; ++j) {
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    pair_f64<KIND>(tx[r], ty[r], tz[r], sp, j, p.kappa, ax[r], ay[r], az[r]);
+            }
+            __syncthreads();
+        }
+        g += nk;
+
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int loc = warp * 32 * R + r * 32 + lane;
+            if (it.w < 0) {
+                if (loc < tt.count) {
+                    const long long t = tt.begin + loc;
+                    double ox = p.scale * ax[r], oy = p.scale * ay[r], oz = p.scale * az[r];
+                    if (p.diag_sigma) {
+                        ox += p.diag * p.diag_sigma[t];
+                        oy += p.diag * p.diag_sigma[p.nt + t];
+                        oz += p.diag * p.diag_sigma[2 * p.nt + t];
+                    }
+                    p.out[t] = ox;
+                    p.out[p.nt + t] = oy;
+                    p.out[2 * p.nt + t] = oz;
+                }
+            } else {
+                double *pp = p.partial + static_cast<size_t>(it.w) * 3 * TT + loc;
+                pp[0] = ax[r];
+                pp[TT] = ay[r];
+                pp[2 * TT] = az[r];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launch table for one kind
+// ---------------------------------------------------------------------------
+template <int KIND>
+struct KindLauncher {
+    template <int R, int W, bool COMP>
+    static cudaError_t f32(int grid, const PairsumParams &p, cudaStream_t s)
+    {
+        const size_t smem = 2 * 3 * TS_F32 * sizeof(float4);
+        pairsum_f32_kernel<KIND, R, W, COMP><<<grid, W * 32, smem, s>>>(p);
+        return cudaGetLastError();
+    }
+    template <int R, int W>
+    static cudaError_t f64(int grid, const PairsumParams &p, cudaStream_t s)
+    {
+        const size_t smem = 2 * 9 * TS_F64 * sizeof(double);
+        pairsum_f64_kernel<KIND, R, W><<<grid, W * 32, smem, s>>>(p);
+        return cudaGetLastError();
+    }
+    template <int R, int W, bool COMP>
+    static int occ32()
+    {
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pairsum_f32_kernel<KIND, R, W, COMP>, W * 32,
+                                                      2 * 3 * TS_F32 * sizeof(float4));
+        return b;
+    }
+    template <int R, int W>
+    static int occ64()
+    {
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pairsum_f64_kernel<KIND, R, W>, W * 32,
+                                                      2 * 9 * TS_F64 * sizeof(double));
+        return b;
+    }
+
+// Supported tile shapes.  FP32: (R, W) in {(2,4), (4,4), (8,4), (4,8)}; FP64: (1,4), (2,4).
+#define SBQ_F32_SHAPES(X) X(2, 4) X(4, 4) X(8, 4) X(4, 8)
+#define SBQ_F64_SHAPES(X) X(1, 4) X(2, 4)
+
+    static cudaError_t launch(int prec, int R, int W, int grid, const PairsumParams &p, cudaStream_t s)
+    {
+        if (prec == SBQ_FP64) {
+#define X(r, w) \
+    if (R == r && W == w) return f64<r, w>(grid, p, s);
+            SBQ_F64_SHAPES(X)
+#undef X
+        } else {
+            const bool comp = (prec == SBQ_FP32_COMP);
+#define X(r, w)                                      \
+    if (R == r && W == w)                            \
+        return comp ? f32<r, w, true>(grid, p, s) : f32<r, w, false>(grid, p, s);
+            SBQ_F32_SHAPES(X)
+#undef X
+        }
+        return cudaErrorInvalidValue;
+    }
+    static int occupancy(int prec, int R, int W)
+    {
+        if (prec == SBQ_FP64) {
+#define X(r, w) \
+    if (R == r && W == w) return occ64<r, w>();
+            SBQ_F64_SHAPES(X)
+#undef X
+        } else {
+            const bool comp = (prec == SBQ_FP32_COMP);
+#define X(r, w) \
+    if (R == r && W == w) return comp ? occ32<r, w, true>() : occ32<r, w, false>();
+            SBQ_F32_SHAPES(X)
+#undef X
+        }
+        return 0;
+    }
+};
+
+}  // namespace sbq

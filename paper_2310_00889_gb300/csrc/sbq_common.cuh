@@ -1,0 +1,193 @@
+// Internal definitions shared by the CUDA translation units of libsbq.
+// Not part of the public ABI (include/sbq.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sbq.h"
+
+namespace sbq {
+
+// Pair-sum kernel kinds: single layer, double layer, combined field
+// (paper Eqs. stokes-sl, stokes-dl, stokes-bie-new).
+enum Kind { KIND_SL = 0, KIND_DL = 1, KIND_CF = 2 };
+
+// Sources per shared-memory tile.  FP32 tiles hold float4 {pos, q, n}; FP64 tiles
+// hold 9 doubles per source {x, y, z, qx, qy, qz, nx, ny, nz}, each field a run of TS.
+constexpr int TS_F32 = 256;
+constexpr int TS_F64 = 128;
+// Compensated FP32: plain FP32 sums over runs of this many sources are merged into
+// the (hi, lo) pair with TwoSum.
+constexpr int COMP_RUN = 64;
+// Position of padding sources in the last (ragged) tile of a segment.  Their weight
+// and normal are zero, so every term they produce is an exact zero.
+constexpr float PAD_POS_F32 = 1.0e15f;
+constexpr double PAD_POS_F64 = 1.0e100;
+
+// Device error word bits.
+constexpr int DEV_ERR_TIMEOUT = 1;
+
+// Geometry of one source or target tile.
+struct __align__(16) TileInfo {
+    double cx, cy, cz;   // FP64 centre (a member node); FP32 tiles store coordinates relative to it
+    float rad;           // max |member - centre| (rounded up), for the self-pair test
+    int count;           // valid members (<= tile size)
+    long long begin;     // global index of the first member
+    int seg;             // segment of the tile
+    int slot_begin;      // target tiles: first partial slot, -1 when the tile has one chunk
+    int slot_count;      // target tiles: number of chunk partials
+    int pad_;
+};
+static_assert(sizeof(TileInfo) == 64, "TileInfo layout");
+
+// Arguments of one pair-sum launch (all pointers are device pointers).
+struct PairsumParams {
+    const void *spack;          // packed source tiles
+    const TileInfo *stiles;     // source tile table
+    const float4 *tpack;        // FP32 paths: packed targets [ttile][TT] (x - c, y - c, z - c, 0)
+    const TileInfo *ttiles;     // target tile table
+    const double *trg;          // FP64 path: targets (SoA, stride nt)
+    long long nt;               // global number of targets (stride of trg / out / diag_sigma)
+    const int4 *items;          // work list {ttile, stile_begin, stile_end, slot (-1: direct)}
+    int n_items;
+    int *counter;               // work-claim counter, zeroed by the density pack kernel
+    int *err;                   // device error word
+    double *out;                // (3, nt) FP64 output
+    double *partial;            // [slot][3][TT] FP64 chunk partials
+    const double *diag_sigma;   // nullable: out += diag * diag_sigma (same indexing as out)
+    double diag;
+    double scale;               // prefactor applied to the accumulated sum
+    double kappa;               // combined field: 6 beta / alpha (ratio of D to S prefactors)
+    int TT;                     // targets per target tile
+};
+
+// ---------------------------------------------------------------------------
+// Inline PTX: mbarrier + bulk async copy (TMA engine, non-tensor form)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// One bulk copy global -> shared that signals `bar` with its byte count on landing.
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes,
+                                              uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of `bar` to complete, giving up after `limit_ns`.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  uint64_t limit_ns = 2000000000ull)
+{
+    if (mbar_try_wait(bar, parity))
+        return true;
+    const uint64_t t0 = global_timer_ns();
+    for (uint32_t i = 0;; ++i) {
+        if (mbar_try_wait(bar, parity))
+            return true;
+        if ((i & 255u) == 255u && global_timer_ns() - t0 > limit_ns)
+            return false;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side helpers
+// ---------------------------------------------------------------------------
+void set_error(const std::string &msg);
+void clear_error();
+int cuda_status(cudaError_t e, const char *what);   // records the message, returns status
+
+#define SBQ_CUDA(call)                                         \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess)                                 \
+            return ::sbq::cuda_status(e_, #call);              \
+    } while (0)
+
+#define SBQ_TRY(call)                                          \
+    do {                                                       \
+        int s_ = (call);                                       \
+        if (s_ != SBQ_OK)                                      \
+            return s_;                                         \
+    } while (0)
+
+struct DeviceProps {
+    int sms = 0, cc_major = 0, cc_minor = 0;
+};
+const DeviceProps &device_props();
+int *device_error_word();   // per-device error word (allocated once per device)
+
+// Launchers implemented per kind (pairsum_{sl,dl,cf}.cu).  prec: sbq_prec.
+// Return cudaErrorInvalidValue for an unsupported (R, W).
+cudaError_t launch_pairsum(int kind, int prec, int R, int W, int grid, const PairsumParams &p,
+                           cudaStream_t s);
+int pairsum_blocks_per_sm(int kind, int prec, int R, int W);
+bool pairsum_shape_supported(int prec, int R, int W);
+size_t pairsum_smem_bytes(int prec);
+
+// pack.cu
+cudaError_t launch_pack_src_geom(int prec, const double *src, const double *nrm, long long ns,
+                                 TileInfo *stiles, int n_stiles, void *spack, cudaStream_t s);
+cudaError_t launch_pack_src_q(int prec, const double *w, const double *sigma, long long ns,
+                              const TileInfo *stiles, int n_stiles, void *spack, int *counter,
+                              cudaStream_t s);
+cudaError_t launch_pack_trg(const double *trg, long long nt, TileInfo *ttiles, int n_ttiles,
+                            int TT, float4 *tpack, cudaStream_t s);
+cudaError_t launch_reduce_partials(const TileInfo *ttiles, int n_ttiles, int TT,
+                                   const double *partial, long long nt, double *out,
+                                   double scale, double diag, const double *diag_sigma,
+                                   cudaStream_t s);
+cudaError_t launch_csr_apply(long long nrows, const int64_t *rowptr, const int64_t *col,
+                             const double *val, const double *x, double *y, cudaStream_t s);
+
+}  // namespace sbq

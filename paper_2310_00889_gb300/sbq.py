@@ -1,0 +1,326 @@
+"""ctypes binding of libsbq (include/sbq.h): argument marshalling only.
+
+Every arithmetic step runs in the CUDA library.  Tensors are torch CUDA float64
+tensors in structure-of-arrays layout, shape (3, N) for point sets, densities and
+velocities; torch is used for device memory and the current stream only.  There is
+no CPU fallback: importing this module raises if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libsbq.so")
+
+OK, EINVAL, ECUDA, ENOCONV, EBREAKDOWN, ENONFINITE, ETIMEOUT, ENOMEM = range(8)
+FP64, FP32, FP32_COMP = 0, 1, 2
+_PREC = {"fp64": FP64, "fp32": FP32, "fp32c": FP32_COMP, "fp32_comp": FP32_COMP,
+         FP64: FP64, FP32: FP32, FP32_COMP: FP32_COMP}
+_STATUS = {0: "SBQ_OK", 1: "SBQ_EINVAL", 2: "SBQ_ECUDA", 3: "SBQ_ENOCONV", 4: "SBQ_EBREAKDOWN",
+           5: "SBQ_ENONFINITE", 6: "SBQ_ETIMEOUT", 7: "SBQ_ENOMEM"}
+
+
+class SbqError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+class Tune(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_int), ("warps", ctypes.c_int), ("chunk_tiles", ctypes.c_int)]
+
+    def as_dict(self):
+        return dict(r=self.r, warps=self.warps, chunk_tiles=self.chunk_tiles)
+
+
+class GmresOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("inner_prec", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("max_outer", ctypes.c_int), ("use_graph", ctypes.c_int)]
+
+
+SBQ_HIST = 64
+
+
+class GmresReport(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("outer_iters", ctypes.c_int),
+                ("matvecs_fp64", ctypes.c_int), ("matvecs_low", ctypes.c_int),
+                ("graph_used", ctypes.c_int), ("kernel_launches", ctypes.c_int),
+                ("rel_res", ctypes.c_double),
+                ("n_hist", ctypes.c_int), ("rel_res_hist", ctypes.c_double * SBQ_HIST),
+                ("time_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return dict(status=self.status, iters=self.iters, outer_iters=self.outer_iters,
+                    matvecs_fp64=self.matvecs_fp64, matvecs_low=self.matvecs_low,
+                    graph_used=bool(self.graph_used), kernel_launches=self.kernel_launches,
+                    rel_res=self.rel_res,
+                    hist=list(self.rel_res_hist[:self.n_hist]), time_ms=self.time_ms)
+
+
+_i64 = ctypes.c_int64
+_vp = ctypes.c_void_p
+_int = ctypes.c_int
+_dbl = ctypes.c_double
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libsbq.so is not built (%s); run __graft_entry__.build() or "
+                           "python paper_2310_00889_gb300/build.py" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "sbq_version": ([], _int),
+        "sbq_last_error": ([], ctypes.c_char_p),
+        "sbq_device_info": ([_vp, _vp, _vp, _vp], _int),
+        "stokes_sl_apply": ([_i64, _vp, _vp, _vp, _i64, _vp, _vp, _int, _vp], _int),
+        "stokes_dl_apply": ([_i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _int, _vp], _int),
+        "stokes_combined_apply": ([_i64, _vp, _vp, _vp, _vp, _i64, _vp, _dbl, _dbl, _vp, _int,
+                                   _vp], _int),
+        "batch_plan": ([_int, _vp, _vp, _vp, ctypes.POINTER(_vp)], _int),
+        "stokes_op_create": ([_i64, _vp, _vp, _vp, _dbl, _dbl, _i64, _vp, _vp, _vp, _vp,
+                              ctypes.POINTER(_vp)], _int),
+        "stokes_matvec": ([_vp, _vp, _vp, _int, _vp], _int),
+        "gmres_solve": ([_vp, _vp, _vp, ctypes.POINTER(GmresOpts), ctypes.POINTER(GmresReport),
+                         _vp], _int),
+        "sbq_autotune": ([_vp, _int, ctypes.POINTER(Tune), _vp], _int),
+        "sbq_op_tune": ([_vp, _int, ctypes.POINTER(Tune)], _int),
+        "sbq_op_stats": ([_vp, _int, ctypes.POINTER(_int), ctypes.POINTER(_dbl)], _int),
+        "sbq_check_device": ([_vp], _int),
+        "sbq_destroy": ([_vp], None),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+lib = _load()
+
+
+def _check(status):
+    if status != OK:
+        msg = lib.sbq_last_error()
+        raise SbqError(status, msg.decode() if msg else "")
+    return status
+
+
+def _prec(p):
+    try:
+        return _PREC[p]
+    except KeyError:
+        raise ValueError("unknown precision %r (fp64, fp32, fp32c)" % (p,))
+
+
+def _dev(t, shape=None, name="array"):
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64):
+        raise TypeError("%s must be a CUDA float64 tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("%s has shape %s, expected %s" % (name, tuple(t.shape), tuple(shape)))
+    return t
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def version():
+    return lib.sbq_version()
+
+
+def device_info():
+    sms, lanes, ma, mi = _int(), _int(), _int(), _int()
+    _check(lib.sbq_device_info(ctypes.byref(sms), ctypes.byref(lanes), ctypes.byref(ma),
+                               ctypes.byref(mi)))
+    return dict(sms=sms.value, fp32_lanes_per_sm=lanes.value, cc=(ma.value, mi.value))
+
+
+def slender_eta(eps):
+    """eta = 1 / (2 eps log(1/eps)), the slender-body mixing parameter (paper Sec. 4.1)."""
+    return 1.0 / (2.0 * eps * math.log(1.0 / eps))
+
+
+def _apply(kind, src, nrm, w, sigma, trg, alpha, beta, prec, out, stream):
+    ns = src.shape[1]
+    nt = trg.shape[1]
+    _dev(src, (3, ns), "src")
+    _dev(w, (ns,), "w")
+    _dev(sigma, (3, ns), "sigma")
+    _dev(trg, (3, nt), "trg")
+    if nrm is not None:
+        _dev(nrm, (3, ns), "nrm")
+    if out is None:
+        out = torch.empty((3, nt), dtype=torch.float64, device=trg.device)
+    _dev(out, (3, nt), "out")
+    p = _prec(prec)
+    st = _stream(stream)
+    if kind == "sl":
+        _check(lib.stokes_sl_apply(ns, _ptr(src), _ptr(w), _ptr(sigma), nt, _ptr(trg), _ptr(out),
+                                   p, st))
+    elif kind == "dl":
+        _check(lib.stokes_dl_apply(ns, _ptr(src), _ptr(nrm), _ptr(w), _ptr(sigma), nt, _ptr(trg),
+                                   _ptr(out), p, st))
+    else:
+        _check(lib.stokes_combined_apply(ns, _ptr(src), _ptr(nrm), _ptr(w), _ptr(sigma), nt,
+                                         _ptr(trg), float(alpha), float(beta), _ptr(out), p, st))
+    return out
+
+
+def sl_apply(src, w, sigma, trg, prec="fp32c", out=None, stream=None):
+    """Single-layer velocity S[sigma] at trg (Eq. stokes-sl, uncorrected Nystrom sum)."""
+    return _apply("sl", src, None, w, sigma, trg, 1.0, 0.0, prec, out, stream)
+
+
+def dl_apply(src, nrm, w, sigma, trg, prec="fp32c", out=None, stream=None):
+    """Double-layer velocity D[sigma] at trg (Eq. stokes-dl)."""
+    return _apply("dl", src, nrm, w, sigma, trg, 0.0, 1.0, prec, out, stream)
+
+
+def combined_apply(src, nrm, w, sigma, trg, alpha, beta, prec="fp32c", out=None, stream=None):
+    """alpha S[sigma] + beta D[sigma] at trg in one pass."""
+    return _apply("cf", src, nrm, w, sigma, trg, alpha, beta, prec, out, stream)
+
+
+def check_device(stream=None):
+    """Synchronise and raise SbqError(ETIMEOUT) if a device-side bounded wait expired."""
+    _check(lib.sbq_check_device(_stream(stream)))
+
+
+class BatchPlan:
+    """Work-list plan for independent segments (prefix offsets, host int64)."""
+
+    def __init__(self, src_off, trg_off=None, tune=None):
+        import numpy as np
+        so = np.ascontiguousarray(src_off, dtype=np.int64)
+        to = so if trg_off is None else np.ascontiguousarray(trg_off, dtype=np.int64)
+        self.src_off, self.trg_off = so, to
+        t = None
+        if tune is not None:
+            t = Tune(int(tune["r"]), int(tune["warps"]), int(tune.get("chunk_tiles", 0)))
+        h = _vp()
+        _check(lib.batch_plan(len(so) - 1, so.ctypes.data_as(_vp), to.ctypes.data_as(_vp),
+                              ctypes.byref(t) if t is not None else None, ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib.sbq_destroy(self.handle)
+            self.handle = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class StokesOp:
+    """K sigma = diag sigma + (D + eta S)[sigma] + E sigma on the nodes (Eq. stokes-bie-new)."""
+
+    def __init__(self, src, nrm, w, eta, diag=0.5, correction=None, plan: BatchPlan | None = None):
+        n = src.shape[1]
+        _dev(src, (3, n), "src")
+        _dev(nrm, (3, n), "nrm")
+        _dev(w, (n,), "w")
+        self.n = n
+        self.eta = float(eta)
+        self.device = src.device
+        rowptr = col = val = None
+        nnz = 0
+        if correction is not None:
+            rowptr, col, val = correction
+            for t, nm, dt in ((rowptr, "rowptr", torch.int64), (col, "col", torch.int64),
+                              (val, "val", torch.float64)):
+                if not (t.is_cuda and t.dtype == dt and t.is_contiguous()):
+                    raise TypeError("correction %s must be a contiguous CUDA %s tensor" % (nm, dt))
+            if rowptr.numel() != 3 * n + 1:
+                raise ValueError("rowptr must have 3n+1 entries")
+            nnz = int(val.numel())
+        h = _vp()
+        _check(lib.stokes_op_create(n, _ptr(src), _ptr(nrm), _ptr(w), self.eta, float(diag), nnz,
+                                    _ptr(rowptr), _ptr(col), _ptr(val),
+                                    plan.handle if plan is not None else None, ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib.sbq_destroy(self.handle)
+            self.handle = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def matvec(self, sigma, prec="fp64", out=None, stream=None):
+        _dev(sigma, (3, self.n), "sigma")
+        if out is None:
+            out = torch.empty_like(sigma)
+        _dev(out, (3, self.n), "out")
+        _check(lib.stokes_matvec(self.handle, _ptr(sigma), _ptr(out), _prec(prec), _stream(stream)))
+        return out
+
+    def solve(self, rhs, x0=None, tol=1e-10, restart=100, max_iter=2000, inner_prec="fp64",
+              inner_tol=1e-5, max_outer=30, use_graph=True, stream=None):
+        """GMRES for K x = rhs; returns (x, report dict)."""
+        _dev(rhs, (3, self.n), "rhs")
+        x = torch.zeros_like(rhs) if x0 is None else x0.clone()
+        _dev(x, (3, self.n), "x0")
+        o = GmresOpts(float(tol), int(restart), int(max_iter), _prec(inner_prec), float(inner_tol),
+                      int(max_outer), 1 if use_graph else 0)
+        rep = GmresReport()
+        st = lib.gmres_solve(self.handle, _ptr(rhs), _ptr(x), ctypes.byref(o), ctypes.byref(rep),
+                             _stream(stream))
+        if st not in (OK, ENOCONV):
+            _check(st)
+        d = rep.as_dict()
+        d["status_name"] = _STATUS.get(st, st)
+        return x, d
+
+    def autotune(self, prec, stream=None):
+        t = Tune()
+        _check(lib.sbq_autotune(self.handle, _prec(prec), ctypes.byref(t), _stream(stream)))
+        return t.as_dict()
+
+    def tune(self, prec):
+        t = Tune()
+        _check(lib.sbq_op_tune(self.handle, _prec(prec), ctypes.byref(t)))
+        return t.as_dict()
+
+    def stats(self, prec):
+        k, p = _int(), _dbl()
+        _check(lib.sbq_op_stats(self.handle, _prec(prec), ctypes.byref(k), ctypes.byref(p)))
+        return dict(kernels_per_matvec=k.value, pairs_per_matvec=p.value)
+
+
+def solve_from_host(src, nrm, w, rhs, eta, tol=1e-10, inner_prec="fp32c", restart=100,
+                    max_iter=2000, inner_tol=1e-5, max_outer=30, use_graph=True, device="cuda"):
+    """End-to-end call on host (pinned CPU) tensors: copy the geometry and data to the GPU,
+    build the operator, solve, and copy the solution back to the host."""
+    dev = torch.device(device)
+    d_src = src.to(dev, non_blocking=True)
+    d_nrm = nrm.to(dev, non_blocking=True)
+    d_w = w.to(dev, non_blocking=True)
+    d_rhs = rhs.to(dev, non_blocking=True)
+    op = StokesOp(d_src, d_nrm, d_w, eta)
+    x, rep = op.solve(d_rhs, tol=tol, inner_prec=inner_prec, restart=restart, max_iter=max_iter,
+                      inner_tol=inner_tol, max_outer=max_outer, use_graph=use_graph)
+    out = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+    out.copy_(x)
+    op.close()
+    return out, rep

@@ -1,0 +1,67 @@
+"""The C-ABI library loads and exports every entry point include/sbq.h declares (no GPU).
+
+Only calls that touch no device are made here: the version and the last-error string.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sbq.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return re.findall(r"SBQ_API\s+[\w\s\*]+?\b(\w+)\s*\(", text)
+
+
+@pytest.fixture(scope="module")
+def libsbq():
+    from paper_2310_00889_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = set(_declared())
+    for required in ("stokes_sl_apply", "stokes_dl_apply", "stokes_matvec", "gmres_solve",
+                     "batch_plan", "stokes_op_create", "sbq_destroy", "sbq_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libsbq):
+    missing = [n for n in _declared() if not hasattr(libsbq, n)]
+    assert not missing, missing
+
+
+def test_host_only_calls(libsbq):
+    libsbq.sbq_version.restype = ctypes.c_int
+    assert libsbq.sbq_version() == 100
+    libsbq.sbq_last_error.restype = ctypes.c_char_p
+    assert libsbq.sbq_last_error() == b""
+    # argument validation happens before any device call
+    libsbq.stokes_sl_apply.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    assert libsbq.stokes_sl_apply(-1, None, None, None, 0, None, None, 0, None) == 1
+    assert b"negative" in libsbq.sbq_last_error()
+    assert libsbq.stokes_sl_apply(4, None, None, None, 4, None, None, 0, None) == 1
+    assert libsbq.stokes_sl_apply(0, None, None, None, 0, None, None, 7, None) == 1
+
+
+def test_batch_plan_validation_on_host(libsbq):
+    vp = ctypes.c_void_p
+    libsbq.batch_plan.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.POINTER(vp)]
+    libsbq.sbq_destroy.argtypes = [vp]
+    off = (ctypes.c_int64 * 4)(0, 10, 25, 40)
+    bad = (ctypes.c_int64 * 4)(0, 10, 5, 40)
+    h = vp()
+    assert libsbq.batch_plan(3, ctypes.cast(off, vp), ctypes.cast(off, vp), None, ctypes.byref(h)) == 0
+    assert h.value
+    libsbq.sbq_destroy(h)
+    h2 = vp()
+    assert libsbq.batch_plan(3, ctypes.cast(bad, vp), ctypes.cast(off, vp), None, ctypes.byref(h2)) == 1
+    assert not h2.value

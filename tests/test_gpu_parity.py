@@ -1,0 +1,291 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Error metric: relative infinity norm ||u - u_oracle||_inf / ||u_oracle||_inf over all
+components (all errors in the paper are relative).  Bars:
+  * FP64 paths: 1e-10;
+  * FP32 and compensated FP32 paths: TOL_F32 below, a bound measured on GB300 (the
+    FP32 unit roundoff is 6e-8; per-term rounding of r = x - y near the surface and the
+    cancellation in the sum put the observed errors at 1e-7..1e-6).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2310_00889_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL_F64 = 1e-10
+TOL_F32 = {"fp32": 2e-5, "fp32c": 2e-5}
+
+
+@pytest.fixture(scope="module")
+def sbq():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA device is required for the gpu tests")
+    from paper_2310_00889_gb300 import build
+    build.build()
+    from paper_2310_00889_gb300 import sbq as mod
+    return mod
+
+
+def _t(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _relerr(u, ref):
+    return float(np.abs(u - ref).max() / np.abs(ref).max())
+
+
+def _apply(sbq, kind, src, nrm, w, sig, trg, prec, alpha=1.3, beta=1.0):
+    if kind == "sl":
+        return _np(sbq.sl_apply(_t(src), _t(w), _t(sig), _t(trg), prec=prec))
+    if kind == "dl":
+        return _np(sbq.dl_apply(_t(src), _t(nrm), _t(w), _t(sig), _t(trg), prec=prec))
+    return _np(sbq.combined_apply(_t(src), _t(nrm), _t(w), _t(sig), _t(trg), alpha, beta, prec=prec))
+
+
+def _oracle(oracle_mod, kind, src, nrm, w, sig, trg, alpha=1.3, beta=1.0):
+    if kind == "sl":
+        return oracle_mod.sl(src, w, sig, trg)
+    if kind == "dl":
+        return oracle_mod.dl(src, nrm, w, sig, trg)
+    return oracle_mod.combined(src, nrm, w, sig, trg, alpha, beta)
+
+
+def _ragged_case():
+    """1000 sources from the arc pipe (4 ragged source tiles) and 777 targets: 500 of the
+    nodes themselves (coincident pairs) plus 277 interior points."""
+    c = I.config2(panels=2)
+    s = c["surf"]
+    idx = np.random.default_rng(3).choice(s.size, 1000, replace=False)
+    src, nrm, w = s.x[:, idx], s.n[:, idx], s.w[idx]
+    sig = I.density(1000, seed=5)
+    rng = np.random.default_rng(6)
+    pts = np.stack([5.0 + 0.5 * rng.standard_normal(277), 0.3 * rng.standard_normal(277),
+                    0.3 * rng.standard_normal(277)])
+    trg = np.concatenate([src[:, :500], pts], axis=1)
+    return src, nrm, w, sig, trg
+
+
+@pytest.mark.parametrize("case", ["config1", "ragged"])
+@pytest.mark.parametrize("kind", ["sl", "dl", "cf"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32c"])
+def test_apply_parity(sbq, oracle_mod, case, kind, prec):
+    if case == "config1":
+        c = I.config1()
+        s = c["surf"]
+        src, nrm, w, sig, trg = s.x, s.n, s.w, c["sigma"], c["trg"]
+    else:
+        src, nrm, w, sig, trg = _ragged_case()
+    u = _apply(sbq, kind, src, nrm, w, sig, trg, prec)
+    ref = _oracle(oracle_mod, kind, src, nrm, w, sig, trg)
+    assert np.all(np.isfinite(u))
+    err = _relerr(u, ref)
+    tol = TOL_F64 if prec == "fp64" else TOL_F32[prec]
+    print("apply %s %s %s relerr %.3e" % (case, kind, prec, err))
+    assert err <= tol
+
+
+@pytest.mark.parametrize("ns,nt", [(1, 1), (1, 300), (255, 1), (256, 256), (257, 513),
+                                   (129, 1025)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_apply_sizes_and_tails(sbq, oracle_mod, ns, nt, prec):
+    rng = np.random.default_rng(ns * 1000 + nt)
+    src = rng.standard_normal((3, ns))
+    nrm = rng.standard_normal((3, ns))
+    nrm /= np.linalg.norm(nrm, axis=0)
+    w = rng.random(ns) + 0.1
+    sig = rng.standard_normal((3, ns))
+    trg = rng.standard_normal((3, nt)) * 1.5
+    u = _apply(sbq, "cf", src, nrm, w, sig, trg, prec, 0.7, 1.0)
+    ref = _oracle(oracle_mod, "cf", src, nrm, w, sig, trg, 0.7, 1.0)
+    tol = TOL_F64 if prec == "fp64" else 1e-4
+    assert _relerr(u, ref) <= tol
+
+
+def test_apply_empty_inputs(sbq):
+    import torch
+    trg = _t(np.ones((3, 5)))
+    z = sbq.sl_apply(_t(np.zeros((3, 0))), _t(np.zeros(0)), _t(np.zeros((3, 0))), trg, prec="fp64")
+    assert torch.count_nonzero(z) == 0
+    out = sbq.sl_apply(_t(np.ones((3, 4))), _t(np.ones(4)), _t(np.ones((3, 4))),
+                       _t(np.zeros((3, 0))), prec="fp32c")
+    assert out.shape == (3, 0)
+
+
+def test_apply_rejects_bad_arguments(sbq):
+    with pytest.raises(ValueError):
+        sbq.sl_apply(_t(np.ones((3, 4))), _t(np.ones(4)), _t(np.ones((3, 4))), _t(np.ones((3, 2))),
+                     prec="fp16")
+    with pytest.raises(sbq.SbqError) as ei:
+        sbq.lib.stokes_sl_apply(-1, None, None, None, 0, None, None, 0, None)
+        sbq._check(1)
+    assert ei.value.status == sbq.EINVAL
+
+
+def test_fp32c_is_deterministic(sbq):
+    c = I.config1()
+    s = c["surf"]
+    u1 = _apply(sbq, "cf", s.x, s.n, s.w, c["sigma"], c["trg"], "fp32c")
+    u2 = _apply(sbq, "cf", s.x, s.n, s.w, c["sigma"], c["trg"], "fp32c")
+    assert np.array_equal(u1, u2)
+
+
+def _small_op_case():
+    c = I.config2(panels=4)
+    s = c["surf"]
+    return s, c["rhs"], I.density(s.size, seed=8)
+
+
+def _random_csr(n, seed=0, per_row=6):
+    rng = np.random.default_rng(seed)
+    rows = 3 * n
+    cols = rng.integers(0, 3 * n, size=(rows, per_row))
+    cols.sort(axis=1)
+    val = 1e-3 * rng.standard_normal((rows, per_row))
+    rowptr = np.arange(0, rows * per_row + 1, per_row, dtype=np.int64)
+    return rowptr, cols.reshape(-1).astype(np.int64), val.reshape(-1)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32c"])
+@pytest.mark.parametrize("with_csr", [False, True])
+def test_operator_matvec_parity(sbq, oracle_mod, prec, with_csr):
+    import torch
+    s, _, sig = _small_op_case()
+    eta = sbq.slender_eta(0.2)
+    corr = None
+    E = None
+    if with_csr:
+        rp, col, val = _random_csr(s.size)
+        E = oracle_mod.CSR(rp, col, val, 3 * s.size, 3 * s.size)
+        corr = (torch.as_tensor(rp, device="cuda"), torch.as_tensor(col, device="cuda"), _t(val))
+    op = sbq.StokesOp(_t(s.x), _t(s.n), _t(s.w), eta, correction=corr)
+    out = _np(op.matvec(_t(sig), prec=prec))
+    ref = oracle_mod.matvec(s.x, s.n, s.w, eta, sig, 0.5, E)
+    err = _relerr(out, ref)
+    print("matvec %s csr=%s relerr %.3e tune %s" % (prec, with_csr, err, op.tune(prec)))
+    assert err <= (TOL_F64 if prec == "fp64" else TOL_F32[prec])
+    st = op.stats(prec)
+    assert st["pairs_per_matvec"] == float(s.size) ** 2
+    op.close()
+
+
+def test_eta_formula_matches_oracle(sbq, oracle_mod):
+    for e in (1e-2, 0.2, 1.0 / 3.0):
+        assert abs(sbq.slender_eta(e) - float(oracle_mod.eta_slender(e))) < 1e-12
+
+
+@pytest.fixture(scope="module")
+def small_solve(sbq, oracle_mod):
+    s, rhs, _ = _small_op_case()
+    eta = sbq.slender_eta(0.2)
+    mv = lambda v: oracle_mod.matvec(s.x, s.n, s.w, eta, v.reshape(3, -1)).reshape(-1)
+    x_ref, info = oracle_mod.gmres(mv, rhs.reshape(-1), tol=1e-12, restart=100, max_iter=600)
+    assert info["rel_res"] <= 1e-12
+    return s, rhs, eta, x_ref.reshape(3, -1)
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_gmres_fp64_matches_oracle(sbq, small_solve, use_graph):
+    s, rhs, eta, x_ref = small_solve
+    op = sbq.StokesOp(_t(s.x), _t(s.n), _t(s.w), eta)
+    x, rep = op.solve(_t(rhs), tol=1e-10, restart=50, inner_prec="fp64", use_graph=use_graph)
+    print("fp64 solve", {k: rep[k] for k in ("iters", "outer_iters", "rel_res", "graph_used")})
+    assert rep["status"] == 0 and rep["rel_res"] <= 1e-10
+    assert rep["graph_used"] == use_graph
+    assert _relerr(_np(x), x_ref) <= 1e-8
+    op.close()
+
+
+@pytest.mark.parametrize("inner", ["fp32c", "fp32"])
+def test_gmres_mixed_refinement_reaches_fp64_tolerance(sbq, small_solve, inner):
+    s, rhs, eta, x_ref = small_solve
+    op = sbq.StokesOp(_t(s.x), _t(s.n), _t(s.w), eta)
+    x, rep = op.solve(_t(rhs), tol=1e-10, restart=100, inner_prec=inner, inner_tol=1e-5)
+    print("mixed", inner, {k: rep[k] for k in ("iters", "outer_iters", "matvecs_fp64",
+                                                 "matvecs_low", "rel_res", "hist")})
+    assert rep["status"] == 0 and rep["rel_res"] <= 1e-10
+    assert rep["matvecs_low"] > rep["matvecs_fp64"]
+    assert _relerr(_np(x), x_ref) <= 1e-8
+    op.close()
+
+
+def test_graph_and_stepwise_solves_identical(sbq, small_solve):
+    import torch
+    s, rhs, eta, _ = small_solve
+    op = sbq.StokesOp(_t(s.x), _t(s.n), _t(s.w), eta)
+    xa, ra = op.solve(_t(rhs), tol=1e-10, inner_prec="fp32c", use_graph=True)
+    xb, rb = op.solve(_t(rhs), tol=1e-10, inner_prec="fp32c", use_graph=False)
+    assert ra["graph_used"] and not rb["graph_used"]
+    assert ra["iters"] == rb["iters"]
+    assert torch.equal(xa, xb)
+    op.close()
+
+
+def test_gmres_restart_and_initial_guess(sbq, small_solve):
+    s, rhs, eta, x_ref = small_solve
+    op = sbq.StokesOp(_t(s.x), _t(s.n), _t(s.w), eta)
+    x, rep = op.solve(_t(rhs), tol=1e-10, restart=8, inner_prec="fp64", max_iter=2000)
+    assert rep["status"] == 0 and rep["outer_iters"] > 1
+    assert _relerr(_np(x), x_ref) <= 1e-8
+    # resuming from the solution converges at once
+    x2, rep2 = op.solve(_t(rhs), x0=x, tol=1e-10, inner_prec="fp64")
+    assert rep2["iters"] == 0 and rep2["rel_res"] <= 1e-10
+    # iteration cap reached: ENOCONV reported, best iterate returned
+    _, rep3 = op.solve(_t(rhs), tol=1e-14, restart=5, inner_prec="fp64", max_iter=5)
+    assert rep3["status"] == sbq.ENOCONV
+    op.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_batched_plan_equals_separate_operators(sbq, prec):
+    """Block-diagonal batch in one persistent launch == each segment on its own (same tile
+    shape and chunking, so the same summation order: bitwise equal)."""
+    import torch
+    segs = [I.capped_arc_pipe(5.0, a, 1.0, k, 8, 32, 8) for a, k in ((0.6, 1), (1.9, 3), (1.1, 2))]
+    tune = dict(r=2, warps=4, chunk_tiles=2) if prec != "fp64" else dict(r=2, warps=4, chunk_tiles=2)
+    allx = np.concatenate([g.x for g in segs], axis=1)
+    alln = np.concatenate([g.n for g in segs], axis=1)
+    allw = np.concatenate([g.w for g in segs])
+    off = np.cumsum([0] + [g.size for g in segs])
+    sig = I.density(int(off[-1]), seed=4)
+    plan = sbq.BatchPlan(off, tune=tune)
+    op = sbq.StokesOp(_t(allx), _t(alln), _t(allw), 1.55, plan=plan)
+    out = op.matvec(_t(sig), prec=prec)
+    for i, g in enumerate(segs):
+        p1 = sbq.BatchPlan([0, g.size], tune=tune)
+        o1 = sbq.StokesOp(_t(g.x), _t(g.n), _t(g.w), 1.55, plan=p1)
+        ref = o1.matvec(_t(sig[:, off[i]:off[i + 1]]), prec=prec)
+        assert torch.equal(out[:, off[i]:off[i + 1]], ref)
+        o1.close()
+    op.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c", "fp32"])
+def test_config2_full_size_sampled_rows(sbq, oracle_mod, prec):
+    """Full curved-pipe operator (16384 wall + 2048 cap nodes) in the launch configuration
+    the benchmark uses (autotuned shape); 384 sampled rows checked against the oracle."""
+    c = I.config2()
+    s = c["surf"]
+    eta = sbq.slender_eta(c["slenderness"])
+    sig = I.density(s.size, seed=12)
+    op = sbq.StokesOp(_t(s.x), _t(s.n), _t(s.w), eta)
+    out = _np(op.matvec(_t(sig), prec=prec))
+    rows = np.sort(np.random.default_rng(13).choice(s.size, 384, replace=False))
+    ref = oracle_mod.combined(s.x, s.n, s.w, sig, s.x[:, rows], eta, 1.0) + 0.5 * sig[:, rows]
+    err = _relerr(out[:, rows], ref)
+    print("config2 sampled %s relerr %.3e tune %s" % (prec, err, op.tune(prec)))
+    assert err <= (TOL_F64 if prec == "fp64" else TOL_F32[prec])
+    op.close()
+
+
+def test_device_error_word_clear(sbq):
+    sbq.check_device()
