@@ -183,9 +183,19 @@ def test_eta_formula_matches_oracle(sbq, oracle_mod):
         assert abs(sbq.slender_eta(e) - float(oracle_mod.eta_slender(e))) < 1e-12
 
 
+def _stokeslet_data(x, x0, f):
+    r = x - np.asarray(x0, float)[:, None]
+    rl = np.linalg.norm(r, axis=0)
+    f = np.asarray(f, float)
+    return (f[:, None] / rl + r * np.sum(r * f[:, None], axis=0) / rl ** 3) / (8 * np.pi)
+
+
 @pytest.fixture(scope="module")
 def small_solve(sbq, oracle_mod):
-    s, rhs, _ = _small_op_case()
+    """Capped arc pipe with 1024 nodes (2 panels x 8 x 32 wall, two 8 x 32 caps) and its
+    Dirichlet data; the oracle's GMRES solution to 1e-12."""
+    c = I.config2(panels=2, nth=32, nr=8)
+    s, rhs = c["surf"], c["rhs"]
     eta = sbq.slender_eta(0.2)
     mv = lambda v: oracle_mod.matvec(s.x, s.n, s.w, eta, v.reshape(3, -1)).reshape(-1)
     x_ref, info = oracle_mod.gmres(mv, rhs.reshape(-1), tol=1e-12, restart=100, max_iter=600)
@@ -197,7 +207,7 @@ def small_solve(sbq, oracle_mod):
 def test_gmres_fp64_matches_oracle(sbq, small_solve, use_graph):
     s, rhs, eta, x_ref = small_solve
     op = sbq.StokesOp(_t(s.x), _t(s.n), _t(s.w), eta)
-    x, rep = op.solve(_t(rhs), tol=1e-10, restart=50, inner_prec="fp64", use_graph=use_graph)
+    x, rep = op.solve(_t(rhs), tol=1e-10, restart=100, inner_prec="fp64", use_graph=use_graph)
     print("fp64 solve", {k: rep[k] for k in ("iters", "outer_iters", "rel_res", "graph_used")})
     assert rep["status"] == 0 and rep["rel_res"] <= 1e-10
     assert rep["graph_used"] == use_graph
@@ -206,7 +216,7 @@ def test_gmres_fp64_matches_oracle(sbq, small_solve, use_graph):
 
 
 @pytest.mark.parametrize("inner", ["fp32c", "fp32"])
-def test_gmres_mixed_refinement_reaches_fp64_tolerance(sbq, small_solve, inner):
+def test_gmres_mixed_refinement_reaches_fp64_tolerance(sbq, oracle_mod, small_solve, inner):
     s, rhs, eta, x_ref = small_solve
     op = sbq.StokesOp(_t(s.x), _t(s.n), _t(s.w), eta)
     x, rep = op.solve(_t(rhs), tol=1e-10, restart=100, inner_prec=inner, inner_tol=1e-5)
@@ -214,7 +224,12 @@ def test_gmres_mixed_refinement_reaches_fp64_tolerance(sbq, small_solve, inner):
                                                  "matvecs_low", "rel_res", "hist")})
     assert rep["status"] == 0 and rep["rel_res"] <= 1e-10
     assert rep["matvecs_low"] > rep["matvecs_fp64"]
-    assert _relerr(_np(x), x_ref) <= 1e-8
+    # the oracle's FP64 residual of the returned x meets the tolerance; x itself agrees with
+    # the oracle's solution to within the conditioning of K times the tolerance
+    xs = _np(x)
+    kx = oracle_mod.matvec(s.x, s.n, s.w, eta, xs)
+    assert np.linalg.norm(rhs - kx) / np.linalg.norm(rhs) <= 1.05e-10
+    assert _relerr(xs, x_ref) <= 1e-6
     op.close()
 
 
@@ -230,16 +245,22 @@ def test_graph_and_stepwise_solves_identical(sbq, small_solve):
     op.close()
 
 
-def test_gmres_restart_and_initial_guess(sbq, small_solve):
-    s, rhs, eta, x_ref = small_solve
-    op = sbq.StokesOp(_t(s.x), _t(s.n), _t(s.w), eta)
+def test_gmres_restart_and_initial_guess(sbq, oracle_mod):
+    """Torus (R = 1, eps = 0.25, 1024 nodes) with the field of an exterior point force as data:
+    GMRES(8) needs several restarts and agrees with the oracle's GMRES(100); a solve started
+    from its own solution stops at once; a too-small iteration cap reports ENOCONV."""
+    t = I.torus(1.0, 0.25, 8, 8, 16)
+    rhs = _stokeslet_data(t.x, (2.5, 0.3, 0.2), (1.0, -0.5, 0.3))
+    eta = sbq.slender_eta(0.25)
+    mv = lambda v: oracle_mod.matvec(t.x, t.n, t.w, eta, v.reshape(3, -1)).reshape(-1)
+    x_ref, info = oracle_mod.gmres(mv, rhs.reshape(-1), tol=1e-12, restart=100)
+    x_ref = x_ref.reshape(3, -1)
+    op = sbq.StokesOp(_t(t.x), _t(t.n), _t(t.w), eta)
     x, rep = op.solve(_t(rhs), tol=1e-10, restart=8, inner_prec="fp64", max_iter=2000)
-    assert rep["status"] == 0 and rep["outer_iters"] > 1
+    assert rep["status"] == 0 and rep["outer_iters"] > 1 and rep["rel_res"] <= 1e-10
     assert _relerr(_np(x), x_ref) <= 1e-8
-    # resuming from the solution converges at once
     x2, rep2 = op.solve(_t(rhs), x0=x, tol=1e-10, inner_prec="fp64")
     assert rep2["iters"] == 0 and rep2["rel_res"] <= 1e-10
-    # iteration cap reached: ENOCONV reported, best iterate returned
     _, rep3 = op.solve(_t(rhs), tol=1e-14, restart=5, inner_prec="fp64", max_iter=5)
     assert rep3["status"] == sbq.ENOCONV
     op.close()
@@ -284,6 +305,26 @@ def test_config2_full_size_sampled_rows(sbq, oracle_mod, prec):
     err = _relerr(out[:, rows], ref)
     print("config2 sampled %s relerr %.3e tune %s" % (prec, err, op.tune(prec)))
     assert err <= (TOL_F64 if prec == "fp64" else TOL_F32[prec])
+    op.close()
+
+
+def test_config2_full_size_mixed_solve_residual_rows(sbq, oracle_mod):
+    """The benchmark's solve (curved pipe, 18432 nodes, compensated-FP32 inner GMRES, FP64
+    refinement to 1e-10, graph-replayed Arnoldi steps): the FP64 residual the library reports
+    is below 1e-10, and the oracle's rows of b - K x on 256 sampled nodes agree with it."""
+    c = I.config2()
+    s, rhs = c["surf"], c["rhs"]
+    eta = sbq.slender_eta(c["slenderness"])
+    op = sbq.StokesOp(_t(s.x), _t(s.n), _t(s.w), eta)
+    x, rep = op.solve(_t(rhs), tol=1e-10, restart=100, inner_prec="fp32c", inner_tol=1e-5)
+    print("config2 mixed", {k: rep[k] for k in ("iters", "outer_iters", "matvecs_fp64",
+                                                 "matvecs_low", "rel_res", "graph_used")})
+    assert rep["status"] == 0 and rep["rel_res"] <= 1e-10 and rep["graph_used"]
+    xs = _np(x)
+    rows = np.sort(np.random.default_rng(14).choice(s.size, 256, replace=False))
+    kx = oracle_mod.combined(s.x, s.n, s.w, xs, s.x[:, rows], eta, 1.0) + 0.5 * xs[:, rows]
+    res_rows = rhs[:, rows] - kx
+    assert np.abs(res_rows).max() <= 1e-9 * np.abs(rhs).max()
     op.close()
 
 
