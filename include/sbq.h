@@ -126,6 +126,28 @@ SBQ_API int sbq_device_info(int *num_sms, int *fp32_lanes_per_sm, int *cc_major,
 SBQ_API int stokes_sl_apply(int64_t ns, const double *src, const double *w, const double *sigma,
                             int64_t nt, const double *trg, double *u, int prec, void *stream);
 
+/*
+ * stokes_sl_apply without any allocation, for callers that cannot allocate GPU memory
+ * when they need the sum (fixed memory budgets, pre-reserved pools, loops that must not
+ * enter the allocator, hosts that forbid cudaMalloc / cudaFree or torch's allocator
+ * after start-up).  The paper has no counterpart: this is a deployment variant of the
+ * single-layer apply above, with the same arguments, meaning and result (up to the
+ * summation grouping of its fixed tile shape).
+ * Scratch: a 32 MiB array in device global memory declared by the library itself; every
+ * GPU that loads the library holds it until the process exits.  Limits: ns <= 131072 and
+ * nt <= 131072, else SBQ_EINVAL with a message naming the limit.
+ * The first call on each device (with that device current) looks up the array's device
+ * address with cudaGetSymbolAddress; make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents (each call rewrites
+ * what it reads): calls whose work may overlap on the GPU (unordered streams, several
+ * host threads on one device) race and must be serialised by the caller.
+ * On success the call performs no allocation of any kind; a rejected call records its
+ * message for sbq_last_error() as every entry point does.
+ */
+SBQ_API int stokes_sl_apply_noalloc(int64_t ns, const double *src, const double *w,
+                                    const double *sigma, int64_t nt, const double *trg, double *u,
+                                    int prec, void *stream);
+
 /* Double-layer velocity u = sum D(x_t - y_s; n_s) w_s sigma_s (Eq. stokes-dl), nrm[3*ns]
  * unit outward normals.  Other arguments and errors as stokes_sl_apply. */
 SBQ_API int stokes_dl_apply(int64_t ns, const double *src, const double *nrm, const double *w,
