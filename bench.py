@@ -53,6 +53,9 @@ def parse():
                     help="CPU work bound of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-reps", type=int, default=20)
+    ap.add_argument("--kernel-only", default=None, choices=["fp32c", "fp32", "fp64"],
+                    help="only time operator applies of this precision on the workload "
+                         "(inside an NVTX range 'kernel_only', for profilers)")
     return ap.parse_args()
 
 
@@ -223,6 +226,9 @@ def run_gpu(args):
     src, nrm, w, rhs = t(s.x), t(s.n), t(s.w), t(c["rhs"])
     stream = torch.cuda.current_stream()
 
+    if args.kernel_only:
+        return kernel_only(args, sbq, I, src, nrm, w, eta, n, t, dev)
+
     t_setup = time.perf_counter()
     op = sbq.StokesOp(src, nrm, w, eta)
     op.autotune("fp32c")
@@ -244,6 +250,7 @@ def run_gpu(args):
     barrier()
     torch.cuda.synchronize()
     times, reps = [], []
+    torch.cuda.nvtx.range_push("bench_timed")
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -254,6 +261,7 @@ def run_gpu(args):
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
         reps.append(rep)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
@@ -392,6 +400,35 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+    return 0
+
+
+def kernel_only(args, sbq, I, src, nrm, w, eta, n, t, dev):
+    """Operator applies of one precision on the workload, for profilers: the tile shape is
+    autotuned first, then --kernel-reps applies run inside the NVTX range 'kernel_only'."""
+    import torch
+    op = sbq.StokesOp(src, nrm, w, eta)
+    op.autotune(args.kernel_only)
+    sig = t(I.density(n, seed=12))
+    out = torch.empty_like(sig)
+    for _ in range(2):
+        op.matvec(sig, prec=args.kernel_only, out=out)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("kernel_only")
+    e0.record(stream)
+    for _ in range(args.kernel_reps):
+        op.matvec(sig, prec=args.kernel_only, out=out)
+    e1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / args.kernel_reps
+    print(json.dumps({"kernel_only": args.kernel_only, "nodes": n, "ms_per_apply": ms,
+                      "pairs_per_s": n * n / (ms * 1e-3), "tune": op.tune(args.kernel_only),
+                      "stats": op.stats(args.kernel_only)}), flush=True)
+    op.close()
     return 0
 
 

@@ -30,10 +30,12 @@
  *  - Every function returns an sbq_status; nothing is thrown across the ABI.  On
  *    failure sbq_last_error() (per host thread) describes the reason.
  *  - A source whose coordinates equal a target's exactly is skipped (the
- *    punctured sum; the correction E adds the true singular part).  The FP32
- *    paths skip a pair whose FP32 difference is zero: they require distinct
- *    points to differ at FP32 resolution relative to their tile, and pair
- *    distances above ~1e-7 in the units of the input.
+ *    punctured sum; the correction E adds the true singular part).  The FP64
+ *    path skips exactly those pairs.  The FP32 paths skip pairs closer than
+ *    4e-6 times the sum of the radii of the two tiles (256 consecutive points)
+ *    holding them, which catches every coincident pair whatever the FP32
+ *    rounding; they therefore require distinct points to be farther apart than
+ *    that, and pair distances above ~1e-7 in the units of the input.
  */
 #ifndef SBQ_H
 #define SBQ_H

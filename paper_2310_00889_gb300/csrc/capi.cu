@@ -59,7 +59,8 @@ int apply_generic(int64_t ns, const double *src, const double *nrm, const double
     SrcPack sp;
     TrgSet ts;
     std::vector<int64_t> soff = {0, ns}, toff = {0, nt};
-    SBQ_TRY(build_src_pack(sp, layout, soff, src, kind == KIND_SL ? nullptr : nrm, ns, s));
+    SBQ_TRY(build_src_pack(sp, layout, soff, src, kind == KIND_SL ? nullptr : nrm,
+                           kind == KIND_CF ? kappa : 1.0, ns, s));
     SBQ_TRY(build_trg_set(ts, kind, prec, default_tune(prec, nt), sp, toff, trg, nt, soff, s));
     SBQ_TRY(run_pairsum(kind, prec, sp, ts, w, sigma, ns, trg, nt, u, scale, kappa, 0.0, nullptr, s));
     return SBQ_OK;
@@ -133,8 +134,11 @@ SBQ_API int batch_plan(int nseg, const int64_t *seg_src_off, const int64_t *seg_
     for (int i = 0; i < nseg; ++i)
         if (seg_src_off[i + 1] < seg_src_off[i] || seg_trg_off[i + 1] < seg_trg_off[i])
             return fail(SBQ_EINVAL, "offsets must be non-decreasing");
-    if (tune && tune->r != 0 && !pairsum_shape_supported(SBQ_FP32, tune->r, tune->warps))
+    if (tune && tune->r != 0 && !pairsum_shape_supported(SBQ_FP32, tune->r, tune->warps) &&
+        !pairsum_shape_supported(SBQ_FP64, tune->r, tune->warps))
         return fail(SBQ_EINVAL, "unsupported tile shape");
+    if (tune && tune->chunk_tiles < 0)
+        return fail(SBQ_EINVAL, "chunk_tiles must be >= 0");
     PlanH *p = new (std::nothrow) PlanH();
     if (!p)
         return fail(SBQ_ENOMEM, "out of host memory");
@@ -224,11 +228,15 @@ SBQ_API int stokes_op_create(int64_t n, const double *src, const double *nrm, co
         if (e != cudaSuccess) return bail(cuda_status(e, "cudaMemcpy (correction)"));
     }
     cudaStream_t s = nullptr;
+    int kind;
+    double scale, kappa;
+    kind_and_scale(eta, 1.0, &kind, &scale, &kappa);
+    const double nscale = (kind == KIND_CF) ? kappa : 1.0;
     if ((st = build_src_pack(op->sp32, SBQ_FP32, op->plan.src_off, op->src.as<double>(),
-                             op->nrm.as<double>(), n, s)) != SBQ_OK)
+                             op->nrm.as<double>(), nscale, n, s)) != SBQ_OK)
         return bail(st);
     if ((st = build_src_pack(op->sp64, SBQ_FP64, op->plan.src_off, op->src.as<double>(),
-                             op->nrm.as<double>(), n, s)) != SBQ_OK)
+                             op->nrm.as<double>(), nscale, n, s)) != SBQ_OK)
         return bail(st);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return bail(cuda_status(e, "stokes_op_create"));

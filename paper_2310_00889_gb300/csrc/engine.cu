@@ -166,7 +166,7 @@ sbq_tune default_tune(int prec, long long nt)
 // Tile tables and work lists
 // ---------------------------------------------------------------------------
 int build_src_pack(SrcPack &sp, int layout, const std::vector<int64_t> &src_off, const double *src,
-                   const double *nrm, long long ns, cudaStream_t s)
+                   const double *nrm, double nscale, long long ns, cudaStream_t s)
 {
     sp.layout = layout;
     sp.TS = (layout == SBQ_FP64) ? TS_F64 : TS_F32;
@@ -194,12 +194,12 @@ int build_src_pack(SrcPack &sp, int layout, const std::vector<int64_t> &src_off,
     }
     SBQ_TRY(sp.stiles.alloc(h.size() * sizeof(TileInfo)));
     const size_t per_tile = (layout == SBQ_FP64) ? 9 * TS_F64 * sizeof(double)
-                                                 : 3 * TS_F32 * sizeof(float4);
+                                                 : F32_TILE_BLOCKS * TS_F32 * sizeof(float4);
     SBQ_TRY(sp.spack.alloc(h.size() * per_tile));
     if (!h.empty()) {
         SBQ_CUDA(cudaMemcpyAsync(sp.stiles.p, h.data(), h.size() * sizeof(TileInfo),
                                  cudaMemcpyHostToDevice, s));
-        SBQ_CUDA(launch_pack_src_geom(layout, src, nrm, ns, sp.stiles.as<TileInfo>(), sp.n_stiles,
+        SBQ_CUDA(launch_pack_src_geom(layout, src, nrm, nscale, ns, sp.stiles.as<TileInfo>(), sp.n_stiles,
                                       sp.spack.p, s));
     }
     return SBQ_OK;
@@ -316,6 +316,10 @@ int build_trg_set(TrgSet &ts, int kind, int prec, const sbq_tune &tune, const Sr
         SBQ_TRY(ts.tpack.alloc(ht.size() * static_cast<size_t>(TT) * sizeof(float4)));
     else
         ts.tpack.release();
+    if (prec == SBQ_FP32_COMP)
+        SBQ_TRY(ts.tpack_lo.alloc(ht.size() * static_cast<size_t>(TT) * sizeof(float4)));
+    else
+        ts.tpack_lo.release();
     if (!ht.empty()) {
         SBQ_CUDA(cudaMemcpyAsync(ts.ttiles.p, ht.data(), ht.size() * sizeof(TileInfo),
                                  cudaMemcpyHostToDevice, s));
@@ -325,7 +329,7 @@ int build_trg_set(TrgSet &ts, int kind, int prec, const sbq_tune &tune, const Sr
     SBQ_CUDA(cudaMemsetAsync(ts.counter.p, 0, sizeof(int), s));
     if (prec != SBQ_FP64 && ts.n_ttiles > 0)
         SBQ_CUDA(launch_pack_trg(trg, nt, ts.ttiles.as<TileInfo>(), ts.n_ttiles, TT,
-                                 ts.tpack.as<float4>(), s));
+                                 ts.tpack.as<float4>(), ts.tpack_lo.as<float4>(), s));
     return SBQ_OK;
 }
 
@@ -346,6 +350,7 @@ int run_pairsum(int kind, int prec, const SrcPack &sp, const TrgSet &ts, const d
     p.spack = sp.spack.p;
     p.stiles = sp.stiles.as<TileInfo>();
     p.tpack = ts.tpack.as<float4>();
+    p.tpack_lo = ts.tpack_lo.as<float4>();
     p.ttiles = ts.ttiles.as<TileInfo>();
     p.trg = trg;
     p.nt = nt;
@@ -520,8 +525,11 @@ int op_ensure_tuned(Op *op, int prec, cudaStream_t s)
     if (op->plan.has_tune) {
         auto ts = std::make_unique<TrgSet>();
         sbq_tune t = op->plan.tune;
-        if (prec == SBQ_FP64 && !pairsum_shape_supported(prec, t.r, t.warps))
-            t = default_tune(prec, op->n);
+        if (!pairsum_shape_supported(prec, t.r, t.warps)) {
+            const int chunk = t.chunk_tiles;
+            t = default_tune(prec, op->n);   // the plan's shape exists for the other precision
+            t.chunk_tiles = chunk;
+        }
         SBQ_TRY(build_trg_set(*ts, kind, prec, t, op_srcpack(op, prec), op->plan.src_off,
                               op->src.as<double>(), op->n, op->plan.src_off, s));
         op->ts[prec] = std::move(ts);

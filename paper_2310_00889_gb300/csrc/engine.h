@@ -61,7 +61,7 @@ struct TrgSet {
     int grid = 0;
     bool needs_reduce = false;
     double pairs = 0.0;         // pair interactions per apply (valid members only)
-    DevBuf ttiles, tpack, items, partial, counter;
+    DevBuf ttiles, tpack, tpack_lo, items, partial, counter;
 };
 
 struct Op {
@@ -83,7 +83,7 @@ struct Op {
 
 // Segment layout helpers.
 int build_src_pack(SrcPack &sp, int layout, const std::vector<int64_t> &src_off, const double *src,
-                   const double *nrm, long long ns, cudaStream_t s);
+                   const double *nrm, double nscale, long long ns, cudaStream_t s);
 int build_trg_set(TrgSet &ts, int kind, int prec, const sbq_tune &tune, const SrcPack &sp,
                   const std::vector<int64_t> &trg_off, const double *trg, long long nt,
                   const std::vector<int64_t> &src_off, cudaStream_t s);

@@ -9,10 +9,13 @@
 //     Givens estimate, the true FP64 residual decides the restart;
 //   * iterative refinement: the FP64 residual r = b - K x is formed, K d = r is solved
 //     by GMRES whose operator applies run in FP32 or compensated FP32, x += d, repeat.
-// Each Arnoldi step (operator apply + CGS2 + Givens) is a fixed sequence of kernels
-// that read the step index from device memory, so one captured copy of it serves every
-// step: it is the body of a CUDA-graph while node, which repeats it on the device until
-// the cycle ends (convergence, breakdown or m steps).
+// Each Arnoldi step is a fixed sequence of kernels that read the step index from device
+// memory, so one captured copy of it serves every step: it is the body of a CUDA-graph
+// while node, which repeats it on the device until the cycle ends (convergence,
+// breakdown or m steps).  One step is: operator apply on v_j; first Gram--Schmidt
+// pass (partial dots, finished by the last block); second pass fused with the first
+// update of w; norm fused with the second update, whose last block also applies the
+// Givens rotations; normalisation that writes v_{j+1} and the next operator input.
 #include "engine.h"
 
 #include <chrono>
@@ -22,6 +25,8 @@ namespace sbq {
 
 constexpr int GB = 256;          // threads of the vector kernels
 constexpr int MAX_RESTART = 256;
+constexpr int NC = 8;            // Krylov vectors handled per sweep of a multi-dot
+constexpr int SOLVE_SMEM_MAX_M = 200;   // back-substitution keeps R in shared memory up to this m
 
 struct GState {
     int j;          // completed Arnoldi steps of the cycle (= index of the next column)
@@ -31,11 +36,13 @@ struct GState {
     int m;          // step limit of this cycle
     int iters;      // Arnoldi steps since the solve began
     int nonfinite;  // a non-finite norm was seen
-    int pad_;
+    unsigned int ctr;   // blocks finished in the current fused kernel
+    int guard;      // steps run in this cycle, counted by k_guard
+    int guard_hit;  // k_guard ended the cycle (the step counter failed to stop it)
     double tol_abs; // absolute tolerance on the residual norm of the system being solved
     double beta;    // residual norm at the start of the cycle
     double res_est; // |g_{j}| after the last step
-    double res_true;// last norm computed by k_norm_fin
+    double res_true;// last norm computed by a norm kernel
     double inv_hn;  // 1 / h_{j+1,j} of the last step (0 on breakdown)
 };
 
@@ -45,7 +52,8 @@ struct GmresWS {
     long long N = 0;
     int nblk = 0;
     int ldp = 0;
-    DevBuf V, H, cs, sn, g, y, hb, w, vin, r, d, ax, part, st;
+    size_t solve_smem = 0;
+    DevBuf V, H, cs, sn, g, y, hb1, hb2, w, vin, r, d, ax, part, st;
     GState *hst = nullptr;             // pinned host mirror
     cudaStream_t cap = nullptr;        // capture stream
     cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
@@ -93,6 +101,7 @@ __device__ double block_sum(double v, double *red)
     return v;   // thread 0
 }
 
+// Rows [a, b) owned by this block; every fused kernel uses the same partition.
 __device__ __forceinline__ void block_rows(long long N, long long &a, long long &b)
 {
     const long long chunk = (N + gridDim.x - 1) / gridDim.x;
@@ -100,64 +109,217 @@ __device__ __forceinline__ void block_rows(long long N, long long &a, long long 
     b = a + chunk < N ? a + chunk : N;
 }
 
-// part[b * ldp + k] = sum over the rows of block b of V[k][i] w[i], k = 0..j.
-__global__ void k_dots(const double *__restrict__ V, long long N, const GState *__restrict__ st,
-                       const double *__restrict__ w, double *part, int ldp)
+// True in the block that finishes last (all other blocks' writes are visible to it).
+__device__ bool last_block(unsigned int *ctr)
 {
-    __shared__ double red[32];
-    const int j = st->j;
+    __shared__ unsigned int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0)
+        s_last = (atomicAdd(ctr, 1u) == gridDim.x - 1) ? 1u : 0u;
+    __syncthreads();
+    if (s_last)
+        __threadfence();
+    return s_last != 0;
+}
+
+// part[blockIdx][k] = sum over the block's rows of V[k][i] w[i], k = 0..j: one warp per
+// Krylov vector, lanes striding over the rows (coalesced), no block barrier.
+__device__ void block_multi_dot(const double *__restrict__ V, long long N, int j,
+                                const double *__restrict__ w, long long a, long long b,
+                                double *part_row)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int k = warp; k <= j; k += nw) {
+        const double *v = V + static_cast<size_t>(k) * N;
+        double acc = 0.0;
+        for (long long i = a + lane; i < b; i += 32)
+            acc = fma(v[i], w[i], acc);
+        for (int o = 16; o > 0; o >>= 1)
+            acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0)
+            part_row[k] = acc;
+    }
+}
+
+// Last block: hb[k] = sum_b part[b][k] (one warp per k, lanes over the blocks, fixed
+// order); column j of H gets (pass 0) or adds (pass 1) it.
+__device__ void finish_dots(const double *part, int ldp, GState *st, double *H, double *hb, int pass)
+{
+    const int j = st->j, ld = st->m + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int k = warp; k <= j; k += nw) {
+        double s = 0.0;
+        for (int bb = lane; bb < (int)gridDim.x; bb += 32)
+            s += __ldcg(part + static_cast<size_t>(bb) * ldp + k);
+        for (int o = 16; o > 0; o >>= 1)
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            hb[k] = s;
+            double *h = H + static_cast<size_t>(j) * ld + k;
+            *h = pass ? *h + s : s;
+        }
+    }
+    if (threadIdx.x == 0)
+        st->ctr = 0;
+}
+
+// First Gram--Schmidt pass: h1 = V[0..j]^T w.
+__global__ void k_cgs_pass1(const double *__restrict__ V, long long N, GState *st,
+                            const double *__restrict__ w, double *part, int ldp, double *H,
+                            double *hb1)
+{
     long long a, b;
     block_rows(N, a, b);
-    for (int k0 = 0; k0 <= j; k0 += 4) {
-        double acc[4] = {0.0, 0.0, 0.0, 0.0};
-        for (long long i = a + threadIdx.x; i < b; i += blockDim.x) {
-            const double wi = w[i];
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (k0 + q <= j)
-                    acc[q] = fma(V[static_cast<size_t>(k0 + q) * N + i], wi, acc[q]);
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const double s = block_sum(acc[q], red);
-            if (threadIdx.x == 0 && k0 + q <= j)
-                part[static_cast<size_t>(blockIdx.x) * ldp + k0 + q] = s;
-        }
-    }
+    block_multi_dot(V, N, st->j, w, a, b, part + static_cast<size_t>(blockIdx.x) * ldp);
+    if (last_block(&st->ctr))
+        finish_dots(part, ldp, st, H, hb1, 0);
 }
 
-// hb[k] = sum_b part[b][k] (fixed order); column j of H gets it (pass 0) or adds it (pass 1).
-__global__ void k_dots_fin(const double *__restrict__ part, int nblk, int ldp, const GState *st,
-                           double *H, double *hb, int pass)
-{
-    const int j = st->j, m1 = MAX_RESTART + 1;
-    (void)m1;
-    const int ld = st->m + 1;
-    for (int k = threadIdx.x; k <= j; k += blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < nblk; ++b)
-            s += part[static_cast<size_t>(b) * ldp + k];
-        hb[k] = s;
-        double *h = H + static_cast<size_t>(j) * ld + k;
-        *h = pass ? *h + s : s;
-    }
-}
-
-// w[i] -= sum_{k <= j} V[k][i] hb[k]
-__global__ void k_axpy_multi(const double *__restrict__ V, long long N, const GState *__restrict__ st,
-                             const double *__restrict__ hb, double *w)
+// w -= V h1 on this block's rows, then the second pass h2 = V^T w on the same rows.
+__global__ void k_cgs_pass2(const double *__restrict__ V, long long N, GState *st,
+                            const double *__restrict__ hb1, double *w, double *part, int ldp,
+                            double *H, double *hb2)
 {
     __shared__ double sh[MAX_RESTART + 1];
     const int j = st->j;
     for (int k = threadIdx.x; k <= j; k += blockDim.x)
-        sh[k] = hb[k];
+        sh[k] = hb1[k];
     __syncthreads();
-    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
-         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    long long a, b;
+    block_rows(N, a, b);
+    for (long long i = a + threadIdx.x; i < b; i += blockDim.x) {
         double acc = w[i];
         for (int k = 0; k <= j; ++k)
             acc = fma(-V[static_cast<size_t>(k) * N + i], sh[k], acc);
         w[i] = acc;
+    }
+    __syncthreads();   // the dots below read rows of w that other threads just updated
+    block_multi_dot(V, N, j, w, a, b, part + static_cast<size_t>(blockIdx.x) * ldp);
+    if (last_block(&st->ctr))
+        finish_dots(part, ldp, st, H, hb2, 1);
+}
+
+// w -= V h2 and ||w||^2 on this block's rows; the last block forms h_{j+1,j}, applies the
+// previous Givens rotations to column j, builds the new one and updates the residual
+// estimate and the stop flags.
+__global__ void k_cgs_norm_givens(const double *__restrict__ V, long long N, GState *st,
+                                  const double *__restrict__ hb2, double *w, double *part,
+                                  double *H, double *cs, double *sn, double *g)
+{
+    __shared__ double sh[MAX_RESTART + 1];
+    __shared__ double red[32];
+    const int j = st->j;
+    for (int k = threadIdx.x; k <= j; k += blockDim.x)
+        sh[k] = hb2[k];
+    __syncthreads();
+    long long a, b;
+    block_rows(N, a, b);
+    double nrm = 0.0;
+    for (long long i = a + threadIdx.x; i < b; i += blockDim.x) {
+        double acc = w[i];
+        for (int k = 0; k <= j; ++k)
+            acc = fma(-V[static_cast<size_t>(k) * N + i], sh[k], acc);
+        w[i] = acc;
+        nrm = fma(acc, acc, nrm);
+    }
+    const double bs = block_sum(nrm, red);
+    if (threadIdx.x == 0)
+        part[blockIdx.x] = bs;
+    if (!last_block(&st->ctr))
+        return;
+    // the last block: column j of H and the rotations into shared memory in parallel,
+    // the sequential rotation sweep by one thread, results written back in parallel
+    __shared__ double scol[MAX_RESTART + 1], scs[MAX_RESTART], ssn[MAX_RESTART];
+    __shared__ double s_hn;
+    const int ld = st->m + 1;
+    double *col = H + static_cast<size_t>(j) * ld;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x)
+        scol[i] = __ldcg(col + i);
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+        scs[i] = __ldcg(cs + i);
+        ssn[i] = __ldcg(sn + i);
+    }
+    if (threadIdx.x < 32) {
+        double t = 0.0;
+        for (int bb = threadIdx.x; bb < (int)gridDim.x; bb += 32)
+            t += __ldcg(part + bb);
+        for (int o = 16; o > 0; o >>= 1)
+            t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0)
+            s_hn = sqrt(t);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->ctr = 0;
+        const double hn = s_hn;
+        for (int i = 0; i < j; ++i) {
+            const double x0 = scol[i], x1 = scol[i + 1];
+            scol[i] = scs[i] * x0 + ssn[i] * x1;
+            scol[i + 1] = -ssn[i] * x0 + scs[i] * x1;
+        }
+        const double x0 = scol[j], x1 = hn;
+        const double den = hypot(x0, x1);
+        const double cj = (den == 0.0) ? 1.0 : x0 / den, sj = (den == 0.0) ? 0.0 : x1 / den;
+        cs[j] = cj;
+        sn[j] = sj;
+        scol[j] = cj * x0 + sj * x1;
+        col[j + 1] = 0.0;
+        const double gj = __ldcg(g + j);
+        g[j + 1] = -sj * gj;
+        g[j] = cj * gj;
+        const double est = fabs(sj * gj);
+        st->res_est = est;
+        st->iters += 1;
+        const bool nonfinite = !isfinite(hn) || !isfinite(est);
+        st->nonfinite |= nonfinite ? 1 : 0;
+        st->conv = est <= st->tol_abs;
+        st->brk = (hn == 0.0);
+        st->inv_hn = (hn > 0.0 && isfinite(hn)) ? 1.0 / hn : 0.0;
+        st->stop = st->conv || st->brk || nonfinite || (j + 1 >= st->m);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= j; i += blockDim.x)
+        col[i] = scol[i];
+}
+
+// v_{j+1} = w / h_{j+1,j}, also written to the operator input buffer; the last block
+// advances j and, inside the graph, sets the while condition.
+__global__ void k_normalize_advance(const double *__restrict__ w, long long N, GState *st,
+                                    double *V, double *vin, cudaGraphConditionalHandle h,
+                                    int use_cond)
+{
+    const int j = st->j;
+    const double s = st->inv_hn;
+    double *v = V + static_cast<size_t>(j + 1) * N;
+    long long a, b;
+    block_rows(N, a, b);
+    for (long long i = a + threadIdx.x; i < b; i += blockDim.x) {
+        const double x = w[i] * s;
+        v[i] = x;
+        vin[i] = x;
+    }
+    if (last_block(&st->ctr) && threadIdx.x == 0) {
+        st->ctr = 0;
+        st->j = j + 1;
+        if (use_cond)
+            cudaGraphSetConditional(h, st->stop ? 0u : 1u);
+    }
+}
+
+// Independent bound on the while loop: ends the cycle after `cap` steps whatever the
+// other kernels did to the step counter.
+__global__ void k_guard(GState *st, cudaGraphConditionalHandle h, int cap, int use_cond)
+{
+    if (threadIdx.x == 0) {
+        st->guard += 1;
+        if (st->guard >= cap || st->j >= cap) {
+            if (!st->stop)
+                st->guard_hit = 1;
+            st->stop = 1;
+            if (use_cond)
+                cudaGraphSetConditional(h, 0u);
+        }
     }
 }
 
@@ -187,73 +349,6 @@ __global__ void k_norm_fin(const double *__restrict__ part, int nblk, GState *st
     }
 }
 
-// New column of H: h_{j+1,j}, previous rotations, new rotation, residual estimate.
-__global__ void k_arnoldi_fin(const double *__restrict__ part, int nblk, GState *st, double *H,
-                              double *cs, double *sn, double *g)
-{
-    if (threadIdx.x != 0)
-        return;
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b)
-        s += part[b];
-    const double hn = sqrt(s);
-    const int j = st->j, ld = st->m + 1;
-    double *col = H + static_cast<size_t>(j) * ld;
-    col[j + 1] = hn;
-    for (int i = 0; i < j; ++i) {
-        const double a = col[i], c = col[i + 1];
-        col[i] = cs[i] * a + sn[i] * c;
-        col[i + 1] = -sn[i] * a + cs[i] * c;
-    }
-    const double a = col[j], c = col[j + 1];
-    const double den = hypot(a, c);
-    const double cj = (den == 0.0) ? 1.0 : a / den, sj = (den == 0.0) ? 0.0 : c / den;
-    cs[j] = cj;
-    sn[j] = sj;
-    col[j] = cj * a + sj * c;
-    col[j + 1] = 0.0;
-    g[j + 1] = -sj * g[j];
-    g[j] = cj * g[j];
-    const double est = fabs(g[j + 1]);
-    st->res_est = est;
-    st->iters += 1;
-    const bool nonfinite = !isfinite(hn) || !isfinite(est);
-    st->nonfinite |= nonfinite ? 1 : 0;
-    st->conv = est <= st->tol_abs;
-    st->brk = (hn == 0.0);
-    st->inv_hn = (hn > 0.0 && isfinite(hn)) ? 1.0 / hn : 0.0;
-    st->stop = st->conv || st->brk || nonfinite || (j + 1 >= st->m);
-}
-
-__global__ void k_normalize(const double *__restrict__ w, long long N, const GState *__restrict__ st,
-                            double *V)
-{
-    const int j = st->j;
-    const double s = st->inv_hn;
-    double *v = V + static_cast<size_t>(j + 1) * N;
-    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
-         i += static_cast<long long>(gridDim.x) * blockDim.x)
-        v[i] = w[i] * s;
-}
-
-__global__ void k_advance(GState *st, cudaGraphConditionalHandle h, int use_cond)
-{
-    if (threadIdx.x == 0) {
-        st->j += 1;
-        if (use_cond)
-            cudaGraphSetConditional(h, st->stop ? 0u : 1u);
-    }
-}
-
-__global__ void k_copy_col(const double *__restrict__ V, long long N, const GState *__restrict__ st,
-                           double *vin)
-{
-    const double *v = V + static_cast<size_t>(st->j) * N;
-    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
-         i += static_cast<long long>(gridDim.x) * blockDim.x)
-        vin[i] = v[i];
-}
-
 // Start a cycle from the residual whose norm k_norm_fin left in res_true.
 __global__ void k_cycle_init(GState *st, double *g, int m, double tol_abs)
 {
@@ -264,6 +359,8 @@ __global__ void k_cycle_init(GState *st, double *g, int m, double tol_abs)
         st->stop = 0;
         st->conv = 0;
         st->brk = 0;
+        st->ctr = 0;
+        st->guard = 0;
         st->m = m;
         st->tol_abs = tol_abs;
         st->res_est = beta;
@@ -273,27 +370,43 @@ __global__ void k_cycle_init(GState *st, double *g, int m, double tol_abs)
     }
 }
 
+// v_0 = r / beta, also the first operator input.
 __global__ void k_scale_first(const double *__restrict__ r, long long N, const GState *__restrict__ st,
-                              double *V)
+                              double *V, double *vin)
 {
     const double inv = 1.0 / st->beta;
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
-         i += static_cast<long long>(gridDim.x) * blockDim.x)
-        V[i] = r[i] * inv;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const double x = r[i] * inv;
+        V[i] = x;
+        vin[i] = x;
+    }
 }
 
-// y = H^{-1} g over the j completed steps (upper triangular after the rotations).
+// y = R^{-1} g over the j completed steps, R the rotated (upper triangular) H, by
+// columns from the last: y_i = g_i / R_ii, then g_l -= R_li y_i for l < i.  R sits in
+// shared memory when it fits (use_smem).
 __global__ void k_solve_y(const GState *__restrict__ st, const double *__restrict__ H,
-                          const double *__restrict__ g, double *y)
+                          const double *__restrict__ g, double *y, int use_smem)
 {
-    if (threadIdx.x != 0)
-        return;
+    extern __shared__ double tri[];
+    __shared__ double gs[MAX_RESTART + 1];
     const int k = st->j, ld = st->m + 1;
+    for (int i = threadIdx.x; i < k; i += blockDim.x)
+        gs[i] = g[i];
+    if (use_smem)
+        for (int c = 0; c < k; ++c)
+            for (int r = threadIdx.x; r <= c; r += blockDim.x)
+                tri[c * (c + 1) / 2 + r] = H[static_cast<size_t>(c) * ld + r];
+    __syncthreads();
     for (int i = k - 1; i >= 0; --i) {
-        double s = g[i];
-        for (int l = i + 1; l < k; ++l)
-            s -= H[static_cast<size_t>(l) * ld + i] * y[l];
-        y[i] = s / H[static_cast<size_t>(i) * ld + i];
+        const double rii = use_smem ? tri[i * (i + 1) / 2 + i] : H[static_cast<size_t>(i) * ld + i];
+        const double yi = gs[i] / rii;
+        if (threadIdx.x == 0)
+            y[i] = yi;
+        for (int l = threadIdx.x; l < i; l += blockDim.x)
+            gs[l] -= (use_smem ? tri[i * (i + 1) / 2 + l] : H[static_cast<size_t>(i) * ld + l]) * yi;
+        __syncthreads();
     }
 }
 
@@ -358,9 +471,10 @@ static int ws_ensure(Op *op, int m)
     ws->m = m;
     ws->N = 3 * op->n;
     const long long N = ws->N;
-    ws->nblk = static_cast<int>(std::max<long long>(1, std::min<long long>(2LL * device_props().sms,
-                                                                        (N + 2047) / 2048)));
+    ws->nblk = static_cast<int>(std::max<long long>(1, std::min<long long>(4LL * device_props().sms,
+                                                                        (N + 255) / 256)));
     ws->ldp = m + 1;
+    ws->solve_smem = (m <= SOLVE_SMEM_MAX_M) ? static_cast<size_t>(m) * (m + 1) / 2 * sizeof(double) : 0;
     int s = SBQ_OK;
     if (s == SBQ_OK) s = ws->V.alloc(static_cast<size_t>(m + 1) * N * sizeof(double));
     if (s == SBQ_OK) s = ws->H.alloc(static_cast<size_t>(m + 1) * m * sizeof(double));
@@ -368,7 +482,8 @@ static int ws_ensure(Op *op, int m)
     if (s == SBQ_OK) s = ws->sn.alloc(m * sizeof(double));
     if (s == SBQ_OK) s = ws->g.alloc((m + 1) * sizeof(double));
     if (s == SBQ_OK) s = ws->y.alloc(m * sizeof(double));
-    if (s == SBQ_OK) s = ws->hb.alloc((m + 1) * sizeof(double));
+    if (s == SBQ_OK) s = ws->hb1.alloc((m + 1) * sizeof(double));
+    if (s == SBQ_OK) s = ws->hb2.alloc((m + 1) * sizeof(double));
     if (s == SBQ_OK) s = ws->w.alloc(N * sizeof(double));
     if (s == SBQ_OK) s = ws->vin.alloc(N * sizeof(double));
     if (s == SBQ_OK) s = ws->r.alloc(N * sizeof(double));
@@ -391,6 +506,14 @@ static int ws_ensure(Op *op, int m)
         if (e != cudaSuccess)
             s = cuda_status(e, "cudaMemset");
     }
+    if (s == SBQ_OK && ws->solve_smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_solve_y, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(ws->solve_smem));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ws->solve_smem = 0;   // keep R in global memory
+        }
+    }
     if (s != SBQ_OK) {
         gmres_destroy(ws);
         return s;
@@ -400,35 +523,33 @@ static int ws_ensure(Op *op, int m)
     return SBQ_OK;
 }
 
-// Enqueue one Arnoldi step on stream s (use_cond: inside the while body).
+// Enqueue one Arnoldi step on stream s (use_cond: inside the while body).  The operator
+// input v_j is already in ws->vin (k_scale_first / k_normalize_advance put it there).
 static int enqueue_step(Op *op, GmresWS *ws, int prec, cudaStream_t s,
                         cudaGraphConditionalHandle h, int use_cond)
 {
     const long long N = ws->N;
     GState *st = ws->st.as<GState>();
-    const int vg = vec_grid(N);
-    k_copy_col<<<vg, GB, 0, s>>>(ws->V.as<double>(), N, st, ws->vin.as<double>());
-    SBQ_CUDA(cudaGetLastError());
     SBQ_TRY(op_matvec(op, ws->vin.as<double>(), ws->w.as<double>(), prec, s));
-    for (int pass = 0; pass < 2; ++pass) {
-        k_dots<<<ws->nblk, GB, 0, s>>>(ws->V.as<double>(), N, st, ws->w.as<double>(),
-                                       ws->part.as<double>(), ws->ldp);
-        k_dots_fin<<<1, GB, 0, s>>>(ws->part.as<double>(), ws->nblk, ws->ldp, st,
-                                    ws->H.as<double>(), ws->hb.as<double>(), pass);
-        k_axpy_multi<<<vg, GB, 0, s>>>(ws->V.as<double>(), N, st, ws->hb.as<double>(),
-                                       ws->w.as<double>());
-    }
-    k_norm_part<<<ws->nblk, GB, 0, s>>>(ws->w.as<double>(), N, ws->part.as<double>());
-    k_arnoldi_fin<<<1, 32, 0, s>>>(ws->part.as<double>(), ws->nblk, st, ws->H.as<double>(),
-                                   ws->cs.as<double>(), ws->sn.as<double>(), ws->g.as<double>());
-    k_normalize<<<vg, GB, 0, s>>>(ws->w.as<double>(), N, st, ws->V.as<double>());
-    k_advance<<<1, 32, 0, s>>>(st, h, use_cond);
+    k_cgs_pass1<<<ws->nblk, GB, 0, s>>>(ws->V.as<double>(), N, st, ws->w.as<double>(),
+                                        ws->part.as<double>(), ws->ldp, ws->H.as<double>(),
+                                        ws->hb1.as<double>());
+    k_cgs_pass2<<<ws->nblk, GB, 0, s>>>(ws->V.as<double>(), N, st, ws->hb1.as<double>(),
+                                        ws->w.as<double>(), ws->part.as<double>(), ws->ldp,
+                                        ws->H.as<double>(), ws->hb2.as<double>());
+    k_cgs_norm_givens<<<ws->nblk, GB, 0, s>>>(ws->V.as<double>(), N, st, ws->hb2.as<double>(),
+                                              ws->w.as<double>(), ws->part.as<double>(),
+                                              ws->H.as<double>(), ws->cs.as<double>(),
+                                              ws->sn.as<double>(), ws->g.as<double>());
+    k_normalize_advance<<<ws->nblk, GB, 0, s>>>(ws->w.as<double>(), N, st, ws->V.as<double>(),
+                                                ws->vin.as<double>(), h, use_cond);
+    k_guard<<<1, 32, 0, s>>>(st, h, ws->m, use_cond);
     SBQ_CUDA(cudaGetLastError());
     return SBQ_OK;
 }
 
 // Kernels of one Arnoldi step (enqueue_step).
-static int step_kernels(const Op *op, int prec) { return 1 + op_kernels_per_matvec(op, prec) + 6 + 4; }
+static int step_kernels(const Op *op, int prec) { return op_kernels_per_matvec(op, prec) + 5; }
 
 // Build the while-node graph of one Arnoldi step for precision prec.
 static int build_graph(Op *op, GmresWS *ws, int prec)
@@ -515,7 +636,7 @@ static int run_cycle(Op *op, GmresWS *ws, int prec, const double *r, double *xu,
     const long long N = ws->N;
     GState *st = ws->st.as<GState>();
     k_cycle_init<<<1, 32, 0, s>>>(st, ws->g.as<double>(), m, tol_abs);
-    k_scale_first<<<vec_grid(N), GB, 0, s>>>(r, N, st, ws->V.as<double>());
+    k_scale_first<<<vec_grid(N), GB, 0, s>>>(r, N, st, ws->V.as<double>(), ws->vin.as<double>());
     SBQ_CUDA(cudaGetLastError());
     bool done = false;
     if (use_graph) {
@@ -540,11 +661,16 @@ static int run_cycle(Op *op, GmresWS *ws, int prec, const double *r, double *xu,
                 break;
         }
     }
-    k_solve_y<<<1, 32, 0, s>>>(st, ws->H.as<double>(), ws->g.as<double>(), ws->y.as<double>());
+    k_solve_y<<<1, GB, ws->solve_smem, s>>>(st, ws->H.as<double>(), ws->g.as<double>(),
+                                             ws->y.as<double>(), ws->solve_smem > 0 ? 1 : 0);
     k_update_x<<<vec_grid(N), GB, 0, s>>>(ws->V.as<double>(), N, st, ws->y.as<double>(), xu);
     SBQ_CUDA(cudaGetLastError());
     SBQ_TRY(read_state(ws, s));
     ws->launches += 4 + static_cast<long long>(ws->hst->j) * step_kernels(op, prec);
+    if (ws->hst->guard_hit) {
+        set_error("Arnoldi loop stopped by its step guard (inconsistent step counter)");
+        return SBQ_ECUDA;
+    }
     return SBQ_OK;
 }
 
@@ -588,8 +714,20 @@ int gmres_solve_impl(Op *op, const double *b, double *x, const sbq_gmres_opts &o
             rep.rel_res_hist[rep.n_hist++] = v;
     };
 
-    SBQ_TRY(residual(op, ws, SBQ_FP64, b, x, ws->r.as<double>(), s));
-    rep.matvecs_fp64 += 1;
+    // Initial residual: b itself when x0 = 0 (no operator apply needed).
+    SBQ_TRY(norm_to_state(ws, x, s));
+    if (ws->hst->res_true == 0.0) {
+        SBQ_CUDA(cudaMemcpyAsync(ws->r.p, b, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        ws->hst->res_true = bnorm;
+        k_norm_part<<<ws->nblk, GB, 0, s>>>(ws->r.as<double>(), N, ws->part.as<double>());
+        k_norm_fin<<<1, 32, 0, s>>>(ws->part.as<double>(), ws->nblk, ws->st.as<GState>());
+        SBQ_CUDA(cudaGetLastError());
+        ws->launches += 2;
+        SBQ_TRY(read_state(ws, s));
+    } else {
+        SBQ_TRY(residual(op, ws, SBQ_FP64, b, x, ws->r.as<double>(), s));
+        rep.matvecs_fp64 += 1;
+    }
     double res = ws->hst->res_true;
     push_hist(res / bnorm);
     int status = SBQ_OK;
@@ -636,8 +774,8 @@ int gmres_solve_impl(Op *op, const double *b, double *x, const sbq_gmres_opts &o
             const double inner_abs = o.inner_tol * res;
             double ires = res;
             const double *rin = ws->r.as<double>();
-            // the inner residual lives in ws->w between restarts; the first cycle starts
-            // from r itself, whose norm is in the state already
+            // the inner residual lives in ws->ax's partner buffer between restarts; the
+            // first cycle starts from r itself, whose norm is in the state already
             for (;;) {
                 const int m = std::min(o.restart, o.max_iter - rep.iters);
                 if (m <= 0)
@@ -653,20 +791,20 @@ int gmres_solve_impl(Op *op, const double *b, double *x, const sbq_gmres_opts &o
                 }
                 if (ws->hst->conv || ws->hst->brk)
                     break;
-                // restart the inner solve from its true low-precision residual
+                // restart the inner solve from its true low-precision residual r - K d,
+                // kept in w (the next cycle reads it before its first step writes w)
                 SBQ_TRY(op_matvec(op, d, ws->ax.as<double>(), low, s));
                 rep.matvecs_low += 1;
                 k_sub<<<vec_grid(N), GB, 0, s>>>(ws->r.as<double>(), ws->ax.as<double>(),
-                                                 ws->vin.as<double>(), N);
+                                                 ws->w.as<double>(), N);
                 SBQ_CUDA(cudaGetLastError());
                 ws->launches += op_kernels_per_matvec(op, low) + 1;
-                SBQ_TRY(norm_to_state(ws, ws->vin.as<double>(), s));
+                SBQ_TRY(norm_to_state(ws, ws->w.as<double>(), s));
                 const double nr = ws->hst->res_true;
                 if (!(nr < ires) || nr <= inner_abs)
                     break;
                 ires = nr;
-                // the cycle overwrites vin (k_copy_col) only after k_scale_first has read it
-                rin = ws->vin.as<double>();
+                rin = ws->w.as<double>();
             }
             if (status != SBQ_OK) {
                 set_error("non-finite value in the inner solve");

@@ -36,7 +36,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Scratch layout of one call (byte offsets from the start of the array).
 struct Layout {
-    size_t err, counter, stiles, ttiles, items, spack, tpack, partial, end;
+    size_t err, counter, stiles, ttiles, items, spack, tpack, tpack_lo, partial, end;
 };
 
 Layout make_layout(int prec, int n_st, int n_tt, int TT, int n_items, long long n_slots)
@@ -55,10 +55,13 @@ Layout make_layout(int prec, int n_st, int n_tt, int TT, int n_items, long long 
     o = align256(o + size_t(n_items) * sizeof(int4));
     L.spack = o;
     const size_t per_tile = (prec == SBQ_FP64) ? 9 * TS_F64 * sizeof(double)
-                                               : 3 * TS_F32 * sizeof(float4);
+                                               : F32_TILE_BLOCKS * TS_F32 * sizeof(float4);
     o = align256(o + size_t(n_st) * per_tile);
     L.tpack = o;
     if (prec != SBQ_FP64)
+        o = align256(o + size_t(n_tt) * TT * sizeof(float4));
+    L.tpack_lo = o;
+    if (prec == SBQ_FP32_COMP)
         o = align256(o + size_t(n_tt) * TT * sizeof(float4));
     L.partial = o;
     o = align256(o + size_t(n_slots) * 3 * TT * sizeof(double));
@@ -203,13 +206,15 @@ extern "C" SBQ_API int stokes_sl_apply_noalloc(int64_t ns, const double *src, co
     SBQ_CUDA(cudaGetLastError());
     TileInfo *stiles = reinterpret_cast<TileInfo *>(b8 + L.stiles);
     TileInfo *ttiles = reinterpret_cast<TileInfo *>(b8 + L.ttiles);
-    SBQ_CUDA(launch_pack_src_geom(prec == SBQ_FP64 ? SBQ_FP64 : SBQ_FP32, src, nullptr, ns, stiles,
+    SBQ_CUDA(launch_pack_src_geom(prec == SBQ_FP64 ? SBQ_FP64 : SBQ_FP32, src, nullptr, 1.0, ns, stiles,
                                   n_st, b8 + L.spack, s));
     int *counter = reinterpret_cast<int *>(b8 + L.counter);
     SBQ_CUDA(launch_pack_src_q(prec == SBQ_FP64 ? SBQ_FP64 : SBQ_FP32, w, sigma, ns, stiles, n_st,
                                b8 + L.spack, counter, s));
     if (prec != SBQ_FP64)
         SBQ_CUDA(launch_pack_trg(trg, nt, ttiles, n_tt, TT, reinterpret_cast<float4 *>(b8 + L.tpack),
+                                 prec == SBQ_FP32_COMP ? reinterpret_cast<float4 *>(b8 + L.tpack_lo)
+                                                       : nullptr,
                                  s));
     int kind;
     double scale, kappa;
@@ -218,6 +223,7 @@ extern "C" SBQ_API int stokes_sl_apply_noalloc(int64_t ns, const double *src, co
     p.spack = b8 + L.spack;
     p.stiles = stiles;
     p.tpack = reinterpret_cast<const float4 *>(b8 + L.tpack);
+    p.tpack_lo = reinterpret_cast<const float4 *>(b8 + L.tpack_lo);
     p.ttiles = ttiles;
     p.trg = trg;
     p.nt = nt;

@@ -41,7 +41,7 @@ __device__ float radius_up(double d2max)
 }
 
 __global__ void pack_src_geom_f32(const double *__restrict__ src, const double *__restrict__ nrm,
-                                  long long ns, TileInfo *stiles, float4 *spack)
+                                  double nscale, long long ns, TileInfo *stiles, float4 *spack)
 {
     constexpr int TS = TS_F32;
     __shared__ double red[32];
@@ -50,22 +50,26 @@ __global__ void pack_src_geom_f32(const double *__restrict__ src, const double *
     const int count = stiles[k].count;
     const long long c = begin + min(TS / 2, count - 1);
     const double cx = src[c], cy = src[ns + c], cz = src[2 * ns + c];
-    float4 *tile = spack + static_cast<size_t>(k) * 3 * TS;
+    float4 *tile = spack + static_cast<size_t>(k) * F32_TILE_BLOCKS * TS;
     double d2 = 0.0;
     if (j < count) {
         const long long s = begin + j;
         const double dx = src[s] - cx, dy = src[ns + s] - cy, dz = src[2 * ns + s] - cz;
-        tile[j] = make_float4(static_cast<float>(dx), static_cast<float>(dy),
-                              static_cast<float>(dz), 0.0f);
-        tile[2 * TS + j] = nrm ? make_float4(static_cast<float>(nrm[s]),
-                                             static_cast<float>(nrm[ns + s]),
-                                             static_cast<float>(nrm[2 * ns + s]), 0.0f)
+        const float fx = static_cast<float>(dx), fy = static_cast<float>(dy),
+                    fz = static_cast<float>(dz);
+        tile[j] = make_float4(fx, fy, fz, 0.0f);
+        tile[3 * TS + j] = make_float4(static_cast<float>(dx - fx), static_cast<float>(dy - fy),
+                                       static_cast<float>(dz - fz), 0.0f);
+        tile[2 * TS + j] = nrm ? make_float4(static_cast<float>(nscale * nrm[s]),
+                                             static_cast<float>(nscale * nrm[ns + s]),
+                                             static_cast<float>(nscale * nrm[2 * ns + s]), 0.0f)
                                : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         d2 = dx * dx + dy * dy + dz * dz;
     } else {
         tile[j] = make_float4(PAD_POS_F32, PAD_POS_F32, PAD_POS_F32, 0.0f);
         tile[TS + j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         tile[2 * TS + j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        tile[3 * TS + j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
     const double m = block_max(d2, red);
     if (j == 0) {
@@ -77,7 +81,7 @@ __global__ void pack_src_geom_f32(const double *__restrict__ src, const double *
 }
 
 __global__ void pack_src_geom_f64(const double *__restrict__ src, const double *__restrict__ nrm,
-                                  long long ns, TileInfo *stiles, double *spack)
+                                  double nscale, long long ns, TileInfo *stiles, double *spack)
 {
     constexpr int TS = TS_F64;
     __shared__ double red[32];
@@ -93,9 +97,9 @@ __global__ void pack_src_geom_f64(const double *__restrict__ src, const double *
         tile[j] = src[s];
         tile[TS + j] = src[ns + s];
         tile[2 * TS + j] = src[2 * ns + s];
-        tile[6 * TS + j] = nrm ? nrm[s] : 0.0;
-        tile[7 * TS + j] = nrm ? nrm[ns + s] : 0.0;
-        tile[8 * TS + j] = nrm ? nrm[2 * ns + s] : 0.0;
+        tile[6 * TS + j] = nrm ? nscale * nrm[s] : 0.0;
+        tile[7 * TS + j] = nrm ? nscale * nrm[ns + s] : 0.0;
+        tile[8 * TS + j] = nrm ? nscale * nrm[2 * ns + s] : 0.0;
         const double dx = src[s] - cx, dy = src[ns + s] - cy, dz = src[2 * ns + s] - cz;
         d2 = dx * dx + dy * dy + dz * dz;
     } else {
@@ -129,7 +133,7 @@ __global__ void pack_src_q_f32(const double *__restrict__ w, const double *__res
         q = make_float4(static_cast<float>(ww * sigma[s]), static_cast<float>(ww * sigma[ns + s]),
                         static_cast<float>(ww * sigma[2 * ns + s]), 0.0f);
     }
-    spack[static_cast<size_t>(k) * 3 * TS + TS + j] = q;
+    spack[static_cast<size_t>(k) * F32_TILE_BLOCKS * TS + TS + j] = q;
 }
 
 __global__ void pack_src_q_f64(const double *__restrict__ w, const double *__restrict__ sigma,
@@ -157,7 +161,7 @@ __global__ void pack_src_q_f64(const double *__restrict__ w, const double *__res
 }
 
 __global__ void pack_trg_f32(const double *__restrict__ trg, long long nt, TileInfo *ttiles, int TT,
-                             float4 *tpack)
+                             float4 *tpack, float4 *tpack_lo)
 {
     __shared__ double red[32];
     const int k = blockIdx.x;
@@ -167,15 +171,19 @@ __global__ void pack_trg_f32(const double *__restrict__ trg, long long nt, TileI
     const double cx = trg[c], cy = trg[nt + c], cz = trg[2 * nt + c];
     double d2 = 0.0;
     for (int j = threadIdx.x; j < TT; j += blockDim.x) {
-        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f), l = v;
         if (j < count) {
             const long long t = begin + j;
             const double dx = trg[t] - cx, dy = trg[nt + t] - cy, dz = trg[2 * nt + t] - cz;
             v = make_float4(static_cast<float>(dx), static_cast<float>(dy), static_cast<float>(dz),
                             0.0f);
+            l = make_float4(static_cast<float>(dx - v.x), static_cast<float>(dy - v.y),
+                            static_cast<float>(dz - v.z), 0.0f);
             d2 = fmax(d2, dx * dx + dy * dy + dz * dz);
         }
         tpack[static_cast<size_t>(k) * TT + j] = v;
+        if (tpack_lo)
+            tpack_lo[static_cast<size_t>(k) * TT + j] = l;
     }
     const double m = block_max(d2, red);
     if (threadIdx.x == 0) {
@@ -223,16 +231,17 @@ __global__ void csr_apply_kernel(long long nrows, const int64_t *__restrict__ ro
 
 }  // namespace
 
-cudaError_t launch_pack_src_geom(int prec, const double *src, const double *nrm, long long ns,
-                                 TileInfo *stiles, int n_stiles, void *spack, cudaStream_t s)
+cudaError_t launch_pack_src_geom(int prec, const double *src, const double *nrm, double nscale,
+                                 long long ns, TileInfo *stiles, int n_stiles, void *spack,
+                                 cudaStream_t s)
 {
     if (n_stiles <= 0)
         return cudaSuccess;
     if (prec == SBQ_FP64)
-        pack_src_geom_f64<<<n_stiles, TS_F64, 0, s>>>(src, nrm, ns, stiles,
+        pack_src_geom_f64<<<n_stiles, TS_F64, 0, s>>>(src, nrm, nscale, ns, stiles,
                                                        static_cast<double *>(spack));
     else
-        pack_src_geom_f32<<<n_stiles, TS_F32, 0, s>>>(src, nrm, ns, stiles,
+        pack_src_geom_f32<<<n_stiles, TS_F32, 0, s>>>(src, nrm, nscale, ns, stiles,
                                                        static_cast<float4 *>(spack));
     return cudaGetLastError();
 }
@@ -253,11 +262,11 @@ cudaError_t launch_pack_src_q(int prec, const double *w, const double *sigma, lo
 }
 
 cudaError_t launch_pack_trg(const double *trg, long long nt, TileInfo *ttiles, int n_ttiles, int TT,
-                            float4 *tpack, cudaStream_t s)
+                            float4 *tpack, float4 *tpack_lo, cudaStream_t s)
 {
     if (n_ttiles <= 0)
         return cudaSuccess;
-    pack_trg_f32<<<n_ttiles, 256, 0, s>>>(trg, nt, ttiles, TT, tpack);
+    pack_trg_f32<<<n_ttiles, 256, 0, s>>>(trg, nt, ttiles, TT, tpack, tpack_lo);
     return cudaGetLastError();
 }
 
@@ -321,7 +330,9 @@ bool pairsum_shape_supported(int prec, int R, int W)
 
 size_t pairsum_smem_bytes(int prec)
 {
-    return prec == SBQ_FP64 ? 2 * 9 * TS_F64 * sizeof(double) : 2 * 3 * TS_F32 * sizeof(float4);
+    if (prec == SBQ_FP64)
+        return 2 * 9 * TS_F64 * sizeof(double);
+    return 2 * (prec == SBQ_FP32_COMP ? F32_TILE_BLOCKS : 3) * TS_F32 * sizeof(float4);
 }
 
 }  // namespace sbq

@@ -15,28 +15,42 @@
 // FP32 path: targets and sources are stored relative to their tile centre (FP64
 // subtraction, then rounding), and per (target tile, source tile) the FP64 offset of
 // the two centres is rounded once and added to the targets.  Pairs whose tiles cannot
-// contain coincident points skip the r^2 == 0 test.  The compensated variant sums runs
-// of COMP_RUN sources in FP32 and merges each run into a (hi, lo) pair with TwoSum.
+// contain coincident points skip the r^2 == 0 test.  The compensated variant
+//  * sums runs of COMP_RUN sources in FP32 and merges each run into a (hi, lo) pair
+//    with TwoSum, and
+//  * in tile pairs whose tiles come within one tile extent of each other (where the
+//    rounding of the centred coordinates is not small next to the pair distance) forms
+//    r = x - y from high and low FP32 parts of both points and of the centre offset, so
+//    that the difference of nearby points keeps its full FP32 accuracy.
 #pragma once
 
 #include "sbq_common.cuh"
 
 namespace sbq {
 
-// Per-pair arithmetic, FP32.  Accumulates (folded prefactors, see the launcher):
+// 1/sqrt(x) on the SFU, denormals flushed (x is a squared distance between distinct
+// points, far above the FP32 denormal range for any admissible input).
+__device__ __forceinline__ float rsqrt_sfu(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Per-pair arithmetic, FP32, given r = (dx, dy, dz).  Accumulates (folded prefactors,
+// see the launcher):
 //   SL: ri q + (r.q) ri^3 r
 //   DL: (r.q)(r.n) ri^5 r
-//   CF: ri q + (r.q) ri^3 (1 + kappa (r.n) ri^2) r
+//   CF: ri q + (r.q) ri^3 (1 + (r.n') ri^2) r,  n' = kappa n stored by the pack
 template <int KIND, bool CHECK>
-__device__ __forceinline__ void pair_f32(float xh, float yh, float zh, const float4 &P,
-                                         const float4 &Q, const float4 &N, float kappa, float &ax,
-                                         float &ay, float &az)
+__device__ __forceinline__ void pair_f32_r(float dx, float dy, float dz, const float4 &Q,
+                                           const float4 &N, float thr2, float &ax, float &ay,
+                                           float &az)
 {
-    const float dx = xh - P.x, dy = yh - P.y, dz = zh - P.z;
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    float ri = rsqrtf(r2);
+    float ri = rsqrt_sfu(r2);
     if (CHECK)
-        ri = (r2 > 0.0f) ? ri : 0.0f;
+        ri = (r2 > thr2) ? ri : 0.0f;
     const float rq = fmaf(dx, Q.x, fmaf(dy, Q.y, dz * Q.z));
     const float ri2 = ri * ri;
     if (KIND == KIND_SL) {
@@ -55,7 +69,7 @@ __device__ __forceinline__ void pair_f32(float xh, float yh, float zh, const flo
         az = fmaf(b, dz, az);
     } else {
         const float rn = fmaf(dx, N.x, fmaf(dy, N.y, dz * N.z));
-        const float g = fmaf(kappa, rn * ri2, 1.0f);
+        const float g = fmaf(rn, ri2, 1.0f);
         const float b = (rq * ri2) * (ri * g);
         ax = fmaf(ri, Q.x, ax);
         ay = fmaf(ri, Q.y, ay);
@@ -76,12 +90,17 @@ __device__ __forceinline__ void two_sum_merge(float &hi, float &lo, float b)
     lo += e;
 }
 
-template <int KIND, int R, bool CHECK, bool COMP>
-__device__ __forceinline__ void tile_f32(const float4 *__restrict__ sp, const float (&xh)[R],
-                                         const float (&yh)[R], const float (&zh)[R], float kappa,
-                                         float (&ax)[R], float (&ay)[R], float (&az)[R],
-                                         float (&hx)[R], float (&hy)[R], float (&hz)[R],
-                                         float (&lx)[R], float (&ly)[R], float (&lz)[R])
+// One staged source tile applied to the thread's R targets.  HILO: targets carry low
+// parts (xl, yl, zl) and the tile its low block at sp[3 * TS + j].  CHECK: pairs with
+// r^2 <= thr2 count as coincident and are skipped.
+template <int KIND, int R, bool CHECK, bool COMP, bool HILO>
+__device__ __forceinline__ void tile_f32(const float4 *__restrict__ sp, float thr2, const float (&xh)[R],
+                                         const float (&yh)[R], const float (&zh)[R],
+                                         const float (&xl)[R], const float (&yl)[R],
+                                         const float (&zl)[R], float (&ax)[R], float (&ay)[R],
+                                         float (&az)[R], float (&hx)[R], float (&hy)[R],
+                                         float (&hz)[R], float (&lx)[R], float (&ly)[R],
+                                         float (&lz)[R])
 {
     constexpr int TS = TS_F32;
     constexpr int RUN = COMP ? COMP_RUN : TS;
@@ -91,12 +110,21 @@ __device__ __forceinline__ void tile_f32(const float4 *__restrict__ sp, const fl
         for (int j = j0; j < j0 + RUN; ++j) {
             const float4 P = sp[j];
             const float4 Q = sp[TS + j];
-            float4 N;
+            float4 N, L;
             if (KIND != KIND_SL)
                 N = sp[2 * TS + j];
+            if (HILO)
+                L = sp[3 * TS + j];
 #pragma unroll
-            for (int r = 0; r < R; ++r)
-                pair_f32<KIND, CHECK>(xh[r], yh[r], zh[r], P, Q, N, kappa, ax[r], ay[r], az[r]);
+            for (int r = 0; r < R; ++r) {
+                float dx = xh[r] - P.x, dy = yh[r] - P.y, dz = zh[r] - P.z;
+                if (HILO) {
+                    dx += xl[r] - L.x;
+                    dy += yl[r] - L.y;
+                    dz += zl[r] - L.z;
+                }
+                pair_f32_r<KIND, CHECK>(dx, dy, dz, Q, N, thr2, ax[r], ay[r], az[r]);
+            }
         }
         if (COMP) {
 #pragma unroll
@@ -110,15 +138,25 @@ __device__ __forceinline__ void tile_f32(const float4 *__restrict__ sp, const fl
     }
 }
 
+// x + d = s + e exactly (TwoSum), returning s; e is added to lo.
+__device__ __forceinline__ float two_sum_add(float x, float d, float &lo)
+{
+    const float s = x + d;
+    const float bb = s - x;
+    lo += (x - (s - bb)) + (d - bb);
+    return s;
+}
+
 template <int KIND, int R, int W, bool COMP>
 __global__ void __launch_bounds__(W * 32) pairsum_f32_kernel(const PairsumParams p)
 {
     constexpr int NT = W * 32;
     constexpr int TT = NT * R;
     constexpr int TS = TS_F32;
-    constexpr int NF = (KIND == KIND_SL) ? 2 : 3;
+    constexpr int NF = COMP ? F32_TILE_BLOCKS : ((KIND == KIND_SL) ? 2 : 3);
     constexpr uint32_t TILE_BYTES = NF * TS * sizeof(float4);
-    constexpr int STAGE = 3 * TS;   // float4 per stage (and per packed tile)
+    constexpr int STAGE = (COMP ? F32_TILE_BLOCKS : 3) * TS;   // float4 per smem stage
+    constexpr int GSTRIDE = F32_TILE_BLOCKS * TS;               // float4 per packed tile
 
     extern __shared__ __align__(128) float4 sbuf[];
     __shared__ __align__(8) uint64_t bar[2];
@@ -127,7 +165,6 @@ __global__ void __launch_bounds__(W * 32) pairsum_f32_kernel(const PairsumParams
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const float4 *__restrict__ spack = static_cast<const float4 *>(p.spack);
-    const float kappa = static_cast<float>(p.kappa);
 
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -149,10 +186,10 @@ __global__ void __launch_bounds__(W * 32) pairsum_f32_kernel(const PairsumParams
         const TileInfo tt = p.ttiles[it.x];
 
         float tx[R], ty[R], tz[R];
-        const float4 *tp = p.tpack + static_cast<size_t>(it.x) * TT + warp * 32 * R + lane;
+        const size_t toff = static_cast<size_t>(it.x) * TT + warp * 32 * R + lane;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const float4 v = tp[r * 32];
+            const float4 v = p.tpack[toff + r * 32];
             tx[r] = v.x;
             ty[r] = v.y;
             tz[r] = v.z;
@@ -169,8 +206,8 @@ __global__ void __launch_bounds__(W * 32) pairsum_f32_kernel(const PairsumParams
         if (tid == 0) {
             const int st = g & 1;
             mbar_arrive_expect_tx(&bar[st], TILE_BYTES);
-            bulk_copy_g2s(sbuf + st * STAGE, spack + static_cast<size_t>(it.y) * STAGE, TILE_BYTES,
-                          &bar[st]);
+            bulk_copy_g2s(sbuf + st * STAGE, spack + static_cast<size_t>(it.y) * GSTRIDE,
+                          TILE_BYTES, &bar[st]);
         }
         for (int k = 0; k < nk; ++k) {
             const uint32_t gk = g + k;
@@ -178,8 +215,9 @@ __global__ void __launch_bounds__(W * 32) pairsum_f32_kernel(const PairsumParams
             if (tid == 0 && k + 1 < nk) {
                 const int sn = (gk + 1) & 1;
                 mbar_arrive_expect_tx(&bar[sn], TILE_BYTES);
-                bulk_copy_g2s(sbuf + sn * STAGE, spack + static_cast<size_t>(it.y + k + 1) * STAGE,
-                              TILE_BYTES, &bar[sn]);
+                bulk_copy_g2s(sbuf + sn * STAGE,
+                              spack + static_cast<size_t>(it.y + k + 1) * GSTRIDE, TILE_BYTES,
+                              &bar[sn]);
             }
             const bool timed_out = !mbar_wait_bounded(&bar[st], (gk >> 1) & 1);
             if (__syncthreads_or(timed_out)) {
@@ -196,23 +234,49 @@ __global__ void __launch_bounds__(W * 32) pairsum_f32_kernel(const PairsumParams
             const double ddx = tt.cx - si.cx, ddy = tt.cy - si.cy, ddz = tt.cz - si.cz;
             const double dist = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
             const double lim = static_cast<double>(tt.rad) + static_cast<double>(si.rad);
+            // near: the tiles may hold coincident points; hilo: within one tile extent.
+            // A coincident pair can come out of the FP32 centring as a difference of a few
+            // ulps of the tile extent rather than an exact zero, so pairs closer than
+            // COINCIDENT_REL x (sum of the two tile radii) count as coincident.
             const bool near = (dist - lim) <= 1.0e-5 * (dist + lim) + 1.0e-30;
+            const float thr = static_cast<float>(COINCIDENT_REL * lim);
+            const float thr2 = thr * thr;
+            const bool hilo = COMP && (dist <= 2.0 * lim);
             const float sx = static_cast<float>(ddx), sy = static_cast<float>(ddy),
                         sz = static_cast<float>(ddz);
-            float xh[R], yh[R], zh[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                xh[r] = tx[r] + sx;
-                yh[r] = ty[r] + sy;
-                zh[r] = tz[r] + sz;
-            }
+            float xh[R], yh[R], zh[R], xl[R], yl[R], zl[R];
             const float4 *sp = sbuf + st * STAGE;
-            if (near)
-                tile_f32<KIND, R, true, COMP>(sp, xh, yh, zh, kappa, ax, ay, az, hx, hy, hz, lx, ly,
-                                              lz);
-            else
-                tile_f32<KIND, R, false, COMP>(sp, xh, yh, zh, kappa, ax, ay, az, hx, hy, hz, lx,
-                                               ly, lz);
+            if (hilo) {
+                const float slx = static_cast<float>(ddx - static_cast<double>(sx));
+                const float sly = static_cast<float>(ddy - static_cast<double>(sy));
+                const float slz = static_cast<float>(ddz - static_cast<double>(sz));
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float4 l = p.tpack_lo[toff + r * 32];   // only hilo tiles need it
+                    xl[r] = l.x + slx;
+                    yl[r] = l.y + sly;
+                    zl[r] = l.z + slz;
+                    xh[r] = two_sum_add(tx[r], sx, xl[r]);
+                    yh[r] = two_sum_add(ty[r], sy, yl[r]);
+                    zh[r] = two_sum_add(tz[r], sz, zl[r]);
+                }
+                tile_f32<KIND, R, true, COMP, COMP>(sp, thr2, xh, yh, zh, xl, yl, zl, ax, ay, az, hx,
+                                                     hy, hz, lx, ly, lz);
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    xh[r] = tx[r] + sx;
+                    yh[r] = ty[r] + sy;
+                    zh[r] = tz[r] + sz;
+                    xl[r] = yl[r] = zl[r] = 0.0f;
+                }
+                if (near)
+                    tile_f32<KIND, R, true, COMP, false>(sp, thr2, xh, yh, zh, xl, yl, zl, ax, ay, az,
+                                                         hx, hy, hz, lx, ly, lz);
+                else
+                    tile_f32<KIND, R, false, COMP, false>(sp, thr2, xh, yh, zh, xl, yl, zl, ax, ay,
+                                                          az, hx, hy, hz, lx, ly, lz);
+            }
             __syncthreads();   // stage st may be refilled from here on
         }
         g += nk;
@@ -254,12 +318,13 @@ __global__ void __launch_bounds__(W * 32) pairsum_f32_kernel(const PairsumParams
     }
 }
 
+
 // ---------------------------------------------------------------------------
 // FP64
 // ---------------------------------------------------------------------------
 template <int KIND>
 __device__ __forceinline__ void pair_f64(double x, double y, double z, const double *__restrict__ s,
-                                         int j, double kappa, double &ax, double &ay, double &az)
+                                         int j, double &ax, double &ay, double &az)
 {
     constexpr int TS = TS_F64;
     const double dx = x - s[j], dy = y - s[TS + j], dz = z - s[2 * TS + j];
@@ -284,7 +349,7 @@ __device__ __forceinline__ void pair_f64(double x, double y, double z, const dou
             ay = fma(b, dy, ay);
             az = fma(b, dz, az);
         } else {
-            const double gg = fma(kappa, rn * ri2, 1.0);
+            const double gg = fma(rn, ri2, 1.0);
             const double b = (rq * ri2) * (ri * gg);
             ax = fma(ri, qx, ax);
             ay = fma(ri, qy, ay);
@@ -374,7 +439,7 @@ __global__ void __launch_bounds__(W * 32) pairsum_f64_kernel(const PairsumParams
             for (int j = 0; j < TS; ++j) {
 #pragma unroll
                 for (int r = 0; r < R; ++r)
-                    pair_f64<KIND>(tx[r], ty[r], tz[r], sp, j, p.kappa, ax[r], ay[r], az[r]);
+                    pair_f64<KIND>(tx[r], ty[r], tz[r], sp, j, ax[r], ay[r], az[r]);
             }
             __syncthreads();
         }
@@ -414,7 +479,7 @@ struct KindLauncher {
     template <int R, int W, bool COMP>
     static cudaError_t f32(int grid, const PairsumParams &p, cudaStream_t s)
     {
-        const size_t smem = 2 * 3 * TS_F32 * sizeof(float4);
+        const size_t smem = pairsum_smem_bytes(COMP ? SBQ_FP32_COMP : SBQ_FP32);
         pairsum_f32_kernel<KIND, R, W, COMP><<<grid, W * 32, smem, s>>>(p);
         return cudaGetLastError();
     }
@@ -430,7 +495,8 @@ struct KindLauncher {
     {
         int b = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pairsum_f32_kernel<KIND, R, W, COMP>, W * 32,
-                                                      2 * 3 * TS_F32 * sizeof(float4));
+                                                      pairsum_smem_bytes(COMP ? SBQ_FP32_COMP
+                                                                              : SBQ_FP32));
         return b;
     }
     template <int R, int W>

@@ -17,13 +17,21 @@ namespace sbq {
 // (paper Eqs. stokes-sl, stokes-dl, stokes-bie-new).
 enum Kind { KIND_SL = 0, KIND_DL = 1, KIND_CF = 2 };
 
-// Sources per shared-memory tile.  FP32 tiles hold float4 {pos, q, n}; FP64 tiles
-// hold 9 doubles per source {x, y, z, qx, qy, qz, nx, ny, nz}, each field a run of TS.
+// Sources per shared-memory tile.  FP32 tiles hold float4 blocks {pos, q, n, pos_lo}
+// (pos_lo: the part of the centred FP64 position lost when rounding it to FP32); FP64
+// tiles hold 9 doubles per source {x, y, z, qx, qy, qz, nx, ny, nz}, each field a run
+// of TS.
 constexpr int TS_F32 = 256;
+constexpr int F32_TILE_BLOCKS = 4;
 constexpr int TS_F64 = 128;
 // Compensated FP32: plain FP32 sums over runs of this many sources are merged into
 // the (hi, lo) pair with TwoSum.
 constexpr int COMP_RUN = 64;
+// FP32 paths: pairs closer than this fraction of the sum of their two tile radii are
+// taken as coincident (skipped).  The FP32 centring rounds a coincident pair to at most
+// ~5 ulps of that sum (3e-7 of it), well below this threshold; distinct nodes of any
+// admissible discretisation are far above it.
+constexpr double COINCIDENT_REL = 4.0e-6;
 // Position of padding sources in the last (ragged) tile of a segment.  Their weight
 // and normal are zero, so every term they produce is an exact zero.
 constexpr float PAD_POS_F32 = 1.0e15f;
@@ -50,6 +58,7 @@ struct PairsumParams {
     const void *spack;          // packed source tiles
     const TileInfo *stiles;     // source tile table
     const float4 *tpack;        // FP32 paths: packed targets [ttile][TT] (x - c, y - c, z - c, 0)
+    const float4 *tpack_lo;     // FP32 paths: parts of the centred targets lost to rounding
     const TileInfo *ttiles;     // target tile table
     const double *trg;          // FP64 path: targets (SoA, stride nt)
     long long nt;               // global number of targets (stride of trg / out / diag_sigma)
@@ -62,7 +71,7 @@ struct PairsumParams {
     const double *diag_sigma;   // nullable: out += diag * diag_sigma (same indexing as out)
     double diag;
     double scale;               // prefactor applied to the accumulated sum
-    double kappa;               // combined field: 6 beta / alpha (ratio of D to S prefactors)
+    double kappa;               // combined field: 6 beta / alpha (folded into the packed normals)
     int TT;                     // targets per target tile
 };
 
@@ -176,13 +185,15 @@ bool pairsum_shape_supported(int prec, int R, int W);
 size_t pairsum_smem_bytes(int prec);
 
 // pack.cu
-cudaError_t launch_pack_src_geom(int prec, const double *src, const double *nrm, long long ns,
-                                 TileInfo *stiles, int n_stiles, void *spack, cudaStream_t s);
+// nscale multiplies the packed normals (the combined-field kernels read kappa * n).
+cudaError_t launch_pack_src_geom(int prec, const double *src, const double *nrm, double nscale,
+                                 long long ns, TileInfo *stiles, int n_stiles, void *spack,
+                                 cudaStream_t s);
 cudaError_t launch_pack_src_q(int prec, const double *w, const double *sigma, long long ns,
                               const TileInfo *stiles, int n_stiles, void *spack, int *counter,
                               cudaStream_t s);
 cudaError_t launch_pack_trg(const double *trg, long long nt, TileInfo *ttiles, int n_ttiles,
-                            int TT, float4 *tpack, cudaStream_t s);
+                            int TT, float4 *tpack, float4 *tpack_lo, cudaStream_t s);
 cudaError_t launch_reduce_partials(const TileInfo *ttiles, int n_ttiles, int TT,
                                    const double *partial, long long nt, double *out,
                                    double scale, double diag, const double *diag_sigma,

@@ -111,6 +111,46 @@ def test_apply_sizes_and_tails(sbq, oracle_mod, ns, nt, prec):
     assert _relerr(u, ref) <= tol
 
 
+@pytest.mark.parametrize("kind", ["sl", "dl", "cf"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32c"])
+def test_coincident_targets_in_misaligned_tiles(sbq, oracle_mod, kind, prec):
+    """Targets that coincide with sources but sit in target tiles whose centres differ from
+    the source tiles' (the nodes in rotated order, and every third node): the punctured sum
+    must skip exactly the coincident pairs whatever the FP32 centring does to them."""
+    c = I.config2(panels=2)
+    s = c["surf"]
+    sig = I.density(s.size, seed=9)
+    for trg in (np.roll(s.x, 37, axis=1), s.x[:, ::3]):
+        u = _apply(sbq, kind, s.x, s.n, s.w, sig, trg, prec)
+        ref = _oracle(oracle_mod, kind, s.x, s.n, s.w, sig, trg)
+        assert np.all(np.isfinite(u))
+        err = _relerr(u, ref)
+        print("misaligned %s %s relerr %.3e" % (kind, prec, err))
+        assert err <= (TOL_F64 if prec == "fp64" else TOL_F32[prec])
+
+
+@pytest.mark.parametrize("shape", [(2, 4), (4, 4), (8, 4), (4, 8), (1, 4)])
+@pytest.mark.parametrize("chunk", [0, 3])
+def test_operator_matvec_every_tile_shape(sbq, oracle_mod, shape, chunk):
+    """Each supported tile shape (targets per CTA 256..1024, tiles not aligned with the
+    256-point source tiles) and chunking gives the operator within the bars."""
+    s, _, sig = _small_op_case()
+    eta = sbq.slender_eta(0.2)
+    ref = oracle_mod.matvec(s.x, s.n, s.w, eta, sig)
+    r, w = shape
+    plan = sbq.BatchPlan([0, s.size], tune=dict(r=r, warps=w, chunk_tiles=chunk))
+    op = sbq.StokesOp(_t(s.x), _t(s.n), _t(s.w), eta, plan=plan)
+    precs = ["fp64"] if r == 1 else ["fp32", "fp32c"]
+    if (r, w) == (2, 4):
+        precs.append("fp64")
+    for prec in precs:
+        out = _np(op.matvec(_t(sig), prec=prec))
+        err = _relerr(out, ref)
+        print("shape %s chunk %d %s relerr %.3e" % (shape, chunk, prec, err))
+        assert err <= (TOL_F64 if prec == "fp64" else TOL_F32[prec])
+    op.close()
+
+
 def test_apply_empty_inputs(sbq):
     import torch
     trg = _t(np.ones((3, 5)))
