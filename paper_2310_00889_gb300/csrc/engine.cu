@@ -272,13 +272,15 @@ int build_trg_set(TrgSet &ts, int kind, int prec, const sbq_tune &tune, const Sr
         const int sb = sp.seg_tile_begin[i], sn = sp.seg_tile_count[i];
         const int ci = std::max(1, std::min(C, sn));
         const int nchunk = (sn + ci - 1) / ci;
+        // FP32 kernels always write partial slots (their FP64 epilogue is the reduction)
+        const bool slots = nchunk > 1 || prec != SBQ_FP64;
         for (int k = 0; k < seg_ntt[i]; ++k) {
             TileInfo ti{};
             ti.begin = trg_off[i] + static_cast<long long>(k) * TT;
             ti.count = static_cast<int>(std::min<long long>(TT, trg_off[i + 1] - ti.begin));
             ti.seg = i;
             const int tidx = static_cast<int>(ht.size());
-            if (nchunk > 1) {
+            if (slots) {
                 ti.slot_begin = slot;
                 ti.slot_count = nchunk;
             } else {
@@ -288,11 +290,11 @@ int build_trg_set(TrgSet &ts, int kind, int prec, const sbq_tune &tune, const Sr
             for (int c = 0; c < nchunk; ++c) {
                 const int a = sb + c * ci, b = std::min(sb + sn, a + ci);
                 Item it;
-                it.v = make_int4(tidx, a, b, nchunk > 1 ? slot + c : -1);
+                it.v = make_int4(tidx, a, b, slots ? slot + c : -1);
                 it.cost = b - a;
                 items.push_back(it);
             }
-            if (nchunk > 1)
+            if (slots)
                 slot += nchunk;
             ht.push_back(ti);
         }
@@ -366,7 +368,11 @@ int run_pairsum(int kind, int prec, const SrcPack &sp, const TrgSet &ts, const d
     p.kappa = kappa;
     p.TT = ts.TT;
     SBQ_CUDA(launch_pairsum(kind, prec, ts.tune.r, ts.tune.warps, ts.grid, p, s));
-    if (ts.needs_reduce)
+    if (prec != SBQ_FP64)
+        SBQ_CUDA(launch_reduce_partials_f32(ts.ttiles.as<TileInfo>(), ts.n_ttiles, ts.TT,
+                                            ts.partial.p, nt, out, scale, diag, diag_sigma,
+                                            prec == SBQ_FP32_COMP ? 1 : 0, s));
+    else if (ts.needs_reduce)
         SBQ_CUDA(launch_reduce_partials(ts.ttiles.as<TileInfo>(), ts.n_ttiles, ts.TT,
                                         ts.partial.as<double>(), nt, out, scale, diag, diag_sigma,
                                         s));
@@ -386,7 +392,7 @@ int op_kernels_per_matvec(const Op *op, int prec)
     const TrgSet *ts = op->ts[prec].get();
     int k = 0;
     if (ts && ts->n_items > 0)
-        k += 2 + (ts->needs_reduce ? 1 : 0);
+        k += 2 + ((ts->needs_reduce || prec != SBQ_FP64) ? 1 : 0);
     if (op->nnz > 0)
         k += 1;
     return k;

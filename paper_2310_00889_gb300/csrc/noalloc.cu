@@ -72,7 +72,7 @@ Layout make_layout(int prec, int n_st, int n_tt, int TT, int n_items, long long 
 // Tile tables and work list of a single segment, written on the device so that the call
 // needs no host staging buffer either; zeroes the error word and the claim counter.
 __global__ void noalloc_tables(unsigned char *base, Layout L, long long ns, long long nt, int TS,
-                               int TT, int n_st, int n_tt, int n_chunks, int C)
+                               int TT, int n_st, int n_tt, int n_chunks, int C, int slots)
 {
     TileInfo *stiles = reinterpret_cast<TileInfo *>(base + L.stiles);
     TileInfo *ttiles = reinterpret_cast<TileInfo *>(base + L.ttiles);
@@ -97,15 +97,15 @@ __global__ void noalloc_tables(unsigned char *base, Layout L, long long ns, long
         ti.begin = k * TT;
         ti.count = static_cast<int>(min(static_cast<long long>(TT), nt - ti.begin));
         ti.seg = 0;
-        ti.slot_begin = n_chunks > 1 ? static_cast<int>(k * n_chunks) : -1;
-        ti.slot_count = n_chunks > 1 ? n_chunks : 0;
+        ti.slot_begin = slots ? static_cast<int>(k * n_chunks) : -1;
+        ti.slot_count = slots ? n_chunks : 0;
         ttiles[k] = ti;
     }
     const long long n_items = static_cast<long long>(n_tt) * n_chunks;
     for (long long i = tid; i < n_items; i += stride) {
         const int k = static_cast<int>(i / n_chunks), c = static_cast<int>(i % n_chunks);
         const int a = c * C, b = min(n_st, a + C);
-        items[i] = make_int4(k, a, b, n_chunks > 1 ? k * n_chunks + c : -1);
+        items[i] = make_int4(k, a, b, slots ? k * n_chunks + c : -1);
     }
 }
 
@@ -186,7 +186,8 @@ extern "C" SBQ_API int stokes_sl_apply_noalloc(int64_t ns, const double *src, co
         const int C = (n_st + n_chunks - 1) / n_chunks;
         n_chunks = (n_st + C - 1) / C;
         L = make_layout(prec, n_st, n_tt, TT, n_tt * n_chunks,
-                        n_chunks > 1 ? static_cast<long long>(n_tt) * n_chunks : 0);
+                        (n_chunks > 1 || prec != SBQ_FP64) ? static_cast<long long>(n_tt) * n_chunks
+                                                           : 0);
         if (L.end <= NOALLOC_SCRATCH_BYTES || n_chunks == 1)
             break;
         n_chunks = std::max(1, n_chunks / 2);
@@ -202,7 +203,9 @@ extern "C" SBQ_API int stokes_sl_apply_noalloc(int64_t ns, const double *src, co
     const int tb = 256;
     const int tg = static_cast<int>(std::min<long long>(
         1024, std::max<long long>(1, (std::max<long long>(n_items, std::max(n_st, n_tt)) + tb - 1) / tb)));
-    noalloc_tables<<<tg, tb, 0, s>>>(b8, L, ns, nt, TS, TT, n_st, n_tt, n_chunks, C);
+    // FP32 kernels always write partial slots; the FP64 kernel only with several chunks
+    const int use_slots = (n_chunks > 1 || prec != SBQ_FP64) ? 1 : 0;
+    noalloc_tables<<<tg, tb, 0, s>>>(b8, L, ns, nt, TS, TT, n_st, n_tt, n_chunks, C, use_slots);
     SBQ_CUDA(cudaGetLastError());
     TileInfo *stiles = reinterpret_cast<TileInfo *>(b8 + L.stiles);
     TileInfo *ttiles = reinterpret_cast<TileInfo *>(b8 + L.ttiles);
@@ -240,7 +243,10 @@ extern "C" SBQ_API int stokes_sl_apply_noalloc(int64_t ns, const double *src, co
     p.TT = TT;
     const int grid = static_cast<int>(std::min<long long>(n_items, slots));
     SBQ_CUDA(launch_pairsum(kind, prec, R, W, grid, p, s));
-    if (n_chunks > 1)
+    if (prec != SBQ_FP64)
+        SBQ_CUDA(launch_reduce_partials_f32(ttiles, n_tt, TT, p.partial, nt, u, scale, 0.0, nullptr,
+                                            prec == SBQ_FP32_COMP ? 1 : 0, s));
+    else if (n_chunks > 1)
         SBQ_CUDA(launch_reduce_partials(ttiles, n_tt, TT, p.partial, nt, u, scale, 0.0, nullptr, s));
     return SBQ_OK;
 }

@@ -33,6 +33,53 @@ __device__ double block_max(double v, double *red)
     return v;   // valid in thread 0
 }
 
+// Block-wide min and max of x, y, z (blockDim.x a multiple of 32); lo/hi valid in all
+// threads on return.  Threads without a point pass +inf / -inf.
+__device__ void block_bbox(double (&lo)[3], double (&hi)[3], double (*red)[32])
+{
+    for (int c = 0; c < 3; ++c)
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[c] = fmin(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
+            hi[c] = fmax(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+        }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0)
+        for (int c = 0; c < 3; ++c) {
+            red[c][warp] = lo[c];
+            red[3 + c][warp] = hi[c];
+        }
+    __syncthreads();
+    for (int c = 0; c < 3; ++c) {
+        lo[c] = red[c][0];
+        hi[c] = red[3 + c][0];
+        for (int w = 1; w < nw; ++w) {
+            lo[c] = fmin(lo[c], red[c][w]);
+            hi[c] = fmax(hi[c], red[3 + c][w]);
+        }
+    }
+}
+
+// Centre of a tile: the midpoint of its points' bounding box (the tile's bounding sphere
+// about it is at most half the box diagonal, smaller than about any member node).
+__device__ void tile_centre(const double *__restrict__ pts, long long stride, long long begin,
+                            int count, int tile_size, double (*red)[32], double &cx, double &cy,
+                            double &cz)
+{
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int j = threadIdx.x; j < tile_size; j += blockDim.x)
+        if (j < count)
+            for (int c = 0; c < 3; ++c) {
+                const double v = pts[c * stride + begin + j];
+                lo[c] = fmin(lo[c], v);
+                hi[c] = fmax(hi[c], v);
+            }
+    block_bbox(lo, hi, red);
+    cx = 0.5 * (lo[0] + hi[0]);
+    cy = 0.5 * (lo[1] + hi[1]);
+    cz = 0.5 * (lo[2] + hi[2]);
+}
+
 // Radius rounded up so that the FP32 value bounds every FP64 distance.
 __device__ float radius_up(double d2max)
 {
@@ -45,11 +92,12 @@ __global__ void pack_src_geom_f32(const double *__restrict__ src, const double *
 {
     constexpr int TS = TS_F32;
     __shared__ double red[32];
+    __shared__ double bb[6][32];
     const int k = blockIdx.x, j = threadIdx.x;
     const long long begin = stiles[k].begin;
     const int count = stiles[k].count;
-    const long long c = begin + min(TS / 2, count - 1);
-    const double cx = src[c], cy = src[ns + c], cz = src[2 * ns + c];
+    double cx, cy, cz;
+    tile_centre(src, ns, begin, count, TS, bb, cx, cy, cz);
     float4 *tile = spack + static_cast<size_t>(k) * F32_TILE_BLOCKS * TS;
     double d2 = 0.0;
     if (j < count) {
@@ -164,11 +212,12 @@ __global__ void pack_trg_f32(const double *__restrict__ trg, long long nt, TileI
                              float4 *tpack, float4 *tpack_lo)
 {
     __shared__ double red[32];
+    __shared__ double bb[6][32];
     const int k = blockIdx.x;
     const long long begin = ttiles[k].begin;
     const int count = ttiles[k].count;
-    const long long c = begin + min(TT / 2, count - 1);
-    const double cx = trg[c], cy = trg[nt + c], cz = trg[2 * nt + c];
+    double cx, cy, cz;
+    tile_centre(trg, nt, begin, count, TT, bb, cx, cy, cz);
     double d2 = 0.0;
     for (int j = threadIdx.x; j < TT; j += blockDim.x) {
         float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f), l = v;
@@ -209,6 +258,38 @@ __global__ void reduce_partials_kernel(const TileInfo *__restrict__ ttiles, int 
             for (int q = 0; q < ti.slot_count; ++q)
                 s += partial[(static_cast<size_t>(ti.slot_begin + q) * 3 + c) * TT + loc];
             double o = scale * s;
+            if (diag_sigma)
+                o += diag * diag_sigma[c * nt + t];
+            out[c * nt + t] = o;
+        }
+    }
+}
+
+// FP32 partials: (hi, lo) float pairs per (slot, component, target).  Compensated sums
+// are merged across slots with TwoSum in FP32, plain ones with FP32 adds; the FP64 result
+// gets the prefactor and the diagonal term.
+__global__ void reduce_partials_f32_kernel(const TileInfo *__restrict__ ttiles, int TT,
+                                           const float2 *__restrict__ partial, long long nt,
+                                           double *out, double scale, double diag,
+                                           const double *__restrict__ diag_sigma, int comp)
+{
+    const TileInfo ti = ttiles[blockIdx.x];
+    for (int loc = threadIdx.x; loc < ti.count; loc += blockDim.x) {
+        const long long t = ti.begin + loc;
+        for (int c = 0; c < 3; ++c) {
+            float hi = 0.0f, lo = 0.0f;
+            for (int q = 0; q < ti.slot_count; ++q) {
+                const float2 v = partial[(static_cast<size_t>(ti.slot_begin + q) * 3 + c) * TT + loc];
+                if (comp) {
+                    const float s = hi + v.x;
+                    const float bb = s - hi;
+                    lo += ((hi - (s - bb)) + (v.x - bb)) + v.y;
+                    hi = s;
+                } else {
+                    hi += v.x;
+                }
+            }
+            double o = scale * (static_cast<double>(hi) + static_cast<double>(lo));
             if (diag_sigma)
                 o += diag * diag_sigma[c * nt + t];
             out[c * nt + t] = o;
@@ -278,6 +359,19 @@ cudaError_t launch_reduce_partials(const TileInfo *ttiles, int n_ttiles, int TT,
         return cudaSuccess;
     reduce_partials_kernel<<<n_ttiles, 256, 0, s>>>(ttiles, TT, partial, nt, out, scale, diag,
                                                      diag_sigma);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_partials_f32(const TileInfo *ttiles, int n_ttiles, int TT,
+                                       const void *partial, long long nt, double *out,
+                                       double scale, double diag, const double *diag_sigma,
+                                       int comp, cudaStream_t s)
+{
+    if (n_ttiles <= 0)
+        return cudaSuccess;
+    reduce_partials_f32_kernel<<<n_ttiles, 256, 0, s>>>(ttiles, TT,
+                                                         static_cast<const float2 *>(partial), nt,
+                                                         out, scale, diag, diag_sigma, comp);
     return cudaGetLastError();
 }
 

@@ -147,6 +147,49 @@ __device__ __forceinline__ float two_sum_add(float x, float d, float &lo)
     return s;
 }
 
+// Parameters of one (target tile, source tile) pair, computed once per pair by the
+// thread that issues the source tile's copy and read by all threads from shared memory.
+struct __align__(16) TilePairParams {
+    float sx, sy, sz;      // centre offset c_T - c_S rounded to FP32
+    float thr2;            // squared coincidence threshold
+    float lx, ly, lz;      // part of the offset lost to that rounding
+    int flags;             // TP_NEAR | TP_HILO
+};
+constexpr int TP_NEAR = 1;   // the tiles may hold coincident points: test r^2 > thr2
+constexpr int TP_HILO = 2;   // form r from high and low parts (compensated kernels)
+// Compensated kernels use high/low differences for tile pairs whose centres are closer
+// than HILO_REL x (sum of the tile radii): there the FP32 centring error is not small
+// next to the shortest pair distances.
+constexpr double HILO_REL = 1.0;
+
+template <bool COMP>
+__device__ __forceinline__ void tile_pair_setup(TilePairParams &tp, double tcx, double tcy,
+                                                double tcz, float trad, const TileInfo &si)
+{
+    const double ddx = tcx - si.cx, ddy = tcy - si.cy, ddz = tcz - si.cz;
+    const double dist = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
+    const double lim = static_cast<double>(trad) + static_cast<double>(si.rad);
+    int flags = 0;
+    if ((dist - lim) <= 1.0e-5 * (dist + lim) + 1.0e-30)
+        flags |= TP_NEAR;
+    if (COMP && dist <= HILO_REL * lim)
+        flags |= TP_HILO | TP_NEAR;
+    const float sx = static_cast<float>(ddx), sy = static_cast<float>(ddy),
+                sz = static_cast<float>(ddz);
+    tp.sx = sx;
+    tp.sy = sy;
+    tp.sz = sz;
+    tp.lx = static_cast<float>(ddx - static_cast<double>(sx));
+    tp.ly = static_cast<float>(ddy - static_cast<double>(sy));
+    tp.lz = static_cast<float>(ddz - static_cast<double>(sz));
+    const float thr = static_cast<float>(COINCIDENT_REL * lim);
+    tp.thr2 = thr * thr;
+    tp.flags = flags;
+}
+
+// FP32 kernels write every item's sums to its partial slot as (hi, lo) float pairs,
+// [slot][3][TT] float2; reduce_partials_f32 adds the slots of a target tile and applies
+// the prefactor and the diagonal term in FP64 (no FP64 work in this kernel's loop).
 template <int KIND, int R, int W, bool COMP>
 __global__ void __launch_bounds__(W * 32) pairsum_f32_kernel(const PairsumParams p)
 {
@@ -161,6 +204,7 @@ __global__ void __launch_bounds__(W * 32) pairsum_f32_kernel(const PairsumParams
     extern __shared__ __align__(128) float4 sbuf[];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int4 s_item;
+    __shared__ TilePairParams s_tp[2];
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -173,17 +217,31 @@ __global__ void __launch_bounds__(W * 32) pairsum_f32_kernel(const PairsumParams
     }
     __syncthreads();
 
-    uint32_t g = 0;   // source tiles consumed by this CTA (ring position)
+    uint32_t g = 0;                  // source tiles consumed by this CTA (ring position)
+    double tcx = 0.0, tcy = 0.0, tcz = 0.0;   // thread 0: centre and radius of the target tile
+    float trad = 0.0f;
     for (;;) {
         if (tid == 0) {
             const int i = atomicAdd(p.counter, 1);
-            s_item = (i < p.n_items) ? p.items[i] : make_int4(-1, 0, 0, 0);
+            const int4 nx = (i < p.n_items) ? p.items[i] : make_int4(-1, 0, 0, 0);
+            s_item = nx;
+            if (nx.x >= 0) {
+                const TileInfo tt = p.ttiles[nx.x];
+                tcx = tt.cx;
+                tcy = tt.cy;
+                tcz = tt.cz;
+                trad = tt.rad;
+                const int st = g & 1;
+                tile_pair_setup<COMP>(s_tp[st], tcx, tcy, tcz, trad, p.stiles[nx.y]);
+                mbar_arrive_expect_tx(&bar[st], TILE_BYTES);
+                bulk_copy_g2s(sbuf + st * STAGE, spack + static_cast<size_t>(nx.y) * GSTRIDE,
+                              TILE_BYTES, &bar[st]);
+            }
         }
         __syncthreads();
         const int4 it = s_item;
         if (it.x < 0)
             break;
-        const TileInfo tt = p.ttiles[it.x];
 
         float tx[R], ty[R], tz[R];
         const size_t toff = static_cast<size_t>(it.x) * TT + warp * 32 * R + lane;
@@ -203,17 +261,12 @@ __global__ void __launch_bounds__(W * 32) pairsum_f32_kernel(const PairsumParams
         }
 
         const int nk = it.z - it.y;
-        if (tid == 0) {
-            const int st = g & 1;
-            mbar_arrive_expect_tx(&bar[st], TILE_BYTES);
-            bulk_copy_g2s(sbuf + st * STAGE, spack + static_cast<size_t>(it.y) * GSTRIDE,
-                          TILE_BYTES, &bar[st]);
-        }
         for (int k = 0; k < nk; ++k) {
             const uint32_t gk = g + k;
             const int st = gk & 1;
             if (tid == 0 && k + 1 < nk) {
                 const int sn = (gk + 1) & 1;
+                tile_pair_setup<COMP>(s_tp[sn], tcx, tcy, tcz, trad, p.stiles[it.y + k + 1]);
                 mbar_arrive_expect_tx(&bar[sn], TILE_BYTES);
                 bulk_copy_g2s(sbuf + sn * STAGE,
                               spack + static_cast<size_t>(it.y + k + 1) * GSTRIDE, TILE_BYTES,
@@ -230,94 +283,58 @@ __global__ void __launch_bounds__(W * 32) pairsum_f32_kernel(const PairsumParams
                     mbar_wait_bounded(&bar[(gk + 1) & 1], ((gk + 1) >> 1) & 1, 100000000ull);
                 return;
             }
-            const TileInfo si = p.stiles[it.y + k];
-            const double ddx = tt.cx - si.cx, ddy = tt.cy - si.cy, ddz = tt.cz - si.cz;
-            const double dist = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
-            const double lim = static_cast<double>(tt.rad) + static_cast<double>(si.rad);
-            // near: the tiles may hold coincident points; hilo: within one tile extent.
-            // A coincident pair can come out of the FP32 centring as a difference of a few
-            // ulps of the tile extent rather than an exact zero, so pairs closer than
-            // COINCIDENT_REL x (sum of the two tile radii) count as coincident.
-            const bool near = (dist - lim) <= 1.0e-5 * (dist + lim) + 1.0e-30;
-            const float thr = static_cast<float>(COINCIDENT_REL * lim);
-            const float thr2 = thr * thr;
-            const bool hilo = COMP && (dist <= 2.0 * lim);
-            const float sx = static_cast<float>(ddx), sy = static_cast<float>(ddy),
-                        sz = static_cast<float>(ddz);
+            const TilePairParams tp = s_tp[st];
             float xh[R], yh[R], zh[R], xl[R], yl[R], zl[R];
             const float4 *sp = sbuf + st * STAGE;
-            if (hilo) {
-                const float slx = static_cast<float>(ddx - static_cast<double>(sx));
-                const float sly = static_cast<float>(ddy - static_cast<double>(sy));
-                const float slz = static_cast<float>(ddz - static_cast<double>(sz));
+            if (COMP && (tp.flags & TP_HILO)) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const float4 l = p.tpack_lo[toff + r * 32];   // only hilo tiles need it
-                    xl[r] = l.x + slx;
-                    yl[r] = l.y + sly;
-                    zl[r] = l.z + slz;
-                    xh[r] = two_sum_add(tx[r], sx, xl[r]);
-                    yh[r] = two_sum_add(ty[r], sy, yl[r]);
-                    zh[r] = two_sum_add(tz[r], sz, zl[r]);
+                    xl[r] = l.x + tp.lx;
+                    yl[r] = l.y + tp.ly;
+                    zl[r] = l.z + tp.lz;
+                    xh[r] = two_sum_add(tx[r], tp.sx, xl[r]);
+                    yh[r] = two_sum_add(ty[r], tp.sy, yl[r]);
+                    zh[r] = two_sum_add(tz[r], tp.sz, zl[r]);
                 }
-                tile_f32<KIND, R, true, COMP, COMP>(sp, thr2, xh, yh, zh, xl, yl, zl, ax, ay, az, hx,
-                                                     hy, hz, lx, ly, lz);
+                tile_f32<KIND, R, true, COMP, COMP>(sp, tp.thr2, xh, yh, zh, xl, yl, zl, ax, ay, az,
+                                                     hx, hy, hz, lx, ly, lz);
             } else {
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    xh[r] = tx[r] + sx;
-                    yh[r] = ty[r] + sy;
-                    zh[r] = tz[r] + sz;
+                    xh[r] = tx[r] + tp.sx;
+                    yh[r] = ty[r] + tp.sy;
+                    zh[r] = tz[r] + tp.sz;
                     xl[r] = yl[r] = zl[r] = 0.0f;
                 }
-                if (near)
-                    tile_f32<KIND, R, true, COMP, false>(sp, thr2, xh, yh, zh, xl, yl, zl, ax, ay, az,
-                                                         hx, hy, hz, lx, ly, lz);
+                if (tp.flags & TP_NEAR)
+                    tile_f32<KIND, R, true, COMP, false>(sp, tp.thr2, xh, yh, zh, xl, yl, zl, ax, ay,
+                                                         az, hx, hy, hz, lx, ly, lz);
                 else
-                    tile_f32<KIND, R, false, COMP, false>(sp, thr2, xh, yh, zh, xl, yl, zl, ax, ay,
-                                                          az, hx, hy, hz, lx, ly, lz);
+                    tile_f32<KIND, R, false, COMP, false>(sp, tp.thr2, xh, yh, zh, xl, yl, zl, ax,
+                                                          ay, az, hx, hy, hz, lx, ly, lz);
             }
-            __syncthreads();   // stage st may be refilled from here on
+            __syncthreads();   // stage st (and its parameters) may be refilled from here on
         }
         g += nk;
 
-        // Epilogue: FP64 totals, direct output or chunk partial.
+        // Epilogue: (hi, lo) pairs to the item's partial slot (padded targets included).
+        float2 *pp = reinterpret_cast<float2 *>(p.partial) + static_cast<size_t>(it.w) * 3 * TT +
+                     warp * 32 * R + lane;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int loc = warp * 32 * R + r * 32 + lane;
-            double sx_, sy_, sz_;
             if (COMP) {
-                sx_ = static_cast<double>(hx[r]) + static_cast<double>(lx[r]);
-                sy_ = static_cast<double>(hy[r]) + static_cast<double>(ly[r]);
-                sz_ = static_cast<double>(hz[r]) + static_cast<double>(lz[r]);
+                pp[r * 32] = make_float2(hx[r], lx[r]);
+                pp[TT + r * 32] = make_float2(hy[r], ly[r]);
+                pp[2 * TT + r * 32] = make_float2(hz[r], lz[r]);
             } else {
-                sx_ = ax[r];
-                sy_ = ay[r];
-                sz_ = az[r];
-            }
-            if (it.w < 0) {
-                if (loc < tt.count) {
-                    const long long t = tt.begin + loc;
-                    double ox = p.scale * sx_, oy = p.scale * sy_, oz = p.scale * sz_;
-                    if (p.diag_sigma) {
-                        ox += p.diag * p.diag_sigma[t];
-                        oy += p.diag * p.diag_sigma[p.nt + t];
-                        oz += p.diag * p.diag_sigma[2 * p.nt + t];
-                    }
-                    p.out[t] = ox;
-                    p.out[p.nt + t] = oy;
-                    p.out[2 * p.nt + t] = oz;
-                }
-            } else {
-                double *pp = p.partial + static_cast<size_t>(it.w) * 3 * TT + loc;
-                pp[0] = sx_;
-                pp[TT] = sy_;
-                pp[2 * TT] = sz_;
+                pp[r * 32] = make_float2(ax[r], 0.0f);
+                pp[TT + r * 32] = make_float2(ay[r], 0.0f);
+                pp[2 * TT + r * 32] = make_float2(az[r], 0.0f);
             }
         }
     }
 }
-
 
 // ---------------------------------------------------------------------------
 // FP64

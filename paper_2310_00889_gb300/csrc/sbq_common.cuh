@@ -67,7 +67,8 @@ struct PairsumParams {
     int *counter;               // work-claim counter, zeroed by the density pack kernel
     int *err;                   // device error word
     double *out;                // (3, nt) FP64 output
-    double *partial;            // [slot][3][TT] FP64 chunk partials
+    double *partial;            // chunk partials: FP64 [slot][3][TT] (FP64 kernel) or
+                                // float2 (hi, lo) [slot][3][TT] (FP32 kernels)
     const double *diag_sigma;   // nullable: out += diag * diag_sigma (same indexing as out)
     double diag;
     double scale;               // prefactor applied to the accumulated sum
@@ -198,6 +199,11 @@ cudaError_t launch_reduce_partials(const TileInfo *ttiles, int n_ttiles, int TT,
                                    const double *partial, long long nt, double *out,
                                    double scale, double diag, const double *diag_sigma,
                                    cudaStream_t s);
+// FP32 partial sums ((hi, lo) float pairs) of every slot of a target tile -> FP64 output.
+cudaError_t launch_reduce_partials_f32(const TileInfo *ttiles, int n_ttiles, int TT,
+                                       const void *partial, long long nt, double *out,
+                                       double scale, double diag, const double *diag_sigma,
+                                       int comp, cudaStream_t s);
 cudaError_t launch_csr_apply(long long nrows, const int64_t *rowptr, const int64_t *col,
                              const double *val, const double *x, double *y, cudaStream_t s);
 
