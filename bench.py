@@ -53,6 +53,9 @@ def parse():
                     help="CPU work bound of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-reps", type=int, default=20)
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch the Arnoldi steps from the host instead of the CUDA graph "
+                         "(profilers cannot resolve kernels inside graphs with while nodes)")
     ap.add_argument("--kernel-only", default=None, choices=["fp32c", "fp32", "fp64"],
                     help="only time operator applies of this precision on the workload "
                          "(inside an NVTX range 'kernel_only', for profilers)")
@@ -236,7 +239,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t_setup) * 1e3
     opts = dict(tol=1e-10, restart=100, inner_prec="fp32c", inner_tol=1e-5, max_outer=30,
-                use_graph=True)
+                use_graph=not args.no_graph)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     for _ in range(args.warmup):
@@ -370,7 +373,7 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "nodes": n, "unknowns": 3 * n, "eta": eta,
                        "tol": 1e-10, "inner": "fp32 compensated, FP64 refinement",
-                       "restart": 100, "graph": True,
+                       "restart": 100, "graph": not args.no_graph,
                        "l2": "flushed between steps (256 MiB write, outside the timed intervals)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "solve": {"mixed_ms": ms, "fp64_ms": fp64_ms, "speedup_vs_fp64": fp64_ms / ms,

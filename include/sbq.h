@@ -225,6 +225,13 @@ SBQ_API int sbq_op_stats(const void *op, int prec, int *kernels_per_matvec,
  * waits inside kernels: SBQ_ETIMEOUT if a wait expired since the last check. */
 SBQ_API int sbq_check_device(void *stream);
 
+/* Failure-path self-test (no counterpart in the paper): launches one kernel on `stream`
+ * that waits on an mbarrier phase no copy will complete, with the same bounded wait the
+ * pair-sum kernels use and a limit of limit_ns nanoseconds (0 < limit_ns <= 2e9).  When
+ * the wait expires the kernel sets the device error word and returns; a following
+ * sbq_check_device() then reports SBQ_ETIMEOUT and clears the word.  Faults nothing. */
+SBQ_API int sbq_selftest_bounded_wait(int64_t limit_ns, void *stream);
+
 /* Free a plan or operator handle (NULL is ignored). */
 SBQ_API void sbq_destroy(void *handle);
 

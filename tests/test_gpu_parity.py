@@ -370,3 +370,24 @@ def test_config2_full_size_mixed_solve_residual_rows(sbq, oracle_mod):
 
 def test_device_error_word_clear(sbq):
     sbq.check_device()
+
+
+def test_bounded_wait_expiry_is_reported(sbq):
+    """Failure detection without a fault: a kernel waits 50 ms on an mbarrier phase that
+    nothing completes; the bounded wait expires, the device error word is set, the host
+    reads SBQ_ETIMEOUT, the word is cleared, and the context keeps working."""
+    import ctypes
+    import torch
+    f = sbq.lib.sbq_selftest_bounded_wait
+    f.argtypes = [ctypes.c_int64, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert f(50_000_000, stream) == 0
+    with pytest.raises(sbq.SbqError) as ei:
+        sbq.check_device()
+    assert ei.value.status == sbq.ETIMEOUT
+    sbq.check_device()   # cleared
+    c = I.config1()
+    s = c["surf"]
+    u = _apply(sbq, "sl", s.x, s.n, s.w, c["sigma"], c["trg"], "fp64")
+    assert np.all(np.isfinite(u))
