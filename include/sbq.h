@@ -67,8 +67,9 @@ typedef enum {
 
 /* Tile shape of the pair-sum kernels.  targets per CTA = 32 * warps * r. */
 typedef struct {
-    int r;             /* targets per thread held in registers: FP32 {2,4,8}, FP64 {1,2} */
-    int warps;         /* warps per CTA: {2,4,8} (FP32), 4 (FP64) */
+    int r;             /* targets per thread held in registers */
+    int warps;         /* warps per CTA.  (r, warps): FP32 (2,4) (4,4) (8,4) (4,8) (4,2) (8,2);
+                          FP64 (1,4) (2,4) */
     int chunk_tiles;   /* source tiles per work item; 0 = chosen from the SM count */
 } sbq_tune;
 

@@ -194,7 +194,7 @@ int build_src_pack(SrcPack &sp, int layout, const std::vector<int64_t> &src_off,
     }
     SBQ_TRY(sp.stiles.alloc(h.size() * sizeof(TileInfo)));
     const size_t per_tile = (layout == SBQ_FP64) ? 9 * TS_F64 * sizeof(double)
-                                                 : F32_TILE_BLOCKS * TS_F32 * sizeof(float4);
+                                                 : F32_TILE_F4 * sizeof(float4);
     SBQ_TRY(sp.spack.alloc(h.size() * per_tile));
     if (!h.empty()) {
         SBQ_CUDA(cudaMemcpyAsync(sp.stiles.p, h.data(), h.size() * sizeof(TileInfo),
@@ -440,7 +440,7 @@ static int autotune_op(Op *op, int prec, cudaStream_t s)
     if (prec == SBQ_FP64) {
         shapes = {{2, 4, 0}, {1, 4, 0}};
     } else {
-        shapes = {{4, 4, 0}, {8, 4, 0}, {2, 4, 0}, {4, 8, 0}};
+        shapes = {{2, 4, 0}, {4, 2, 0}, {4, 4, 0}, {8, 2, 0}, {8, 4, 0}, {4, 8, 0}};
     }
     DevBuf zs, zo;
     SBQ_TRY(zs.alloc(3 * static_cast<size_t>(op->n) * sizeof(double)));

@@ -25,7 +25,6 @@ namespace sbq {
 
 constexpr int GB = 256;          // threads of the vector kernels
 constexpr int MAX_RESTART = 256;
-constexpr int NC = 8;            // Krylov vectors handled per sweep of a multi-dot
 constexpr int SOLVE_SMEM_MAX_M = 200;   // back-substitution keeps R in shared memory up to this m
 
 struct GState {
@@ -132,9 +131,17 @@ __device__ void block_multi_dot(const double *__restrict__ V, long long N, int j
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int k = warp; k <= j; k += nw) {
         const double *v = V + static_cast<size_t>(k) * N;
-        double acc = 0.0;
-        for (long long i = a + lane; i < b; i += 32)
-            acc = fma(v[i], w[i], acc);
+        double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+        long long i = a + lane;
+        for (; i + 96 < b; i += 128) {
+            acc0 = fma(v[i], w[i], acc0);
+            acc1 = fma(v[i + 32], w[i + 32], acc1);
+            acc2 = fma(v[i + 64], w[i + 64], acc2);
+            acc3 = fma(v[i + 96], w[i + 96], acc3);
+        }
+        for (; i < b; i += 32)
+            acc0 = fma(v[i], w[i], acc0);
+        double acc = (acc0 + acc1) + (acc2 + acc3);
         for (int o = 16; o > 0; o >>= 1)
             acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0)
@@ -190,6 +197,7 @@ __global__ void k_cgs_pass2(const double *__restrict__ V, long long N, GState *s
     block_rows(N, a, b);
     for (long long i = a + threadIdx.x; i < b; i += blockDim.x) {
         double acc = w[i];
+#pragma unroll 8
         for (int k = 0; k <= j; ++k)
             acc = fma(-V[static_cast<size_t>(k) * N + i], sh[k], acc);
         w[i] = acc;
@@ -218,6 +226,7 @@ __global__ void k_cgs_norm_givens(const double *__restrict__ V, long long N, GSt
     double nrm = 0.0;
     for (long long i = a + threadIdx.x; i < b; i += blockDim.x) {
         double acc = w[i];
+#pragma unroll 8
         for (int k = 0; k <= j; ++k)
             acc = fma(-V[static_cast<size_t>(k) * N + i], sh[k], acc);
         w[i] = acc;
@@ -472,7 +481,7 @@ static int ws_ensure(Op *op, int m)
     ws->N = 3 * op->n;
     const long long N = ws->N;
     ws->nblk = static_cast<int>(std::max<long long>(1, std::min<long long>(4LL * device_props().sms,
-                                                                        (N + 255) / 256)));
+                                                                        (N + 127) / 128)));
     ws->ldp = m + 1;
     ws->solve_smem = (m <= SOLVE_SMEM_MAX_M) ? static_cast<size_t>(m) * (m + 1) / 2 * sizeof(double) : 0;
     int s = SBQ_OK;

@@ -55,7 +55,7 @@ Layout make_layout(int prec, int n_st, int n_tt, int TT, int n_items, long long 
     o = align256(o + size_t(n_items) * sizeof(int4));
     L.spack = o;
     const size_t per_tile = (prec == SBQ_FP64) ? 9 * TS_F64 * sizeof(double)
-                                               : F32_TILE_BLOCKS * TS_F32 * sizeof(float4);
+                                               : F32_TILE_F4 * sizeof(float4);
     o = align256(o + size_t(n_st) * per_tile);
     L.tpack = o;
     if (prec != SBQ_FP64)

@@ -98,26 +98,27 @@ __global__ void pack_src_geom_f32(const double *__restrict__ src, const double *
     const int count = stiles[k].count;
     double cx, cy, cz;
     tile_centre(src, ns, begin, count, TS, bb, cx, cy, cz);
-    float4 *tile = spack + static_cast<size_t>(k) * F32_TILE_BLOCKS * TS;
+    float *tile = reinterpret_cast<float *>(spack + static_cast<size_t>(k) * F32_TILE_F4);
     double d2 = 0.0;
     if (j < count) {
         const long long s = begin + j;
         const double dx = src[s] - cx, dy = src[ns + s] - cy, dz = src[2 * ns + s] - cz;
         const float fx = static_cast<float>(dx), fy = static_cast<float>(dy),
                     fz = static_cast<float>(dz);
-        tile[j] = make_float4(fx, fy, fz, 0.0f);
-        tile[3 * TS + j] = make_float4(static_cast<float>(dx - fx), static_cast<float>(dy - fy),
-                                       static_cast<float>(dz - fz), 0.0f);
-        tile[2 * TS + j] = nrm ? make_float4(static_cast<float>(nscale * nrm[s]),
-                                             static_cast<float>(nscale * nrm[ns + s]),
-                                             static_cast<float>(nscale * nrm[2 * ns + s]), 0.0f)
-                               : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        tile[f32_slot(FX, j)] = fx;
+        tile[f32_slot(FY, j)] = fy;
+        tile[f32_slot(FZ, j)] = fz;
+        tile[f32_slot(FLX, j)] = static_cast<float>(dx - fx);
+        tile[f32_slot(FLY, j)] = static_cast<float>(dy - fy);
+        tile[f32_slot(FLZ, j)] = static_cast<float>(dz - fz);
+        tile[f32_slot(FNX, j)] = nrm ? static_cast<float>(nscale * nrm[s]) : 0.0f;
+        tile[f32_slot(FNY, j)] = nrm ? static_cast<float>(nscale * nrm[ns + s]) : 0.0f;
+        tile[f32_slot(FNZ, j)] = nrm ? static_cast<float>(nscale * nrm[2 * ns + s]) : 0.0f;
         d2 = dx * dx + dy * dy + dz * dz;
     } else {
-        tile[j] = make_float4(PAD_POS_F32, PAD_POS_F32, PAD_POS_F32, 0.0f);
-        tile[TS + j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        tile[2 * TS + j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        tile[3 * TS + j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        tile[f32_slot(FX, j)] = tile[f32_slot(FY, j)] = tile[f32_slot(FZ, j)] = PAD_POS_F32;
+        for (int f = FQX; f <= FLZ; ++f)
+            tile[f32_slot(f, j)] = 0.0f;
     }
     const double m = block_max(d2, red);
     if (j == 0) {
@@ -168,20 +169,23 @@ __global__ void pack_src_q_f32(const double *__restrict__ w, const double *__res
                                long long ns, const TileInfo *__restrict__ stiles, float4 *spack,
                                int *counter)
 {
-    constexpr int TS = TS_F32;
     if (blockIdx.x == 0 && threadIdx.x == 0 && counter)
         *counter = 0;
     const int k = blockIdx.x, j = threadIdx.x;
     const long long begin = stiles[k].begin;
     const int count = stiles[k].count;
-    float4 q = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float qx = 0.0f, qy = 0.0f, qz = 0.0f;
     if (j < count) {
         const long long s = begin + j;
         const double ww = w[s];
-        q = make_float4(static_cast<float>(ww * sigma[s]), static_cast<float>(ww * sigma[ns + s]),
-                        static_cast<float>(ww * sigma[2 * ns + s]), 0.0f);
+        qx = static_cast<float>(ww * sigma[s]);
+        qy = static_cast<float>(ww * sigma[ns + s]);
+        qz = static_cast<float>(ww * sigma[2 * ns + s]);
     }
-    spack[static_cast<size_t>(k) * F32_TILE_BLOCKS * TS + TS + j] = q;
+    float *tile = reinterpret_cast<float *>(spack + static_cast<size_t>(k) * F32_TILE_F4);
+    tile[f32_slot(FQX, j)] = qx;
+    tile[f32_slot(FQY, j)] = qy;
+    tile[f32_slot(FQZ, j)] = qz;
 }
 
 __global__ void pack_src_q_f64(const double *__restrict__ w, const double *__restrict__ sigma,
@@ -267,33 +271,48 @@ __global__ void reduce_partials_kernel(const TileInfo *__restrict__ ttiles, int 
 
 // FP32 partials: (hi, lo) float pairs per (slot, component, target).  Compensated sums
 // are merged across slots with TwoSum in FP32, plain ones with FP32 adds; the FP64 result
-// gets the prefactor and the diagonal term.
+// gets the prefactor and the diagonal term.  Block (tile, component); four slot loads in
+// flight per thread.
+__device__ __forceinline__ void merge_partial(float &hi, float &lo, float2 v, int comp)
+{
+    if (comp) {
+        const float s = hi + v.x;
+        const float bb = s - hi;
+        lo += ((hi - (s - bb)) + (v.x - bb)) + v.y;
+        hi = s;
+    } else {
+        hi += v.x;
+    }
+}
+
 __global__ void reduce_partials_f32_kernel(const TileInfo *__restrict__ ttiles, int TT,
                                            const float2 *__restrict__ partial, long long nt,
                                            double *out, double scale, double diag,
                                            const double *__restrict__ diag_sigma, int comp)
 {
     const TileInfo ti = ttiles[blockIdx.x];
+    const int c = blockIdx.y;
+    const int nq = ti.slot_count;
     for (int loc = threadIdx.x; loc < ti.count; loc += blockDim.x) {
         const long long t = ti.begin + loc;
-        for (int c = 0; c < 3; ++c) {
-            float hi = 0.0f, lo = 0.0f;
-            for (int q = 0; q < ti.slot_count; ++q) {
-                const float2 v = partial[(static_cast<size_t>(ti.slot_begin + q) * 3 + c) * TT + loc];
-                if (comp) {
-                    const float s = hi + v.x;
-                    const float bb = s - hi;
-                    lo += ((hi - (s - bb)) + (v.x - bb)) + v.y;
-                    hi = s;
-                } else {
-                    hi += v.x;
-                }
-            }
-            double o = scale * (static_cast<double>(hi) + static_cast<double>(lo));
-            if (diag_sigma)
-                o += diag * diag_sigma[c * nt + t];
-            out[c * nt + t] = o;
+        const float2 *pp = partial + (static_cast<size_t>(ti.slot_begin) * 3 + c) * TT + loc;
+        const size_t qs = static_cast<size_t>(3) * TT;   // stride between slots
+        float hi = 0.0f, lo = 0.0f;
+        int q = 0;
+        for (; q + 4 <= nq; q += 4) {
+            const float2 v0 = pp[q * qs], v1 = pp[(q + 1) * qs], v2 = pp[(q + 2) * qs],
+                         v3 = pp[(q + 3) * qs];
+            merge_partial(hi, lo, v0, comp);
+            merge_partial(hi, lo, v1, comp);
+            merge_partial(hi, lo, v2, comp);
+            merge_partial(hi, lo, v3, comp);
         }
+        for (; q < nq; ++q)
+            merge_partial(hi, lo, pp[q * qs], comp);
+        double o = scale * (static_cast<double>(hi) + static_cast<double>(lo));
+        if (diag_sigma)
+            o += diag * diag_sigma[c * nt + t];
+        out[c * nt + t] = o;
     }
 }
 
@@ -369,7 +388,7 @@ cudaError_t launch_reduce_partials_f32(const TileInfo *ttiles, int n_ttiles, int
 {
     if (n_ttiles <= 0)
         return cudaSuccess;
-    reduce_partials_f32_kernel<<<n_ttiles, 256, 0, s>>>(ttiles, TT,
+    reduce_partials_f32_kernel<<<dim3(n_ttiles, 3), 256, 0, s>>>(ttiles, TT,
                                                          static_cast<const float2 *>(partial), nt,
                                                          out, scale, diag, diag_sigma, comp);
     return cudaGetLastError();
@@ -419,14 +438,15 @@ bool pairsum_shape_supported(int prec, int R, int W)
 {
     if (prec == SBQ_FP64)
         return W == 4 && (R == 1 || R == 2);
-    return (W == 4 && (R == 2 || R == 4 || R == 8)) || (W == 8 && R == 4);
+    return (W == 4 && (R == 2 || R == 4 || R == 8)) || (W == 8 && R == 4) ||
+           (W == 2 && (R == 4 || R == 8));
 }
 
 size_t pairsum_smem_bytes(int prec)
 {
     if (prec == SBQ_FP64)
         return 2 * 9 * TS_F64 * sizeof(double);
-    return 2 * (prec == SBQ_FP32_COMP ? F32_TILE_BLOCKS : 3) * TS_F32 * sizeof(float4);
+    return 2 * F32_TILE_F4 * sizeof(float4);
 }
 
 }  // namespace sbq

@@ -12,7 +12,9 @@
 // covers the whole source range of its target tile, else to its partial slot, which a
 // fixed-order reduction adds up later (deterministic results).
 //
-// FP32 path: targets and sources are stored relative to their tile centre (FP64
+// FP32 path: the inner loop takes two sources per step with the packed FP32x2
+// instructions (one issue slot for two FP32 operations), each thread applying them to its
+// R targets.  Targets and sources are stored relative to their tile centre (FP64
 // subtraction, then rounding), and per (target tile, source tile) the FP64 offset of
 // the two centres is rounded once and added to the targets.  Pairs whose tiles cannot
 // contain coincident points skip the r^2 == 0 test.  The compensated variant
@@ -37,46 +39,90 @@ __device__ __forceinline__ float rsqrt_sfu(float x)
     return y;
 }
 
-// Per-pair arithmetic, FP32, given r = (dx, dy, dz).  Accumulates (folded prefactors,
-// see the launcher):
+// Packed FP32 pairs: one 64-bit register holds the values of two sources (2m, 2m + 1);
+// the f32x2 instructions process both in one issue slot.
+using f2 = unsigned long long;
+
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b)
+{
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b)
+{
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b)
+{
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_pack(float lo, float hi)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+// Per-pair arithmetic for one target against two sources at once, given r = (dx, dy, dz)
+// (packed).  Accumulates (folded prefactors, see the launcher):
 //   SL: ri q + (r.q) ri^3 r
 //   DL: (r.q)(r.n) ri^5 r
 //   CF: ri q + (r.q) ri^3 (1 + (r.n') ri^2) r,  n' = kappa n stored by the pack
 template <int KIND, bool CHECK>
-__device__ __forceinline__ void pair_f32_r(float dx, float dy, float dz, const float4 &Q,
-                                           const float4 &N, float thr2, float &ax, float &ay,
-                                           float &az)
+__device__ __forceinline__ void pair2(f2 dx, f2 dy, f2 dz, f2 QX, f2 QY, f2 QZ, f2 NX, f2 NY, f2 NZ,
+                                      float thr2, f2 &ax, f2 &ay, f2 &az)
 {
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    float ri = rsqrt_sfu(r2);
-    if (CHECK)
-        ri = (r2 > thr2) ? ri : 0.0f;
-    const float rq = fmaf(dx, Q.x, fmaf(dy, Q.y, dz * Q.z));
-    const float ri2 = ri * ri;
+    const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
+    float r2a, r2b;
+    f2_unpack(r2, r2a, r2b);
+    float ra = rsqrt_sfu(r2a), rb = rsqrt_sfu(r2b);
+    if (CHECK) {
+        ra = (r2a > thr2) ? ra : 0.0f;
+        rb = (r2b > thr2) ? rb : 0.0f;
+    }
+    const f2 ri = f2_pack(ra, rb);
+    const f2 rq = f2_fma(dx, QX, f2_fma(dy, QY, f2_mul(dz, QZ)));
+    const f2 ri2 = f2_mul(ri, ri);
     if (KIND == KIND_SL) {
-        const float b = (rq * ri2) * ri;
-        ax = fmaf(ri, Q.x, ax);
-        ay = fmaf(ri, Q.y, ay);
-        az = fmaf(ri, Q.z, az);
-        ax = fmaf(b, dx, ax);
-        ay = fmaf(b, dy, ay);
-        az = fmaf(b, dz, az);
+        const f2 b = f2_mul(f2_mul(rq, ri2), ri);
+        ax = f2_fma(ri, QX, ax);
+        ay = f2_fma(ri, QY, ay);
+        az = f2_fma(ri, QZ, az);
+        ax = f2_fma(b, dx, ax);
+        ay = f2_fma(b, dy, ay);
+        az = f2_fma(b, dz, az);
     } else if (KIND == KIND_DL) {
-        const float rn = fmaf(dx, N.x, fmaf(dy, N.y, dz * N.z));
-        const float b = ((rq * ri2) * (rn * ri2)) * ri;
-        ax = fmaf(b, dx, ax);
-        ay = fmaf(b, dy, ay);
-        az = fmaf(b, dz, az);
+        const f2 rn = f2_fma(dx, NX, f2_fma(dy, NY, f2_mul(dz, NZ)));
+        const f2 b = f2_mul(f2_mul(f2_mul(rq, ri2), f2_mul(rn, ri2)), ri);
+        ax = f2_fma(b, dx, ax);
+        ay = f2_fma(b, dy, ay);
+        az = f2_fma(b, dz, az);
     } else {
-        const float rn = fmaf(dx, N.x, fmaf(dy, N.y, dz * N.z));
-        const float g = fmaf(rn, ri2, 1.0f);
-        const float b = (rq * ri2) * (ri * g);
-        ax = fmaf(ri, Q.x, ax);
-        ay = fmaf(ri, Q.y, ay);
-        az = fmaf(ri, Q.z, az);
-        ax = fmaf(b, dx, ax);
-        ay = fmaf(b, dy, ay);
-        az = fmaf(b, dz, az);
+        const f2 one = f2_pack(1.0f, 1.0f);
+        const f2 rn = f2_fma(dx, NX, f2_fma(dy, NY, f2_mul(dz, NZ)));
+        const f2 g = f2_fma(rn, ri2, one);
+        const f2 b = f2_mul(f2_mul(rq, ri2), f2_mul(ri, g));
+        ax = f2_fma(ri, QX, ax);
+        ay = f2_fma(ri, QY, ay);
+        az = f2_fma(ri, QZ, az);
+        ax = f2_fma(b, dx, ax);
+        ay = f2_fma(b, dy, ay);
+        az = f2_fma(b, dz, az);
     }
 }
 
@@ -90,50 +136,90 @@ __device__ __forceinline__ void two_sum_merge(float &hi, float &lo, float b)
     lo += e;
 }
 
-// One staged source tile applied to the thread's R targets.  HILO: targets carry low
-// parts (xl, yl, zl) and the tile its low block at sp[3 * TS + j].  CHECK: pairs with
-// r^2 <= thr2 count as coincident and are skipped.
-template <int KIND, int R, bool CHECK, bool COMP, bool HILO>
-__device__ __forceinline__ void tile_f32(const float4 *__restrict__ sp, float thr2, const float (&xh)[R],
-                                         const float (&yh)[R], const float (&zh)[R],
-                                         const float (&xl)[R], const float (&yl)[R],
-                                         const float (&zl)[R], float (&ax)[R], float (&ay)[R],
-                                         float (&az)[R], float (&hx)[R], float (&hy)[R],
-                                         float (&hz)[R], float (&lx)[R], float (&ly)[R],
-                                         float (&lz)[R])
+// Fold a packed accumulator (even- and odd-indexed sources) into a scalar sum.
+__device__ __forceinline__ void fold_packed(f2 &acc, float &hi, float &lo, bool comp)
 {
-    constexpr int TS = TS_F32;
-    constexpr int RUN = COMP ? COMP_RUN : TS;
+    float a, b;
+    f2_unpack(acc, a, b);
+    if (comp) {
+        two_sum_merge(hi, lo, a);
+        two_sum_merge(hi, lo, b);
+    } else {
+        hi += a + b;
+    }
+    acc = 0ull;
+}
+
+// One staged source tile (pair layout, see sbq_common.cuh) applied to the thread's R
+// targets, two sources per step.  HILO: targets carry low parts (xl, yl, zl) and r is
+// formed from high and low parts.  CHECK: pairs with r^2 <= thr2 count as coincident.
+// COMP: packed partial sums are merged into (hi, lo) with TwoSum every COMP_RUN sources;
+// otherwise they are folded into hi once per tile.
+template <int KIND, int R, bool CHECK, bool COMP, bool HILO>
+__device__ __forceinline__ void tile_f32(const float4 *__restrict__ sp, float thr2,
+                                         const float (&xh)[R], const float (&yh)[R],
+                                         const float (&zh)[R], const float (&xl)[R],
+                                         const float (&yl)[R], const float (&zl)[R],
+                                         float (&hx)[R], float (&hy)[R], float (&hz)[R],
+                                         float (&lx)[R], float (&ly)[R], float (&lz)[R])
+{
+    constexpr int H = TS_F32 / 2;           // source pairs per tile
+    constexpr int RUN = COMP ? COMP_RUN / 2 : H;
+    const ulonglong2 *__restrict__ s2 = reinterpret_cast<const ulonglong2 *>(sp);
+    f2 XT[R], YT[R], ZT[R], XL[R], YL[R], ZL[R], ax[R], ay[R], az[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        XT[r] = f2_pack(xh[r], xh[r]);
+        YT[r] = f2_pack(yh[r], yh[r]);
+        ZT[r] = f2_pack(zh[r], zh[r]);
+        if (HILO) {
+            XL[r] = f2_pack(xl[r], xl[r]);
+            YL[r] = f2_pack(yl[r], yl[r]);
+            ZL[r] = f2_pack(zl[r], zl[r]);
+        }
+        ax[r] = ay[r] = az[r] = 0ull;
+    }
 #pragma unroll 1
-    for (int j0 = 0; j0 < TS; j0 += RUN) {
-#pragma unroll 4
-        for (int j = j0; j < j0 + RUN; ++j) {
-            const float4 P = sp[j];
-            const float4 Q = sp[TS + j];
-            float4 N, L;
+    for (int m0 = 0; m0 < H; m0 += RUN) {
+#pragma unroll 2
+        for (int m = m0; m < m0 + RUN; ++m) {
+            const ulonglong2 a0 = s2[m];           // X, Y
+            const ulonglong2 a1 = s2[H + m];       // Z, QX
+            const ulonglong2 a2 = s2[2 * H + m];   // QY, QZ
+            ulonglong2 b0, b1, b2;
+            if (KIND != KIND_SL || HILO)
+                b1 = s2[4 * H + m];                // NZ, LX
             if (KIND != KIND_SL)
-                N = sp[2 * TS + j];
+                b0 = s2[3 * H + m];                // NX, NY
             if (HILO)
-                L = sp[3 * TS + j];
+                b2 = s2[5 * H + m];                // LY, LZ
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                float dx = xh[r] - P.x, dy = yh[r] - P.y, dz = zh[r] - P.z;
+                f2 dx = f2_sub(XT[r], a0.x), dy = f2_sub(YT[r], a0.y), dz = f2_sub(ZT[r], a1.x);
                 if (HILO) {
-                    dx += xl[r] - L.x;
-                    dy += yl[r] - L.y;
-                    dz += zl[r] - L.z;
+                    dx = f2_add(dx, f2_sub(XL[r], b1.y));
+                    dy = f2_add(dy, f2_sub(YL[r], b2.x));
+                    dz = f2_add(dz, f2_sub(ZL[r], b2.y));
                 }
-                pair_f32_r<KIND, CHECK>(dx, dy, dz, Q, N, thr2, ax[r], ay[r], az[r]);
+                pair2<KIND, CHECK>(dx, dy, dz, a1.y, a2.x, a2.y, b0.x, b0.y, b1.x, thr2, ax[r],
+                                   ay[r], az[r]);
             }
         }
         if (COMP) {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                two_sum_merge(hx[r], lx[r], ax[r]);
-                two_sum_merge(hy[r], ly[r], ay[r]);
-                two_sum_merge(hz[r], lz[r], az[r]);
-                ax[r] = ay[r] = az[r] = 0.0f;
+                fold_packed(ax[r], hx[r], lx[r], true);
+                fold_packed(ay[r], hy[r], ly[r], true);
+                fold_packed(az[r], hz[r], lz[r], true);
             }
+        }
+    }
+    if (!COMP) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            fold_packed(ax[r], hx[r], lx[r], false);
+            fold_packed(ay[r], hy[r], ly[r], false);
+            fold_packed(az[r], hz[r], lz[r], false);
         }
     }
 }
@@ -196,10 +282,12 @@ __global__ void __launch_bounds__(W * 32) pairsum_f32_kernel(const PairsumParams
     constexpr int NT = W * 32;
     constexpr int TT = NT * R;
     constexpr int TS = TS_F32;
-    constexpr int NF = COMP ? F32_TILE_BLOCKS : ((KIND == KIND_SL) ? 2 : 3);
-    constexpr uint32_t TILE_BYTES = NF * TS * sizeof(float4);
-    constexpr int STAGE = (COMP ? F32_TILE_BLOCKS : 3) * TS;   // float4 per smem stage
-    constexpr int GSTRIDE = F32_TILE_BLOCKS * TS;               // float4 per packed tile
+    // blocks of TS/2 float4 to copy: SL {X,Y} {Z,QX} {QY,QZ}; DL/CF add {NX,NY} {NZ,LX};
+    // compensated kernels also need {LY,LZ} (and LX)
+    constexpr int NB = COMP ? F32_TILE_BLOCKS : ((KIND == KIND_SL) ? 3 : 5);
+    constexpr uint32_t TILE_BYTES = NB * (TS / 2) * sizeof(float4);
+    constexpr int STAGE = F32_TILE_BLOCKS * (TS / 2);   // float4 per smem stage
+    constexpr int GSTRIDE = F32_TILE_BLOCKS * (TS / 2); // float4 per packed tile
 
     extern __shared__ __align__(128) float4 sbuf[];
     __shared__ __align__(8) uint64_t bar[2];
@@ -217,25 +305,41 @@ __global__ void __launch_bounds__(W * 32) pairsum_f32_kernel(const PairsumParams
     }
     __syncthreads();
 
+    // Ring protocol (two stages, one barrier per tile): the copy of the next tile is
+    // issued right after the barrier that follows the wait for the current tile, when
+    // every thread has finished the tile that last used the other stage.  During an item's
+    // last tile, thread 0 already claims the next item and issues its first tile.
     uint32_t g = 0;                  // source tiles consumed by this CTA (ring position)
     double tcx = 0.0, tcy = 0.0, tcz = 0.0;   // thread 0: centre and radius of the target tile
     float trad = 0.0f;
+    int4 pending = make_int4(-1, 0, 0, 0);   // thread 0: next item, first tile already issued
+    bool have_pending = false;
+
+    // thread 0: claim an item and issue its first source tile into stage `st`
+    auto claim_and_issue = [&](int st) -> int4 {
+        const int i = atomicAdd(p.counter, 1);
+        const int4 nx = (i < p.n_items) ? p.items[i] : make_int4(-1, 0, 0, 0);
+        if (nx.x >= 0) {
+            const TileInfo tt = p.ttiles[nx.x];
+            tcx = tt.cx;
+            tcy = tt.cy;
+            tcz = tt.cz;
+            trad = tt.rad;
+            tile_pair_setup<COMP>(s_tp[st], tcx, tcy, tcz, trad, p.stiles[nx.y]);
+            mbar_arrive_expect_tx(&bar[st], TILE_BYTES);
+            bulk_copy_g2s(sbuf + st * STAGE, spack + static_cast<size_t>(nx.y) * GSTRIDE,
+                          TILE_BYTES, &bar[st]);
+        }
+        return nx;
+    };
+
     for (;;) {
         if (tid == 0) {
-            const int i = atomicAdd(p.counter, 1);
-            const int4 nx = (i < p.n_items) ? p.items[i] : make_int4(-1, 0, 0, 0);
-            s_item = nx;
-            if (nx.x >= 0) {
-                const TileInfo tt = p.ttiles[nx.x];
-                tcx = tt.cx;
-                tcy = tt.cy;
-                tcz = tt.cz;
-                trad = tt.rad;
-                const int st = g & 1;
-                tile_pair_setup<COMP>(s_tp[st], tcx, tcy, tcz, trad, p.stiles[nx.y]);
-                mbar_arrive_expect_tx(&bar[st], TILE_BYTES);
-                bulk_copy_g2s(sbuf + st * STAGE, spack + static_cast<size_t>(nx.y) * GSTRIDE,
-                              TILE_BYTES, &bar[st]);
+            if (have_pending) {
+                s_item = pending;
+                have_pending = false;
+            } else {
+                s_item = claim_and_issue(g & 1);
             }
         }
         __syncthreads();
@@ -252,10 +356,9 @@ __global__ void __launch_bounds__(W * 32) pairsum_f32_kernel(const PairsumParams
             ty[r] = v.y;
             tz[r] = v.z;
         }
-        float ax[R], ay[R], az[R], hx[R], hy[R], hz[R], lx[R], ly[R], lz[R];
+        float hx[R], hy[R], hz[R], lx[R], ly[R], lz[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            ax[r] = ay[r] = az[r] = 0.0f;
             hx[r] = hy[r] = hz[r] = 0.0f;
             lx[r] = ly[r] = lz[r] = 0.0f;
         }
@@ -264,24 +367,28 @@ __global__ void __launch_bounds__(W * 32) pairsum_f32_kernel(const PairsumParams
         for (int k = 0; k < nk; ++k) {
             const uint32_t gk = g + k;
             const int st = gk & 1;
-            if (tid == 0 && k + 1 < nk) {
-                const int sn = (gk + 1) & 1;
-                tile_pair_setup<COMP>(s_tp[sn], tcx, tcy, tcz, trad, p.stiles[it.y + k + 1]);
-                mbar_arrive_expect_tx(&bar[sn], TILE_BYTES);
-                bulk_copy_g2s(sbuf + sn * STAGE,
-                              spack + static_cast<size_t>(it.y + k + 1) * GSTRIDE, TILE_BYTES,
-                              &bar[sn]);
-            }
             const bool timed_out = !mbar_wait_bounded(&bar[st], (gk >> 1) & 1);
             if (__syncthreads_or(timed_out)) {
-                // The copy never landed: flag it, give the copies in flight a bounded
-                // chance to land, and leave without touching the output.
+                // The copy never landed: flag it, give it a bounded chance to land, and
+                // leave without touching the output (no other copy is in flight here).
                 if (tid == 0)
                     atomicOr(p.err, DEV_ERR_TIMEOUT);
                 mbar_wait_bounded(&bar[st], (gk >> 1) & 1, 100000000ull);
-                if (k + 1 < nk)
-                    mbar_wait_bounded(&bar[(gk + 1) & 1], ((gk + 1) >> 1) & 1, 100000000ull);
                 return;
+            }
+            // every thread is past tile gk - 1: the other stage can be refilled
+            if (tid == 0) {
+                const int sn = (gk + 1) & 1;
+                if (k + 1 < nk) {
+                    tile_pair_setup<COMP>(s_tp[sn], tcx, tcy, tcz, trad, p.stiles[it.y + k + 1]);
+                    mbar_arrive_expect_tx(&bar[sn], TILE_BYTES);
+                    bulk_copy_g2s(sbuf + sn * STAGE,
+                                  spack + static_cast<size_t>(it.y + k + 1) * GSTRIDE, TILE_BYTES,
+                                  &bar[sn]);
+                } else {
+                    pending = claim_and_issue(sn);
+                    have_pending = true;
+                }
             }
             const TilePairParams tp = s_tp[st];
             float xh[R], yh[R], zh[R], xl[R], yl[R], zl[R];
@@ -297,8 +404,8 @@ __global__ void __launch_bounds__(W * 32) pairsum_f32_kernel(const PairsumParams
                     yh[r] = two_sum_add(ty[r], tp.sy, yl[r]);
                     zh[r] = two_sum_add(tz[r], tp.sz, zl[r]);
                 }
-                tile_f32<KIND, R, true, COMP, COMP>(sp, tp.thr2, xh, yh, zh, xl, yl, zl, ax, ay, az,
-                                                     hx, hy, hz, lx, ly, lz);
+                tile_f32<KIND, R, true, COMP, COMP>(sp, tp.thr2, xh, yh, zh, xl, yl, zl, hx, hy, hz,
+                                                     lx, ly, lz);
             } else {
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
@@ -308,13 +415,12 @@ __global__ void __launch_bounds__(W * 32) pairsum_f32_kernel(const PairsumParams
                     xl[r] = yl[r] = zl[r] = 0.0f;
                 }
                 if (tp.flags & TP_NEAR)
-                    tile_f32<KIND, R, true, COMP, false>(sp, tp.thr2, xh, yh, zh, xl, yl, zl, ax, ay,
-                                                         az, hx, hy, hz, lx, ly, lz);
+                    tile_f32<KIND, R, true, COMP, false>(sp, tp.thr2, xh, yh, zh, xl, yl, zl, hx, hy,
+                                                         hz, lx, ly, lz);
                 else
-                    tile_f32<KIND, R, false, COMP, false>(sp, tp.thr2, xh, yh, zh, xl, yl, zl, ax,
-                                                          ay, az, hx, hy, hz, lx, ly, lz);
+                    tile_f32<KIND, R, false, COMP, false>(sp, tp.thr2, xh, yh, zh, xl, yl, zl, hx,
+                                                          hy, hz, lx, ly, lz);
             }
-            __syncthreads();   // stage st (and its parameters) may be refilled from here on
         }
         g += nk;
 
@@ -323,15 +429,9 @@ __global__ void __launch_bounds__(W * 32) pairsum_f32_kernel(const PairsumParams
                      warp * 32 * R + lane;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            if (COMP) {
-                pp[r * 32] = make_float2(hx[r], lx[r]);
-                pp[TT + r * 32] = make_float2(hy[r], ly[r]);
-                pp[2 * TT + r * 32] = make_float2(hz[r], lz[r]);
-            } else {
-                pp[r * 32] = make_float2(ax[r], 0.0f);
-                pp[TT + r * 32] = make_float2(ay[r], 0.0f);
-                pp[2 * TT + r * 32] = make_float2(az[r], 0.0f);
-            }
+            pp[r * 32] = make_float2(hx[r], lx[r]);
+            pp[TT + r * 32] = make_float2(hy[r], ly[r]);
+            pp[2 * TT + r * 32] = make_float2(hz[r], lz[r]);
         }
     }
 }
@@ -525,8 +625,9 @@ struct KindLauncher {
         return b;
     }
 
-// Supported tile shapes.  FP32: (R, W) in {(2,4), (4,4), (8,4), (4,8)}; FP64: (1,4), (2,4).
-#define SBQ_F32_SHAPES(X) X(2, 4) X(4, 4) X(8, 4) X(4, 8)
+// Supported tile shapes.  FP32: (R, W) in {(2,4), (4,4), (8,4), (4,8), (4,2), (8,2)};
+// FP64: (1,4), (2,4).
+#define SBQ_F32_SHAPES(X) X(2, 4) X(4, 4) X(8, 4) X(4, 8) X(4, 2) X(8, 2)
 #define SBQ_F64_SHAPES(X) X(1, 4) X(2, 4)
 
     static cudaError_t launch(int prec, int R, int W, int grid, const PairsumParams &p, cudaStream_t s)

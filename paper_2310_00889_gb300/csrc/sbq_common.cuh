@@ -17,12 +17,23 @@ namespace sbq {
 // (paper Eqs. stokes-sl, stokes-dl, stokes-bie-new).
 enum Kind { KIND_SL = 0, KIND_DL = 1, KIND_CF = 2 };
 
-// Sources per shared-memory tile.  FP32 tiles hold float4 blocks {pos, q, n, pos_lo}
-// (pos_lo: the part of the centred FP64 position lost when rounding it to FP32); FP64
-// tiles hold 9 doubles per source {x, y, z, qx, qy, qz, nx, ny, nz}, each field a run
-// of TS.
+// Sources per shared-memory tile.
+// FP32 tiles store every field as packed pairs (value of source 2m, value of source 2m+1)
+// so that one 64-bit operand feeds the f32x2 instructions.  Fields, in order:
+// x, y, z, qx, qy, qz, nx, ny, nz, lx, ly, lz (l: the part of the centred FP64 position
+// lost when rounding it to FP32).  Two fields share a float4; six blocks of TS/2 float4
+// make a tile: {x,y} {z,qx} {qy,qz} {nx,ny} {nz,lx} {ly,lz}.
+// FP64 tiles hold 9 doubles per source {x, y, z, qx, qy, qz, nx, ny, nz}, each field a
+// run of TS.
 constexpr int TS_F32 = 256;
-constexpr int F32_TILE_BLOCKS = 4;
+constexpr int F32_TILE_BLOCKS = 6;            // blocks of TS_F32 / 2 float4 per tile
+constexpr int F32_TILE_F4 = F32_TILE_BLOCKS * (TS_F32 / 2);
+enum F32Field { FX = 0, FY, FZ, FQX, FQY, FQZ, FNX, FNY, FNZ, FLX, FLY, FLZ };
+// float index of field f of source j within a packed FP32 tile
+__host__ __device__ constexpr int f32_slot(int f, int j)
+{
+    return ((f >> 1) * (TS_F32 / 2) + (j >> 1)) * 4 + (f & 1) * 2 + (j & 1);
+}
 constexpr int TS_F64 = 128;
 // Compensated FP32: plain FP32 sums over runs of this many sources are merged into
 // the (hi, lo) pair with TwoSum.

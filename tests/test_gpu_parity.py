@@ -129,7 +129,7 @@ def test_coincident_targets_in_misaligned_tiles(sbq, oracle_mod, kind, prec):
         assert err <= (TOL_F64 if prec == "fp64" else TOL_F32[prec])
 
 
-@pytest.mark.parametrize("shape", [(2, 4), (4, 4), (8, 4), (4, 8), (1, 4)])
+@pytest.mark.parametrize("shape", [(2, 4), (4, 4), (8, 4), (4, 8), (4, 2), (8, 2), (1, 4)])
 @pytest.mark.parametrize("chunk", [0, 3])
 def test_operator_matvec_every_tile_shape(sbq, oracle_mod, shape, chunk):
     """Each supported tile shape (targets per CTA 256..1024, tiles not aligned with the
