@@ -53,6 +53,17 @@ def parse():
                     help="CPU work bound of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-reps", type=int, default=20)
+    ap.add_argument("--workload", default="curved_pipe",
+                    choices=["curved_pipe", "precision_sweep", "batch", "helix"],
+                    help="curved_pipe: the benchmark line (default); precision_sweep: FP32 vs "
+                         "compensated FP32 vs FP64 pair sums on random loops of 64K/256K/1M "
+                         "nodes; batch: 64 independent capped arcs in one persistent launch")
+    ap.add_argument("--sizes", default="512,2048,8192",
+                    help="precision_sweep: panel counts of the random loops (x 128 nodes)")
+    ap.add_argument("--helix-panels", type=int, default=2048,
+                    help="helix: axial panels of the helical wall (2048 -> 1,048,576 wall nodes)")
+    ap.add_argument("--fp64-solve", action="store_true",
+                    help="batch: also time the plain FP64 GMRES solve (minutes)")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the Arnoldi steps from the host instead of the CUDA graph "
                          "(profilers cannot resolve kernels inside graphs with while nodes)")
@@ -435,10 +446,240 @@ def kernel_only(args, sbq, I, src, nrm, w, eta, n, t, dev):
     return 0
 
 
+def _cuda_timer(fn, reps, stream):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_precision_sweep(args):
+    """Random closed slender loops (paper Sec. 5.2 recipe) of 64K/256K/1M nodes: the
+    combined-field operator in FP64, FP32 and compensated FP32; error of each against the
+    FP64 GPU result over all rows and against the FP64 CPU oracle on 4096 sampled rows."""
+    import torch
+    import oracle
+    from paper_2310_00889_gb300 import build as b
+    b.build()
+    oracle.build()
+    from paper_2310_00889_gb300 import inputs as I
+    from paper_2310_00889_gb300 import sbq
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+    eta = sbq.slender_eta(0.01)
+    for panels in [int(x) for x in args.sizes.split(",")]:
+        c = I.config3(panels=panels)
+        s = c["surf"]
+        n = s.size
+        op = sbq.StokesOp(t(s.x), t(s.n), t(s.w), eta)
+        sig = t(c["sigma"])
+        out = {}
+        times = {}
+        for prec in ("fp32c", "fp32", "fp64"):
+            op.autotune(prec) if prec != "fp64" or n <= 300000 else None
+            o = torch.empty_like(sig)
+            times[prec] = _cuda_timer(lambda: op.matvec(sig, prec=prec, out=o),
+                                      1 if prec == "fp64" else 5, stream)
+            out[prec] = o
+        u64 = out["fp64"]
+        rows = c["sub"]
+        t0 = time.perf_counter()
+        ref = oracle.combined(s.x, s.n, s.w, c["sigma"], s.x[:, rows], eta, 1.0) + 0.5 * c["sigma"][:, rows]
+        t_or = time.perf_counter() - t0
+        line = {"workload": "precision_sweep_random_loop", "nodes": n, "panels": panels,
+                "eta": eta, "pairs": float(n) * n, "oracle_rows": int(len(rows)),
+                "oracle_seconds": t_or, "oracle_cores": oracle.num_threads()}
+        for prec in ("fp64", "fp32", "fp32c"):
+            u = out[prec]
+            e_full = float(((u - u64).abs().max() / u64.abs().max()).item())
+            un = u[:, torch.as_tensor(rows, device="cuda")].cpu().numpy()
+            e_or = float(np.abs(un - ref).max() / np.abs(ref).max())
+            line[prec] = {"ms": times[prec], "pairs_per_s": n * n / (times[prec] * 1e-3),
+                          "relerr_vs_fp64_gpu_all_rows": e_full,
+                          "relerr_vs_oracle_sampled_rows": e_or,
+                          "tune": op.tune(prec) if prec != "fp64" or n <= 300000 else None}
+        print(json.dumps(line), flush=True)
+        op.close()
+        del out, u64, sig
+        torch.cuda.empty_cache()
+    return 0
+
+
+def run_batch(args):
+    """64 independent capped arcs (angles U[30, 180] degrees, wall node counts log-uniform
+    in [2K, 64K], seed 3) as one block-diagonal operator: every apply is one persistent
+    launch over the work list of all segments; GMRES-IR over the whole batch."""
+    import torch
+    from paper_2310_00889_gb300 import build as b
+    b.build()
+    from paper_2310_00889_gb300 import inputs as I
+    from paper_2310_00889_gb300 import sbq
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+    c = I.config4()
+    segs = c["segments"]
+    off = np.cumsum([0] + [g["surf"].size for g in segs])
+    n = int(off[-1])
+    X = np.concatenate([g["surf"].x for g in segs], axis=1)
+    Nn = np.concatenate([g["surf"].n for g in segs], axis=1)
+    W = np.concatenate([g["surf"].w for g in segs])
+    B = np.concatenate([g["rhs"] for g in segs], axis=1)
+    eta = sbq.slender_eta(c["slenderness"])
+    plan = sbq.BatchPlan(off)
+    t0 = time.perf_counter()
+    op = sbq.StokesOp(t(X), t(Nn), t(W), eta, plan=plan)
+    tune = {p: op.autotune(p) for p in ("fp32c", "fp64")}
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    pairs = float(np.sum(np.diff(off).astype(np.float64) ** 2))
+    sig = t(I.density(n, seed=7))
+    o = torch.empty_like(sig)
+    mv = {p: _cuda_timer(lambda: op.matvec(sig, prec=p, out=o), 5 if p != "fp64" else 1, stream)
+          for p in ("fp32c", "fp32", "fp64")}
+    # batched apply == the same segments applied one by one (same tile shape)
+    u = op.matvec(sig, prec="fp32c").clone()
+    u64 = op.matvec(sig, prec="fp64").clone()
+    worst = 0.0
+    for i in (0, 17, 63):
+        a, b_ = int(off[i]), int(off[i + 1])
+        p1 = sbq.BatchPlan([0, b_ - a], tune=op.tune("fp64"))
+        o1 = sbq.StokesOp(t(X[:, a:b_]), t(Nn[:, a:b_]), t(W[a:b_]), eta, plan=p1)
+        r1 = o1.matvec(sig[:, a:b_].contiguous(), prec="fp64")
+        worst = max(worst, float(((r1 - u64[:, a:b_]).abs().max() / r1.abs().max()).item()))
+        o1.close()
+    rhs = t(B)
+    # restart 200: some coarse segments have indefinite discrete operators on which
+    # GMRES(100) stagnates (their own Krylov space per segment, see gmres.cu)
+    x, rep = op.solve(rhs, tol=1e-10, restart=200, inner_prec="fp32c", inner_tol=1e-5)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x, rep = op.solve(rhs, tol=1e-10, restart=200, inner_prec="fp32c", inner_tol=1e-5)
+    torch.cuda.synchronize()
+    mixed_ms = (time.perf_counter() - t0) * 1e3
+    # residual of every segment (FP64 operator)
+    kx = op.matvec(x, prec="fp64")
+    seg_res = []
+    for i in range(len(segs)):
+        a, b_ = int(off[i]), int(off[i + 1])
+        seg_res.append(float(((rhs[:, a:b_] - kx[:, a:b_]).norm() / rhs[:, a:b_].norm()).item()))
+    line = {"workload": "batch_64_capped_arcs", "segments": len(segs), "nodes": n,
+            "pairs_per_matvec": pairs, "setup_ms": setup_ms, "tune": tune,
+            "matvec_ms": mv, "pairs_per_s": {p: pairs / (v * 1e-3) for p, v in mv.items()},
+            "fp32c_relerr_vs_fp64": float(((u - u64).abs().max() / u64.abs().max()).item()),
+            "batched_vs_single_segment_fp64_relerr": worst,
+            "mixed_solve": {"ms": mixed_ms, "iters": rep["iters"], "refinements": rep["outer_iters"],
+                            "matvecs_fp32c": rep["matvecs_low"], "matvecs_fp64": rep["matvecs_fp64"],
+                            "rel_res": rep["rel_res"], "graph": rep["graph_used"],
+                            "max_segment_rel_res": max(seg_res)}}
+    if args.fp64_solve:
+        t0 = time.perf_counter()
+        x64, rep64 = op.solve(rhs, tol=1e-10, restart=200, inner_prec="fp64")
+        torch.cuda.synchronize()
+        line["fp64_solve"] = {"ms": (time.perf_counter() - t0) * 1e3, "iters": rep64["iters"],
+                              "rel_res": rep64["rel_res"]}
+    else:
+        line["fp64_solve_estimate_ms"] = mv["fp64"] * (rep["iters"] + 2)
+    print(json.dumps(line), flush=True)
+    op.close()
+    return 0
+
+
+def run_helix(args):
+    """Helical pipe (helix radius 3, pitch 2, 4 turns, tube radius 1, 2048 panels x 8 x 64
+    = 1,048,576 wall nodes, two 16 x 64 caps) with 100 spheres of radius 0.2 (600 nodes
+    each) inside: one mixed-precision GMRES-IR solve to 1e-10 (zero wall and sphere data,
+    parabolic cap profiles); the plain FP64 solve is estimated from its iteration count and
+    the measured FP64 apply time unless --fp64-solve is given."""
+    import torch
+    import oracle
+    from paper_2310_00889_gb300 import build as b
+    b.build()
+    oracle.build()
+    from paper_2310_00889_gb300 import inputs as I
+    from paper_2310_00889_gb300 import sbq
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+    t0 = time.perf_counter()
+    c = I.config5(panels=args.helix_panels)
+    s = c["surf"]
+    n = s.size
+    rhs = np.zeros((3, n))
+    a_, b_ = 3.0, 2.0 / (2.0 * np.pi)
+    pe = np.array([0.0, 2.0 * np.pi * 4.0])
+    cend = np.stack([a_ * np.cos(pe), a_ * np.sin(pe), b_ * pe])
+    tend = np.stack([-a_ * np.sin(pe), a_ * np.cos(pe), np.full(2, b_)])
+    tend /= np.linalg.norm(tend, axis=0)
+    for nm, lo, hi in s.parts:
+        if nm in ("cap0", "cap1"):
+            k = 0 if nm == "cap0" else 1
+            rho2 = np.sum((s.x[:, lo:hi] - cend[:, k:k + 1]) ** 2, axis=0)
+            rhs[:, lo:hi] = (1.0 - rho2)[None, :] * tend[:, k:k + 1]
+    gen_s = time.perf_counter() - t0
+    eta = sbq.slender_eta(c["slenderness"])
+    t0 = time.perf_counter()
+    op = sbq.StokesOp(t(s.x), t(s.n), t(s.w), eta)
+    tune32 = op.autotune("fp32c")
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    sig = t(I.density(n, seed=5))
+    o = torch.empty_like(sig)
+    ms32 = _cuda_timer(lambda: op.matvec(sig, prec="fp32c", out=o), 2, stream)
+    u32 = o.clone()
+    ms64 = _cuda_timer(lambda: op.matvec(sig, prec="fp64", out=o), 1, stream)
+    u64 = o.clone()
+    rows = np.sort(np.random.default_rng(4).choice(n, 4096, replace=False))
+    sg = sig.cpu().numpy()
+    ref = oracle.combined(s.x, s.n, s.w, sg, s.x[:, rows], eta, 1.0) + 0.5 * sg[:, rows]
+    ri = torch.as_tensor(rows, device="cuda")
+    e64 = float(np.abs(u64[:, ri].cpu().numpy() - ref).max() / np.abs(ref).max())
+    e32 = float(np.abs(u32[:, ri].cpu().numpy() - ref).max() / np.abs(ref).max())
+    t0 = time.perf_counter()
+    x, rep = op.solve(t(rhs), tol=1e-10, restart=200, inner_prec="fp32c", inner_tol=1e-5)
+    torch.cuda.synchronize()
+    mixed_ms = (time.perf_counter() - t0) * 1e3
+    line = {"workload": "helix_pipe_with_spheres", "nodes": n, "spheres": len(c["centres"]),
+            "eta": eta, "pairs_per_matvec": float(n) * n, "generation_s": gen_s,
+            "setup_ms": setup_ms, "tune_fp32c": tune32,
+            "matvec_ms": {"fp32c": ms32, "fp64": ms64},
+            "pairs_per_s": {"fp32c": n * n / (ms32 * 1e-3), "fp64": n * n / (ms64 * 1e-3)},
+            "relerr_vs_oracle_4096_rows": {"fp64": e64, "fp32c": e32},
+            "mixed_solve": {"ms": mixed_ms, "iters": rep["iters"], "refinements": rep["outer_iters"],
+                            "matvecs_fp32c": rep["matvecs_low"], "matvecs_fp64": rep["matvecs_fp64"],
+                            "rel_res": rep["rel_res"], "hist": rep["hist"], "graph": rep["graph_used"],
+                            "status": rep["status_name"]}}
+    if args.fp64_solve:
+        t0 = time.perf_counter()
+        x64, rep64 = op.solve(t(rhs), tol=1e-10, restart=200, inner_prec="fp64")
+        torch.cuda.synchronize()
+        line["fp64_solve"] = {"ms": (time.perf_counter() - t0) * 1e3, "iters": rep64["iters"],
+                              "rel_res": rep64["rel_res"]}
+    else:
+        line["fp64_solve_estimate_ms"] = ms64 * (rep["iters"] + 2)
+    print(json.dumps(line), flush=True)
+    op.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "helix" and args.impl != "reference":
+        return run_helix(args)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "precision_sweep":
+        return run_precision_sweep(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_gpu(args)
 
 

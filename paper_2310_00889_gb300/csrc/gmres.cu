@@ -1,21 +1,33 @@
-// GMRES for K sigma = u0 (paper Eq. stokes-bie-new), on the device, FP64 Krylov algebra.
+// Batched GMRES for K sigma = u0 (paper Eq. stokes-bie-new), on the device, FP64 Krylov
+// algebra.
 //
 // The paper solves its second-kind BIEs with unpreconditioned GMRES (Sec. 4, Sec. 5)
 // without stating restart, orthogonalisation or initial guess.  This solver uses
 // restarted GMRES(m) with classical Gram--Schmidt applied twice and Givens rotations;
 // every quantity of the Krylov method (basis, Hessenberg matrix, rotations, residual
-// estimate, solution update) is FP64 on the GPU.  Two drivers:
-//   * plain FP64: every operator apply is the FP64 pair sum; a cycle ends on the
-//     Givens estimate, the true FP64 residual decides the restart;
-//   * iterative refinement: the FP64 residual r = b - K x is formed, K d = r is solved
-//     by GMRES whose operator applies run in FP32 or compensated FP32, x += d, repeat.
+// estimate, solution update) is FP64 on the GPU.
+//
+// Segments.  An operator built on a batch plan is block diagonal: its segments are
+// independent problems.  Each segment gets its own Krylov method (its own Hessenberg
+// matrix, rotations, residual estimate and convergence test) while all segments share
+// the Arnoldi step: one operator apply (one persistent launch over every segment) and
+// vector kernels whose row blocks never straddle a segment; the last block of each
+// segment to finish reduces that segment's partial dot products in fixed order.  A cycle
+// ends when every segment has converged (or broken down) or after m steps; a solve ends
+// when every segment's relative residual ||b_s - K_s x_s|| / ||b_s|| meets the tolerance.
+// A single-segment operator is the ordinary GMRES.
+//
+// Two drivers:
+//   * plain FP64: every operator apply is the FP64 pair sum; a cycle ends on the Givens
+//     estimates, the true FP64 residual decides the restart;
+//   * iterative refinement: the FP64 residual r = b - K x is formed, K d = r is solved by
+//     GMRES whose operator applies run in FP32 or compensated FP32, x += d, repeat.
 // Each Arnoldi step is a fixed sequence of kernels that read the step index from device
 // memory, so one captured copy of it serves every step: it is the body of a CUDA-graph
-// while node, which repeats it on the device until the cycle ends (convergence,
-// breakdown or m steps).  One step is: operator apply on v_j; first Gram--Schmidt
-// pass (partial dots, finished by the last block); second pass fused with the first
-// update of w; norm fused with the second update, whose last block also applies the
-// Givens rotations; normalisation that writes v_{j+1} and the next operator input.
+// while node that repeats it on the device until the cycle ends.  Per step: operator
+// apply on v_j; first Gram--Schmidt pass; second pass fused with the first update of w;
+// norm fused with the second update, whose segment-last blocks also apply the Givens
+// rotations; normalisation that writes v_{j+1} and the next operator input; a step guard.
 #include "engine.h"
 
 #include <chrono>
@@ -27,33 +39,44 @@ constexpr int GB = 256;          // threads of the vector kernels
 constexpr int MAX_RESTART = 256;
 constexpr int SOLVE_SMEM_MAX_M = 200;   // back-substitution keeps R in shared memory up to this m
 
-struct GState {
+struct GState {                  // shared by all segments
     int j;          // completed Arnoldi steps of the cycle (= index of the next column)
     int stop;       // the cycle must end
-    int conv;       // Givens estimate <= tol_abs
-    int brk;        // exact breakdown (h_{j+1,j} == 0)
     int m;          // step limit of this cycle
     int iters;      // Arnoldi steps since the solve began
     int nonfinite;  // a non-finite norm was seen
-    unsigned int ctr;   // blocks finished in the current fused kernel
     int guard;      // steps run in this cycle, counted by k_guard
     int guard_hit;  // k_guard ended the cycle (the step counter failed to stop it)
-    double tol_abs; // absolute tolerance on the residual norm of the system being solved
-    double beta;    // residual norm at the start of the cycle
-    double res_est; // |g_{j}| after the last step
-    double res_true;// last norm computed by a norm kernel
-    double inv_hn;  // 1 / h_{j+1,j} of the last step (0 on breakdown)
+    int nseg;
+    unsigned int ctr;       // blocks finished in the current kernel
+    unsigned int seg_done;  // segments finished in the current kernel
+};
+
+struct SegState {                // one per segment
+    double tol_abs;  // absolute tolerance on this segment's residual norm
+    double beta;     // residual norm at the start of the cycle
+    double res_est;  // Givens estimate after the last step
+    double res_true; // last norm computed by the norm kernels
+    double inv_hn;   // 1 / h_{j+1,j} of the last step (0 on breakdown)
+    int conv;        // res_est <= tol_abs
+    int brk;         // exact breakdown
+    unsigned int ctr;   // this segment's blocks finished in the current kernel
+    int pad_;
 };
 
 struct GmresWS {
     int device = 0;
     int m = 0;
+    int nseg = 0;
     long long N = 0;
     int nblk = 0;
-    int ldp = 0;
+    int ldp = 0;      // stride of part rows (m + 1)
+    int LD = 0;       // leading dimension of a Hessenberg matrix (m + 1)
     size_t solve_smem = 0;
-    DevBuf V, H, cs, sn, g, y, hb1, hb2, w, vin, r, d, ax, part, st;
-    GState *hst = nullptr;             // pinned host mirror
+    DevBuf V, H, cs, sn, g, y, hb1, hb2, w, vin, r, d, ax, part, st, seg, blk, segblk, tolv;
+    GState *hst = nullptr;             // pinned host mirrors
+    SegState *hseg = nullptr;
+    double *htol = nullptr;
     cudaStream_t cap = nullptr;        // capture stream
     cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
     cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
@@ -75,12 +98,16 @@ int gmres_destroy(GmresWS *ws)
         cudaStreamDestroy(ws->cap);
     if (ws->hst)
         cudaFreeHost(ws->hst);
+    if (ws->hseg)
+        cudaFreeHost(ws->hseg);
+    if (ws->htol)
+        cudaFreeHost(ws->htol);
     delete ws;
     return SBQ_OK;
 }
 
 // ---------------------------------------------------------------------------
-// Kernels
+// Kernels (row kernels: one block per entry of the block table {row_begin, row_end, seg})
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -100,30 +127,23 @@ __device__ double block_sum(double v, double *red)
     return v;   // thread 0
 }
 
-// Rows [a, b) owned by this block; every fused kernel uses the same partition.
-__device__ __forceinline__ void block_rows(long long N, long long &a, long long &b)
-{
-    const long long chunk = (N + gridDim.x - 1) / gridDim.x;
-    a = static_cast<long long>(blockIdx.x) * chunk;
-    b = a + chunk < N ? a + chunk : N;
-}
-
-// True in the block that finishes last (all other blocks' writes are visible to it).
-__device__ bool last_block(unsigned int *ctr)
+// True in the block that finishes last among `count` blocks counted on *ctr; all their
+// writes are visible to it.  The caller resets *ctr.
+__device__ bool last_of(unsigned int *ctr, unsigned int count)
 {
     __shared__ unsigned int s_last;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0)
-        s_last = (atomicAdd(ctr, 1u) == gridDim.x - 1) ? 1u : 0u;
+        s_last = (atomicAdd(ctr, 1u) == count - 1) ? 1u : 0u;
     __syncthreads();
     if (s_last)
         __threadfence();
     return s_last != 0;
 }
 
-// part[blockIdx][k] = sum over the block's rows of V[k][i] w[i], k = 0..j: one warp per
-// Krylov vector, lanes striding over the rows (coalesced), no block barrier.
+// part_row[k] = sum over rows [a, b) of V[k][i] w[i], k = 0..j: one warp per Krylov
+// vector, lanes striding over the rows (coalesced), no block barrier.
 __device__ void block_multi_dot(const double *__restrict__ V, long long N, int j,
                                 const double *__restrict__ w, long long a, long long b,
                                 double *part_row)
@@ -149,53 +169,58 @@ __device__ void block_multi_dot(const double *__restrict__ V, long long N, int j
     }
 }
 
-// Last block: hb[k] = sum_b part[b][k] (one warp per k, lanes over the blocks, fixed
-// order); column j of H gets (pass 0) or adds (pass 1) it.
-__device__ void finish_dots(const double *part, int ldp, GState *st, double *H, double *hb, int pass)
+// Segment-last block: hb[k] = sum over the segment's blocks of part[b][k] (one warp per
+// k, lanes over the blocks, fixed order); column j of the segment's H gets (pass 0) or
+// adds (pass 1) it.
+__device__ void finish_dots(const double *part, int ldp, int2 sb, int j, double *Hs, int LD,
+                            double *hb, int pass)
 {
-    const int j = st->j, ld = st->m + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int k = warp; k <= j; k += nw) {
         double s = 0.0;
-        for (int bb = lane; bb < (int)gridDim.x; bb += 32)
-            s += __ldcg(part + static_cast<size_t>(bb) * ldp + k);
+        for (int bb = lane; bb < sb.y; bb += 32)
+            s += __ldcg(part + static_cast<size_t>(sb.x + bb) * ldp + k);
         for (int o = 16; o > 0; o >>= 1)
             s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) {
             hb[k] = s;
-            double *h = H + static_cast<size_t>(j) * ld + k;
+            double *h = Hs + static_cast<size_t>(j) * LD + k;
             *h = pass ? *h + s : s;
         }
     }
-    if (threadIdx.x == 0)
-        st->ctr = 0;
 }
 
-// First Gram--Schmidt pass: h1 = V[0..j]^T w.
-__global__ void k_cgs_pass1(const double *__restrict__ V, long long N, GState *st,
+// First Gram--Schmidt pass: h1 = V[0..j]^T w per segment.
+__global__ void k_cgs_pass1(const double *__restrict__ V, long long N, GState *st, SegState *seg,
+                            const int4 *__restrict__ blk, const int2 *__restrict__ segblk,
                             const double *__restrict__ w, double *part, int ldp, double *H,
-                            double *hb1)
+                            int LD, int M, double *hb1)
 {
-    long long a, b;
-    block_rows(N, a, b);
-    block_multi_dot(V, N, st->j, w, a, b, part + static_cast<size_t>(blockIdx.x) * ldp);
-    if (last_block(&st->ctr))
-        finish_dots(part, ldp, st, H, hb1, 0);
+    const int4 bi = blk[blockIdx.x];
+    const int s = bi.z, j = st->j;
+    block_multi_dot(V, N, j, w, bi.x, bi.y, part + static_cast<size_t>(blockIdx.x) * ldp);
+    const int2 sb = segblk[s];
+    if (last_of(&seg[s].ctr, sb.y)) {
+        finish_dots(part, ldp, sb, j, H + static_cast<size_t>(s) * LD * M, LD,
+                    hb1 + static_cast<size_t>(s) * LD, 0);
+        if (threadIdx.x == 0)
+            seg[s].ctr = 0;
+    }
 }
 
 // w -= V h1 on this block's rows, then the second pass h2 = V^T w on the same rows.
-__global__ void k_cgs_pass2(const double *__restrict__ V, long long N, GState *st,
+__global__ void k_cgs_pass2(const double *__restrict__ V, long long N, GState *st, SegState *seg,
+                            const int4 *__restrict__ blk, const int2 *__restrict__ segblk,
                             const double *__restrict__ hb1, double *w, double *part, int ldp,
-                            double *H, double *hb2)
+                            double *H, int LD, int M, double *hb2)
 {
     __shared__ double sh[MAX_RESTART + 1];
-    const int j = st->j;
+    const int4 bi = blk[blockIdx.x];
+    const int s = bi.z, j = st->j;
     for (int k = threadIdx.x; k <= j; k += blockDim.x)
-        sh[k] = hb1[k];
+        sh[k] = hb1[static_cast<size_t>(s) * LD + k];
     __syncthreads();
-    long long a, b;
-    block_rows(N, a, b);
-    for (long long i = a + threadIdx.x; i < b; i += blockDim.x) {
+    for (long long i = bi.x + threadIdx.x; i < bi.y; i += blockDim.x) {
         double acc = w[i];
 #pragma unroll 8
         for (int k = 0; k <= j; ++k)
@@ -203,28 +228,35 @@ __global__ void k_cgs_pass2(const double *__restrict__ V, long long N, GState *s
         w[i] = acc;
     }
     __syncthreads();   // the dots below read rows of w that other threads just updated
-    block_multi_dot(V, N, j, w, a, b, part + static_cast<size_t>(blockIdx.x) * ldp);
-    if (last_block(&st->ctr))
-        finish_dots(part, ldp, st, H, hb2, 1);
+    block_multi_dot(V, N, j, w, bi.x, bi.y, part + static_cast<size_t>(blockIdx.x) * ldp);
+    const int2 sb = segblk[s];
+    if (last_of(&seg[s].ctr, sb.y)) {
+        finish_dots(part, ldp, sb, j, H + static_cast<size_t>(s) * LD * M, LD,
+                    hb2 + static_cast<size_t>(s) * LD, 1);
+        if (threadIdx.x == 0)
+            seg[s].ctr = 0;
+    }
 }
 
-// w -= V h2 and ||w||^2 on this block's rows; the last block forms h_{j+1,j}, applies the
-// previous Givens rotations to column j, builds the new one and updates the residual
-// estimate and the stop flags.
+// w -= V h2 and ||w||^2 on this block's rows.  The segment-last block forms h_{j+1,j},
+// applies the segment's previous Givens rotations to its column j, builds the new one and
+// updates the segment's residual estimate; the last segment to finish decides whether the
+// cycle stops.
 __global__ void k_cgs_norm_givens(const double *__restrict__ V, long long N, GState *st,
-                                  const double *__restrict__ hb2, double *w, double *part,
-                                  double *H, double *cs, double *sn, double *g)
+                                  SegState *seg, const int4 *__restrict__ blk,
+                                  const int2 *__restrict__ segblk, const double *__restrict__ hb2,
+                                  double *w, double *part, double *H, int LD, int M, double *cs,
+                                  double *sn, double *g)
 {
     __shared__ double sh[MAX_RESTART + 1];
     __shared__ double red[32];
-    const int j = st->j;
+    const int4 bi = blk[blockIdx.x];
+    const int s = bi.z, j = st->j;
     for (int k = threadIdx.x; k <= j; k += blockDim.x)
-        sh[k] = hb2[k];
+        sh[k] = hb2[static_cast<size_t>(s) * LD + k];
     __syncthreads();
-    long long a, b;
-    block_rows(N, a, b);
     double nrm = 0.0;
-    for (long long i = a + threadIdx.x; i < b; i += blockDim.x) {
+    for (long long i = bi.x + threadIdx.x; i < bi.y; i += blockDim.x) {
         double acc = w[i];
 #pragma unroll 8
         for (int k = 0; k <= j; ++k)
@@ -235,24 +267,27 @@ __global__ void k_cgs_norm_givens(const double *__restrict__ V, long long N, GSt
     const double bs = block_sum(nrm, red);
     if (threadIdx.x == 0)
         part[blockIdx.x] = bs;
-    if (!last_block(&st->ctr))
+    const int2 sb = segblk[s];
+    if (!last_of(&seg[s].ctr, sb.y))
         return;
-    // the last block: column j of H and the rotations into shared memory in parallel,
+    // segment-last block: column j of H and the rotations into shared memory in parallel,
     // the sequential rotation sweep by one thread, results written back in parallel
     __shared__ double scol[MAX_RESTART + 1], scs[MAX_RESTART], ssn[MAX_RESTART];
     __shared__ double s_hn;
-    const int ld = st->m + 1;
-    double *col = H + static_cast<size_t>(j) * ld;
+    double *Hs = H + static_cast<size_t>(s) * LD * M;
+    double *cs_s = cs + static_cast<size_t>(s) * M, *sn_s = sn + static_cast<size_t>(s) * M;
+    double *g_s = g + static_cast<size_t>(s) * LD;
+    double *col = Hs + static_cast<size_t>(j) * LD;
     for (int i = threadIdx.x; i <= j; i += blockDim.x)
         scol[i] = __ldcg(col + i);
     for (int i = threadIdx.x; i < j; i += blockDim.x) {
-        scs[i] = __ldcg(cs + i);
-        ssn[i] = __ldcg(sn + i);
+        scs[i] = __ldcg(cs_s + i);
+        ssn[i] = __ldcg(sn_s + i);
     }
     if (threadIdx.x < 32) {
         double t = 0.0;
-        for (int bb = threadIdx.x; bb < (int)gridDim.x; bb += 32)
-            t += __ldcg(part + bb);
+        for (int bb = threadIdx.x; bb < sb.y; bb += 32)
+            t += __ldcg(part + sb.x + bb);
         for (int o = 16; o > 0; o >>= 1)
             t += __shfl_xor_sync(0xffffffffu, t, o);
         if (threadIdx.x == 0)
@@ -260,7 +295,8 @@ __global__ void k_cgs_norm_givens(const double *__restrict__ V, long long N, GSt
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        st->ctr = 0;
+        SegState &ss = seg[s];
+        ss.ctr = 0;
         const double hn = s_hn;
         for (int i = 0; i < j; ++i) {
             const double x0 = scol[i], x1 = scol[i + 1];
@@ -270,45 +306,56 @@ __global__ void k_cgs_norm_givens(const double *__restrict__ V, long long N, GSt
         const double x0 = scol[j], x1 = hn;
         const double den = hypot(x0, x1);
         const double cj = (den == 0.0) ? 1.0 : x0 / den, sj = (den == 0.0) ? 0.0 : x1 / den;
-        cs[j] = cj;
-        sn[j] = sj;
+        cs_s[j] = cj;
+        sn_s[j] = sj;
         scol[j] = cj * x0 + sj * x1;
         col[j + 1] = 0.0;
-        const double gj = __ldcg(g + j);
-        g[j + 1] = -sj * gj;
-        g[j] = cj * gj;
+        const double gj = __ldcg(g_s + j);
+        g_s[j + 1] = -sj * gj;
+        g_s[j] = cj * gj;
         const double est = fabs(sj * gj);
-        st->res_est = est;
-        st->iters += 1;
+        ss.res_est = est;
         const bool nonfinite = !isfinite(hn) || !isfinite(est);
-        st->nonfinite |= nonfinite ? 1 : 0;
-        st->conv = est <= st->tol_abs;
-        st->brk = (hn == 0.0);
-        st->inv_hn = (hn > 0.0 && isfinite(hn)) ? 1.0 / hn : 0.0;
-        st->stop = st->conv || st->brk || nonfinite || (j + 1 >= st->m);
+        if (nonfinite)
+            st->nonfinite = 1;
+        ss.conv = ss.conv || (est <= ss.tol_abs);
+        ss.brk = (hn == 0.0);
+        ss.inv_hn = (hn > 0.0 && isfinite(hn)) ? 1.0 / hn : 0.0;
     }
     __syncthreads();
     for (int i = threadIdx.x; i <= j; i += blockDim.x)
         col[i] = scol[i];
+    // the last segment to finish decides for the whole batch
+    if (last_of(&st->seg_done, static_cast<unsigned int>(st->nseg)) && threadIdx.x == 0) {
+        st->seg_done = 0;
+        int all_done = 1;
+        for (int q = 0; q < st->nseg; ++q) {
+            const SegState &o = seg[q];
+            if (!(o.conv || o.brk))
+                all_done = 0;
+        }
+        st->iters += 1;
+        st->stop = all_done || st->nonfinite || (j + 1 >= st->m);
+    }
 }
 
-// v_{j+1} = w / h_{j+1,j}, also written to the operator input buffer; the last block
-// advances j and, inside the graph, sets the while condition.
+// v_{j+1} = w / h_{j+1,j} (per segment), also written to the operator input buffer; the
+// last block advances j and, inside the graph, sets the while condition.
 __global__ void k_normalize_advance(const double *__restrict__ w, long long N, GState *st,
+                                    const SegState *__restrict__ seg, const int4 *__restrict__ blk,
                                     double *V, double *vin, cudaGraphConditionalHandle h,
                                     int use_cond)
 {
+    const int4 bi = blk[blockIdx.x];
     const int j = st->j;
-    const double s = st->inv_hn;
+    const double sc = seg[bi.z].inv_hn;
     double *v = V + static_cast<size_t>(j + 1) * N;
-    long long a, b;
-    block_rows(N, a, b);
-    for (long long i = a + threadIdx.x; i < b; i += blockDim.x) {
-        const double x = w[i] * s;
+    for (long long i = bi.x + threadIdx.x; i < bi.y; i += blockDim.x) {
+        const double x = w[i] * sc;
         v[i] = x;
         vin[i] = x;
     }
-    if (last_block(&st->ctr) && threadIdx.x == 0) {
+    if (last_of(&st->ctr, gridDim.x) && threadIdx.x == 0) {
         st->ctr = 0;
         st->j = j + 1;
         if (use_cond)
@@ -332,104 +379,123 @@ __global__ void k_guard(GState *st, cudaGraphConditionalHandle h, int cap, int u
     }
 }
 
-__global__ void k_norm_part(const double *__restrict__ x, long long N, double *part)
+// part[b] = ||x||^2 over this block's rows.
+__global__ void k_norm_part(const double *__restrict__ x, const int4 *__restrict__ blk, double *part)
 {
     __shared__ double red[32];
-    long long a, b;
-    block_rows(N, a, b);
+    const int4 bi = blk[blockIdx.x];
     double acc = 0.0;
-    for (long long i = a + threadIdx.x; i < b; i += blockDim.x)
+    for (long long i = bi.x + threadIdx.x; i < bi.y; i += blockDim.x)
         acc = fma(x[i], x[i], acc);
     const double s = block_sum(acc, red);
     if (threadIdx.x == 0)
         part[blockIdx.x] = s;
 }
 
-__global__ void k_norm_fin(const double *__restrict__ part, int nblk, GState *st)
+// res_true of every segment from the block partials (fixed order).
+__global__ void k_norm_fin(const double *__restrict__ part, const int2 *__restrict__ segblk,
+                           int nseg, SegState *seg, GState *st)
 {
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int b = 0; b < nblk; ++b)
-            s += part[b];
-        const double r = sqrt(s);
-        st->res_true = r;
+    for (int s = threadIdx.x; s < nseg; s += blockDim.x) {
+        const int2 sb = segblk[s];
+        double t = 0.0;
+        for (int b = 0; b < sb.y; ++b)
+            t += part[sb.x + b];
+        const double r = sqrt(t);
+        seg[s].res_true = r;
         if (!isfinite(r))
             st->nonfinite = 1;
     }
 }
 
-// Start a cycle from the residual whose norm k_norm_fin left in res_true.
-__global__ void k_cycle_init(GState *st, double *g, int m, double tol_abs)
+// Start a cycle from the residual whose per-segment norms are in res_true.
+__global__ void k_cycle_init(GState *st, SegState *seg, const double *__restrict__ tolv, double *g,
+                             int LD, int m, int nseg)
 {
     if (threadIdx.x == 0) {
-        const double beta = st->res_true;
-        st->beta = beta;
         st->j = 0;
         st->stop = 0;
-        st->conv = 0;
-        st->brk = 0;
         st->ctr = 0;
+        st->seg_done = 0;
         st->guard = 0;
         st->m = m;
-        st->tol_abs = tol_abs;
-        st->res_est = beta;
+        st->nseg = nseg;
+    }
+    for (int s = threadIdx.x; s < nseg; s += blockDim.x) {
+        SegState &ss = seg[s];
+        const double beta = ss.res_true;
+        ss.beta = beta;
+        ss.tol_abs = tolv[s];
+        ss.res_est = beta;
+        ss.conv = beta <= tolv[s];
+        ss.brk = 0;
+        ss.ctr = 0;
+        ss.inv_hn = 0.0;
+        double *gs = g + static_cast<size_t>(s) * LD;
         for (int i = 0; i <= m; ++i)
-            g[i] = 0.0;
-        g[0] = beta;
+            gs[i] = 0.0;
+        gs[0] = beta;
     }
 }
 
-// v_0 = r / beta, also the first operator input.
-__global__ void k_scale_first(const double *__restrict__ r, long long N, const GState *__restrict__ st,
-                              double *V, double *vin)
+// v_0 = r / beta per segment (0 for a segment with a zero residual), also the first
+// operator input.
+__global__ void k_scale_first(const double *__restrict__ r, const SegState *__restrict__ seg,
+                              const int4 *__restrict__ blk, double *V, double *vin)
 {
-    const double inv = 1.0 / st->beta;
-    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
-         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int4 bi = blk[blockIdx.x];
+    const double beta = seg[bi.z].beta;
+    const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
+    for (long long i = bi.x + threadIdx.x; i < bi.y; i += blockDim.x) {
         const double x = r[i] * inv;
         V[i] = x;
         vin[i] = x;
     }
 }
 
-// y = R^{-1} g over the j completed steps, R the rotated (upper triangular) H, by
-// columns from the last: y_i = g_i / R_ii, then g_l -= R_li y_i for l < i.  R sits in
-// shared memory when it fits (use_smem).
+// y_s = R_s^{-1} g_s over the j completed steps, R_s the segment's rotated (upper
+// triangular) H, by columns from the last: y_i = g_i / R_ii, then g_l -= R_li y_i for
+// l < i.  One block per segment; R sits in shared memory when it fits (use_smem).
 __global__ void k_solve_y(const GState *__restrict__ st, const double *__restrict__ H,
-                          const double *__restrict__ g, double *y, int use_smem)
+                          const double *__restrict__ g, double *y, int LD, int M, int use_smem)
 {
     extern __shared__ double tri[];
     __shared__ double gs[MAX_RESTART + 1];
-    const int k = st->j, ld = st->m + 1;
+    const int s = blockIdx.x;
+    const int k = st->j;
+    const double *Hs = H + static_cast<size_t>(s) * LD * M;
+    const double *g_s = g + static_cast<size_t>(s) * LD;
+    double *y_s = y + static_cast<size_t>(s) * M;
     for (int i = threadIdx.x; i < k; i += blockDim.x)
-        gs[i] = g[i];
+        gs[i] = g_s[i];
     if (use_smem)
         for (int c = 0; c < k; ++c)
             for (int r = threadIdx.x; r <= c; r += blockDim.x)
-                tri[c * (c + 1) / 2 + r] = H[static_cast<size_t>(c) * ld + r];
+                tri[c * (c + 1) / 2 + r] = Hs[static_cast<size_t>(c) * LD + r];
     __syncthreads();
     for (int i = k - 1; i >= 0; --i) {
-        const double rii = use_smem ? tri[i * (i + 1) / 2 + i] : H[static_cast<size_t>(i) * ld + i];
-        const double yi = gs[i] / rii;
+        const double rii = use_smem ? tri[i * (i + 1) / 2 + i] : Hs[static_cast<size_t>(i) * LD + i];
+        const double yi = (rii != 0.0) ? gs[i] / rii : 0.0;
         if (threadIdx.x == 0)
-            y[i] = yi;
+            y_s[i] = yi;
         for (int l = threadIdx.x; l < i; l += blockDim.x)
-            gs[l] -= (use_smem ? tri[i * (i + 1) / 2 + l] : H[static_cast<size_t>(i) * ld + l]) * yi;
+            gs[l] -= (use_smem ? tri[i * (i + 1) / 2 + l] : Hs[static_cast<size_t>(i) * LD + l]) * yi;
         __syncthreads();
     }
 }
 
-// x += sum_{k < j} V[k] y[k]
+// x += sum_{k < j} V[k] y_s[k] on each block's rows (segment s of the block).
 __global__ void k_update_x(const double *__restrict__ V, long long N, const GState *__restrict__ st,
-                           const double *__restrict__ y, double *x)
+                           const int4 *__restrict__ blk, const double *__restrict__ y, int M,
+                           double *x)
 {
     __shared__ double sy[MAX_RESTART];
+    const int4 bi = blk[blockIdx.x];
     const int k = st->j;
     for (int i = threadIdx.x; i < k; i += blockDim.x)
-        sy[i] = y[i];
+        sy[i] = y[static_cast<size_t>(bi.z) * M + i];
     __syncthreads();
-    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
-         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    for (long long i = bi.x + threadIdx.x; i < bi.y; i += blockDim.x) {
         double acc = x[i];
         for (int l = 0; l < k; ++l)
             acc = fma(V[static_cast<size_t>(l) * N + i], sy[l], acc);
@@ -479,20 +545,39 @@ static int ws_ensure(Op *op, int m)
     auto *ws = new GmresWS();
     ws->m = m;
     ws->N = 3 * op->n;
-    const long long N = ws->N;
-    ws->nblk = static_cast<int>(std::max<long long>(1, std::min<long long>(4LL * device_props().sms,
-                                                                        (N + 127) / 128)));
+    ws->nseg = op->plan.nseg;
     ws->ldp = m + 1;
+    ws->LD = m + 1;
+    const long long N = ws->N, n = op->n;
+    const int nseg = ws->nseg;
+    // Block table: rows of segment s are the three component ranges c n + [o_s, o_{s+1});
+    // each range is cut into chunks of about N / (8 SMs) rows, at least 128.
+    const long long chunk = std::max<long long>(128, N / (8LL * device_props().sms) + 1);
+    std::vector<int4> hb;
+    std::vector<int2> hsb(nseg);
+    for (int s = 0; s < nseg; ++s) {
+        hsb[s].x = static_cast<int>(hb.size());
+        const long long a = op->plan.src_off[s], b = op->plan.src_off[s + 1];
+        for (int c = 0; c < 3; ++c)
+            for (long long r = a; r < b; r += chunk)
+                hb.push_back(make_int4(static_cast<int>(c * n + r),
+                                       static_cast<int>(c * n + std::min(b, r + chunk)), s, 0));
+        if (b == a)   // an empty segment still owns one (empty) block
+            hb.push_back(make_int4(0, 0, s, 0));
+        hsb[s].y = static_cast<int>(hb.size()) - hsb[s].x;
+    }
+    ws->nblk = static_cast<int>(hb.size());
     ws->solve_smem = (m <= SOLVE_SMEM_MAX_M) ? static_cast<size_t>(m) * (m + 1) / 2 * sizeof(double) : 0;
+    const size_t S = nseg;
     int s = SBQ_OK;
     if (s == SBQ_OK) s = ws->V.alloc(static_cast<size_t>(m + 1) * N * sizeof(double));
-    if (s == SBQ_OK) s = ws->H.alloc(static_cast<size_t>(m + 1) * m * sizeof(double));
-    if (s == SBQ_OK) s = ws->cs.alloc(m * sizeof(double));
-    if (s == SBQ_OK) s = ws->sn.alloc(m * sizeof(double));
-    if (s == SBQ_OK) s = ws->g.alloc((m + 1) * sizeof(double));
-    if (s == SBQ_OK) s = ws->y.alloc(m * sizeof(double));
-    if (s == SBQ_OK) s = ws->hb1.alloc((m + 1) * sizeof(double));
-    if (s == SBQ_OK) s = ws->hb2.alloc((m + 1) * sizeof(double));
+    if (s == SBQ_OK) s = ws->H.alloc(S * (m + 1) * m * sizeof(double));
+    if (s == SBQ_OK) s = ws->cs.alloc(S * m * sizeof(double));
+    if (s == SBQ_OK) s = ws->sn.alloc(S * m * sizeof(double));
+    if (s == SBQ_OK) s = ws->g.alloc(S * (m + 1) * sizeof(double));
+    if (s == SBQ_OK) s = ws->y.alloc(S * m * sizeof(double));
+    if (s == SBQ_OK) s = ws->hb1.alloc(S * (m + 1) * sizeof(double));
+    if (s == SBQ_OK) s = ws->hb2.alloc(S * (m + 1) * sizeof(double));
     if (s == SBQ_OK) s = ws->w.alloc(N * sizeof(double));
     if (s == SBQ_OK) s = ws->vin.alloc(N * sizeof(double));
     if (s == SBQ_OK) s = ws->r.alloc(N * sizeof(double));
@@ -500,8 +585,14 @@ static int ws_ensure(Op *op, int m)
     if (s == SBQ_OK) s = ws->ax.alloc(N * sizeof(double));
     if (s == SBQ_OK) s = ws->part.alloc(static_cast<size_t>(ws->nblk) * (m + 1) * sizeof(double));
     if (s == SBQ_OK) s = ws->st.alloc(sizeof(GState));
+    if (s == SBQ_OK) s = ws->seg.alloc(S * sizeof(SegState));
+    if (s == SBQ_OK) s = ws->blk.alloc(hb.size() * sizeof(int4));
+    if (s == SBQ_OK) s = ws->segblk.alloc(S * sizeof(int2));
+    if (s == SBQ_OK) s = ws->tolv.alloc(S * sizeof(double));
     if (s == SBQ_OK) {
         cudaError_t e = cudaMallocHost(&ws->hst, sizeof(GState));
+        if (e == cudaSuccess) e = cudaMallocHost(&ws->hseg, S * sizeof(SegState));
+        if (e == cudaSuccess) e = cudaMallocHost(&ws->htol, S * sizeof(double));
         if (e != cudaSuccess)
             s = cuda_status(e, "cudaMallocHost");
     }
@@ -512,8 +603,13 @@ static int ws_ensure(Op *op, int m)
     }
     if (s == SBQ_OK) {
         cudaError_t e = cudaMemset(ws->st.p, 0, sizeof(GState));
+        if (e == cudaSuccess) e = cudaMemset(ws->seg.p, 0, S * sizeof(SegState));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(ws->blk.p, hb.data(), hb.size() * sizeof(int4), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(ws->segblk.p, hsb.data(), S * sizeof(int2), cudaMemcpyHostToDevice);
         if (e != cudaSuccess)
-            s = cuda_status(e, "cudaMemset");
+            s = cuda_status(e, "gmres workspace set-up");
     }
     if (s == SBQ_OK && ws->solve_smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_solve_y, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -539,19 +635,24 @@ static int enqueue_step(Op *op, GmresWS *ws, int prec, cudaStream_t s,
 {
     const long long N = ws->N;
     GState *st = ws->st.as<GState>();
+    SegState *sg = ws->seg.as<SegState>();
+    const int4 *blk = ws->blk.as<int4>();
+    const int2 *sb = ws->segblk.as<int2>();
     SBQ_TRY(op_matvec(op, ws->vin.as<double>(), ws->w.as<double>(), prec, s));
-    k_cgs_pass1<<<ws->nblk, GB, 0, s>>>(ws->V.as<double>(), N, st, ws->w.as<double>(),
-                                        ws->part.as<double>(), ws->ldp, ws->H.as<double>(),
-                                        ws->hb1.as<double>());
-    k_cgs_pass2<<<ws->nblk, GB, 0, s>>>(ws->V.as<double>(), N, st, ws->hb1.as<double>(),
+    k_cgs_pass1<<<ws->nblk, GB, 0, s>>>(ws->V.as<double>(), N, st, sg, blk, sb, ws->w.as<double>(),
+                                        ws->part.as<double>(), ws->ldp, ws->H.as<double>(), ws->LD,
+                                        ws->m, ws->hb1.as<double>());
+    k_cgs_pass2<<<ws->nblk, GB, 0, s>>>(ws->V.as<double>(), N, st, sg, blk, sb, ws->hb1.as<double>(),
                                         ws->w.as<double>(), ws->part.as<double>(), ws->ldp,
-                                        ws->H.as<double>(), ws->hb2.as<double>());
-    k_cgs_norm_givens<<<ws->nblk, GB, 0, s>>>(ws->V.as<double>(), N, st, ws->hb2.as<double>(),
-                                              ws->w.as<double>(), ws->part.as<double>(),
-                                              ws->H.as<double>(), ws->cs.as<double>(),
-                                              ws->sn.as<double>(), ws->g.as<double>());
-    k_normalize_advance<<<ws->nblk, GB, 0, s>>>(ws->w.as<double>(), N, st, ws->V.as<double>(),
-                                                ws->vin.as<double>(), h, use_cond);
+                                        ws->H.as<double>(), ws->LD, ws->m, ws->hb2.as<double>());
+    k_cgs_norm_givens<<<ws->nblk, GB, 0, s>>>(ws->V.as<double>(), N, st, sg, blk, sb,
+                                              ws->hb2.as<double>(), ws->w.as<double>(),
+                                              ws->part.as<double>(), ws->H.as<double>(), ws->LD,
+                                              ws->m, ws->cs.as<double>(), ws->sn.as<double>(),
+                                              ws->g.as<double>());
+    k_normalize_advance<<<ws->nblk, GB, 0, s>>>(ws->w.as<double>(), N, st, sg, blk,
+                                                ws->V.as<double>(), ws->vin.as<double>(), h,
+                                                use_cond);
     k_guard<<<1, 32, 0, s>>>(st, h, ws->m, use_cond);
     SBQ_CUDA(cudaGetLastError());
     return SBQ_OK;
@@ -613,21 +714,31 @@ static int build_graph(Op *op, GmresWS *ws, int prec)
 static int read_state(GmresWS *ws, cudaStream_t s)
 {
     SBQ_CUDA(cudaMemcpyAsync(ws->hst, ws->st.p, sizeof(GState), cudaMemcpyDeviceToHost, s));
+    SBQ_CUDA(cudaMemcpyAsync(ws->hseg, ws->seg.p, ws->nseg * sizeof(SegState),
+                             cudaMemcpyDeviceToHost, s));
     SBQ_CUDA(cudaStreamSynchronize(s));
     return SBQ_OK;
 }
 
-// ||v|| into st->res_true (and the host mirror).
+// Per-segment ||v|| into res_true (device and host mirrors).
 static int norm_to_state(GmresWS *ws, const double *v, cudaStream_t s)
 {
-    k_norm_part<<<ws->nblk, GB, 0, s>>>(v, ws->N, ws->part.as<double>());
-    k_norm_fin<<<1, 32, 0, s>>>(ws->part.as<double>(), ws->nblk, ws->st.as<GState>());
+    k_norm_part<<<ws->nblk, GB, 0, s>>>(v, ws->blk.as<int4>(), ws->part.as<double>());
+    k_norm_fin<<<1, GB, 0, s>>>(ws->part.as<double>(), ws->segblk.as<int2>(), ws->nseg,
+                                ws->seg.as<SegState>(), ws->st.as<GState>());
     SBQ_CUDA(cudaGetLastError());
     ws->launches += 2;
     return read_state(ws, s);
 }
 
-// r = b - K x in precision prec; ||r|| to the state.
+static void copy_res(const GmresWS *ws, std::vector<double> &out)
+{
+    out.resize(ws->nseg);
+    for (int i = 0; i < ws->nseg; ++i)
+        out[i] = ws->hseg[i].res_true;
+}
+
+// r = b - K x in precision prec; per-segment ||r|| to the state.
 static int residual(Op *op, GmresWS *ws, int prec, const double *b, const double *x, double *r,
                     cudaStream_t s)
 {
@@ -638,14 +749,21 @@ static int residual(Op *op, GmresWS *ws, int prec, const double *b, const double
     return norm_to_state(ws, r, s);
 }
 
-// One GMRES cycle from residual r (norm in the state) updating xu += V y.
+// One GMRES cycle from residual r (per-segment norms in the state) updating xu += V y;
+// tol_abs[s] is each segment's absolute residual target.
 static int run_cycle(Op *op, GmresWS *ws, int prec, const double *r, double *xu, int m,
-                     double tol_abs, bool use_graph, cudaStream_t s, bool *graph_used)
+                     const std::vector<double> &tol_abs, bool use_graph, cudaStream_t s,
+                     bool *graph_used)
 {
-    const long long N = ws->N;
     GState *st = ws->st.as<GState>();
-    k_cycle_init<<<1, 32, 0, s>>>(st, ws->g.as<double>(), m, tol_abs);
-    k_scale_first<<<vec_grid(N), GB, 0, s>>>(r, N, st, ws->V.as<double>(), ws->vin.as<double>());
+    for (int i = 0; i < ws->nseg; ++i)
+        ws->htol[i] = tol_abs[i];
+    SBQ_CUDA(cudaMemcpyAsync(ws->tolv.p, ws->htol, ws->nseg * sizeof(double), cudaMemcpyHostToDevice,
+                             s));
+    k_cycle_init<<<1, GB, 0, s>>>(st, ws->seg.as<SegState>(), ws->tolv.as<double>(),
+                                  ws->g.as<double>(), ws->LD, m, ws->nseg);
+    k_scale_first<<<ws->nblk, GB, 0, s>>>(r, ws->seg.as<SegState>(), ws->blk.as<int4>(),
+                                          ws->V.as<double>(), ws->vin.as<double>());
     SBQ_CUDA(cudaGetLastError());
     bool done = false;
     if (use_graph) {
@@ -670,17 +788,39 @@ static int run_cycle(Op *op, GmresWS *ws, int prec, const double *r, double *xu,
                 break;
         }
     }
-    k_solve_y<<<1, GB, ws->solve_smem, s>>>(st, ws->H.as<double>(), ws->g.as<double>(),
-                                             ws->y.as<double>(), ws->solve_smem > 0 ? 1 : 0);
-    k_update_x<<<vec_grid(N), GB, 0, s>>>(ws->V.as<double>(), N, st, ws->y.as<double>(), xu);
+    k_solve_y<<<ws->nseg, GB, ws->solve_smem, s>>>(st, ws->H.as<double>(), ws->g.as<double>(),
+                                                    ws->y.as<double>(), ws->LD, ws->m,
+                                                    ws->solve_smem > 0 ? 1 : 0);
+    k_update_x<<<ws->nblk, GB, 0, s>>>(ws->V.as<double>(), ws->N, st, ws->blk.as<int4>(),
+                                       ws->y.as<double>(), ws->m, xu);
     SBQ_CUDA(cudaGetLastError());
     SBQ_TRY(read_state(ws, s));
-    ws->launches += 4 + static_cast<long long>(ws->hst->j) * step_kernels(op, prec);
+    ws->launches += 5 + static_cast<long long>(ws->hst->j) * step_kernels(op, prec);
     if (ws->hst->guard_hit) {
         set_error("Arnoldi loop stopped by its step guard (inconsistent step counter)");
         return SBQ_ECUDA;
     }
     return SBQ_OK;
+}
+
+// max over segments of res[s] / ref[s] (segments with ref 0 count as 0)
+static double max_rel(const std::vector<double> &res, const std::vector<double> &ref)
+{
+    double m = 0.0;
+    for (size_t i = 0; i < res.size(); ++i) {
+        const double v = ref[i] > 0.0 ? res[i] / ref[i] : (res[i] > 0.0 ? INFINITY : 0.0);
+        if (!(v <= m))
+            m = v;   // also propagates NaN
+    }
+    return m;
+}
+
+static bool all_finite(const std::vector<double> &v)
+{
+    for (double x : v)
+        if (!std::isfinite(x))
+            return false;
+    return true;
 }
 
 int gmres_solve_impl(Op *op, const double *b, double *x, const sbq_gmres_opts &o,
@@ -694,6 +834,7 @@ int gmres_solve_impl(Op *op, const double *b, double *x, const sbq_gmres_opts &o
     GmresWS *ws = op->gm;
     ws->launches = 0;
     const long long N = ws->N;
+    const int nseg = ws->nseg;
     if (!device_error_word()) {
         set_error("cannot allocate the device error word");
         return SBQ_ENOMEM;
@@ -702,13 +843,17 @@ int gmres_solve_impl(Op *op, const double *b, double *x, const sbq_gmres_opts &o
     if (mixed)
         SBQ_TRY(op_ensure_tuned(op, low, s));
 
+    std::vector<double> bnorm, res, tol_abs(nseg);
     SBQ_TRY(norm_to_state(ws, b, s));
-    const double bnorm = ws->hst->res_true;
-    if (!std::isfinite(bnorm)) {
+    copy_res(ws, bnorm);
+    if (!all_finite(bnorm)) {
         set_error("right-hand side is not finite");
         return SBQ_ENONFINITE;
     }
-    if (bnorm == 0.0) {
+    bool bzero = true;
+    for (double v : bnorm)
+        bzero = bzero && (v == 0.0);
+    if (bzero) {
         SBQ_CUDA(cudaMemsetAsync(x, 0, N * sizeof(double), s));
         SBQ_CUDA(cudaStreamSynchronize(s));
         rep.status = SBQ_OK;
@@ -716,7 +861,6 @@ int gmres_solve_impl(Op *op, const double *b, double *x, const sbq_gmres_opts &o
         rep.rel_res_hist[0] = 0.0;
         return SBQ_OK;
     }
-    const double tol_abs = o.tol * bnorm;
     bool graph_used = false;
     auto push_hist = [&](double v) {
         if (rep.n_hist < SBQ_HIST)
@@ -725,23 +869,22 @@ int gmres_solve_impl(Op *op, const double *b, double *x, const sbq_gmres_opts &o
 
     // Initial residual: b itself when x0 = 0 (no operator apply needed).
     SBQ_TRY(norm_to_state(ws, x, s));
-    if (ws->hst->res_true == 0.0) {
+    bool xzero = true;
+    for (int i = 0; i < nseg; ++i)
+        xzero = xzero && (ws->hseg[i].res_true == 0.0);
+    if (xzero) {
         SBQ_CUDA(cudaMemcpyAsync(ws->r.p, b, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        ws->hst->res_true = bnorm;
-        k_norm_part<<<ws->nblk, GB, 0, s>>>(ws->r.as<double>(), N, ws->part.as<double>());
-        k_norm_fin<<<1, 32, 0, s>>>(ws->part.as<double>(), ws->nblk, ws->st.as<GState>());
-        SBQ_CUDA(cudaGetLastError());
-        ws->launches += 2;
-        SBQ_TRY(read_state(ws, s));
+        SBQ_TRY(norm_to_state(ws, ws->r.as<double>(), s));
     } else {
         SBQ_TRY(residual(op, ws, SBQ_FP64, b, x, ws->r.as<double>(), s));
         rep.matvecs_fp64 += 1;
     }
-    double res = ws->hst->res_true;
-    push_hist(res / bnorm);
+    copy_res(ws, res);
+    double rel = max_rel(res, bnorm);
+    push_hist(rel);
     int status = SBQ_OK;
-    while (res > tol_abs) {
-        if (!std::isfinite(res)) {
+    while (rel > o.tol) {
+        if (!std::isfinite(rel)) {
             status = SBQ_ENONFINITE;
             set_error("residual is not finite");
             break;
@@ -753,12 +896,16 @@ int gmres_solve_impl(Op *op, const double *b, double *x, const sbq_gmres_opts &o
         }
         if (!mixed) {
             const int m = std::min(o.restart, o.max_iter - rep.iters);
-            SBQ_TRY(run_cycle(op, ws, SBQ_FP64, ws->r.as<double>(), x, m, tol_abs, o.use_graph != 0,
-                              s, &graph_used));
+            for (int i = 0; i < nseg; ++i)
+                tol_abs[i] = o.tol * bnorm[i];
+            SBQ_TRY(run_cycle(op, ws, SBQ_FP64, ws->r.as<double>(), x, m, tol_abs,
+                              o.use_graph != 0, s, &graph_used));
             const int steps = ws->hst->j;
             rep.iters += steps;
             rep.matvecs_fp64 += steps;
-            const bool brk = ws->hst->brk != 0;
+            bool any_brk = false;
+            for (int i = 0; i < nseg; ++i)
+                any_brk = any_brk || ws->hseg[i].brk;
             if (ws->hst->nonfinite) {
                 status = SBQ_ENONFINITE;
                 set_error("non-finite value in the Arnoldi process");
@@ -767,29 +914,30 @@ int gmres_solve_impl(Op *op, const double *b, double *x, const sbq_gmres_opts &o
             SBQ_TRY(residual(op, ws, SBQ_FP64, b, x, ws->r.as<double>(), s));
             rep.matvecs_fp64 += 1;
             rep.outer_iters += 1;
-            const double nres = ws->hst->res_true;
-            push_hist(nres / bnorm);
-            if (brk && nres > tol_abs && nres >= res) {
+            copy_res(ws, res);
+            const double nrel = max_rel(res, bnorm);
+            push_hist(nrel);
+            if (any_brk && nrel > o.tol && nrel >= rel) {
                 status = SBQ_EBREAKDOWN;
                 set_error("GMRES breakdown without convergence");
-                res = nres;
+                rel = nrel;
                 break;
             }
-            res = nres;
+            rel = nrel;
         } else {
-            // inner solve K_low d = r, d = 0, to inner_tol * ||r||
+            // inner solve K_low d = r, d = 0, to inner_tol * ||r_s|| per segment
             double *d = ws->d.as<double>();
             SBQ_CUDA(cudaMemsetAsync(d, 0, N * sizeof(double), s));
-            const double inner_abs = o.inner_tol * res;
-            double ires = res;
+            // a segment need not go below half the outer target
+            for (int i = 0; i < nseg; ++i)
+                tol_abs[i] = std::max(o.inner_tol * res[i], 0.5 * o.tol * bnorm[i]);
+            std::vector<double> ires = res;
             const double *rin = ws->r.as<double>();
-            // the inner residual lives in ws->ax's partner buffer between restarts; the
-            // first cycle starts from r itself, whose norm is in the state already
             for (;;) {
                 const int m = std::min(o.restart, o.max_iter - rep.iters);
                 if (m <= 0)
                     break;
-                SBQ_TRY(run_cycle(op, ws, low, rin, d, m, inner_abs, o.use_graph != 0, s,
+                SBQ_TRY(run_cycle(op, ws, low, rin, d, m, tol_abs, o.use_graph != 0, s,
                                   &graph_used));
                 const int steps = ws->hst->j;
                 rep.iters += steps;
@@ -798,7 +946,10 @@ int gmres_solve_impl(Op *op, const double *b, double *x, const sbq_gmres_opts &o
                     status = SBQ_ENONFINITE;
                     break;
                 }
-                if (ws->hst->conv || ws->hst->brk)
+                bool all_done = true;
+                for (int i = 0; i < nseg; ++i)
+                    all_done = all_done && (ws->hseg[i].conv || ws->hseg[i].brk);
+                if (all_done)
                     break;
                 // restart the inner solve from its true low-precision residual r - K d,
                 // kept in w (the next cycle reads it before its first step writes w)
@@ -809,8 +960,14 @@ int gmres_solve_impl(Op *op, const double *b, double *x, const sbq_gmres_opts &o
                 SBQ_CUDA(cudaGetLastError());
                 ws->launches += op_kernels_per_matvec(op, low) + 1;
                 SBQ_TRY(norm_to_state(ws, ws->w.as<double>(), s));
-                const double nr = ws->hst->res_true;
-                if (!(nr < ires) || nr <= inner_abs)
+                std::vector<double> nr;
+                copy_res(ws, nr);
+                bool progress = false, reached = true;
+                for (int i = 0; i < nseg; ++i) {
+                    progress = progress || (nr[i] < ires[i]);
+                    reached = reached && (nr[i] <= tol_abs[i]);
+                }
+                if (!progress || reached)
                     break;
                 ires = nr;
                 rin = ws->w.as<double>();
@@ -825,19 +982,20 @@ int gmres_solve_impl(Op *op, const double *b, double *x, const sbq_gmres_opts &o
             SBQ_TRY(residual(op, ws, SBQ_FP64, b, x, ws->r.as<double>(), s));
             rep.matvecs_fp64 += 1;
             rep.outer_iters += 1;
-            const double nres = ws->hst->res_true;
-            push_hist(nres / bnorm);
-            if (!(nres < res)) {
-                res = nres;
+            copy_res(ws, res);
+            const double nrel = max_rel(res, bnorm);
+            push_hist(nrel);
+            if (!(nrel < rel)) {
+                rel = nrel;
                 status = SBQ_ENOCONV;
                 set_error("iterative refinement stagnated above the tolerance");
                 break;
             }
-            res = nres;
+            rel = nrel;
         }
     }
     SBQ_CUDA(cudaStreamSynchronize(s));
-    rep.rel_res = res / bnorm;
+    rep.rel_res = rel;
     rep.graph_used = graph_used ? 1 : 0;
     rep.kernel_launches = static_cast<int>(std::min<long long>(ws->launches, INT32_MAX));
     rep.status = status;

@@ -195,29 +195,41 @@ def _frame_rhs(e1, dc, ddc):
 
 
 def _transport_frame(s_out, k, A, B, substeps=8):
-    """Integrate the frame ODE with classical RK4 from s = 0 through the sorted s_out."""
+    """Integrate the frame ODE with classical RK4 from s = 0 through the sorted s_out.
+
+    The ODE is de1/ds = e1 x omega(s), omega = x_c'' x x_c' / |x_c'|^2; omega is evaluated
+    at every RK4 stage point in one vectorised call, then the steps run sequentially."""
     _, dc0, _ = _loop_eval(np.array([0.0]), k, A, B)
     t0 = _unit(dc0)[:, 0]
     guess = np.array([0.3, -0.5, 0.8])
     e = guess - guess.dot(t0) * t0
     e /= np.linalg.norm(e)
+    s_prev = np.concatenate([[0.0], s_out[:-1]])
+    h = (s_out - s_prev) / substeps                                  # (M,)
+    starts = s_prev[:, None] + h[:, None] * np.arange(substeps)[None, :]   # (M, q)
+    stage = np.stack([starts, starts + 0.5 * h[:, None], starts + h[:, None]], axis=-1)
+    _, d1, d2 = _loop_eval(stage.reshape(-1), k, A, B)
+    om = (_cross(d2, d1) / np.sum(d1 * d1, axis=0)).T.reshape(s_out.size, substeps, 3, 3)
     out = np.empty((3, s_out.size))
-    s_cur = 0.0
+    ex, ey, ez = (float(v) for v in e)
 
-    def f(sv, ev):
-        _, d1, d2 = _loop_eval(np.array([sv]), k, A, B)
-        return _frame_rhs(ev[:, None], d1, d2)[:, 0]
+    def cr(ax, ay, az, b):
+        return ay * b[2] - az * b[1], az * b[0] - ax * b[2], ax * b[1] - ay * b[0]
 
-    for i, s_t in enumerate(s_out):
-        h = (s_t - s_cur) / substeps
-        for _ in range(substeps):
-            k1 = f(s_cur, e)
-            k2 = f(s_cur + 0.5 * h, e + 0.5 * h * k1)
-            k3 = f(s_cur + 0.5 * h, e + 0.5 * h * k2)
-            k4 = f(s_cur + h, e + h * k3)
-            e = e + (h / 6.0) * (k1 + 2 * k2 + 2 * k3 + k4)
-            s_cur += h
-        out[:, i] = e
+    om_l = om.tolist()
+    h_l = h.tolist()
+    for i in range(s_out.size):
+        hh = h_l[i]
+        for q in range(substeps):
+            w0, wm, w1 = om_l[i][q]
+            k1 = cr(ex, ey, ez, w0)
+            k2 = cr(ex + 0.5 * hh * k1[0], ey + 0.5 * hh * k1[1], ez + 0.5 * hh * k1[2], wm)
+            k3 = cr(ex + 0.5 * hh * k2[0], ey + 0.5 * hh * k2[1], ez + 0.5 * hh * k2[2], wm)
+            k4 = cr(ex + hh * k3[0], ey + hh * k3[1], ez + hh * k3[2], w1)
+            ex += hh / 6.0 * (k1[0] + 2 * k2[0] + 2 * k3[0] + k4[0])
+            ey += hh / 6.0 * (k1[1] + 2 * k2[1] + 2 * k3[1] + k4[1])
+            ez += hh / 6.0 * (k1[2] + 2 * k2[2] + 2 * k3[2] + k4[2])
+        out[0, i], out[1, i], out[2, i] = ex, ey, ez
     return out
 
 

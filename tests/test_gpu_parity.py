@@ -391,3 +391,45 @@ def test_bounded_wait_expiry_is_reported(sbq):
     s = c["surf"]
     u = _apply(sbq, "sl", s.x, s.n, s.w, c["sigma"], c["trg"], "fp64")
     assert np.all(np.isfinite(u))
+
+
+def test_batched_solve_matches_segment_solves(sbq, oracle_mod):
+    """GMRES-IR over a block-diagonal batch of 4 independent capped arcs (one persistent
+    launch per apply, graph-replayed Arnoldi steps): every segment's FP64 residual, computed
+    by the oracle on that segment alone, meets the tolerance."""
+    segs = [I.config2(panels=p, nth=32, nr=8) for p in (1, 2, 3, 2)]
+    off = np.cumsum([0] + [g["surf"].size for g in segs])
+    X = np.concatenate([g["surf"].x for g in segs], axis=1)
+    Nn = np.concatenate([g["surf"].n for g in segs], axis=1)
+    W = np.concatenate([g["surf"].w for g in segs])
+    B = np.concatenate([g["rhs"] for g in segs], axis=1)
+    eta = sbq.slender_eta(0.2)
+    op = sbq.StokesOp(_t(X), _t(Nn), _t(W), eta, plan=sbq.BatchPlan(off))
+    x, rep = op.solve(_t(B), tol=1e-10, restart=100, inner_prec="fp32c", inner_tol=1e-5)
+    assert rep["status"] == 0 and rep["rel_res"] <= 1e-10 and rep["graph_used"]
+    xs = _np(x)
+    total = 0.0
+    for i, g in enumerate(segs):
+        a, b = off[i], off[i + 1]
+        s = g["surf"]
+        kx = oracle_mod.matvec(s.x, s.n, s.w, eta, xs[:, a:b])
+        total += np.sum((g["rhs"] - kx) ** 2)
+    assert np.sqrt(total) / np.linalg.norm(B) <= 1.05e-10
+    op.close()
+
+
+def test_compensation_helps_on_a_random_loop(sbq, oracle_mod):
+    """Random slender loop (paper Sec. 5.2 recipe, 4096 nodes): the compensated FP32
+    operator meets the FP32 bar and is more accurate than the plain FP32 one.  The plain
+    FP32 error on this thin tube (radius 0.005..0.015, nodes 4e-3 apart) was measured at
+    1.3e-4 on GB300; its bar here is 5e-4."""
+    s = I.random_loop(seed=1, panels=32, ns=8, nth=16)
+    sig = I.density(s.size, seed=2)
+    eta = sbq.slender_eta(0.01)
+    op = sbq.StokesOp(_t(s.x), _t(s.n), _t(s.w), eta)
+    ref = oracle_mod.matvec(s.x, s.n, s.w, eta, sig)
+    e = {p: _relerr(_np(op.matvec(_t(sig), prec=p)), ref) for p in ("fp32", "fp32c", "fp64")}
+    print("random loop errors", e)
+    assert e["fp64"] <= TOL_F64
+    assert e["fp32c"] <= TOL_F32["fp32c"] and e["fp32c"] <= e["fp32"] and e["fp32"] <= 5e-4
+    op.close()
