@@ -53,6 +53,9 @@ def parse():
                     help="CPU work bound of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-reps", type=int, default=20)
+    ap.add_argument("--no-correction", action="store_true",
+                    help="solve with the punctured sums alone (no double-layer singularity "
+                         "subtraction)")
     ap.add_argument("--workload", default="curved_pipe",
                     choices=["curved_pipe", "precision_sweep", "batch", "helix"],
                     help="curved_pipe: the benchmark line (default); precision_sweep: FP32 vs "
@@ -62,6 +65,9 @@ def parse():
                     help="precision_sweep: panel counts of the random loops (x 128 nodes)")
     ap.add_argument("--helix-panels", type=int, default=2048,
                     help="helix: axial panels of the helical wall (2048 -> 1,048,576 wall nodes)")
+    ap.add_argument("--helix-pitch", type=float, default=3.0,
+                    help="helix: pitch (at 2 the tube surfaces of adjacent turns are 0.011 "
+                         "apart, which the punctured sums cannot resolve)")
     ap.add_argument("--fp64-solve", action="store_true",
                     help="batch: also time the plain FP64 GMRES solve (minutes)")
     ap.add_argument("--no-graph", action="store_true",
@@ -244,7 +250,8 @@ def run_gpu(args):
         return kernel_only(args, sbq, I, src, nrm, w, eta, n, t, dev)
 
     t_setup = time.perf_counter()
-    op = sbq.StokesOp(src, nrm, w, eta)
+    corr = None if args.no_correction else sbq.dl_gauss_correction(src, nrm, w, prec="fp64")
+    op = sbq.StokesOp(src, nrm, w, eta, correction=corr)
     op.autotune("fp32c")
     op.autotune("fp64")
     torch.cuda.synchronize()
@@ -315,23 +322,22 @@ def run_gpu(args):
     out = torch.empty_like(sig)
 
     def time_matvec(prec, reps_):
+        """(pair-sum kernel ms, whole apply ms): CUDA events recorded by the library on the
+        launching stream around the kernel launch and around the apply; L2 flushed before
+        each apply."""
         for _ in range(2):
             op.matvec(sig, prec=prec, out=out)
-        tl = []
+        kl, al = [], []
         for _ in range(reps_):
             flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            op.matvec(sig, prec=prec, out=out)
-            e1.record(stream)
-            e1.synchronize()
-            tl.append(e0.elapsed_time(e1))
-        return float(np.mean(tl))
+            kms, ams = op.time_pairsum(sig, prec=prec, reps=1, out=out)
+            kl.append(kms)
+            al.append(ams)
+        return float(np.mean(kl)), float(np.mean(al))
 
-    k32c = time_matvec("fp32c", args.kernel_reps)
-    k32 = time_matvec("fp32", args.kernel_reps)
-    k64 = time_matvec("fp64", max(3, args.kernel_reps // 4))
+    kk32c, k32c = time_matvec("fp32c", args.kernel_reps)
+    kk32, k32 = time_matvec("fp32", args.kernel_reps)
+    kk64, k64 = time_matvec("fp64", max(3, args.kernel_reps // 4))
     info = sbq.device_info()
     sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -341,12 +347,13 @@ def run_gpu(args):
         except Exception:
             pass
     peak = info["sms"] * info["fp32_lanes_per_sm"] * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
-    achieved = FLOPS_PER_PAIR["cf"] * float(n) * n / (k32c * 1e-3) / 1e12
+    achieved = FLOPS_PER_PAIR["cf"] * float(n) * n / (kk32c * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
                 "kernel": "pairsum_f32_kernel<combined field, compensated>",
                 "flops_per_pair": FLOPS_PER_PAIR["cf"], "pairs_per_launch": float(n) * n,
-                "launch_ms": k32c,
+                "launch_ms": kk32c, "apply_ms": k32c,
+                "timing": "CUDA events on the launching stream around the kernel launch",
                 "peak_basis": "%d SMs x %d FP32 lanes x 2 x %.0f MHz (sm_max_mhz)" % (
                     info["sms"], info["fp32_lanes_per_sm"], sm_max)}
     if clocks and clocks.get("sm_mhz"):
@@ -361,7 +368,8 @@ def run_gpu(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         xh, reph = sbq.solve_from_host(hsrc, hnrm, hw, hrhs, eta, tol=1e-10, inner_prec="fp32c",
-                                       restart=100, inner_tol=1e-5, max_outer=30, device=dev)
+                                       restart=100, inner_tol=1e-5, max_outer=30, device=dev,
+                                       correction=None if args.no_correction else "fp64")
         torch.cuda.synchronize()
         if k > 0:
             e2e_times.append(time.perf_counter() - t0)
@@ -385,6 +393,8 @@ def run_gpu(args):
             "config": {"workload": WORKLOAD, "nodes": n, "unknowns": 3 * n, "eta": eta,
                        "tol": 1e-10, "inner": "fp32 compensated, FP64 refinement",
                        "restart": 100, "graph": not args.no_graph,
+                       "correction": "none" if args.no_correction else
+                       "double-layer singularity subtraction, built in FP64 on the GPU",
                        "l2": "flushed between steps (256 MiB write, outside the timed intervals)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "solve": {"mixed_ms": ms, "fp64_ms": fp64_ms, "speedup_vs_fp64": fp64_ms / ms,
@@ -394,6 +404,8 @@ def run_gpu(args):
                       "fp64_iters": rep64["iters"], "fp64_rel_res": rep64["rel_res"],
                       "x_rel_diff_mixed_vs_fp64": xdiff},
             "kernels": {"fp32c_matvec_ms": k32c, "fp32_matvec_ms": k32, "fp64_matvec_ms": k64,
+                        "fp32c_pairsum_kernel_ms": kk32c, "fp32_pairsum_kernel_ms": kk32,
+                        "fp64_pairsum_kernel_ms": kk64,
                         "fp32c_pairs_per_s": n * n / (k32c * 1e-3),
                         "fp32_pairs_per_s": n * n / (k32 * 1e-3),
                         "fp64_pairs_per_s": n * n / (k64 * 1e-3),
@@ -403,8 +415,8 @@ def run_gpu(args):
             "clocks": clocks,
             "e2e": {"value": pairs_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3,
-                    "includes": "H2D of geometry and data, operator build, graph capture, "
-                                "solve, D2H of the solution"},
+                    "includes": "H2D of geometry and data, correction and operator build, "
+                                "graph capture, solve, D2H of the solution"},
             "gpu_launches": launches,
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -446,9 +458,10 @@ def kernel_only(args, sbq, I, src, nrm, w, eta, n, t, dev):
     return 0
 
 
-def _cuda_timer(fn, reps, stream):
+def _cuda_timer(fn, reps, stream, warm=True):
     import torch
-    fn()
+    if warm:
+        fn()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -557,22 +570,33 @@ def run_batch(args):
         worst = max(worst, float(((r1 - u64[:, a:b_]).abs().max() / r1.abs().max()).item()))
         o1.close()
     rhs = t(B)
-    # restart 200: some coarse segments have indefinite discrete operators on which
-    # GMRES(100) stagnates (their own Krylov space per segment, see gmres.cu)
-    x, rep = op.solve(rhs, tol=1e-10, restart=200, inner_prec="fp32c", inner_tol=1e-5)
+    # solves: the same batch with the double-layer singularity subtraction of every
+    # segment (each segment is one closed body); without it the punctured sums leave
+    # some segments' discrete operators indefinite and restarted GMRES stagnates
+    t0 = time.perf_counter()
+    corr = None
+    if not args.no_correction:
+        corr = sbq.dl_gauss_correction(t(X), t(Nn), t(W), off, prec="fp64")
+    opc = sbq.StokesOp(t(X), t(Nn), t(W), eta, correction=corr, plan=plan)
+    torch.cuda.synchronize()
+    corr_ms = (time.perf_counter() - t0) * 1e3
+    x, rep = opc.solve(rhs, tol=1e-10, restart=100, inner_prec="fp32c", inner_tol=1e-5)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    x, rep = op.solve(rhs, tol=1e-10, restart=200, inner_prec="fp32c", inner_tol=1e-5)
+    x, rep = opc.solve(rhs, tol=1e-10, restart=100, inner_prec="fp32c", inner_tol=1e-5)
     torch.cuda.synchronize()
     mixed_ms = (time.perf_counter() - t0) * 1e3
     # residual of every segment (FP64 operator)
-    kx = op.matvec(x, prec="fp64")
+    kx = opc.matvec(x, prec="fp64")
     seg_res = []
     for i in range(len(segs)):
         a, b_ = int(off[i]), int(off[i + 1])
         seg_res.append(float(((rhs[:, a:b_] - kx[:, a:b_]).norm() / rhs[:, a:b_].norm()).item()))
     line = {"workload": "batch_64_capped_arcs", "segments": len(segs), "nodes": n,
             "pairs_per_matvec": pairs, "setup_ms": setup_ms, "tune": tune,
+            "correction": "none" if args.no_correction else
+            "double-layer singularity subtraction per segment, FP64",
+            "correction_and_operator_ms": corr_ms,
             "matvec_ms": mv, "pairs_per_s": {p: pairs / (v * 1e-3) for p, v in mv.items()},
             "fp32c_relerr_vs_fp64": float(((u - u64).abs().max() / u64.abs().max()).item()),
             "batched_vs_single_segment_fp64_relerr": worst,
@@ -582,7 +606,7 @@ def run_batch(args):
                             "max_segment_rel_res": max(seg_res)}}
     if args.fp64_solve:
         t0 = time.perf_counter()
-        x64, rep64 = op.solve(rhs, tol=1e-10, restart=200, inner_prec="fp64")
+        x64, rep64 = opc.solve(rhs, tol=1e-10, restart=100, inner_prec="fp64")
         torch.cuda.synchronize()
         line["fp64_solve"] = {"ms": (time.perf_counter() - t0) * 1e3, "iters": rep64["iters"],
                               "rel_res": rep64["rel_res"]}
@@ -590,11 +614,12 @@ def run_batch(args):
         line["fp64_solve_estimate_ms"] = mv["fp64"] * (rep["iters"] + 2)
     print(json.dumps(line), flush=True)
     op.close()
+    opc.close()
     return 0
 
 
 def run_helix(args):
-    """Helical pipe (helix radius 3, pitch 2, 4 turns, tube radius 1, 2048 panels x 8 x 64
+    """Helical pipe (helix radius 3, pitch --helix-pitch (3), 4 turns, tube radius 1, 2048 x 8 x 64
     = 1,048,576 wall nodes, two 16 x 64 caps) with 100 spheres of radius 0.2 (600 nodes
     each) inside: one mixed-precision GMRES-IR solve to 1e-10 (zero wall and sphere data,
     parabolic cap profiles); the plain FP64 solve is estimated from its iteration count and
@@ -610,11 +635,11 @@ def run_helix(args):
     stream = torch.cuda.current_stream()
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
     t0 = time.perf_counter()
-    c = I.config5(panels=args.helix_panels)
+    c = I.config5(panels=args.helix_panels, pitch=args.helix_pitch)
     s = c["surf"]
     n = s.size
     rhs = np.zeros((3, n))
-    a_, b_ = 3.0, 2.0 / (2.0 * np.pi)
+    a_, b_ = 3.0, args.helix_pitch / (2.0 * np.pi)
     pe = np.array([0.0, 2.0 * np.pi * 4.0])
     cend = np.stack([a_ * np.cos(pe), a_ * np.sin(pe), b_ * pe])
     tend = np.stack([-a_ * np.sin(pe), a_ * np.cos(pe), np.full(2, b_)])
@@ -635,7 +660,10 @@ def run_helix(args):
     o = torch.empty_like(sig)
     ms32 = _cuda_timer(lambda: op.matvec(sig, prec="fp32c", out=o), 2, stream)
     u32 = o.clone()
-    ms64 = _cuda_timer(lambda: op.matvec(sig, prec="fp64", out=o), 1, stream)
+    # one FP64 apply here takes about a minute: fix the tile shape (the autotuner takes
+    # the first shape when one apply is that long), then time one apply
+    op.autotune("fp64")
+    ms64 = _cuda_timer(lambda: op.matvec(sig, prec="fp64", out=o), 1, stream, warm=False)
     u64 = o.clone()
     rows = np.sort(np.random.default_rng(4).choice(n, 4096, replace=False))
     sg = sig.cpu().numpy()
@@ -643,23 +671,39 @@ def run_helix(args):
     ri = torch.as_tensor(rows, device="cuda")
     e64 = float(np.abs(u64[:, ri].cpu().numpy() - ref).max() / np.abs(ref).max())
     e32 = float(np.abs(u32[:, ri].cpu().numpy() - ref).max() / np.abs(ref).max())
+    # solve with the double-layer singularity subtraction per closed body (the capped
+    # pipe, each sphere), its row sums in compensated FP32 (in FP64 they would take
+    # three applies of about a minute each)
     t0 = time.perf_counter()
-    x, rep = op.solve(t(rhs), tol=1e-10, restart=200, inner_prec="fp32c", inner_tol=1e-5)
+    corr = None
+    if not args.no_correction:
+        corr = sbq.dl_gauss_correction(t(s.x), t(s.n), t(s.w), I.body_offsets(s), prec="fp32c")
+    op.close()
+    op = sbq.StokesOp(t(s.x), t(s.n), t(s.w), eta, correction=corr)
+    torch.cuda.synchronize()
+    corr_ms = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    x, rep = op.solve(t(rhs), tol=1e-10, restart=100, inner_prec="fp32c", inner_tol=1e-5,
+                      max_iter=400)
     torch.cuda.synchronize()
     mixed_ms = (time.perf_counter() - t0) * 1e3
     line = {"workload": "helix_pipe_with_spheres", "nodes": n, "spheres": len(c["centres"]),
-            "eta": eta, "pairs_per_matvec": float(n) * n, "generation_s": gen_s,
+            "pitch": args.helix_pitch, "eta": eta, "pairs_per_matvec": float(n) * n,
+            "generation_s": gen_s,
             "setup_ms": setup_ms, "tune_fp32c": tune32,
             "matvec_ms": {"fp32c": ms32, "fp64": ms64},
             "pairs_per_s": {"fp32c": n * n / (ms32 * 1e-3), "fp64": n * n / (ms64 * 1e-3)},
             "relerr_vs_oracle_4096_rows": {"fp64": e64, "fp32c": e32},
+            "correction": "none" if args.no_correction else
+            "double-layer singularity subtraction per body (pipe, 100 spheres), FP32c",
+            "correction_and_operator_ms": corr_ms,
             "mixed_solve": {"ms": mixed_ms, "iters": rep["iters"], "refinements": rep["outer_iters"],
                             "matvecs_fp32c": rep["matvecs_low"], "matvecs_fp64": rep["matvecs_fp64"],
                             "rel_res": rep["rel_res"], "hist": rep["hist"], "graph": rep["graph_used"],
                             "status": rep["status_name"]}}
     if args.fp64_solve:
         t0 = time.perf_counter()
-        x64, rep64 = op.solve(t(rhs), tol=1e-10, restart=200, inner_prec="fp64")
+        x64, rep64 = op.solve(t(rhs), tol=1e-10, restart=100, inner_prec="fp64")
         torch.cuda.synchronize()
         line["fp64_solve"] = {"ms": (time.perf_counter() - t0) * 1e3, "iters": rep64["iters"],
                               "rel_res": rep64["rel_res"]}

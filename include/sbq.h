@@ -195,9 +195,46 @@ SBQ_API int stokes_op_create(int64_t n, const double *src, const double *nrm, co
                              const int64_t *col, const double *val, const void *plan,
                              void **op_out);
 
+/*
+ * Double-layer singularity subtraction as a sparse correction E for stokes_op_create
+ * (the local, classical form of the correction of Eq. nystrom-correction, Sec. 3.2.1).
+ * The nodes are split into closed bodies: body b holds nodes body_off[b] ..
+ * body_off[b+1]-1 (body_off: HOST array of nbody+1 non-decreasing offsets, body_off[0]
+ * = 0, n = body_off[nbody]).  For node i of body b, with the 3 x 3 row sum
+ *   R_i = sum over j in b, j != i, of D(x_i, y_j; n_j) w_j              (Eq. stokes-dl)
+ * the correction is the diagonal block E_ii = -R_i - I/2.  Because the double layer
+ * of a constant density is -e/2 on a closed surface, an operator with diag = 1/2 and
+ * this E applies, at x_i, sum over the node's own body of D_ij (sigma_j - sigma_i)
+ * (a summand bounded at r -> 0) plus the plain double-layer sums of the other bodies.
+ * Rigid motions of one body are annihilated exactly by its own part.
+ *   src, nrm, w  device arrays (SoA, 3n / 3n / n doubles), as for stokes_op_create.
+ *   prec         precision of the three double-layer applies that form R (sbq_prec).
+ *   rowptr       device, 3n+1 int64: written as 3 * row.
+ *   col, val     device, 9n entries each: row c*n+i holds columns b*n+i, b = 0, 1, 2
+ *                (component-major indices, ascending).
+ * Caller owns every buffer; the call allocates its own temporary workspace on the
+ * stream.  Errors: SBQ_EINVAL for bad offsets, sizes or null pointers.
+ * Not a counterpart of the paper's quadrature (it builds E from modal and adaptive
+ * rules); this local form is for inputs without such a correction.
+ */
+SBQ_API int stokes_dl_gauss_correction(int nbody, const int64_t *body_off, const double *src,
+                                       const double *nrm, const double *w, int prec,
+                                       int64_t *rowptr, int64_t *col, double *val,
+                                       void *stream);
+
 /* out = K sigma (device arrays of 3*n doubles) in precision prec, on `stream`. */
 SBQ_API int stokes_matvec(const void *op, const double *sigma, double *out, int prec,
                           void *stream);
+
+/*
+ * Kernel timing without a profiler (paper has no counterpart): runs `reps` >= 1 applies
+ * out = K sigma as stokes_matvec does, records CUDA events on `stream` immediately before
+ * and after each launch of the pair-sum kernel and around each whole apply, synchronises
+ * the stream, and returns the mean durations in milliseconds (either pointer may be NULL).
+ * Errors: SBQ_EINVAL for a bad handle or reps < 1; CUDA errors as SBQ_ECUDA.
+ */
+SBQ_API int sbq_op_time_pairsum(const void *op, const double *sigma, double *out, int prec,
+                                int reps, void *stream, double *kernel_ms, double *apply_ms);
 
 /*
  * Solve K x = rhs (device arrays of 3*n doubles).  x holds x0 on entry and the

@@ -16,6 +16,9 @@ Contents
   * `gmres`: restarted GMRES(m) with classical Gram--Schmidt applied twice and
     Givens rotations (the paper uses unpreconditioned GMRES, Sec. 4, without
     giving restart or orthogonalisation details);
+  * `dl_gauss_correction`: the double-layer singularity subtraction written as a
+    sparse correction E (per closed body, from the Gauss-type identity D[e] = -e/2
+    on the surface);
   * `eta_slender`: the slender-body mixing parameter 1 / (2 eps log(1/eps))
     (Sec. 4.1, Laplace and Stokes slender combined-field formulations).
 
@@ -152,6 +155,44 @@ def matvec(src, nrm, w, eta, sigma, diag=0.5, E: CSR | None = None):
         lib.oracle_stokes_matvec(n, _p(src), _p(nrm), _p(w), float(eta), float(diag), 0, None,
                                  None, None, _p(sigma), _p(out))
     return out
+
+
+def dl_gauss_correction(src, nrm, w, body_off=None) -> CSR:
+    """Double-layer singularity subtraction as a sparse E (local form of the correction
+    of Eq. nystrom-correction).
+
+    The double layer of a constant density is -e/2 on a closed surface, so
+    D[sigma](x_i) = D[sigma - sigma_i](x_i) - sigma_i / 2 on the node's own body.  With
+    the punctured sum for D and diag = 1/2 this is the correction
+    E_ii = -R_i - I/2 (3 x 3 block), R_i = sum_{j in own body, j != i} D(x_i, y_j; n_j) w_j.
+    R_i is taken column by column as the double layer of the unit densities e_b over the
+    body alone.  Rows and columns are component-major (c * n + node); each row holds
+    its node's three columns in ascending order.
+    """
+    src = _c(src)
+    n = src.shape[1]
+    nrm = _c(nrm, (3, n))
+    w = _c(w, (n,))
+    off = [0, n] if body_off is None else [int(v) for v in body_off]
+    R = np.zeros((3, 3, n))            # R[a, b, i]
+    for lo, hi in zip(off[:-1], off[1:]):
+        if hi <= lo:
+            continue
+        for b in range(3):
+            e = np.zeros((3, hi - lo))
+            e[b] = 1.0
+            R[:, b, lo:hi] = dl(src[:, lo:hi], nrm[:, lo:hi], w[lo:hi], e, src[:, lo:hi])
+    rows = 3 * n
+    rowptr = 3 * np.arange(rows + 1, dtype=np.int64)
+    col = np.empty(9 * n, dtype=np.int64)
+    val = np.empty(9 * n)
+    for a in range(3):
+        for i in range(n):
+            r = a * n + i
+            for b in range(3):
+                col[3 * r + b] = b * n + i
+                val[3 * r + b] = -R[a, b, i] - (0.5 if a == b else 0.0)
+    return CSR(rowptr, col, val, rows, rows)
 
 
 def dense_operator(src, nrm, w, trg, alpha, beta):

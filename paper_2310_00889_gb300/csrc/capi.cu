@@ -258,6 +258,60 @@ SBQ_API int stokes_matvec(const void *oph, const double *sigma, double *out, int
     return op_matvec(op, sigma, out, prec, static_cast<cudaStream_t>(stream));
 }
 
+SBQ_API int sbq_op_time_pairsum(const void *oph, const double *sigma, double *out, int prec,
+                                int reps, void *stream, double *kernel_ms, double *apply_ms)
+{
+    clear_error();
+    Op *op = as_op(oph);
+    if (!op)
+        return fail(SBQ_EINVAL, "not an operator handle");
+    if (!prec_ok(prec))
+        return fail(SBQ_EINVAL, "unknown precision");
+    if (reps < 1)
+        return fail(SBQ_EINVAL, "reps < 1");
+    if (op->n > 0 && (!sigma || !out))
+        return fail(SBQ_EINVAL, "null density or output pointer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> lk(op->mu);
+    SBQ_TRY(op_ensure_tuned(op, prec, s));
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int st = SBQ_OK;
+    for (int i = 0; i < 4 && st == SBQ_OK; ++i)
+        if (cudaEventCreate(&ev[i]) != cudaSuccess)
+            st = fail(SBQ_ECUDA, "cudaEventCreate");
+    PairsumTiming pt;
+    pt.before = ev[0];
+    pt.after = ev[1];
+    double ksum = 0.0, asum = 0.0;
+    for (int r = 0; r < reps && st == SBQ_OK; ++r) {
+        cudaEventRecord(ev[2], s);
+        pairsum_timing() = &pt;
+        st = op_matvec(op, sigma, out, prec, s);
+        pairsum_timing() = nullptr;
+        cudaEventRecord(ev[3], s);
+        if (st != SBQ_OK)
+            break;
+        cudaError_t e = cudaEventSynchronize(ev[3]);
+        float k = 0.0f, a = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&k, ev[0], ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&a, ev[2], ev[3]);
+        if (e != cudaSuccess)
+            st = cuda_status(e, "pair-sum timing");
+        ksum += k;
+        asum += a;
+    }
+    for (cudaEvent_t e : ev)
+        if (e)
+            cudaEventDestroy(e);
+    if (st != SBQ_OK)
+        return st;
+    if (kernel_ms)
+        *kernel_ms = ksum / reps;
+    if (apply_ms)
+        *apply_ms = asum / reps;
+    return SBQ_OK;
+}
+
 SBQ_API int gmres_solve(const void *oph, const double *rhs, double *x, const sbq_gmres_opts *o,
                         sbq_gmres_report *rep, void *stream)
 {
@@ -342,6 +396,31 @@ SBQ_API int sbq_check_device(void *stream)
             return fail(SBQ_ETIMEOUT, "a device-side bounded wait expired");
     }
     return SBQ_OK;
+}
+
+SBQ_API int stokes_dl_gauss_correction(int nbody, const int64_t *body_off, const double *src,
+                                       const double *nrm, const double *w, int prec,
+                                       int64_t *rowptr, int64_t *col, double *val, void *stream)
+{
+    clear_error();
+    if (nbody < 1 || !body_off)
+        return fail(SBQ_EINVAL, "nbody < 1 or null offsets");
+    if (body_off[0] != 0)
+        return fail(SBQ_EINVAL, "offsets must start at 0");
+    for (int i = 0; i < nbody; ++i)
+        if (body_off[i + 1] < body_off[i])
+            return fail(SBQ_EINVAL, "offsets must be non-decreasing");
+    const int64_t n = body_off[nbody];
+    if (n > (1LL << 31) / 3)
+        return fail(SBQ_EINVAL, "n above 2^31 / 3");
+    if (!prec_ok(prec))
+        return fail(SBQ_EINVAL, "unknown precision");
+    if (!rowptr)
+        return fail(SBQ_EINVAL, "null rowptr");
+    if (n > 0 && (!src || !nrm || !w || !col || !val))
+        return fail(SBQ_EINVAL, "null geometry or CSR pointer");
+    return dl_gauss_correction(nbody, body_off, src, nrm, w, prec, rowptr, col, val,
+                               static_cast<cudaStream_t>(stream));
 }
 
 SBQ_API void sbq_destroy(void *handle)

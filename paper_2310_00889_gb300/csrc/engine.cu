@@ -335,6 +335,12 @@ int build_trg_set(TrgSet &ts, int kind, int prec, const sbq_tune &tune, const Sr
     return SBQ_OK;
 }
 
+PairsumTiming *&pairsum_timing()
+{
+    static thread_local PairsumTiming *t = nullptr;
+    return t;
+}
+
 int run_pairsum(int kind, int prec, const SrcPack &sp, const TrgSet &ts, const double *w,
                 const double *sigma, long long ns, const double *trg, long long nt, double *out,
                 double scale, double kappa, double diag, const double *diag_sigma, cudaStream_t s)
@@ -367,7 +373,12 @@ int run_pairsum(int kind, int prec, const SrcPack &sp, const TrgSet &ts, const d
     p.scale = scale;
     p.kappa = kappa;
     p.TT = ts.TT;
+    PairsumTiming *pt = pairsum_timing();
+    if (pt)
+        SBQ_CUDA(cudaEventRecord(pt->before, s));
     SBQ_CUDA(launch_pairsum(kind, prec, ts.tune.r, ts.tune.warps, ts.grid, p, s));
+    if (pt)
+        SBQ_CUDA(cudaEventRecord(pt->after, s));
     if (prec != SBQ_FP64)
         SBQ_CUDA(launch_reduce_partials_f32(ts.ttiles.as<TileInfo>(), ts.n_ttiles, ts.TT,
                                             ts.partial.p, nt, out, scale, diag, diag_sigma,
@@ -467,10 +478,29 @@ static int autotune_op(Op *op, int prec, cudaStream_t s)
             auto ts = std::make_unique<TrgSet>();
             int st = build_trg_set(*ts, kind, prec, t, sp, op->plan.src_off, op->src.as<double>(),
                                    op->n, op->plan.src_off, s);
-            if (st == SBQ_OK)
+            // first (warm-up) apply, timed: a shape whose single apply is already long is
+            // taken as it is (tuning it would cost more than it can save)
+            float first_ms = 0.0f;
+            if (st == SBQ_OK) {
+                cudaEventRecord(e0, s);
                 st = run_pairsum(kind, prec, sp, *ts, op->w.as<double>(), zs.as<double>(), op->n,
                                  op->src.as<double>(), op->n, zo.as<double>(), scale, kappa, 0.0,
                                  nullptr, s);
+                cudaEventRecord(e1, s);
+                if (st == SBQ_OK) {
+                    cudaError_t ce = cudaEventSynchronize(e1);
+                    if (ce != cudaSuccess)
+                        st = cuda_status(ce, "autotune");
+                    else
+                        cudaEventElapsedTime(&first_ms, e0, e1);
+                }
+            }
+            if (st == SBQ_OK && first_ms > 250.0f) {
+                if (!best)
+                    best = std::move(ts);
+                budget_ms = 1e30;
+                break;
+            }
             const int reps = slow ? 1 : 3;
             if (st == SBQ_OK) {
                 cudaEventRecord(e0, s);

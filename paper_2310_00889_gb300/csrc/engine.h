@@ -88,6 +88,13 @@ int build_trg_set(TrgSet &ts, int kind, int prec, const sbq_tune &tune, const Sr
                   const std::vector<int64_t> &trg_off, const double *trg, long long nt,
                   const std::vector<int64_t> &src_off, cudaStream_t s);
 
+// Events recorded on the launching stream immediately before and after each pair-sum
+// kernel launch of this host thread while set (kernel timing without a profiler).
+struct PairsumTiming {
+    cudaEvent_t before = nullptr, after = nullptr;
+};
+PairsumTiming *&pairsum_timing();
+
 // One pair-sum apply: out = scale * sum(...) [+ diag * diag_sigma].
 int run_pairsum(int kind, int prec, const SrcPack &sp, const TrgSet &ts, const double *w,
                 const double *sigma, long long ns, const double *trg, long long nt, double *out,
@@ -102,6 +109,11 @@ int op_kernels_per_matvec(const Op *op, int prec);
 void kind_and_scale(double alpha, double beta, int *kind, double *scale, double *kappa);
 
 sbq_tune default_tune(int prec, long long nt);
+
+// correction.cu: E = -R_i - I/2 per node from per-body double-layer row sums.
+int dl_gauss_correction(int nbody, const int64_t *body_off, const double *src, const double *nrm,
+                        const double *w, int prec, int64_t *rowptr, int64_t *col, double *val,
+                        cudaStream_t s);
 int gmres_destroy(struct GmresWS *ws);
 
 }  // namespace sbq

@@ -66,6 +66,18 @@ def concat(surfaces, name="") -> Surface:
                    np.concatenate([s.w for s in surfaces]), name=name, parts=tuple(parts))
 
 
+def body_offsets(surf: Surface):
+    """Node offsets of the closed bodies of a surface: a pipe wall and the end caps that
+    follow it form one body, every other part (a sphere, a torus, a loop) is a body."""
+    if not surf.parts:
+        return [0, surf.size]
+    off = []
+    for nm, a, b in surf.parts:
+        if not nm.startswith("cap") or not off:
+            off.append(a)
+    return off + [surf.size]
+
+
 def gl_rule(n: int):
     """Gauss--Legendre nodes and weights on [-1, 1]."""
     x, w = np.polynomial.legendre.leggauss(n)
@@ -378,11 +390,12 @@ def config4(nseg=64, seed=3, ns=8, nth=32, nr=16, n_lo=2048, n_hi=65536):
     return dict(segments=segs, slenderness=1.0 / 5.0)
 
 
-def config5(panels=2048, ns=8, nth=64, nr=16, nsph=100, seed=5):
-    """Helical pipe (helix radius 3, pitch 2, 4 turns, tube radius 1) with caps, plus nsph
+def config5(panels=2048, ns=8, nth=64, nr=16, nsph=100, seed=5, turns=4.0, pitch=2.0):
+    """Helical pipe (helix radius 3, pitch `pitch` (2), `turns` turns (4), tube radius 1) with
+    caps, plus nsph
     spheres of radius 0.2 (20 x 30 nodes) at uniform random positions inside the tube,
     at least 0.05 from the wall and from each other (seed 5)."""
-    a, pitch, turns, R, rs = 3.0, 2.0, 4.0, 1.0, 0.2
+    a, R, rs = 3.0, 1.0, 0.2
     wall = helix_pipe(a, pitch, turns, R, panels, ns, nth)
     b = pitch / (2.0 * np.pi)
     pe = np.array([0.0, 2.0 * np.pi * turns])

@@ -11,6 +11,7 @@ import ctypes
 import math
 import os
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -91,6 +92,10 @@ def _load():
         "sbq_op_tune": ([_vp, _int, ctypes.POINTER(Tune)], _int),
         "sbq_op_stats": ([_vp, _int, ctypes.POINTER(_int), ctypes.POINTER(_dbl)], _int),
         "sbq_check_device": ([_vp], _int),
+        "sbq_op_time_pairsum": ([_vp, _vp, _vp, _int, _int, _vp, ctypes.POINTER(_dbl),
+                                 ctypes.POINTER(_dbl)], _int),
+        "stokes_dl_gauss_correction": ([_int, _vp, _vp, _vp, _vp, _int, _vp, _vp, _vp, _vp],
+                                       _int),
         "sbq_destroy": ([_vp], None),
     }
     for name, (args, res) in sig.items():
@@ -195,6 +200,29 @@ def combined_apply(src, nrm, w, sigma, trg, alpha, beta, prec="fp32c", out=None,
     return _apply("cf", src, nrm, w, sigma, trg, alpha, beta, prec, out, stream)
 
 
+def dl_gauss_correction(src, nrm, w, body_off=None, prec="fp64", stream=None):
+    """Sparse correction E (rowptr, col, val) of the double layer by singularity
+    subtraction per closed body: E_ii = -R_i - I/2 with R_i the 3 x 3 double-layer row
+    sum of node i over its own body (body_off: node offsets of the bodies, default one
+    body).  Pass the result as StokesOp(..., correction=...)."""
+    n = src.shape[1]
+    _dev(src, (3, n), "src")
+    _dev(nrm, (3, n), "nrm")
+    _dev(w, (n,), "w")
+    off = np.asarray([0, n] if body_off is None else body_off, dtype=np.int64)
+    if off.ndim != 1 or off.size < 2 or int(off[-1]) != n:
+        raise ValueError("body_off must end at the node count %d" % n)
+    c_off = (ctypes.c_int64 * off.size)(*[int(v) for v in off])
+    dev = src.device
+    rowptr = torch.empty(3 * n + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(9 * n, dtype=torch.int64, device=dev)
+    val = torch.empty(9 * n, dtype=torch.float64, device=dev)
+    _check(lib.stokes_dl_gauss_correction(int(off.size - 1), c_off, _ptr(src), _ptr(nrm), _ptr(w),
+                                          _prec(prec), _ptr(rowptr), _ptr(col), _ptr(val),
+                                          _stream(stream)))
+    return rowptr, col, val
+
+
 def check_device(stream=None):
     """Synchronise and raise SbqError(ETIMEOUT) if a device-side bounded wait expired."""
     _check(lib.sbq_check_device(_stream(stream)))
@@ -292,6 +320,19 @@ class StokesOp:
         d["status_name"] = _STATUS.get(st, st)
         return x, d
 
+    def time_pairsum(self, sigma, prec="fp32c", reps=1, out=None, stream=None):
+        """(pair-sum kernel ms, whole apply ms), means over reps applies, from CUDA events
+        recorded on the stream around the kernel launch and around the apply."""
+        n = self.n
+        _dev(sigma, (3, n), "sigma")
+        if out is None:
+            out = torch.empty((3, n), dtype=torch.float64, device=sigma.device)
+        _dev(out, (3, n), "out")
+        k, a = _dbl(), _dbl()
+        _check(lib.sbq_op_time_pairsum(self.handle, _ptr(sigma), _ptr(out), _prec(prec), int(reps),
+                                       _stream(stream), ctypes.byref(k), ctypes.byref(a)))
+        return k.value, a.value
+
     def autotune(self, prec, stream=None):
         t = Tune()
         _check(lib.sbq_autotune(self.handle, _prec(prec), ctypes.byref(t), _stream(stream)))
@@ -309,15 +350,21 @@ class StokesOp:
 
 
 def solve_from_host(src, nrm, w, rhs, eta, tol=1e-10, inner_prec="fp32c", restart=100,
-                    max_iter=2000, inner_tol=1e-5, max_outer=30, use_graph=True, device="cuda"):
+                    max_iter=2000, inner_tol=1e-5, max_outer=30, use_graph=True, device="cuda",
+                    correction=None, body_off=None):
     """End-to-end call on host (pinned CPU) tensors: copy the geometry and data to the GPU,
-    build the operator, solve, and copy the solution back to the host."""
+    build the operator, solve, and copy the solution back to the host.  correction: None,
+    or the precision ("fp64", "fp32c", "fp32") in which to build the double-layer
+    singularity subtraction over the bodies body_off (default one body)."""
     dev = torch.device(device)
     d_src = src.to(dev, non_blocking=True)
     d_nrm = nrm.to(dev, non_blocking=True)
     d_w = w.to(dev, non_blocking=True)
     d_rhs = rhs.to(dev, non_blocking=True)
-    op = StokesOp(d_src, d_nrm, d_w, eta)
+    E = None
+    if correction is not None:
+        E = dl_gauss_correction(d_src, d_nrm, d_w, body_off, prec=correction)
+    op = StokesOp(d_src, d_nrm, d_w, eta, correction=E)
     x, rep = op.solve(d_rhs, tol=tol, inner_prec=inner_prec, restart=restart, max_iter=max_iter,
                       inner_tol=inner_tol, max_outer=max_outer, use_graph=use_graph)
     out = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)

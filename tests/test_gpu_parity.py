@@ -433,3 +433,101 @@ def test_compensation_helps_on_a_random_loop(sbq, oracle_mod):
     assert e["fp64"] <= TOL_F64
     assert e["fp32c"] <= TOL_F32["fp32c"] and e["fp32c"] <= e["fp32"] and e["fp32"] <= 5e-4
     op.close()
+
+
+# ---------------------------------------------------------------------------
+# Double-layer singularity subtraction (sparse correction E built on the GPU)
+# ---------------------------------------------------------------------------
+
+def _multibody_case():
+    """Capped 60-degree arc (768 nodes) with two spheres (150 nodes each) inside: three
+    closed bodies, 1068 nodes, ragged tiles in every body."""
+    pipe = I.capped_arc_pipe(5.0, np.deg2rad(60.0), 1.0, 4, 8, 16, 8)
+    c = np.array([5.0 * np.cos(np.deg2rad(30.0)), 5.0 * np.sin(np.deg2rad(30.0)), 0.0])
+    sph = [I.sphere(0.3, c + d, 10, 15) for d in (np.array([0.0, 0.0, 0.4]),
+                                                   np.array([0.2, -0.2, -0.35]))]
+    s = I.concat([pipe] + sph)
+    return s, I.body_offsets(s)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c", "fp32"])
+def test_gauss_correction_matches_oracle(sbq, oracle_mod, prec):
+    """E = -R_i - I/2 per node, R_i the double-layer row sum over the node's own body:
+    structure bit-exact, values within the apply bar of the precision (relative to the
+    largest entry)."""
+    s, off = _multibody_case()
+    assert len(off) == 4
+    ref = oracle_mod.dl_gauss_correction(s.x, s.n, s.w, off)
+    rowptr, col, val = sbq.dl_gauss_correction(_t(s.x), _t(s.n), _t(s.w), off, prec=prec)
+    assert np.array_equal(_np(rowptr), ref.rowptr)
+    assert np.array_equal(_np(col), ref.col)
+    err = np.abs(_np(val) - ref.val).max() / np.abs(ref.val).max()
+    print("gauss correction", prec, err)
+    assert err <= (TOL_F64 if prec == "fp64" else TOL_F32[prec])
+
+
+def test_gauss_correction_operator_and_solve(sbq, oracle_mod):
+    """Operator with the GPU-built correction (FP64) equals the oracle operator with the
+    oracle-built one; GMRES (plain FP64 and compensated-FP32 refinement) converges on the
+    multi-body case and its FP64 residual, recomputed by the oracle, meets the tolerance."""
+    s, off = _multibody_case()
+    E = oracle_mod.dl_gauss_correction(s.x, s.n, s.w, off)
+    eta = sbq.slender_eta(0.2)
+    corr = sbq.dl_gauss_correction(_t(s.x), _t(s.n), _t(s.w), off, prec="fp64")
+    op = sbq.StokesOp(_t(s.x), _t(s.n), _t(s.w), eta, correction=corr)
+    sig = I.density(s.size, seed=31)
+    ref = oracle_mod.matvec(s.x, s.n, s.w, eta, sig, E=E)
+    assert _relerr(_np(op.matvec(_t(sig), prec="fp64")), ref) <= TOL_F64
+    assert _relerr(_np(op.matvec(_t(sig), prec="fp32c")), ref) <= TOL_F32["fp32c"]
+    b = I.density(s.size, seed=32)
+    for inner in ("fp64", "fp32c"):
+        x, rep = op.solve(_t(b), tol=1e-10, restart=100, inner_prec=inner)
+        print("corrected solve", inner, rep["iters"], rep["rel_res"])
+        assert rep["status"] == 0 and rep["iters"] <= 160
+        r = b - oracle_mod.matvec(s.x, s.n, s.w, eta, _np(x), E=E)
+        assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.05e-10
+    op.close()
+
+
+def test_gauss_correction_batched_bodies_equal_separate(sbq):
+    """Per-body row sums from one batched launch (one segment per body) equal the row
+    sums of each body built alone."""
+    segs = [I.capped_arc_pipe(5.0, np.deg2rad(a), 1.0, p, 8, 16, 8)
+            for a, p in ((40.0, 2), (90.0, 3), (150.0, 5))]
+    s = I.concat(segs)
+    off = np.cumsum([0] + [g.size for g in segs])
+    _, _, val = sbq.dl_gauss_correction(_t(s.x), _t(s.n), _t(s.w), off, prec="fp64")
+    v = _np(val).reshape(3, s.size, 3)      # [row component][node][column component]
+    for i, g in enumerate(segs):
+        _, _, vi = sbq.dl_gauss_correction(_t(g.x), _t(g.n), _t(g.w), None, prec="fp64")
+        vi = _np(vi).reshape(3, g.size, 3)
+        a, b = off[i], off[i + 1]
+        assert np.abs(v[:, a:b] - vi).max() <= 1e-12 * np.abs(vi).max()
+
+
+def test_gauss_correction_rejects_bad_offsets(sbq):
+    s = I.sphere(1.0, (0, 0, 0), 6, 8)
+    args = (_t(s.x), _t(s.n), _t(s.w))
+    for off in ([1, s.size], [0, 10, 5, s.size]):
+        with pytest.raises(sbq.SbqError) as ei:
+            sbq.dl_gauss_correction(*args, off, prec="fp64")
+        assert ei.value.status == 1
+
+
+def test_pairsum_kernel_timing(sbq):
+    """The kernel-timing entry point applies the operator like stokes_matvec (same output)
+    and reports a pair-sum kernel time inside the whole apply's time."""
+    c = I.config2(panels=2)
+    s = c["surf"]
+    op = sbq.StokesOp(_t(s.x), _t(s.n), _t(s.w), 1.5)
+    sig = _t(I.density(s.size, seed=41))
+    for prec in ("fp64", "fp32c"):
+        ref = _np(op.matvec(sig, prec=prec))
+        import torch
+        out = torch.empty_like(sig)
+        k, a = op.time_pairsum(sig, prec=prec, reps=3, out=out)
+        assert np.array_equal(_np(out), ref)
+        assert 0.0 < k <= a
+    with pytest.raises(sbq.SbqError):
+        op.time_pairsum(sig, prec="fp32c", reps=0)
+    op.close()

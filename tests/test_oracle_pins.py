@@ -287,3 +287,110 @@ def test_exterior_dirichlet_solve_converges(oracle_mod):
         errs.append(np.abs(u - exact).max() / np.abs(exact).max())
     assert errs[0] < 0.04
     assert 0.4 < errs[1] / errs[0] < 0.6
+
+
+# ---------------------------------------------------------------------------
+# Double-layer singularity subtraction as a sparse correction E (local form of the
+# correction of Eq. nystrom-correction; Gauss-type identity of Eq. stokes-dl)
+# ---------------------------------------------------------------------------
+
+def _corrected_dl(oracle_mod, s, E, sig):
+    """(I/2 + D + E) sigma on the nodes."""
+    y = np.ascontiguousarray(0.5 * sig + oracle_mod.dl(s.x, s.n, s.w, sig, s.x))
+    oracle_mod.csr_apply(E, sig, y.reshape(-1))
+    return y
+
+
+@pytest.mark.parametrize("geom", ["sphere", "torus"])
+def test_gauss_correction_rigid_motions(oracle_mod, geom):
+    """On a closed surface the double layer of a rigid motion v is -v/2 (pv value between
+    -v inside and 0 outside), so I/2 + D annihilates rigid motions.  The corrected sum
+    applies sum_j D_ij (v_j - v_i), and v_j - v_i = w x (y_j - y_i) or 0 is orthogonal to
+    r in D's r (r . q) factor: exact to rounding.  The punctured sum misses it by O(h).
+    A wrong sign of the I/2 term, a missing or mis-signed row sum fails here."""
+    if geom == "sphere":
+        s = I.sphere(1.0, (0.1, 0.2, -0.3), 20, 30)
+        c0 = np.array([0.1, 0.2, -0.3])
+    else:
+        s = I.torus(1.0, 0.25, 16, 8, 32)
+        c0 = np.zeros(3)
+    E = oracle_mod.dl_gauss_correction(s.x, s.n, s.w)
+    om = np.array([0.3, -0.7, 0.5])
+    rot = np.cross(om[:, None], s.x - c0[:, None], axis=0)
+    tr = _rep([0.4, -1.0, 0.8], s.size)
+    for v in (rot, tr):
+        assert np.abs(_corrected_dl(oracle_mod, s, E, v)).max() < 1e-13
+        punct = 0.5 * v + oracle_mod.dl(s.x, s.n, s.w, v, s.x)
+        assert np.abs(punct).max() > 1e-3
+
+
+def test_gauss_correction_normal_field_sphere(oracle_mod):
+    """Double layer of the normal field on a sphere of radius a, worked out by hand: with
+    (x - y) . n_y = -|x - y|^2 / (2a) the integrand reduces to 3 (x - y) / (16 pi a^2 |x - y|);
+    over the sphere (x - y) / |x - y| integrates to (8/3) pi a^2 n_x, so D[n] = n / 2 and
+    (I/2 + D)[n] = n.  The corrected sum converges to it at second order (a factor of
+    about 3.5 per halving of h)."""
+    errs = []
+    for nphi, nth in ((10, 15), (20, 30), (40, 60)):
+        s = I.sphere(1.0, (0.1, 0.2, -0.3), nphi, nth)
+        E = oracle_mod.dl_gauss_correction(s.x, s.n, s.w)
+        errs.append(np.abs(_corrected_dl(oracle_mod, s, E, s.n) - s.n).max())
+    assert errs[1] < 4e-4
+    assert errs[1] / errs[0] < 0.35 and errs[2] / errs[1] < 0.35
+
+
+def test_gauss_correction_is_per_body(oracle_mod):
+    """Row sums run over the node's own closed body only.  Two nested spheres, constant
+    density e on both: on the inner sphere the outer one's double layer is the interior
+    value -e (Gauss identity, spectrally accurate off-surface), on the outer sphere the
+    inner one's is the exterior value 0; the own-body parts vanish exactly.  Row sums over
+    all nodes would give 0 on the inner sphere instead."""
+    so = I.sphere(1.0, (0, 0, 0), 20, 30)
+    si = I.sphere(0.4, (0.1, -0.05, 0.2), 20, 30)
+    s = I.concat([so, si])
+    no = so.size
+    E = oracle_mod.dl_gauss_correction(s.x, s.n, s.w, [0, no, s.size])
+    for comp in range(3):
+        sig = np.zeros((3, s.size))
+        sig[comp] = 1.0
+        y = _corrected_dl(oracle_mod, s, E, sig)
+        assert np.abs(y[:, :no]).max() < 1e-8
+        want = np.zeros((3, s.size - no))
+        want[comp] = -1.0
+        assert np.abs(y[:, no:] - want).max() < 1e-6
+
+
+def test_gauss_correction_layout(oracle_mod):
+    """Three entries per row, the row node's three components in ascending column order."""
+    s = I.capped_straight_pipe(1.0, 4.0, 2, 8, 8, 4)
+    E = oracle_mod.dl_gauss_correction(s.x, s.n, s.w)
+    n = s.size
+    assert E.nrows == 3 * n and E.nnz == 9 * n
+    assert np.array_equal(E.rowptr, 3 * np.arange(3 * n + 1))
+    r = np.arange(3 * n)
+    node = r % n
+    for b in range(3):
+        assert np.array_equal(E.col[3 * r + b], b * n + node)
+
+
+def test_gauss_correction_bounds_gmres_iterations(oracle_mod):
+    """Second-kind behaviour restored: on a capped arc pipe (flat caps meet the wall at a
+    right-angle rim) the punctured double-layer row sums stray far from -1/2 near the rim
+    and GMRES needs more iterations as h shrinks; with the correction the count stays
+    nearly flat.  Exterior Dirichlet data: a point force inside the pipe."""
+    f = np.array([1.0, -0.5, 0.3])
+    ang = np.deg2rad(60.0)
+    its = {}
+    for panels, nth, nr in ((4, 16, 8), (8, 32, 16)):
+        s = I.capped_arc_pipe(5.0, ang, 1.0, panels, 8, nth, nr)
+        x0 = np.array([5.0 * np.cos(ang / 2) + 0.1, 5.0 * np.sin(ang / 2) + 0.2, 0.1])
+        b = _stokeslet_field(s.x, x0, f).reshape(-1)
+        E = oracle_mod.dl_gauss_correction(s.x, s.n, s.w)
+        for name, EE in (("punctured", None), ("corrected", E)):
+            x, info = oracle_mod.gmres(
+                lambda v: oracle_mod.matvec(s.x, s.n, s.w, 1.0, v.reshape(3, -1), E=EE).reshape(-1),
+                b, tol=1e-10, restart=200, max_iter=1000)
+            assert info["rel_res"] <= 1e-10
+            its[(name, s.size)] = info["iters"]
+    assert its[("corrected", 3072)] <= 60 and its[("corrected", 768)] <= 50
+    assert its[("punctured", 3072)] > 2 * its[("corrected", 3072)]
