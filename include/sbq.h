@@ -99,7 +99,9 @@ typedef struct {
     int graph_used;           /* 1 if the Arnoldi steps ran inside a CUDA graph */
     int kernel_launches;      /* kernels of this library executed by the solve (graph
                                  replays included) */
-    double rel_res;           /* final FP64 true relative residual ||b - K x|| / ||b|| */
+    double rel_res;           /* final FP64 true relative residual ||b - K x|| / ||b||; for an
+                                 operator with a batch plan, the largest of the segments'
+                                 ratios (each segment is solved to tol on its own norm) */
     int n_hist;               /* entries used in rel_res_hist */
     double rel_res_hist[SBQ_HIST]; /* FP64 true relative residual after each refinement
                                       step / restart cycle, starting with x0 */
