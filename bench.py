@@ -53,6 +53,10 @@ def parse():
                     help="CPU work bound of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-reps", type=int, default=20)
+    ap.add_argument("--resid-prec", default="df32", choices=["fp64", "df32"],
+                    help="precision of the refinement residuals b - K x of the timed solve "
+                         "(df32: double-float, FP64-class; the returned x is checked with an "
+                         "FP64 residual after the timed region either way)")
     ap.add_argument("--no-correction", action="store_true",
                     help="solve with the punctured sums alone (no double-layer singularity "
                          "subtraction)")
@@ -257,7 +261,8 @@ def run_gpu(args):
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t_setup) * 1e3
     opts = dict(tol=1e-10, restart=100, inner_prec="fp32c", inner_tol=1e-5, max_outer=30,
-                use_graph=not args.no_graph)
+                use_graph=not args.no_graph, resid_prec=args.resid_prec)
+    op.autotune(args.resid_prec)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     for _ in range(args.warmup):
@@ -297,6 +302,24 @@ def run_gpu(args):
     for r in reps:
         if r["status"] != 0 or r["rel_res"] > 1e-10:
             raise RuntimeError("a timed solve missed the tolerance: %s" % r)
+    # the returned x, checked with an FP64 residual (outside the timed region)
+    kx = op.matvec(x, prec="fp64")
+    fp64_check = float((rhs - kx).norm() / rhs.norm())
+    if fp64_check > 1e-10:
+        raise RuntimeError("FP64 residual of the timed solve's x is %.3e" % fp64_check)
+    # the other residual precision, same inner solve (for comparison)
+    other = "fp64" if args.resid_prec == "df32" else "df32"
+    oth_times = []
+    for k in range(3):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xo, repo = op.solve(rhs, **dict(opts, resid_prec=other))
+        e1.record(stream)
+        e1.synchronize()
+        oth_times.append(e0.elapsed_time(e1))
+    oth_ms = float(np.min(oth_times[1:]))
     pairs_step = float(rep["matvecs_fp64"] + rep["matvecs_low"]) * n * n
     value = world * pairs_step / (ms * 1e-3)
     kpm32 = op.stats("fp32c")["kernels_per_matvec"]
@@ -337,6 +360,7 @@ def run_gpu(args):
 
     kk32c, k32c = time_matvec("fp32c", args.kernel_reps)
     kk32, k32 = time_matvec("fp32", args.kernel_reps)
+    kkdf, kdf = time_matvec("df32", max(3, args.kernel_reps // 2))
     kk64, k64 = time_matvec("fp64", max(3, args.kernel_reps // 4))
     info = sbq.device_info()
     sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
@@ -369,7 +393,8 @@ def run_gpu(args):
         t0 = time.perf_counter()
         xh, reph = sbq.solve_from_host(hsrc, hnrm, hw, hrhs, eta, tol=1e-10, inner_prec="fp32c",
                                        restart=100, inner_tol=1e-5, max_outer=30, device=dev,
-                                       correction=None if args.no_correction else "fp64")
+                                       correction=None if args.no_correction else "fp64",
+                                       resid_prec=args.resid_prec)
         torch.cuda.synchronize()
         if k > 0:
             e2e_times.append(time.perf_counter() - t0)
@@ -391,8 +416,10 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "nodes": n, "unknowns": 3 * n, "eta": eta,
-                       "tol": 1e-10, "inner": "fp32 compensated, FP64 refinement",
+                       "tol": 1e-10, "inner": "fp32 compensated GMRES inside iterative refinement",
                        "restart": 100, "graph": not args.no_graph,
+                       "resid": args.resid_prec + (" (double-float, FP64-class)"
+                                                   if args.resid_prec == "df32" else ""),
                        "correction": "none" if args.no_correction else
                        "double-layer singularity subtraction, built in FP64 on the GPU",
                        "l2": "flushed between steps (256 MiB write, outside the timed intervals)",
@@ -402,10 +429,16 @@ def run_gpu(args):
                       "mixed_matvecs_fp32c": rep["matvecs_low"],
                       "mixed_matvecs_fp64": rep["matvecs_fp64"], "mixed_rel_res": rep["rel_res"],
                       "fp64_iters": rep64["iters"], "fp64_rel_res": rep64["rel_res"],
-                      "x_rel_diff_mixed_vs_fp64": xdiff},
+                      "x_rel_diff_mixed_vs_fp64": xdiff,
+                      "mixed_x_fp64_rel_res": fp64_check,
+                      "mixed_ms_with_%s_residuals" % other: oth_ms,
+                      "mixed_iters_with_%s_residuals" % other: repo["iters"]},
             "kernels": {"fp32c_matvec_ms": k32c, "fp32_matvec_ms": k32, "fp64_matvec_ms": k64,
                         "fp32c_pairsum_kernel_ms": kk32c, "fp32_pairsum_kernel_ms": kk32,
-                        "fp64_pairsum_kernel_ms": kk64,
+                        "fp64_pairsum_kernel_ms": kk64, "df32_matvec_ms": kdf,
+                        "df32_pairsum_kernel_ms": kkdf,
+                        "df32_pairs_per_s": n * n / (kkdf * 1e-3),
+                        "tune_df32": op.tune("df32"),
                         "fp32c_pairs_per_s": n * n / (k32c * 1e-3),
                         "fp32_pairs_per_s": n * n / (k32 * 1e-3),
                         "fp64_pairs_per_s": n * n / (k64 * 1e-3),

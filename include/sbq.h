@@ -62,14 +62,17 @@ typedef enum {
 typedef enum {
     SBQ_FP64 = 0,         /* FP64 pair arithmetic and accumulation */
     SBQ_FP32 = 1,         /* FP32 pair arithmetic, plain FP32 accumulation per work item */
-    SBQ_FP32_COMP = 2     /* FP32 pair arithmetic, TwoSum-compensated (hi, lo) accumulation */
+    SBQ_FP32_COMP = 2,    /* FP32 pair arithmetic, TwoSum-compensated (hi, lo) accumulation */
+    SBQ_DF32 = 3          /* double-float: every value an unevaluated sum of two FP32 numbers,
+                             error-free transformations throughout; about 1e-13 of the largest
+                             term (FP64: 1e-15) at several times the FP64 pair rate */
 } sbq_prec;
 
 /* Tile shape of the pair-sum kernels.  targets per CTA = 32 * warps * r. */
 typedef struct {
     int r;             /* targets per thread held in registers */
     int warps;         /* warps per CTA.  (r, warps): FP32 (2,4) (4,4) (8,4) (4,8) (4,2) (8,2);
-                          FP64 (1,4) (2,4) */
+                          FP64 (1,4) (2,4); DF32 (1,4) (2,4) (4,4) (2,8) */
     int chunk_tiles;   /* source tiles per work item; 0 = chosen from the SM count */
 } sbq_tune;
 
@@ -80,13 +83,16 @@ typedef struct {
     double tol;        /* stop when ||b - K x||_2 <= tol * ||b||_2 (FP64 true residual) */
     int restart;       /* Krylov vectors per cycle m, 1..256 */
     int max_iter;      /* cap on Arnoldi steps (summed over cycles and refinement steps) */
-    int inner_prec;    /* SBQ_FP64: plain FP64 GMRES.  SBQ_FP32 / SBQ_FP32_COMP: the inner
-                          GMRES applies K in that precision and an FP64 residual
-                          b - K x refines x (iterative refinement) */
+    int inner_prec;    /* SBQ_FP64 / SBQ_DF32: plain GMRES with K applied in that precision.
+                          SBQ_FP32 / SBQ_FP32_COMP: the inner GMRES applies K in that
+                          precision and a residual b - K x in resid_prec refines x
+                          (iterative refinement) */
     double inner_tol;  /* relative tolerance of each inner solve (refinement only) */
     int max_outer;     /* cap on refinement steps */
     int use_graph;     /* 1: each Arnoldi step runs inside one CUDA graph whose while
                           node repeats it on the device until the cycle ends */
+    int resid_prec;    /* refinement only: SBQ_FP64 (0, default) or SBQ_DF32, the precision of
+                          the residuals b - K x that decide convergence */
 } sbq_gmres_opts;
 
 #define SBQ_HIST 64
@@ -94,7 +100,8 @@ typedef struct {
     int status;               /* sbq_status of the solve */
     int iters;                /* Arnoldi steps in total */
     int outer_iters;          /* refinement steps (mixed) or restart cycles (FP64) */
-    int matvecs_fp64;         /* FP64 operator applications */
+    int matvecs_fp64;         /* operator applications in the high precision (SBQ_FP64 or
+                                 SBQ_DF32: the plain solve's precision or resid_prec) */
     int matvecs_low;          /* FP32 / compensated-FP32 operator applications */
     int graph_used;           /* 1 if the Arnoldi steps ran inside a CUDA graph */
     int kernel_launches;      /* kernels of this library executed by the solve (graph

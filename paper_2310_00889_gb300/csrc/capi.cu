@@ -16,7 +16,10 @@ using namespace sbq;
 
 namespace {
 
-bool prec_ok(int prec) { return prec == SBQ_FP64 || prec == SBQ_FP32 || prec == SBQ_FP32_COMP; }
+bool prec_ok(int prec)
+{
+    return prec == SBQ_FP64 || prec == SBQ_FP32 || prec == SBQ_FP32_COMP || prec == SBQ_DF32;
+}
 
 int fail(int code, const std::string &msg)
 {
@@ -54,7 +57,7 @@ int apply_generic(int64_t ns, const double *src, const double *nrm, const double
     int kind;
     double scale, kappa;
     kind_and_scale(alpha, beta, &kind, &scale, &kappa);
-    const int layout = (prec == SBQ_FP64) ? SBQ_FP64 : SBQ_FP32;
+    const int layout = (prec == SBQ_FP64 || prec == SBQ_DF32) ? prec : SBQ_FP32;
     AsyncAllocScope scope(s);
     SrcPack sp;
     TrgSet ts;
@@ -238,6 +241,9 @@ SBQ_API int stokes_op_create(int64_t n, const double *src, const double *nrm, co
     if ((st = build_src_pack(op->sp64, SBQ_FP64, op->plan.src_off, op->src.as<double>(),
                              op->nrm.as<double>(), nscale, n, s)) != SBQ_OK)
         return bail(st);
+    if ((st = build_src_pack(op->spdf, SBQ_DF32, op->plan.src_off, op->src.as<double>(),
+                             op->nrm.as<double>(), nscale, n, s)) != SBQ_OK)
+        return bail(st);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return bail(cuda_status(e, "stokes_op_create"));
     *op_out = op;
@@ -326,8 +332,11 @@ SBQ_API int gmres_solve(const void *oph, const double *rhs, double *x, const sbq
     if (!(o->tol > 0.0) || o->restart < 1 || o->restart > 256 || o->max_iter < 1 ||
         !prec_ok(o->inner_prec))
         return fail(SBQ_EINVAL, "bad GMRES options (tol > 0, 1 <= restart <= 256, max_iter >= 1)");
-    if (o->inner_prec != SBQ_FP64 && (!(o->inner_tol > 0.0) || o->inner_tol >= 1.0 || o->max_outer < 1))
+    const bool mixed = (o->inner_prec == SBQ_FP32 || o->inner_prec == SBQ_FP32_COMP);
+    if (mixed && (!(o->inner_tol > 0.0) || o->inner_tol >= 1.0 || o->max_outer < 1))
         return fail(SBQ_EINVAL, "bad refinement options (0 < inner_tol < 1, max_outer >= 1)");
+    if (mixed && o->resid_prec != SBQ_FP64 && o->resid_prec != SBQ_DF32)
+        return fail(SBQ_EINVAL, "resid_prec must be SBQ_FP64 or SBQ_DF32");
     sbq_gmres_report local{};
     sbq_gmres_report &r = rep ? *rep : local;
     if (op->n == 0) {

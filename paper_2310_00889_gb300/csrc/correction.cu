@@ -58,7 +58,7 @@ int dl_gauss_correction(int nbody, const int64_t *body_off, const double *src, c
     int kind;
     double scale, kappa;
     kind_and_scale(0.0, 1.0, &kind, &scale, &kappa);
-    const int layout = (prec == SBQ_FP64) ? SBQ_FP64 : SBQ_FP32;
+    const int layout = (prec == SBQ_FP64 || prec == SBQ_DF32) ? prec : SBQ_FP32;
     AsyncAllocScope scope(s);
     const std::vector<int64_t> off(body_off, body_off + nbody + 1);
     SrcPack sp;

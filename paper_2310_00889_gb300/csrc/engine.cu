@@ -151,7 +151,7 @@ void kind_and_scale(double alpha, double beta, int *kind, double *scale, double 
 sbq_tune default_tune(int prec, long long nt)
 {
     sbq_tune t{};
-    if (prec == SBQ_FP64) {
+    if (prec == SBQ_FP64 || prec == SBQ_DF32) {
         t.r = 2;
         t.warps = 4;
     } else {
@@ -169,7 +169,7 @@ int build_src_pack(SrcPack &sp, int layout, const std::vector<int64_t> &src_off,
                    const double *nrm, double nscale, long long ns, cudaStream_t s)
 {
     sp.layout = layout;
-    sp.TS = (layout == SBQ_FP64) ? TS_F64 : TS_F32;
+    sp.TS = (layout == SBQ_FP64) ? TS_F64 : (layout == SBQ_DF32) ? TS_DF : TS_F32;
     const int nseg = static_cast<int>(src_off.size()) - 1;
     std::vector<TileInfo> h;
     sp.seg_tile_begin.assign(nseg, 0);
@@ -193,8 +193,9 @@ int build_src_pack(SrcPack &sp, int layout, const std::vector<int64_t> &src_off,
         return SBQ_EINVAL;
     }
     SBQ_TRY(sp.stiles.alloc(h.size() * sizeof(TileInfo)));
-    const size_t per_tile = (layout == SBQ_FP64) ? 9 * TS_F64 * sizeof(double)
-                                                 : F32_TILE_F4 * sizeof(float4);
+    const size_t per_tile = (layout == SBQ_FP64)   ? 9 * TS_F64 * sizeof(double)
+                            : (layout == SBQ_DF32) ? DF_TILE_F4 * sizeof(float4)
+                                                   : F32_TILE_F4 * sizeof(float4);
     SBQ_TRY(sp.spack.alloc(h.size() * per_tile));
     if (!h.empty()) {
         SBQ_CUDA(cudaMemcpyAsync(sp.stiles.p, h.data(), h.size() * sizeof(TileInfo),
@@ -318,7 +319,7 @@ int build_trg_set(TrgSet &ts, int kind, int prec, const sbq_tune &tune, const Sr
         SBQ_TRY(ts.tpack.alloc(ht.size() * static_cast<size_t>(TT) * sizeof(float4)));
     else
         ts.tpack.release();
-    if (prec == SBQ_FP32_COMP)
+    if (prec == SBQ_FP32_COMP || prec == SBQ_DF32)
         SBQ_TRY(ts.tpack_lo.alloc(ht.size() * static_cast<size_t>(TT) * sizeof(float4)));
     else
         ts.tpack_lo.release();
@@ -382,7 +383,8 @@ int run_pairsum(int kind, int prec, const SrcPack &sp, const TrgSet &ts, const d
     if (prec != SBQ_FP64)
         SBQ_CUDA(launch_reduce_partials_f32(ts.ttiles.as<TileInfo>(), ts.n_ttiles, ts.TT,
                                             ts.partial.p, nt, out, scale, diag, diag_sigma,
-                                            prec == SBQ_FP32_COMP ? 1 : 0, s));
+                                            prec == SBQ_FP32_COMP ? 1 : (prec == SBQ_DF32 ? 2 : 0),
+                                            s));
     else if (ts.needs_reduce)
         SBQ_CUDA(launch_reduce_partials(ts.ttiles.as<TileInfo>(), ts.n_ttiles, ts.TT,
                                         ts.partial.as<double>(), nt, out, scale, diag, diag_sigma,
@@ -395,7 +397,7 @@ int run_pairsum(int kind, int prec, const SrcPack &sp, const TrgSet &ts, const d
 // ---------------------------------------------------------------------------
 static const SrcPack &op_srcpack(const Op *op, int prec)
 {
-    return prec == SBQ_FP64 ? op->sp64 : op->sp32;
+    return prec == SBQ_FP64 ? op->sp64 : (prec == SBQ_DF32 ? op->spdf : op->sp32);
 }
 
 int op_kernels_per_matvec(const Op *op, int prec)
@@ -450,6 +452,8 @@ static int autotune_op(Op *op, int prec, cudaStream_t s)
     std::vector<sbq_tune> shapes;
     if (prec == SBQ_FP64) {
         shapes = {{2, 4, 0}, {1, 4, 0}};
+    } else if (prec == SBQ_DF32) {
+        shapes = {{2, 4, 0}, {1, 4, 0}, {4, 4, 0}, {2, 8, 0}};
     } else {
         shapes = {{2, 4, 0}, {4, 2, 0}, {4, 4, 0}, {8, 2, 0}, {8, 4, 0}, {4, 8, 0}};
     }

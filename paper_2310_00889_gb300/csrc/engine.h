@@ -43,9 +43,10 @@ struct PlanH {
     sbq_tune tune{};
 };
 
-// Source tiles of one precision layout (FP32: TS_F32 float4 x3; FP64: TS_F64 doubles x9).
+// Source tiles of one precision layout (FP32: packed pairs, FP64: TS_F64 doubles x9,
+// double-float: TS_DF records of five float4).
 struct SrcPack {
-    int layout = -1;            // SBQ_FP32 (shared by FP32 and FP32_COMP) or SBQ_FP64
+    int layout = -1;            // SBQ_FP32 (shared by FP32 and FP32_COMP), SBQ_FP64 or SBQ_DF32
     int TS = 0;
     int n_stiles = 0;
     std::vector<int> seg_tile_begin, seg_tile_count;
@@ -73,9 +74,9 @@ struct Op {
     DevBuf src, nrm, w;                // library copies (SoA)
     DevBuf rowptr, col, val;           // CSR correction
     PlanH plan;                        // segments (one segment if none given)
-    SrcPack sp32, sp64;
-    std::unique_ptr<TrgSet> ts[3];     // per sbq_prec
-    bool tuned[3] = {false, false, false};
+    SrcPack sp32, sp64, spdf;          // FP32 (plain and compensated), FP64, double-float
+    std::unique_ptr<TrgSet> ts[4];     // per sbq_prec
+    bool tuned[4] = {false, false, false, false};
     std::mutex mu;
     struct GmresWS *gm = nullptr;      // solver workspace (gmres.cu)
     ~Op();

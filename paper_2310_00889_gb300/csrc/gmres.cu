@@ -78,9 +78,9 @@ struct GmresWS {
     SegState *hseg = nullptr;
     double *htol = nullptr;
     cudaStream_t cap = nullptr;        // capture stream
-    cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
-    cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
-    bool graph_tried[3] = {false, false, false};
+    cudaGraph_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaGraphExec_t exec[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool graph_tried[4] = {false, false, false, false};
     long long launches = 0;            // kernels executed by the current solve
 };
 
@@ -88,7 +88,7 @@ int gmres_destroy(GmresWS *ws)
 {
     if (!ws)
         return SBQ_OK;
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 4; ++i) {
         if (ws->exec[i])
             cudaGraphExecDestroy(ws->exec[i]);
         if (ws->graph[i])
@@ -830,6 +830,8 @@ int gmres_solve_impl(Op *op, const double *b, double *x, const sbq_gmres_opts &o
     rep = sbq_gmres_report{};
     const int low = o.inner_prec;
     const bool mixed = (low == SBQ_FP32 || low == SBQ_FP32_COMP);
+    // the precision of the residuals that decide convergence (and of the plain solve)
+    const int hp = mixed ? o.resid_prec : low;
     SBQ_TRY(ws_ensure(op, o.restart));
     GmresWS *ws = op->gm;
     ws->launches = 0;
@@ -839,7 +841,7 @@ int gmres_solve_impl(Op *op, const double *b, double *x, const sbq_gmres_opts &o
         set_error("cannot allocate the device error word");
         return SBQ_ENOMEM;
     }
-    SBQ_TRY(op_ensure_tuned(op, SBQ_FP64, s));
+    SBQ_TRY(op_ensure_tuned(op, hp, s));
     if (mixed)
         SBQ_TRY(op_ensure_tuned(op, low, s));
 
@@ -876,7 +878,7 @@ int gmres_solve_impl(Op *op, const double *b, double *x, const sbq_gmres_opts &o
         SBQ_CUDA(cudaMemcpyAsync(ws->r.p, b, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
         SBQ_TRY(norm_to_state(ws, ws->r.as<double>(), s));
     } else {
-        SBQ_TRY(residual(op, ws, SBQ_FP64, b, x, ws->r.as<double>(), s));
+        SBQ_TRY(residual(op, ws, hp, b, x, ws->r.as<double>(), s));
         rep.matvecs_fp64 += 1;
     }
     copy_res(ws, res);
@@ -898,7 +900,7 @@ int gmres_solve_impl(Op *op, const double *b, double *x, const sbq_gmres_opts &o
             const int m = std::min(o.restart, o.max_iter - rep.iters);
             for (int i = 0; i < nseg; ++i)
                 tol_abs[i] = o.tol * bnorm[i];
-            SBQ_TRY(run_cycle(op, ws, SBQ_FP64, ws->r.as<double>(), x, m, tol_abs,
+            SBQ_TRY(run_cycle(op, ws, hp, ws->r.as<double>(), x, m, tol_abs,
                               o.use_graph != 0, s, &graph_used));
             const int steps = ws->hst->j;
             rep.iters += steps;
@@ -911,7 +913,7 @@ int gmres_solve_impl(Op *op, const double *b, double *x, const sbq_gmres_opts &o
                 set_error("non-finite value in the Arnoldi process");
                 break;
             }
-            SBQ_TRY(residual(op, ws, SBQ_FP64, b, x, ws->r.as<double>(), s));
+            SBQ_TRY(residual(op, ws, hp, b, x, ws->r.as<double>(), s));
             rep.matvecs_fp64 += 1;
             rep.outer_iters += 1;
             copy_res(ws, res);
@@ -979,7 +981,7 @@ int gmres_solve_impl(Op *op, const double *b, double *x, const sbq_gmres_opts &o
             k_add<<<vec_grid(N), GB, 0, s>>>(d, x, N);
             SBQ_CUDA(cudaGetLastError());
             ws->launches += 1;
-            SBQ_TRY(residual(op, ws, SBQ_FP64, b, x, ws->r.as<double>(), s));
+            SBQ_TRY(residual(op, ws, hp, b, x, ws->r.as<double>(), s));
             rep.matvecs_fp64 += 1;
             rep.outer_iters += 1;
             copy_res(ws, res);

@@ -212,6 +212,84 @@ __global__ void pack_src_q_f64(const double *__restrict__ w, const double *__res
     tile[5 * TS + j] = qz;
 }
 
+// Double-float source tiles (record layout in pairsum_df.cuh): float index of field f of
+// source j.  Fields: 0 xh 1 yh 2 zh 3 qxh 4 qyh 5 qzh 6 nxh 7 nyh 8 nzh 9 xl 10 yl 11 zl
+// 12 qxl 13 qyl 14 qzl 15 nxl 16 nyl 17 nzl (18, 19 unused).
+__device__ __forceinline__ int df_slot(int f, int j) { return 20 * j + f; }
+
+__device__ __forceinline__ void split_df(double v, float &h, float &l)
+{
+    h = static_cast<float>(v);
+    l = static_cast<float>(v - static_cast<double>(h));
+}
+
+__global__ void pack_src_geom_df(const double *__restrict__ src, const double *__restrict__ nrm,
+                                 double nscale, long long ns, TileInfo *stiles, float4 *spack)
+{
+    constexpr int TS = TS_DF;
+    __shared__ double red[32];
+    __shared__ double bb[6][32];
+    const int k = blockIdx.x, j = threadIdx.x;
+    const long long begin = stiles[k].begin;
+    const int count = stiles[k].count;
+    double cx, cy, cz;
+    tile_centre(src, ns, begin, count, TS, bb, cx, cy, cz);
+    float *tile = reinterpret_cast<float *>(spack + static_cast<size_t>(k) * DF_TILE_F4);
+    double d2 = 0.0;
+    float v[20];
+    for (int f = 0; f < 20; ++f)
+        v[f] = 0.0f;
+    if (j < count) {
+        const long long s = begin + j;
+        const double dx = src[s] - cx, dy = src[ns + s] - cy, dz = src[2 * ns + s] - cz;
+        split_df(dx, v[0], v[9]);
+        split_df(dy, v[1], v[10]);
+        split_df(dz, v[2], v[11]);
+        if (nrm) {
+            split_df(nscale * nrm[s], v[6], v[15]);
+            split_df(nscale * nrm[ns + s], v[7], v[16]);
+            split_df(nscale * nrm[2 * ns + s], v[8], v[17]);
+        }
+        d2 = dx * dx + dy * dy + dz * dz;
+    } else {
+        v[0] = v[1] = v[2] = PAD_POS_F32;
+    }
+    for (int f = 0; f < 20; ++f)
+        if (f < 3 || f > 5)
+            if (f < 12 || f > 14)
+                tile[df_slot(f, j)] = v[f];
+    const double m = block_max(d2, red);
+    if (j == 0) {
+        stiles[k].cx = cx;
+        stiles[k].cy = cy;
+        stiles[k].cz = cz;
+        stiles[k].rad = radius_up(m);
+    }
+}
+
+__global__ void pack_src_q_df(const double *__restrict__ w, const double *__restrict__ sigma,
+                              long long ns, const TileInfo *__restrict__ stiles, float4 *spack,
+                              int *counter)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0 && counter)
+        *counter = 0;
+    const int k = blockIdx.x, j = threadIdx.x;
+    const long long begin = stiles[k].begin;
+    const int count = stiles[k].count;
+    float qh[3] = {0.0f, 0.0f, 0.0f}, ql[3] = {0.0f, 0.0f, 0.0f};
+    if (j < count) {
+        const long long s = begin + j;
+        const double ww = w[s];
+        for (int c = 0; c < 3; ++c)
+            split_df(ww * sigma[c * ns + s], qh[c], ql[c]);
+    }
+    float *tile = reinterpret_cast<float *>(spack + static_cast<size_t>(k) * DF_TILE_F4);
+    for (int c = 0; c < 3; ++c) {
+        tile[df_slot(3 + c, j)] = qh[c];
+        tile[df_slot(12 + c, j)] = ql[c];
+    }
+}
+
 __global__ void pack_trg_f32(const double *__restrict__ trg, long long nt, TileInfo *ttiles, int TT,
                              float4 *tpack, float4 *tpack_lo)
 {
@@ -270,8 +348,9 @@ __global__ void reduce_partials_kernel(const TileInfo *__restrict__ ttiles, int 
 }
 
 // FP32 partials: (hi, lo) float pairs per (slot, component, target).  Compensated sums
-// are merged across slots with TwoSum in FP32, plain ones with FP32 adds; the FP64 result
-// gets the prefactor and the diagonal term.  Block (tile, component); four slot loads in
+// (comp 1) are merged across slots with TwoSum in FP32, plain ones (comp 0) with FP32 adds,
+// double-float ones (comp 2) in FP64; the FP64 result gets the prefactor and the diagonal
+// term.  Block (tile, component); four slot loads in
 // flight per thread.
 __device__ __forceinline__ void merge_partial(float &hi, float &lo, float2 v, int comp)
 {
@@ -297,6 +376,19 @@ __global__ void reduce_partials_f32_kernel(const TileInfo *__restrict__ ttiles, 
         const long long t = ti.begin + loc;
         const float2 *pp = partial + (static_cast<size_t>(ti.slot_begin) * 3 + c) * TT + loc;
         const size_t qs = static_cast<size_t>(3) * TT;   // stride between slots
+        if (comp == 2) {
+            // double-float partials: each slot's (hi, lo) is exact in FP64; add in FP64
+            double acc = 0.0;
+            for (int q = 0; q < nq; ++q) {
+                const float2 v = pp[q * qs];
+                acc += static_cast<double>(v.x) + static_cast<double>(v.y);
+            }
+            double o = scale * acc;
+            if (diag_sigma)
+                o += diag * diag_sigma[c * nt + t];
+            out[c * nt + t] = o;
+            continue;
+        }
         float hi = 0.0f, lo = 0.0f;
         int q = 0;
         for (; q + 4 <= nq; q += 4) {
@@ -340,6 +432,9 @@ cudaError_t launch_pack_src_geom(int prec, const double *src, const double *nrm,
     if (prec == SBQ_FP64)
         pack_src_geom_f64<<<n_stiles, TS_F64, 0, s>>>(src, nrm, nscale, ns, stiles,
                                                        static_cast<double *>(spack));
+    else if (prec == SBQ_DF32)
+        pack_src_geom_df<<<n_stiles, TS_DF, 0, s>>>(src, nrm, nscale, ns, stiles,
+                                                     static_cast<float4 *>(spack));
     else
         pack_src_geom_f32<<<n_stiles, TS_F32, 0, s>>>(src, nrm, nscale, ns, stiles,
                                                        static_cast<float4 *>(spack));
@@ -355,6 +450,9 @@ cudaError_t launch_pack_src_q(int prec, const double *w, const double *sigma, lo
     if (prec == SBQ_FP64)
         pack_src_q_f64<<<n_stiles, TS_F64, 0, s>>>(w, sigma, ns, stiles,
                                                     static_cast<double *>(spack), counter);
+    else if (prec == SBQ_DF32)
+        pack_src_q_df<<<n_stiles, TS_DF, 0, s>>>(w, sigma, ns, stiles,
+                                                  static_cast<float4 *>(spack), counter);
     else
         pack_src_q_f32<<<n_stiles, TS_F32, 0, s>>>(w, sigma, ns, stiles,
                                                     static_cast<float4 *>(spack), counter);
@@ -438,6 +536,8 @@ bool pairsum_shape_supported(int prec, int R, int W)
 {
     if (prec == SBQ_FP64)
         return W == 4 && (R == 1 || R == 2);
+    if (prec == SBQ_DF32)
+        return (W == 4 && (R == 1 || R == 2 || R == 4)) || (W == 8 && R == 2);
     return (W == 4 && (R == 2 || R == 4 || R == 8)) || (W == 8 && R == 4) ||
            (W == 2 && (R == 4 || R == 8));
 }
@@ -446,6 +546,8 @@ size_t pairsum_smem_bytes(int prec)
 {
     if (prec == SBQ_FP64)
         return 2 * 9 * TS_F64 * sizeof(double);
+    if (prec == SBQ_DF32)
+        return 2 * DF_TILE_F4 * sizeof(float4);
     return 2 * F32_TILE_F4 * sizeof(float4);
 }
 

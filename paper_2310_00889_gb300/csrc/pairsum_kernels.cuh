@@ -588,6 +588,12 @@ __global__ void __launch_bounds__(W * 32) pairsum_f64_kernel(const PairsumParams
     }
 }
 
+}  // namespace sbq
+
+#include "pairsum_df.cuh"
+
+namespace sbq {
+
 // ---------------------------------------------------------------------------
 // Launch table for one kind
 // ---------------------------------------------------------------------------
@@ -606,6 +612,20 @@ struct KindLauncher {
         const size_t smem = 2 * 9 * TS_F64 * sizeof(double);
         pairsum_f64_kernel<KIND, R, W><<<grid, W * 32, smem, s>>>(p);
         return cudaGetLastError();
+    }
+    template <int R, int W>
+    static cudaError_t df(int grid, const PairsumParams &p, cudaStream_t s)
+    {
+        pairsum_df_kernel<KIND, R, W><<<grid, W * 32, pairsum_smem_bytes(SBQ_DF32), s>>>(p);
+        return cudaGetLastError();
+    }
+    template <int R, int W>
+    static int occdf()
+    {
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pairsum_df_kernel<KIND, R, W>, W * 32,
+                                                      pairsum_smem_bytes(SBQ_DF32));
+        return b;
     }
     template <int R, int W, bool COMP>
     static int occ32()
@@ -626,9 +646,10 @@ struct KindLauncher {
     }
 
 // Supported tile shapes.  FP32: (R, W) in {(2,4), (4,4), (8,4), (4,8), (4,2), (8,2)};
-// FP64: (1,4), (2,4).
+// FP64: (1,4), (2,4); double-float: (1,4), (2,4), (4,4), (2,8).
 #define SBQ_F32_SHAPES(X) X(2, 4) X(4, 4) X(8, 4) X(4, 8) X(4, 2) X(8, 2)
 #define SBQ_F64_SHAPES(X) X(1, 4) X(2, 4)
+#define SBQ_DF_SHAPES(X) X(1, 4) X(2, 4) X(4, 4) X(2, 8)
 
     static cudaError_t launch(int prec, int R, int W, int grid, const PairsumParams &p, cudaStream_t s)
     {
@@ -636,6 +657,11 @@ struct KindLauncher {
 #define X(r, w) \
     if (R == r && W == w) return f64<r, w>(grid, p, s);
             SBQ_F64_SHAPES(X)
+#undef X
+        } else if (prec == SBQ_DF32) {
+#define X(r, w) \
+    if (R == r && W == w) return df<r, w>(grid, p, s);
+            SBQ_DF_SHAPES(X)
 #undef X
         } else {
             const bool comp = (prec == SBQ_FP32_COMP);
@@ -653,6 +679,11 @@ struct KindLauncher {
 #define X(r, w) \
     if (R == r && W == w) return occ64<r, w>();
             SBQ_F64_SHAPES(X)
+#undef X
+        } else if (prec == SBQ_DF32) {
+#define X(r, w) \
+    if (R == r && W == w) return occdf<r, w>();
+            SBQ_DF_SHAPES(X)
 #undef X
         } else {
             const bool comp = (prec == SBQ_FP32_COMP);

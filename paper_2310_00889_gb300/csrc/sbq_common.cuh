@@ -35,6 +35,13 @@ __host__ __device__ constexpr int f32_slot(int f, int j)
     return ((f >> 1) * (TS_F32 / 2) + (j >> 1)) * 4 + (f & 1) * 2 + (j & 1);
 }
 constexpr int TS_F64 = 128;
+// Double-float tiles: TS_DF sources, five float4 per source (layout in pairsum_df.cuh).
+constexpr int TS_DF = 128;
+constexpr int DF_TILE_F4 = 5 * TS_DF;
+// Double-float path: pairs closer than this fraction of the sum of their tile radii are
+// coincident.  Centring in double-float leaves a coincident pair a few 2^-48 of that sum
+// apart; distinct nodes of any admissible discretisation are orders of magnitude farther.
+constexpr double DF_COINCIDENT_REL = 1.0e-10;
 // Compensated FP32: plain FP32 sums over runs of this many sources are merged into
 // the (hi, lo) pair with TwoSum.
 constexpr int COMP_RUN = 64;

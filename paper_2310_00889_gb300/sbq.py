@@ -18,9 +18,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libsbq.so")
 
 OK, EINVAL, ECUDA, ENOCONV, EBREAKDOWN, ENONFINITE, ETIMEOUT, ENOMEM = range(8)
-FP64, FP32, FP32_COMP = 0, 1, 2
-_PREC = {"fp64": FP64, "fp32": FP32, "fp32c": FP32_COMP, "fp32_comp": FP32_COMP,
-         FP64: FP64, FP32: FP32, FP32_COMP: FP32_COMP}
+FP64, FP32, FP32_COMP, DF32 = 0, 1, 2, 3
+_PREC = {"fp64": FP64, "fp32": FP32, "fp32c": FP32_COMP, "fp32_comp": FP32_COMP, "df32": DF32,
+         FP64: FP64, FP32: FP32, FP32_COMP: FP32_COMP, DF32: DF32}
 _STATUS = {0: "SBQ_OK", 1: "SBQ_EINVAL", 2: "SBQ_ECUDA", 3: "SBQ_ENOCONV", 4: "SBQ_EBREAKDOWN",
            5: "SBQ_ENONFINITE", 6: "SBQ_ETIMEOUT", 7: "SBQ_ENOMEM"}
 
@@ -41,7 +41,8 @@ class Tune(ctypes.Structure):
 class GmresOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("inner_prec", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("max_outer", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("max_outer", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("resid_prec", ctypes.c_int)]
 
 
 SBQ_HIST = 64
@@ -304,13 +305,15 @@ class StokesOp:
         return out
 
     def solve(self, rhs, x0=None, tol=1e-10, restart=100, max_iter=2000, inner_prec="fp64",
-              inner_tol=1e-5, max_outer=30, use_graph=True, stream=None):
-        """GMRES for K x = rhs; returns (x, report dict)."""
+              inner_tol=1e-5, max_outer=30, use_graph=True, resid_prec="fp64", stream=None):
+        """GMRES for K x = rhs; returns (x, report dict).  inner_prec fp64 / df32: plain
+        GMRES in that precision; fp32 / fp32c: iterative refinement whose residuals are
+        formed in resid_prec (fp64 or df32)."""
         _dev(rhs, (3, self.n), "rhs")
         x = torch.zeros_like(rhs) if x0 is None else x0.clone()
         _dev(x, (3, self.n), "x0")
         o = GmresOpts(float(tol), int(restart), int(max_iter), _prec(inner_prec), float(inner_tol),
-                      int(max_outer), 1 if use_graph else 0)
+                      int(max_outer), 1 if use_graph else 0, _prec(resid_prec))
         rep = GmresReport()
         st = lib.gmres_solve(self.handle, _ptr(rhs), _ptr(x), ctypes.byref(o), ctypes.byref(rep),
                              _stream(stream))
@@ -351,7 +354,7 @@ class StokesOp:
 
 def solve_from_host(src, nrm, w, rhs, eta, tol=1e-10, inner_prec="fp32c", restart=100,
                     max_iter=2000, inner_tol=1e-5, max_outer=30, use_graph=True, device="cuda",
-                    correction=None, body_off=None):
+                    correction=None, body_off=None, resid_prec="fp64"):
     """End-to-end call on host (pinned CPU) tensors: copy the geometry and data to the GPU,
     build the operator, solve, and copy the solution back to the host.  correction: None,
     or the precision ("fp64", "fp32c", "fp32") in which to build the double-layer
@@ -366,7 +369,8 @@ def solve_from_host(src, nrm, w, rhs, eta, tol=1e-10, inner_prec="fp32c", restar
         E = dl_gauss_correction(d_src, d_nrm, d_w, body_off, prec=correction)
     op = StokesOp(d_src, d_nrm, d_w, eta, correction=E)
     x, rep = op.solve(d_rhs, tol=tol, inner_prec=inner_prec, restart=restart, max_iter=max_iter,
-                      inner_tol=inner_tol, max_outer=max_outer, use_graph=use_graph)
+                      inner_tol=inner_tol, max_outer=max_outer, use_graph=use_graph,
+                      resid_prec=resid_prec)
     out = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
     out.copy_(x)
     op.close()
