@@ -254,7 +254,7 @@ def run_gpu(args):
         return kernel_only(args, sbq, I, src, nrm, w, eta, n, t, dev)
 
     t_setup = time.perf_counter()
-    corr = None if args.no_correction else sbq.dl_gauss_correction(src, nrm, w, prec="fp64")
+    corr = None if args.no_correction else sbq.dl_gauss_correction(src, nrm, w, prec="df32")
     op = sbq.StokesOp(src, nrm, w, eta, correction=corr)
     op.autotune("fp32c")
     op.autotune("fp64")
@@ -393,7 +393,7 @@ def run_gpu(args):
         t0 = time.perf_counter()
         xh, reph = sbq.solve_from_host(hsrc, hnrm, hw, hrhs, eta, tol=1e-10, inner_prec="fp32c",
                                        restart=100, inner_tol=1e-5, max_outer=30, device=dev,
-                                       correction=None if args.no_correction else "fp64",
+                                       correction=None if args.no_correction else "df32",
                                        resid_prec=args.resid_prec)
         torch.cuda.synchronize()
         if k > 0:
@@ -421,7 +421,7 @@ def run_gpu(args):
                        "resid": args.resid_prec + (" (double-float, FP64-class)"
                                                    if args.resid_prec == "df32" else ""),
                        "correction": "none" if args.no_correction else
-                       "double-layer singularity subtraction, built in FP64 on the GPU",
+                       "double-layer singularity subtraction, row sums in double-float",
                        "l2": "flushed between steps (256 MiB write, outside the timed intervals)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "solve": {"mixed_ms": ms, "fp64_ms": fp64_ms, "speedup_vs_fp64": fp64_ms / ms,
@@ -590,7 +590,7 @@ def run_batch(args):
     sig = t(I.density(n, seed=7))
     o = torch.empty_like(sig)
     mv = {p: _cuda_timer(lambda: op.matvec(sig, prec=p, out=o), 5 if p != "fp64" else 1, stream)
-          for p in ("fp32c", "fp32", "fp64")}
+          for p in ("fp32c", "fp32", "df32", "fp64")}
     # batched apply == the same segments applied one by one (same tile shape)
     u = op.matvec(sig, prec="fp32c").clone()
     u64 = op.matvec(sig, prec="fp64").clone()
@@ -609,14 +609,16 @@ def run_batch(args):
     t0 = time.perf_counter()
     corr = None
     if not args.no_correction:
-        corr = sbq.dl_gauss_correction(t(X), t(Nn), t(W), off, prec="fp64")
+        corr = sbq.dl_gauss_correction(t(X), t(Nn), t(W), off, prec="df32")
     opc = sbq.StokesOp(t(X), t(Nn), t(W), eta, correction=corr, plan=plan)
     torch.cuda.synchronize()
     corr_ms = (time.perf_counter() - t0) * 1e3
-    x, rep = opc.solve(rhs, tol=1e-10, restart=100, inner_prec="fp32c", inner_tol=1e-5)
+    sopt = dict(tol=1e-10, restart=100, inner_prec="fp32c", inner_tol=1e-5,
+                resid_prec=args.resid_prec)
+    x, rep = opc.solve(rhs, **sopt)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    x, rep = opc.solve(rhs, tol=1e-10, restart=100, inner_prec="fp32c", inner_tol=1e-5)
+    x, rep = opc.solve(rhs, **sopt)
     torch.cuda.synchronize()
     mixed_ms = (time.perf_counter() - t0) * 1e3
     # residual of every segment (FP64 operator)
@@ -628,7 +630,8 @@ def run_batch(args):
     line = {"workload": "batch_64_capped_arcs", "segments": len(segs), "nodes": n,
             "pairs_per_matvec": pairs, "setup_ms": setup_ms, "tune": tune,
             "correction": "none" if args.no_correction else
-            "double-layer singularity subtraction per segment, FP64",
+            "double-layer singularity subtraction per segment, double-float row sums",
+            "resid": args.resid_prec,
             "correction_and_operator_ms": corr_ms,
             "matvec_ms": mv, "pairs_per_s": {p: pairs / (v * 1e-3) for p, v in mv.items()},
             "fp32c_relerr_vs_fp64": float(((u - u64).abs().max() / u64.abs().max()).item()),
@@ -698,37 +701,42 @@ def run_helix(args):
     op.autotune("fp64")
     ms64 = _cuda_timer(lambda: op.matvec(sig, prec="fp64", out=o), 1, stream, warm=False)
     u64 = o.clone()
+    op.autotune("df32")
+    msdf = _cuda_timer(lambda: op.matvec(sig, prec="df32", out=o), 1, stream, warm=False)
+    udf = o.clone()
     rows = np.sort(np.random.default_rng(4).choice(n, 4096, replace=False))
     sg = sig.cpu().numpy()
     ref = oracle.combined(s.x, s.n, s.w, sg, s.x[:, rows], eta, 1.0) + 0.5 * sg[:, rows]
     ri = torch.as_tensor(rows, device="cuda")
     e64 = float(np.abs(u64[:, ri].cpu().numpy() - ref).max() / np.abs(ref).max())
     e32 = float(np.abs(u32[:, ri].cpu().numpy() - ref).max() / np.abs(ref).max())
+    edf = float(np.abs(udf[:, ri].cpu().numpy() - ref).max() / np.abs(ref).max())
     # solve with the double-layer singularity subtraction per closed body (the capped
-    # pipe, each sphere), its row sums in compensated FP32 (in FP64 they would take
-    # three applies of about a minute each)
+    # pipe, each sphere), its row sums in double-float
     t0 = time.perf_counter()
     corr = None
     if not args.no_correction:
-        corr = sbq.dl_gauss_correction(t(s.x), t(s.n), t(s.w), I.body_offsets(s), prec="fp32c")
+        corr = sbq.dl_gauss_correction(t(s.x), t(s.n), t(s.w), I.body_offsets(s), prec="df32")
     op.close()
     op = sbq.StokesOp(t(s.x), t(s.n), t(s.w), eta, correction=corr)
     torch.cuda.synchronize()
     corr_ms = (time.perf_counter() - t0) * 1e3
     t0 = time.perf_counter()
     x, rep = op.solve(t(rhs), tol=1e-10, restart=100, inner_prec="fp32c", inner_tol=1e-5,
-                      max_iter=400)
+                      max_iter=400, resid_prec=args.resid_prec)
     torch.cuda.synchronize()
     mixed_ms = (time.perf_counter() - t0) * 1e3
     line = {"workload": "helix_pipe_with_spheres", "nodes": n, "spheres": len(c["centres"]),
             "pitch": args.helix_pitch, "eta": eta, "pairs_per_matvec": float(n) * n,
             "generation_s": gen_s,
             "setup_ms": setup_ms, "tune_fp32c": tune32,
-            "matvec_ms": {"fp32c": ms32, "fp64": ms64},
-            "pairs_per_s": {"fp32c": n * n / (ms32 * 1e-3), "fp64": n * n / (ms64 * 1e-3)},
-            "relerr_vs_oracle_4096_rows": {"fp64": e64, "fp32c": e32},
+            "matvec_ms": {"fp32c": ms32, "df32": msdf, "fp64": ms64},
+            "pairs_per_s": {"fp32c": n * n / (ms32 * 1e-3), "df32": n * n / (msdf * 1e-3),
+                            "fp64": n * n / (ms64 * 1e-3)},
+            "relerr_vs_oracle_4096_rows": {"fp64": e64, "df32": edf, "fp32c": e32},
             "correction": "none" if args.no_correction else
-            "double-layer singularity subtraction per body (pipe, 100 spheres), FP32c",
+            "double-layer singularity subtraction per body (pipe, 100 spheres), double-float",
+            "resid": args.resid_prec,
             "correction_and_operator_ms": corr_ms,
             "mixed_solve": {"ms": mixed_ms, "iters": rep["iters"], "refinements": rep["outer_iters"],
                             "matvecs_fp32c": rep["matvecs_low"], "matvecs_fp64": rep["matvecs_fp64"],

@@ -138,7 +138,8 @@ SBQ_API int batch_plan(int nseg, const int64_t *seg_src_off, const int64_t *seg_
         if (seg_src_off[i + 1] < seg_src_off[i] || seg_trg_off[i + 1] < seg_trg_off[i])
             return fail(SBQ_EINVAL, "offsets must be non-decreasing");
     if (tune && tune->r != 0 && !pairsum_shape_supported(SBQ_FP32, tune->r, tune->warps) &&
-        !pairsum_shape_supported(SBQ_FP64, tune->r, tune->warps))
+        !pairsum_shape_supported(SBQ_FP64, tune->r, tune->warps) &&
+        !pairsum_shape_supported(SBQ_DF32, tune->r, tune->warps))
         return fail(SBQ_EINVAL, "unsupported tile shape");
     if (tune && tune->chunk_tiles < 0)
         return fail(SBQ_EINVAL, "chunk_tiles must be >= 0");

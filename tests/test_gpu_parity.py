@@ -465,7 +465,7 @@ def _multibody_case():
     return s, I.body_offsets(s)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32c", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "df32", "fp32c", "fp32"])
 def test_gauss_correction_matches_oracle(sbq, oracle_mod, prec):
     """E = -R_i - I/2 per node, R_i the double-layer row sum over the node's own body:
     structure bit-exact, values within the apply bar of the precision (relative to the
@@ -478,7 +478,7 @@ def test_gauss_correction_matches_oracle(sbq, oracle_mod, prec):
     assert np.array_equal(_np(col), ref.col)
     err = np.abs(_np(val) - ref.val).max() / np.abs(ref.val).max()
     print("gauss correction", prec, err)
-    assert err <= (TOL_F64 if prec == "fp64" else TOL_F32[prec])
+    assert err <= _tol(prec)
 
 
 def test_gauss_correction_operator_and_solve(sbq, oracle_mod):
