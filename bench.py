@@ -627,6 +627,8 @@ def run_batch(args):
     for i in range(len(segs)):
         a, b_ = int(off[i]), int(off[i + 1])
         seg_res.append(float(((rhs[:, a:b_] - kx[:, a:b_]).norm() / rhs[:, a:b_].norm()).item()))
+    if max(seg_res) > 1e-10:
+        raise RuntimeError("batched solve: a segment's FP64 residual is %.3e" % max(seg_res))
     line = {"workload": "batch_64_capped_arcs", "segments": len(segs), "nodes": n,
             "pairs_per_matvec": pairs, "setup_ms": setup_ms, "tune": tune,
             "correction": "none" if args.no_correction else
@@ -726,6 +728,9 @@ def run_helix(args):
                       max_iter=400, resid_prec=args.resid_prec)
     torch.cuda.synchronize()
     mixed_ms = (time.perf_counter() - t0) * 1e3
+    # the returned x, checked with an FP64 residual (one FP64 apply)
+    rhs_d = t(rhs)
+    x64chk = float((rhs_d - op.matvec(x, prec="fp64")).norm() / rhs_d.norm())
     line = {"workload": "helix_pipe_with_spheres", "nodes": n, "spheres": len(c["centres"]),
             "pitch": args.helix_pitch, "eta": eta, "pairs_per_matvec": float(n) * n,
             "generation_s": gen_s,
@@ -740,7 +745,8 @@ def run_helix(args):
             "correction_and_operator_ms": corr_ms,
             "mixed_solve": {"ms": mixed_ms, "iters": rep["iters"], "refinements": rep["outer_iters"],
                             "matvecs_fp32c": rep["matvecs_low"], "matvecs_fp64": rep["matvecs_fp64"],
-                            "rel_res": rep["rel_res"], "hist": rep["hist"], "graph": rep["graph_used"],
+                            "rel_res": rep["rel_res"], "x_fp64_rel_res": x64chk,
+                            "hist": rep["hist"], "graph": rep["graph_used"],
                             "status": rep["status_name"]}}
     if args.fp64_solve:
         t0 = time.perf_counter()

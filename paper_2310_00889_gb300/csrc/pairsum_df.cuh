@@ -314,18 +314,28 @@ __global__ void __launch_bounds__(W * 32) pairsum_df_kernel(const PairsumParams 
                     T[q][r] = df_two_sum(th[q][r], dh[q], e);
                     C[q][r] = fa(fa(tl[q][r], dl[q]), e);
                 }
+            // the tile's sums start from zero and join the item's sums with a full
+            // double-float addition, so rounding inside a tile stays relative to that
+            // tile's own sum, not to the running sum of thousands of tiles
+            float tacc[R][6];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int q = 0; q < 6; ++q)
+                    tacc[r][q] = 0.0f;
             const float4 *sp = sbuf + st * STAGE;
             if (tp.flags & TP_NEAR)
-                tile_df<KIND, R, true>(sp, tp.thr2, T, C, acc);
+                tile_df<KIND, R, true>(sp, tp.thr2, T, C, tacc);
             else
-                tile_df<KIND, R, false>(sp, tp.thr2, T, C, acc);
+                tile_df<KIND, R, false>(sp, tp.thr2, T, C, tacc);
 #pragma unroll
             for (int r = 0; r < R; ++r)
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    float e;
-                    acc[r][q] = df_two_sum(acc[r][q], acc[r][q + 3], e);
-                    acc[r][q + 3] = e;
+                    const dfl v = df_norm(df_add({acc[r][q], acc[r][q + 3]},
+                                                 df_norm({tacc[r][q], tacc[r][q + 3]})));
+                    acc[r][q] = v.h;
+                    acc[r][q + 3] = v.l;
                 }
         }
         g += nk;
