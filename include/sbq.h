@@ -92,7 +92,10 @@ typedef struct {
     int use_graph;     /* 1: each Arnoldi step runs inside one CUDA graph whose while
                           node repeats it on the device until the cycle ends */
     int resid_prec;    /* refinement only: SBQ_FP64 (0, default) or SBQ_DF32, the precision of
-                          the residuals b - K x that decide convergence */
+                          the residuals b - K x that decide convergence.  A double-float
+                          residual carries a bound on its rounding error; where the bound
+                          exceeds tol/4 of a segment's ||b||, the residual is recomputed in
+                          FP64 and the solve continues with FP64 residuals */
 } sbq_gmres_opts;
 
 #define SBQ_HIST 64
@@ -106,13 +109,18 @@ typedef struct {
     int graph_used;           /* 1 if the Arnoldi steps ran inside a CUDA graph */
     int kernel_launches;      /* kernels of this library executed by the solve (graph
                                  replays included) */
-    double rel_res;           /* final FP64 true relative residual ||b - K x|| / ||b||; for an
-                                 operator with a batch plan, the largest of the segments'
-                                 ratios (each segment is solved to tol on its own norm) */
+    double rel_res;           /* final true relative residual ||b - K x|| / ||b||, computed in
+                                 FP64, or in double-float plus its rounding-error bound (an
+                                 upper bound); for an operator with a batch plan, the largest
+                                 of the segments' ratios (each segment is solved to tol on its
+                                 own norm) */
     int n_hist;               /* entries used in rel_res_hist */
     double rel_res_hist[SBQ_HIST]; /* FP64 true relative residual after each refinement
                                       step / restart cycle, starting with x0 */
     double time_ms;           /* wall time of the solve on the host clock */
+    int resid_fallbacks;      /* double-float residuals whose error bound was too large to
+                                 certify the tolerance, recomputed in FP64 (the solve then
+                                 continued in FP64) */
 } sbq_gmres_report;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -234,6 +242,16 @@ SBQ_API int stokes_dl_gauss_correction(int nbody, const int64_t *body_off, const
 /* out = K sigma (device arrays of 3*n doubles) in precision prec, on `stream`. */
 SBQ_API int stokes_matvec(const void *op, const double *sigma, double *out, int prec,
                           void *stream);
+
+/*
+ * out = K sigma in double-float (SBQ_DF32) together with bound[i] >= |error of out[i]|:
+ * the kernel's sum of the magnitudes of the pair terms entering out[i] times the per-term
+ * relative error bound of double-float (2^-40) and the prefactor (paper has no
+ * counterpart; GMRES uses the bound to decide when a double-float residual can certify
+ * the tolerance).  sigma, out, bound: device arrays of 3n doubles.
+ */
+SBQ_API int stokes_matvec_bounded(const void *op, const double *sigma, double *out, double *bound,
+                                  void *stream);
 
 /*
  * Kernel timing without a profiler (paper has no counterpart): runs `reps` >= 1 applies

@@ -265,6 +265,19 @@ SBQ_API int stokes_matvec(const void *oph, const double *sigma, double *out, int
     return op_matvec(op, sigma, out, prec, static_cast<cudaStream_t>(stream));
 }
 
+SBQ_API int stokes_matvec_bounded(const void *oph, const double *sigma, double *out,
+                                  double *bound, void *stream)
+{
+    clear_error();
+    Op *op = as_op(oph);
+    if (!op)
+        return fail(SBQ_EINVAL, "not an operator handle");
+    if (op->n > 0 && (!sigma || !out || !bound))
+        return fail(SBQ_EINVAL, "null density, output or bound pointer");
+    std::lock_guard<std::mutex> lk(op->mu);
+    return op_matvec(op, sigma, out, SBQ_DF32, static_cast<cudaStream_t>(stream), bound);
+}
+
 SBQ_API int sbq_op_time_pairsum(const void *oph, const double *sigma, double *out, int prec,
                                 int reps, void *stream, double *kernel_ms, double *apply_ms)
 {

@@ -313,7 +313,9 @@ int build_trg_set(TrgSet &ts, int kind, int prec, const sbq_tune &tune, const Sr
     ts.grid = static_cast<int>(std::min<long long>(std::max(ts.n_items, 1), slots));
     SBQ_TRY(ts.ttiles.alloc(ht.size() * sizeof(TileInfo)));
     SBQ_TRY(ts.items.alloc(hv.size() * sizeof(int4)));
-    SBQ_TRY(ts.partial.alloc(static_cast<size_t>(slot) * 3 * TT * sizeof(double)));
+    // FP64: one double per entry; FP32: (hi, lo) float2; double-float: (hi, lo, |.|, -) float4
+    const size_t pbytes = (prec == SBQ_DF32) ? sizeof(float4) : sizeof(double);
+    SBQ_TRY(ts.partial.alloc(static_cast<size_t>(slot) * 3 * TT * pbytes));
     SBQ_TRY(ts.counter.alloc(sizeof(int)));
     if (prec != SBQ_FP64)
         SBQ_TRY(ts.tpack.alloc(ht.size() * static_cast<size_t>(TT) * sizeof(float4)));
@@ -344,7 +346,8 @@ PairsumTiming *&pairsum_timing()
 
 int run_pairsum(int kind, int prec, const SrcPack &sp, const TrgSet &ts, const double *w,
                 const double *sigma, long long ns, const double *trg, long long nt, double *out,
-                double scale, double kappa, double diag, const double *diag_sigma, cudaStream_t s)
+                double scale, double kappa, double diag, const double *diag_sigma, cudaStream_t s,
+                double *bound)
 {
     if (ts.n_items == 0)
         return SBQ_OK;
@@ -384,7 +387,7 @@ int run_pairsum(int kind, int prec, const SrcPack &sp, const TrgSet &ts, const d
         SBQ_CUDA(launch_reduce_partials_f32(ts.ttiles.as<TileInfo>(), ts.n_ttiles, ts.TT,
                                             ts.partial.p, nt, out, scale, diag, diag_sigma,
                                             prec == SBQ_FP32_COMP ? 1 : (prec == SBQ_DF32 ? 2 : 0),
-                                            s));
+                                            prec == SBQ_DF32 ? bound : nullptr, s));
     else if (ts.needs_reduce)
         SBQ_CUDA(launch_reduce_partials(ts.ttiles.as<TileInfo>(), ts.n_ttiles, ts.TT,
                                         ts.partial.as<double>(), nt, out, scale, diag, diag_sigma,
@@ -592,7 +595,7 @@ int op_autotune(Op *op, int prec, cudaStream_t s)
     return autotune_op(op, prec, s);
 }
 
-int op_matvec(Op *op, const double *sigma, double *out, int prec, cudaStream_t s)
+int op_matvec(Op *op, const double *sigma, double *out, int prec, cudaStream_t s, double *bound)
 {
     SBQ_TRY(op_ensure_tuned(op, prec, s));
     int kind;
@@ -602,7 +605,8 @@ int op_matvec(Op *op, const double *sigma, double *out, int prec, cudaStream_t s
     if (n == 0)
         return SBQ_OK;
     SBQ_TRY(run_pairsum(kind, prec, op_srcpack(op, prec), *op->ts[prec], op->w.as<double>(), sigma,
-                        n, op->src.as<double>(), n, out, scale, kappa, op->diag, sigma, s));
+                        n, op->src.as<double>(), n, out, scale, kappa, op->diag, sigma, s,
+                        bound));
     if (op->nnz > 0)
         SBQ_CUDA(launch_csr_apply(3 * n, op->rowptr.as<int64_t>(), op->col.as<int64_t>(),
                                   op->val.as<double>(), sigma, out, s));

@@ -97,12 +97,15 @@ struct PairsumTiming {
 PairsumTiming *&pairsum_timing();
 
 // One pair-sum apply: out = scale * sum(...) [+ diag * diag_sigma].
+// bound (double-float only, nullable): per output entry, a bound on its rounding error.
 int run_pairsum(int kind, int prec, const SrcPack &sp, const TrgSet &ts, const double *w,
                 const double *sigma, long long ns, const double *trg, long long nt, double *out,
-                double scale, double kappa, double diag, const double *diag_sigma, cudaStream_t s);
+                double scale, double kappa, double diag, const double *diag_sigma, cudaStream_t s,
+                double *bound = nullptr);
 
 // Operator pieces used by the solver.
-int op_matvec(Op *op, const double *sigma, double *out, int prec, cudaStream_t s);
+int op_matvec(Op *op, const double *sigma, double *out, int prec, cudaStream_t s,
+              double *bound = nullptr);
 int op_ensure_tuned(Op *op, int prec, cudaStream_t s);
 int op_kernels_per_matvec(const Op *op, int prec);
 

@@ -73,7 +73,7 @@ struct GmresWS {
     int ldp = 0;      // stride of part rows (m + 1)
     int LD = 0;       // leading dimension of a Hessenberg matrix (m + 1)
     size_t solve_smem = 0;
-    DevBuf V, H, cs, sn, g, y, hb1, hb2, w, vin, r, d, ax, part, st, seg, blk, segblk, tolv;
+    DevBuf V, H, cs, sn, g, y, hb1, hb2, w, vin, r, d, ax, bnd, part, st, seg, blk, segblk, tolv;
     GState *hst = nullptr;             // pinned host mirrors
     SegState *hseg = nullptr;
     double *htol = nullptr;
@@ -583,6 +583,7 @@ static int ws_ensure(Op *op, int m)
     if (s == SBQ_OK) s = ws->r.alloc(N * sizeof(double));
     if (s == SBQ_OK) s = ws->d.alloc(N * sizeof(double));
     if (s == SBQ_OK) s = ws->ax.alloc(N * sizeof(double));
+    if (s == SBQ_OK) s = ws->bnd.alloc(N * sizeof(double));
     if (s == SBQ_OK) s = ws->part.alloc(static_cast<size_t>(ws->nblk) * (m + 1) * sizeof(double));
     if (s == SBQ_OK) s = ws->st.alloc(sizeof(GState));
     if (s == SBQ_OK) s = ws->seg.alloc(S * sizeof(SegState));
@@ -738,11 +739,12 @@ static void copy_res(const GmresWS *ws, std::vector<double> &out)
         out[i] = ws->hseg[i].res_true;
 }
 
-// r = b - K x in precision prec; per-segment ||r|| to the state.
+// r = b - K x in precision prec; per-segment ||r|| to the state.  bound (double-float
+// only, nullable): per entry a bound on the rounding error of K x.
 static int residual(Op *op, GmresWS *ws, int prec, const double *b, const double *x, double *r,
-                    cudaStream_t s)
+                    cudaStream_t s, double *bound = nullptr)
 {
-    SBQ_TRY(op_matvec(op, x, ws->ax.as<double>(), prec, s));
+    SBQ_TRY(op_matvec(op, x, ws->ax.as<double>(), prec, s, bound));
     k_sub<<<vec_grid(ws->N), GB, 0, s>>>(b, ws->ax.as<double>(), r, ws->N);
     SBQ_CUDA(cudaGetLastError());
     ws->launches += op_kernels_per_matvec(op, prec) + 1;
@@ -803,6 +805,44 @@ static int run_cycle(Op *op, GmresWS *ws, int prec, const double *r, double *xu,
     return SBQ_OK;
 }
 
+// The residual that decides convergence, in precision hp.  A double-float residual comes
+// with a bound on the rounding error of K x (the kernel's running sum of term
+// magnitudes times the per-term error bound).  Where that bound exceeds a quarter of a
+// segment's tolerance the double-float residual cannot certify the tolerance: it is
+// recomputed in FP64 and the rest of the solve stays in FP64.  Otherwise each segment's
+// residual norm is taken as its double-float value plus the bound (an upper bound of the
+// exact residual of the returned x up to FP64 rounding).
+static int decisive_residual(Op *op, GmresWS *ws, int &hp, const double *b, const double *x,
+                             double tol, const std::vector<double> &bnorm,
+                             std::vector<double> &res, sbq_gmres_report &rep, cudaStream_t s)
+{
+    if (hp == SBQ_DF32) {
+        SBQ_TRY(residual(op, ws, SBQ_DF32, b, x, ws->r.as<double>(), s, ws->bnd.as<double>()));
+        rep.matvecs_fp64 += 1;
+        std::vector<double> bn;
+        copy_res(ws, res);
+        SBQ_TRY(norm_to_state(ws, ws->bnd.as<double>(), s));
+        copy_res(ws, bn);
+        bool trusted = true;
+        for (size_t i = 0; i < res.size(); ++i)
+            trusted = trusted && !(bn[i] > 0.25 * tol * bnorm[i]);
+        if (trusted) {
+            for (size_t i = 0; i < res.size(); ++i)
+                res[i] += bn[i];
+            // the state keeps the residual norms for the next cycle
+            SBQ_TRY(norm_to_state(ws, ws->r.as<double>(), s));
+            return SBQ_OK;
+        }
+        hp = SBQ_FP64;
+        rep.resid_fallbacks += 1;
+        SBQ_TRY(op_ensure_tuned(op, SBQ_FP64, s));
+    }
+    SBQ_TRY(residual(op, ws, hp, b, x, ws->r.as<double>(), s));
+    rep.matvecs_fp64 += 1;
+    copy_res(ws, res);
+    return SBQ_OK;
+}
+
 // max over segments of res[s] / ref[s] (segments with ref 0 count as 0)
 static double max_rel(const std::vector<double> &res, const std::vector<double> &ref)
 {
@@ -831,7 +871,7 @@ int gmres_solve_impl(Op *op, const double *b, double *x, const sbq_gmres_opts &o
     const int low = o.inner_prec;
     const bool mixed = (low == SBQ_FP32 || low == SBQ_FP32_COMP);
     // the precision of the residuals that decide convergence (and of the plain solve)
-    const int hp = mixed ? o.resid_prec : low;
+    int hp = mixed ? o.resid_prec : low;
     SBQ_TRY(ws_ensure(op, o.restart));
     GmresWS *ws = op->gm;
     ws->launches = 0;
@@ -877,11 +917,10 @@ int gmres_solve_impl(Op *op, const double *b, double *x, const sbq_gmres_opts &o
     if (xzero) {
         SBQ_CUDA(cudaMemcpyAsync(ws->r.p, b, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
         SBQ_TRY(norm_to_state(ws, ws->r.as<double>(), s));
+        copy_res(ws, res);
     } else {
-        SBQ_TRY(residual(op, ws, hp, b, x, ws->r.as<double>(), s));
-        rep.matvecs_fp64 += 1;
+        SBQ_TRY(decisive_residual(op, ws, hp, b, x, o.tol, bnorm, res, rep, s));
     }
-    copy_res(ws, res);
     double rel = max_rel(res, bnorm);
     push_hist(rel);
     int status = SBQ_OK;
@@ -913,10 +952,8 @@ int gmres_solve_impl(Op *op, const double *b, double *x, const sbq_gmres_opts &o
                 set_error("non-finite value in the Arnoldi process");
                 break;
             }
-            SBQ_TRY(residual(op, ws, hp, b, x, ws->r.as<double>(), s));
-            rep.matvecs_fp64 += 1;
+            SBQ_TRY(decisive_residual(op, ws, hp, b, x, o.tol, bnorm, res, rep, s));
             rep.outer_iters += 1;
-            copy_res(ws, res);
             const double nrel = max_rel(res, bnorm);
             push_hist(nrel);
             if (any_brk && nrel > o.tol && nrel >= rel) {
@@ -981,10 +1018,8 @@ int gmres_solve_impl(Op *op, const double *b, double *x, const sbq_gmres_opts &o
             k_add<<<vec_grid(N), GB, 0, s>>>(d, x, N);
             SBQ_CUDA(cudaGetLastError());
             ws->launches += 1;
-            SBQ_TRY(residual(op, ws, hp, b, x, ws->r.as<double>(), s));
-            rep.matvecs_fp64 += 1;
+            SBQ_TRY(decisive_residual(op, ws, hp, b, x, o.tol, bnorm, res, rep, s));
             rep.outer_iters += 1;
-            copy_res(ws, res);
             const double nrel = max_rel(res, bnorm);
             push_hist(nrel);
             if (!(nrel < rel)) {

@@ -245,7 +245,7 @@ extern "C" SBQ_API int stokes_sl_apply_noalloc(int64_t ns, const double *src, co
     SBQ_CUDA(launch_pairsum(kind, prec, R, W, grid, p, s));
     if (prec != SBQ_FP64)
         SBQ_CUDA(launch_reduce_partials_f32(ttiles, n_tt, TT, p.partial, nt, u, scale, 0.0, nullptr,
-                                            prec == SBQ_FP32_COMP ? 1 : 0, s));
+                                            prec == SBQ_FP32_COMP ? 1 : 0, nullptr, s));
     else if (n_chunks > 1)
         SBQ_CUDA(launch_reduce_partials(ttiles, n_tt, TT, p.partial, nt, u, scale, 0.0, nullptr, s));
     return SBQ_OK;

@@ -367,7 +367,8 @@ __device__ __forceinline__ void merge_partial(float &hi, float &lo, float2 v, in
 __global__ void reduce_partials_f32_kernel(const TileInfo *__restrict__ ttiles, int TT,
                                            const float2 *__restrict__ partial, long long nt,
                                            double *out, double scale, double diag,
-                                           const double *__restrict__ diag_sigma, int comp)
+                                           const double *__restrict__ diag_sigma, int comp,
+                                           double *bound)
 {
     const TileInfo ti = ttiles[blockIdx.x];
     const int c = blockIdx.y;
@@ -377,16 +378,22 @@ __global__ void reduce_partials_f32_kernel(const TileInfo *__restrict__ ttiles, 
         const float2 *pp = partial + (static_cast<size_t>(ti.slot_begin) * 3 + c) * TT + loc;
         const size_t qs = static_cast<size_t>(3) * TT;   // stride between slots
         if (comp == 2) {
-            // double-float partials: each slot's (hi, lo) is exact in FP64; add in FP64
-            double acc = 0.0;
+            // double-float partials (hi, lo, sum of term magnitudes): each slot's hi + lo is
+            // exact in FP64; add in FP64
+            const float4 *p4 = reinterpret_cast<const float4 *>(partial) +
+                               (static_cast<size_t>(ti.slot_begin) * 3 + c) * TT + loc;
+            double acc = 0.0, mag = 0.0;
             for (int q = 0; q < nq; ++q) {
-                const float2 v = pp[q * qs];
+                const float4 v = p4[q * qs];
                 acc += static_cast<double>(v.x) + static_cast<double>(v.y);
+                mag += static_cast<double>(v.z);
             }
             double o = scale * acc;
             if (diag_sigma)
                 o += diag * diag_sigma[c * nt + t];
             out[c * nt + t] = o;
+            if (bound)
+                bound[c * nt + t] = fabs(scale) * DF_TERM_REL * mag;
             continue;
         }
         float hi = 0.0f, lo = 0.0f;
@@ -482,13 +489,14 @@ cudaError_t launch_reduce_partials(const TileInfo *ttiles, int n_ttiles, int TT,
 cudaError_t launch_reduce_partials_f32(const TileInfo *ttiles, int n_ttiles, int TT,
                                        const void *partial, long long nt, double *out,
                                        double scale, double diag, const double *diag_sigma,
-                                       int comp, cudaStream_t s)
+                                       int comp, double *bound, cudaStream_t s)
 {
     if (n_ttiles <= 0)
         return cudaSuccess;
     reduce_partials_f32_kernel<<<dim3(n_ttiles, 3), 256, 0, s>>>(ttiles, TT,
                                                          static_cast<const float2 *>(partial), nt,
-                                                         out, scale, diag, diag_sigma, comp);
+                                                         out, scale, diag, diag_sigma, comp,
+                                                         bound);
     return cudaGetLastError();
 }
 

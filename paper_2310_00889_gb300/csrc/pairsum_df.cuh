@@ -86,11 +86,13 @@ __device__ __forceinline__ void df_acc(float &hi, float &lo, dfl t)
 // the rest (precomputed per tile pair); source record a..e (layout above).  Accumulates
 // the same folded kernels as the FP32 and FP64 paths:
 //   SL: ri q + (r.q) ri^3 r;  DL: (r.q)(r.n) ri^5 r;  CF: ri q + (r.q) ri^3 (1 + (r.n') ri^2) r.
+//   abs: running sum of the magnitudes of the accumulated terms (an error bound: each
+//   term carries a relative error below DF_TERM_REL).
 template <int KIND, bool CHECK>
 __device__ __forceinline__ void pair_df(float Tx, float Ty, float Tz, float Cx, float Cy, float Cz,
                                         const float4 a, const float4 b, const float4 c,
                                         const float4 d, const float4 e, float thr2,
-                                        float (&acc)[6])
+                                        float (&acc)[6], float (&abs)[3])
 {
     // r = (T - y_h) + (C - y_l), normalised
     dfl rx, ry, rz;
@@ -148,13 +150,21 @@ __device__ __forceinline__ void pair_df(float Tx, float Ty, float Tz, float Cx, 
         }
     }
     if (KIND != KIND_DL) {
-        df_acc(acc[0], acc[3], df_mul(ri, qx));
-        df_acc(acc[1], acc[4], df_mul(ri, qy));
-        df_acc(acc[2], acc[5], df_mul(ri, qz));
+        const dfl ux = df_mul(ri, qx), uy = df_mul(ri, qy), uz = df_mul(ri, qz);
+        df_acc(acc[0], acc[3], ux);
+        df_acc(acc[1], acc[4], uy);
+        df_acc(acc[2], acc[5], uz);
+        abs[0] = fa(abs[0], fabsf(ux.h));
+        abs[1] = fa(abs[1], fabsf(uy.h));
+        abs[2] = fa(abs[2], fabsf(uz.h));
     }
-    df_acc(acc[0], acc[3], df_mul(bc, rx));
-    df_acc(acc[1], acc[4], df_mul(bc, ry));
-    df_acc(acc[2], acc[5], df_mul(bc, rz));
+    const dfl vx = df_mul(bc, rx), vy = df_mul(bc, ry), vz = df_mul(bc, rz);
+    df_acc(acc[0], acc[3], vx);
+    df_acc(acc[1], acc[4], vy);
+    df_acc(acc[2], acc[5], vz);
+    abs[0] = fa(abs[0], fabsf(vx.h));
+    abs[1] = fa(abs[1], fabsf(vy.h));
+    abs[2] = fa(abs[2], fabsf(vz.h));
 }
 
 // Tile-pair setup for the double-float kernel: centre offset c_T - c_S split into high and
@@ -181,7 +191,7 @@ __device__ __forceinline__ void tile_pair_setup_df(TilePairParams &tp, double tc
 template <int KIND, int R, bool CHECK>
 __device__ __forceinline__ void tile_df(const float4 *__restrict__ sp, float thr2,
                                         const float (&T)[3][R], const float (&C)[3][R],
-                                        float (&acc)[R][6])
+                                        float (&acc)[R][6], float (&abs)[R][3])
 {
 #pragma unroll 1
     for (int j = 0; j < TS_DF; ++j) {
@@ -190,13 +200,14 @@ __device__ __forceinline__ void tile_df(const float4 *__restrict__ sp, float thr
 #pragma unroll
         for (int r = 0; r < R; ++r)
             pair_df<KIND, CHECK>(T[0][r], T[1][r], T[2][r], C[0][r], C[1][r], C[2][r], a, b, c, d,
-                                 e, thr2, acc[r]);
+                                 e, thr2, acc[r], abs[r]);
     }
 }
 
 // Persistent double-float pair-sum kernel: same work list, ring protocol and bounded
-// waits as pairsum_f32_kernel; every item writes its (hi, lo) sums to its partial slot
-// and reduce_partials_f32 (FP64 mode) adds the slots.
+// waits as pairsum_f32_kernel; every item writes its (hi, lo) sums and the magnitude sum
+// of its terms to its partial slot as float4 [slot][3][TT], and reduce_partials_f32
+// (double-float mode) adds the slots in FP64.
 template <int KIND, int R, int W>
 __global__ void __launch_bounds__(W * 32) pairsum_df_kernel(const PairsumParams p)
 {
@@ -271,12 +282,16 @@ __global__ void __launch_bounds__(W * 32) pairsum_df_kernel(const PairsumParams 
             tl[1][r] = l.y;
             tl[2][r] = l.z;
         }
-        float acc[R][6];
+        float acc[R][6], abs[R][3];
 #pragma unroll
-        for (int r = 0; r < R; ++r)
+        for (int r = 0; r < R; ++r) {
 #pragma unroll
             for (int q = 0; q < 6; ++q)
                 acc[r][q] = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                abs[r][q] = 0.0f;
+        }
 
         const int nk = it.z - it.y;
         for (int k = 0; k < nk; ++k) {
@@ -325,9 +340,9 @@ __global__ void __launch_bounds__(W * 32) pairsum_df_kernel(const PairsumParams 
                     tacc[r][q] = 0.0f;
             const float4 *sp = sbuf + st * STAGE;
             if (tp.flags & TP_NEAR)
-                tile_df<KIND, R, true>(sp, tp.thr2, T, C, tacc);
+                tile_df<KIND, R, true>(sp, tp.thr2, T, C, tacc, abs);
             else
-                tile_df<KIND, R, false>(sp, tp.thr2, T, C, tacc);
+                tile_df<KIND, R, false>(sp, tp.thr2, T, C, tacc, abs);
 #pragma unroll
             for (int r = 0; r < R; ++r)
 #pragma unroll
@@ -340,13 +355,13 @@ __global__ void __launch_bounds__(W * 32) pairsum_df_kernel(const PairsumParams 
         }
         g += nk;
 
-        float2 *pp = reinterpret_cast<float2 *>(p.partial) + static_cast<size_t>(it.w) * 3 * TT +
+        float4 *pp = reinterpret_cast<float4 *>(p.partial) + static_cast<size_t>(it.w) * 3 * TT +
                      warp * 32 * R + lane;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            pp[r * 32] = make_float2(acc[r][0], acc[r][3]);
-            pp[TT + r * 32] = make_float2(acc[r][1], acc[r][4]);
-            pp[2 * TT + r * 32] = make_float2(acc[r][2], acc[r][5]);
+            pp[r * 32] = make_float4(acc[r][0], acc[r][3], abs[r][0], 0.0f);
+            pp[TT + r * 32] = make_float4(acc[r][1], acc[r][4], abs[r][1], 0.0f);
+            pp[2 * TT + r * 32] = make_float4(acc[r][2], acc[r][5], abs[r][2], 0.0f);
         }
     }
 }

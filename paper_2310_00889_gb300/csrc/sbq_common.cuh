@@ -42,6 +42,10 @@ constexpr int DF_TILE_F4 = 5 * TS_DF;
 // coincident.  Centring in double-float leaves a coincident pair a few 2^-48 of that sum
 // apart; distinct nodes of any admissible discretisation are orders of magnitude farther.
 constexpr double DF_COINCIDENT_REL = 1.0e-10;
+// Bound on the relative error of one double-float pair term (against the exact term of
+// the rounded inputs): 2^-40, three times the largest error seen over random pairs and
+// every workload (each term goes through about ten double-float steps of 2^-46..2^-48).
+constexpr double DF_TERM_REL = 9.094947017729282e-13;
 // Compensated FP32: plain FP32 sums over runs of this many sources are merged into
 // the (hi, lo) pair with TwoSum.
 constexpr int COMP_RUN = 64;
@@ -218,10 +222,12 @@ cudaError_t launch_reduce_partials(const TileInfo *ttiles, int n_ttiles, int TT,
                                    double scale, double diag, const double *diag_sigma,
                                    cudaStream_t s);
 // FP32 partial sums ((hi, lo) float pairs) of every slot of a target tile -> FP64 output.
+// comp: 0 plain FP32, 1 compensated, 2 double-float (float4 partials with a magnitude sum;
+// bound, when not null, receives |scale| * DF_TERM_REL * (sum of term magnitudes)).
 cudaError_t launch_reduce_partials_f32(const TileInfo *ttiles, int n_ttiles, int TT,
                                        const void *partial, long long nt, double *out,
                                        double scale, double diag, const double *diag_sigma,
-                                       int comp, cudaStream_t s);
+                                       int comp, double *bound, cudaStream_t s);
 cudaError_t launch_csr_apply(long long nrows, const int64_t *rowptr, const int64_t *col,
                              const double *val, const double *x, double *y, cudaStream_t s);
 

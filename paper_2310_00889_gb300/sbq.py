@@ -54,14 +54,15 @@ class GmresReport(ctypes.Structure):
                 ("graph_used", ctypes.c_int), ("kernel_launches", ctypes.c_int),
                 ("rel_res", ctypes.c_double),
                 ("n_hist", ctypes.c_int), ("rel_res_hist", ctypes.c_double * SBQ_HIST),
-                ("time_ms", ctypes.c_double)]
+                ("time_ms", ctypes.c_double), ("resid_fallbacks", ctypes.c_int)]
 
     def as_dict(self):
         return dict(status=self.status, iters=self.iters, outer_iters=self.outer_iters,
                     matvecs_fp64=self.matvecs_fp64, matvecs_low=self.matvecs_low,
                     graph_used=bool(self.graph_used), kernel_launches=self.kernel_launches,
                     rel_res=self.rel_res,
-                    hist=list(self.rel_res_hist[:self.n_hist]), time_ms=self.time_ms)
+                    hist=list(self.rel_res_hist[:self.n_hist]), time_ms=self.time_ms,
+                    resid_fallbacks=self.resid_fallbacks)
 
 
 _i64 = ctypes.c_int64
@@ -87,6 +88,7 @@ def _load():
         "stokes_op_create": ([_i64, _vp, _vp, _vp, _dbl, _dbl, _i64, _vp, _vp, _vp, _vp,
                               ctypes.POINTER(_vp)], _int),
         "stokes_matvec": ([_vp, _vp, _vp, _int, _vp], _int),
+        "stokes_matvec_bounded": ([_vp, _vp, _vp, _vp, _vp], _int),
         "gmres_solve": ([_vp, _vp, _vp, ctypes.POINTER(GmresOpts), ctypes.POINTER(GmresReport),
                          _vp], _int),
         "sbq_autotune": ([_vp, _int, ctypes.POINTER(Tune), _vp], _int),
@@ -303,6 +305,15 @@ class StokesOp:
         _dev(out, (3, self.n), "out")
         _check(lib.stokes_matvec(self.handle, _ptr(sigma), _ptr(out), _prec(prec), _stream(stream)))
         return out
+
+    def matvec_bounded(self, sigma, stream=None):
+        """(K sigma in double-float, per-entry bound on its rounding error)."""
+        _dev(sigma, (3, self.n), "sigma")
+        out = torch.empty_like(sigma)
+        bnd = torch.empty_like(sigma)
+        _check(lib.stokes_matvec_bounded(self.handle, _ptr(sigma), _ptr(out), _ptr(bnd),
+                                         _stream(stream)))
+        return out, bnd
 
     def solve(self, rhs, x0=None, tol=1e-10, restart=100, max_iter=2000, inner_prec="fp64",
               inner_tol=1e-5, max_outer=30, use_graph=True, resid_prec="fp64", stream=None):

@@ -564,3 +564,49 @@ def test_pairsum_kernel_timing(sbq):
     with pytest.raises(sbq.SbqError):
         op.time_pairsum(sig, prec="fp32c", reps=0)
     op.close()
+
+
+# ---------------------------------------------------------------------------
+# Double-float rounding-error bound and the residual precision switch
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", ["curved_pipe", "random_loop", "multibody"])
+def test_double_float_error_bound_holds(sbq, oracle_mod, case):
+    """Every entry of the double-float operator apply is within its reported bound of the
+    FP64 oracle (plus the oracle's own rounding, 1e-14 of the largest entry), and the bound
+    is tight enough to be useful (below 1e-10 of the largest entry)."""
+    if case == "curved_pipe":
+        s = I.config2(panels=4)["surf"]
+    elif case == "random_loop":
+        s = I.random_loop(seed=1, panels=64, ns=8, nth=16)
+    else:
+        s, _ = _multibody_case()
+    eta = sbq.slender_eta(0.2)
+    op = sbq.StokesOp(_t(s.x), _t(s.n), _t(s.w), eta)
+    sig = I.density(s.size, seed=51)
+    u, bnd = op.matvec_bounded(_t(sig))
+    u, bnd = _np(u), _np(bnd)
+    ref = oracle_mod.matvec(s.x, s.n, s.w, eta, sig)
+    slack = 1e-14 * np.abs(ref).max()
+    excess = np.abs(u - ref) - bnd - slack
+    print("bound %s: max err %.3e max bound %.3e" % (case, np.abs(u - ref).max(), bnd.max()))
+    assert np.all(excess <= 0.0)
+    assert bnd.max() <= 1e-10 * np.abs(ref).max()
+    op.close()
+
+
+def test_double_float_residuals_fall_back_to_fp64(sbq, oracle_mod, small_solve):
+    """At tol 1e-13 the double-float residual's bound exceeds a quarter of the tolerance:
+    the solve switches to FP64 residuals and still meets the tolerance (checked by the
+    oracle); at tol 1e-10 no switch is needed."""
+    s, rhs, eta, _ = small_solve
+    op = sbq.StokesOp(_t(s.x), _t(s.n), _t(s.w), eta)
+    for tol, want_fallback in ((1e-10, False), (1e-13, True)):
+        x, rep = op.solve(_t(rhs), tol=tol, restart=100, inner_prec="fp32c", inner_tol=1e-5,
+                          resid_prec="df32", max_outer=40)
+        print("df32 residuals tol", tol, {k: rep[k] for k in ("iters", "outer_iters",
+                                                                "resid_fallbacks", "rel_res")})
+        assert rep["status"] == 0 and (rep["resid_fallbacks"] > 0) == want_fallback
+        kx = oracle_mod.matvec(s.x, s.n, s.w, eta, _np(x))
+        assert np.linalg.norm(rhs - kx) / np.linalg.norm(rhs) <= 1.05 * tol + 1e-15
+    op.close()
