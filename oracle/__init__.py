@@ -104,6 +104,36 @@ def combined(src, nrm, w, sigma, trg, alpha, beta):
     return u
 
 
+def combined_extended(src, nrm, w, sigma, trg, alpha, beta):
+    """The same sum as `combined`, evaluated in numpy long double (64-bit significand on
+    x86, 113-bit on aarch64), row by row with numpy; for few targets.  Used where the FP64
+    evaluation's own rounding (r = x - y from absolute coordinates) is not small next to
+    the error being checked."""
+    ld = np.longdouble
+    src = np.asarray(src, dtype=ld)
+    trg = np.asarray(trg, dtype=ld)
+    w = np.asarray(w, dtype=ld)
+    q = np.asarray(sigma, dtype=ld) * w[None, :]
+    nrm = np.asarray(nrm, dtype=ld) if nrm is not None else None
+    pi = ld("3.14159265358979323846264338327950288")
+    out = np.empty((3, trg.shape[1]), dtype=ld)
+    for t in range(trg.shape[1]):
+        r = trg[:, t:t + 1] - src
+        r2 = np.sum(r * r, axis=0)
+        keep = r2 != 0
+        r, r2, qq = r[:, keep], r2[keep], q[:, keep]
+        rl = np.sqrt(r2)
+        rq = np.sum(r * qq, axis=0)
+        u = np.zeros(3, dtype=ld)
+        if alpha != 0:
+            u += ld(alpha) / (8 * pi) * (np.sum(qq / rl, axis=1) + np.sum(r * (rq / (r2 * rl)), axis=1))
+        if beta != 0:
+            rn = np.sum(r * nrm[:, keep], axis=0)
+            u += ld(beta) * 3 / (4 * pi) * np.sum(r * (rn * rq / (r2 * r2 * rl)), axis=1)
+        out[:, t] = u
+    return out
+
+
 def sl(src, w, sigma, trg):
     """Single-layer potential S[sigma] (paper Eq. stokes-sl), uncorrected Nystrom sum."""
     return combined(src, None, w, sigma, trg, 1.0, 0.0)

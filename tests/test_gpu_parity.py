@@ -573,8 +573,10 @@ def test_pairsum_kernel_timing(sbq):
 @pytest.mark.parametrize("case", ["curved_pipe", "random_loop", "multibody"])
 def test_double_float_error_bound_holds(sbq, oracle_mod, case):
     """Every entry of the double-float operator apply is within its reported bound of the
-    FP64 oracle (plus the oracle's own rounding, 1e-14 of the largest entry), and the bound
-    is tight enough to be useful (below 1e-10 of the largest entry)."""
+    exact sum, taken from the oracle's long-double row evaluator on 96 sampled nodes (the
+    FP64 oracle's own rounding of x - y is not small enough next to the bound on thin
+    tubes), and the bound is tight enough to be useful (below 1e-10 of the largest
+    entry)."""
     if case == "curved_pipe":
         s = I.config2(panels=4)["surf"]
     elif case == "random_loop":
@@ -586,8 +588,11 @@ def test_double_float_error_bound_holds(sbq, oracle_mod, case):
     sig = I.density(s.size, seed=51)
     u, bnd = op.matvec_bounded(_t(sig))
     u, bnd = _np(u), _np(bnd)
-    ref = oracle_mod.matvec(s.x, s.n, s.w, eta, sig)
-    slack = 1e-14 * np.abs(ref).max()
+    rows = np.sort(np.random.default_rng(52).choice(s.size, 96, replace=False))
+    ext = oracle_mod.combined_extended(s.x, s.n, s.w, sig, s.x[:, rows], eta, 1.0)
+    ref = np.asarray(ext + np.longdouble(0.5) * sig[:, rows], dtype=np.float64)
+    u, bnd = u[:, rows], bnd[:, rows]
+    slack = 4e-16 * np.abs(ref).max()
     excess = np.abs(u - ref) - bnd - slack
     print("bound %s: max err %.3e max bound %.3e" % (case, np.abs(u - ref).max(), bnd.max()))
     assert np.all(excess <= 0.0)

@@ -223,6 +223,18 @@ def test_c_sum_matches_numpy_dense_operator(oracle_mod):
     assert np.abs(A @ c["sigma"].reshape(-1) - u.reshape(-1)).max() < 1e-12 * np.abs(u).max()
 
 
+def test_extended_precision_rows_match_fp64(oracle_mod):
+    """The long-double row evaluator is a third coding of the same sum: on the straight pipe
+    (no severe cancellation in x - y) it agrees with the FP64 C loop to FP64 rounding."""
+    c = I.config1()
+    s = c["surf"]
+    trg = c["trg"][:, ::37]
+    for alpha, beta in ((1.0, 0.0), (0.0, 1.0), (1.7, 1.0)):
+        u = oracle_mod.combined(s.x, s.n, s.w, c["sigma"], trg, alpha, beta)
+        v = oracle_mod.combined_extended(s.x, s.n, s.w, c["sigma"], trg, alpha, beta)
+        assert np.abs(np.asarray(v, dtype=np.float64) - u).max() <= 1e-13 * np.abs(u).max()
+
+
 def test_csr_apply_matches_scipy(oracle_mod):
     """Sparse correction apply y += E x (Eq. nystrom-correction) against scipy's CSR product."""
     sp = pytest.importorskip("scipy.sparse")
