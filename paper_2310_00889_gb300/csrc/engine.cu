@@ -325,6 +325,10 @@ int build_trg_set(TrgSet &ts, int kind, int prec, const sbq_tune &tune, const Sr
         SBQ_TRY(ts.tpack_lo.alloc(ht.size() * static_cast<size_t>(TT) * sizeof(float4)));
     else
         ts.tpack_lo.release();
+    if (prec == SBQ_DF32)
+        SBQ_TRY(ts.tpack_l2.alloc(ht.size() * static_cast<size_t>(TT) * sizeof(float4)));
+    else
+        ts.tpack_l2.release();
     if (!ht.empty()) {
         SBQ_CUDA(cudaMemcpyAsync(ts.ttiles.p, ht.data(), ht.size() * sizeof(TileInfo),
                                  cudaMemcpyHostToDevice, s));
@@ -334,7 +338,8 @@ int build_trg_set(TrgSet &ts, int kind, int prec, const sbq_tune &tune, const Sr
     SBQ_CUDA(cudaMemsetAsync(ts.counter.p, 0, sizeof(int), s));
     if (prec != SBQ_FP64 && ts.n_ttiles > 0)
         SBQ_CUDA(launch_pack_trg(trg, nt, ts.ttiles.as<TileInfo>(), ts.n_ttiles, TT,
-                                 ts.tpack.as<float4>(), ts.tpack_lo.as<float4>(), s));
+                                 ts.tpack.as<float4>(), ts.tpack_lo.as<float4>(),
+                                 ts.tpack_l2.as<float4>(), s));
     return SBQ_OK;
 }
 
@@ -363,6 +368,7 @@ int run_pairsum(int kind, int prec, const SrcPack &sp, const TrgSet &ts, const d
     p.stiles = sp.stiles.as<TileInfo>();
     p.tpack = ts.tpack.as<float4>();
     p.tpack_lo = ts.tpack_lo.as<float4>();
+    p.tpack_l2 = ts.tpack_l2.as<float4>();
     p.ttiles = ts.ttiles.as<TileInfo>();
     p.trg = trg;
     p.nt = nt;

@@ -62,7 +62,7 @@ struct TrgSet {
     int grid = 0;
     bool needs_reduce = false;
     double pairs = 0.0;         // pair interactions per apply (valid members only)
-    DevBuf ttiles, tpack, tpack_lo, items, partial, counter;
+    DevBuf ttiles, tpack, tpack_lo, tpack_l2, items, partial, counter;
 };
 
 struct Op {

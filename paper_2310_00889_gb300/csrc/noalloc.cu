@@ -218,7 +218,7 @@ extern "C" SBQ_API int stokes_sl_apply_noalloc(int64_t ns, const double *src, co
         SBQ_CUDA(launch_pack_trg(trg, nt, ttiles, n_tt, TT, reinterpret_cast<float4 *>(b8 + L.tpack),
                                  prec == SBQ_FP32_COMP ? reinterpret_cast<float4 *>(b8 + L.tpack_lo)
                                                        : nullptr,
-                                 s));
+                                 nullptr, s));
     int kind;
     double scale, kappa;
     kind_and_scale(1.0, 0.0, &kind, &scale, &kappa);

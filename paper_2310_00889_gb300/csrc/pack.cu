@@ -213,14 +213,28 @@ __global__ void pack_src_q_f64(const double *__restrict__ w, const double *__res
 }
 
 // Double-float source tiles (record layout in pairsum_df.cuh): float index of field f of
-// source j.  Fields: 0 xh 1 yh 2 zh 3 qxh 4 qyh 5 qzh 6 nxh 7 nyh 8 nzh 9 xl 10 yl 11 zl
-// 12 qxl 13 qyl 14 qzl 15 nxl 16 nyl 17 nzl (18, 19 unused).
-__device__ __forceinline__ int df_slot(int f, int j) { return 20 * j + f; }
+// source j.  Fields: 0 xh 1 yh 2 zh 3 qxh 4 qyh 5 qzh 6 nxh 7 nyh 8 nzh 9 xm 10 ym 11 zm
+// 12 qxl 13 qyl 14 qzl 15 nxl 16 nyl 17 nzl 18 |q|_1 19 |n|_1 (both rounded up; they feed
+// the rounding-error bound only) 20 xl 21 yl 22 zl (23 unused).
+__device__ __forceinline__ int df_slot(int f, int j) { return 24 * j + f; }
 
 __device__ __forceinline__ void split_df(double v, float &h, float &l)
 {
     h = static_cast<float>(v);
     l = static_cast<float>(v - static_cast<double>(h));
+}
+
+// a - b = h + m + l to about 2^-72 |a - b|: the FP64 difference with its exact rounding
+// error (TwoSum), split into three FP32 parts.
+__device__ __forceinline__ void split3(double a, double b, float &h, float &m, float &l)
+{
+    const double s = a - b;
+    const double bb = s - a;
+    const double e = (a - (s - bb)) - (b + bb);
+    h = static_cast<float>(s);
+    const double r1 = s - static_cast<double>(h);
+    m = static_cast<float>(r1);
+    l = static_cast<float>((r1 - static_cast<double>(m)) + e);
 }
 
 __global__ void pack_src_geom_df(const double *__restrict__ src, const double *__restrict__ nrm,
@@ -236,27 +250,29 @@ __global__ void pack_src_geom_df(const double *__restrict__ src, const double *_
     tile_centre(src, ns, begin, count, TS, bb, cx, cy, cz);
     float *tile = reinterpret_cast<float *>(spack + static_cast<size_t>(k) * DF_TILE_F4);
     double d2 = 0.0;
-    float v[20];
-    for (int f = 0; f < 20; ++f)
+    float v[24];
+    for (int f = 0; f < 24; ++f)
         v[f] = 0.0f;
     if (j < count) {
         const long long s = begin + j;
         const double dx = src[s] - cx, dy = src[ns + s] - cy, dz = src[2 * ns + s] - cz;
-        split_df(dx, v[0], v[9]);
-        split_df(dy, v[1], v[10]);
-        split_df(dz, v[2], v[11]);
+        split3(src[s], cx, v[0], v[9], v[20]);
+        split3(src[ns + s], cy, v[1], v[10], v[21]);
+        split3(src[2 * ns + s], cz, v[2], v[11], v[22]);
         if (nrm) {
             split_df(nscale * nrm[s], v[6], v[15]);
             split_df(nscale * nrm[ns + s], v[7], v[16]);
             split_df(nscale * nrm[2 * ns + s], v[8], v[17]);
+            v[19] = __double2float_ru(fabs(nscale) * (fabs(nrm[s]) + fabs(nrm[ns + s]) +
+                                                      fabs(nrm[2 * ns + s])) * (1.0 + 1e-12));
         }
         d2 = dx * dx + dy * dy + dz * dz;
     } else {
         v[0] = v[1] = v[2] = PAD_POS_F32;
     }
-    for (int f = 0; f < 20; ++f)
+    for (int f = 0; f < 24; ++f)
         if (f < 3 || f > 5)
-            if (f < 12 || f > 14)
+            if ((f < 12 || f > 14) && f != 18)
                 tile[df_slot(f, j)] = v[f];
     const double m = block_max(d2, red);
     if (j == 0) {
@@ -276,22 +292,28 @@ __global__ void pack_src_q_df(const double *__restrict__ w, const double *__rest
     const int k = blockIdx.x, j = threadIdx.x;
     const long long begin = stiles[k].begin;
     const int count = stiles[k].count;
-    float qh[3] = {0.0f, 0.0f, 0.0f}, ql[3] = {0.0f, 0.0f, 0.0f};
+    float qh[3] = {0.0f, 0.0f, 0.0f}, ql[3] = {0.0f, 0.0f, 0.0f}, qn = 0.0f;
     if (j < count) {
         const long long s = begin + j;
         const double ww = w[s];
-        for (int c = 0; c < 3; ++c)
-            split_df(ww * sigma[c * ns + s], qh[c], ql[c]);
+        double a = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            const double q = ww * sigma[c * ns + s];
+            split_df(q, qh[c], ql[c]);
+            a += fabs(q);
+        }
+        qn = __double2float_ru(a * (1.0 + 1e-12));
     }
     float *tile = reinterpret_cast<float *>(spack + static_cast<size_t>(k) * DF_TILE_F4);
     for (int c = 0; c < 3; ++c) {
         tile[df_slot(3 + c, j)] = qh[c];
         tile[df_slot(12 + c, j)] = ql[c];
     }
+    tile[df_slot(18, j)] = qn;
 }
 
 __global__ void pack_trg_f32(const double *__restrict__ trg, long long nt, TileInfo *ttiles, int TT,
-                             float4 *tpack, float4 *tpack_lo)
+                             float4 *tpack, float4 *tpack_lo, float4 *tpack_l2)
 {
     __shared__ double red[32];
     __shared__ double bb[6][32];
@@ -302,19 +324,20 @@ __global__ void pack_trg_f32(const double *__restrict__ trg, long long nt, TileI
     tile_centre(trg, nt, begin, count, TT, bb, cx, cy, cz);
     double d2 = 0.0;
     for (int j = threadIdx.x; j < TT; j += blockDim.x) {
-        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f), l = v;
+        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f), l = v, l2 = v;
         if (j < count) {
             const long long t = begin + j;
             const double dx = trg[t] - cx, dy = trg[nt + t] - cy, dz = trg[2 * nt + t] - cz;
-            v = make_float4(static_cast<float>(dx), static_cast<float>(dy), static_cast<float>(dz),
-                            0.0f);
-            l = make_float4(static_cast<float>(dx - v.x), static_cast<float>(dy - v.y),
-                            static_cast<float>(dz - v.z), 0.0f);
+            split3(trg[t], cx, v.x, l.x, l2.x);
+            split3(trg[nt + t], cy, v.y, l.y, l2.y);
+            split3(trg[2 * nt + t], cz, v.z, l.z, l2.z);
             d2 = fmax(d2, dx * dx + dy * dy + dz * dz);
         }
         tpack[static_cast<size_t>(k) * TT + j] = v;
         if (tpack_lo)
             tpack_lo[static_cast<size_t>(k) * TT + j] = l;
+        if (tpack_l2)
+            tpack_l2[static_cast<size_t>(k) * TT + j] = l2;
     }
     const double m = block_max(d2, red);
     if (threadIdx.x == 0) {
@@ -378,8 +401,8 @@ __global__ void reduce_partials_f32_kernel(const TileInfo *__restrict__ ttiles, 
         const float2 *pp = partial + (static_cast<size_t>(ti.slot_begin) * 3 + c) * TT + loc;
         const size_t qs = static_cast<size_t>(3) * TT;   // stride between slots
         if (comp == 2) {
-            // double-float partials (hi, lo, sum of term magnitudes): each slot's hi + lo is
-            // exact in FP64; add in FP64
+            // double-float partials (hi, lo, error bound): each slot's hi + lo is exact in
+            // FP64; add in FP64
             const float4 *p4 = reinterpret_cast<const float4 *>(partial) +
                                (static_cast<size_t>(ti.slot_begin) * 3 + c) * TT + loc;
             double acc = 0.0, mag = 0.0;
@@ -393,7 +416,7 @@ __global__ void reduce_partials_f32_kernel(const TileInfo *__restrict__ ttiles, 
                 o += diag * diag_sigma[c * nt + t];
             out[c * nt + t] = o;
             if (bound)
-                bound[c * nt + t] = fabs(scale) * DF_TERM_REL * mag;
+                bound[c * nt + t] = fabs(scale) * mag * (1.0 + 1e-6);
             continue;
         }
         float hi = 0.0f, lo = 0.0f;
@@ -467,11 +490,11 @@ cudaError_t launch_pack_src_q(int prec, const double *w, const double *sigma, lo
 }
 
 cudaError_t launch_pack_trg(const double *trg, long long nt, TileInfo *ttiles, int n_ttiles, int TT,
-                            float4 *tpack, float4 *tpack_lo, cudaStream_t s)
+                            float4 *tpack, float4 *tpack_lo, float4 *tpack_l2, cudaStream_t s)
 {
     if (n_ttiles <= 0)
         return cudaSuccess;
-    pack_trg_f32<<<n_ttiles, 256, 0, s>>>(trg, nt, ttiles, TT, tpack, tpack_lo);
+    pack_trg_f32<<<n_ttiles, 256, 0, s>>>(trg, nt, ttiles, TT, tpack, tpack_lo, tpack_l2);
     return cudaGetLastError();
 }
 

@@ -13,11 +13,23 @@
 // All arithmetic below goes through the __f*_rn intrinsics: the compiler never fuses or
 // reorders them, which the error-free transformations rely on.
 //
-// Source tile layout (TS_DF sources, five float4 per source, source-major):
-//   {xh, yh, zh, qxh} {qyh, qzh, nxh, nyh} {nzh, xl, yl, zl} {qxl, qyl, qzl, nxl} {nyl, nzl, 0, 0}
-// positions relative to the tile centre (FP64 subtraction, then split into high and low
-// FP32 parts), q = w sigma and the scaled normals split the same way.  Targets use the
-// FP32 target tiles with their low parts (tpack, tpack_lo).
+// Source tile layout (TS_DF sources, six float4 per source, source-major):
+//   {xh, yh, zh, qxh} {qyh, qzh, nxh, nyh} {nzh, xm, ym, zm} {qxl, qyl, qzl, nxl}
+//   {nyl, nzl, |q|, |n|} {xl, yl, zl, 0}
+// positions relative to the tile centre in three FP32 parts h + m + l (to about 2^-72 of
+// the offset), q = w sigma and the scaled normals in two parts, and the 1-norms of q and
+// of the scaled normal (rounded up, for the error bound).  Targets use the FP32 target
+// tiles with their second and third parts (tpack, tpack_lo, tpack_l2).
+//
+// Forming r.  Each target is rebased once per tile pair onto the source tile's centre as
+// T + C + D (T one float, C the next 24 bits, D the rest).  Where the closest possible pair
+// of the two tiles is at least DF_EXACT_R of (radii + centre distance) away, r = (T - y_h)
+// + (C + D - y_m), within about 2^-46 of |r|.  Nearer tile pairs form r exactly from all
+// three parts (two more TwoSums), so close pairs in wide tiles keep 2^-48 of |r| too.
+//
+// Rounding-error bound.  Every pair adds its envelope E = |q| ri (2 + |n| ri) (SL: 2 |q| ri,
+// DL: |q| |n| ri^2), which bounds the magnitude of every intermediate product of the pair
+// whatever cancels, to a running sum; an item's bound is DF_TERM_REL x that sum.
 #pragma once
 
 #include "sbq_common.cuh"
@@ -82,29 +94,33 @@ __device__ __forceinline__ void df_acc(float &hi, float &lo, dfl t)
     lo = fa(lo, fa(e, t.l));
 }
 
-// One pair in double-float.  Target: T + C with T = high part of (x_t + c_T - c_S) and C
-// the rest (precomputed per tile pair); source record a..e (layout above).  Accumulates
-// the same folded kernels as the FP32 and FP64 paths:
-//   SL: ri q + (r.q) ri^3 r;  DL: (r.q)(r.n) ri^5 r;  CF: ri q + (r.q) ri^3 (1 + (r.n') ri^2) r.
-//   abs: running sum of the magnitudes of the accumulated terms (an error bound: each
-//   term carries a relative error below DF_TERM_REL).
-template <int KIND, bool CHECK>
-__device__ __forceinline__ void pair_df(float Tx, float Ty, float Tz, float Cx, float Cy, float Cz,
-                                        const float4 a, const float4 b, const float4 c,
-                                        const float4 d, const float4 e, float thr2,
-                                        float (&acc)[6], float (&abs)[3])
+// One pair in double-float.  Target: T + C + D (the target rebased onto the source tile's
+// centre, see above); source record a..f (layout above).  Accumulates the same folded
+// kernels as the FP32 and FP64 paths:
+//   SL: ri q + (r.q) ri^3 r;  DL: (r.q)(r.n) ri^5 r;  CF: ri q + (r.q) ri^3 (1 + (r.n') ri^2) r
+// and the pair's envelope into env (see the error bound above).
+template <int KIND, bool CHECK, bool EXACT>
+__device__ __forceinline__ void pair_df(const float (&T)[3], const float (&C)[3],
+                                        const float (&D)[3], const float4 a, const float4 b,
+                                        const float4 c, const float4 d, const float4 e,
+                                        const float4 f, float thr2, float (&acc)[6], float &env)
 {
-    // r = (T - y_h) + (C - y_l), normalised
-    dfl rx, ry, rz;
-    {
-        float ex, ey, ez;
-        const float sx = df_two_sum(Tx, -a.x, ex);
-        const float sy = df_two_sum(Ty, -a.y, ey);
-        const float sz = df_two_sum(Tz, -a.z, ez);
-        rx = df_norm({sx, fa(ex, fs(Cx, c.y))});
-        ry = df_norm({sy, fa(ey, fs(Cy, c.z))});
-        rz = df_norm({sz, fa(ez, fs(Cz, c.w))});
+    const float ph[3] = {a.x, a.y, a.z}, pm[3] = {c.y, c.z, c.w}, pl[3] = {f.x, f.y, f.z};
+    dfl rv[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float e1;
+        const float s1 = df_two_sum(T[k], -ph[k], e1);
+        if (EXACT) {
+            float e2, e3;
+            const float s2 = df_two_sum(C[k], -pm[k], e2);
+            const float h = df_two_sum(s1, s2, e3);
+            rv[k] = df_norm({h, fa(fa(e1, e2), fa(e3, fs(D[k], pl[k])))});
+        } else {
+            rv[k] = df_norm({s1, fa(e1, fs(fa(C[k], D[k]), pm[k]))});
+        }
     }
+    const dfl rx = rv[0], ry = rv[1], rz = rv[2];
     // r^2: exact squares of the high parts, cross terms 2 h l, two TwoSums
     dfl r2;
     {
@@ -150,57 +166,73 @@ __device__ __forceinline__ void pair_df(float Tx, float Ty, float Tz, float Cx, 
         }
     }
     if (KIND != KIND_DL) {
-        const dfl ux = df_mul(ri, qx), uy = df_mul(ri, qy), uz = df_mul(ri, qz);
-        df_acc(acc[0], acc[3], ux);
-        df_acc(acc[1], acc[4], uy);
-        df_acc(acc[2], acc[5], uz);
-        abs[0] = fa(abs[0], fabsf(ux.h));
-        abs[1] = fa(abs[1], fabsf(uy.h));
-        abs[2] = fa(abs[2], fabsf(uz.h));
+        df_acc(acc[0], acc[3], df_mul(ri, qx));
+        df_acc(acc[1], acc[4], df_mul(ri, qy));
+        df_acc(acc[2], acc[5], df_mul(ri, qz));
     }
-    const dfl vx = df_mul(bc, rx), vy = df_mul(bc, ry), vz = df_mul(bc, rz);
-    df_acc(acc[0], acc[3], vx);
-    df_acc(acc[1], acc[4], vy);
-    df_acc(acc[2], acc[5], vz);
-    abs[0] = fa(abs[0], fabsf(vx.h));
-    abs[1] = fa(abs[1], fabsf(vy.h));
-    abs[2] = fa(abs[2], fabsf(vz.h));
+    df_acc(acc[0], acc[3], df_mul(bc, rx));
+    df_acc(acc[1], acc[4], df_mul(bc, ry));
+    df_acc(acc[2], acc[5], df_mul(bc, rz));
+    if (KIND == KIND_SL)
+        env = ff(fa(e.z, e.z), y, env);
+    else if (KIND == KIND_DL)
+        env = ff(fm(e.z, e.w), yy, env);
+    else
+        env = ff(fm(e.z, y), ff(e.w, y, 2.0f), env);
 }
 
-// Tile-pair setup for the double-float kernel: centre offset c_T - c_S split into high and
-// low FP32 parts, coincidence threshold, near flag (bounding spheres touch).
-__device__ __forceinline__ void tile_pair_setup_df(TilePairParams &tp, double tcx, double tcy,
+// Parameters of one (target tile, source tile) pair for the double-float kernel.
+struct __align__(16) DfPairParams {
+    float dh[3], dm[3], dl[3];   // c_T - c_S = dh + dm + dl
+    float thr2;                  // squared coincidence threshold
+    int flags;                   // TP_NEAR (coincidence test) | TP_EXACT (exact r)
+    float pad_;
+};
+constexpr int TP_EXACT = 4;
+
+__device__ __forceinline__ void df_split3(double a, double b, float &h, float &m, float &l)
+{
+    const double s = a - b;
+    const double bb = s - a;
+    const double e = (a - (s - bb)) - (b + bb);
+    h = static_cast<float>(s);
+    const double r1 = s - static_cast<double>(h);
+    m = static_cast<float>(r1);
+    l = static_cast<float>((r1 - static_cast<double>(m)) + e);
+}
+
+__device__ __forceinline__ void tile_pair_setup_df(DfPairParams &tp, double tcx, double tcy,
                                                    double tcz, float trad, const TileInfo &si)
 {
     const double ddx = tcx - si.cx, ddy = tcy - si.cy, ddz = tcz - si.cz;
     const double dist = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
     const double lim = static_cast<double>(trad) + static_cast<double>(si.rad);
-    tp.flags = ((dist - lim) <= 1.0e-5 * (dist + lim) + 1.0e-30) ? TP_NEAR : 0;
-    const float sx = static_cast<float>(ddx), sy = static_cast<float>(ddy),
-                sz = static_cast<float>(ddz);
-    tp.sx = sx;
-    tp.sy = sy;
-    tp.sz = sz;
-    tp.lx = static_cast<float>(ddx - static_cast<double>(sx));
-    tp.ly = static_cast<float>(ddy - static_cast<double>(sy));
-    tp.lz = static_cast<float>(ddz - static_cast<double>(sz));
+    int flags = 0;
+    if ((dist - lim) <= 1.0e-5 * (dist + lim) + 1.0e-30)
+        flags |= TP_NEAR | TP_EXACT;
+    if ((dist - lim) < DF_EXACT_R * (dist + lim))
+        flags |= TP_EXACT;
+    tp.flags = flags;
+    df_split3(tcx, si.cx, tp.dh[0], tp.dm[0], tp.dl[0]);
+    df_split3(tcy, si.cy, tp.dh[1], tp.dm[1], tp.dl[1]);
+    df_split3(tcz, si.cz, tp.dh[2], tp.dm[2], tp.dl[2]);
     const float thr = static_cast<float>(DF_COINCIDENT_REL * lim);
     tp.thr2 = thr * thr;
 }
 
-template <int KIND, int R, bool CHECK>
+template <int KIND, int R, bool CHECK, bool EXACT>
 __device__ __forceinline__ void tile_df(const float4 *__restrict__ sp, float thr2,
-                                        const float (&T)[3][R], const float (&C)[3][R],
-                                        float (&acc)[R][6], float (&abs)[R][3])
+                                        const float (&T)[R][3], const float (&C)[R][3],
+                                        const float (&D)[R][3], float (&acc)[R][6],
+                                        float (&env)[R])
 {
 #pragma unroll 1
     for (int j = 0; j < TS_DF; ++j) {
-        const float4 *rec = sp + 5 * j;
-        const float4 a = rec[0], b = rec[1], c = rec[2], d = rec[3], e = rec[4];
+        const float4 *rec = sp + 6 * j;
+        const float4 a = rec[0], b = rec[1], c = rec[2], d = rec[3], e = rec[4], f = rec[5];
 #pragma unroll
         for (int r = 0; r < R; ++r)
-            pair_df<KIND, CHECK>(T[0][r], T[1][r], T[2][r], C[0][r], C[1][r], C[2][r], a, b, c, d,
-                                 e, thr2, acc[r], abs[r]);
+            pair_df<KIND, CHECK, EXACT>(T[r], C[r], D[r], a, b, c, d, e, f, thr2, acc[r], env[r]);
     }
 }
 
@@ -219,7 +251,7 @@ __global__ void __launch_bounds__(W * 32) pairsum_df_kernel(const PairsumParams 
     extern __shared__ __align__(128) float4 sbuf[];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int4 s_item;
-    __shared__ TilePairParams s_tp[2];
+    __shared__ DfPairParams s_tp[2];
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -269,28 +301,30 @@ __global__ void __launch_bounds__(W * 32) pairsum_df_kernel(const PairsumParams 
         if (it.x < 0)
             break;
 
-        float th[3][R], tl[3][R];
+        float th[R][3], tm[R][3], tl[R][3];   // target - c_T in three parts
         const size_t toff = static_cast<size_t>(it.x) * TT + warp * 32 * R + lane;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const float4 v = p.tpack[toff + r * 32];
-            const float4 l = p.tpack_lo[toff + r * 32];
-            th[0][r] = v.x;
-            th[1][r] = v.y;
-            th[2][r] = v.z;
-            tl[0][r] = l.x;
-            tl[1][r] = l.y;
-            tl[2][r] = l.z;
+            const float4 m = p.tpack_lo[toff + r * 32];
+            const float4 l = p.tpack_l2[toff + r * 32];
+            th[r][0] = v.x;
+            th[r][1] = v.y;
+            th[r][2] = v.z;
+            tm[r][0] = m.x;
+            tm[r][1] = m.y;
+            tm[r][2] = m.z;
+            tl[r][0] = l.x;
+            tl[r][1] = l.y;
+            tl[r][2] = l.z;
         }
-        float acc[R][6], abs[R][3];
+        float acc[R][6], env[R];   // item sums; sum of the pair envelopes
 #pragma unroll
         for (int r = 0; r < R; ++r) {
 #pragma unroll
             for (int q = 0; q < 6; ++q)
                 acc[r][q] = 0.0f;
-#pragma unroll
-            for (int q = 0; q < 3; ++q)
-                abs[r][q] = 0.0f;
+            env[r] = 0.0f;
         }
 
         const int nk = it.z - it.y;
@@ -317,17 +351,18 @@ __global__ void __launch_bounds__(W * 32) pairsum_df_kernel(const PairsumParams 
                     have_pending = true;
                 }
             }
-            const TilePairParams tp = s_tp[st];
-            // T + C = (target high + low) + (offset high + low), T a single float
-            float T[3][R], C[3][R];
-            const float dh[3] = {tp.sx, tp.sy, tp.sz}, dl[3] = {tp.lx, tp.ly, tp.lz};
+            const DfPairParams tp = s_tp[st];
+            // target rebased onto the source tile's centre: T + C + D
+            float T[R][3], C[R][3], D[R][3];
 #pragma unroll
-            for (int q = 0; q < 3; ++q)
+            for (int r = 0; r < R; ++r)
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    float e;
-                    T[q][r] = df_two_sum(th[q][r], dh[q], e);
-                    C[q][r] = fa(fa(tl[q][r], dl[q]), e);
+                for (int q = 0; q < 3; ++q) {
+                    float e1, e2, e3;
+                    T[r][q] = df_two_sum(th[r][q], tp.dh[q], e1);
+                    const float c0 = df_two_sum(tm[r][q], tp.dm[q], e2);
+                    C[r][q] = df_two_sum(c0, e1, e3);
+                    D[r][q] = fa(fa(tl[r][q], tp.dl[q]), fa(e2, e3));
                 }
             // the tile's sums start from zero and join the item's sums with a full
             // double-float addition, so rounding inside a tile stays relative to that
@@ -340,9 +375,11 @@ __global__ void __launch_bounds__(W * 32) pairsum_df_kernel(const PairsumParams 
                     tacc[r][q] = 0.0f;
             const float4 *sp = sbuf + st * STAGE;
             if (tp.flags & TP_NEAR)
-                tile_df<KIND, R, true>(sp, tp.thr2, T, C, tacc, abs);
+                tile_df<KIND, R, true, true>(sp, tp.thr2, T, C, D, tacc, env);
+            else if (tp.flags & TP_EXACT)
+                tile_df<KIND, R, false, true>(sp, tp.thr2, T, C, D, tacc, env);
             else
-                tile_df<KIND, R, false>(sp, tp.thr2, T, C, tacc, abs);
+                tile_df<KIND, R, false, false>(sp, tp.thr2, T, C, D, tacc, env);
 #pragma unroll
             for (int r = 0; r < R; ++r)
 #pragma unroll
@@ -359,9 +396,10 @@ __global__ void __launch_bounds__(W * 32) pairsum_df_kernel(const PairsumParams 
                      warp * 32 * R + lane;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            pp[r * 32] = make_float4(acc[r][0], acc[r][3], abs[r][0], 0.0f);
-            pp[TT + r * 32] = make_float4(acc[r][1], acc[r][4], abs[r][1], 0.0f);
-            pp[2 * TT + r * 32] = make_float4(acc[r][2], acc[r][5], abs[r][2], 0.0f);
+            const float bd = fm(static_cast<float>(DF_TERM_REL), env[r]);
+            pp[r * 32] = make_float4(acc[r][0], acc[r][3], bd, 0.0f);
+            pp[TT + r * 32] = make_float4(acc[r][1], acc[r][4], bd, 0.0f);
+            pp[2 * TT + r * 32] = make_float4(acc[r][2], acc[r][5], bd, 0.0f);
         }
     }
 }

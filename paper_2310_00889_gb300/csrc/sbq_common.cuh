@@ -35,17 +35,23 @@ __host__ __device__ constexpr int f32_slot(int f, int j)
     return ((f >> 1) * (TS_F32 / 2) + (j >> 1)) * 4 + (f & 1) * 2 + (j & 1);
 }
 constexpr int TS_F64 = 128;
-// Double-float tiles: TS_DF sources, five float4 per source (layout in pairsum_df.cuh).
+// Double-float tiles: TS_DF sources, six float4 per source (layout in pairsum_df.cuh).
 constexpr int TS_DF = 128;
-constexpr int DF_TILE_F4 = 5 * TS_DF;
+constexpr int DF_TILE_F4 = 6 * TS_DF;
 // Double-float path: pairs closer than this fraction of the sum of their tile radii are
 // coincident.  Centring in double-float leaves a coincident pair a few 2^-48 of that sum
 // apart; distinct nodes of any admissible discretisation are orders of magnitude farther.
 constexpr double DF_COINCIDENT_REL = 1.0e-10;
-// Bound on the relative error of one double-float pair term (against the exact term of
-// the rounded inputs): 2^-40, three times the largest error seen over random pairs and
-// every workload (each term goes through about ten double-float steps of 2^-46..2^-48).
-constexpr double DF_TERM_REL = 9.094947017729282e-13;
+// Rounding-error bound of one double-float pair term, relative to the term's envelope
+// |q|_1 ri (2 + |n'|_1 ri) (which bounds every intermediate product, cancellations
+// included): 2^-41, several times the sum of the ten or so double-float steps of
+// 2^-46..2^-48 a term goes through, r included (formed to 2^-46 of |r| or better, see
+// DF_EXACT_R).
+constexpr double DF_TERM_REL = 4.547473508864641e-13;
+// Tile pairs whose closest possible pair distance is below this fraction of (radii +
+// centre distance) form r from three-part coordinates exactly; elsewhere the two-part
+// form is within 2^-48 x 2 of |r| (each coordinate part within 2^-48 of the extent).
+constexpr double DF_EXACT_R = 0.5;
 // Compensated FP32: plain FP32 sums over runs of this many sources are merged into
 // the (hi, lo) pair with TwoSum.
 constexpr int COMP_RUN = 64;
@@ -81,6 +87,7 @@ struct PairsumParams {
     const TileInfo *stiles;     // source tile table
     const float4 *tpack;        // FP32 paths: packed targets [ttile][TT] (x - c, y - c, z - c, 0)
     const float4 *tpack_lo;     // FP32 paths: parts of the centred targets lost to rounding
+    const float4 *tpack_l2;     // double-float: third parts of the centred targets
     const TileInfo *ttiles;     // target tile table
     const double *trg;          // FP64 path: targets (SoA, stride nt)
     long long nt;               // global number of targets (stride of trg / out / diag_sigma)
@@ -215,15 +222,18 @@ cudaError_t launch_pack_src_geom(int prec, const double *src, const double *nrm,
 cudaError_t launch_pack_src_q(int prec, const double *w, const double *sigma, long long ns,
                               const TileInfo *stiles, int n_stiles, void *spack, int *counter,
                               cudaStream_t s);
+// tpack_l2 (nullable): third parts; then tpack / tpack_lo / tpack_l2 hold x - c as
+// h + m + l to about 2^-72 of |x - c|.
 cudaError_t launch_pack_trg(const double *trg, long long nt, TileInfo *ttiles, int n_ttiles,
-                            int TT, float4 *tpack, float4 *tpack_lo, cudaStream_t s);
+                            int TT, float4 *tpack, float4 *tpack_lo, float4 *tpack_l2,
+                            cudaStream_t s);
 cudaError_t launch_reduce_partials(const TileInfo *ttiles, int n_ttiles, int TT,
                                    const double *partial, long long nt, double *out,
                                    double scale, double diag, const double *diag_sigma,
                                    cudaStream_t s);
 // FP32 partial sums ((hi, lo) float pairs) of every slot of a target tile -> FP64 output.
-// comp: 0 plain FP32, 1 compensated, 2 double-float (float4 partials with a magnitude sum;
-// bound, when not null, receives |scale| * DF_TERM_REL * (sum of term magnitudes)).
+// comp: 0 plain FP32, 1 compensated, 2 double-float (float4 partials carrying each item's
+// error bound; bound, when not null, receives |scale| x the sum of the items' bounds).
 cudaError_t launch_reduce_partials_f32(const TileInfo *ttiles, int n_ttiles, int TT,
                                        const void *partial, long long nt, double *out,
                                        double scale, double diag, const double *diag_sigma,
