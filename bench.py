@@ -77,7 +77,7 @@ def parse():
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the Arnoldi steps from the host instead of the CUDA graph "
                          "(profilers cannot resolve kernels inside graphs with while nodes)")
-    ap.add_argument("--kernel-only", default=None, choices=["fp32c", "fp32", "fp64"],
+    ap.add_argument("--kernel-only", default=None, choices=["fp32c", "fp32", "fp64", "df32"],
                     help="only time operator applies of this precision on the workload "
                          "(inside an NVTX range 'kernel_only', for profilers)")
     return ap.parse_args()
