@@ -2,7 +2,10 @@
 // handle management, dispatch to the engine.
 #include "engine.h"
 
+#include <algorithm>
 #include <cmath>
+#include <utility>
+#include <vector>
 #include <new>
 
 namespace sbq {
@@ -66,6 +69,126 @@ int apply_generic(int64_t ns, const double *src, const double *nrm, const double
                            kind == KIND_CF ? kappa : 1.0, ns, s));
     SBQ_TRY(build_trg_set(ts, kind, prec, default_tune(prec, nt), sp, toff, trg, nt, soff, s));
     SBQ_TRY(run_pairsum(kind, prec, sp, ts, w, sigma, ns, trg, nt, u, scale, kappa, 0.0, nullptr, s));
+    return SBQ_OK;
+}
+
+// Recursive coordinate bisection of the nodes [b, e): split at the median of the longest
+// bounding-box axis, at a multiple of 256 nodes (128 at the last level), so that every
+// aligned block of 128 or 256 nodes is one subtree: a compact patch of the surface.
+static void rcb_order(const std::vector<double> &hx, long long n, int *b, int *e)
+{
+    const long long m = e - b;
+    if (m <= 128)
+        return;
+    double mn[3], mx[3];
+    for (int c = 0; c < 3; ++c) {
+        mn[c] = INFINITY;
+        mx[c] = -INFINITY;
+    }
+    for (int *p = b; p < e; ++p)
+        for (int c = 0; c < 3; ++c) {
+            mn[c] = std::min(mn[c], hx[c * n + *p]);
+            mx[c] = std::max(mx[c], hx[c * n + *p]);
+        }
+    int ax = 0;
+    for (int c = 1; c < 3; ++c)
+        if (mx[c] - mn[c] > mx[ax] - mn[ax])
+            ax = c;
+    const long long unit = m > 256 ? 256 : 128;
+    long long half = std::llround(0.5 * static_cast<double>(m) / unit) * unit;
+    half = std::max(half, unit);
+    if (half >= m)
+        half = m - unit;
+    std::nth_element(b, b + half, e,
+                     [&](int i, int j) { return hx[ax * n + i] < hx[ax * n + j]; });
+    rcb_order(hx, n, b, b + half);
+    rcb_order(hx, n, b + half, e);
+}
+
+// Mean bounding radius (about the bounding-box midpoint) of the blocks of 256 consecutive
+// nodes of order[a..b).
+static double mean_tile_radius(const std::vector<double> &hx, long long n, const int *order,
+                               long long cnt)
+{
+    double sum = 0.0;
+    long long tiles = 0;
+    for (long long t = 0; t < cnt; t += 256) {
+        const long long te = std::min(cnt, t + 256);
+        double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (long long k = t; k < te; ++k)
+            for (int c = 0; c < 3; ++c) {
+                mn[c] = std::min(mn[c], hx[c * n + order[k]]);
+                mx[c] = std::max(mx[c], hx[c * n + order[k]]);
+            }
+        double r2 = 0.0;
+        for (long long k = t; k < te; ++k) {
+            double d2 = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                const double d = hx[c * n + order[k]] - 0.5 * (mn[c] + mx[c]);
+                d2 += d * d;
+            }
+            r2 = std::max(r2, d2);
+        }
+        sum += std::sqrt(r2);
+        ++tiles;
+    }
+    return tiles ? sum / tiles : 0.0;
+}
+
+// Internal node order of an operator: within each segment, either the caller's order or a
+// recursive coordinate bisection of the nodes, whichever makes the smaller tiles (mean
+// bounding radius of blocks of 256).  Consecutive caller nodes are often compact already
+// (rings of a thin tube); on a fat tube a block of 256 nodes is a full ring as wide as the
+// tube, and bisection turns it into a compact patch.  Small tiles have small bounding
+// spheres: fewer tile pairs need the near-field treatment (coincidence test, high/low or
+// exact differences).  The operator keeps its geometry in the internal order and
+// perm[k] = the caller's index of internal node k; the density pack gathers through perm
+// and the reductions scatter through it, so callers never see the internal order.
+static int internal_order(Op *op, const double *src, const double *nrm, const double *w)
+{
+    const long long n = op->n;
+    std::vector<double> hx(3 * n), hn(3 * n), hw(n);
+    cudaError_t e = cudaMemcpy(hx.data(), src, 3 * n * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(hn.data(), nrm, 3 * n * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(hw.data(), w, n * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return cuda_status(e, "cudaMemcpy (operator geometry)");
+    for (double v : hx)
+        if (!std::isfinite(v))
+            return fail(SBQ_EINVAL, "non-finite source coordinate");
+    std::vector<int> perm(n), alt;
+    for (long long k = 0; k < n; ++k)
+        perm[k] = static_cast<int>(k);
+    for (int sgi = 0; sgi < op->plan.nseg; ++sgi) {
+        const long long a = op->plan.src_off[sgi], b = op->plan.src_off[sgi + 1];
+        if (b - a <= 256)
+            continue;
+        alt.assign(perm.begin() + a, perm.begin() + b);
+        rcb_order(hx, n, alt.data(), alt.data() + alt.size());
+        if (mean_tile_radius(hx, n, alt.data(), b - a) <
+            mean_tile_radius(hx, n, perm.data() + a, b - a))
+            std::copy(alt.begin(), alt.end(), perm.begin() + a);
+    }
+    std::vector<double> px(3 * n), pn(3 * n), pw(n);
+    for (long long k = 0; k < n; ++k) {
+        const long long u = perm[k];
+        for (int c = 0; c < 3; ++c) {
+            px[c * n + k] = hx[c * n + u];
+            pn[c * n + k] = hn[c * n + u];
+        }
+        pw[k] = hw[u];
+    }
+    e = cudaMemcpy(op->src.p, px.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(op->nrm.p, pn.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(op->w.p, pw.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(op->perm.p, perm.data(), n * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess)
+        return cuda_status(e, "cudaMemcpy (operator geometry)");
     return SBQ_OK;
 }
 
@@ -210,14 +333,9 @@ SBQ_API int stokes_op_create(int64_t n, const double *src, const double *nrm, co
     if ((st = op->src.alloc(vb)) != SBQ_OK) return bail(st);
     if ((st = op->nrm.alloc(vb)) != SBQ_OK) return bail(st);
     if ((st = op->w.alloc(static_cast<size_t>(n) * sizeof(double))) != SBQ_OK) return bail(st);
-    if (n > 0) {
-        cudaError_t e = cudaMemcpy(op->src.p, src, vb, cudaMemcpyDeviceToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(op->nrm.p, nrm, vb, cudaMemcpyDeviceToDevice);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(op->w.p, w, static_cast<size_t>(n) * sizeof(double),
-                           cudaMemcpyDeviceToDevice);
-        if (e != cudaSuccess) return bail(cuda_status(e, "cudaMemcpy (operator geometry)"));
-    }
+    if ((st = op->perm.alloc(static_cast<size_t>(n) * sizeof(int))) != SBQ_OK) return bail(st);
+    if (n > 0 && (st = internal_order(op, src, nrm, w)) != SBQ_OK)
+        return bail(st);
     if (nnz > 0) {
         if ((st = op->rowptr.alloc((3 * static_cast<size_t>(n) + 1) * sizeof(int64_t))) != SBQ_OK)
             return bail(st);

@@ -352,7 +352,7 @@ PairsumTiming *&pairsum_timing()
 int run_pairsum(int kind, int prec, const SrcPack &sp, const TrgSet &ts, const double *w,
                 const double *sigma, long long ns, const double *trg, long long nt, double *out,
                 double scale, double kappa, double diag, const double *diag_sigma, cudaStream_t s,
-                double *bound)
+                double *bound, const int *perm)
 {
     if (ts.n_items == 0)
         return SBQ_OK;
@@ -362,7 +362,7 @@ int run_pairsum(int kind, int prec, const SrcPack &sp, const TrgSet &ts, const d
         return SBQ_ENOMEM;
     }
     SBQ_CUDA(launch_pack_src_q(prec, w, sigma, ns, sp.stiles.as<TileInfo>(), sp.n_stiles, sp.spack.p,
-                               ts.counter.as<int>(), s));
+                               ts.counter.as<int>(), perm, s));
     PairsumParams p{};
     p.spack = sp.spack.p;
     p.stiles = sp.stiles.as<TileInfo>();
@@ -379,6 +379,7 @@ int run_pairsum(int kind, int prec, const SrcPack &sp, const TrgSet &ts, const d
     p.out = out;
     p.partial = ts.partial.as<double>();
     p.diag_sigma = diag_sigma;
+    p.perm = perm;
     p.diag = diag;
     p.scale = scale;
     p.kappa = kappa;
@@ -393,11 +394,11 @@ int run_pairsum(int kind, int prec, const SrcPack &sp, const TrgSet &ts, const d
         SBQ_CUDA(launch_reduce_partials_f32(ts.ttiles.as<TileInfo>(), ts.n_ttiles, ts.TT,
                                             ts.partial.p, nt, out, scale, diag, diag_sigma,
                                             prec == SBQ_FP32_COMP ? 1 : (prec == SBQ_DF32 ? 2 : 0),
-                                            prec == SBQ_DF32 ? bound : nullptr, s));
+                                            prec == SBQ_DF32 ? bound : nullptr, perm, s));
     else if (ts.needs_reduce)
         SBQ_CUDA(launch_reduce_partials(ts.ttiles.as<TileInfo>(), ts.n_ttiles, ts.TT,
                                         ts.partial.as<double>(), nt, out, scale, diag, diag_sigma,
-                                        s));
+                                        perm, s));
     return SBQ_OK;
 }
 
@@ -612,7 +613,7 @@ int op_matvec(Op *op, const double *sigma, double *out, int prec, cudaStream_t s
         return SBQ_OK;
     SBQ_TRY(run_pairsum(kind, prec, op_srcpack(op, prec), *op->ts[prec], op->w.as<double>(), sigma,
                         n, op->src.as<double>(), n, out, scale, kappa, op->diag, sigma, s,
-                        bound));
+                        bound, op->perm.as<int>()));
     if (op->nnz > 0)
         SBQ_CUDA(launch_csr_apply(3 * n, op->rowptr.as<int64_t>(), op->col.as<int64_t>(),
                                   op->val.as<double>(), sigma, out, s));

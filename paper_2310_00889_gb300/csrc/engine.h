@@ -71,7 +71,8 @@ struct Op {
     long long n = 0;
     double eta = 0.0, diag = 0.5;
     long long nnz = 0;
-    DevBuf src, nrm, w;                // library copies (SoA)
+    DevBuf src, nrm, w;                // library copies (SoA), in the internal node order
+    DevBuf perm;                       // int: caller's index of each internal node
     DevBuf rowptr, col, val;           // CSR correction
     PlanH plan;                        // segments (one segment if none given)
     SrcPack sp32, sp64, spdf;          // FP32 (plain and compensated), FP64, double-float
@@ -98,10 +99,13 @@ PairsumTiming *&pairsum_timing();
 
 // One pair-sum apply: out = scale * sum(...) [+ diag * diag_sigma].
 // bound (double-float only, nullable): per output entry, a bound on its rounding error.
+// perm (nullable): the sources and targets are the same nodes in an internal order, perm
+// gives each internal node's index in the caller's order (sigma, diag_sigma, out and bound
+// are in the caller's order).
 int run_pairsum(int kind, int prec, const SrcPack &sp, const TrgSet &ts, const double *w,
                 const double *sigma, long long ns, const double *trg, long long nt, double *out,
                 double scale, double kappa, double diag, const double *diag_sigma, cudaStream_t s,
-                double *bound = nullptr);
+                double *bound = nullptr, const int *perm = nullptr);
 
 // Operator pieces used by the solver.
 int op_matvec(Op *op, const double *sigma, double *out, int prec, cudaStream_t s,

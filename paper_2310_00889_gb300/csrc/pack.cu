@@ -167,7 +167,7 @@ __global__ void pack_src_geom_f64(const double *__restrict__ src, const double *
 
 __global__ void pack_src_q_f32(const double *__restrict__ w, const double *__restrict__ sigma,
                                long long ns, const TileInfo *__restrict__ stiles, float4 *spack,
-                               int *counter)
+                               int *counter, const int *__restrict__ perm)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0 && counter)
         *counter = 0;
@@ -177,10 +177,11 @@ __global__ void pack_src_q_f32(const double *__restrict__ w, const double *__res
     float qx = 0.0f, qy = 0.0f, qz = 0.0f;
     if (j < count) {
         const long long s = begin + j;
+        const long long u = perm ? perm[s] : s;   // caller's index of internal node s
         const double ww = w[s];
-        qx = static_cast<float>(ww * sigma[s]);
-        qy = static_cast<float>(ww * sigma[ns + s]);
-        qz = static_cast<float>(ww * sigma[2 * ns + s]);
+        qx = static_cast<float>(ww * sigma[u]);
+        qy = static_cast<float>(ww * sigma[ns + u]);
+        qz = static_cast<float>(ww * sigma[2 * ns + u]);
     }
     float *tile = reinterpret_cast<float *>(spack + static_cast<size_t>(k) * F32_TILE_F4);
     tile[f32_slot(FQX, j)] = qx;
@@ -190,7 +191,7 @@ __global__ void pack_src_q_f32(const double *__restrict__ w, const double *__res
 
 __global__ void pack_src_q_f64(const double *__restrict__ w, const double *__restrict__ sigma,
                                long long ns, const TileInfo *__restrict__ stiles, double *spack,
-                               int *counter)
+                               int *counter, const int *__restrict__ perm)
 {
     constexpr int TS = TS_F64;
     if (blockIdx.x == 0 && threadIdx.x == 0 && counter)
@@ -202,10 +203,11 @@ __global__ void pack_src_q_f64(const double *__restrict__ w, const double *__res
     double qx = 0.0, qy = 0.0, qz = 0.0;
     if (j < count) {
         const long long s = begin + j;
+        const long long u = perm ? perm[s] : s;
         const double ww = w[s];
-        qx = ww * sigma[s];
-        qy = ww * sigma[ns + s];
-        qz = ww * sigma[2 * ns + s];
+        qx = ww * sigma[u];
+        qy = ww * sigma[ns + u];
+        qz = ww * sigma[2 * ns + u];
     }
     tile[3 * TS + j] = qx;
     tile[4 * TS + j] = qy;
@@ -284,8 +286,8 @@ __global__ void pack_src_geom_df(const double *__restrict__ src, const double *_
 }
 
 __global__ void pack_src_q_df(const double *__restrict__ w, const double *__restrict__ sigma,
-                              long long ns, const TileInfo *__restrict__ stiles, float4 *spack,
-                              int *counter)
+                               long long ns, const TileInfo *__restrict__ stiles, float4 *spack,
+                               int *counter, const int *__restrict__ perm)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0 && counter)
         *counter = 0;
@@ -295,10 +297,11 @@ __global__ void pack_src_q_df(const double *__restrict__ w, const double *__rest
     float qh[3] = {0.0f, 0.0f, 0.0f}, ql[3] = {0.0f, 0.0f, 0.0f}, qn = 0.0f;
     if (j < count) {
         const long long s = begin + j;
+        const long long u = perm ? perm[s] : s;
         const double ww = w[s];
         double a = 0.0;
         for (int c = 0; c < 3; ++c) {
-            const double q = ww * sigma[c * ns + s];
+            const double q = ww * sigma[c * ns + u];
             split_df(q, qh[c], ql[c]);
             a += fabs(q);
         }
@@ -351,13 +354,15 @@ __global__ void pack_trg_f32(const double *__restrict__ trg, long long nt, TileI
 __global__ void reduce_partials_kernel(const TileInfo *__restrict__ ttiles, int TT,
                                        const double *__restrict__ partial, long long nt,
                                        double *out, double scale, double diag,
-                                       const double *__restrict__ diag_sigma)
+                                       const double *__restrict__ diag_sigma,
+                                       const int *__restrict__ perm)
 {
     const TileInfo ti = ttiles[blockIdx.x];
     if (ti.slot_begin < 0)
         return;
     for (int loc = threadIdx.x; loc < ti.count; loc += blockDim.x) {
-        const long long t = ti.begin + loc;
+        const long long t0 = ti.begin + loc;
+        const long long t = perm ? perm[t0] : t0;   // caller's index of internal target t0
         for (int c = 0; c < 3; ++c) {
             double s = 0.0;
             for (int q = 0; q < ti.slot_count; ++q)
@@ -391,13 +396,14 @@ __global__ void reduce_partials_f32_kernel(const TileInfo *__restrict__ ttiles, 
                                            const float2 *__restrict__ partial, long long nt,
                                            double *out, double scale, double diag,
                                            const double *__restrict__ diag_sigma, int comp,
-                                           double *bound)
+                                           double *bound, const int *__restrict__ perm)
 {
     const TileInfo ti = ttiles[blockIdx.x];
     const int c = blockIdx.y;
     const int nq = ti.slot_count;
     for (int loc = threadIdx.x; loc < ti.count; loc += blockDim.x) {
-        const long long t = ti.begin + loc;
+        const long long t0 = ti.begin + loc;
+        const long long t = perm ? perm[t0] : t0;
         const float2 *pp = partial + (static_cast<size_t>(ti.slot_begin) * 3 + c) * TT + loc;
         const size_t qs = static_cast<size_t>(3) * TT;   // stride between slots
         if (comp == 2) {
@@ -473,19 +479,22 @@ cudaError_t launch_pack_src_geom(int prec, const double *src, const double *nrm,
 
 cudaError_t launch_pack_src_q(int prec, const double *w, const double *sigma, long long ns,
                               const TileInfo *stiles, int n_stiles, void *spack, int *counter,
-                              cudaStream_t s)
+                              const int *perm, cudaStream_t s)
 {
     if (n_stiles <= 0)
         return cudaSuccess;
     if (prec == SBQ_FP64)
         pack_src_q_f64<<<n_stiles, TS_F64, 0, s>>>(w, sigma, ns, stiles,
-                                                    static_cast<double *>(spack), counter);
+                                                    static_cast<double *>(spack), counter,
+                                                    perm);
     else if (prec == SBQ_DF32)
         pack_src_q_df<<<n_stiles, TS_DF, 0, s>>>(w, sigma, ns, stiles,
-                                                  static_cast<float4 *>(spack), counter);
+                                                  static_cast<float4 *>(spack), counter,
+                                                    perm);
     else
         pack_src_q_f32<<<n_stiles, TS_F32, 0, s>>>(w, sigma, ns, stiles,
-                                                    static_cast<float4 *>(spack), counter);
+                                                    static_cast<float4 *>(spack), counter,
+                                                    perm);
     return cudaGetLastError();
 }
 
@@ -500,26 +509,27 @@ cudaError_t launch_pack_trg(const double *trg, long long nt, TileInfo *ttiles, i
 
 cudaError_t launch_reduce_partials(const TileInfo *ttiles, int n_ttiles, int TT,
                                    const double *partial, long long nt, double *out, double scale,
-                                   double diag, const double *diag_sigma, cudaStream_t s)
+                                   double diag, const double *diag_sigma, const int *perm,
+                                   cudaStream_t s)
 {
     if (n_ttiles <= 0)
         return cudaSuccess;
     reduce_partials_kernel<<<n_ttiles, 256, 0, s>>>(ttiles, TT, partial, nt, out, scale, diag,
-                                                     diag_sigma);
+                                                     diag_sigma, perm);
     return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_partials_f32(const TileInfo *ttiles, int n_ttiles, int TT,
                                        const void *partial, long long nt, double *out,
                                        double scale, double diag, const double *diag_sigma,
-                                       int comp, double *bound, cudaStream_t s)
+                                       int comp, double *bound, const int *perm, cudaStream_t s)
 {
     if (n_ttiles <= 0)
         return cudaSuccess;
     reduce_partials_f32_kernel<<<dim3(n_ttiles, 3), 256, 0, s>>>(ttiles, TT,
                                                          static_cast<const float2 *>(partial), nt,
                                                          out, scale, diag, diag_sigma, comp,
-                                                         bound);
+                                                         bound, perm);
     return cudaGetLastError();
 }
 

@@ -567,7 +567,7 @@ __global__ void __launch_bounds__(W * 32) pairsum_f64_kernel(const PairsumParams
             const int loc = warp * 32 * R + r * 32 + lane;
             if (it.w < 0) {
                 if (loc < tt.count) {
-                    const long long t = tt.begin + loc;
+                    const long long t = p.perm ? p.perm[tt.begin + loc] : tt.begin + loc;
                     double ox = p.scale * ax[r], oy = p.scale * ay[r], oz = p.scale * az[r];
                     if (p.diag_sigma) {
                         ox += p.diag * p.diag_sigma[t];

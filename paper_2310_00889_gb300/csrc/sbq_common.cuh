@@ -99,6 +99,8 @@ struct PairsumParams {
     double *partial;            // chunk partials: FP64 [slot][3][TT] (FP64 kernel) or
                                 // float2 (hi, lo) [slot][3][TT] (FP32 kernels)
     const double *diag_sigma;   // nullable: out += diag * diag_sigma (same indexing as out)
+    const int *perm;            // nullable: caller's index of each internal target (FP64
+                                // kernel's direct output)
     double diag;
     double scale;               // prefactor applied to the accumulated sum
     double kappa;               // combined field: 6 beta / alpha (folded into the packed normals)
@@ -219,25 +221,30 @@ size_t pairsum_smem_bytes(int prec);
 cudaError_t launch_pack_src_geom(int prec, const double *src, const double *nrm, double nscale,
                                  long long ns, TileInfo *stiles, int n_stiles, void *spack,
                                  cudaStream_t s);
+// perm (nullable): caller's index of each internal node; sigma is read through it (w and
+// the tiles are in internal order).
 cudaError_t launch_pack_src_q(int prec, const double *w, const double *sigma, long long ns,
                               const TileInfo *stiles, int n_stiles, void *spack, int *counter,
-                              cudaStream_t s);
+                              const int *perm, cudaStream_t s);
 // tpack_l2 (nullable): third parts; then tpack / tpack_lo / tpack_l2 hold x - c as
 // h + m + l to about 2^-72 of |x - c|.
 cudaError_t launch_pack_trg(const double *trg, long long nt, TileInfo *ttiles, int n_ttiles,
                             int TT, float4 *tpack, float4 *tpack_lo, float4 *tpack_l2,
                             cudaStream_t s);
+// perm (nullable): out, diag_sigma and bound are indexed by the caller's index of each
+// internal target.
 cudaError_t launch_reduce_partials(const TileInfo *ttiles, int n_ttiles, int TT,
                                    const double *partial, long long nt, double *out,
                                    double scale, double diag, const double *diag_sigma,
-                                   cudaStream_t s);
+                                   const int *perm, cudaStream_t s);
 // FP32 partial sums ((hi, lo) float pairs) of every slot of a target tile -> FP64 output.
 // comp: 0 plain FP32, 1 compensated, 2 double-float (float4 partials carrying each item's
 // error bound; bound, when not null, receives |scale| x the sum of the items' bounds).
 cudaError_t launch_reduce_partials_f32(const TileInfo *ttiles, int n_ttiles, int TT,
                                        const void *partial, long long nt, double *out,
                                        double scale, double diag, const double *diag_sigma,
-                                       int comp, double *bound, cudaStream_t s);
+                                       int comp, double *bound, const int *perm,
+                                       cudaStream_t s);
 cudaError_t launch_csr_apply(long long nrows, const int64_t *rowptr, const int64_t *col,
                              const double *val, const double *x, double *y, cudaStream_t s);
 

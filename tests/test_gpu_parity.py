@@ -615,3 +615,24 @@ def test_double_float_residuals_fall_back_to_fp64(sbq, oracle_mod, small_solve):
         kx = oracle_mod.matvec(s.x, s.n, s.w, eta, _np(x))
         assert np.linalg.norm(rhs - kx) / np.linalg.norm(rhs) <= 1.05 * tol + 1e-15
     op.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c", "df32"])
+def test_node_order_is_invisible(sbq, prec):
+    """The operator reorders nodes internally (recursive bisection where it gives smaller
+    tiles); a caller who shuffles the nodes gets the same operator, shuffled: equal to the
+    unshuffled result within the precision's rounding (the summation order differs)."""
+    s = I.config2(panels=4)["surf"]
+    rng = np.random.default_rng(61)
+    p = rng.permutation(s.size)
+    sig = I.density(s.size, seed=62)
+    eta = sbq.slender_eta(0.2)
+    a = sbq.StokesOp(_t(s.x), _t(s.n), _t(s.w), eta)
+    b = sbq.StokesOp(_t(s.x[:, p]), _t(s.n[:, p]), _t(s.w[p]), eta)
+    ua = _np(a.matvec(_t(sig), prec=prec))
+    ub = _np(b.matvec(_t(sig[:, p]), prec=prec))
+    err = _relerr(ub, ua[:, p])
+    print("shuffled %s relerr %.3e" % (prec, err))
+    assert err <= {"fp64": 1e-13, "df32": 1e-11, "fp32c": 2e-6}[prec]
+    a.close()
+    b.close()
