@@ -636,3 +636,48 @@ def test_node_order_is_invisible(sbq, prec):
     assert err <= {"fp64": 1e-13, "df32": 1e-11, "fp32c": 2e-6}[prec]
     a.close()
     b.close()
+
+
+def test_batch_with_empty_segment(sbq, oracle_mod):
+    """A batch plan whose middle segment is empty: the operator apply equals the two
+    non-empty segments applied alone, the per-body correction skips the empty body, and a
+    batched mixed solve (double-float residuals) meets the tolerance on both segments."""
+    import torch
+    segs = [I.capped_arc_pipe(5.0, a, 1.0, k, 8, 16, 8) for a, k in ((0.8, 2), (1.6, 3))]
+    off = [0, segs[0].size, segs[0].size, segs[0].size + segs[1].size]
+    X = np.concatenate([g.x for g in segs], axis=1)
+    Nn = np.concatenate([g.n for g in segs], axis=1)
+    W = np.concatenate([g.w for g in segs])
+    eta = sbq.slender_eta(0.2)
+    corr = sbq.dl_gauss_correction(_t(X), _t(Nn), _t(W), off, prec="fp64")
+    op = sbq.StokesOp(_t(X), _t(Nn), _t(W), eta, correction=corr, plan=sbq.BatchPlan(off))
+    sig = I.density(off[-1], seed=71)
+    out = _np(op.matvec(_t(sig), prec="fp64"))
+    rhs = I.density(off[-1], seed=72)
+    x, rep = op.solve(_t(rhs), tol=1e-10, restart=100, inner_prec="fp32c", resid_prec="df32")
+    assert rep["status"] == 0, rep
+    xs = _np(x)
+    for i, (a, b) in enumerate(((off[0], off[1]), (off[2], off[3]))):
+        g = segs[i]
+        E = oracle_mod.dl_gauss_correction(g.x, g.n, g.w)
+        ref = oracle_mod.matvec(g.x, g.n, g.w, eta, sig[:, a:b], E=E)
+        assert _relerr(out[:, a:b], ref) <= TOL_F64
+        r = rhs[:, a:b] - oracle_mod.matvec(g.x, g.n, g.w, eta, xs[:, a:b], E=E)
+        assert np.linalg.norm(r) / np.linalg.norm(rhs[:, a:b]) <= 1.05e-10
+    op.close()
+
+
+def test_solve_from_host_with_correction(sbq, oracle_mod):
+    """End-to-end call from pinned host tensors (copies, correction, operator, solve, copy
+    back): the returned x meets the tolerance against the oracle operator."""
+    import torch
+    c = I.config2(panels=2, nth=32, nr=8)
+    s = c["surf"]
+    eta = sbq.slender_eta(0.2)
+    h = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
+    x, rep = sbq.solve_from_host(h(s.x), h(s.n), h(s.w), h(c["rhs"]), eta, tol=1e-10,
+                                 correction="df32", resid_prec="df32")
+    assert not x.is_cuda and rep["status"] == 0
+    E = oracle_mod.dl_gauss_correction(s.x, s.n, s.w)
+    r = c["rhs"] - oracle_mod.matvec(s.x, s.n, s.w, eta, x.numpy(), E=E)
+    assert np.linalg.norm(r) / np.linalg.norm(c["rhs"]) <= 1.05e-10
