@@ -196,6 +196,29 @@ SBQ_API int batch_plan(int nseg, const int64_t *seg_src_off, const int64_t *seg_
                        const sbq_tune *tune, void **plan_out);
 
 /*
+ * Laplace layer potentials (Sec. 4.1; the scalar problem the paper studies first):
+ *   laplace_sl_apply        u_t = sum_{y_s != x_t} G(x_t - y_s) w_s sigma_s,  G(r) = 1/(4 pi |r|)
+ *   laplace_dl_apply        u_t = sum_{y_s != x_t} dG/dn_y w_s sigma_s
+ *                                = sum ((x_t - y_s).n_s) / (4 pi |x_t - y_s|^3) w_s sigma_s
+ *                           (the double layer of a constant density is -1 inside a closed
+ *                           surface with outward normals, 0 outside)
+ *   laplace_combined_apply  alpha S + beta D in one pass (Eq. laplace-bie-rep-new uses
+ *                           alpha = 1/(2 eps log(1/eps)), beta = 1)
+ * Same conventions as the Stokes applies, with SCALAR densities and outputs: sigma holds ns
+ * doubles, u holds nt doubles (overwritten).  Precisions, coincident-pair skipping, errors:
+ * as stokes_sl_apply.
+ */
+SBQ_API int laplace_sl_apply(int64_t ns, const double *src, const double *w, const double *sigma,
+                             int64_t nt, const double *trg, double *u, int prec, void *stream);
+SBQ_API int laplace_dl_apply(int64_t ns, const double *src, const double *nrm, const double *w,
+                             const double *sigma, int64_t nt, const double *trg, double *u,
+                             int prec, void *stream);
+SBQ_API int laplace_combined_apply(int64_t ns, const double *src, const double *nrm,
+                                   const double *w, const double *sigma, int64_t nt,
+                                   const double *trg, double alpha, double beta, double *u,
+                                   int prec, void *stream);
+
+/*
  * Combined-field operator on the surface nodes (targets = sources):
  *   K sigma = diag sigma + (D + eta S)[sigma] + E sigma           Eq. stokes-bie-new
  * with the uncorrected pair sums and an optional sparse correction E (FP64 CSR over

@@ -11,6 +11,7 @@ Contents
     sparse correction apply, the combined-field operator K = diag I + D + eta S + E
     (paper Sec. 3.2.1 Eq. nystrom-no-correction / nystrom-correction,
     Eqs. stokes-sl / stokes-dl / stokes-bie-new);
+  * `laplace`: the Laplace single / double layer / combined field (Sec. 4.1), scalar;
   * `dense_operator`: the same kernels written a second time with numpy, as an
     explicit 3N x 3N matrix, for tiny systems;
   * `gmres`: restarted GMRES(m) with classical Gram--Schmidt applied twice and
@@ -66,6 +67,8 @@ def _load():
             lib.oracle_stokes_matvec.argtypes = [_i64, _d, _d, _d, ctypes.c_double,
                                                  ctypes.c_double, _i64, _i64p, _i64p, _d,
                                                  _d, _d]
+            lib.oracle_laplace_combined.argtypes = [_i64, _d, _d, _d, _d, _i64, _d,
+                                                    ctypes.c_double, ctypes.c_double, _d]
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -132,6 +135,25 @@ def combined_extended(src, nrm, w, sigma, trg, alpha, beta):
             u += ld(beta) * 3 / (4 * pi) * np.sum(r * (rn * rq / (r2 * r2 * rl)), axis=1)
         out[:, t] = u
     return out
+
+
+def laplace(src, nrm, w, sigma, trg, alpha, beta):
+    """Laplace u = sum_s (alpha G + beta dG/dn_y)(x_t, y_s) w_s sigma_s over y_s != x_t, scalar
+    sigma (ns,) and u (nt,) (paper Sec. 4.1; double-layer sign in stokes_oracle.c)."""
+    lib = _load()
+    src = _c(src)
+    ns = src.shape[1]
+    trg = _c(trg)
+    nt = trg.shape[1]
+    w = _c(w, (ns,))
+    sigma = _c(sigma, (ns,))
+    nrm = _c(nrm, (3, ns)) if nrm is not None else None
+    if beta != 0.0 and nrm is None:
+        raise ValueError("double layer needs normals")
+    u = np.empty(nt)
+    lib.oracle_laplace_combined(ns, _p(src), _p(nrm), _p(w), _p(sigma), nt, _p(trg),
+                                float(alpha), float(beta), _p(u))
+    return u
 
 
 def sl(src, w, sigma, trg):

@@ -148,6 +148,40 @@ void oracle_stokes_matvec(int64_t n, const double *src, const double *nrm, const
         oracle_csr_apply(3 * n, rowptr, col, val, sigma, out);
 }
 
+/*
+ * Laplace (paper Sec. 4.1): single layer G(r) = 1/(4 pi |r|), double layer
+ * dG/dn_y = ((x - y) . n_y) / (4 pi |x - y|^3) (the double layer of a constant is -1
+ * inside a closed surface with outward normals, 0 outside: consistent with the interior
+ * Green's representation u = S[du/dn] - D[u] of Eq. greens-rep).
+ *   u(x_t) = sum_{s : y_s != x_t} (alpha G + beta dG/dn_y) w_s sigma_s,  scalar sigma and u.
+ */
+void oracle_laplace_combined(int64_t ns, const double *src, const double *nrm, const double *w,
+                             const double *sigma, int64_t nt, const double *trg, double alpha,
+                             double beta, double *u)
+{
+    int64_t t;
+#pragma omp parallel for schedule(static)
+    for (t = 0; t < nt; ++t) {
+        const double x[3] = {trg[t], trg[nt + t], trg[2 * nt + t]};
+        double acc = 0.0;
+        for (int64_t s = 0; s < ns; ++s) {
+            const double r[3] = {x[0] - src[s], x[1] - src[ns + s], x[2] - src[2 * ns + s]};
+            if (r[0] == 0.0 && r[1] == 0.0 && r[2] == 0.0)
+                continue;
+            const double rl = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+            double g = 0.0;
+            if (alpha != 0.0)
+                g += alpha / (4.0 * ORACLE_PI * rl);
+            if (beta != 0.0) {
+                const double rn = r[0] * nrm[s] + r[1] * nrm[ns + s] + r[2] * nrm[2 * ns + s];
+                g += beta * rn / (4.0 * ORACLE_PI * rl * rl * rl);
+            }
+            acc += g * w[s] * sigma[s];
+        }
+        u[t] = acc;
+    }
+}
+
 int oracle_num_threads(void)
 {
     int n = 1;

@@ -33,7 +33,7 @@ int fail(int code, const std::string &msg)
 // Generic apply: u = alpha S[sigma] + beta D[sigma] at the targets.
 int apply_generic(int64_t ns, const double *src, const double *nrm, const double *w,
                   const double *sigma, int64_t nt, const double *trg, double alpha, double beta,
-                  double *u, int prec, void *stream)
+                  double *u, int prec, void *stream, bool laplace = false)
 {
     clear_error();
     if (ns < 0 || nt < 0)
@@ -53,20 +53,24 @@ int apply_generic(int64_t ns, const double *src, const double *nrm, const double
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (nt == 0)
         return SBQ_OK;
+    const size_t ncomp = laplace ? 1 : 3;
     if (ns == 0 || (alpha == 0.0 && beta == 0.0)) {
-        SBQ_CUDA(cudaMemsetAsync(u, 0, 3 * static_cast<size_t>(nt) * sizeof(double), s));
+        SBQ_CUDA(cudaMemsetAsync(u, 0, ncomp * static_cast<size_t>(nt) * sizeof(double), s));
         return SBQ_OK;
     }
     int kind;
     double scale, kappa;
-    kind_and_scale(alpha, beta, &kind, &scale, &kappa);
+    if (laplace)
+        laplace_kind_and_scale(alpha, beta, &kind, &scale, &kappa);
+    else
+        kind_and_scale(alpha, beta, &kind, &scale, &kappa);
     const int layout = (prec == SBQ_FP64 || prec == SBQ_DF32) ? prec : SBQ_FP32;
     AsyncAllocScope scope(s);
     SrcPack sp;
     TrgSet ts;
     std::vector<int64_t> soff = {0, ns}, toff = {0, nt};
-    SBQ_TRY(build_src_pack(sp, layout, soff, src, kind == KIND_SL ? nullptr : nrm,
-                           kind == KIND_CF ? kappa : 1.0, ns, s));
+    SBQ_TRY(build_src_pack(sp, layout, soff, src, kind_has_normals(kind) ? nrm : nullptr,
+                           (kind == KIND_CF || kind == KIND_LCF) ? kappa : 1.0, ns, s));
     SBQ_TRY(build_trg_set(ts, kind, prec, default_tune(prec, nt), sp, toff, trg, nt, soff, s));
     SBQ_TRY(run_pairsum(kind, prec, sp, ts, w, sigma, ns, trg, nt, u, scale, kappa, 0.0, nullptr, s));
     return SBQ_OK;
@@ -244,6 +248,27 @@ SBQ_API int stokes_combined_apply(int64_t ns, const double *src, const double *n
                                   int prec, void *stream)
 {
     return apply_generic(ns, src, nrm, w, sigma, nt, trg, alpha, beta, u, prec, stream);
+}
+
+SBQ_API int laplace_sl_apply(int64_t ns, const double *src, const double *w, const double *sigma,
+                             int64_t nt, const double *trg, double *u, int prec, void *stream)
+{
+    return apply_generic(ns, src, nullptr, w, sigma, nt, trg, 1.0, 0.0, u, prec, stream, true);
+}
+
+SBQ_API int laplace_dl_apply(int64_t ns, const double *src, const double *nrm, const double *w,
+                             const double *sigma, int64_t nt, const double *trg, double *u,
+                             int prec, void *stream)
+{
+    return apply_generic(ns, src, nrm, w, sigma, nt, trg, 0.0, 1.0, u, prec, stream, true);
+}
+
+SBQ_API int laplace_combined_apply(int64_t ns, const double *src, const double *nrm,
+                                   const double *w, const double *sigma, int64_t nt,
+                                   const double *trg, double alpha, double beta, double *u,
+                                   int prec, void *stream)
+{
+    return apply_generic(ns, src, nrm, w, sigma, nt, trg, alpha, beta, u, prec, stream, true);
 }
 
 SBQ_API int batch_plan(int nseg, const int64_t *seg_src_off, const int64_t *seg_trg_off,

@@ -131,6 +131,23 @@ Op::~Op()
 // ---------------------------------------------------------------------------
 static const double kPi = 3.14159265358979323846264338327950288;
 
+void laplace_kind_and_scale(double alpha, double beta, int *kind, double *scale, double *kappa)
+{
+    // alpha S + beta D with S = 1/(4 pi |r|), D = (r.n_y)/(4 pi |r|^3).
+    *kappa = 0.0;
+    if (beta == 0.0) {
+        *kind = KIND_LSL;
+        *scale = alpha / (4.0 * kPi);
+    } else if (alpha == 0.0) {
+        *kind = KIND_LDL;
+        *scale = beta / (4.0 * kPi);
+    } else {
+        *kind = KIND_LCF;
+        *scale = alpha / (4.0 * kPi);
+        *kappa = beta / alpha;
+    }
+}
+
 void kind_and_scale(double alpha, double beta, int *kind, double *scale, double *kappa)
 {
     // alpha S + beta D with S = (1/8pi)(...), D = (3/4pi)(...).
@@ -361,8 +378,9 @@ int run_pairsum(int kind, int prec, const SrcPack &sp, const TrgSet &ts, const d
         set_error("cannot allocate the device error word");
         return SBQ_ENOMEM;
     }
+    const int ncomp = kind_laplace(kind) ? 1 : 3;
     SBQ_CUDA(launch_pack_src_q(prec, w, sigma, ns, sp.stiles.as<TileInfo>(), sp.n_stiles, sp.spack.p,
-                               ts.counter.as<int>(), perm, s));
+                               ts.counter.as<int>(), perm, ncomp == 1, s));
     PairsumParams p{};
     p.spack = sp.spack.p;
     p.stiles = sp.stiles.as<TileInfo>();
@@ -380,6 +398,7 @@ int run_pairsum(int kind, int prec, const SrcPack &sp, const TrgSet &ts, const d
     p.partial = ts.partial.as<double>();
     p.diag_sigma = diag_sigma;
     p.perm = perm;
+    p.ncomp = ncomp;
     p.diag = diag;
     p.scale = scale;
     p.kappa = kappa;
@@ -394,11 +413,11 @@ int run_pairsum(int kind, int prec, const SrcPack &sp, const TrgSet &ts, const d
         SBQ_CUDA(launch_reduce_partials_f32(ts.ttiles.as<TileInfo>(), ts.n_ttiles, ts.TT,
                                             ts.partial.p, nt, out, scale, diag, diag_sigma,
                                             prec == SBQ_FP32_COMP ? 1 : (prec == SBQ_DF32 ? 2 : 0),
-                                            prec == SBQ_DF32 ? bound : nullptr, perm, s));
+                                            prec == SBQ_DF32 ? bound : nullptr, perm, ncomp, s));
     else if (ts.needs_reduce)
         SBQ_CUDA(launch_reduce_partials(ts.ttiles.as<TileInfo>(), ts.n_ttiles, ts.TT,
                                         ts.partial.as<double>(), nt, out, scale, diag, diag_sigma,
-                                        perm, s));
+                                        perm, ncomp, s));
     return SBQ_OK;
 }
 

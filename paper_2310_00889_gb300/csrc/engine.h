@@ -113,8 +113,9 @@ int op_matvec(Op *op, const double *sigma, double *out, int prec, cudaStream_t s
 int op_ensure_tuned(Op *op, int prec, cudaStream_t s);
 int op_kernels_per_matvec(const Op *op, int prec);
 
-// Kind and prefactors of alpha S + beta D.
+// Kind and prefactors of alpha S + beta D (Stokes; Laplace).
 void kind_and_scale(double alpha, double beta, int *kind, double *scale, double *kappa);
+void laplace_kind_and_scale(double alpha, double beta, int *kind, double *scale, double *kappa);
 
 sbq_tune default_tune(int prec, long long nt);
 

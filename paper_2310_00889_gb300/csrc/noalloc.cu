@@ -213,7 +213,7 @@ extern "C" SBQ_API int stokes_sl_apply_noalloc(int64_t ns, const double *src, co
                                   n_st, b8 + L.spack, s));
     int *counter = reinterpret_cast<int *>(b8 + L.counter);
     SBQ_CUDA(launch_pack_src_q(prec == SBQ_FP64 ? SBQ_FP64 : SBQ_FP32, w, sigma, ns, stiles, n_st,
-                               b8 + L.spack, counter, nullptr, s));
+                               b8 + L.spack, counter, nullptr, 0, s));
     if (prec != SBQ_FP64)
         SBQ_CUDA(launch_pack_trg(trg, nt, ttiles, n_tt, TT, reinterpret_cast<float4 *>(b8 + L.tpack),
                                  prec == SBQ_FP32_COMP ? reinterpret_cast<float4 *>(b8 + L.tpack_lo)
@@ -245,9 +245,9 @@ extern "C" SBQ_API int stokes_sl_apply_noalloc(int64_t ns, const double *src, co
     SBQ_CUDA(launch_pairsum(kind, prec, R, W, grid, p, s));
     if (prec != SBQ_FP64)
         SBQ_CUDA(launch_reduce_partials_f32(ttiles, n_tt, TT, p.partial, nt, u, scale, 0.0, nullptr,
-                                            prec == SBQ_FP32_COMP ? 1 : 0, nullptr, nullptr, s));
+                                            prec == SBQ_FP32_COMP ? 1 : 0, nullptr, nullptr, 3, s));
     else if (n_chunks > 1)
         SBQ_CUDA(launch_reduce_partials(ttiles, n_tt, TT, p.partial, nt, u, scale, 0.0, nullptr,
-                                        nullptr, s));
+                                        nullptr, 3, s));
     return SBQ_OK;
 }

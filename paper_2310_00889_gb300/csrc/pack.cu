@@ -167,7 +167,7 @@ __global__ void pack_src_geom_f64(const double *__restrict__ src, const double *
 
 __global__ void pack_src_q_f32(const double *__restrict__ w, const double *__restrict__ sigma,
                                long long ns, const TileInfo *__restrict__ stiles, float4 *spack,
-                               int *counter, const int *__restrict__ perm)
+                               int *counter, const int *__restrict__ perm, int scalar)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0 && counter)
         *counter = 0;
@@ -180,8 +180,10 @@ __global__ void pack_src_q_f32(const double *__restrict__ w, const double *__res
         const long long u = perm ? perm[s] : s;   // caller's index of internal node s
         const double ww = w[s];
         qx = static_cast<float>(ww * sigma[u]);
-        qy = static_cast<float>(ww * sigma[ns + u]);
-        qz = static_cast<float>(ww * sigma[2 * ns + u]);
+        if (!scalar) {   // scalar (Laplace) densities: one component, in qx
+            qy = static_cast<float>(ww * sigma[ns + u]);
+            qz = static_cast<float>(ww * sigma[2 * ns + u]);
+        }
     }
     float *tile = reinterpret_cast<float *>(spack + static_cast<size_t>(k) * F32_TILE_F4);
     tile[f32_slot(FQX, j)] = qx;
@@ -191,7 +193,7 @@ __global__ void pack_src_q_f32(const double *__restrict__ w, const double *__res
 
 __global__ void pack_src_q_f64(const double *__restrict__ w, const double *__restrict__ sigma,
                                long long ns, const TileInfo *__restrict__ stiles, double *spack,
-                               int *counter, const int *__restrict__ perm)
+                               int *counter, const int *__restrict__ perm, int scalar)
 {
     constexpr int TS = TS_F64;
     if (blockIdx.x == 0 && threadIdx.x == 0 && counter)
@@ -206,8 +208,10 @@ __global__ void pack_src_q_f64(const double *__restrict__ w, const double *__res
         const long long u = perm ? perm[s] : s;
         const double ww = w[s];
         qx = ww * sigma[u];
-        qy = ww * sigma[ns + u];
-        qz = ww * sigma[2 * ns + u];
+        if (!scalar) {
+            qy = ww * sigma[ns + u];
+            qz = ww * sigma[2 * ns + u];
+        }
     }
     tile[3 * TS + j] = qx;
     tile[4 * TS + j] = qy;
@@ -287,7 +291,7 @@ __global__ void pack_src_geom_df(const double *__restrict__ src, const double *_
 
 __global__ void pack_src_q_df(const double *__restrict__ w, const double *__restrict__ sigma,
                                long long ns, const TileInfo *__restrict__ stiles, float4 *spack,
-                               int *counter, const int *__restrict__ perm)
+                               int *counter, const int *__restrict__ perm, int scalar)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0 && counter)
         *counter = 0;
@@ -300,7 +304,7 @@ __global__ void pack_src_q_df(const double *__restrict__ w, const double *__rest
         const long long u = perm ? perm[s] : s;
         const double ww = w[s];
         double a = 0.0;
-        for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < (scalar ? 1 : 3); ++c) {
             const double q = ww * sigma[c * ns + u];
             split_df(q, qh[c], ql[c]);
             a += fabs(q);
@@ -355,7 +359,7 @@ __global__ void reduce_partials_kernel(const TileInfo *__restrict__ ttiles, int 
                                        const double *__restrict__ partial, long long nt,
                                        double *out, double scale, double diag,
                                        const double *__restrict__ diag_sigma,
-                                       const int *__restrict__ perm)
+                                       const int *__restrict__ perm, int ncomp)
 {
     const TileInfo ti = ttiles[blockIdx.x];
     if (ti.slot_begin < 0)
@@ -363,7 +367,7 @@ __global__ void reduce_partials_kernel(const TileInfo *__restrict__ ttiles, int 
     for (int loc = threadIdx.x; loc < ti.count; loc += blockDim.x) {
         const long long t0 = ti.begin + loc;
         const long long t = perm ? perm[t0] : t0;   // caller's index of internal target t0
-        for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < ncomp; ++c) {
             double s = 0.0;
             for (int q = 0; q < ti.slot_count; ++q)
                 s += partial[(static_cast<size_t>(ti.slot_begin + q) * 3 + c) * TT + loc];
@@ -479,22 +483,22 @@ cudaError_t launch_pack_src_geom(int prec, const double *src, const double *nrm,
 
 cudaError_t launch_pack_src_q(int prec, const double *w, const double *sigma, long long ns,
                               const TileInfo *stiles, int n_stiles, void *spack, int *counter,
-                              const int *perm, cudaStream_t s)
+                              const int *perm, int scalar, cudaStream_t s)
 {
     if (n_stiles <= 0)
         return cudaSuccess;
     if (prec == SBQ_FP64)
         pack_src_q_f64<<<n_stiles, TS_F64, 0, s>>>(w, sigma, ns, stiles,
                                                     static_cast<double *>(spack), counter,
-                                                    perm);
+                                                    perm, scalar);
     else if (prec == SBQ_DF32)
         pack_src_q_df<<<n_stiles, TS_DF, 0, s>>>(w, sigma, ns, stiles,
                                                   static_cast<float4 *>(spack), counter,
-                                                    perm);
+                                                    perm, scalar);
     else
         pack_src_q_f32<<<n_stiles, TS_F32, 0, s>>>(w, sigma, ns, stiles,
                                                     static_cast<float4 *>(spack), counter,
-                                                    perm);
+                                                    perm, scalar);
     return cudaGetLastError();
 }
 
@@ -510,23 +514,24 @@ cudaError_t launch_pack_trg(const double *trg, long long nt, TileInfo *ttiles, i
 cudaError_t launch_reduce_partials(const TileInfo *ttiles, int n_ttiles, int TT,
                                    const double *partial, long long nt, double *out, double scale,
                                    double diag, const double *diag_sigma, const int *perm,
-                                   cudaStream_t s)
+                                   int ncomp, cudaStream_t s)
 {
     if (n_ttiles <= 0)
         return cudaSuccess;
     reduce_partials_kernel<<<n_ttiles, 256, 0, s>>>(ttiles, TT, partial, nt, out, scale, diag,
-                                                     diag_sigma, perm);
+                                                     diag_sigma, perm, ncomp);
     return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_partials_f32(const TileInfo *ttiles, int n_ttiles, int TT,
                                        const void *partial, long long nt, double *out,
                                        double scale, double diag, const double *diag_sigma,
-                                       int comp, double *bound, const int *perm, cudaStream_t s)
+                                       int comp, double *bound, const int *perm, int ncomp,
+                                       cudaStream_t s)
 {
     if (n_ttiles <= 0)
         return cudaSuccess;
-    reduce_partials_f32_kernel<<<dim3(n_ttiles, 3), 256, 0, s>>>(ttiles, TT,
+    reduce_partials_f32_kernel<<<dim3(n_ttiles, ncomp), 256, 0, s>>>(ttiles, TT,
                                                          static_cast<const float2 *>(partial), nt,
                                                          out, scale, diag, diag_sigma, comp,
                                                          bound, perm);
@@ -559,6 +564,9 @@ cudaError_t launch_pairsum(int kind, int prec, int R, int W, int grid, const Pai
     case KIND_SL: return launch_pairsum_sl(prec, R, W, grid, p, s);
     case KIND_DL: return launch_pairsum_dl(prec, R, W, grid, p, s);
     case KIND_CF: return launch_pairsum_cf(prec, R, W, grid, p, s);
+    case KIND_LSL:
+    case KIND_LDL:
+    case KIND_LCF: return launch_pairsum_laplace(kind, prec, R, W, grid, p, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -569,6 +577,9 @@ int pairsum_blocks_per_sm(int kind, int prec, int R, int W)
     case KIND_SL: return occupancy_pairsum_sl(prec, R, W);
     case KIND_DL: return occupancy_pairsum_dl(prec, R, W);
     case KIND_CF: return occupancy_pairsum_cf(prec, R, W);
+    case KIND_LSL:
+    case KIND_LDL:
+    case KIND_LCF: return occupancy_pairsum_laplace(kind, prec, R, W);
     default: return 0;
     }
 }

@@ -98,7 +98,9 @@ __device__ __forceinline__ void df_acc(float &hi, float &lo, dfl t)
 // centre, see above); source record a..f (layout above).  Accumulates the same folded
 // kernels as the FP32 and FP64 paths:
 //   SL: ri q + (r.q) ri^3 r;  DL: (r.q)(r.n) ri^5 r;  CF: ri q + (r.q) ri^3 (1 + (r.n') ri^2) r
-// and the pair's envelope into env (see the error bound above).
+//   Laplace (scalar q): LSL ri q, LDL (r.n) ri^3 q, LCF ri q (1 + (r.n') ri^2)
+// and the pair's envelope into env (see the error bound above; Laplace: |q| ri,
+// |q| |n| ri^2, |q| ri (1 + |n| ri)).
 template <int KIND, bool CHECK, bool EXACT>
 __device__ __forceinline__ void pair_df(const float (&T)[3], const float (&C)[3],
                                         const float (&D)[3], const float4 a, const float4 b,
@@ -148,6 +150,28 @@ __device__ __forceinline__ void pair_df(const float (&T)[3], const float (&C)[3]
     const dfl ri2 = {yy, ff(fa(y, y), ri.l, yl)};
     const dfl ri3 = df_mul(ri2, ri);
     const dfl qx = {a.w, d.x}, qy = {b.x, d.y}, qz = {b.y, d.z};
+    if (kind_laplace(KIND)) {   // scalar q in qx, one output component
+        dfl tq;
+        if (KIND == KIND_LSL) {
+            tq = ri;
+            env = ff(e.z, y, env);
+        } else {
+            const dfl nx = {b.z, d.w}, ny = {b.w, e.x}, nz = {c.x, e.y};
+            const dfl rn = df_norm(df_add(df_add(df_mul(rx, nx), df_mul(ry, ny)), df_mul(rz, nz)));
+            if (KIND == KIND_LDL) {
+                tq = df_mul(rn, ri3);
+                env = ff(fm(e.z, e.w), yy, env);
+            } else {
+                const dfl m = df_mul(rn, ri2);
+                float eg;
+                const float gh = df_two_sum(1.0f, m.h, eg);
+                tq = df_mul(ri, df_norm({gh, fa(eg, m.l)}));
+                env = ff(fm(e.z, y), ff(e.w, y, 1.0f), env);
+            }
+        }
+        df_acc(acc[0], acc[3], df_mul(tq, qx));
+        return;
+    }
     const dfl rq = df_norm(df_add(df_add(df_mul(rx, qx), df_mul(ry, qy)), df_mul(rz, qz)));
     dfl bc;
     if (KIND == KIND_SL) {

@@ -83,6 +83,7 @@ __device__ __forceinline__ void f2_unpack(f2 v, float &lo, float &hi)
 //   SL: ri q + (r.q) ri^3 r
 //   DL: (r.q)(r.n) ri^5 r
 //   CF: ri q + (r.q) ri^3 (1 + (r.n') ri^2) r,  n' = kappa n stored by the pack
+//   Laplace (scalar q): LSL ri q, LDL (r.n) ri^3 q, LCF ri q (1 + (r.n') ri^2)
 template <int KIND, bool CHECK>
 __device__ __forceinline__ void pair2(f2 dx, f2 dy, f2 dz, f2 QX, f2 QY, f2 QZ, f2 NX, f2 NY, f2 NZ,
                                       float thr2, f2 &ax, f2 &ay, f2 &az)
@@ -112,7 +113,7 @@ __device__ __forceinline__ void pair2(f2 dx, f2 dy, f2 dz, f2 QX, f2 QY, f2 QZ, 
         ax = f2_fma(b, dx, ax);
         ay = f2_fma(b, dy, ay);
         az = f2_fma(b, dz, az);
-    } else {
+    } else if (KIND == KIND_CF) {
         const f2 one = f2_pack(1.0f, 1.0f);
         const f2 rn = f2_fma(dx, NX, f2_fma(dy, NY, f2_mul(dz, NZ)));
         const f2 g = f2_fma(rn, ri2, one);
@@ -123,6 +124,15 @@ __device__ __forceinline__ void pair2(f2 dx, f2 dy, f2 dz, f2 QX, f2 QY, f2 QZ, 
         ax = f2_fma(b, dx, ax);
         ay = f2_fma(b, dy, ay);
         az = f2_fma(b, dz, az);
+    } else if (KIND == KIND_LSL) {   // Laplace: scalar q in QX, sum in ax
+        ax = f2_fma(ri, QX, ax);
+    } else if (KIND == KIND_LDL) {
+        const f2 rn = f2_fma(dx, NX, f2_fma(dy, NY, f2_mul(dz, NZ)));
+        ax = f2_fma(f2_mul(rn, f2_mul(ri2, ri)), QX, ax);
+    } else {                         // KIND_LCF: ri q (1 + (r.n') ri^2), n' = kappa n
+        const f2 one = f2_pack(1.0f, 1.0f);
+        const f2 rn = f2_fma(dx, NX, f2_fma(dy, NY, f2_mul(dz, NZ)));
+        ax = f2_fma(f2_mul(ri, f2_fma(rn, ri2, one)), QX, ax);
     }
 }
 
@@ -187,9 +197,9 @@ __device__ __forceinline__ void tile_f32(const float4 *__restrict__ sp, float th
             const ulonglong2 a1 = s2[H + m];       // Z, QX
             const ulonglong2 a2 = s2[2 * H + m];   // QY, QZ
             ulonglong2 b0, b1, b2;
-            if (KIND != KIND_SL || HILO)
+            if (kind_has_normals(KIND) || HILO)
                 b1 = s2[4 * H + m];                // NZ, LX
-            if (KIND != KIND_SL)
+            if (kind_has_normals(KIND))
                 b0 = s2[3 * H + m];                // NX, NY
             if (HILO)
                 b2 = s2[5 * H + m];                // LY, LZ
@@ -284,7 +294,8 @@ __global__ void __launch_bounds__(W * 32) pairsum_f32_kernel(const PairsumParams
     constexpr int TS = TS_F32;
     // blocks of TS/2 float4 to copy: SL {X,Y} {Z,QX} {QY,QZ}; DL/CF add {NX,NY} {NZ,LX};
     // compensated kernels also need {LY,LZ} (and LX)
-    constexpr int NB = COMP ? F32_TILE_BLOCKS : ((KIND == KIND_SL) ? 3 : 5);
+    constexpr int NB = COMP ? F32_TILE_BLOCKS
+                            : ((KIND == KIND_SL || KIND == KIND_LSL) ? 3 : 5);
     constexpr uint32_t TILE_BYTES = NB * (TS / 2) * sizeof(float4);
     constexpr int STAGE = F32_TILE_BLOCKS * (TS / 2);   // float4 per smem stage
     constexpr int GSTRIDE = F32_TILE_BLOCKS * (TS / 2); // float4 per packed tile
@@ -458,6 +469,14 @@ __device__ __forceinline__ void pair_f64(double x, double y, double z, const dou
         ax = fma(b, dx, ax);
         ay = fma(b, dy, ay);
         az = fma(b, dz, az);
+    } else if (KIND == KIND_LSL) {
+        ax = fma(ri, qx, ax);
+    } else if (KIND == KIND_LDL || KIND == KIND_LCF) {
+        const double rn = fma(dx, s[6 * TS + j], fma(dy, s[7 * TS + j], dz * s[8 * TS + j]));
+        if (KIND == KIND_LDL)
+            ax = fma(rn * (ri2 * ri), qx, ax);
+        else
+            ax = fma(ri * fma(rn, ri2, 1.0), qx, ax);
     } else {
         const double rn = fma(dx, s[6 * TS + j], fma(dy, s[7 * TS + j], dz * s[8 * TS + j]));
         if (KIND == KIND_DL) {
@@ -484,7 +503,7 @@ __global__ void __launch_bounds__(W * 32) pairsum_f64_kernel(const PairsumParams
     constexpr int NT = W * 32;
     constexpr int TT = NT * R;
     constexpr int TS = TS_F64;
-    constexpr int NF = (KIND == KIND_SL) ? 6 : 9;
+    constexpr int NF = (KIND == KIND_SL || KIND == KIND_LSL) ? 6 : 9;
     constexpr uint32_t TILE_BYTES = NF * TS * sizeof(double);
     constexpr int STAGE = 9 * TS;   // doubles per stage (and per packed tile)
 
@@ -569,6 +588,12 @@ __global__ void __launch_bounds__(W * 32) pairsum_f64_kernel(const PairsumParams
                 if (loc < tt.count) {
                     const long long t = p.perm ? p.perm[tt.begin + loc] : tt.begin + loc;
                     double ox = p.scale * ax[r], oy = p.scale * ay[r], oz = p.scale * az[r];
+                    if (kind_laplace(KIND)) {
+                        if (p.diag_sigma)
+                            ox += p.diag * p.diag_sigma[t];
+                        p.out[t] = ox;
+                        continue;
+                    }
                     if (p.diag_sigma) {
                         ox += p.diag * p.diag_sigma[t];
                         oy += p.diag * p.diag_sigma[p.nt + t];

@@ -13,9 +13,16 @@
 
 namespace sbq {
 
-// Pair-sum kernel kinds: single layer, double layer, combined field
-// (paper Eqs. stokes-sl, stokes-dl, stokes-bie-new).
-enum Kind { KIND_SL = 0, KIND_DL = 1, KIND_CF = 2 };
+// Pair-sum kernel kinds: Stokes single layer, double layer, combined field
+// (paper Eqs. stokes-sl, stokes-dl, stokes-bie-new) and the Laplace ones (Sec. 4.1: kernels
+// G = 1/(4 pi |r|) and dG/dn_y, combined field of Eq. laplace-bie-rep-new).  Laplace kinds
+// carry a scalar density in the first charge component and produce one output component.
+enum Kind { KIND_SL = 0, KIND_DL = 1, KIND_CF = 2, KIND_LSL = 3, KIND_LDL = 4, KIND_LCF = 5 };
+__host__ __device__ constexpr bool kind_laplace(int k) { return k >= KIND_LSL; }
+__host__ __device__ constexpr bool kind_has_normals(int k)
+{
+    return k == KIND_DL || k == KIND_CF || k == KIND_LDL || k == KIND_LCF;
+}
 
 // Sources per shared-memory tile.
 // FP32 tiles store every field as packed pairs (value of source 2m, value of source 2m+1)
@@ -101,6 +108,7 @@ struct PairsumParams {
     const double *diag_sigma;   // nullable: out += diag * diag_sigma (same indexing as out)
     const int *perm;            // nullable: caller's index of each internal target (FP64
                                 // kernel's direct output)
+    int ncomp;                  // output components: 3 (Stokes) or 1 (Laplace)
     double diag;
     double scale;               // prefactor applied to the accumulated sum
     double kappa;               // combined field: 6 beta / alpha (folded into the packed normals)
@@ -212,6 +220,10 @@ int *device_error_word();   // per-device error word (allocated once per device)
 // Return cudaErrorInvalidValue for an unsupported (R, W).
 cudaError_t launch_pairsum(int kind, int prec, int R, int W, int grid, const PairsumParams &p,
                            cudaStream_t s);
+// pairsum_laplace.cu
+cudaError_t launch_pairsum_laplace(int kind, int prec, int R, int W, int grid,
+                                   const PairsumParams &p, cudaStream_t s);
+int occupancy_pairsum_laplace(int kind, int prec, int R, int W);
 int pairsum_blocks_per_sm(int kind, int prec, int R, int W);
 bool pairsum_shape_supported(int prec, int R, int W);
 size_t pairsum_smem_bytes(int prec);
@@ -225,7 +237,7 @@ cudaError_t launch_pack_src_geom(int prec, const double *src, const double *nrm,
 // the tiles are in internal order).
 cudaError_t launch_pack_src_q(int prec, const double *w, const double *sigma, long long ns,
                               const TileInfo *stiles, int n_stiles, void *spack, int *counter,
-                              const int *perm, cudaStream_t s);
+                              const int *perm, int scalar, cudaStream_t s);
 // tpack_l2 (nullable): third parts; then tpack / tpack_lo / tpack_l2 hold x - c as
 // h + m + l to about 2^-72 of |x - c|.
 cudaError_t launch_pack_trg(const double *trg, long long nt, TileInfo *ttiles, int n_ttiles,
@@ -236,14 +248,14 @@ cudaError_t launch_pack_trg(const double *trg, long long nt, TileInfo *ttiles, i
 cudaError_t launch_reduce_partials(const TileInfo *ttiles, int n_ttiles, int TT,
                                    const double *partial, long long nt, double *out,
                                    double scale, double diag, const double *diag_sigma,
-                                   const int *perm, cudaStream_t s);
+                                   const int *perm, int ncomp, cudaStream_t s);
 // FP32 partial sums ((hi, lo) float pairs) of every slot of a target tile -> FP64 output.
 // comp: 0 plain FP32, 1 compensated, 2 double-float (float4 partials carrying each item's
 // error bound; bound, when not null, receives |scale| x the sum of the items' bounds).
 cudaError_t launch_reduce_partials_f32(const TileInfo *ttiles, int n_ttiles, int TT,
                                        const void *partial, long long nt, double *out,
                                        double scale, double diag, const double *diag_sigma,
-                                       int comp, double *bound, const int *perm,
+                                       int comp, double *bound, const int *perm, int ncomp,
                                        cudaStream_t s);
 cudaError_t launch_csr_apply(long long nrows, const int64_t *rowptr, const int64_t *col,
                              const double *val, const double *x, double *y, cudaStream_t s);

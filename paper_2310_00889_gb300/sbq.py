@@ -84,6 +84,10 @@ def _load():
         "stokes_dl_apply": ([_i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _int, _vp], _int),
         "stokes_combined_apply": ([_i64, _vp, _vp, _vp, _vp, _i64, _vp, _dbl, _dbl, _vp, _int,
                                    _vp], _int),
+        "laplace_sl_apply": ([_i64, _vp, _vp, _vp, _i64, _vp, _vp, _int, _vp], _int),
+        "laplace_dl_apply": ([_i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _int, _vp], _int),
+        "laplace_combined_apply": ([_i64, _vp, _vp, _vp, _vp, _i64, _vp, _dbl, _dbl, _vp, _int,
+                                    _vp], _int),
         "batch_plan": ([_int, _vp, _vp, _vp, ctypes.POINTER(_vp)], _int),
         "stokes_op_create": ([_i64, _vp, _vp, _vp, _dbl, _dbl, _i64, _vp, _vp, _vp, _vp,
                               ctypes.POINTER(_vp)], _int),
@@ -224,6 +228,35 @@ def dl_gauss_correction(src, nrm, w, body_off=None, prec="fp64", stream=None):
                                           _prec(prec), _ptr(rowptr), _ptr(col), _ptr(val),
                                           _stream(stream)))
     return rowptr, col, val
+
+
+def laplace_apply(src, nrm, w, sigma, trg, alpha=1.0, beta=0.0, prec="fp32c", out=None,
+                  stream=None):
+    """Laplace alpha S[sigma] + beta D[sigma] at trg (Sec. 4.1), scalar sigma (ns,) -> (nt,)."""
+    ns = src.shape[1]
+    nt = trg.shape[1]
+    _dev(src, (3, ns), "src")
+    _dev(w, (ns,), "w")
+    _dev(sigma, (ns,), "sigma")
+    _dev(trg, (3, nt), "trg")
+    if nrm is not None:
+        _dev(nrm, (3, ns), "nrm")
+    if out is None:
+        out = torch.empty((nt,), dtype=torch.float64, device=trg.device)
+    _dev(out, (nt,), "out")
+    p, st = _prec(prec), _stream(stream)
+    if beta == 0.0:
+        _check(lib.laplace_sl_apply(ns, _ptr(src), _ptr(w), _ptr(sigma), nt, _ptr(trg), _ptr(out),
+                                    p, st) if alpha == 1.0 else
+               lib.laplace_combined_apply(ns, _ptr(src), _ptr(nrm), _ptr(w), _ptr(sigma), nt,
+                                          _ptr(trg), float(alpha), 0.0, _ptr(out), p, st))
+    elif alpha == 0.0 and beta == 1.0:
+        _check(lib.laplace_dl_apply(ns, _ptr(src), _ptr(nrm), _ptr(w), _ptr(sigma), nt, _ptr(trg),
+                                    _ptr(out), p, st))
+    else:
+        _check(lib.laplace_combined_apply(ns, _ptr(src), _ptr(nrm), _ptr(w), _ptr(sigma), nt,
+                                          _ptr(trg), float(alpha), float(beta), _ptr(out), p, st))
+    return out
 
 
 def check_device(stream=None):

@@ -406,3 +406,66 @@ def test_gauss_correction_bounds_gmres_iterations(oracle_mod):
             its[(name, s.size)] = info["iters"]
     assert its[("corrected", 3072)] <= 60 and its[("corrected", 768)] <= 50
     assert its[("punctured", 3072)] > 2 * its[("corrected", 3072)]
+
+
+# ---------------------------------------------------------------------------
+# Laplace layer potentials (Sec. 4.1) and the torus Green's-identity test (Eq. greens-rep)
+# ---------------------------------------------------------------------------
+
+def _torus_green_data(t, x0):
+    r = t.x - x0[:, None]
+    rl = np.linalg.norm(r, axis=0)
+    u = 1.0 / (4 * np.pi * rl)
+    dudn = -np.sum(r * t.n, axis=0) / (4 * np.pi * rl ** 3)
+    return u, dudn
+
+
+def test_laplace_sphere_closed_forms(oracle_mod):
+    """Unit density on a sphere of radius a: single layer a inside, a^2/|x - c| outside;
+    double layer -1 inside, 0 outside (Gauss).  A wrong 1/(4 pi), power of |r| or sign of
+    the double layer fails here; spectrally accurate at 40 x 60 nodes."""
+    a, c = 0.7, np.array([0.1, 0.2, 0.3])
+    sp = I.sphere(a, c, 40, 60)
+    one = np.ones(sp.size)
+    inn = c[:, None] + np.array([[0.1, -0.2, 0.05], [0.0, 0.3, -0.2]]).T
+    out = c[:, None] + np.array([[1.5, 0.2, 0.1], [-0.3, 0.9, 1.2]]).T
+    assert np.abs(oracle_mod.laplace(sp.x, None, sp.w, one, inn, 1.0, 0.0) - a).max() < 1e-13
+    ext = a ** 2 / np.linalg.norm(out - c[:, None], axis=0)
+    assert np.abs(oracle_mod.laplace(sp.x, None, sp.w, one, out, 1.0, 0.0) - ext).max() < 1e-13
+    assert np.abs(oracle_mod.laplace(sp.x, sp.n, sp.w, one, inn, 0.0, 1.0) + 1.0).max() < 1e-13
+    assert np.abs(oracle_mod.laplace(sp.x, sp.n, sp.w, one, out, 0.0, 1.0)).max() < 1e-13
+
+
+def test_laplace_torus_green_identity(oracle_mod):
+    """The paper's quadrature test (Eq. greens-rep): u = G(x - x0) for a point charge x0
+    outside a torus (R = 1, radius 0.25); inside the tube S[du/dn] - D[u] = u (spectral
+    convergence: below 1e-10 at 16384 nodes), and on the surface with the punctured sums
+    u/2 + S[du/dn] - D[u] -> u at first order (halving h nearly halves the error)."""
+    x0 = np.array([1.0, 0.0, 0.45])
+    phi = np.linspace(0, 2 * np.pi, 7)[:-1]
+    xin = np.stack([np.cos(phi), np.sin(phi), 0.05 * np.ones_like(phi)])
+    g_in = 1.0 / (4 * np.pi * np.linalg.norm(xin - x0[:, None], axis=0))
+    e_in, e_on = [], []
+    for panels, nth in ((8, 16), (16, 32), (32, 64)):
+        t = I.torus(1.0, 0.25, panels, 8, nth)
+        u, dudn = _torus_green_data(t, x0)
+        lhs = (oracle_mod.laplace(t.x, None, t.w, dudn, xin, 1.0, 0.0)
+               - oracle_mod.laplace(t.x, t.n, t.w, u, xin, 0.0, 1.0))
+        e_in.append(np.abs(lhs - g_in).max() / np.abs(g_in).max())
+        on = (0.5 * u + oracle_mod.laplace(t.x, None, t.w, dudn, t.x, 1.0, 0.0)
+              - oracle_mod.laplace(t.x, t.n, t.w, u, t.x, 0.0, 1.0))
+        e_on.append(np.abs(on - u).max() / np.abs(u).max())
+    assert e_in[2] < 1e-10 and e_in[1] < 1e-6 and e_in[0] > e_in[1] > e_in[2]
+    assert 0.45 < e_on[1] / e_on[0] < 0.7 and 0.45 < e_on[2] / e_on[1] < 0.7
+
+
+def test_laplace_combined_is_linear(oracle_mod):
+    """alpha S + beta D in one pass equals the two layers combined."""
+    c = I.config1()
+    s = c["surf"]
+    sig = c["sigma"][0]
+    trg = c["trg"][:, ::11]
+    uc = oracle_mod.laplace(s.x, s.n, s.w, sig, trg, 2.5, -0.75)
+    us = oracle_mod.laplace(s.x, None, s.w, sig, trg, 1.0, 0.0)
+    ud = oracle_mod.laplace(s.x, s.n, s.w, sig, trg, 0.0, 1.0)
+    assert np.abs(uc - (2.5 * us - 0.75 * ud)).max() <= 1e-13 * np.abs(uc).max()
