@@ -61,7 +61,7 @@ def parse():
                     help="solve with the punctured sums alone (no double-layer singularity "
                          "subtraction)")
     ap.add_argument("--workload", default="curved_pipe",
-                    choices=["curved_pipe", "precision_sweep", "batch", "helix"],
+                    choices=["curved_pipe", "precision_sweep", "batch", "helix", "laplace"],
                     help="curved_pipe: the benchmark line (default); precision_sweep: FP32 vs "
                          "compensated FP32 vs FP64 pair sums on random loops of 64K/256K/1M "
                          "nodes; batch: 64 independent capped arcs in one persistent launch")
@@ -549,11 +549,11 @@ def run_precision_sweep(args):
         sig = t(c["sigma"])
         out = {}
         times = {}
-        for prec in ("fp32c", "fp32", "fp64"):
+        for prec in ("fp32c", "fp32", "df32", "fp64"):
             op.autotune(prec) if prec != "fp64" or n <= 300000 else None
             o = torch.empty_like(sig)
-            times[prec] = _cuda_timer(lambda: op.matvec(sig, prec=prec, out=o),
-                                      1 if prec == "fp64" else 5, stream)
+            reps = 1 if prec == "fp64" or (prec == "df32" and n > 300000) else 5
+            times[prec] = _cuda_timer(lambda: op.matvec(sig, prec=prec, out=o), reps, stream)
             out[prec] = o
         u64 = out["fp64"]
         rows = c["sub"]
@@ -563,7 +563,7 @@ def run_precision_sweep(args):
         line = {"workload": "precision_sweep_random_loop", "nodes": n, "panels": panels,
                 "eta": eta, "pairs": float(n) * n, "oracle_rows": int(len(rows)),
                 "oracle_seconds": t_or, "oracle_cores": oracle.num_threads()}
-        for prec in ("fp64", "fp32", "fp32c"):
+        for prec in ("fp64", "df32", "fp32", "fp32c"):
             u = out[prec]
             e_full = float(((u - u64).abs().max() / u64.abs().max()).item())
             un = u[:, torch.as_tensor(rows, device="cuda")].cpu().numpy()
@@ -781,6 +781,75 @@ def run_helix(args):
     return 0
 
 
+def run_laplace(args):
+    """Laplace combined field (paper Sec. 4.1, eta = 1/(2 eps log(1/eps)), eps = 0.01) on
+    random slender loops of 65,536 and 262,144 nodes: time of every precision's apply (CUDA
+    events), error against the FP64 oracle on 1024 sampled rows; and the torus
+    Green's-identity test (Eq. greens-rep) inside the tube under refinement."""
+    import torch
+    import oracle
+    from paper_2310_00889_gb300 import build as b
+    b.build()
+    oracle.build()
+    from paper_2310_00889_gb300 import inputs as I
+    from paper_2310_00889_gb300 import sbq
+    torch.cuda.set_device(0)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+    eta = sbq.slender_eta(0.01)
+    flops_lcf = 19
+    info = sbq.device_info()
+    peak = info["sms"] * info["fp32_lanes_per_sm"] * 2 * 2070.0e6 / 1e12
+    for panels in (512, 2048):
+        s = I.random_loop(seed=1, panels=panels, ns=8, nth=16)
+        n = s.size
+        sig = I.density(n, seed=2)[0]
+        src, nrm, w, sg = t(s.x), t(s.n), t(s.w), t(sig)
+        rows = np.sort(np.random.default_rng(3).choice(n, 1024, replace=False))
+        ref = oracle.laplace(s.x, s.n, s.w, sig, s.x[:, rows], eta, 1.0)
+        out = torch.empty(n, dtype=torch.float64, device="cuda")
+        res = {}
+        for prec in ("fp32c", "fp32", "df32", "fp64"):
+            sbq.laplace_apply(src, nrm, w, sg, src, eta, 1.0, prec=prec, out=out)
+            torch.cuda.synchronize()
+            reps = 3 if prec != "fp64" else 1
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                sbq.laplace_apply(src, nrm, w, sg, src, eta, 1.0, prec=prec, out=out)
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            u = out.cpu().numpy()[rows]
+            res[prec] = {"ms": ms, "pairs_per_s": n * n / (ms * 1e-3),
+                         "relerr_vs_oracle_1024_rows":
+                             float(np.abs(u - ref).max() / np.abs(ref).max())}
+        res["fp32c"]["tflops"] = flops_lcf * n * n / (res["fp32c"]["ms"] * 1e-3) / 1e12
+        res["fp32c"]["frac_of_fp32_peak"] = res["fp32c"]["tflops"] / peak
+        print(json.dumps({"workload": "laplace_combined_random_loop", "nodes": n, "eta": eta,
+                          "flops_per_pair": flops_lcf, "apply": res,
+                          "timing": "CUDA events around the whole apply (pack, kernel, "
+                                    "reduction), temporary packs included"}), flush=True)
+    green = []
+    x0 = np.array([1.0, 0.0, 0.45])
+    phi = np.linspace(0, 2 * np.pi, 7)[:-1]
+    xin = np.stack([np.cos(phi), np.sin(phi), 0.05 * np.ones_like(phi)])
+    g_in = 1.0 / (4 * np.pi * np.linalg.norm(xin - x0[:, None], axis=0))
+    for panels, nth in ((8, 16), (16, 32), (32, 64), (64, 128)):
+        tor = I.torus(1.0, 0.25, panels, 8, nth)
+        r = tor.x - x0[:, None]
+        rl = np.linalg.norm(r, axis=0)
+        u = 1.0 / (4 * np.pi * rl)
+        dudn = -np.sum(r * tor.n, axis=0) / (4 * np.pi * rl ** 3)
+        sp = sbq.laplace_apply(t(tor.x), None, t(tor.w), t(dudn), t(xin), 1.0, 0.0, prec="fp64")
+        dp = sbq.laplace_apply(t(tor.x), t(tor.n), t(tor.w), t(u), t(xin), 0.0, 1.0, prec="fp64")
+        err = float(np.abs(sp.cpu().numpy() - dp.cpu().numpy() - g_in).max() / np.abs(g_in).max())
+        green.append({"nodes": tor.size, "interior_relerr": err})
+    print(json.dumps({"workload": "laplace_torus_green_identity", "R": 1.0, "radius": 0.25,
+                      "charge": x0.tolist(), "refinement": green}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.workload == "helix" and args.impl != "reference":
@@ -791,6 +860,8 @@ def main():
         return run_precision_sweep(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "laplace":
+        return run_laplace(args)
     return run_gpu(args)
 
 
