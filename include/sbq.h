@@ -262,7 +262,22 @@ SBQ_API int stokes_dl_gauss_correction(int nbody, const int64_t *body_off, const
                                        int64_t *rowptr, int64_t *col, double *val,
                                        void *stream);
 
-/* out = K sigma (device arrays of 3*n doubles) in precision prec, on `stream`. */
+/*
+ * Laplace combined-field operator on the surface nodes (Eq. laplace-bie-new; eta = 1/(2 eps
+ * log(1/eps)) for slender bodies):
+ *   K sigma = diag sigma + (D + eta S)[sigma] + E sigma,  scalar sigma (n doubles)
+ * with the Laplace layers of laplace_combined_apply.  Same arguments and ownership as
+ * stokes_op_create, with the CSR correction over n rows (rowptr[n+1]).  stokes_matvec,
+ * stokes_matvec_bounded, gmres_solve, sbq_autotune and sbq_destroy take the handle; their
+ * vectors then hold n doubles.
+ */
+SBQ_API int laplace_op_create(int64_t n, const double *src, const double *nrm, const double *w,
+                              double eta, double diag, int64_t nnz, const int64_t *rowptr,
+                              const int64_t *col, const double *val, const void *plan,
+                              void **op_out);
+
+/* out = K sigma (device arrays of 3*n doubles; n for a Laplace operator) in precision prec,
+ * on `stream`. */
 SBQ_API int stokes_matvec(const void *op, const double *sigma, double *out, int prec,
                           void *stream);
 

@@ -305,10 +305,10 @@ SBQ_API int batch_plan(int nseg, const int64_t *seg_src_off, const int64_t *seg_
     return SBQ_OK;
 }
 
-SBQ_API int stokes_op_create(int64_t n, const double *src, const double *nrm, const double *w,
-                             double eta, double diag, int64_t nnz, const int64_t *rowptr,
-                             const int64_t *col, const double *val, const void *plan,
-                             void **op_out)
+static int op_create_impl(int64_t n, const double *src, const double *nrm, const double *w,
+                          double eta, double diag, int64_t nnz, const int64_t *rowptr,
+                          const int64_t *col, const double *val, const void *plan, void **op_out,
+                          bool laplace)
 {
     clear_error();
     if (!op_out)
@@ -346,6 +346,8 @@ SBQ_API int stokes_op_create(int64_t n, const double *src, const double *nrm, co
     op->eta = eta;
     op->diag = diag;
     op->nnz = nnz;
+    op->laplace = laplace;
+    op->ncomp = laplace ? 1 : 3;
     if (pl)
         op->plan = *pl;
     else {
@@ -362,11 +364,12 @@ SBQ_API int stokes_op_create(int64_t n, const double *src, const double *nrm, co
     if (n > 0 && (st = internal_order(op, src, nrm, w)) != SBQ_OK)
         return bail(st);
     if (nnz > 0) {
-        if ((st = op->rowptr.alloc((3 * static_cast<size_t>(n) + 1) * sizeof(int64_t))) != SBQ_OK)
+        const size_t rows = static_cast<size_t>(op->ncomp) * n;
+        if ((st = op->rowptr.alloc((rows + 1) * sizeof(int64_t))) != SBQ_OK)
             return bail(st);
         if ((st = op->col.alloc(static_cast<size_t>(nnz) * sizeof(int64_t))) != SBQ_OK) return bail(st);
         if ((st = op->val.alloc(static_cast<size_t>(nnz) * sizeof(double))) != SBQ_OK) return bail(st);
-        cudaError_t e = cudaMemcpy(op->rowptr.p, rowptr, (3 * n + 1) * sizeof(int64_t),
+        cudaError_t e = cudaMemcpy(op->rowptr.p, rowptr, (rows + 1) * sizeof(int64_t),
                                    cudaMemcpyDeviceToDevice);
         if (e == cudaSuccess)
             e = cudaMemcpy(op->col.p, col, nnz * sizeof(int64_t), cudaMemcpyDeviceToDevice);
@@ -377,8 +380,11 @@ SBQ_API int stokes_op_create(int64_t n, const double *src, const double *nrm, co
     cudaStream_t s = nullptr;
     int kind;
     double scale, kappa;
-    kind_and_scale(eta, 1.0, &kind, &scale, &kappa);
-    const double nscale = (kind == KIND_CF) ? kappa : 1.0;
+    if (laplace)
+        laplace_kind_and_scale(eta, 1.0, &kind, &scale, &kappa);
+    else
+        kind_and_scale(eta, 1.0, &kind, &scale, &kappa);
+    const double nscale = (kind == KIND_CF || kind == KIND_LCF) ? kappa : 1.0;
     if ((st = build_src_pack(op->sp32, SBQ_FP32, op->plan.src_off, op->src.as<double>(),
                              op->nrm.as<double>(), nscale, n, s)) != SBQ_OK)
         return bail(st);
@@ -392,6 +398,22 @@ SBQ_API int stokes_op_create(int64_t n, const double *src, const double *nrm, co
     if (e != cudaSuccess) return bail(cuda_status(e, "stokes_op_create"));
     *op_out = op;
     return SBQ_OK;
+}
+
+SBQ_API int stokes_op_create(int64_t n, const double *src, const double *nrm, const double *w,
+                             double eta, double diag, int64_t nnz, const int64_t *rowptr,
+                             const int64_t *col, const double *val, const void *plan,
+                             void **op_out)
+{
+    return op_create_impl(n, src, nrm, w, eta, diag, nnz, rowptr, col, val, plan, op_out, false);
+}
+
+SBQ_API int laplace_op_create(int64_t n, const double *src, const double *nrm, const double *w,
+                              double eta, double diag, int64_t nnz, const int64_t *rowptr,
+                              const int64_t *col, const double *val, const void *plan,
+                              void **op_out)
+{
+    return op_create_impl(n, src, nrm, w, eta, diag, nnz, rowptr, col, val, plan, op_out, true);
 }
 
 SBQ_API int stokes_matvec(const void *oph, const double *sigma, double *out, int prec, void *stream)

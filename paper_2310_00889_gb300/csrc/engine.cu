@@ -442,7 +442,10 @@ int op_kernels_per_matvec(const Op *op, int prec)
 
 static int op_kind(const Op *op, int *kind, double *scale, double *kappa)
 {
-    kind_and_scale(op->eta, 1.0, kind, scale, kappa);
+    if (op->laplace)
+        laplace_kind_and_scale(op->eta, 1.0, kind, scale, kappa);
+    else
+        kind_and_scale(op->eta, 1.0, kind, scale, kappa);
     return SBQ_OK;
 }
 
@@ -634,7 +637,7 @@ int op_matvec(Op *op, const double *sigma, double *out, int prec, cudaStream_t s
                         n, op->src.as<double>(), n, out, scale, kappa, op->diag, sigma, s,
                         bound, op->perm.as<int>()));
     if (op->nnz > 0)
-        SBQ_CUDA(launch_csr_apply(3 * n, op->rowptr.as<int64_t>(), op->col.as<int64_t>(),
+        SBQ_CUDA(launch_csr_apply(op->ncomp * n, op->rowptr.as<int64_t>(), op->col.as<int64_t>(),
                                   op->val.as<double>(), sigma, out, s));
     return SBQ_OK;
 }

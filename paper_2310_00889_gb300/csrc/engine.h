@@ -70,6 +70,8 @@ struct Op {
     int device = 0;
     long long n = 0;
     double eta = 0.0, diag = 0.5;
+    bool laplace = false;              // Laplace operator (scalar densities)
+    int ncomp = 3;                     // components per node: 3 (Stokes) or 1 (Laplace)
     long long nnz = 0;
     DevBuf src, nrm, w;                // library copies (SoA), in the internal node order
     DevBuf perm;                       // int: caller's index of each internal node

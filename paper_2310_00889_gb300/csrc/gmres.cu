@@ -544,13 +544,13 @@ static int ws_ensure(Op *op, int m)
     }
     auto *ws = new GmresWS();
     ws->m = m;
-    ws->N = 3 * op->n;
+    ws->N = static_cast<long long>(op->ncomp) * op->n;
     ws->nseg = op->plan.nseg;
     ws->ldp = m + 1;
     ws->LD = m + 1;
     const long long N = ws->N, n = op->n;
     const int nseg = ws->nseg;
-    // Block table: rows of segment s are the three component ranges c n + [o_s, o_{s+1});
+    // Block table: rows of segment s are the component ranges c n + [o_s, o_{s+1});
     // each range is cut into chunks of about N / (8 SMs) rows, at least 128.
     const long long chunk = std::max<long long>(128, N / (8LL * device_props().sms) + 1);
     std::vector<int4> hb;
@@ -558,7 +558,7 @@ static int ws_ensure(Op *op, int m)
     for (int s = 0; s < nseg; ++s) {
         hsb[s].x = static_cast<int>(hb.size());
         const long long a = op->plan.src_off[s], b = op->plan.src_off[s + 1];
-        for (int c = 0; c < 3; ++c)
+        for (int c = 0; c < op->ncomp; ++c)
             for (long long r = a; r < b; r += chunk)
                 hb.push_back(make_int4(static_cast<int>(c * n + r),
                                        static_cast<int>(c * n + std::min(b, r + chunk)), s, 0));

@@ -91,6 +91,8 @@ def _load():
         "batch_plan": ([_int, _vp, _vp, _vp, ctypes.POINTER(_vp)], _int),
         "stokes_op_create": ([_i64, _vp, _vp, _vp, _dbl, _dbl, _i64, _vp, _vp, _vp, _vp,
                               ctypes.POINTER(_vp)], _int),
+        "laplace_op_create": ([_i64, _vp, _vp, _vp, _dbl, _dbl, _i64, _vp, _vp, _vp, _vp,
+                               ctypes.POINTER(_vp)], _int),
         "stokes_matvec": ([_vp, _vp, _vp, _int, _vp], _int),
         "stokes_matvec_bounded": ([_vp, _vp, _vp, _vp, _vp], _int),
         "gmres_solve": ([_vp, _vp, _vp, ctypes.POINTER(GmresOpts), ctypes.POINTER(GmresReport),
@@ -295,8 +297,12 @@ class BatchPlan:
 class StokesOp:
     """K sigma = diag sigma + (D + eta S)[sigma] + E sigma on the nodes (Eq. stokes-bie-new)."""
 
+    _ncomp = 3
+    _create = "stokes_op_create"
+
     def __init__(self, src, nrm, w, eta, diag=0.5, correction=None, plan: BatchPlan | None = None):
         n = src.shape[1]
+        self.vshape = (3, n) if self._ncomp == 3 else (n,)
         _dev(src, (3, n), "src")
         _dev(nrm, (3, n), "nrm")
         _dev(w, (n,), "w")
@@ -311,13 +317,14 @@ class StokesOp:
                               (val, "val", torch.float64)):
                 if not (t.is_cuda and t.dtype == dt and t.is_contiguous()):
                     raise TypeError("correction %s must be a contiguous CUDA %s tensor" % (nm, dt))
-            if rowptr.numel() != 3 * n + 1:
-                raise ValueError("rowptr must have 3n+1 entries")
+            if rowptr.numel() != self._ncomp * n + 1:
+                raise ValueError("rowptr must have %d entries" % (self._ncomp * n + 1))
             nnz = int(val.numel())
         h = _vp()
-        _check(lib.stokes_op_create(n, _ptr(src), _ptr(nrm), _ptr(w), self.eta, float(diag), nnz,
-                                    _ptr(rowptr), _ptr(col), _ptr(val),
-                                    plan.handle if plan is not None else None, ctypes.byref(h)))
+        _check(getattr(lib, self._create)(n, _ptr(src), _ptr(nrm), _ptr(w), self.eta, float(diag),
+                                          nnz, _ptr(rowptr), _ptr(col), _ptr(val),
+                                          plan.handle if plan is not None else None,
+                                          ctypes.byref(h)))
         self.handle = h
 
     def close(self):
@@ -332,16 +339,16 @@ class StokesOp:
             pass
 
     def matvec(self, sigma, prec="fp64", out=None, stream=None):
-        _dev(sigma, (3, self.n), "sigma")
+        _dev(sigma, self.vshape, "sigma")
         if out is None:
             out = torch.empty_like(sigma)
-        _dev(out, (3, self.n), "out")
+        _dev(out, self.vshape, "out")
         _check(lib.stokes_matvec(self.handle, _ptr(sigma), _ptr(out), _prec(prec), _stream(stream)))
         return out
 
     def matvec_bounded(self, sigma, stream=None):
         """(K sigma in double-float, per-entry bound on its rounding error)."""
-        _dev(sigma, (3, self.n), "sigma")
+        _dev(sigma, self.vshape, "sigma")
         out = torch.empty_like(sigma)
         bnd = torch.empty_like(sigma)
         _check(lib.stokes_matvec_bounded(self.handle, _ptr(sigma), _ptr(out), _ptr(bnd),
@@ -353,9 +360,9 @@ class StokesOp:
         """GMRES for K x = rhs; returns (x, report dict).  inner_prec fp64 / df32: plain
         GMRES in that precision; fp32 / fp32c: iterative refinement whose residuals are
         formed in resid_prec (fp64 or df32)."""
-        _dev(rhs, (3, self.n), "rhs")
+        _dev(rhs, self.vshape, "rhs")
         x = torch.zeros_like(rhs) if x0 is None else x0.clone()
-        _dev(x, (3, self.n), "x0")
+        _dev(x, self.vshape, "x0")
         o = GmresOpts(float(tol), int(restart), int(max_iter), _prec(inner_prec), float(inner_tol),
                       int(max_outer), 1 if use_graph else 0, _prec(resid_prec))
         rep = GmresReport()
@@ -370,11 +377,10 @@ class StokesOp:
     def time_pairsum(self, sigma, prec="fp32c", reps=1, out=None, stream=None):
         """(pair-sum kernel ms, whole apply ms), means over reps applies, from CUDA events
         recorded on the stream around the kernel launch and around the apply."""
-        n = self.n
-        _dev(sigma, (3, n), "sigma")
+        _dev(sigma, self.vshape, "sigma")
         if out is None:
-            out = torch.empty((3, n), dtype=torch.float64, device=sigma.device)
-        _dev(out, (3, n), "out")
+            out = torch.empty(self.vshape, dtype=torch.float64, device=sigma.device)
+        _dev(out, self.vshape, "out")
         k, a = _dbl(), _dbl()
         _check(lib.sbq_op_time_pairsum(self.handle, _ptr(sigma), _ptr(out), _prec(prec), int(reps),
                                        _stream(stream), ctypes.byref(k), ctypes.byref(a)))
@@ -394,6 +400,14 @@ class StokesOp:
         k, p = _int(), _dbl()
         _check(lib.sbq_op_stats(self.handle, _prec(prec), ctypes.byref(k), ctypes.byref(p)))
         return dict(kernels_per_matvec=k.value, pairs_per_matvec=p.value)
+
+
+class LaplaceOp(StokesOp):
+    """K sigma = diag sigma + (D + eta S)[sigma] + E sigma for the Laplace layers (Eq.
+    laplace-bie-new), scalar densities of shape (n,); same methods as StokesOp."""
+
+    _ncomp = 1
+    _create = "laplace_op_create"
 
 
 def solve_from_host(src, nrm, w, rhs, eta, tol=1e-10, inner_prec="fp32c", restart=100,
