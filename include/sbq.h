@@ -276,6 +276,29 @@ SBQ_API int laplace_op_create(int64_t n, const double *src, const double *nrm, c
                               const int64_t *col, const double *val, const void *plan,
                               void **op_out);
 
+/*
+ * Stokes mobility problem, slender combined-field formulation (Sec. 4.2, Eqs.
+ * new-mobility-bie and recover-rigidbody-motion):
+ *   (K (I - L) + L) sigma = u_s - S nu,     V = -L sigma
+ * L: orthogonal projector onto the rigid-body motions of each body in the quadrature
+ * L^2 inner product sum_j w_j f_j . g_j; nu: the completion-flow density, on each body the
+ * rigid motion whose force sum w nu and torque sum w (x - c_b) x nu (about the body's
+ * weighted centroid c_b) are the given F_b, T_b.
+ * stokes_op_set_mobility turns a Stokes operator handle into the mobility operator for the
+ *   bodies body_off[0] = 0 <= ... <= body_off[nbody] = n (HOST array): from then on
+ *   stokes_matvec and gmres_solve apply K (I - L) + L.  Not reversible on the handle.
+ * stokes_mobility_rhs: rhs = u_s - S nu for FT (HOST, 6 per body: F then T); us (device,
+ *   3n, nullable for no slip); the single layer in precision prec.  Synchronises the stream.
+ * stokes_mobility_velocity: V = -L sigma as the rigid motion of each body, UW (HOST, 6 per
+ *   body: translational velocity of the centroid, then angular velocity).  Synchronises.
+ * Errors: SBQ_EINVAL for bad offsets, a Laplace handle, a body with a singular inertia
+ * tensor, or a handle without the mobility set-up.
+ */
+SBQ_API int stokes_op_set_mobility(void *op, int nbody, const int64_t *body_off, void *stream);
+SBQ_API int stokes_mobility_rhs(void *op, const double *FT, const double *us, double *rhs,
+                                int prec, void *stream);
+SBQ_API int stokes_mobility_velocity(void *op, const double *sigma, double *UW, void *stream);
+
 /* out = K sigma (device arrays of 3*n doubles; n for a Laplace operator) in precision prec,
  * on `stream`. */
 SBQ_API int stokes_matvec(const void *op, const double *sigma, double *out, int prec,

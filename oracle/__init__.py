@@ -12,6 +12,8 @@ Contents
     (paper Sec. 3.2.1 Eq. nystrom-no-correction / nystrom-correction,
     Eqs. stokes-sl / stokes-dl / stokes-bie-new);
   * `laplace`: the Laplace single / double layer / combined field (Sec. 4.1), scalar;
+  * `mobility_solve`: the slender combined-field mobility formulation (Sec. 4.2) with the
+    rigid-motion projector built from a Gram--Schmidt basis;
   * `dense_operator`: the same kernels written a second time with numpy, as an
     explicit 3N x 3N matrix, for tiny systems;
   * `gmres`: restarted GMRES(m) with classical Gram--Schmidt applied twice and
@@ -245,6 +247,96 @@ def dl_gauss_correction(src, nrm, w, body_off=None) -> CSR:
                 col[3 * r + b] = b * n + i
                 val[3 * r + b] = -R[a, b, i] - (0.5 if a == b else 0.0)
     return CSR(rowptr, col, val, rows, rows)
+
+
+def rigid_basis(x, w, centre):
+    """Orthonormal basis of the rigid motions of one body in the quadrature L^2 inner product
+    <f, g> = sum w f . g (paper Sec. 4.2: the three translations and the three rotations about
+    the centre, orthonormalised by Gram--Schmidt).  Returns (6, 3, nb)."""
+    d = x - np.asarray(centre, dtype=np.float64)[:, None]
+    nb = x.shape[1]
+    vecs = []
+    for k in range(3):
+        v = np.zeros((3, nb))
+        v[k] = 1.0
+        vecs.append(v)
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = 1.0
+        vecs.append(np.cross(e[:, None], d, axis=0))
+    ip = lambda f, g: float(np.sum(w * np.sum(f * g, axis=0)))
+    out = []
+    for v in vecs:
+        u = v.copy()
+        for q in out:
+            u -= ip(q, u) * q
+        out.append(u / np.sqrt(ip(u, u)))
+    return np.array(out)
+
+
+def rigid_projector(x, w, body_off, centres):
+    """L sigma = sum_i v_i <v_i, sigma>_w over the rigid bases of all bodies (Eq. L)."""
+    bases = [rigid_basis(x[:, a:b], w[a:b], centres[i])
+             for i, (a, b) in enumerate(zip(body_off[:-1], body_off[1:]))]
+
+    def L(sigma):
+        out = np.zeros_like(sigma)
+        for i, (a, b) in enumerate(zip(body_off[:-1], body_off[1:])):
+            for v in bases[i]:
+                out[:, a:b] += float(np.sum(w[a:b] * np.sum(v * sigma[:, a:b], axis=0))) * v
+        return out
+    return L
+
+
+def mobility_solve(src, nrm, w, eta, body_off, F, T, us=None, E: CSR | None = None, tol=1e-11,
+                   restart=100, max_iter=2000):
+    """Stokes mobility problem, slender combined-field formulation (Sec. 4.2): completion
+    flow nu (on each body the rigid motion alpha + beta x (x - c) whose quadrature force and
+    torque about c are F_b, T_b: a 6 x 6 system assembled column by column), right-hand side
+    u_s - S nu, GMRES on (K (I - L) + L) sigma, rigid velocity V = -L sigma, and each body's
+    (U, Omega) by a least-squares fit of V on its nodes.  Centres: the weighted centroids.
+    Returns (UW (nbody, 6), sigma, info)."""
+    src = _c(src)
+    n = src.shape[1]
+    w = _c(w, (n,))
+    off = [int(v) for v in body_off]
+    nb = len(off) - 1
+    cen = [np.sum(w[a:b] * src[:, a:b], axis=1) / np.sum(w[a:b]) for a, b in zip(off[:-1], off[1:])]
+    L = rigid_projector(src, w, off, cen)
+    nu = np.zeros((3, n))
+    for i, (a, b) in enumerate(zip(off[:-1], off[1:])):
+        d = src[:, a:b] - cen[i][:, None]
+        cols = []
+        for k in range(6):
+            ab = np.zeros(6)
+            ab[k] = 1.0
+            v = ab[:3, None] + np.cross(ab[3:][:, None], d, axis=0)
+            cols.append(np.concatenate([np.sum(w[a:b] * v, axis=1),
+                                        np.sum(w[a:b] * np.cross(d, v, axis=0), axis=1)]))
+        ab = np.linalg.solve(np.array(cols).T, np.concatenate([F[i], T[i]]))
+        nu[:, a:b] = ab[:3, None] + np.cross(ab[3:][:, None], d, axis=0)
+    rhs = -sl(src, w, nu, src)
+    if us is not None:
+        rhs = rhs + us
+
+    def A(v):
+        s3 = v.reshape(3, n)
+        lv = L(s3)
+        return (matvec(src, nrm, w, eta, s3 - lv, 0.5, E) + lv).reshape(-1)
+    x, info = gmres(A, rhs.reshape(-1), tol=tol, restart=restart, max_iter=max_iter)
+    sigma = x.reshape(3, n)
+    V = -L(sigma)
+    uw = np.zeros((nb, 6))
+    for i, (a, b) in enumerate(zip(off[:-1], off[1:])):
+        d = src[:, a:b] - cen[i][:, None]
+        m = b - a
+        M = np.zeros((3 * m, 6))
+        for k in range(6):
+            ab = np.zeros(6)
+            ab[k] = 1.0
+            M[:, k] = (ab[:3, None] + np.cross(ab[3:][:, None], d, axis=0)).reshape(-1)
+        uw[i] = np.linalg.lstsq(M, V[:, a:b].reshape(-1), rcond=None)[0]
+    return uw, sigma, info
 
 
 def dense_operator(src, nrm, w, trg, alpha, beta):

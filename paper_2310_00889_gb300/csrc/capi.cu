@@ -416,6 +416,50 @@ SBQ_API int laplace_op_create(int64_t n, const double *src, const double *nrm, c
     return op_create_impl(n, src, nrm, w, eta, diag, nnz, rowptr, col, val, plan, op_out, true);
 }
 
+SBQ_API int stokes_op_set_mobility(void *oph, int nbody, const int64_t *body_off, void *stream)
+{
+    clear_error();
+    Op *op = as_op(oph);
+    if (!op)
+        return fail(SBQ_EINVAL, "not an operator handle");
+    if (op->laplace)
+        return fail(SBQ_EINVAL, "the mobility formulation is a Stokes formulation");
+    if (nbody < 1 || !body_off || body_off[0] != 0 || body_off[nbody] != op->n)
+        return fail(SBQ_EINVAL, "body offsets must run from 0 to n");
+    for (int b = 0; b < nbody; ++b)
+        if (body_off[b + 1] < body_off[b])
+            return fail(SBQ_EINVAL, "body offsets must be non-decreasing");
+    std::lock_guard<std::mutex> lk(op->mu);
+    return mob_setup(op, nbody, body_off, static_cast<cudaStream_t>(stream));
+}
+
+SBQ_API int stokes_mobility_rhs(void *oph, const double *FT, const double *us, double *rhs,
+                                int prec, void *stream)
+{
+    clear_error();
+    Op *op = as_op(oph);
+    if (!op || !op->mob)
+        return fail(SBQ_EINVAL, "not a mobility operator (stokes_op_set_mobility)");
+    if (!FT || (op->n > 0 && !rhs))
+        return fail(SBQ_EINVAL, "null force/torque or right-hand-side pointer");
+    if (!prec_ok(prec))
+        return fail(SBQ_EINVAL, "unknown precision");
+    std::lock_guard<std::mutex> lk(op->mu);
+    return mob_rhs(op, FT, us, rhs, prec, static_cast<cudaStream_t>(stream));
+}
+
+SBQ_API int stokes_mobility_velocity(void *oph, const double *sigma, double *UW, void *stream)
+{
+    clear_error();
+    Op *op = as_op(oph);
+    if (!op || !op->mob)
+        return fail(SBQ_EINVAL, "not a mobility operator (stokes_op_set_mobility)");
+    if (!UW || (op->n > 0 && !sigma))
+        return fail(SBQ_EINVAL, "null density or velocity pointer");
+    std::lock_guard<std::mutex> lk(op->mu);
+    return mob_velocity(op, sigma, UW, static_cast<cudaStream_t>(stream));
+}
+
 SBQ_API int stokes_matvec(const void *oph, const double *sigma, double *out, int prec, void *stream)
 {
     clear_error();

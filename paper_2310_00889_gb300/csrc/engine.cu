@@ -437,6 +437,8 @@ int op_kernels_per_matvec(const Op *op, int prec)
         k += 2 + ((ts->needs_reduce || prec != SBQ_FP64) ? 1 : 0);
     if (op->nnz > 0)
         k += 1;
+    if (op->mob)
+        k += 4;   // moments, rigid motions, sigma - L sigma, + L sigma
     return k;
 }
 
@@ -633,12 +635,21 @@ int op_matvec(Op *op, const double *sigma, double *out, int prec, cudaStream_t s
     const long long n = op->n;
     if (n == 0)
         return SBQ_OK;
-    SBQ_TRY(run_pairsum(kind, prec, op_srcpack(op, prec), *op->ts[prec], op->w.as<double>(), sigma,
-                        n, op->src.as<double>(), n, out, scale, kappa, op->diag, sigma, s,
+    // mobility: K (sigma - L sigma) + L sigma, with y = sigma - L sigma in the state's scratch
+    const double *y = sigma;
+    if (op->mob) {
+        SBQ_TRY(mob_project(op, sigma, 1.0, s));
+        SBQ_TRY(mob_field(op, sigma, -1.0, op->mob->y.as<double>(), s));
+        y = op->mob->y.as<double>();
+    }
+    SBQ_TRY(run_pairsum(kind, prec, op_srcpack(op, prec), *op->ts[prec], op->w.as<double>(), y,
+                        n, op->src.as<double>(), n, out, scale, kappa, op->diag, y, s,
                         bound, op->perm.as<int>()));
     if (op->nnz > 0)
         SBQ_CUDA(launch_csr_apply(op->ncomp * n, op->rowptr.as<int64_t>(), op->col.as<int64_t>(),
-                                  op->val.as<double>(), sigma, out, s));
+                                  op->val.as<double>(), y, out, s));
+    if (op->mob)
+        SBQ_TRY(mob_field(op, out, 1.0, out, s));
     return SBQ_OK;
 }
 

@@ -65,6 +65,15 @@ struct TrgSet {
     DevBuf ttiles, tpack, tpack_lo, tpack_l2, items, partial, counter;
 };
 
+// Mobility formulation state of an operator (mobility.cu): bodies, their areas, centroids
+// and inverse inertia tensors, per-body reduction blocks and scratch.
+struct MobState {
+    int nbody = 0;
+    int nblk = 0;
+    std::vector<double> h_area, h_iinv, h_cen;
+    DevBuf x, w, body_of, blk, bodyblk, cen, area, iinv, part, rigid, y, r;
+};
+
 struct Op {
     uint32_t magic = OP_MAGIC;
     int device = 0;
@@ -82,6 +91,7 @@ struct Op {
     bool tuned[4] = {false, false, false, false};
     std::mutex mu;
     struct GmresWS *gm = nullptr;      // solver workspace (gmres.cu)
+    std::unique_ptr<MobState> mob;     // set: the operator is K (I - L) + L (mobility)
     ~Op();
 };
 
@@ -120,6 +130,14 @@ void kind_and_scale(double alpha, double beta, int *kind, double *scale, double 
 void laplace_kind_and_scale(double alpha, double beta, int *kind, double *scale, double *kappa);
 
 sbq_tune default_tune(int prec, long long nt);
+
+// mobility.cu
+int mob_setup(Op *op, int nbody, const int64_t *body_off, cudaStream_t s);
+int mob_project(const Op *op, const double *sigma, double sign, cudaStream_t s);
+int mob_field(const Op *op, const double *base, double s_r, double *out, cudaStream_t s);
+int mob_rhs(Op *op, const double *FT, const double *us, double *rhs, int prec, cudaStream_t s);
+int mob_velocity(Op *op, const double *sigma, double *UW, cudaStream_t s);
+int mob_axpy(long long n, double a, const double *x, double *y, cudaStream_t s);
 
 // correction.cu: E = -R_i - I/2 per node from per-body double-layer row sums.
 int dl_gauss_correction(int nbody, const int64_t *body_off, const double *src, const double *nrm,

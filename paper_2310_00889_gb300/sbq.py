@@ -94,6 +94,9 @@ def _load():
         "laplace_op_create": ([_i64, _vp, _vp, _vp, _dbl, _dbl, _i64, _vp, _vp, _vp, _vp,
                                ctypes.POINTER(_vp)], _int),
         "stokes_matvec": ([_vp, _vp, _vp, _int, _vp], _int),
+        "stokes_op_set_mobility": ([_vp, _int, _vp, _vp], _int),
+        "stokes_mobility_rhs": ([_vp, _vp, _vp, _vp, _int, _vp], _int),
+        "stokes_mobility_velocity": ([_vp, _vp, _vp, _vp], _int),
         "stokes_matvec_bounded": ([_vp, _vp, _vp, _vp, _vp], _int),
         "gmres_solve": ([_vp, _vp, _vp, ctypes.POINTER(GmresOpts), ctypes.POINTER(GmresReport),
                          _vp], _int),
@@ -345,6 +348,35 @@ class StokesOp:
         _dev(out, self.vshape, "out")
         _check(lib.stokes_matvec(self.handle, _ptr(sigma), _ptr(out), _prec(prec), _stream(stream)))
         return out
+
+    def set_mobility(self, body_off, stream=None):
+        """Make this operator the mobility operator K (I - L) + L for the bodies with node
+        offsets body_off (Sec. 4.2, Eq. new-mobility-bie)."""
+        off = np.asarray(body_off, dtype=np.int64)
+        c_off = (ctypes.c_int64 * off.size)(*[int(v) for v in off])
+        _check(lib.stokes_op_set_mobility(self.handle, int(off.size - 1), c_off, _stream(stream)))
+        self.nbody = int(off.size - 1)
+
+    def mobility_rhs(self, F, T, us=None, prec="fp64", stream=None):
+        """u_s - S nu for body forces F and torques T ((nbody, 3) each, torque about each
+        body's weighted centroid); us: slip velocity on the nodes or None."""
+        F = np.asarray(F, dtype=np.float64).reshape(self.nbody, 3)
+        T = np.asarray(T, dtype=np.float64).reshape(self.nbody, 3)
+        ft = np.concatenate([F, T], axis=1).reshape(-1)
+        c_ft = (ctypes.c_double * ft.size)(*ft.tolist())
+        if us is not None:
+            _dev(us, self.vshape, "us")
+        rhs = torch.empty(self.vshape, dtype=torch.float64, device=self.device)
+        _check(lib.stokes_mobility_rhs(self.handle, c_ft, _ptr(us), _ptr(rhs), _prec(prec),
+                                       _stream(stream)))
+        return rhs
+
+    def mobility_velocity(self, sigma, stream=None):
+        """V = -L sigma as (nbody, 6): centroid velocity U, then angular velocity Omega."""
+        _dev(sigma, self.vshape, "sigma")
+        uw = (ctypes.c_double * (6 * self.nbody))()
+        _check(lib.stokes_mobility_velocity(self.handle, _ptr(sigma), uw, _stream(stream)))
+        return np.array(uw[:]).reshape(self.nbody, 6)
 
     def matvec_bounded(self, sigma, stream=None):
         """(K sigma in double-float, per-entry bound on its rounding error)."""

@@ -469,3 +469,51 @@ def test_laplace_combined_is_linear(oracle_mod):
     us = oracle_mod.laplace(s.x, None, s.w, sig, trg, 1.0, 0.0)
     ud = oracle_mod.laplace(s.x, s.n, s.w, sig, trg, 0.0, 1.0)
     assert np.abs(uc - (2.5 * us - 0.75 * ud)).max() <= 1e-13 * np.abs(uc).max()
+
+
+# ---------------------------------------------------------------------------
+# Mobility formulation (Sec. 4.2, Eqs. new-mobility-bie, recover-rigidbody-motion)
+# ---------------------------------------------------------------------------
+
+def test_rigid_projector_is_orthogonal(oracle_mod):
+    """L (Eq. L) is an orthogonal projector in the quadrature inner product that keeps rigid
+    motions: L L = L, <L f, g> = <f, L g>, L v = v for v rigid on each body."""
+    s = I.concat([I.sphere(0.5, (0, 0, 0), 10, 15), I.torus(1.0, 0.25, 8, 8, 8)])
+    off = I.body_offsets(s)
+    cen = [np.sum(s.w[a:b] * s.x[:, a:b], axis=1) / np.sum(s.w[a:b]) for a, b in zip(off[:-1], off[1:])]
+    L = oracle_mod.rigid_projector(s.x, s.w, off, cen)
+    rng = np.random.default_rng(5)
+    f, g = rng.standard_normal((2, 3, s.size))
+    ip = lambda p, q: float(np.sum(s.w * np.sum(p * q, axis=0)))
+    Lf = L(f)
+    assert np.abs(L(Lf) - Lf).max() < 1e-12 * np.abs(Lf).max()
+    assert abs(ip(Lf, g) - ip(f, L(g))) < 1e-12 * abs(ip(f, g))
+    v = np.zeros((3, s.size))
+    for i, (a, b) in enumerate(zip(off[:-1], off[1:])):
+        d = s.x[:, a:b] - cen[i][:, None]
+        v[:, a:b] = rng.standard_normal(3)[:, None] + np.cross(rng.standard_normal(3)[:, None], d, axis=0)
+    assert np.abs(L(v) - v).max() < 1e-12 * np.abs(v).max()
+
+
+@pytest.mark.parametrize("load", ["force", "torque"])
+def test_mobility_sphere_stokes_law(oracle_mod, load):
+    """A sphere of radius a under a force F translates at U = F / (6 pi a) (Stokes drag,
+    viscosity 1) and under a torque T rotates at Omega = T / (8 pi a^3); the slender
+    combined-field mobility solve (punctured sums) converges to both at first order (the
+    error halves with h) and leaves the other motion at zero."""
+    a = 0.5
+    errs = []
+    for nphi, nth in ((10, 15), (20, 30), (40, 60)):
+        sp = I.sphere(a, (0.1, 0.2, 0.3), nphi, nth)
+        if load == "force":
+            F, T = np.array([[0.3, -0.2, 1.0]]), np.zeros((1, 3))
+            want, got, other = F[0] / (6 * np.pi * a), slice(0, 3), slice(3, 6)
+        else:
+            F, T = np.zeros((1, 3)), np.array([[0.2, 0.5, -0.4]])
+            want, got, other = T[0] / (8 * np.pi * a ** 3), slice(3, 6), slice(0, 3)
+        uw, _, info = oracle_mod.mobility_solve(sp.x, sp.n, sp.w, 1.0, [0, sp.size], F, T)
+        assert info["rel_res"] <= 1e-11 and info["iters"] <= 20
+        errs.append(np.linalg.norm(uw[0, got] - want) / np.linalg.norm(want))
+        assert np.abs(uw[0, other]).max() < 1e-12 * np.linalg.norm(want)
+    assert errs[2] < (0.03 if load == "force" else 0.06)
+    assert 0.45 < errs[1] / errs[0] < 0.55 and 0.45 < errs[2] / errs[1] < 0.55
