@@ -390,6 +390,25 @@ def config4(nseg=64, seed=3, ns=8, nth=32, nr=16, n_lo=2048, n_hi=65536):
     return dict(segments=segs, slenderness=1.0 / 5.0)
 
 
+def rings(nring=32, eps=0.05, panels=64, ns=8, nth=16, spacing=3.0, seed=9):
+    """nring tori (R = 1, tube radius eps) with centres on a 4 x 4 x (nring/16) lattice of the
+    given spacing, each turned by an independent uniformly random rotation (seed 9); a
+    body per ring."""
+    rng = np.random.default_rng(seed)
+    base = torus(1.0, eps, panels, ns, nth)
+    out = []
+    for i in range(nring):
+        c = spacing * np.array([i % 4, (i // 4) % 4, i // 16], dtype=np.float64)
+        q = rng.standard_normal(4)
+        q /= np.linalg.norm(q)
+        a, b, cc, d = q
+        Rm = np.array([[a * a + b * b - cc * cc - d * d, 2 * (b * cc - a * d), 2 * (b * d + a * cc)],
+                       [2 * (b * cc + a * d), a * a - b * b + cc * cc - d * d, 2 * (cc * d - a * b)],
+                       [2 * (b * d - a * cc), 2 * (cc * d + a * b), a * a - b * b - cc * cc + d * d]])
+        out.append(Surface(Rm @ base.x + c[:, None], Rm @ base.n, base.w.copy(), name="ring"))
+    return concat(out, name="rings")
+
+
 def config5(panels=2048, ns=8, nth=64, nr=16, nsph=100, seed=5, turns=4.0, pitch=2.0):
     """Helical pipe (helix radius 3, pitch `pitch` (2), `turns` turns (4), tube radius 1) with
     caps, plus nsph

@@ -80,3 +80,13 @@ def test_config_sizes_and_seeds():
     for seg in c4["segments"]:
         wall = seg["surf"].parts[0]
         assert (wall[2] - wall[1]) % 256 == 0
+
+
+def test_rings_generator():
+    """32 rigidly turned tori, one body each, weights summing to the torus area 4 pi^2 R eps."""
+    s = I.rings()
+    off = I.body_offsets(s)
+    assert s.size == 32 * 64 * 8 * 16 and len(off) == 33
+    for a, b in zip(off[:-1], off[1:]):
+        assert abs(np.sum(s.w[a:b]) - 4 * np.pi ** 2 * 0.05) < 1e-12
+        assert np.allclose(np.linalg.norm(s.n[:, a:b], axis=0), 1.0)
