@@ -7,8 +7,10 @@
  * Eq. nystrom-no-correction), the combined-field operator
  * K = diag I + D + eta S (+ sparse correction E, Eq. nystrom-correction) of the
  * slender-body BIE (Sec. 4.1, Eq. stokes-bie-new), and solves K sigma = u0 with
- * GMRES (plain FP64, or FP32 / compensated-FP32 inner solves with FP64
- * iterative refinement).
+ * GMRES (plain FP64 or double-float, or FP32 / compensated-FP32 inner solves with
+ * FP64 or bound-certified double-float iterative refinement).  Also: the Laplace
+ * layers and operator (Sec. 4.1), the Stokes mobility formulation (Sec. 4.2) and the
+ * double-layer singularity subtraction as a sparse correction.
  *
  * Kernels (viscosity 1, r = x - y, n = outward unit normal at the source y):
  *   S(r)    = (1/8pi) (I/|r| + r r^T / |r|^3)                     Eq. stokes-sl
@@ -32,10 +34,14 @@
  *  - A source whose coordinates equal a target's exactly is skipped (the
  *    punctured sum; the correction E adds the true singular part).  The FP64
  *    path skips exactly those pairs.  The FP32 paths skip pairs closer than
- *    4e-6 times the sum of the radii of the two tiles (256 consecutive points)
- *    holding them, which catches every coincident pair whatever the FP32
- *    rounding; they therefore require distinct points to be farther apart than
- *    that, and pair distances above ~1e-7 in the units of the input.
+ *    4e-6 times the sum of the radii of the two tiles (256 points) holding them,
+ *    which catches every coincident pair whatever the FP32 rounding; they
+ *    therefore require distinct points to be farther apart than that, and pair
+ *    distances above ~1e-7 in the units of the input.  The double-float path
+ *    uses 1e-10 of the radii of its 128-point tiles.
+ *  - Operator handles may keep their nodes in an internal order (per segment, the
+ *    caller's order or a recursive bisection of the nodes, whichever gives more
+ *    compact tiles); every vector crossing the ABI is in the caller's order.
  */
 #ifndef SBQ_H
 #define SBQ_H
@@ -115,8 +121,8 @@ typedef struct {
                                  of the segments' ratios (each segment is solved to tol on its
                                  own norm) */
     int n_hist;               /* entries used in rel_res_hist */
-    double rel_res_hist[SBQ_HIST]; /* FP64 true relative residual after each refinement
-                                      step / restart cycle, starting with x0 */
+    double rel_res_hist[SBQ_HIST]; /* the decisive relative residual (as rel_res) after each
+                                      refinement step / restart cycle, starting with x0 */
     double time_ms;           /* wall time of the solve on the host clock */
     int resid_fallbacks;      /* double-float residuals whose error bound was too large to
                                  certify the tolerance, recomputed in FP64 (the solve then
@@ -164,6 +170,7 @@ SBQ_API int stokes_sl_apply(int64_t ns, const double *src, const double *w, cons
  * On success the call performs no allocation of any kind; a rejected call records its
  * message for sbq_last_error() as every entry point does.
  */
+/* (prec: SBQ_FP64, SBQ_FP32 or SBQ_FP32_COMP; SBQ_DF32 is not offered here: SBQ_EINVAL.) */
 SBQ_API int stokes_sl_apply_noalloc(int64_t ns, const double *src, const double *w,
                                     const double *sigma, int64_t nt, const double *trg, double *u,
                                     int prec, void *stream);

@@ -208,7 +208,7 @@ Op *as_op(const void *h)
 
 extern "C" {
 
-SBQ_API int sbq_version(void) { return 100; }
+SBQ_API int sbq_version(void) { return 200; }
 
 SBQ_API const char *sbq_last_error(void) { return last_error_cstr(); }
 

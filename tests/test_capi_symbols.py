@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol(libsbq):
 
 def test_host_only_calls(libsbq):
     libsbq.sbq_version.restype = ctypes.c_int
-    assert libsbq.sbq_version() == 100
+    assert libsbq.sbq_version() == 200
     libsbq.sbq_last_error.restype = ctypes.c_char_p
     assert libsbq.sbq_last_error() == b""
     # argument validation happens before any device call
