@@ -43,7 +43,12 @@ WORKLOAD = "curved_pipe_arc90_Rc5_R1_16384wall_2048cap_gmres_ir_1e-10"
 L2_FLUSH_BYTES = 256 << 20
 
 
-def parse():
+def parse_args_for_test():
+    """Default arguments, as `python bench.py` with no flags."""
+    return parse([])
+
+
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -81,7 +86,7 @@ def parse():
     ap.add_argument("--kernel-only", default=None, choices=["fp32c", "fp32", "fp64", "df32"],
                     help="only time operator applies of this precision on the workload "
                          "(inside an NVTX range 'kernel_only', for profilers)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def dist_env():
@@ -89,6 +94,23 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(ms, world, device=None):
+    """The slowest rank's time (the job's time): all-reduce MAX over the process group."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(pairs_per_step, ms, world):
+    """Whole-job throughput of `world` independent replicas (weak scaling): every rank
+    processes pairs_per_step per step, the job takes the slowest rank's ms."""
+    return world * float(pairs_per_step) / (float(ms) * 1e-3)
 
 
 # ---------------------------------------------------------------------------
@@ -295,12 +317,7 @@ def run_gpu(args):
     barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    ms = float(np.mean(times))
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(float(np.mean(times)), world, dev)
     rep = reps[-1]
     for r in reps:
         if r["status"] != 0 or r["rel_res"] > 1e-10:
@@ -324,7 +341,7 @@ def run_gpu(args):
         oth_times.append(e0.elapsed_time(e1))
     oth_ms = float(np.min(oth_times[1:]))
     pairs_step = float(rep["matvecs_fp64"] + rep["matvecs_low"]) * n * n
-    value = world * pairs_step / (ms * 1e-3)
+    value = replica_value(pairs_step, ms, world)
     kpm32 = op.stats("fp32c")["kernels_per_matvec"]
     launches = rep["kernel_launches"] * args.steps
 
