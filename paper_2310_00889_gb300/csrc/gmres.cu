@@ -418,6 +418,8 @@ __global__ void k_cycle_init(GState *st, SegState *seg, const double *__restrict
         st->ctr = 0;
         st->seg_done = 0;
         st->guard = 0;
+        st->guard_hit = 0;
+        st->nonfinite = 0;   // per cycle (a norm pass before the cycle may have set it)
         st->m = m;
         st->nseg = nseg;
     }
