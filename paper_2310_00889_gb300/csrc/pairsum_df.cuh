@@ -250,7 +250,7 @@ __device__ __forceinline__ void tile_df(const float4 *__restrict__ sp, float thr
                                         const float (&D)[R][3], float (&acc)[R][6],
                                         float (&env)[R])
 {
-#pragma unroll 1
+#pragma unroll 2
     for (int j = 0; j < TS_DF; ++j) {
         const float4 *rec = sp + 6 * j;
         const float4 a = rec[0], b = rec[1], c = rec[2], d = rec[3], e = rec[4], f = rec[5];

@@ -191,7 +191,7 @@ __device__ __forceinline__ void tile_f32(const float4 *__restrict__ sp, float th
     }
 #pragma unroll 1
     for (int m0 = 0; m0 < H; m0 += RUN) {
-#pragma unroll 2
+#pragma unroll 4
         for (int m = m0; m < m0 + RUN; ++m) {
             const ulonglong2 a0 = s2[m];           // X, Y
             const ulonglong2 a1 = s2[H + m];       // Z, QX
