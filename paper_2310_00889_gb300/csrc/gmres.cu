@@ -553,8 +553,9 @@ static int ws_ensure(Op *op, int m)
     const long long N = ws->N, n = op->n;
     const int nseg = ws->nseg;
     // Block table: rows of segment s are the component ranges c n + [o_s, o_{s+1});
-    // each range is cut into chunks of about N / (8 SMs) rows, at least 128.
-    const long long chunk = std::max<long long>(128, N / (8LL * device_props().sms) + 1);
+    // each range is cut into chunks of about N / (8 SMs) rows, at least 256 (one row per
+    // thread of the update loops).
+    const long long chunk = std::max<long long>(256, N / (8LL * device_props().sms) + 1);
     std::vector<int4> hb;
     std::vector<int2> hsb(nseg);
     for (int s = 0; s < nseg; ++s) {
