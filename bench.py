@@ -3,20 +3,23 @@
 
 Workload (curved pipe): quarter-circle arc of centreline radius 5, tube radius 1,
 32 panels x 8 Gauss-Legendre x 64 trapezoid = 16384 wall nodes plus two 16 x 64 end
-caps (18432 nodes, 55296 unknowns); combined-field operator K = I/2 + D + eta S with
-eta = 1/(2 eps log(1/eps)), eps = 1/5 (paper Eq. stokes-bie-new, uncorrected Nystrom
-sums); Dirichlet data: parabolic profile on the caps, zero on the wall.
+caps (18432 nodes, 55296 unknowns); combined-field operator K = I/2 + D + eta S + E with
+eta = 1/(2 eps log(1/eps)), eps = 1/5 (paper Eq. stokes-bie-new) and E the double-layer
+singularity subtraction; Dirichlet data: parabolic profile on the caps, zero on the wall.
 
 One step = one GMRES solve of K x = u0 to a 1e-10 FP64 relative residual from x0 = 0:
-compensated-FP32 pair sums inside the Krylov iterations, FP64 residual refinement,
+compensated-FP32 pair sums inside the Krylov iterations, FP64 residual refinement
+(--resid-prec df32: bound-certified double-float residuals, timed beside it either way),
 each Arnoldi step replayed by a CUDA-graph while node.  Inputs are resident in HBM
 before the timed region; the operator (geometry packing, tile-shape autotuning) is
 built once before it.  The L2 cache is flushed (256 MiB write) between steps, outside
 the timed intervals.
 
-metric: pair interactions per second over the whole solve (every FP32 and FP64 operator
-apply counted, N^2 pairs each), with the solve time (ms_per_step) and the plain-FP64
-GMRES solve time of the same system reported beside it.
+metric: pair interactions per second over the whole solve (every operator apply counted,
+N^2 pairs each), with the solve time (ms_per_step) and the plain-FP64 GMRES solve time of
+the same system reported beside it.
+
+Other workloads (--workload): precision_sweep, batch, helix, laplace, mobility.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -58,10 +61,11 @@ def parse(argv=None):
                     help="CPU work bound of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-reps", type=int, default=20)
-    ap.add_argument("--resid-prec", default="df32", choices=["fp64", "df32"],
-                    help="precision of the refinement residuals b - K x of the timed solve "
-                         "(df32: double-float, FP64-class; the returned x is checked with an "
-                         "FP64 residual after the timed region either way)")
+    ap.add_argument("--resid-prec", default="fp64", choices=["fp64", "df32"],
+                    help="precision of the refinement residuals b - K x of the timed solve: "
+                         "fp64 (default), or df32 (double-float, used where its rounding-error "
+                         "bound certifies the tolerance); the other one is timed beside it and "
+                         "the returned x is checked with an FP64 residual either way")
     ap.add_argument("--no-correction", action="store_true",
                     help="solve with the punctured sums alone (no double-layer singularity "
                          "subtraction)")
