@@ -1,0 +1,158 @@
+"""Pins of the quadrature-correction oracle (oracle/tube_quadrature.py) against values fixed by
+the mathematics: closed forms, an independent adaptive integral and Green's identities on a
+closed tube.  CPU only."""
+import math
+import warnings
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import tube_quadrature as T
+from paper_2310_00889_gb300 import inputs as I
+
+special = pytest.importorskip("scipy.special")
+integrate = pytest.importorskip("scipy.integrate")
+
+
+def test_singular_rule_integrates_log_times_polynomial():
+    # int_0^1 t^k log t dt = -1/(k+1)^2, int_0^1 t^k dt = 1/(k+1)
+    u, w = T.singular_rule()
+    for k in range(12):
+        assert abs(np.sum(w * u ** k * np.log(u)) + 1.0 / (k + 1) ** 2) < 1e-13
+        assert abs(np.sum(w * u ** k) - 1.0 / (k + 1)) < 1e-13
+
+
+@pytest.mark.parametrize("d", [2.0, 0.3, 1e-3])
+@pytest.mark.parametrize("psi", [0.0, 1.0, 2.5])
+def test_angular_rule_ring_potential(d, psi):
+    """Sec. 3.2.3: the refined angular rule integrates 1/|x - y(theta)| over the unit circle
+    for a target at distance d; closed form 4 K(m) / sqrt((rho + 1)^2 + z^2)."""
+    x = np.array([1.0 + d * math.cos(psi), 0.0, d * math.sin(psi)])
+    rho, z = math.hypot(x[0], x[1]), x[2]
+    den = (rho + 1.0) ** 2 + z * z
+    exact = 4.0 * special.ellipkm1(((rho - 1.0) ** 2 + z * z) / den) / math.sqrt(den)
+    phi, om = T.theta_rule(d, 16)
+    y = np.stack([np.cos(phi), np.sin(phi), 0.0 * phi])
+    val = np.sum(om / np.linalg.norm(x[:, None] - y, axis=0))
+    assert abs(val - exact) < 1e-13 * exact
+
+
+def _cylinder(rho, L, ns, nt):
+    g, gw = I.gl_rule(ns)
+    s = 0.5 * L * g
+    th = 2.0 * np.pi * np.arange(nt) / nt
+    ct, st = np.cos(th)[None, :].repeat(ns, 0), np.sin(th)[None, :].repeat(ns, 0)
+    y = np.stack([rho * ct, rho * st, s[:, None].repeat(nt, 1)])
+    n = np.stack([ct, st, 0.0 * ct])
+    w = (rho * 0.5 * L * gw)[:, None].repeat(nt, 1) * 2.0 * np.pi / nt
+    return y, n, w, s
+
+
+@pytest.mark.parametrize("rho,L,i0", [(0.1, 0.4, 0), (0.1, 0.4, 3), (0.01, 0.5, 3)])
+def test_on_element_single_layer_matches_adaptive_integral(rho, L, i0):
+    """Sec. 3.2.5: the corrected single layer of a constant density over one straight tube
+    element at its own node equals the exact integral (ring closed form in theta, adaptive
+    quadrature in s with the log singularity split off); the punctured sum does not."""
+    ns, nt, j0 = 8, 16, 5
+    y, n, w, s = _cylinder(rho, L, ns, nt)
+    el = T.Element(y, n, w)
+    x, s0 = y[:, i0, j0], s[i0]
+
+    def f(zz):
+        dz = zz - s0
+        den = 4.0 * rho * rho + dz * dz
+        return rho * 4.0 * special.ellipkm1(dz * dz / den) / math.sqrt(den) / (4.0 * np.pi)
+
+    exact = (integrate.quad(f, -0.5 * L, s0, limit=200, epsabs=0, epsrel=2e-14)[0]
+             + integrate.quad(f, s0, 0.5 * L, limit=200, epsabs=0, epsrel=2e-14)[0])
+    E = T.element_block(el, x, "laplace", 1.0, 0.0, own=(i0, j0))
+    with np.errstate(divide="ignore"):
+        G = T.kernel("laplace", 1.0, 0.0, x, y.reshape(3, -1), n.reshape(3, -1))[0] * w.reshape(-1)
+    G[i0 * nt + j0] = 0.0
+    assert abs(G.sum() + E.sum() - exact) < 1e-12 * exact
+    assert abs(G.sum() - exact) > 1e-3 * exact
+
+
+def _torus():
+    return I.torus(R0=1.0, eps=0.25, panels=16, ns=8, nth=32), 16, 8, 32
+
+
+@pytest.mark.parametrize("near_factor,bound", [(0.5, 2e-9), (-100.0, None)])
+def test_laplace_green_identity_on_torus(near_factor, bound):
+    """Green's identity on the surface (Eq. greens-rep, on-surface limit):
+    u / 2 = S[du/dn] - D[u] for u = 1/|x - x0| harmonic inside the tube.  With the
+    corrections of the own and the near elements it holds to ~1e-10; with the own element
+    alone (near_factor < 0) or with none it fails."""
+    S, panels, ns, nt = _torus()
+    n = S.size
+    x0 = np.array([0.3, 0.2, 0.1])
+    d = S.x - x0[:, None]
+    r = np.linalg.norm(d, axis=0)
+    u, dudn = 1.0 / r, -np.sum(d * S.n, axis=0) / r ** 3
+    tg = np.random.default_rng(0).choice(n, 4, replace=False)
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        rS = T.correction_dense_rows(T.correction_rows(S.x, S.n, S.w, panels, ns, nt, "laplace", 1.0, 0.0,
+                                                       near_factor, tg), n, "laplace")
+        rD = T.correction_dense_rows(T.correction_rows(S.x, S.n, S.w, panels, ns, nt, "laplace", 0.0, 1.0,
+                                                       near_factor, tg), n, "laplace")
+    Sp = oracle.laplace(S.x, S.n, S.w, dudn, S.x[:, tg], 1.0, 0.0)
+    Dp = oracle.laplace(S.x, S.n, S.w, u, S.x[:, tg], 0.0, 1.0)
+    err = max(abs(Sp[k] + rS[t] @ dudn - Dp[k] - rD[t] @ u - 0.5 * u[t]) for k, t in enumerate(tg))
+    punct = max(abs(Sp[k] - Dp[k] - 0.5 * u[t]) for k, t in enumerate(tg))
+    scale = np.max(np.abs(u))
+    assert punct > 1e-3 * scale
+    if bound is not None:
+        assert err < bound * scale
+    else:
+        assert err > 1e-6 * scale
+
+
+@pytest.mark.parametrize("near_factor,bound", [(0.5, 1e-10), (-100.0, None)])
+def test_stokes_green_identity_on_torus(near_factor, bound):
+    """u / 2 = S[f] - D[u] on the surface for the flow of a point force outside the tube
+    (Appendix A representation, on-surface limit; double-layer sign as stokes_oracle.c):
+    Stokeslet velocity u = S(x - x0) F and traction f = -(3/4pi) r (r.F)(r.n)/|r|^5."""
+    S, panels, ns, nt = _torus()
+    n = S.size
+    x0, F = np.array([0.3, 0.2, 0.1]), np.array([0.5, -1.0, 0.7])
+    r = S.x - x0[:, None]
+    rl = np.linalg.norm(r, axis=0)
+    rf = F @ r
+    u = (F[:, None] / rl + r * rf / rl ** 3) / (8.0 * np.pi)
+    trac = -(3.0 / (4.0 * np.pi)) * r * rf * np.sum(r * S.n, axis=0) / rl ** 5
+    tg = np.random.default_rng(1).choice(n, 3, replace=False)
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        rS = T.correction_dense_rows(T.correction_rows(S.x, S.n, S.w, panels, ns, nt, "stokes", 1.0, 0.0,
+                                                       near_factor, tg), n, "stokes")
+        rD = T.correction_dense_rows(T.correction_rows(S.x, S.n, S.w, panels, ns, nt, "stokes", 0.0, 1.0,
+                                                       near_factor, tg), n, "stokes")
+    Sp = oracle.combined(S.x, S.n, S.w, trac, S.x[:, tg], 1.0, 0.0)
+    Dp = oracle.combined(S.x, S.n, S.w, u, S.x[:, tg], 0.0, 1.0)
+    scale = np.max(np.abs(u))
+    err = max(np.max(np.abs(Sp[:, k] + rS[t] @ trac.reshape(-1) - Dp[:, k] - rD[t] @ u.reshape(-1)
+                            - 0.5 * u[:, t])) for k, t in enumerate(tg))
+    punct = max(np.max(np.abs(Sp[:, k] - Dp[:, k] - 0.5 * u[:, t])) for k, t in enumerate(tg))
+    assert punct > 1e-3 * scale
+    if bound is not None:
+        assert err < bound * scale
+    else:
+        assert err > 1e-6 * scale
+
+
+def test_combined_kernel_block_is_linear_in_alpha_beta():
+    """The correction is linear in the kernel: E(alpha, beta) = alpha E(1, 0) + beta E(0, 1)."""
+    S, panels, ns, nt = _torus()
+    els = T.elements_of(S.x, S.n, S.w, panels, ns, nt)
+    x = S.x[:, 3 * ns * nt + 7 * nt + 7]         # last GL node of element 3, next to element 4
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        for own, k in (((7, 7), 3), (None, 4)):
+            e1 = T.element_block(els[k], x, "stokes", 1.0, 0.0, own)
+            e2 = T.element_block(els[k], x, "stokes", 0.0, 1.0, own)
+            e3 = T.element_block(els[k], x, "stokes", 1.7, -0.4, own)
+            scale = max(np.max(np.abs(e1)), np.max(np.abs(e2)))
+            assert scale > 1e-4
+            assert np.max(np.abs(e3 - 1.7 * e1 + 0.4 * e2)) < 1e-12 * scale
