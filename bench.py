@@ -19,7 +19,7 @@ metric: pair interactions per second over the whole solve (every operator apply 
 N^2 pairs each), with the solve time (ms_per_step) and the plain-FP64 GMRES solve time of
 the same system reported beside it.
 
-Other workloads (--workload): precision_sweep, batch, helix, laplace, mobility.
+Other workloads (--workload): precision_sweep, batch, helix, laplace, mobility, quadrature.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -71,7 +71,7 @@ def parse(argv=None):
                          "subtraction)")
     ap.add_argument("--workload", default="curved_pipe",
                     choices=["curved_pipe", "precision_sweep", "batch", "helix", "laplace",
-                             "mobility"],
+                             "mobility", "quadrature"],
                     help="curved_pipe: the benchmark line (default); precision_sweep: FP32 vs "
                          "compensated FP32 vs FP64 pair sums on random loops of 64K/256K/1M "
                          "nodes; batch: 64 independent capped arcs in one persistent launch")
@@ -82,6 +82,10 @@ def parse(argv=None):
     ap.add_argument("--helix-pitch", type=float, default=3.0,
                     help="helix: pitch (at 2 the tube surfaces of adjacent turns are 0.011 "
                          "apart, which the punctured sums cannot resolve)")
+    ap.add_argument("--quad-panels", type=int, default=512,
+                    help="quadrature: panels of the random loop (x 128 nodes)")
+    ap.add_argument("--near-factor", type=float, default=0.5,
+                    help="quadrature: near region of an element, radius + f max(length, 2 radius)")
     ap.add_argument("--fp64-solve", action="store_true",
                     help="batch: also time the plain FP64 GMRES solve (minutes)")
     ap.add_argument("--no-graph", action="store_true",
@@ -923,6 +927,123 @@ def run_mobility(args):
     return 0
 
 
+def run_quadrature(args):
+    """Quadrature correction E of the tube elements (Sec. 3.2.1-3.2.4).
+    (1) The paper's torus test (Sec. 5.1, Table t:conv-biest): on-surface Laplace Green's
+        identity at every node for its four discretisations, with the E build time.
+    (2) The paper's slender-loop problem (Sec. 5.2): exterior Laplace Dirichlet problem
+        u = 1 on a random loop of radius 0.005..0.015, eta = 64; GMRES-IR (compensated FP32
+        inner, FP64 residuals) with E at panels x 8 x 16 and at 2 panels x 8 x 24 nodes, and
+        with the punctured operator; the field at points at least 0.5 from the surface is
+        compared with the finer corrected solution.
+    (3) Build time of the Stokes combined-field E on the coarse loop."""
+    import torch
+    from paper_2310_00889_gb300 import build as b
+    b.build()
+    from paper_2310_00889_gb300 import inputs as I
+    from paper_2310_00889_gb300 import sbq
+    torch.cuda.set_device(0)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed_build(*a, **k):
+        ms = []
+        for _ in range(2):
+            e0.record()
+            E = sbq.tube_correction(*a, **k)
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return E, ms[-1]
+
+    def csr_apply(E, v):
+        rowptr, col, val = E
+        m = torch.sparse_csr_tensor(rowptr, col, val, size=(rowptr.shape[0] - 1, v.shape[0]))
+        return (m @ v.unsqueeze(1)).squeeze(1)
+
+    # (1) the paper's torus table
+    printed = {320: (3.3e-3, 0.016), 720: (7.6e-7, 0.055), 1280: (1.1e-9, 0.166), 2000: (2.1e-10, 0.357)}
+    table = []
+    x0 = np.array([1.0, 2.0, 3.0])
+    for ne, nt in ((4, 8), (6, 12), (8, 16), (10, 20)):
+        S = I.torus(R0=1.0, eps=0.25, panels=ne, ns=10, nth=nt)
+        d = S.x - x0[:, None]
+        r = np.linalg.norm(d, axis=0)
+        u = 1.0 / (4.0 * np.pi * r)
+        dudn = -np.sum(d * S.n, axis=0) / (4.0 * np.pi * r ** 3)
+        src, nrm, w = t(S.x), t(S.n), t(S.w)
+        ES, ms_s = timed_build(src, nrm, w, ne, 10, nt, kind="laplace", alpha=1.0, beta=0.0,
+                               near_factor=args.near_factor)
+        ED, ms_d = timed_build(src, nrm, w, ne, 10, nt, kind="laplace", alpha=0.0, beta=1.0,
+                               near_factor=args.near_factor)
+        Sp = sbq.laplace_apply(src, nrm, w, t(dudn), src, 1.0, 0.0, prec="fp64")
+        Dp = sbq.laplace_apply(src, nrm, w, t(u), src, 0.0, 1.0, prec="fp64")
+        lhs = (Sp + csr_apply(ES, t(dudn)) - Dp - csr_apply(ED, t(u))).cpu().numpy()
+        err = float(np.abs(lhs - 0.5 * u).max() / np.abs(u).max())
+        punct = float(np.abs((Sp - Dp).cpu().numpy() - 0.5 * u).max() / np.abs(u).max())
+        table.append({"N": S.size, "elements": ne, "ntheta": nt, "relerr_all_nodes": err,
+                      "relerr_punctured": punct, "paper_err": printed[S.size][0],
+                      "setup_ms_S_and_D": ms_s + ms_d, "paper_setup_s": printed[S.size][1]})
+    print(json.dumps({"workload": "quadrature_paper_torus_table", "ns": 10, "charge": x0.tolist(),
+                      "rows": table}), flush=True)
+
+    # (2) the slender loop, exterior Laplace Dirichlet u = 1
+    eta = 64.0
+    P = args.quad_panels
+    res = {}
+    pts = None
+    fields = {}
+    for tag, panels, nt, corrected in (("coarse_E", P, 16, True), ("fine_E", 2 * P, 24, True),
+                                        ("coarse_punctured", P, 16, False)):
+        s = I.random_loop(seed=1, panels=panels, ns=8, nth=nt)
+        n = s.size
+        if pts is None:
+            rng = np.random.default_rng(5)
+            lo, hi = s.x.min(axis=1), s.x.max(axis=1)
+            cand = lo[:, None] + (hi - lo)[:, None] * rng.random((3, 4096))
+            dmin = np.array([np.linalg.norm(s.x - cand[:, k:k + 1], axis=0).min() for k in range(4096)])
+            pts = cand[:, dmin > 0.5][:, :512]
+        src, nrm, w = t(s.x), t(s.n), t(s.w)
+        E, ms = (timed_build(src, nrm, w, panels, 8, nt, kind="laplace", alpha=eta, beta=1.0,
+                             near_factor=args.near_factor) if corrected else (None, 0.0))
+        op = sbq.LaplaceOp(src, nrm, w, eta, correction=E)
+        op.autotune("fp32c")
+        rhs = torch.ones(n, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        tt = time.perf_counter()
+        x, rep = op.solve(rhs, tol=1e-10, restart=100, inner_prec="fp32c", inner_tol=1e-5,
+                          resid_prec="fp64")
+        torch.cuda.synchronize()
+        solve_ms = (time.perf_counter() - tt) * 1e3
+        fields[tag] = sbq.laplace_apply(src, nrm, w, x, t(pts), eta, 1.0, prec="fp64").cpu().numpy()
+        res[tag] = {"nodes": n, "panels": panels, "ntheta": nt, "setup_ms": ms,
+                    "setup_unknowns_per_s": n / (ms * 1e-3) if ms else None,
+                    "nnz": int(E[2].shape[0]) if E is not None else 0,
+                    "solve_ms": solve_ms, "iters": rep["iters"], "refinements": rep["outer_iters"],
+                    "rel_res": rep["rel_res"], "status": rep["status_name"]}
+        op.close()
+        del E
+        torch.cuda.empty_cache()
+    ref = fields["fine_E"]
+    for tag in ("coarse_E", "coarse_punctured"):
+        res[tag]["field_err_vs_fine_E"] = float(np.abs(fields[tag] - ref).max() / np.abs(ref).max())
+    print(json.dumps({"workload": "quadrature_slender_loop_laplace_u1", "eta": eta,
+                      "check_points": int(pts.shape[1]), "check_min_distance": 0.5,
+                      "near_factor": args.near_factor, "solves": res}), flush=True)
+
+    # (3) Stokes combined-field E on the coarse loop
+    s = I.random_loop(seed=1, panels=P, ns=8, nth=16)
+    E, ms = timed_build(t(s.x), t(s.n), t(s.w), P, 8, 16, kind="stokes", alpha=sbq.slender_eta(0.01),
+                        beta=1.0, near_factor=args.near_factor)
+    nnz = int(E[2].shape[0])
+    items = nnz // (9 * 8 * 16)
+    print(json.dumps({"workload": "quadrature_stokes_build_random_loop", "nodes": s.size,
+                      "build_ms": ms, "nnz": nnz, "csr_bytes": nnz * 16,
+                      "target_element_items": items, "us_per_item": ms * 1e3 / items,
+                      "unknowns_per_s": 3 * s.size / (ms * 1e-3)}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.workload == "helix" and args.impl != "reference":
@@ -937,6 +1058,8 @@ def main():
         return run_laplace(args)
     if args.workload == "mobility":
         return run_mobility(args)
+    if args.workload == "quadrature":
+        return run_quadrature(args)
     return run_gpu(args)
 
 

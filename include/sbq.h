@@ -270,6 +270,43 @@ SBQ_API int stokes_dl_gauss_correction(int nbody, const int64_t *body_off, const
                                        void *stream);
 
 /*
+ * Quadrature correction E of tube elements for stokes_op_create / laplace_op_create: the
+ * paper's on-surface corrections (Eq. nystrom-correction; angular weights of Sec. 3.2.2,
+ * Eqs. modal-greens-fn-coeff / modal-greens-fn-wts; near-singular rule of Sec. 3.2.3;
+ * singular rule of Sec. 3.2.4, Eq. sing-nyst-correc).
+ *   nodes 0 .. nelem*ns*nt - 1 are tube elements: element k holds ns Gauss-Legendre nodes in
+ *   its panel parameter times nt equispaced angles 2 pi j / nt, node k*ns*nt + i*nt + j, and
+ *   every GL row of an element lies on a circle (a tube y = x_c(s) + rho(s)(e1 cos + e2
+ *   sin), Eq. surface-coord).  n_total >= nelem*ns*nt is the operator's node count; nodes
+ *   past the tubes (spheres, caps) get empty rows.
+ *   src, nrm, w  device SoA arrays over n_total nodes, as for stokes_op_create.
+ *   laplace      0: Stokes kernel alpha S + beta D (3 x 3 blocks, Eqs. stokes-sl /
+ *                stokes-dl with the double-layer sign of stokes_dl_apply);
+ *                1: Laplace alpha G + beta dG/dn_y (scalar).  An operator K = diag I + D +
+ *                eta S takes alpha = eta, beta = 1.
+ *   near_factor  element k corrects target x when x lies closer than radius_k + near_factor
+ *                * max(length_k, 2 radius_k) to one of its centreline samples (its GL
+ *                centres and the panel ends); its own element always.  0.5 .. 1 is typical;
+ *                a negative value keeps the own element only.
+ * For target node x and a near element k, row (a, x) gets the entries
+ *   E_ij(x) = sum_m P_mi w_m h_j(x, t_m) - G(x, y_ij) w_ij     (G w of x's own node left out)
+ * for every node (i, j) of k (times the three source components for Stokes): the
+ * correction that turns the punctured sum over k into the accurate integral over k.
+ * Layout: rows component-major (a * n_total + node), columns likewise; a target's row
+ * lists its near elements in increasing order, each as (source component, node) blocks.
+ * Two-phase use: with rowptr == NULL the call only runs the near search and stores the
+ * entry count in *nnz_out (host); then allocate col/val of that size and rowptr of
+ * (laplace ? 1 : 3) * n_total + 1 int64 and call again with the same arguments.
+ * All CSR arrays are device memory; the call synchronises the stream before returning.
+ * Errors: SBQ_EINVAL for sizes (ns in 2..16, nt even in 4..64), null pointers, or rows of
+ * nodes that are not circles.  FP64 throughout.
+ */
+SBQ_API int tube_correction(int64_t nelem, int ns, int nt, int64_t n_total, const double *src,
+                            const double *nrm, const double *w, int laplace, double alpha,
+                            double beta, double near_factor, int64_t *nnz_out, int64_t *rowptr,
+                            int64_t *col, double *val, void *stream);
+
+/*
  * Laplace combined-field operator on the surface nodes (Eq. laplace-bie-new; eta = 1/(2 eps
  * log(1/eps)) for slender bodies):
  *   K sigma = diag sigma + (D + eta S)[sigma] + E sigma,  scalar sigma (n doubles)

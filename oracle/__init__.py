@@ -23,7 +23,7 @@ Contents
     sparse correction E (per closed body, from the Gauss-type identity D[e] = -e/2
     on the surface);
   * `tube_quadrature` (module): the quadrature correction E of tube elements (Sec.
-    3.2.2-3.2.5): modal angular weights, near-singular and singular rules in s, the
+    3.2.1-3.2.4): modal angular weights, near-singular and singular rules in s, the
     sparse E over whole tubes;
   * `eta_slender`: the slender-body mixing parameter 1 / (2 eps log(1/eps))
     (Sec. 4.1, Laplace and Stokes slender combined-field formulations).

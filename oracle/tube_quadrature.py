@@ -1,4 +1,4 @@
-"""CPU FP64 oracle for the quadrature correction E of tube elements (paper Sec. 3.2.2-3.2.5).
+"""CPU FP64 oracle for the quadrature correction E of tube elements (paper Sec. 3.2.1-3.2.4).
 
 TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU-baseline leg of
 the benchmark use it; it shares no code with the CUDA library.
@@ -21,7 +21,7 @@ leaves it out.  The pieces, in the paper's order:
     nodes (discrete Fourier modes 0 and 1) and interpolated in t with the Lagrange basis
     of the GL nodes, so y(t, theta), its derivatives, the unit normal n and the area
     element J = |y_t x y_theta| are defined at every (t, theta);
-  * angular weights h_j(x, t) (Sec. 3.2.3): find the angle theta_0 of the point of the
+  * angular weights h_j(x, t) (Sec. 3.2.2): find the angle theta_0 of the point of the
     circle at t closest to x and its relative distance alpha = dist / radius; integrate
     the modal integrands G(x, y(t, theta)) e^{i l theta} J, l = 0 .. N_theta/2, with a
     composite Gauss--Legendre rule in theta - theta_0 on [-pi, pi] whose panels are refined
@@ -30,18 +30,18 @@ leaves it out.  The pieces, in the paper's order:
     modal-greens-fn-wts), the Nyquist mode entering as cos(N_theta theta / 2);
   * outer rule in t: for a target on the element (one of its nodes, parameter t_0) each
     side of t_0 is split dyadically towards t_0 until the panel next to t_0 is no longer
-    than the tube radius; that panel takes a rule for p(t) log|t - t_0| + q(t) (Sec. 3.2.5),
+    than the tube radius; that panel takes a rule for p(t) log|t - t_0| + q(t) (Sec. 3.2.4),
     the others Gauss--Legendre.  For a target off the element, each side of the closest
     parameter t* is split dyadically towards t* until the panel next to it is no longer
-    than the distance d* of x from the element (Sec. 3.2.4);
+    than the distance d* of x from the element (Sec. 3.2.3);
   * P: Lagrange interpolation from the element's GL nodes to the outer rule's nodes.
 
 Readings (the paper is silent on them): the log-singular rule is Gauss--Legendre after the
 substitution t = t_0 + h u^6 (exact for the grading, accurate to rounding for p log + q);
 panels carry 16 Gauss--Legendre nodes; the element's near region is the set of points
 closer than radius + f max(length, 2 radius) to its centreline samples (f = near_factor).
-The generalized Chebyshev compression of the angular and singular rules (Sec. 3.2.3,
-Sec. 3.2.5, App. B) is an optimisation of these same integrals and is not part of the
+The generalized Chebyshev compression of the angular and singular rules (Sec. 3.2.2,
+Sec. 3.2.4, App. B) is an optimisation of these same integrals and is not part of the
 definition here.
 
 Kernels: Stokes alpha S + beta D (3 x 3, with the double-layer sign of stokes_oracle.c),
@@ -349,7 +349,7 @@ def _levels(phys, scale):
 
 
 def s_rule_on_element(el: Element, t0):
-    """Outer rule for a target at the element's own node with parameter t0 (Sec. 3.2.5),
+    """Outer rule for a target at the element's own node with parameter t0 (Sec. 3.2.4),
     as offsets delta = t - t0 and weights."""
     g, gw = gl01(Q_S)
     us, uw = singular_rule()
@@ -397,7 +397,7 @@ def nearest_parameter(el: Element, x):
 
 
 def s_rule_near(el: Element, tstar, dstar):
-    """Outer rule for a target off the element (Sec. 3.2.4)."""
+    """Outer rule for a target off the element (Sec. 3.2.3)."""
     g, gw = gl01(Q_S)
     ts, ws = [], []
     for ell in (1.0 - tstar, -1.0 - tstar):

@@ -143,6 +143,11 @@ int mob_axpy(long long n, double a, const double *x, double *y, cudaStream_t s);
 int dl_gauss_correction(int nbody, const int64_t *body_off, const double *src, const double *nrm,
                         const double *w, int prec, int64_t *rowptr, int64_t *col, double *val,
                         cudaStream_t s);
+// tube_quad.cu: quadrature correction of tube elements (on-surface targets).
+int build_tube_correction(long long nelem, int ns, int nt, long long ntot, const double *src,
+                    const double *nrm, const double *w, int laplace, double alpha, double beta,
+                    double near_factor, int64_t *nnz_out, int64_t *rowptr, int64_t *col,
+                    double *val, cudaStream_t s);
 int gmres_destroy(struct GmresWS *ws);
 
 }  // namespace sbq

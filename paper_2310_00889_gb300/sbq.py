@@ -108,6 +108,8 @@ def _load():
                                  ctypes.POINTER(_dbl)], _int),
         "stokes_dl_gauss_correction": ([_int, _vp, _vp, _vp, _vp, _int, _vp, _vp, _vp, _vp],
                                        _int),
+        "tube_correction": ([_i64, _int, _int, _i64, _vp, _vp, _vp, _int, _dbl, _dbl, _dbl,
+                             ctypes.POINTER(_i64), _vp, _vp, _vp, _vp], _int),
         "sbq_destroy": ([_vp], None),
     }
     for name, (args, res) in sig.items():
@@ -233,6 +235,34 @@ def dl_gauss_correction(src, nrm, w, body_off=None, prec="fp64", stream=None):
                                           _prec(prec), _ptr(rowptr), _ptr(col), _ptr(val),
                                           _stream(stream)))
     return rowptr, col, val
+
+
+def tube_correction(src, nrm, w, nelem, ns, nt, kind="stokes", alpha=1.0, beta=1.0,
+                    near_factor=0.5, stream=None):
+    """Quadrature correction E (rowptr, col, val) of the tube elements that make up the first
+    nelem * ns * nt nodes (Sec. 3.2.1-3.2.4): for every tube node and every element whose
+    near region holds it, the entries that turn the punctured sum over the element into the
+    accurate integral.  kind "stokes" (alpha S + beta D, 3 x 3) or "laplace" (scalar); an
+    operator K = diag I + D + eta S takes alpha = eta, beta = 1.  Pass the result as
+    StokesOp / LaplaceOp (..., correction=...)."""
+    n = src.shape[1]
+    _dev(src, (3, n), "src")
+    _dev(nrm, (3, n), "nrm")
+    _dev(w, (n,), "w")
+    if kind not in ("stokes", "laplace"):
+        raise ValueError("kind must be 'stokes' or 'laplace'")
+    lap = 1 if kind == "laplace" else 0
+    nnz = _i64(0)
+    args = (int(nelem), int(ns), int(nt), int(n), _ptr(src), _ptr(nrm), _ptr(w), lap, float(alpha),
+            float(beta), float(near_factor))
+    _check(lib.tube_correction(*args, ctypes.byref(nnz), None, None, None, _stream(stream)))
+    dev = src.device
+    rowptr = torch.empty((1 if lap else 3) * n + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(max(nnz.value, 1), dtype=torch.int64, device=dev)
+    val = torch.empty(max(nnz.value, 1), dtype=torch.float64, device=dev)
+    _check(lib.tube_correction(*args, ctypes.byref(nnz), _ptr(rowptr), _ptr(col), _ptr(val),
+                               _stream(stream)))
+    return rowptr, col[:nnz.value], val[:nnz.value]
 
 
 def laplace_apply(src, nrm, w, sigma, trg, alpha=1.0, beta=0.0, prec="fp32c", out=None,
