@@ -39,7 +39,6 @@ constexpr int TQ_SING_N = 24;      // log-singular rule: GL in u after t = u^6
 constexpr int TQ_SING_G = 6;
 constexpr int TQ_LMAX = 60;        // deepest dyadic level
 constexpr int TQ_NS_MAX = 16;
-constexpr int TQ_NT_MAX = 64;
 constexpr int TQ_REFINE = 3;       // rounds of 128-point refinement of t*
 
 struct ElemGeo {
@@ -112,8 +111,7 @@ __device__ __forceinline__ void kern(const double r[3], const double n[3], doubl
                                      double beta, double K[NC])
 {
     const double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-    const double rl = sqrt(r2);
-    const double ri = 1.0 / rl;
+    const double ri = rsqrt(r2);
     const double rn = r[0] * n[0] + r[1] * n[1] + r[2] * n[2];
     constexpr double PI_ = 3.14159265358979323846;
     if (NC == 1) {
@@ -278,21 +276,6 @@ __host__ __device__ inline size_t tq_smem_doubles(int NC, int ns, int nt)
            + static_cast<size_t>(NC) * ns * nt + 128 + 8;
 }
 
-// Coefficients C, A, B (and derivatives) of the circle at t from the basis in s.L / s.dL.
-__device__ __forceinline__ void circle_coeffs(const Smem &s, int ns, double t_unused, double *G6)
-{
-    (void)t_unused;
-    for (int v = 0; v < 18; ++v) {
-        const int which = v / 3, d = v % 3;
-        const double *src = (which % 3 == 0) ? s.sc : (which % 3 == 1) ? s.sa : s.sb;
-        const double *basis = which < 3 ? s.L : s.dL;
-        double acc = 0.0;
-        for (int i = 0; i < ns; ++i)
-            acc += basis[i] * src[d * ns + i];
-        G6[v] = acc;
-    }
-}
-
 template <int NC>
 __global__ void __launch_bounds__(TQ_THREADS)
 k_tube_items(TQParams p, const Item *__restrict__ items, const ElemGeo *__restrict__ geo,
@@ -342,6 +325,8 @@ k_tube_items(TQParams p, const Item *__restrict__ items, const ElemGeo *__restri
     const bool own = (it.t / per) == it.k;
     const int i0 = own ? (it.t % per) / nt : 0, j0 = own ? it.t % nt : 0;
     const double sgn = g.sgn, rho_max = g.rho_max, speed = g.speed_max;
+    double sj0, cj0;
+    sincospi(2.0 * j0 / nt, &sj0, &cj0);
     constexpr double PI_ = 3.14159265358979323846;
     __syncthreads();
 
@@ -502,65 +487,70 @@ k_tube_items(TQParams p, const Item *__restrict__ items, const ElemGeo *__restri
                             out[d] = C[d] + A[d] * cs + B[d] * sn - x[d];
                     }
                 };
-                // closest angle: Newton on (y - x) . y_theta (own: as an offset psi from thj0)
-                double th0;
-                if (own) {
-                    th0 = 0.0;   // psi
-                    for (int itn = 0; itn < 4; ++itn) {
-                        const double ang = thj0 + th0;
-                        double ymx[3];
-                        ymx_at(ang, th0, ymx);
-                        double sn, cs;
-                        sincos(ang, &sn, &cs);
-                        double yth[3], ythth[3];
-                        for (int d = 0; d < 3; ++d) {
-                            const double Ad = a0[d] + dA[d], Bd = b0[d] + dB[d];
-                            yth[d] = -Ad * sn + Bd * cs;
-                            ythth[d] = -Ad * cs - Bd * sn;
+                // closest angle (Newton on (y - x) . y_theta; own: as an offset psi from thj0),
+                // relative distance and depth of the angular rule: one thread, broadcast
+                if (tid == 0) {
+                    double th0;
+                    if (own) {
+                        th0 = 0.0;   // psi
+                        for (int itn = 0; itn < 4; ++itn) {
+                            const double ang = thj0 + th0;
+                            double ymx[3];
+                            ymx_at(ang, th0, ymx);
+                            double sn, cs;
+                            sincos(ang, &sn, &cs);
+                            double yth[3], ythth[3];
+                            for (int d = 0; d < 3; ++d) {
+                                const double Ad = a0[d] + dA[d], Bd = b0[d] + dB[d];
+                                yth[d] = -Ad * sn + Bd * cs;
+                                ythth[d] = -Ad * cs - Bd * sn;
+                            }
+                            const double fp = dot3(yth, yth) + dot3(ymx, ythth);
+                            if (fp <= 0.0)
+                                break;
+                            th0 -= dot3(ymx, yth) / fp;
                         }
-                        const double fp = dot3(yth, yth) + dot3(ymx, ythth);
-                        if (fp <= 0.0)
-                            break;
-                        th0 -= dot3(ymx, yth) / fp;
-                    }
-                } else {
-                    const double dx[3] = {x[0] - C[0], x[1] - C[1], x[2] - C[2]};
-                    th0 = atan2(dot3(dx, B), dot3(dx, A));
-                    for (int itn = 0; itn < 3; ++itn) {
-                        double sn, cs;
-                        sincos(th0, &sn, &cs);
-                        double ymx[3], yth[3], ythth[3];
-                        for (int d = 0; d < 3; ++d) {
-                            ymx[d] = C[d] + A[d] * cs + B[d] * sn - x[d];
-                            yth[d] = -A[d] * sn + B[d] * cs;
-                            ythth[d] = -A[d] * cs - B[d] * sn;
+                    } else {
+                        const double dx[3] = {x[0] - C[0], x[1] - C[1], x[2] - C[2]};
+                        th0 = atan2(dot3(dx, B), dot3(dx, A));
+                        for (int itn = 0; itn < 3; ++itn) {
+                            double sn, cs;
+                            sincos(th0, &sn, &cs);
+                            double ymx[3], yth[3], ythth[3];
+                            for (int d = 0; d < 3; ++d) {
+                                ymx[d] = C[d] + A[d] * cs + B[d] * sn - x[d];
+                                yth[d] = -A[d] * sn + B[d] * cs;
+                                ythth[d] = -A[d] * cs - B[d] * sn;
+                            }
+                            const double fp = dot3(yth, yth) + dot3(ymx, ythth);
+                            if (fp <= 0.0)
+                                break;
+                            th0 -= dot3(ymx, yth) / fp;
                         }
-                        const double fp = dot3(yth, yth) + dot3(ymx, ythth);
-                        if (fp <= 0.0)
-                            break;
-                        th0 -= dot3(ymx, yth) / fp;
                     }
-                }
-                double rho2 = 0.0;
-                for (int d = 0; d < 3; ++d) {
-                    const double Ad = own ? a0[d] + dA[d] : A[d];
-                    const double Bd = own ? b0[d] + dB[d] : B[d];
-                    rho2 += Ad * Ad + Bd * Bd;
-                }
-                const double rho = sqrt(0.5 * rho2);
-                double alpha_rel;
-                {
+                    double rho2 = 0.0;
+                    for (int d = 0; d < 3; ++d) {
+                        const double Ad = own ? a0[d] + dA[d] : A[d];
+                        const double Bd = own ? b0[d] + dB[d] : B[d];
+                        rho2 += Ad * Ad + Bd * Bd;
+                    }
+                    const double rho = sqrt(0.5 * rho2);
                     double ymx[3];
                     ymx_at(own ? thj0 + th0 : th0, th0, ymx);
-                    alpha_rel = sqrt(dot3(ymx, ymx)) / rho;
+                    const double alpha_rel = sqrt(dot3(ymx, ymx)) / rho;
+                    int Lv;
+                    if (alpha_rel >= lb)
+                        Lv = 0;
+                    else if (alpha_rel <= 0.0)
+                        Lv = TQ_LMAX;
+                    else
+                        Lv = min(TQ_LMAX, static_cast<int>(ceil(log2(lb / alpha_rel))));
+                    s.SD[1] = th0;
+                    s.SD[2] = static_cast<double>(Lv);
                 }
-                int L;
-                if (alpha_rel >= lb)
-                    L = 0;
-                else if (alpha_rel <= 0.0)
-                    L = TQ_LMAX;
-                else
-                    L = min(TQ_LMAX, static_cast<int>(ceil(log2(lb / alpha_rel))));
+                __syncthreads();
+                const double th0 = s.SD[1];
+                const int L = static_cast<int>(s.SD[2]);
                 const int Mh = TQ_Q * (L + nb);
                 const int M = 2 * Mh;
                 double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
@@ -585,11 +575,24 @@ k_tube_items(TQParams p, const Item *__restrict__ items, const ElemGeo *__restri
                         if (sidek == 0)
                             phi = -phi;
                         const double psi = th0 + phi;                 // own: offset from thj0
-                        const double ang = own ? thj0 + psi : psi;
-                        double ymx[3];
-                        ymx_at(ang, psi, ymx);
-                        double sn, cs;
-                        sincos(ang, &sn, &cs);
+                        double sn, cs, ymx[3];
+                        if (own) {
+                            // one sincos: half-angle of psi, the rest by angle addition
+                            double s2, c2;
+                            sincos(0.5 * psi, &s2, &c2);
+                            const double spsi = 2.0 * s2 * c2, cpsi = 1.0 - 2.0 * s2 * s2;
+                            sn = sj0 * cpsi + cj0 * spsi;
+                            cs = cj0 * cpsi - sj0 * spsi;
+                            const double sh = sj0 * c2 + cj0 * s2;   // sin(thj0 + psi / 2)
+                            const double ch = cj0 * c2 - sj0 * s2;   // cos(thj0 + psi / 2)
+                            const double dcos = -2.0 * sh * s2, dsin = 2.0 * ch * s2;
+                            for (int d = 0; d < 3; ++d)
+                                ymx[d] = dC[d] + dA[d] * cs + a0[d] * dcos + dB[d] * sn + b0[d] * dsin;
+                        } else {
+                            sincos(psi, &sn, &cs);
+                            for (int d = 0; d < 3; ++d)
+                                ymx[d] = C[d] + A[d] * cs + B[d] * sn - x[d];
+                        }
                         double yt[3], yth[3];
                         for (int d = 0; d < 3; ++d) {
                             yt[d] = Ct[d] + At[d] * cs + Bt[d] * sn;
@@ -597,8 +600,10 @@ k_tube_items(TQParams p, const Item *__restrict__ items, const ElemGeo *__restri
                         }
                         double cr[3] = {yth[1] * yt[2] - yth[2] * yt[1], yth[2] * yt[0] - yth[0] * yt[2],
                                         yth[0] * yt[1] - yth[1] * yt[0]};
-                        const double J = sqrt(dot3(cr, cr));
-                        const double inv = sgn / J;
+                        const double J2 = dot3(cr, cr);
+                        const double invJ = rsqrt(J2);
+                        const double J = J2 * invJ;
+                        const double inv = sgn * invJ;
                         const double nn[3] = {cr[0] * inv, cr[1] * inv, cr[2] * inv};
                         const double r[3] = {-ymx[0], -ymx[1], -ymx[2]};
                         double K[NC];
