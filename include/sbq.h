@@ -9,8 +9,9 @@
  * slender-body BIE (Sec. 4.1, Eq. stokes-bie-new), and solves K sigma = u0 with
  * GMRES (plain FP64 or double-float, or FP32 / compensated-FP32 inner solves with
  * FP64 or bound-certified double-float iterative refinement).  Also: the Laplace
- * layers and operator (Sec. 4.1), the Stokes mobility formulation (Sec. 4.2) and the
- * double-layer singularity subtraction as a sparse correction.
+ * layers and operator (Sec. 4.1), the Stokes mobility formulation (Sec. 4.2), the
+ * paper's quadrature correction E of tube elements (Sec. 3.2.1-3.2.4, tube_correction)
+ * and the double-layer singularity subtraction as a sparse correction.
  *
  * Kernels (viscosity 1, r = x - y, n = outward unit normal at the source y):
  *   S(r)    = (1/8pi) (I/|r| + r r^T / |r|^3)                     Eq. stokes-sl
