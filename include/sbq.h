@@ -308,6 +308,25 @@ SBQ_API int tube_correction(int64_t nelem, int ns, int nt, int64_t n_total, cons
                             int64_t *col, double *val, void *stream);
 
 /*
+ * The same correction for off-surface targets near the tubes (Sec. 3.2.3, near-singular
+ * quadrature): evaluating a layer potential at points close to a slender body.
+ *   trg    device SoA array of ntrg target points (3 * ntrg doubles).  Targets must lie off
+ *          the surface; a target on it takes the near-singular rule, which converges there
+ *          only as fast as the dyadic refinement (60 levels at most) allows.
+ *   Rows are component-major over the targets (a * ntrg + target), columns over the nodes
+ *   (b * n_total + node), as for tube_correction; an element corrects a target when the
+ *   target lies in its near region (near_factor as above; no element is the target's own).
+ * Use: u(trg) = (alpha S + beta D)[sigma](trg) from stokes_combined_apply (or the Laplace
+ * apply) plus this E times sigma.  Same two-phase use, ownership and errors as
+ * tube_correction; rowptr holds (laplace ? 1 : 3) * ntrg + 1 entries.
+ */
+SBQ_API int tube_correction_targets(int64_t nelem, int ns, int nt, int64_t n_total,
+                                    const double *src, const double *nrm, const double *w,
+                                    int64_t ntrg, const double *trg, int laplace, double alpha,
+                                    double beta, double near_factor, int64_t *nnz_out,
+                                    int64_t *rowptr, int64_t *col, double *val, void *stream);
+
+/*
  * Laplace combined-field operator on the surface nodes (Eq. laplace-bie-new; eta = 1/(2 eps
  * log(1/eps)) for slender bodies):
  *   K sigma = diag sigma + (D + eta S)[sigma] + E sigma,  scalar sigma (n doubles)

@@ -483,6 +483,20 @@ def correction_rows(src, nrm, w, nelem, ns, nt, kind, alpha, beta, near_factor, 
     return out
 
 
+def correction_rows_offsurface(src, nrm, w, nelem, ns, nt, kind, alpha, beta, near_factor, trg):
+    """Rows of E for off-surface targets trg (3, m) (Sec. 3.2.3): for every element whose near
+    region holds the target, the near-singular rule; returns a dict k -> list of (element,
+    block) keyed by the target's column index in trg."""
+    els = elements_of(src, nrm, w, nelem, ns, nt)
+    trg = np.asarray(trg, dtype=np.float64)
+    out = {}
+    for m in range(trg.shape[1]):
+        x = trg[:, m]
+        out[m] = [(k, element_block(els[k], x, kind, alpha, beta, None))
+                  for k in near_elements(els, x, -1, near_factor)]
+    return out
+
+
 def correction_dense_rows(rows, n, kind):
     """Dense rows of E (component-major rows and columns, as the CSR layout): for Stokes
     a dict target -> (3, 3 n), for Laplace target -> (n,)."""

@@ -679,9 +679,39 @@ SBQ_API int tube_correction(int64_t nelem, int ns, int nt, int64_t n_total, cons
         return fail(SBQ_EINVAL, "null rowptr and nnz_out");
     if (nelem > 0 && (!src || !nrm || !w))
         return fail(SBQ_EINVAL, "null geometry pointer");
-    return build_tube_correction(nelem, ns, nt, n_total, src, nrm, w, laplace, alpha, beta,
-                           near_factor, nnz_out, rowptr, col, val,
-                           static_cast<cudaStream_t>(stream));
+    return build_tube_correction(nelem, ns, nt, n_total, src, nrm, w, 0, nullptr, laplace, alpha,
+                                 beta, near_factor, nnz_out, rowptr, col, val,
+                                 static_cast<cudaStream_t>(stream));
+}
+
+SBQ_API int tube_correction_targets(int64_t nelem, int ns, int nt, int64_t n_total,
+                                    const double *src, const double *nrm, const double *w,
+                                    int64_t ntrg, const double *trg, int laplace, double alpha,
+                                    double beta, double near_factor, int64_t *nnz_out,
+                                    int64_t *rowptr, int64_t *col, double *val, void *stream)
+{
+    clear_error();
+    if (nelem < 0 || n_total < 0 || ntrg < 0)
+        return fail(SBQ_EINVAL, "negative size");
+    if (ns < 2 || ns > 16)
+        return fail(SBQ_EINVAL, "ns must be in 2..16");
+    if (nt < 4 || nt > 64 || (nt & 1))
+        return fail(SBQ_EINVAL, "nt must be even and in 4..64");
+    if (nelem * ns * nt > n_total)
+        return fail(SBQ_EINVAL, "n_total below nelem * ns * nt");
+    if (n_total > (1LL << 31) / 3 || ntrg > (1LL << 31) / 3)
+        return fail(SBQ_EINVAL, "n_total or ntrg above 2^31 / 3");
+    if (laplace != 0 && laplace != 1)
+        return fail(SBQ_EINVAL, "laplace must be 0 or 1");
+    if (!std::isfinite(alpha) || !std::isfinite(beta) || !std::isfinite(near_factor))
+        return fail(SBQ_EINVAL, "non-finite alpha, beta or near_factor");
+    if (!rowptr && !nnz_out)
+        return fail(SBQ_EINVAL, "null rowptr and nnz_out");
+    if ((nelem > 0 && (!src || !nrm || !w)) || (ntrg > 0 && !trg))
+        return fail(SBQ_EINVAL, "null geometry or target pointer");
+    return build_tube_correction(nelem, ns, nt, n_total, src, nrm, w, ntrg, trg ? trg : src,
+                                 laplace, alpha, beta, near_factor, nnz_out, rowptr, col, val,
+                                 static_cast<cudaStream_t>(stream));
 }
 
 SBQ_API void sbq_destroy(void *handle)

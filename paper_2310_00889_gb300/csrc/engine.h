@@ -144,10 +144,13 @@ int dl_gauss_correction(int nbody, const int64_t *body_off, const double *src, c
                         const double *w, int prec, int64_t *rowptr, int64_t *col, double *val,
                         cudaStream_t s);
 // tube_quad.cu: quadrature correction of tube elements (on-surface targets).
+// trg == nullptr: targets are the tube nodes (rows over all ntot nodes); else ntrg
+// off-surface points.
 int build_tube_correction(long long nelem, int ns, int nt, long long ntot, const double *src,
-                    const double *nrm, const double *w, int laplace, double alpha, double beta,
-                    double near_factor, int64_t *nnz_out, int64_t *rowptr, int64_t *col,
-                    double *val, cudaStream_t s);
+                          const double *nrm, const double *w, long long ntrg, const double *trg,
+                          int laplace, double alpha, double beta, double near_factor,
+                          int64_t *nnz_out, int64_t *rowptr, int64_t *col, double *val,
+                          cudaStream_t s);
 int gmres_destroy(struct GmresWS *ws);
 
 }  // namespace sbq

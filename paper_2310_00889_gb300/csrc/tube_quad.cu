@@ -231,15 +231,27 @@ __device__ __forceinline__ bool is_near(const ElemGeo &g, int ns, const double x
     return lim > 0.0 && d2 < lim * lim;
 }
 
-__global__ void k_near(long long ntube, long long nelem, TQParams p, double f,
-                       const double *__restrict__ src, const ElemGeo *__restrict__ geo,
-                       const long long *__restrict__ off, int *out)
+// Targets: the tube nodes (trg == nullptr; each has its own element) or an array of
+// off-surface points trg (SoA, ntarget points, no own element).
+__global__ void k_near(long long ntarget, long long nelem, TQParams p, double f,
+                       const double *__restrict__ src, const double *__restrict__ trg,
+                       const ElemGeo *__restrict__ geo, const long long *__restrict__ off, int *out)
 {
     const long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
-    if (t >= ntube)
+    if (t >= ntarget)
         return;
-    const double x[3] = {src[t], src[p.ntot + t], src[2 * p.ntot + t]};
-    const long long own = t / p.per;
+    double x[3];
+    long long own = -1;
+    if (trg) {
+        x[0] = trg[t];
+        x[1] = trg[ntarget + t];
+        x[2] = trg[2 * ntarget + t];
+    } else {
+        x[0] = src[t];
+        x[1] = src[p.ntot + t];
+        x[2] = src[2 * p.ntot + t];
+        own = t / p.per;
+    }
     int c = 0;
     for (long long k = 0; k < nelem; ++k) {
         if (k == own || is_near(geo[k], p.ns, x, f)) {
@@ -280,8 +292,9 @@ template <int NC>
 __global__ void __launch_bounds__(TQ_THREADS)
 k_tube_items(TQParams p, const Item *__restrict__ items, const ElemGeo *__restrict__ geo,
              const double *__restrict__ src, const double *__restrict__ nrm,
-             const double *__restrict__ wgt, const int64_t *__restrict__ rowptr,
-             int64_t *__restrict__ col, double *__restrict__ val)
+             const double *__restrict__ wgt, const double *__restrict__ trg, long long ntarget,
+             const int64_t *__restrict__ rowptr, int64_t *__restrict__ col,
+             double *__restrict__ val)
 {
     extern __shared__ double sm[];
     const int tid = threadIdx.x;
@@ -321,8 +334,11 @@ k_tube_items(TQParams p, const Item *__restrict__ items, const ElemGeo *__restri
     }
     for (int e = tid; e < NC * ns * nt; e += TQ_THREADS)
         s.EB[e] = 0.0;
-    const double x[3] = {src[it.t], src[N + it.t], src[2 * N + it.t]};
-    const bool own = (it.t / per) == it.k;
+    // rows: component-major over the targets (the nodes: stride N; off-surface: ntarget)
+    const long long RS = trg ? ntarget : N;
+    const double x[3] = {trg ? trg[it.t] : src[it.t], trg ? trg[ntarget + it.t] : src[N + it.t],
+                         trg ? trg[2 * ntarget + it.t] : src[2 * N + it.t]};
+    const bool own = !trg && (it.t / per) == it.k;
     const int i0 = own ? (it.t % per) / nt : 0, j0 = own ? it.t % nt : 0;
     const double sgn = g.sgn, rho_max = g.rho_max, speed = g.speed_max;
     double sj0, cj0;
@@ -734,7 +750,7 @@ k_tube_items(TQParams p, const Item *__restrict__ items, const ElemGeo *__restri
         for (int e = tid; e < 9 * per; e += TQ_THREADS) {
             const int a = e / (3 * per), rem = e % (3 * per);
             const int b = rem / per, node = rem % per;
-            const int64_t pos = rowptr[a * N + it.t] + static_cast<int64_t>(it.slot) * 3 * per
+            const int64_t pos = rowptr[a * RS + it.t] + static_cast<int64_t>(it.slot) * 3 * per
                                 + static_cast<int64_t>(b) * per + node;
             col[pos] = b * N + kbase + node;
             val[pos] = s.EB[sym[a][b] * per + node];
@@ -783,12 +799,17 @@ void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
 }  // namespace
 
 int build_tube_correction(long long nelem, int ns, int nt, long long ntot, const double *src,
-                    const double *nrm, const double *w, int laplace, double alpha, double beta,
-                    double near_factor, int64_t *nnz_out, int64_t *rowptr, int64_t *col,
-                    double *val, cudaStream_t s)
+                          const double *nrm, const double *w, long long ntrg, const double *trg,
+                          int laplace, double alpha, double beta, double near_factor,
+                          int64_t *nnz_out, int64_t *rowptr, int64_t *col, double *val,
+                          cudaStream_t s)
 {
     const long long per = static_cast<long long>(ns) * nt;
     const long long ntube = nelem * per;
+    // targets: the tube nodes (rows over all ntot nodes, tube nodes first) or ntrg
+    // off-surface points
+    const long long ntarget = trg ? ntrg : ntube;
+    const long long nrows_per_comp = trg ? ntrg : ntot;
     const int nc_rows = laplace ? 1 : 3;
     TQParams p{};
     {
@@ -819,51 +840,54 @@ int build_tube_correction(long long nelem, int ns, int nt, long long ntot, const
     std::vector<long long> cnt_off;
     std::vector<int> h_cnt, h_list;
     DevBuf d_geo, d_bad, d_cnt, d_off, d_list;
-    if (ntube > 0) {
+    if (ntube > 0 && ntarget > 0) {
         SBQ_TRY(d_geo.alloc(nelem * sizeof(ElemGeo)));
         SBQ_TRY(d_bad.alloc(sizeof(int)));
-        SBQ_TRY(d_cnt.alloc(ntube * sizeof(int)));
+        SBQ_TRY(d_cnt.alloc(ntarget * sizeof(int)));
         SBQ_CUDA(cudaMemsetAsync(d_bad.p, 0, sizeof(int), s));
         const unsigned ge = static_cast<unsigned>((nelem + 63) / 64);
         k_elem_setup<<<ge, 64, 0, s>>>(nelem, p, src, nrm, d_geo.as<ElemGeo>(), d_bad.as<int>());
         SBQ_CUDA(cudaGetLastError());
-        const unsigned gt = static_cast<unsigned>((ntube + 127) / 128);
-        k_near<<<gt, 128, 0, s>>>(ntube, nelem, p, near_factor, src, d_geo.as<ElemGeo>(), nullptr,
-                                  d_cnt.as<int>());
+        const unsigned gt = static_cast<unsigned>((ntarget + 127) / 128);
+        k_near<<<gt, 128, 0, s>>>(ntarget, nelem, p, near_factor, src, trg, d_geo.as<ElemGeo>(),
+                                  nullptr, d_cnt.as<int>());
         SBQ_CUDA(cudaGetLastError());
         int bad = 0;
-        h_cnt.resize(ntube);
+        h_cnt.resize(ntarget);
         SBQ_CUDA(cudaMemcpyAsync(&bad, d_bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-        SBQ_CUDA(cudaMemcpyAsync(h_cnt.data(), d_cnt.p, ntube * sizeof(int), cudaMemcpyDeviceToHost, s));
+        SBQ_CUDA(cudaMemcpyAsync(h_cnt.data(), d_cnt.p, ntarget * sizeof(int), cudaMemcpyDeviceToHost, s));
         SBQ_CUDA(cudaStreamSynchronize(s));
         if (bad) {
             set_error("tube_correction: element rows of nodes are not circles (nodes must be "
                       "panel-major, then GL node, then equispaced angle)");
             return SBQ_EINVAL;
         }
-        cnt_off.assign(ntube + 1, 0);
-        for (long long t = 0; t < ntube; ++t)
+        cnt_off.assign(ntarget + 1, 0);
+        for (long long t = 0; t < ntarget; ++t)
             cnt_off[t + 1] = cnt_off[t] + h_cnt[t];
-        SBQ_TRY(d_off.alloc((ntube + 1) * sizeof(long long)));
-        SBQ_TRY(d_list.alloc(std::max<long long>(cnt_off[ntube], 1) * sizeof(int)));
-        SBQ_CUDA(cudaMemcpyAsync(d_off.p, cnt_off.data(), (ntube + 1) * sizeof(long long),
+        SBQ_TRY(d_off.alloc((ntarget + 1) * sizeof(long long)));
+        SBQ_TRY(d_list.alloc(std::max<long long>(cnt_off[ntarget], 1) * sizeof(int)));
+        SBQ_CUDA(cudaMemcpyAsync(d_off.p, cnt_off.data(), (ntarget + 1) * sizeof(long long),
                                  cudaMemcpyHostToDevice, s));
-        k_near<<<gt, 128, 0, s>>>(ntube, nelem, p, near_factor, src, d_geo.as<ElemGeo>(),
+        k_near<<<gt, 128, 0, s>>>(ntarget, nelem, p, near_factor, src, trg, d_geo.as<ElemGeo>(),
                                   d_off.as<long long>(), d_list.as<int>());
         SBQ_CUDA(cudaGetLastError());
-        h_list.resize(cnt_off[ntube]);
-        SBQ_CUDA(cudaMemcpyAsync(h_list.data(), d_list.p, cnt_off[ntube] * sizeof(int),
+        h_list.resize(cnt_off[ntarget]);
+        SBQ_CUDA(cudaMemcpyAsync(h_list.data(), d_list.p, cnt_off[ntarget] * sizeof(int),
                                  cudaMemcpyDeviceToHost, s));
         SBQ_CUDA(cudaStreamSynchronize(s));
+    } else {
+        h_cnt.assign(ntarget, 0);
+        cnt_off.assign(ntarget + 1, 0);
     }
     // rows: component-major over all ntot nodes; a tube target's row holds its near
     // elements' nodes (times the three source components for Stokes)
-    std::vector<int64_t> h_rowptr(static_cast<size_t>(nc_rows) * ntot + 1, 0);
+    std::vector<int64_t> h_rowptr(static_cast<size_t>(nc_rows) * nrows_per_comp + 1, 0);
     const int64_t row_mul = laplace ? per : 3 * per;
     for (int a = 0; a < nc_rows; ++a)
-        for (long long t = 0; t < ntot; ++t) {
-            const size_t r = static_cast<size_t>(a) * ntot + t;
-            h_rowptr[r + 1] = h_rowptr[r] + (t < ntube ? h_cnt[t] * row_mul : 0);
+        for (long long t = 0; t < nrows_per_comp; ++t) {
+            const size_t r = static_cast<size_t>(a) * nrows_per_comp + t;
+            h_rowptr[r + 1] = h_rowptr[r] + (t < ntarget ? h_cnt[t] * row_mul : 0);
         }
     const int64_t nnz = h_rowptr.back();
     if (nnz_out)
@@ -876,7 +900,7 @@ int build_tube_correction(long long nelem, int ns, int nt, long long ntot, const
     }
     SBQ_CUDA(cudaMemcpyAsync(rowptr, h_rowptr.data(), h_rowptr.size() * sizeof(int64_t),
                              cudaMemcpyHostToDevice, s));
-    const long long n_items = ntube > 0 ? cnt_off[ntube] : 0;
+    const long long n_items = cnt_off[ntarget];
     if (n_items == 0) {
         SBQ_CUDA(cudaStreamSynchronize(s));
         return SBQ_OK;
@@ -886,7 +910,7 @@ int build_tube_correction(long long nelem, int ns, int nt, long long ntot, const
         return SBQ_EINVAL;
     }
     std::vector<Item> h_items(n_items);
-    for (long long t = 0; t < ntube; ++t)
+    for (long long t = 0; t < ntarget; ++t)
         for (int q = 0; q < h_cnt[t]; ++q)
             h_items[cnt_off[t] + q] = Item{static_cast<int>(t), h_list[cnt_off[t] + q], q, 0};
     DevBuf d_items;
@@ -899,12 +923,14 @@ int build_tube_correction(long long nelem, int ns, int nt, long long ntot, const
         SBQ_CUDA(cudaFuncSetAttribute(k_tube_items<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       static_cast<int>(smem)));
         k_tube_items<1><<<static_cast<unsigned>(n_items), TQ_THREADS, smem, s>>>(
-            p, d_items.as<Item>(), d_geo.as<ElemGeo>(), src, nrm, w, rowptr, col, val);
+            p, d_items.as<Item>(), d_geo.as<ElemGeo>(), src, nrm, w, trg, ntarget, rowptr, col,
+            val);
     } else {
         SBQ_CUDA(cudaFuncSetAttribute(k_tube_items<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       static_cast<int>(smem)));
         k_tube_items<6><<<static_cast<unsigned>(n_items), TQ_THREADS, smem, s>>>(
-            p, d_items.as<Item>(), d_geo.as<ElemGeo>(), src, nrm, w, rowptr, col, val);
+            p, d_items.as<Item>(), d_geo.as<ElemGeo>(), src, nrm, w, trg, ntarget, rowptr, col,
+            val);
     }
     SBQ_CUDA(cudaGetLastError());
     // the host vectors above go out of scope here: wait until the copies have been made

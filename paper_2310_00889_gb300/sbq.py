@@ -110,6 +110,8 @@ def _load():
                                        _int),
         "tube_correction": ([_i64, _int, _int, _i64, _vp, _vp, _vp, _int, _dbl, _dbl, _dbl,
                              ctypes.POINTER(_i64), _vp, _vp, _vp, _vp], _int),
+        "tube_correction_targets": ([_i64, _int, _int, _i64, _vp, _vp, _vp, _i64, _vp, _int, _dbl,
+                                     _dbl, _dbl, ctypes.POINTER(_i64), _vp, _vp, _vp, _vp], _int),
         "sbq_destroy": ([_vp], None),
     }
     for name, (args, res) in sig.items():
@@ -262,6 +264,33 @@ def tube_correction(src, nrm, w, nelem, ns, nt, kind="stokes", alpha=1.0, beta=1
     val = torch.empty(max(nnz.value, 1), dtype=torch.float64, device=dev)
     _check(lib.tube_correction(*args, ctypes.byref(nnz), _ptr(rowptr), _ptr(col), _ptr(val),
                                _stream(stream)))
+    return rowptr, col[:nnz.value], val[:nnz.value]
+
+
+def tube_correction_targets(src, nrm, w, nelem, ns, nt, trg, kind="stokes", alpha=1.0, beta=1.0,
+                            near_factor=0.5, stream=None):
+    """Correction E (rowptr, col, val) for off-surface targets trg (3, m) near the tube elements
+    (Sec. 3.2.3): rows component-major over the targets, columns over the nodes.  The layer
+    potential at trg is the plain sum (combined_apply / laplace_apply) plus E sigma."""
+    n = src.shape[1]
+    m = trg.shape[1]
+    _dev(src, (3, n), "src")
+    _dev(nrm, (3, n), "nrm")
+    _dev(w, (n,), "w")
+    _dev(trg, (3, m), "trg")
+    if kind not in ("stokes", "laplace"):
+        raise ValueError("kind must be 'stokes' or 'laplace'")
+    lap = 1 if kind == "laplace" else 0
+    nnz = _i64(0)
+    args = (int(nelem), int(ns), int(nt), int(n), _ptr(src), _ptr(nrm), _ptr(w), int(m), _ptr(trg),
+            lap, float(alpha), float(beta), float(near_factor))
+    _check(lib.tube_correction_targets(*args, ctypes.byref(nnz), None, None, None, _stream(stream)))
+    dev = src.device
+    rowptr = torch.empty((1 if lap else 3) * m + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(max(nnz.value, 1), dtype=torch.int64, device=dev)
+    val = torch.empty(max(nnz.value, 1), dtype=torch.float64, device=dev)
+    _check(lib.tube_correction_targets(*args, ctypes.byref(nnz), _ptr(rowptr), _ptr(col), _ptr(val),
+                                       _stream(stream)))
     return rowptr, col[:nnz.value], val[:nnz.value]
 
 

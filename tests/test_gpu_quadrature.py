@@ -264,3 +264,78 @@ def test_paper_torus_table_all_nodes(sbq):
         got.append((nu, err, printed))
         assert err <= printed, (nu, err, printed)
     print("paper torus table (N, ours, printed): %s" % got)
+
+
+def _near_surface_points(S, m, seed):
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(S.size, m, replace=False)
+    h = 10.0 ** rng.uniform(-4, -1, m)
+    return S.x[:, idx] - h * S.n[:, idx]
+
+
+def test_offsurface_rows_match_oracle(sbq, tq):
+    S = I.torus(R0=1.0, eps=0.25, panels=16, ns=8, nth=32)
+    n = S.size
+    trg = _near_surface_points(S, 3, 21)
+    trg = np.concatenate([trg, S.x[:, [100, 2000]] + 0.05 * S.n[:, [100, 2000]]], axis=1)  # outside too
+    m = trg.shape[1]
+    for kind, alpha, beta in (("laplace", 1.0, 1.0), ("stokes", 1.55, 1.0)):
+        E = sbq.tube_correction_targets(_t(S.x), _t(S.n), _t(S.w), 16, 8, 32, _t(trg), kind=kind,
+                                        alpha=alpha, beta=beta, near_factor=0.5)
+        nr = m if kind == "laplace" else 3 * m
+        nc = n if kind == "laplace" else 3 * n
+        M = _csr_host(E, nr, nc)
+        with warnings.catch_warnings():
+            warnings.simplefilter("ignore")
+            ref = tq.correction_dense_rows(tq.correction_rows_offsurface(S.x, S.n, S.w, 16, 8, 32, kind, alpha,
+                                                                         beta, 0.5, trg), n, kind)
+        worst = 0.0
+        for k in range(m):
+            a = (M.getrow(k).toarray()[0] if kind == "laplace"
+                 else np.stack([M.getrow(c * m + k).toarray()[0] for c in range(3)]))
+            worst = max(worst, np.abs(a - ref[k]).max() / np.abs(ref[k]).max())
+        print("off-surface %s rows: worst %.3e" % (kind, worst))
+        assert worst <= TOL_ROW
+
+
+def test_near_surface_interior_representation(sbq):
+    """u = S[du/dn] - D[u] (Laplace) and u = S[f] - D[u] (Stokes, exterior point force) at
+    200 points between 1e-4 and 1e-1 inside the torus surface, with the GPU-built
+    near-singular corrections: ~1e-11, against O(1) and worse for the plain sums."""
+    S = I.torus(R0=1.0, eps=0.25, panels=16, ns=8, nth=32)
+    n = S.size
+    trg = _near_surface_points(S, 200, 22)
+    m = trg.shape[1]
+    x0 = X0
+    d = S.x - x0[:, None]
+    r = np.linalg.norm(d, axis=0)
+    u, dudn = 1.0 / r, -np.sum(d * S.n, axis=0) / r ** 3
+    ex = 1.0 / np.linalg.norm(trg - x0[:, None], axis=0)
+    ES = _csr_host(sbq.tube_correction_targets(_t(S.x), _t(S.n), _t(S.w), 16, 8, 32, _t(trg), kind="laplace",
+                                               alpha=1.0, beta=0.0, near_factor=0.5), m, n)
+    ED = _csr_host(sbq.tube_correction_targets(_t(S.x), _t(S.n), _t(S.w), 16, 8, 32, _t(trg), kind="laplace",
+                                               alpha=0.0, beta=1.0, near_factor=0.5), m, n)
+    Sp = _np(sbq.laplace_apply(_t(S.x), _t(S.n), _t(S.w), _t(dudn), _t(trg), 1.0, 0.0, prec="fp64"))
+    Dp = _np(sbq.laplace_apply(_t(S.x), _t(S.n), _t(S.w), _t(u), _t(trg), 0.0, 1.0, prec="fp64"))
+    lap = np.abs(Sp + ES @ dudn - Dp - ED @ u - ex).max() / np.abs(u).max()
+    lap_plain = np.abs(Sp - Dp - ex).max() / np.abs(u).max()
+    F = np.array([0.5, -1.0, 0.7])
+    rf = F @ d
+    uu = (F[:, None] / r + d * rf / r ** 3) / (8.0 * np.pi)
+    trac = -(3.0 / (4.0 * np.pi)) * d * rf * np.sum(d * S.n, axis=0) / r ** 5
+    dt = trg - x0[:, None]
+    rt = np.linalg.norm(dt, axis=0)
+    uex = (F[:, None] / rt + dt * (F @ dt) / rt ** 3) / (8.0 * np.pi)
+    KS = _csr_host(sbq.tube_correction_targets(_t(S.x), _t(S.n), _t(S.w), 16, 8, 32, _t(trg), kind="stokes",
+                                               alpha=1.0, beta=0.0, near_factor=0.5), 3 * m, 3 * n)
+    KD = _csr_host(sbq.tube_correction_targets(_t(S.x), _t(S.n), _t(S.w), 16, 8, 32, _t(trg), kind="stokes",
+                                               alpha=0.0, beta=1.0, near_factor=0.5), 3 * m, 3 * n)
+    sp = _np(sbq.sl_apply(_t(S.x), _t(S.w), _t(trac), _t(trg), prec="fp64"))
+    dp = _np(sbq.dl_apply(_t(S.x), _t(S.n), _t(S.w), _t(uu), _t(trg), prec="fp64"))
+    lhs = sp + (KS @ trac.reshape(-1)).reshape(3, m) - dp - (KD @ uu.reshape(-1)).reshape(3, m)
+    sto = np.abs(lhs - uex).max() / np.abs(uu).max()
+    sto_plain = np.abs(sp - dp - uex).max() / np.abs(uu).max()
+    print("near-surface interior representation: laplace %.3e (plain %.3e), stokes %.3e (plain %.3e)"
+          % (lap, lap_plain, sto, sto_plain))
+    assert lap_plain > 1e-1 and sto_plain > 1e-1
+    assert lap < 1e-10 and sto < 1e-10
