@@ -1037,10 +1037,29 @@ def run_quadrature(args):
                         beta=1.0, near_factor=args.near_factor)
     nnz = int(E[2].shape[0])
     items = nnz // (9 * 8 * 16)
+    # the oracle building rows of the same E, on a bounded sample of targets (CPU baseline)
+    import warnings
+    from oracle import tube_quadrature as TQ
+    tg = np.random.default_rng(17).choice(s.size, 4, replace=False)
+    tt = time.perf_counter()
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        rows = TQ.correction_rows(s.x, s.n, s.w, P, 8, 16, "stokes", sbq.slender_eta(0.01), 1.0,
+                                  args.near_factor, tg)
+    sec = time.perf_counter() - tt
+    o_items = sum(len(v) for v in rows.values())
     print(json.dumps({"workload": "quadrature_stokes_build_random_loop", "nodes": s.size,
                       "build_ms": ms, "nnz": nnz, "csr_bytes": nnz * 16,
                       "target_element_items": items, "us_per_item": ms * 1e3 / items,
-                      "unknowns_per_s": 3 * s.size / (ms * 1e-3)}), flush=True)
+                      "items_per_s": items / (ms * 1e-3),
+                      "unknowns_per_s": 3 * s.size / (ms * 1e-3),
+                      "roofline": {"bound": "fp64", "profile":
+                                   "profiles/tube_correction_stokes_random_loop_8192.md"},
+                      "cpu_baseline": {"kind": "oracle", "value": o_items / sec,
+                                       "unit": "(target, element) items/s", "cores": 1,
+                                       "sample": "%d targets, %d items of the same E in %.1f s "
+                                                 "(numpy)" % (len(tg), o_items, sec)}}),
+          flush=True)
     return 0
 
 
