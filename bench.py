@@ -41,7 +41,7 @@ if ROOT not in sys.path:
 
 METRIC = "pair interactions/s and GMRES solve time at 1e-10 residual, FP32-mixed vs plain FP64"
 UNIT = "pairs/s"
-FLOPS_PER_PAIR = {"sl": 28, "dl": 29, "cf": 37}   # FP32 flops per pair (FMA = 2), see the design doc
+FLOPS_PER_PAIR = {"sl": 28, "dl": 29, "cf": 37}   # algorithmic FP32 flops per pair (FMA = 2)
 WORKLOAD = "curved_pipe_arc90_Rc5_R1_16384wall_2048cap_gmres_ir_1e-10"
 L2_FLUSH_BYTES = 256 << 20
 
