@@ -65,3 +65,41 @@ def test_batch_plan_validation_on_host(libsbq):
     h2 = vp()
     assert libsbq.batch_plan(3, ctypes.cast(bad, vp), ctypes.cast(off, vp), None, ctypes.byref(h2)) == 1
     assert not h2.value
+
+
+def test_tube_correction_validation_on_host(libsbq):
+    """The quadrature-correction entry points reject bad element layouts, sizes, kinds and
+    pointers before touching a device."""
+    vp, i64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+    libsbq.tube_correction.argtypes = [i64, ctypes.c_int, ctypes.c_int, i64, vp, vp, vp, ctypes.c_int,
+                                       dbl, dbl, dbl, ctypes.POINTER(i64), vp, vp, vp, vp]
+    libsbq.tube_correction_targets.argtypes = [i64, ctypes.c_int, ctypes.c_int, i64, vp, vp, vp, i64, vp,
+                                               ctypes.c_int, dbl, dbl, dbl, ctypes.POINTER(i64), vp, vp,
+                                               vp, vp]
+    libsbq.sbq_last_error.restype = ctypes.c_char_p
+    nnz = i64(0)
+    fake = vp(16)      # never dereferenced: every call below fails validation first
+    cases = [
+        ((4, 1, 16, 512), b"ns"),           # ns below 2
+        ((4, 8, 15, 512), b"nt"),           # odd N_theta
+        ((4, 8, 66, 2112), b"nt"),          # N_theta above 64
+        ((4, 8, 16, 511), b"n_total"),      # fewer nodes than the elements hold
+        ((-1, 8, 16, 512), b"negative"),
+    ]
+    for (ne, ns, nt, ntot), msg in cases:
+        st = libsbq.tube_correction(ne, ns, nt, ntot, fake, fake, fake, 0, 1.0, 1.0, 0.5,
+                                    ctypes.byref(nnz), None, None, None, None)
+        assert st == 1 and msg in libsbq.sbq_last_error(), (ne, ns, nt, ntot)
+    assert libsbq.tube_correction(4, 8, 16, 512, fake, fake, fake, 2, 1.0, 1.0, 0.5,
+                                  ctypes.byref(nnz), None, None, None, None) == 1
+    assert libsbq.tube_correction(4, 8, 16, 512, None, fake, fake, 0, 1.0, 1.0, 0.5,
+                                  ctypes.byref(nnz), None, None, None, None) == 1
+    assert libsbq.tube_correction(4, 8, 16, 512, fake, fake, fake, 0, float("nan"), 1.0, 0.5,
+                                  ctypes.byref(nnz), None, None, None, None) == 1
+    assert libsbq.tube_correction(4, 8, 16, 512, fake, fake, fake, 0, 1.0, 1.0, 0.5,
+                                  None, None, None, None, None) == 1
+    # off-surface targets: a null target array with targets requested
+    assert libsbq.tube_correction_targets(4, 8, 16, 512, fake, fake, fake, 10, None, 0, 1.0, 1.0, 0.5,
+                                          ctypes.byref(nnz), None, None, None, None) == 1
+    assert libsbq.tube_correction_targets(4, 8, 16, 512, fake, fake, fake, -3, fake, 0, 1.0, 1.0, 0.5,
+                                          ctypes.byref(nnz), None, None, None, None) == 1
