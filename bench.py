@@ -71,7 +71,7 @@ def parse(argv=None):
                          "subtraction)")
     ap.add_argument("--workload", default="curved_pipe",
                     choices=["curved_pipe", "precision_sweep", "batch", "helix", "laplace",
-                             "mobility", "quadrature"],
+                             "mobility", "quadrature", "peaks"],
                     help="curved_pipe: the benchmark line (default); precision_sweep: FP32 vs "
                          "compensated FP32 vs FP64 pair sums on random loops of 64K/256K/1M "
                          "nodes; batch: 64 independent capped arcs in one persistent launch")
@@ -1063,6 +1063,34 @@ def run_quadrature(args):
     return 0
 
 
+def run_peaks(args):
+    """Arithmetic peaks measured with FMA chains on every SM (FP32, packed FP32x2, FP64),
+    beside the FP32 peak the pair-sum roofline uses (SMs x 128 lanes x 2 x max SM clock) and
+    the SM clock sampled while they run."""
+    import torch
+    from paper_2310_00889_gb300 import build as b
+    b.build()
+    from paper_2310_00889_gb300 import sbq
+    torch.cuda.set_device(0)
+    info = sbq.device_info()
+    sm_max = 2070.0
+    try:
+        sm_max = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("sm_max_mhz", sm_max))
+    except (OSError, ValueError):
+        pass
+    model = info["sms"] * info["fp32_lanes_per_sm"] * 2 * sm_max * 1e6 / 1e12
+    res = {}
+    for kind in ("fp32", "fp32x2", "fp64"):
+        tf, ms = sbq.peak_probe(kind)
+        tf, ms = sbq.peak_probe(kind)
+        res[kind] = {"tflops": tf, "ms": ms}
+    print(json.dumps({"workload": "peaks_fma_chains", "sms": info["sms"],
+                      "fp32_model_tflops": model, "sm_max_mhz": sm_max, "measured": res,
+                      "fp32_measured_over_model": res["fp32"]["tflops"] / model,
+                      "fp32x2_measured_over_model": res["fp32x2"]["tflops"] / model}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.workload == "helix" and args.impl != "reference":
@@ -1079,6 +1107,8 @@ def main():
         return run_mobility(args)
     if args.workload == "quadrature":
         return run_quadrature(args)
+    if args.workload == "peaks":
+        return run_peaks(args)
     return run_gpu(args)
 
 

@@ -320,6 +320,15 @@ SBQ_API int tube_correction(int64_t nelem, int ns, int nt, int64_t n_total, cons
  * apply) plus this E times sigma.  Same two-phase use, ownership and errors as
  * tube_correction; rowptr holds (laplace ? 1 : 3) * ntrg + 1 entries.
  */
+/*
+ * Arithmetic-peak probe (measurement aid, not part of the method): times one launch of
+ * long independent fused-multiply-add chains on every SM and returns the achieved rate.
+ *   kind 0: FP32 FMA; 1: packed FP32x2 FMA (fma.rn.f32x2); 2: FP64 FMA.
+ *   tflops, ms: HOST outputs (TFLOP/s with an FMA counted as 2 flops; kernel time).
+ * Synchronises the stream.  Errors: SBQ_EINVAL for a bad kind or null outputs.
+ */
+SBQ_API int sbq_peak_probe(int kind, double *tflops, double *ms, void *stream);
+
 SBQ_API int tube_correction_targets(int64_t nelem, int ns, int nt, int64_t n_total,
                                     const double *src, const double *nrm, const double *w,
                                     int64_t ntrg, const double *trg, int laplace, double alpha,

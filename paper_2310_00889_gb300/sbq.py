@@ -110,6 +110,7 @@ def _load():
                                        _int),
         "tube_correction": ([_i64, _int, _int, _i64, _vp, _vp, _vp, _int, _dbl, _dbl, _dbl,
                              ctypes.POINTER(_i64), _vp, _vp, _vp, _vp], _int),
+        "sbq_peak_probe": ([_int, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), _vp], _int),
         "tube_correction_targets": ([_i64, _int, _int, _i64, _vp, _vp, _vp, _i64, _vp, _int, _dbl,
                                      _dbl, _dbl, ctypes.POINTER(_i64), _vp, _vp, _vp, _vp], _int),
         "sbq_destroy": ([_vp], None),
@@ -265,6 +266,15 @@ def tube_correction(src, nrm, w, nelem, ns, nt, kind="stokes", alpha=1.0, beta=1
     _check(lib.tube_correction(*args, ctypes.byref(nnz), _ptr(rowptr), _ptr(col), _ptr(val),
                                _stream(stream)))
     return rowptr, col[:nnz.value], val[:nnz.value]
+
+
+def peak_probe(kind, stream=None):
+    """Achieved TFLOP/s of long FMA chains on every SM: kind "fp32", "fp32x2" (packed) or
+    "fp64"; returns (tflops, ms)."""
+    k = {"fp32": 0, "fp32x2": 1, "fp64": 2}[kind]
+    tf, ms = _dbl(0.0), _dbl(0.0)
+    _check(lib.sbq_peak_probe(k, ctypes.byref(tf), ctypes.byref(ms), _stream(stream)))
+    return tf.value, ms.value
 
 
 def tube_correction_targets(src, nrm, w, nelem, ns, nt, trg, kind="stokes", alpha=1.0, beta=1.0,

@@ -111,3 +111,21 @@ def test_mismatched_sizes_and_wrong_plan_handle(sbq, pipe):
     with pytest.raises(sbq.SbqError):        # mobility needs offsets covering the nodes
         op.set_mobility([0, n // 2])
     op.close()
+
+
+def test_peak_probe_reports_a_plausible_fp32_rate():
+    """The FMA-chain probe runs and its scalar FP32 rate stays at or below the model peak
+    (SMs x 128 lanes x 2 flops x 2.07 GHz) the pair-sum roofline divides by."""
+    import torch
+    from paper_2310_00889_gb300 import build
+    build.build()
+    from paper_2310_00889_gb300 import sbq
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA device is required for the gpu tests")
+    info = sbq.device_info()
+    model = info["sms"] * info["fp32_lanes_per_sm"] * 2 * 2.07e9 / 1e12
+    for kind in ("fp32", "fp32x2", "fp64"):
+        tf, ms = sbq.peak_probe(kind)
+        assert tf > 0 and ms > 0 and np.isfinite(tf)
+    tf, _ = sbq.peak_probe("fp32")
+    assert 0.3 * model < tf < 1.05 * model, (tf, model)
