@@ -238,3 +238,49 @@ def test_near_surface_interior_green_representation():
         plain = max(abs(Sp[k] - Dp[k] - ex[k]) for k in range(2)) / np.abs(u).max()
         assert err < 1e-10, (h, err)
         assert plain > 1e-2, (h, plain)
+
+
+@pytest.mark.parametrize("alpha,beta", [(1.0, 0.0), (0.0, 1.0)])
+def test_on_element_stokes_layers_match_nested_adaptive_integral(alpha, beta):
+    """Sec. 3.2.4 for the Stokes kernels: single and double layer of a constant vector density
+    over one straight tube element, at the element's own node, against nested adaptive
+    quadrature (theta inside s, both split at the singular point); the punctured sum is
+    off by 1e-2 or more."""
+    rho, L, ns, nt, i0, j0 = 0.1, 0.4, 8, 16, 3, 5
+    y, n, w, s = _cylinder(rho, L, ns, nt)
+    x, s0, th0 = y[:, i0, j0], s[i0], 2.0 * np.pi * j0 / nt
+    sig = np.array([0.3, -0.2, 1.0])
+
+    def integrand(z, th, a):
+        # x - y on the cylinder from product formulas, free of cancellation near x
+        h = 0.5 * (th0 - th)
+        sh, m = math.sin(h), 0.5 * (th0 + th)
+        r = np.array([-2.0 * rho * math.sin(m) * sh, 2.0 * rho * math.cos(m) * sh, s0 - z])
+        rl = math.sqrt(4.0 * rho * rho * sh * sh + (s0 - z) ** 2)
+        rn = -2.0 * rho * sh * sh                           # (x - y) . n_y
+        v = 0.0
+        if alpha:
+            v += alpha * (sig[a] / rl + r[a] * (r @ sig) / rl ** 3) / (8.0 * math.pi)
+        if beta:
+            v += beta * 3.0 / (4.0 * math.pi) * rn * r[a] * (r @ sig) / rl ** 5
+        return rho * v
+
+    def inner(z, a):
+        return sum(integrate.quad(lambda th: integrand(z, th, a), lo, hi, limit=400, epsabs=1e-15,
+                                  epsrel=1e-13)[0] for lo, hi in ((th0 - math.pi, th0), (th0, th0 + math.pi)))
+
+    exact = np.array([sum(integrate.quad(lambda z: inner(z, a), lo, hi, limit=200, epsabs=1e-15,
+                                         epsrel=1e-12)[0] for lo, hi in ((-0.5 * L, s0), (s0, 0.5 * L)))
+                      for a in range(3)])
+    el = T.Element(y, n, w)
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        E = T.element_block(el, x, "stokes", alpha, beta, own=(i0, j0))
+        G = T.kernel("stokes", alpha, beta, x, y.reshape(3, -1), n.reshape(3, -1)) * w.reshape(-1)[None, :]
+    G[:, i0 * nt + j0] = 0.0
+    K = G + E.reshape(9, -1)
+    u = np.array([sum(K[a * 3 + b].sum() * sig[b] for b in range(3)) for a in range(3)])
+    up = np.array([sum(G[a * 3 + b].sum() * sig[b] for b in range(3)) for a in range(3)])
+    scale = np.abs(exact).max()
+    assert np.abs(u - exact).max() < 1e-11 * scale
+    assert np.abs(up - exact).max() > 1e-2 * scale
