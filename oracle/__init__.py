@@ -25,6 +25,8 @@ Contents
   * `tube_quadrature` (module): the quadrature correction E of tube elements (Sec.
     3.2.1-3.2.4): modal angular weights, near-singular and singular rules in s, the
     sparse E over whole tubes;
+  * `gen_chebyshev` (module): the generalized Chebyshev rules of Appendix B and the
+    compressed angular rules of Sec. 3.2.2 built with them;
   * `eta_slender`: the slender-body mixing parameter 1 / (2 eps log(1/eps))
     (Sec. 4.1, Laplace and Stokes slender combined-field formulations).
 
