@@ -35,11 +35,20 @@ def gl01(n):
     return 0.5 * (x + 1.0), 0.5 * w
 
 
-def chebyshev_rule(F, x, w, eps):
+def chebyshev_rule(F, x, w, eps, psi=None):
     """Appendix B: from integrand values F (m, k) at the fine nodes x (m,) with weights w (m,),
-    a rule (nodes y, weights omega) integrating every column to about eps."""
+    a rule (nodes y, weights omega) integrating every column to about eps.  psi (m,) > 0:
+    run the construction in the measure psi dx on the functions F / psi (the weights are
+    divided by psi at the chosen nodes at the end); for peaked families this makes the L2
+    truncation control the integrals, which double precision needs where the paper works in
+    quad precision."""
     F = np.asarray(F, dtype=np.float64)
-    sw = np.sqrt(np.asarray(w, dtype=np.float64))
+    w = np.asarray(w, dtype=np.float64)
+    if psi is not None:
+        y, om = chebyshev_rule(F / psi[:, None], x, w * psi, eps)
+        sel = np.searchsorted(np.asarray(x), y)
+        return y, om / psi[sel]
+    sw = np.sqrt(w)
     A = F * sw[:, None]
     U, S, _ = np.linalg.svd(A, full_matrices=False)
     n = int(np.sum(S > eps * S[0]))
@@ -69,27 +78,50 @@ def angular_fine_rule(alpha, q=32, nb=2):
 
 
 def annulus_targets(alpha, nr=12, npsi=24):
-    """Polar grid on the annulus alpha..2 alpha about (1, 0, 0) in the x-z plane."""
+    """Polar grid on the annulus alpha..2 alpha about (1, 0, 0) in the x-z plane, as offsets
+    (dx, dz) from that point (the target is (1 + dx, 0, dz))."""
     rr = alpha * (1.5 + 0.5 * np.cos(np.pi * (np.arange(nr) + 0.5) / nr))
     ps = 2.0 * np.pi * np.arange(npsi) / npsi
-    return np.array([[1.0 + r * math.cos(p), 0.0, r * math.sin(p)] for r in rr for p in ps]).T
+    return np.array([[r * math.cos(p), r * math.sin(p)] for r in rr for p in ps]).T
 
 
-def modal_family(x_targets, theta, l0):
-    """Columns G(x_k, y(theta)) cos(l theta) and sin(l theta), l = 0..l0 (sin l = 0 left out)."""
+def kernel_components(kind, r, n):
+    """Kernel components for offsets r = x - y (3, M) and source normals n: "laplace": 1/|r|;
+    "stokes": the six components of the single layer (delta/|r| + r_a r_b/|r|^3) and of the
+    double layer ((r . n) r_a r_b / |r|^5), each up to its constant."""
+    r2 = np.sum(r * r, axis=0)
+    rl = np.sqrt(r2)
+    if kind == "laplace":
+        return [1.0 / rl]
+    rn = np.sum(r * n, axis=0)
+    out = []
+    for a, b in ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)):
+        out.append((1.0 / rl if a == b else 0.0) + r[a] * r[b] / (rl * r2))
+        out.append(rn * r[a] * r[b] / (r2 * r2 * rl))
+    return out
+
+
+def modal_family(x_targets, theta, l0, kind="laplace"):
+    """Columns G_c(x_k, y(theta)) cos(l theta) and sin(l theta), l = 0..l0 (sin l = 0 left
+    out), for every kernel component c of `kind`; targets given as annulus offsets."""
     y = np.stack([np.cos(theta), np.sin(theta), np.zeros_like(theta)])
+    one_m_cos = 2.0 * np.sin(0.5 * theta) ** 2          # 1 - cos(theta) without cancellation
     cols = []
     for k in range(x_targets.shape[1]):
-        G = 1.0 / np.linalg.norm(x_targets[:, k:k + 1] - y, axis=0)
-        for l in range(l0 + 1):
-            cols.append(G * np.cos(l * theta))
-            if l:
-                cols.append(G * np.sin(l * theta))
+        dx, dz = x_targets[0, k], x_targets[1, k]
+        r = np.stack([one_m_cos + dx, -np.sin(theta), np.full_like(theta, dz)])   # x - y(theta)
+        for G in kernel_components(kind, r, y):
+            for l in range(l0 + 1):
+                cols.append(G * np.cos(l * theta))
+                if l:
+                    cols.append(G * np.sin(l * theta))
     return np.array(cols).T
 
 
-def angular_rule(alpha, l0, eps):
+def angular_rule(alpha, l0, eps, kind="laplace", nr=12, npsi=24):
     """Compressed angular rule for relative distances alpha..2 alpha (Sec. 3.2.2 with App. B):
     nodes (offsets from the closest angle) and weights."""
     th, w = angular_fine_rule(alpha)
-    return chebyshev_rule(modal_family(annulus_targets(alpha), th, l0), th, w, eps)
+    psi = 1.0 / np.sqrt((1.5 * alpha) ** 2 + (2.0 * np.sin(0.5 * th)) ** 2)
+    return chebyshev_rule(modal_family(annulus_targets(alpha, nr, npsi), th, l0, kind), th, w, eps,
+                          psi=psi)
