@@ -321,6 +321,29 @@ SBQ_API int tube_correction(int64_t nelem, int ns, int nt, int64_t n_total, cons
  * tube_correction; rowptr holds (laplace ? 1 : 3) * ntrg + 1 entries.
  */
 /*
+ * tube_correction / tube_correction_targets with compressed angular rules (Sec. 3.2.2 with
+ * the generalized Chebyshev rules of Appendix B): for relative distances 2^-30 <= alpha < 1
+ * of a target from a source circle, the angular integrals take the caller's rule of level
+ * lev = ceil(-log2 alpha) instead of the dyadically refined one.
+ *   trg == NULL: on-surface targets (the tube nodes, as tube_correction; ntrg ignored);
+ *   otherwise ntrg off-surface targets (as tube_correction_targets).
+ *   nlev, rule_phi, rule_w, rule_cnt: HOST tables; level l (0 <= l < nlev <= 31) holds
+ *   rule_cnt[l] <= 64 nodes: angle offsets rule_phi[l * 64 + m] from the circle point
+ *   closest to the target, in [-pi, pi], and weights rule_w[l * 64 + m] (rule_cnt[l] = 0:
+ *   that level keeps the dyadic rule).  The rules must integrate, for targets at relative
+ *   distance alpha..2 alpha from the unit circle, the kernel components times e^{i l theta}
+ *   up to l = N_theta/2 + 1 (paper_2310_00889_gb300/angular_rules.py writes such tables).
+ * Otherwise the same arguments, layout, two-phase use and errors as tube_correction.
+ */
+SBQ_API int tube_correction_rules(int64_t nelem, int ns, int nt, int64_t n_total,
+                                  const double *src, const double *nrm, const double *w,
+                                  int64_t ntrg, const double *trg, int laplace, double alpha,
+                                  double beta, double near_factor, int nlev,
+                                  const double *rule_phi, const double *rule_w,
+                                  const int *rule_cnt, int64_t *nnz_out, int64_t *rowptr,
+                                  int64_t *col, double *val, void *stream);
+
+/*
  * Arithmetic-peak probe (measurement aid, not part of the method): times one launch of
  * long independent fused-multiply-add chains on every SM and returns the achieved rate.
  *   kind 0: FP32 FMA; 1: packed FP32x2 FMA (fma.rn.f32x2); 2: FP64 FMA.

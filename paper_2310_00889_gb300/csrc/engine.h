@@ -146,11 +146,13 @@ int dl_gauss_correction(int nbody, const int64_t *body_off, const double *src, c
 // tube_quad.cu: quadrature correction of tube elements (on-surface targets).
 // trg == nullptr: targets are the tube nodes (rows over all ntot nodes); else ntrg
 // off-surface points.
+// rules_*: optional compressed angular rules (HOST arrays, rules_nlev levels of 64 slots).
 int build_tube_correction(long long nelem, int ns, int nt, long long ntot, const double *src,
                           const double *nrm, const double *w, long long ntrg, const double *trg,
                           int laplace, double alpha, double beta, double near_factor,
                           int64_t *nnz_out, int64_t *rowptr, int64_t *col, double *val,
-                          cudaStream_t s);
+                          cudaStream_t s, int rules_nlev = 0, const double *rules_phi = nullptr,
+                          const double *rules_w = nullptr, const int *rules_cnt = nullptr);
 int gmres_destroy(struct GmresWS *ws);
 
 }  // namespace sbq

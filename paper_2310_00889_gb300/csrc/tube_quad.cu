@@ -40,6 +40,8 @@ constexpr int TQ_SING_G = 6;
 constexpr int TQ_LMAX = 60;        // deepest dyadic level
 constexpr int TQ_NS_MAX = 16;
 constexpr int TQ_REFINE = 3;       // rounds of 128-point refinement of t*
+constexpr int TQ_RULE_SLOT = 64;   // nodes reserved per level of a compressed angular rule
+constexpr int TQ_RULE_MAXLEV = 30; // compressed rules serve 2^-30 <= alpha < 1
 
 struct ElemGeo {
     double c[3][TQ_NS_MAX], a[3][TQ_NS_MAX], b[3][TQ_NS_MAX];
@@ -54,6 +56,11 @@ struct TQParams {
     double alpha, beta;
     long long ntot;
     int ns, nt, per;
+    // optional compressed angular rules: level lev (alpha in [2^-lev, 2^(1-lev))) holds
+    // rcnt[lev] <= TQ_RULE_SLOT nodes rphi[lev * TQ_RULE_SLOT + m] with weights rw[...]
+    const double *rphi, *rw;
+    const int *rcnt;
+    int rnlev;
 };
 
 struct Item {
@@ -561,14 +568,23 @@ k_tube_items(TQParams p, const Item *__restrict__ items, const ElemGeo *__restri
                         Lv = TQ_LMAX;
                     else
                         Lv = min(TQ_LMAX, static_cast<int>(ceil(log2(lb / alpha_rel))));
+                    int tl = 0;
+                    if (p.rcnt && alpha_rel < 1.0 && alpha_rel >= ldexp(1.0, -TQ_RULE_MAXLEV)) {
+                        tl = static_cast<int>(ceil(-log2(alpha_rel)));
+                        tl = max(1, min(TQ_RULE_MAXLEV, tl));
+                        if (tl >= p.rnlev || p.rcnt[tl] <= 0 || p.rcnt[tl] > TQ_RULE_SLOT)
+                            tl = 0;
+                    }
                     s.SD[1] = th0;
                     s.SD[2] = static_cast<double>(Lv);
+                    s.SD[3] = static_cast<double>(tl);
                 }
                 __syncthreads();
                 const double th0 = s.SD[1];
                 const int L = static_cast<int>(s.SD[2]);
+                const int TL = static_cast<int>(s.SD[3]);   // > 0: compressed rule of that level
                 const int Mh = TQ_Q * (L + nb);
-                const int M = 2 * Mh;
+                const int M = TL ? p.rcnt[TL] : 2 * Mh;
                 double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
                 for (int base = 0; base < M; base += TQ_THREADS) {
                     const int kq = base + tid;
@@ -587,9 +603,13 @@ k_tube_items(TQParams p, const Item *__restrict__ items, const ElemGeo *__restri
                             hi = lb * (pn - L + 1);
                         }
                         double phi = lo + (hi - lo) * p.gx[qq];
-                        const double om = (hi - lo) * p.gw[qq];
+                        double om = (hi - lo) * p.gw[qq];
                         if (sidek == 0)
                             phi = -phi;
+                        if (TL) {
+                            phi = p.rphi[TL * TQ_RULE_SLOT + kq];
+                            om = p.rw[TL * TQ_RULE_SLOT + kq];
+                        }
                         const double psi = th0 + phi;                 // own: offset from thj0
                         double sn, cs, ymx[3];
                         if (own) {
@@ -802,7 +822,8 @@ int build_tube_correction(long long nelem, int ns, int nt, long long ntot, const
                           const double *nrm, const double *w, long long ntrg, const double *trg,
                           int laplace, double alpha, double beta, double near_factor,
                           int64_t *nnz_out, int64_t *rowptr, int64_t *col, double *val,
-                          cudaStream_t s)
+                          cudaStream_t s, int rules_nlev, const double *rules_phi,
+                          const double *rules_w, const int *rules_cnt)
 {
     const long long per = static_cast<long long>(ns) * nt;
     const long long ntube = nelem * per;
@@ -835,6 +856,9 @@ int build_tube_correction(long long nelem, int ns, int nt, long long ntot, const
     p.ns = ns;
     p.nt = nt;
     p.per = static_cast<int>(per);
+    p.rphi = p.rw = nullptr;
+    p.rcnt = nullptr;
+    p.rnlev = 0;
 
     AsyncAllocScope scope(s);
     std::vector<long long> cnt_off;
@@ -913,6 +937,20 @@ int build_tube_correction(long long nelem, int ns, int nt, long long ntot, const
     for (long long t = 0; t < ntarget; ++t)
         for (int q = 0; q < h_cnt[t]; ++q)
             h_items[cnt_off[t] + q] = Item{static_cast<int>(t), h_list[cnt_off[t] + q], q, 0};
+    DevBuf d_rphi, d_rw, d_rcnt;
+    if (rules_nlev > 0) {
+        const size_t nd = static_cast<size_t>(rules_nlev) * TQ_RULE_SLOT;
+        SBQ_TRY(d_rphi.alloc(nd * sizeof(double)));
+        SBQ_TRY(d_rw.alloc(nd * sizeof(double)));
+        SBQ_TRY(d_rcnt.alloc(rules_nlev * sizeof(int)));
+        SBQ_CUDA(cudaMemcpyAsync(d_rphi.p, rules_phi, nd * sizeof(double), cudaMemcpyHostToDevice, s));
+        SBQ_CUDA(cudaMemcpyAsync(d_rw.p, rules_w, nd * sizeof(double), cudaMemcpyHostToDevice, s));
+        SBQ_CUDA(cudaMemcpyAsync(d_rcnt.p, rules_cnt, rules_nlev * sizeof(int), cudaMemcpyHostToDevice, s));
+        p.rphi = d_rphi.as<double>();
+        p.rw = d_rw.as<double>();
+        p.rcnt = d_rcnt.as<int>();
+        p.rnlev = rules_nlev;
+    }
     DevBuf d_items;
     SBQ_TRY(d_items.alloc(n_items * sizeof(Item)));
     SBQ_CUDA(cudaMemcpyAsync(d_items.p, h_items.data(), n_items * sizeof(Item),
@@ -944,3 +982,51 @@ size_t tube_correction_smem_bytes(int laplace, int ns, int nt)
 }
 
 }  // namespace sbq
+
+// Quadrature correction with compressed angular rules (see sbq.h): the same builder, the
+// angular integrals of relative distance 2^-30 <= alpha < 1 taken with the caller's rule of
+// level ceil(-log2 alpha) instead of the dyadic one.
+extern "C" __attribute__((visibility("default"))) int tube_correction_rules(
+    int64_t nelem, int ns, int nt, int64_t n_total, const double *src, const double *nrm,
+    const double *w, int64_t ntrg, const double *trg, int laplace, double alpha, double beta,
+    double near_factor, int nlev, const double *rule_phi, const double *rule_w,
+    const int *rule_cnt, int64_t *nnz_out, int64_t *rowptr, int64_t *col, double *val,
+    void *stream)
+{
+    using namespace sbq;
+    clear_error();
+    auto bad = [](const char *m) { set_error(m); return static_cast<int>(SBQ_EINVAL); };
+    if (nelem < 0 || n_total < 0 || ntrg < 0)
+        return bad("negative size");
+    if (ns < 2 || ns > 16)
+        return bad("ns must be in 2..16");
+    if (nt < 4 || nt > 64 || (nt & 1))
+        return bad("nt must be even and in 4..64");
+    if (nelem * ns * nt > n_total)
+        return bad("n_total below nelem * ns * nt");
+    if (n_total > (1LL << 31) / 3 || ntrg > (1LL << 31) / 3)
+        return bad("n_total or ntrg above 2^31 / 3");
+    if (laplace != 0 && laplace != 1)
+        return bad("laplace must be 0 or 1");
+    if (!std::isfinite(alpha) || !std::isfinite(beta) || !std::isfinite(near_factor))
+        return bad("non-finite alpha, beta or near_factor");
+    if (!rowptr && !nnz_out)
+        return bad("null rowptr and nnz_out");
+    if (nelem > 0 && (!src || !nrm || !w))
+        return bad("null geometry pointer");
+    if (nlev < 1 || nlev > TQ_RULE_MAXLEV + 1 || !rule_phi || !rule_w || !rule_cnt)
+        return bad("rules: nlev must be in 1..31 with non-null tables");
+    for (int l = 0; l < nlev; ++l) {
+        if (rule_cnt[l] < 0 || rule_cnt[l] > TQ_RULE_SLOT)
+            return bad("rules: a level holds more than 64 nodes");
+        for (int m = 0; m < rule_cnt[l]; ++m) {
+            const double a = rule_phi[l * TQ_RULE_SLOT + m], b = rule_w[l * TQ_RULE_SLOT + m];
+            if (!std::isfinite(a) || !std::isfinite(b) || std::fabs(a) > 3.14159265358979323846)
+                return bad("rules: non-finite entry or offset outside [-pi, pi]");
+        }
+    }
+    return build_tube_correction(nelem, ns, nt, n_total, src, nrm, w, trg ? ntrg : 0, trg,
+                                 laplace, alpha, beta, near_factor, nnz_out, rowptr, col, val,
+                                 static_cast<cudaStream_t>(stream), nlev, rule_phi, rule_w,
+                                 rule_cnt);
+}

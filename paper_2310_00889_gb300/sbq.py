@@ -110,6 +110,9 @@ def _load():
                                        _int),
         "tube_correction": ([_i64, _int, _int, _i64, _vp, _vp, _vp, _int, _dbl, _dbl, _dbl,
                              ctypes.POINTER(_i64), _vp, _vp, _vp, _vp], _int),
+        "tube_correction_rules": ([_i64, _int, _int, _i64, _vp, _vp, _vp, _i64, _vp, _int, _dbl,
+                                   _dbl, _dbl, _int, _vp, _vp, _vp, ctypes.POINTER(_i64), _vp,
+                                   _vp, _vp, _vp], _int),
         "sbq_peak_probe": ([_int, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), _vp], _int),
         "tube_correction_targets": ([_i64, _int, _int, _i64, _vp, _vp, _vp, _i64, _vp, _int, _dbl,
                                      _dbl, _dbl, ctypes.POINTER(_i64), _vp, _vp, _vp, _vp], _int),
@@ -240,14 +243,41 @@ def dl_gauss_correction(src, nrm, w, body_off=None, prec="fp64", stream=None):
     return rowptr, col, val
 
 
+def _rules_call(src, nrm, w, nelem, ns, nt, trg, lap, alpha, beta, near_factor, rules, stream):
+    """tube_correction_rules with host tables rules = (phi, w, cnt) of shapes (L, 64),
+    (L, 64), (L,)."""
+    rphi = np.ascontiguousarray(rules[0], dtype=np.float64)
+    rw = np.ascontiguousarray(rules[1], dtype=np.float64)
+    rcnt = np.ascontiguousarray(rules[2], dtype=np.int32)
+    nlev = int(rcnt.shape[0])
+    if rphi.shape != (nlev, 64) or rw.shape != (nlev, 64):
+        raise ValueError("rules: phi and w must be (levels, 64)")
+    n = src.shape[1]
+    m = trg.shape[1] if trg is not None else 0
+    nnz = _i64(0)
+    dptr = lambda a: a.ctypes.data_as(_vp)
+    args = (int(nelem), int(ns), int(nt), int(n), _ptr(src), _ptr(nrm), _ptr(w), int(m),
+            _ptr(trg) if trg is not None else None, lap, float(alpha), float(beta), float(near_factor),
+            nlev, dptr(rphi), dptr(rw), dptr(rcnt))
+    _check(lib.tube_correction_rules(*args, ctypes.byref(nnz), None, None, None, _stream(stream)))
+    rows = (1 if lap else 3) * (m if trg is not None else n)
+    rowptr = torch.empty(rows + 1, dtype=torch.int64, device=src.device)
+    col = torch.empty(max(nnz.value, 1), dtype=torch.int64, device=src.device)
+    val = torch.empty(max(nnz.value, 1), dtype=torch.float64, device=src.device)
+    _check(lib.tube_correction_rules(*args, ctypes.byref(nnz), _ptr(rowptr), _ptr(col), _ptr(val),
+                                     _stream(stream)))
+    return rowptr, col[:nnz.value], val[:nnz.value]
+
+
 def tube_correction(src, nrm, w, nelem, ns, nt, kind="stokes", alpha=1.0, beta=1.0,
-                    near_factor=0.5, stream=None):
+                    near_factor=0.5, stream=None, rules=None):
     """Quadrature correction E (rowptr, col, val) of the tube elements that make up the first
     nelem * ns * nt nodes (Sec. 3.2.1-3.2.4): for every tube node and every element whose
     near region holds it, the entries that turn the punctured sum over the element into the
     accurate integral.  kind "stokes" (alpha S + beta D, 3 x 3) or "laplace" (scalar); an
     operator K = diag I + D + eta S takes alpha = eta, beta = 1.  Pass the result as
-    StokesOp / LaplaceOp (..., correction=...)."""
+    StokesOp / LaplaceOp (..., correction=...).  rules: None (dyadically refined angular
+    rules) or compressed angular rules (phi, w, cnt), e.g. angular_rules.load(nt)."""
     n = src.shape[1]
     _dev(src, (3, n), "src")
     _dev(nrm, (3, n), "nrm")
@@ -255,6 +285,9 @@ def tube_correction(src, nrm, w, nelem, ns, nt, kind="stokes", alpha=1.0, beta=1
     if kind not in ("stokes", "laplace"):
         raise ValueError("kind must be 'stokes' or 'laplace'")
     lap = 1 if kind == "laplace" else 0
+    if rules is not None:
+        return _rules_call(src, nrm, w, nelem, ns, nt, None, lap, alpha, beta, near_factor, rules,
+                           stream)
     nnz = _i64(0)
     args = (int(nelem), int(ns), int(nt), int(n), _ptr(src), _ptr(nrm), _ptr(w), lap, float(alpha),
             float(beta), float(near_factor))
@@ -278,7 +311,7 @@ def peak_probe(kind, stream=None):
 
 
 def tube_correction_targets(src, nrm, w, nelem, ns, nt, trg, kind="stokes", alpha=1.0, beta=1.0,
-                            near_factor=0.5, stream=None):
+                            near_factor=0.5, stream=None, rules=None):
     """Correction E (rowptr, col, val) for off-surface targets trg (3, m) near the tube elements
     (Sec. 3.2.3): rows component-major over the targets, columns over the nodes.  The layer
     potential at trg is the plain sum (combined_apply / laplace_apply) plus E sigma."""
@@ -291,6 +324,9 @@ def tube_correction_targets(src, nrm, w, nelem, ns, nt, trg, kind="stokes", alph
     if kind not in ("stokes", "laplace"):
         raise ValueError("kind must be 'stokes' or 'laplace'")
     lap = 1 if kind == "laplace" else 0
+    if rules is not None:
+        return _rules_call(src, nrm, w, nelem, ns, nt, trg, lap, alpha, beta, near_factor, rules,
+                           stream)
     nnz = _i64(0)
     args = (int(nelem), int(ns), int(nt), int(n), _ptr(src), _ptr(nrm), _ptr(w), int(m), _ptr(trg),
             lap, float(alpha), float(beta), float(near_factor))

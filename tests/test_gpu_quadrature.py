@@ -346,3 +346,38 @@ def test_near_surface_interior_representation(sbq):
     # and the double layer's (r.n)/r^3 structure leaves ~1e-10 (the oracle: 2e-11..3e-9 at
     # depths 1e-4..1e-5)
     assert lap < 1e-10 and sto < 5e-10
+
+
+def test_compressed_angular_rules_match_dyadic(sbq):
+    """The builder with the compressed angular rules (Sec. 3.2.2 with Appendix B, the table
+    written by angular_rules.py for N_theta = 16) gives the E of the dyadic rules: same
+    pattern, every row within 1e-10 of its largest entry, Laplace and Stokes."""
+    import time
+    import torch
+    from paper_2310_00889_gb300 import angular_rules
+    rules = angular_rules.load(16)
+    assert rules is not None
+    S = I.torus(R0=1.0, eps=0.25, panels=16, ns=8, nth=16)
+    n = S.size
+    for kind, a, b in (("laplace", 1.0, 1.0), ("stokes", 1.55, 1.0)):
+        args = (_t(S.x), _t(S.n), _t(S.w), 16, 8, 16)
+        Ed = sbq.tube_correction(*args, kind=kind, alpha=a, beta=b, near_factor=0.5)
+        Er = sbq.tube_correction(*args, kind=kind, alpha=a, beta=b, near_factor=0.5, rules=rules)
+        assert np.array_equal(_np(Ed[0]), _np(Er[0])) and np.array_equal(_np(Ed[1]), _np(Er[1]))
+        vd, vr = _np(Ed[2]), _np(Er[2])
+        rp = _np(Ed[0])
+        worst = max(np.abs(vd[rp[r]:rp[r + 1]] - vr[rp[r]:rp[r + 1]]).max() / np.abs(vd[rp[r]:rp[r + 1]]).max()
+                    for r in range(len(rp) - 1) if rp[r + 1] > rp[r])
+        print("compressed rules, %s: worst row difference %.3e" % (kind, worst))
+        assert worst <= 1e-10
+    L = I.random_loop(seed=1, panels=128, ns=8, nth=16)
+    args = (_t(L.x), _t(L.n), _t(L.w), 128, 8, 16)
+    times = {}
+    for name, r in (("dyadic", None), ("compressed", rules)):
+        sbq.tube_correction(*args, kind="stokes", alpha=10.86, beta=1.0, rules=r)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sbq.tube_correction(*args, kind="stokes", alpha=10.86, beta=1.0, rules=r)
+        torch.cuda.synchronize()
+        times[name] = time.perf_counter() - t0
+    print("Stokes E build, 16384-node loop: dyadic %.3f s, compressed %.3f s" % (times["dyadic"], times["compressed"]))
