@@ -78,7 +78,7 @@ typedef enum {
 /* Tile shape of the pair-sum kernels.  targets per CTA = 32 * warps * r. */
 typedef struct {
     int r;             /* targets per thread held in registers */
-    int warps;         /* warps per CTA.  (r, warps): FP32 (2,4) (4,4) (8,4) (4,8) (4,2) (8,2);
+    int warps;         /* warps per CTA.  (r, warps): FP32 (1,4) (1,8) (2,4) (4,4) (8,4) (4,8) (4,2) (8,2);
                           FP64 (1,4) (2,4); DF32 (1,4) (2,4) (4,4) (2,8) */
     int chunk_tiles;   /* source tiles per work item; 0 = chosen from the SM count */
 } sbq_tune;
@@ -170,6 +170,10 @@ SBQ_API int stokes_sl_apply(int64_t ns, const double *src, const double *w, cons
  * host threads on one device) race and must be serialised by the caller.
  * On success the call performs no allocation of any kind; a rejected call records its
  * message for sbq_last_error() as every entry point does.
+ * Like the other applies it returns before the kernels finish: a bounded wait that expired
+ * inside them (SBQ_ETIMEOUT, output then incomplete) is recorded in a word of the fixed
+ * array, kept across calls, and reported and cleared by the next sbq_check_device() on
+ * that device.  Callers check it there after the apply.
  */
 /* (prec: SBQ_FP64, SBQ_FP32 or SBQ_FP32_COMP; SBQ_DF32 is not offered here: SBQ_EINVAL.) */
 SBQ_API int stokes_sl_apply_noalloc(int64_t ns, const double *src, const double *w,
@@ -391,6 +395,13 @@ SBQ_API int laplace_op_create(int64_t n, const double *src, const double *nrm, c
  * tensor, or a handle without the mobility set-up.
  */
 SBQ_API int stokes_op_set_mobility(void *op, int nbody, const int64_t *body_off, void *stream);
+/* Correction of the single layer alone for stokes_mobility_rhs: S nu is then the punctured
+ * sum plus this E times nu (Eq. nystrom-correction with the kernel S; e.g. tube_correction
+ * with alpha = 1, beta = 0).  CSR over the operator's nodes as for stokes_op_create (device
+ * arrays, rowptr of 3n + 1 entries, copied into the handle; nnz = 0 removes it).
+ * Synchronises the stream.  Errors: SBQ_EINVAL for a Laplace handle or bad pointers. */
+SBQ_API int stokes_op_set_sl_correction(void *op, int64_t nnz, const int64_t *rowptr,
+                                        const int64_t *col, const double *val, void *stream);
 SBQ_API int stokes_mobility_rhs(void *op, const double *FT, const double *us, double *rhs,
                                 int prec, void *stream);
 SBQ_API int stokes_mobility_velocity(void *op, const double *sigma, double *UW, void *stream);
@@ -443,8 +454,10 @@ SBQ_API int sbq_op_tune(const void *op, int prec, sbq_tune *out);
 SBQ_API int sbq_op_stats(const void *op, int prec, int *kernels_per_matvec,
                          double *pairs_per_matvec);
 
-/* Synchronise `stream` and report (then clear) the device error word set by bounded
- * waits inside kernels: SBQ_ETIMEOUT if a wait expired since the last check. */
+/* Synchronise `stream` and report (then clear) the device error words set by bounded
+ * waits inside kernels (the library's word of the current device and the word of
+ * stokes_sl_apply_noalloc's fixed array): SBQ_ETIMEOUT if a wait expired since the last
+ * check. */
 SBQ_API int sbq_check_device(void *stream);
 
 /* Failure-path self-test (no counterpart in the paper): launches one kernel on `stream`
@@ -453,6 +466,43 @@ SBQ_API int sbq_check_device(void *stream);
  * the wait expires the kernel sets the device error word and returns; a following
  * sbq_check_device() then reports SBQ_ETIMEOUT and clears the word.  Faults nothing. */
 SBQ_API int sbq_selftest_bounded_wait(int64_t limit_ns, void *stream);
+
+/*
+ * Slender-body mixing parameter of the combined-field formulations (Sec. 4.1):
+ *   eta = 1 / (2 eps log(1/eps)),  natural logarithm,
+ * eps the slenderness (tube radius over length scale, or over centreline radius of
+ * curvature).  eta: HOST output.  Errors: SBQ_EINVAL unless 0 < eps < 1.
+ */
+SBQ_API int sbq_slender_eta(double eps, double *eta);
+
+/*
+ * End-to-end calls on HOST buffers (paper has no counterpart: the same computation as the
+ * device-pointer calls, with the host<->device copies done by the library on `stream`).
+ * Every array argument is a HOST array (pinned memory makes the copies asynchronous DMA);
+ * the library allocates, fills and frees its device copies inside the call, which returns
+ * after synchronising the stream.  No tile shape is timed inside these calls: `tune`
+ * (HOST, nullable) fixes the shape, else the process-wide tuning cache's entry for this
+ * problem shape is used (filled by sbq_autotune or by the first apply of an operator of
+ * the same shape), else the default shape.
+ *
+ * stokes_apply_host: out = diag sigma + (D + eta S)[sigma] on the n surface nodes
+ *   (Eq. stokes-bie-new without a correction), precision prec.  src, nrm: 3n, w: n,
+ *   sigma, out: 3n doubles (SoA).
+ * stokes_solve_host: solves K x = rhs, K = diag I + D + eta S + E with GMRES (options and
+ *   report as gmres_solve; o and rep HOST).  E: none when nbody == 0, else the double-layer
+ *   singularity subtraction of stokes_dl_gauss_correction over the bodies body_off[0] = 0
+ *   <= ... <= body_off[nbody] = n, its row sums in precision corr_prec.  x: in x0, out the
+ *   solution (written back also for SBQ_ENOCONV).
+ * Errors: as stokes_op_create / stokes_matvec / gmres_solve; SBQ_ENONFINITE for a
+ * non-finite rhs.
+ */
+SBQ_API int stokes_apply_host(int64_t n, const double *src, const double *nrm, const double *w,
+                              double eta, double diag, const double *sigma, double *out, int prec,
+                              const sbq_tune *tune, void *stream);
+SBQ_API int stokes_solve_host(int64_t n, const double *src, const double *nrm, const double *w,
+                              double eta, double diag, int nbody, const int64_t *body_off,
+                              int corr_prec, const double *rhs, double *x,
+                              const sbq_gmres_opts *o, sbq_gmres_report *rep, void *stream);
 
 /* Free a plan or operator handle (NULL is ignored). */
 SBQ_API void sbq_destroy(void *handle);

@@ -294,12 +294,14 @@ def rigid_projector(x, w, body_off, centres):
 
 
 def mobility_solve(src, nrm, w, eta, body_off, F, T, us=None, E: CSR | None = None, tol=1e-11,
-                   restart=100, max_iter=2000):
+                   restart=100, max_iter=2000, E_S: CSR | None = None):
     """Stokes mobility problem, slender combined-field formulation (Sec. 4.2): completion
     flow nu (on each body the rigid motion alpha + beta x (x - c) whose quadrature force and
     torque about c are F_b, T_b: a 6 x 6 system assembled column by column), right-hand side
     u_s - S nu, GMRES on (K (I - L) + L) sigma, rigid velocity V = -L sigma, and each body's
     (U, Omega) by a least-squares fit of V on its nodes.  Centres: the weighted centroids.
+    E corrects the operator K (its eta S + D part), E_S the single layer S nu of the
+    right-hand side (the punctured sum plus E_S nu; Eq. nystrom-correction for S alone).
     Returns (UW (nbody, 6), sigma, info)."""
     src = _c(src)
     n = src.shape[1]
@@ -320,7 +322,10 @@ def mobility_solve(src, nrm, w, eta, body_off, F, T, us=None, E: CSR | None = No
                                         np.sum(w[a:b] * np.cross(d, v, axis=0), axis=1)]))
         ab = np.linalg.solve(np.array(cols).T, np.concatenate([F[i], T[i]]))
         nu[:, a:b] = ab[:3, None] + np.cross(ab[3:][:, None], d, axis=0)
-    rhs = -sl(src, w, nu, src)
+    snu = sl(src, w, nu, src)
+    if E_S is not None and E_S.nnz > 0:
+        snu = csr_apply(E_S, nu, snu)
+    rhs = -snu
     if us is not None:
         rhs = rhs + us
 

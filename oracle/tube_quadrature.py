@@ -77,24 +77,26 @@ def singular_rule():
 
 
 def lagrange(tn, t):
-    """Lagrange basis of the nodes tn and its derivative at the points t: (len t, len tn)."""
+    """Lagrange basis of the nodes tn and its derivative at the points t: (len t, len tn).
+    l_i(t) = prod_{k != i} (t - tn_k) / (tn_i - tn_k) and
+    l_i'(t) = sum_{m != i} 1 / (tn_i - tn_m) prod_{k != i, m} (t - tn_k) / (tn_i - tn_k),
+    the products taken over the factor axis of an array of all ratios (a factor that the
+    formula leaves out is replaced by 1)."""
     tn = np.asarray(tn, dtype=np.float64)
     t = np.atleast_1d(np.asarray(t, dtype=np.float64))
     ns = tn.shape[0]
-    L = np.ones((t.shape[0], ns))
+    eye = np.eye(ns, dtype=bool)
+    den = np.where(eye, 1.0, tn[:, None] - tn[None, :])            # (i, k)
+    ratio = (t[:, None, None] - tn[None, None, :]) / den[None]     # (point, i, k)
+    ratio = np.where(eye[None], 1.0, ratio)
+    L = np.prod(ratio, axis=2)
     dL = np.zeros((t.shape[0], ns))
-    for i in range(ns):
-        for k in range(ns):
-            if k != i:
-                L[:, i] *= (t - tn[k]) / (tn[i] - tn[k])
-        for m in range(ns):
-            if m == i:
-                continue
-            prod = np.full(t.shape[0], 1.0 / (tn[i] - tn[m]))
-            for k in range(ns):
-                if k != i and k != m:
-                    prod *= (t - tn[k]) / (tn[i] - tn[k])
-            dL[:, i] += prod
+    for m in range(ns):
+        rm = ratio.copy()
+        rm[:, :, m] = 1.0
+        term = np.prod(rm, axis=2) / den[:, m][None, :]
+        term[:, m] = 0.0                                           # m != i
+        dL += term
     return L, dL
 
 

@@ -148,17 +148,26 @@ static double mean_tile_radius(const std::vector<double> &hx, long long n, const
 // exact differences).  The operator keeps its geometry in the internal order and
 // perm[k] = the caller's index of internal node k; the density pack gathers through perm
 // and the reductions scatter through it, so callers never see the internal order.
-static int internal_order(Op *op, const double *src, const double *nrm, const double *w)
+// host_geom: src, nrm, w are host arrays (else device arrays, read back here).
+static int internal_order(Op *op, const double *src, const double *nrm, const double *w,
+                          bool host_geom)
 {
     const long long n = op->n;
     std::vector<double> hx(3 * n), hn(3 * n), hw(n);
-    cudaError_t e = cudaMemcpy(hx.data(), src, 3 * n * sizeof(double), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(hn.data(), nrm, 3 * n * sizeof(double), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(hw.data(), w, n * sizeof(double), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess)
-        return cuda_status(e, "cudaMemcpy (operator geometry)");
+    cudaError_t e = cudaSuccess;
+    if (host_geom) {
+        std::copy(src, src + 3 * n, hx.begin());
+        std::copy(nrm, nrm + 3 * n, hn.begin());
+        std::copy(w, w + n, hw.begin());
+    } else {
+        e = cudaMemcpy(hx.data(), src, 3 * n * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(hn.data(), nrm, 3 * n * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(hw.data(), w, n * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess)
+            return cuda_status(e, "cudaMemcpy (operator geometry)");
+    }
     for (double v : hx)
         if (!std::isfinite(v))
             return fail(SBQ_EINVAL, "non-finite source coordinate");
@@ -208,7 +217,7 @@ Op *as_op(const void *h)
 
 extern "C" {
 
-SBQ_API int sbq_version(void) { return 200; }
+SBQ_API int sbq_version(void) { return 300; }
 
 SBQ_API const char *sbq_last_error(void) { return last_error_cstr(); }
 
@@ -308,7 +317,7 @@ SBQ_API int batch_plan(int nseg, const int64_t *seg_src_off, const int64_t *seg_
 static int op_create_impl(int64_t n, const double *src, const double *nrm, const double *w,
                           double eta, double diag, int64_t nnz, const int64_t *rowptr,
                           const int64_t *col, const double *val, const void *plan, void **op_out,
-                          bool laplace)
+                          bool laplace, bool host_geom = false)
 {
     clear_error();
     if (!op_out)
@@ -361,7 +370,7 @@ static int op_create_impl(int64_t n, const double *src, const double *nrm, const
     if ((st = op->nrm.alloc(vb)) != SBQ_OK) return bail(st);
     if ((st = op->w.alloc(static_cast<size_t>(n) * sizeof(double))) != SBQ_OK) return bail(st);
     if ((st = op->perm.alloc(static_cast<size_t>(n) * sizeof(int))) != SBQ_OK) return bail(st);
-    if (n > 0 && (st = internal_order(op, src, nrm, w)) != SBQ_OK)
+    if (n > 0 && (st = internal_order(op, src, nrm, w, host_geom)) != SBQ_OK)
         return bail(st);
     if (nnz > 0) {
         const size_t rows = static_cast<size_t>(op->ncomp) * n;
@@ -416,6 +425,157 @@ SBQ_API int laplace_op_create(int64_t n, const double *src, const double *nrm, c
     return op_create_impl(n, src, nrm, w, eta, diag, nnz, rowptr, col, val, plan, op_out, true);
 }
 
+SBQ_API int sbq_slender_eta(double eps, double *eta)
+{
+    clear_error();
+    if (!eta)
+        return fail(SBQ_EINVAL, "null output");
+    if (!(eps > 0.0 && eps < 1.0))
+        return fail(SBQ_EINVAL, "slenderness must lie in (0, 1)");
+    // Sec. 4.1: eta = 1 / (2 eps log(1/eps)), natural logarithm
+    *eta = 1.0 / (2.0 * eps * std::log(1.0 / eps));
+    return SBQ_OK;
+}
+
+// Operator of the host-buffer entry points: geometry read from host arrays, no correction
+// or the double-layer singularity subtraction over the bodies (built on the device).
+namespace {
+
+struct HostOpGuard {
+    Op *op = nullptr;
+    ~HostOpGuard() { delete op; }
+};
+
+int host_vec_ok(const double *p, long long cnt)
+{
+    for (long long i = 0; i < cnt; ++i)
+        if (!std::isfinite(p[i]))
+            return 0;
+    return 1;
+}
+
+}  // namespace
+
+SBQ_API int stokes_apply_host(int64_t n, const double *src, const double *nrm, const double *w,
+                              double eta, double diag, const double *sigma, double *out, int prec,
+                              const sbq_tune *tune, void *stream)
+{
+    clear_error();
+    if (n < 0)
+        return fail(SBQ_EINVAL, "negative size");
+    if (!prec_ok(prec))
+        return fail(SBQ_EINVAL, "unknown precision");
+    if (n > 0 && (!src || !nrm || !w || !sigma || !out))
+        return fail(SBQ_EINVAL, "null host pointer");
+    if (tune && tune->r != 0 && !pairsum_shape_supported(prec, tune->r, tune->warps))
+        return fail(SBQ_EINVAL, "unsupported tile shape for this precision");
+    if (n == 0)
+        return SBQ_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    HostOpGuard g;
+    void *h = nullptr;
+    SBQ_TRY(op_create_impl(n, src, nrm, w, eta, diag, 0, nullptr, nullptr, nullptr, nullptr, &h,
+                           false, true));
+    g.op = static_cast<Op *>(h);
+    const size_t vb = 3 * static_cast<size_t>(n) * sizeof(double);
+    DevBuf d_sig, d_out;
+    SBQ_TRY(d_sig.alloc(vb));
+    SBQ_TRY(d_out.alloc(vb));
+    SBQ_CUDA(cudaMemcpyAsync(d_sig.p, sigma, vb, cudaMemcpyHostToDevice, s));
+    SBQ_TRY(op_prepare_untimed(g.op, prec, tune, s));
+    SBQ_TRY(op_matvec(g.op, d_sig.as<double>(), d_out.as<double>(), prec, s));
+    SBQ_CUDA(cudaMemcpyAsync(out, d_out.p, vb, cudaMemcpyDeviceToHost, s));
+    SBQ_CUDA(cudaStreamSynchronize(s));
+    return SBQ_OK;
+}
+
+SBQ_API int stokes_solve_host(int64_t n, const double *src, const double *nrm, const double *w,
+                              double eta, double diag, int nbody, const int64_t *body_off,
+                              int corr_prec, const double *rhs, double *x,
+                              const sbq_gmres_opts *o, sbq_gmres_report *rep, void *stream)
+{
+    clear_error();
+    if (n < 0)
+        return fail(SBQ_EINVAL, "negative size");
+    if (!o)
+        return fail(SBQ_EINVAL, "null options");
+    if (n > 0 && (!src || !nrm || !w || !rhs || !x))
+        return fail(SBQ_EINVAL, "null host pointer");
+    if (nbody < 0 || (nbody > 0 && !body_off))
+        return fail(SBQ_EINVAL, "nbody < 0 or null body offsets");
+    if (nbody > 0) {
+        if (body_off[0] != 0 || body_off[nbody] != n)
+            return fail(SBQ_EINVAL, "body offsets must run from 0 to n");
+        for (int b = 0; b < nbody; ++b)
+            if (body_off[b + 1] < body_off[b])
+                return fail(SBQ_EINVAL, "body offsets must be non-decreasing");
+        if (!prec_ok(corr_prec))
+            return fail(SBQ_EINVAL, "unknown correction precision");
+    }
+    if (!(o->tol > 0.0) || o->restart < 1 || o->restart > 256 || o->max_iter < 1 ||
+        !prec_ok(o->inner_prec))
+        return fail(SBQ_EINVAL, "bad GMRES options (tol > 0, 1 <= restart <= 256, max_iter >= 1)");
+    const bool mixed = (o->inner_prec == SBQ_FP32 || o->inner_prec == SBQ_FP32_COMP);
+    if (mixed && (!(o->inner_tol > 0.0) || o->inner_tol >= 1.0 || o->max_outer < 1))
+        return fail(SBQ_EINVAL, "bad refinement options (0 < inner_tol < 1, max_outer >= 1)");
+    if (mixed && o->resid_prec != SBQ_FP64 && o->resid_prec != SBQ_DF32)
+        return fail(SBQ_EINVAL, "resid_prec must be SBQ_FP64 or SBQ_DF32");
+    sbq_gmres_report local{};
+    sbq_gmres_report &r = rep ? *rep : local;
+    r = sbq_gmres_report{};
+    if (n == 0)
+        return SBQ_OK;
+    if (!host_vec_ok(rhs, 3 * n))
+        return fail(SBQ_ENONFINITE, "non-finite right-hand side");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t vb = 3 * static_cast<size_t>(n) * sizeof(double);
+    DevBuf d_rowptr, d_col, d_val;
+    int64_t nnz = 0;
+    if (nbody > 0) {
+        // the correction is built from device copies of the geometry
+        DevBuf d_src, d_nrm, d_w;
+        SBQ_TRY(d_src.alloc(vb));
+        SBQ_TRY(d_nrm.alloc(vb));
+        SBQ_TRY(d_w.alloc(static_cast<size_t>(n) * sizeof(double)));
+        SBQ_CUDA(cudaMemcpyAsync(d_src.p, src, vb, cudaMemcpyHostToDevice, s));
+        SBQ_CUDA(cudaMemcpyAsync(d_nrm.p, nrm, vb, cudaMemcpyHostToDevice, s));
+        SBQ_CUDA(cudaMemcpyAsync(d_w.p, w, static_cast<size_t>(n) * sizeof(double),
+                                 cudaMemcpyHostToDevice, s));
+        nnz = 9 * n;
+        SBQ_TRY(d_rowptr.alloc((3 * static_cast<size_t>(n) + 1) * sizeof(int64_t)));
+        SBQ_TRY(d_col.alloc(static_cast<size_t>(nnz) * sizeof(int64_t)));
+        SBQ_TRY(d_val.alloc(static_cast<size_t>(nnz) * sizeof(double)));
+        SBQ_TRY(dl_gauss_correction(nbody, body_off, d_src.as<double>(), d_nrm.as<double>(),
+                                    d_w.as<double>(), corr_prec, d_rowptr.as<int64_t>(),
+                                    d_col.as<int64_t>(), d_val.as<double>(), s));
+        SBQ_CUDA(cudaStreamSynchronize(s));
+    }
+    HostOpGuard g;
+    void *h = nullptr;
+    SBQ_TRY(op_create_impl(n, src, nrm, w, eta, diag, nnz, d_rowptr.as<int64_t>(),
+                           d_col.as<int64_t>(), d_val.as<double>(), nullptr, &h, false, true));
+    g.op = static_cast<Op *>(h);
+    DevBuf d_rhs, d_x;
+    SBQ_TRY(d_rhs.alloc(vb));
+    SBQ_TRY(d_x.alloc(vb));
+    SBQ_CUDA(cudaMemcpyAsync(d_rhs.p, rhs, vb, cudaMemcpyHostToDevice, s));
+    SBQ_CUDA(cudaMemcpyAsync(d_x.p, x, vb, cudaMemcpyHostToDevice, s));
+    // every precision the solve applies K in: shapes from the tuning cache, nothing timed
+    SBQ_TRY(op_prepare_untimed(g.op, o->inner_prec, nullptr, s));
+    if (mixed) {
+        SBQ_TRY(op_prepare_untimed(g.op, o->resid_prec, nullptr, s));
+        if (o->resid_prec == SBQ_DF32)
+            SBQ_TRY(op_prepare_untimed(g.op, SBQ_FP64, nullptr, s));
+    }
+    const int st = gmres_solve_impl(g.op, d_rhs.as<double>(), d_x.as<double>(), *o, r, s);
+    r.status = st;
+    if (st != SBQ_OK && st != SBQ_ENOCONV)
+        return st;
+    SBQ_CUDA(cudaMemcpyAsync(x, d_x.p, vb, cudaMemcpyDeviceToHost, s));
+    SBQ_CUDA(cudaStreamSynchronize(s));
+    return st;
+}
+
 SBQ_API int stokes_op_set_mobility(void *oph, int nbody, const int64_t *body_off, void *stream)
 {
     clear_error();
@@ -431,6 +591,39 @@ SBQ_API int stokes_op_set_mobility(void *oph, int nbody, const int64_t *body_off
             return fail(SBQ_EINVAL, "body offsets must be non-decreasing");
     std::lock_guard<std::mutex> lk(op->mu);
     return mob_setup(op, nbody, body_off, static_cast<cudaStream_t>(stream));
+}
+
+SBQ_API int stokes_op_set_sl_correction(void *oph, int64_t nnz, const int64_t *rowptr,
+                                        const int64_t *col, const double *val, void *stream)
+{
+    clear_error();
+    Op *op = as_op(oph);
+    if (!op)
+        return fail(SBQ_EINVAL, "not an operator handle");
+    if (op->laplace)
+        return fail(SBQ_EINVAL, "the single-layer correction serves the Stokes mobility problem");
+    if (nnz < 0 || (nnz > 0 && (!rowptr || !col || !val)))
+        return fail(SBQ_EINVAL, "negative nnz or null CSR pointer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> lk(op->mu);
+    op->sl_nnz = 0;
+    if (nnz == 0) {
+        op->sl_rowptr.release();
+        op->sl_col.release();
+        op->sl_val.release();
+        return SBQ_OK;
+    }
+    const size_t rows = 3 * static_cast<size_t>(op->n);
+    SBQ_TRY(op->sl_rowptr.alloc((rows + 1) * sizeof(int64_t)));
+    SBQ_TRY(op->sl_col.alloc(static_cast<size_t>(nnz) * sizeof(int64_t)));
+    SBQ_TRY(op->sl_val.alloc(static_cast<size_t>(nnz) * sizeof(double)));
+    SBQ_CUDA(cudaMemcpyAsync(op->sl_rowptr.p, rowptr, (rows + 1) * sizeof(int64_t),
+                             cudaMemcpyDeviceToDevice, s));
+    SBQ_CUDA(cudaMemcpyAsync(op->sl_col.p, col, nnz * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    SBQ_CUDA(cudaMemcpyAsync(op->sl_val.p, val, nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    SBQ_CUDA(cudaStreamSynchronize(s));
+    op->sl_nnz = nnz;
+    return SBQ_OK;
 }
 
 SBQ_API int stokes_mobility_rhs(void *oph, const double *FT, const double *us, double *rhs,
@@ -622,11 +815,13 @@ SBQ_API int sbq_check_device(void *stream)
         return fail(SBQ_ENOMEM, "cannot allocate the device error word");
     int h = 0;
     SBQ_CUDA(cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (h != 0) {
+    if (h != 0)
         SBQ_CUDA(cudaMemset(err, 0, sizeof(int)));
-        if (h & DEV_ERR_TIMEOUT)
-            return fail(SBQ_ETIMEOUT, "a device-side bounded wait expired");
-    }
+    // the allocation-free apply keeps its own word inside its fixed scratch array
+    int hn = 0;
+    SBQ_TRY(noalloc_take_error(&hn));
+    if ((h | hn) & DEV_ERR_TIMEOUT)
+        return fail(SBQ_ETIMEOUT, "a device-side bounded wait expired");
     return SBQ_OK;
 }
 

@@ -283,6 +283,7 @@ int build_trg_set(TrgSet &ts, int kind, int prec, const sbq_tune &tune, const Sr
     struct Item {
         int4 v;
         int cost;
+        double pairs;
     };
     std::vector<Item> items;
     int slot = 0;
@@ -310,6 +311,10 @@ int build_trg_set(TrgSet &ts, int kind, int prec, const sbq_tune &tune, const Sr
                 Item it;
                 it.v = make_int4(tidx, a, b, slots ? slot + c : -1);
                 it.cost = b - a;
+                const long long src_a = src_off[i] + static_cast<long long>(a - sb) * sp.TS;
+                const long long src_b = std::min<long long>(
+                    src_off[i + 1], src_off[i] + static_cast<long long>(b - sb) * sp.TS);
+                it.pairs = static_cast<double>(ti.count) * static_cast<double>(src_b - src_a);
                 items.push_back(it);
             }
             if (slots)
@@ -321,8 +326,11 @@ int build_trg_set(TrgSet &ts, int kind, int prec, const sbq_tune &tune, const Sr
     std::stable_sort(items.begin(), items.end(),
                      [](const Item &x, const Item &y) { return x.cost > y.cost; });
     std::vector<int4> hv(items.size());
-    for (size_t i = 0; i < items.size(); ++i)
+    ts.item_pairs.resize(items.size());
+    for (size_t i = 0; i < items.size(); ++i) {
         hv[i] = items[i].v;
+        ts.item_pairs[i] = items[i].pairs;
+    }
 
     ts.n_ttiles = static_cast<int>(ht.size());
     ts.n_items = static_cast<int>(hv.size());
@@ -465,6 +473,60 @@ static std::tuple<int, int, int, long long, long long, int> tune_key(const Op *o
                            device_props().sms);
 }
 
+// Kernel time of the pair sums over the first `items` work items of ts (the longest ones:
+// the list is sorted by cost), from events recorded around the pair-sum launch; the pack
+// and reduction kernels run as in an apply.  Returns pair interactions per millisecond.
+static int time_prefix(int kind, int prec, const SrcPack &sp, TrgSet &ts, const Op *op,
+                       const double *zs, double *zo, double scale, double kappa, int items,
+                       cudaStream_t s, double *rate, float *kernel_ms)
+{
+    const int saved = ts.n_items;
+    items = std::max(1, std::min(items, saved));
+    double pairs = 0.0;
+    for (int i = 0; i < items; ++i)
+        pairs += ts.item_pairs[i];
+    PairsumTiming pt;
+    SBQ_CUDA(cudaEventCreate(&pt.before));
+    cudaError_t ce = cudaEventCreate(&pt.after);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(pt.before);
+        return cuda_status(ce, "autotune");
+    }
+    // warm-up over one item: the first launch of a kernel loads its module
+    ts.n_items = 1;
+    int st = run_pairsum(kind, prec, sp, ts, op->w.as<double>(), zs, op->n, op->src.as<double>(),
+                         op->n, zo, scale, kappa, 0.0, nullptr, s);
+    PairsumTiming *prev = pairsum_timing();
+    pairsum_timing() = &pt;
+    ts.n_items = items;
+    if (st == SBQ_OK)
+        st = run_pairsum(kind, prec, sp, ts, op->w.as<double>(), zs, op->n, op->src.as<double>(),
+                         op->n, zo, scale, kappa, 0.0, nullptr, s);
+    ts.n_items = saved;
+    pairsum_timing() = prev;
+    float ms = 0.0f;
+    if (st == SBQ_OK) {
+        ce = cudaEventSynchronize(pt.after);
+        if (ce == cudaSuccess)
+            ce = cudaEventElapsedTime(&ms, pt.before, pt.after);
+        if (ce != cudaSuccess)
+            st = cuda_status(ce, "autotune");
+    }
+    cudaEventDestroy(pt.before);
+    cudaEventDestroy(pt.after);
+    *kernel_ms = ms;
+    *rate = (ms > 0.0f) ? pairs / ms : 0.0;
+    return st;
+}
+
+// Tile-shape autotuner.  Small problems: every candidate (shape, chunking) is timed on
+// whole applies (pack, pair sums, reduction), which includes the tail of the persistent
+// grid.  Large problems (an apply of the first candidate estimated above 20 ms): each
+// shape, at its default chunking (where the tail is a small part of the apply), is timed
+// on two waves of its longest work items (two items per resident CTA), whose cost is
+// representative of the whole list, best of two runs, and the candidates are compared by
+// pair interactions per millisecond.  If one wave of the first candidate already takes
+// longer than 250 ms (FP64 at a million nodes), it is kept untimed.
 static int autotune_op(Op *op, int prec, cudaStream_t s)
 {
     int kind;
@@ -489,7 +551,8 @@ static int autotune_op(Op *op, int prec, cudaStream_t s)
     } else if (prec == SBQ_DF32) {
         shapes = {{2, 4, 0}, {1, 4, 0}, {4, 4, 0}, {2, 8, 0}};
     } else {
-        shapes = {{2, 4, 0}, {4, 2, 0}, {4, 4, 0}, {8, 2, 0}, {8, 4, 0}, {4, 8, 0}};
+        shapes = {{2, 4, 0}, {4, 2, 0}, {4, 4, 0}, {1, 4, 0}, {1, 8, 0}, {8, 2, 0}, {8, 4, 0},
+                  {4, 8, 0}};
     }
     DevBuf zs, zo;
     SBQ_TRY(zs.alloc(3 * static_cast<size_t>(op->n) * sizeof(double)));
@@ -498,14 +561,19 @@ static int autotune_op(Op *op, int prec, cudaStream_t s)
     cudaEvent_t e0, e1;
     SBQ_CUDA(cudaEventCreate(&e0));
     SBQ_CUDA(cudaEventCreate(&e1));
-    float best_ms = 1e30f;
+    auto done = [&](int st) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return st;
+    };
+    double best_rate = -1.0;       // pair interactions per ms (higher is better)
     std::unique_ptr<TrgSet> best;
     double budget_ms = 0.0;
-    bool slow = false;
+    int mode = 0;                  // 0: undecided, 1: whole applies, 2: two-wave prefixes
     for (size_t si = 0; si < shapes.size() && budget_ms < 4000.0; ++si) {
         const int c0 = auto_chunk_tiles(kind, prec, shapes[si], sp, op->plan.src_off);
         std::vector<int> cands = {c0};
-        if (!slow) {
+        if (mode != 2) {
             if (c0 > 1)
                 cands.push_back(std::max(1, c0 / 2));
             cands.push_back(2 * c0);
@@ -516,66 +584,78 @@ static int autotune_op(Op *op, int prec, cudaStream_t s)
             auto ts = std::make_unique<TrgSet>();
             int st = build_trg_set(*ts, kind, prec, t, sp, op->plan.src_off, op->src.as<double>(),
                                    op->n, op->plan.src_off, s);
-            // first (warm-up) apply, timed: a shape whose single apply is already long is
-            // taken as it is (tuning it would cost more than it can save)
-            float first_ms = 0.0f;
-            if (st == SBQ_OK) {
-                cudaEventRecord(e0, s);
-                st = run_pairsum(kind, prec, sp, *ts, op->w.as<double>(), zs.as<double>(), op->n,
-                                 op->src.as<double>(), op->n, zo.as<double>(), scale, kappa, 0.0,
-                                 nullptr, s);
-                cudaEventRecord(e1, s);
-                if (st == SBQ_OK) {
-                    cudaError_t ce = cudaEventSynchronize(e1);
-                    if (ce != cudaSuccess)
-                        st = cuda_status(ce, "autotune");
-                    else
-                        cudaEventElapsedTime(&first_ms, e0, e1);
-                }
-            }
-            if (st == SBQ_OK && first_ms > 250.0f) {
-                if (!best)
-                    best = std::move(ts);
+            if (st != SBQ_OK)
+                return done(st);
+            if (ts->n_items == 0) {   // nothing to time
+                best = std::move(ts);
                 budget_ms = 1e30;
                 break;
             }
-            const int reps = slow ? 1 : 3;
-            if (st == SBQ_OK) {
-                cudaEventRecord(e0, s);
-                for (int r = 0; r < reps && st == SBQ_OK; ++r)
+            double rate = 0.0;
+            if (mode != 1) {
+                float kms = 0.0f;
+                if (mode == 0) {
+                    // one wave decides how to time the candidates
+                    st = time_prefix(kind, prec, sp, *ts, op, zs.as<double>(), zo.as<double>(),
+                                     scale, kappa, ts->grid, s, &rate, &kms);
+                    if (st != SBQ_OK)
+                        return done(st);
+                    budget_ms += kms;
+                    const double est_full_ms = rate > 0.0 ? ts->pairs / rate : 0.0;
+                    if (kms > 250.0f) {   // too long to tune: keep the first candidate
+                        best = std::move(ts);
+                        budget_ms = 1e30;
+                        break;
+                    }
+                    mode = (est_full_ms > 20.0 && ts->n_items > 4 * ts->grid) ? 2 : 1;
+                }
+                if (mode == 2) {
+                    // the measurement: two waves, best of two runs
+                    rate = 0.0;
+                    for (int rep = 0; rep < 2; ++rep) {
+                        double r2 = 0.0;
+                        st = time_prefix(kind, prec, sp, *ts, op, zs.as<double>(), zo.as<double>(),
+                                         scale, kappa, 2 * ts->grid, s, &r2, &kms);
+                        if (st != SBQ_OK)
+                            return done(st);
+                        budget_ms += kms;
+                        rate = std::max(rate, r2);
+                    }
+                }
+            }
+            if (mode == 1) {
+                // one warm-up apply, then three timed ones
+                const int reps = 3;
+                for (int r = 0; r <= reps && st == SBQ_OK; ++r) {
+                    if (r == 1)
+                        cudaEventRecord(e0, s);
                     st = run_pairsum(kind, prec, sp, *ts, op->w.as<double>(), zs.as<double>(),
                                      op->n, op->src.as<double>(), op->n, zo.as<double>(), scale,
                                      kappa, 0.0, nullptr, s);
+                }
                 cudaEventRecord(e1, s);
                 if (st == SBQ_OK) {
                     cudaError_t ce = cudaEventSynchronize(e1);
                     if (ce != cudaSuccess)
                         st = cuda_status(ce, "autotune");
                 }
+                if (st != SBQ_OK)
+                    return done(st);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms /= reps;
+                budget_ms += ms * (reps + 1);
+                rate = ms > 0.0f ? ts->pairs / ms : 0.0;
             }
-            if (st != SBQ_OK) {
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                return st;
-            }
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            ms /= reps;
-            budget_ms += ms * (reps + 1);
-            if (ms < best_ms) {
-                best_ms = ms;
+            if (rate > best_rate) {
+                best_rate = rate;
                 best = std::move(ts);
             }
-            if (ms > 50.0f)
-                slow = true;
-            if (ms > 1000.0f)
-                budget_ms = 1e30;   // one launch per shape is already too long to tune
             if (budget_ms >= 4000.0)
                 break;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    done(SBQ_OK);
     if (!best) {
         set_error("autotune found no runnable tile shape");
         return SBQ_ECUDA;
@@ -586,6 +666,27 @@ static int autotune_op(Op *op, int prec, cudaStream_t s)
     }
     op->ts[prec] = std::move(best);
     op->tuned[prec] = true;
+    return SBQ_OK;
+}
+
+int op_prepare_untimed(Op *op, int prec, const sbq_tune *tune, cudaStream_t s)
+{
+    int kind;
+    double scale, kappa;
+    op_kind(op, &kind, &scale, &kappa);
+    sbq_tune t = default_tune(prec, op->n);
+    if (tune && tune->r != 0) {
+        t = *tune;
+    } else {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(tune_key(op, kind, prec));
+        if (it != g_tune_cache.end())
+            t = it->second;
+    }
+    auto ts = std::make_unique<TrgSet>();
+    SBQ_TRY(build_trg_set(*ts, kind, prec, t, op_srcpack(op, prec), op->plan.src_off,
+                          op->src.as<double>(), op->n, op->plan.src_off, s));
+    op->ts[prec] = std::move(ts);
     return SBQ_OK;
 }
 

@@ -62,6 +62,7 @@ struct TrgSet {
     int grid = 0;
     bool needs_reduce = false;
     double pairs = 0.0;         // pair interactions per apply (valid members only)
+    std::vector<double> item_pairs;   // host: pair interactions of each work item, list order
     DevBuf ttiles, tpack, tpack_lo, tpack_l2, items, partial, counter;
 };
 
@@ -85,6 +86,8 @@ struct Op {
     DevBuf src, nrm, w;                // library copies (SoA), in the internal node order
     DevBuf perm;                       // int: caller's index of each internal node
     DevBuf rowptr, col, val;           // CSR correction
+    long long sl_nnz = 0;              // correction of the single layer alone (mobility S nu)
+    DevBuf sl_rowptr, sl_col, sl_val;
     PlanH plan;                        // segments (one segment if none given)
     SrcPack sp32, sp64, spdf;          // FP32 (plain and compensated), FP64, double-float
     std::unique_ptr<TrgSet> ts[4];     // per sbq_prec
@@ -123,6 +126,9 @@ int run_pairsum(int kind, int prec, const SrcPack &sp, const TrgSet &ts, const d
 int op_matvec(Op *op, const double *sigma, double *out, int prec, cudaStream_t s,
               double *bound = nullptr);
 int op_ensure_tuned(Op *op, int prec, cudaStream_t s);
+// Work list of op for prec without timing anything: the given shape, else the tuning
+// cache's entry for this problem shape, else the default shape.
+int op_prepare_untimed(Op *op, int prec, const sbq_tune *tune, cudaStream_t s);
 int op_kernels_per_matvec(const Op *op, int prec);
 
 // Kind and prefactors of alpha S + beta D (Stokes; Laplace).

@@ -263,6 +263,10 @@ int mob_rhs(Op *op, const double *FT, const double *us, double *rhs, int prec, c
     SBQ_TRY(run_pairsum(kind, prec, sp, *op->ts[prec], op->w.as<double>(), m.r.as<double>(),
                         op->n, op->src.as<double>(), op->n, m.y.as<double>(), scale, kappa, 0.0,
                         nullptr, s, nullptr, op->perm.as<int>()));
+    // the accurate single layer: the punctured sum plus its correction, when one is set
+    if (op->sl_nnz > 0)
+        SBQ_CUDA(launch_csr_apply(3 * op->n, op->sl_rowptr.as<int64_t>(), op->sl_col.as<int64_t>(),
+                                  op->sl_val.as<double>(), m.r.as<double>(), m.y.as<double>(), s));
     // rhs = u_s - S nu
     SBQ_CUDA(cudaMemsetAsync(rhs, 0, 3 * op->n * sizeof(double), s));
     if (us)

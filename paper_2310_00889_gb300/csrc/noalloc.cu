@@ -70,7 +70,9 @@ Layout make_layout(int prec, int n_st, int n_tt, int TT, int n_items, long long 
 }
 
 // Tile tables and work list of a single segment, written on the device so that the call
-// needs no host staging buffer either; zeroes the error word and the claim counter.
+// needs no host staging buffer either; zeroes the claim counter.  The error word at the
+// start of the array is left alone: a bounded wait that expired in an earlier call stays
+// recorded until sbq_check_device() reads and clears it.
 __global__ void noalloc_tables(unsigned char *base, Layout L, long long ns, long long nt, int TS,
                                int TT, int n_st, int n_tt, int n_chunks, int C, int slots)
 {
@@ -79,10 +81,8 @@ __global__ void noalloc_tables(unsigned char *base, Layout L, long long ns, long
     int4 *items = reinterpret_cast<int4 *>(base + L.items);
     const long long tid = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
     const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
-    if (tid == 0) {
-        *reinterpret_cast<int *>(base + L.err) = 0;
+    if (tid == 0)
         *reinterpret_cast<int *>(base + L.counter) = 0;
-    }
     for (long long k = tid; k < n_st; k += stride) {
         TileInfo ti{};
         ti.begin = k * TS;
@@ -110,6 +110,35 @@ __global__ void noalloc_tables(unsigned char *base, Layout L, long long ns, long
 }
 
 }  // namespace
+
+namespace sbq {
+
+// Error word of the allocation-free apply on the current device (offset 0 of its array):
+// returns the bits set since the last call and clears them.  0 when the entry point has
+// not been used on this device (the array was never addressed: nothing to read).
+int noalloc_take_error(int *bits)
+{
+    *bits = 0;
+    int dev = 0;
+    SBQ_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+        return SBQ_OK;
+    void *p = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        p = g_noalloc_ptr[dev];
+    }
+    if (!p)
+        return SBQ_OK;
+    int h = 0;
+    SBQ_CUDA(cudaMemcpy(&h, p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h != 0)
+        SBQ_CUDA(cudaMemset(p, 0, sizeof(int)));
+    *bits = h;
+    return SBQ_OK;
+}
+
+}  // namespace sbq
 
 extern "C" SBQ_API int stokes_sl_apply_noalloc(int64_t ns, const double *src, const double *w,
                                                const double *sigma, int64_t nt,

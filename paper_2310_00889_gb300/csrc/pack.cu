@@ -590,7 +590,7 @@ bool pairsum_shape_supported(int prec, int R, int W)
         return W == 4 && (R == 1 || R == 2);
     if (prec == SBQ_DF32)
         return (W == 4 && (R == 1 || R == 2 || R == 4)) || (W == 8 && R == 2);
-    return (W == 4 && (R == 2 || R == 4 || R == 8)) || (W == 8 && R == 4) ||
+    return (W == 4 && (R == 1 || R == 2 || R == 4 || R == 8)) || (W == 8 && (R == 1 || R == 4)) ||
            (W == 2 && (R == 4 || R == 8));
 }
 

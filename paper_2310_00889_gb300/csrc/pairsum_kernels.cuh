@@ -78,12 +78,25 @@ __device__ __forceinline__ void f2_unpack(f2 v, float &lo, float &hi)
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
 
+// 1/x on the SFU, denormals flushed (x as for rsqrt_sfu).
+__device__ __forceinline__ float rcp_sfu(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Per-pair arithmetic for one target against two sources at once, given r = (dx, dy, dz)
 // (packed).  Accumulates (folded prefactors, see the launcher):
-//   SL: ri q + (r.q) ri^3 r
+//   SL: ri (q + (r.q) ri^2 r)
 //   DL: (r.q)(r.n) ri^5 r
-//   CF: ri q + (r.q) ri^3 (1 + (r.n') ri^2) r,  n' = kappa n stored by the pack
+//   CF: ri (q + (r.q) ri^2 (1 + (r.n') ri^2) r),  n' = kappa n stored by the pack
 //   Laplace (scalar q): LSL ri q, LDL (r.n) ri^3 q, LCF ri q (1 + (r.n') ri^2)
+// ri^2 comes from the SFU reciprocal of r^2 (a second SFU operation per pair in place of
+// an FP32-pipe multiply: the FP32 pipe is the kernel's bound, the SFU has room), except
+// in tile pairs that may hold coincident points (CHECK), where ri is zeroed for skipped
+// pairs and ri^2 = ri ri inherits that zero.  Per two pairs the combined field takes 21
+// packed FP32 operations (3 sub, 13 fma, 5 mul) and 4 SFU operations.
 template <int KIND, bool CHECK>
 __device__ __forceinline__ void pair2(f2 dx, f2 dy, f2 dz, f2 QX, f2 QY, f2 QZ, f2 NX, f2 NY, f2 NZ,
                                       float thr2, f2 &ax, f2 &ay, f2 &az)
@@ -97,42 +110,41 @@ __device__ __forceinline__ void pair2(f2 dx, f2 dy, f2 dz, f2 QX, f2 QY, f2 QZ, 
         rb = (r2b > thr2) ? rb : 0.0f;
     }
     const f2 ri = f2_pack(ra, rb);
-    const f2 rq = f2_fma(dx, QX, f2_fma(dy, QY, f2_mul(dz, QZ)));
-    const f2 ri2 = f2_mul(ri, ri);
+    auto inv_r2 = [&]() -> f2 {
+        return CHECK ? f2_mul(ri, ri) : f2_pack(rcp_sfu(r2a), rcp_sfu(r2b));
+    };
     if (KIND == KIND_SL) {
-        const f2 b = f2_mul(f2_mul(rq, ri2), ri);
-        ax = f2_fma(ri, QX, ax);
-        ay = f2_fma(ri, QY, ay);
-        az = f2_fma(ri, QZ, az);
-        ax = f2_fma(b, dx, ax);
-        ay = f2_fma(b, dy, ay);
-        az = f2_fma(b, dz, az);
+        const f2 rq = f2_fma(dx, QX, f2_fma(dy, QY, f2_mul(dz, QZ)));
+        const f2 b = f2_mul(rq, inv_r2());
+        ax = f2_fma(ri, f2_fma(b, dx, QX), ax);
+        ay = f2_fma(ri, f2_fma(b, dy, QY), ay);
+        az = f2_fma(ri, f2_fma(b, dz, QZ), az);
     } else if (KIND == KIND_DL) {
+        const f2 rq = f2_fma(dx, QX, f2_fma(dy, QY, f2_mul(dz, QZ)));
         const f2 rn = f2_fma(dx, NX, f2_fma(dy, NY, f2_mul(dz, NZ)));
+        const f2 ri2 = inv_r2();
         const f2 b = f2_mul(f2_mul(f2_mul(rq, ri2), f2_mul(rn, ri2)), ri);
         ax = f2_fma(b, dx, ax);
         ay = f2_fma(b, dy, ay);
         az = f2_fma(b, dz, az);
     } else if (KIND == KIND_CF) {
         const f2 one = f2_pack(1.0f, 1.0f);
+        const f2 rq = f2_fma(dx, QX, f2_fma(dy, QY, f2_mul(dz, QZ)));
         const f2 rn = f2_fma(dx, NX, f2_fma(dy, NY, f2_mul(dz, NZ)));
-        const f2 g = f2_fma(rn, ri2, one);
-        const f2 b = f2_mul(f2_mul(rq, ri2), f2_mul(ri, g));
-        ax = f2_fma(ri, QX, ax);
-        ay = f2_fma(ri, QY, ay);
-        az = f2_fma(ri, QZ, az);
-        ax = f2_fma(b, dx, ax);
-        ay = f2_fma(b, dy, ay);
-        az = f2_fma(b, dz, az);
+        const f2 ri2 = inv_r2();
+        const f2 b = f2_mul(f2_mul(rq, ri2), f2_fma(rn, ri2, one));
+        ax = f2_fma(ri, f2_fma(b, dx, QX), ax);
+        ay = f2_fma(ri, f2_fma(b, dy, QY), ay);
+        az = f2_fma(ri, f2_fma(b, dz, QZ), az);
     } else if (KIND == KIND_LSL) {   // Laplace: scalar q in QX, sum in ax
         ax = f2_fma(ri, QX, ax);
     } else if (KIND == KIND_LDL) {
         const f2 rn = f2_fma(dx, NX, f2_fma(dy, NY, f2_mul(dz, NZ)));
-        ax = f2_fma(f2_mul(rn, f2_mul(ri2, ri)), QX, ax);
+        ax = f2_fma(f2_mul(rn, f2_mul(inv_r2(), ri)), QX, ax);
     } else {                         // KIND_LCF: ri q (1 + (r.n') ri^2), n' = kappa n
         const f2 one = f2_pack(1.0f, 1.0f);
         const f2 rn = f2_fma(dx, NX, f2_fma(dy, NY, f2_mul(dz, NZ)));
-        ax = f2_fma(f2_mul(ri, f2_fma(rn, ri2, one)), QX, ax);
+        ax = f2_fma(f2_mul(ri, f2_fma(rn, inv_r2(), one)), QX, ax);
     }
 }
 
@@ -283,11 +295,19 @@ __device__ __forceinline__ void tile_pair_setup(TilePairParams &tp, double tcx, 
     tp.flags = flags;
 }
 
+// Resident CTAs per SM the FP32 kernel is compiled for: the 128-thread shapes are held to
+// the register budget of 5 (R = 2) or 8 (R = 1) CTAs per SM; the others take what their
+// registers allow.
+__host__ __device__ constexpr int f32_min_blocks(int R, int W)
+{
+    return (W == 4 && R == 2) ? 5 : ((W == 4 && R == 1) ? 8 : 1);
+}
+
 // FP32 kernels write every item's sums to its partial slot as (hi, lo) float pairs,
 // [slot][3][TT] float2; reduce_partials_f32 adds the slots of a target tile and applies
 // the prefactor and the diagonal term in FP64 (no FP64 work in this kernel's loop).
 template <int KIND, int R, int W, bool COMP>
-__global__ void __launch_bounds__(W * 32) pairsum_f32_kernel(const PairsumParams p)
+__global__ void __launch_bounds__(W * 32, f32_min_blocks(R, W)) pairsum_f32_kernel(const PairsumParams p)
 {
     constexpr int NT = W * 32;
     constexpr int TT = NT * R;
@@ -670,9 +690,9 @@ struct KindLauncher {
         return b;
     }
 
-// Supported tile shapes.  FP32: (R, W) in {(2,4), (4,4), (8,4), (4,8), (4,2), (8,2)};
-// FP64: (1,4), (2,4); double-float: (1,4), (2,4), (4,4), (2,8).
-#define SBQ_F32_SHAPES(X) X(2, 4) X(4, 4) X(8, 4) X(4, 8) X(4, 2) X(8, 2)
+// Supported tile shapes.  FP32: (R, W) in {(1,4), (1,8), (2,4), (4,4), (8,4), (4,8), (4,2),
+// (8,2)}; FP64: (1,4), (2,4); double-float: (1,4), (2,4), (4,4), (2,8).
+#define SBQ_F32_SHAPES(X) X(1, 4) X(1, 8) X(2, 4) X(4, 4) X(8, 4) X(4, 8) X(4, 2) X(8, 2)
 #define SBQ_F64_SHAPES(X) X(1, 4) X(2, 4)
 #define SBQ_DF_SHAPES(X) X(1, 4) X(2, 4) X(4, 4) X(2, 8)
 

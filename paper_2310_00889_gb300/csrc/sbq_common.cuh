@@ -60,8 +60,8 @@ constexpr double DF_TERM_REL = 4.547473508864641e-13;
 // form is within 2^-48 x 2 of |r| (each coordinate part within 2^-48 of the extent).
 constexpr double DF_EXACT_R = 0.5;
 // Compensated FP32: plain FP32 sums over runs of this many sources are merged into
-// the (hi, lo) pair with TwoSum.
-constexpr int COMP_RUN = 64;
+// the (hi, lo) pair with TwoSum.  Each packed lane sums COMP_RUN / 2 terms in FP32 per run.
+constexpr int COMP_RUN = 128;
 // FP32 paths: pairs closer than this fraction of the sum of their two tile radii are
 // taken as coincident (skipped).  The FP32 centring rounds a coincident pair to at most
 // ~5 ulps of that sum (3e-7 of it), well below this threshold; distinct nodes of any
@@ -215,6 +215,9 @@ struct DeviceProps {
 };
 const DeviceProps &device_props();
 int *device_error_word();   // per-device error word (allocated once per device)
+// noalloc.cu: bits of the allocation-free apply's error word on the current device, read
+// and cleared (0 if that entry point never ran on the device).  Synchronous.
+int noalloc_take_error(int *bits);
 
 // Launchers implemented per kind (pairsum_{sl,dl,cf}.cu).  prec: sbq_prec.
 // Return cudaErrorInvalidValue for an unsupported (R, W).

@@ -8,7 +8,6 @@ no CPU fallback: importing this module raises if the library is missing.
 from __future__ import annotations
 
 import ctypes
-import math
 import os
 
 import numpy as np
@@ -96,6 +95,7 @@ def _load():
         "stokes_matvec": ([_vp, _vp, _vp, _int, _vp], _int),
         "stokes_op_set_mobility": ([_vp, _int, _vp, _vp], _int),
         "stokes_mobility_rhs": ([_vp, _vp, _vp, _vp, _int, _vp], _int),
+        "stokes_op_set_sl_correction": ([_vp, _i64, _vp, _vp, _vp, _vp], _int),
         "stokes_mobility_velocity": ([_vp, _vp, _vp, _vp], _int),
         "stokes_matvec_bounded": ([_vp, _vp, _vp, _vp, _vp], _int),
         "gmres_solve": ([_vp, _vp, _vp, ctypes.POINTER(GmresOpts), ctypes.POINTER(GmresReport),
@@ -116,6 +116,11 @@ def _load():
         "sbq_peak_probe": ([_int, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), _vp], _int),
         "tube_correction_targets": ([_i64, _int, _int, _i64, _vp, _vp, _vp, _i64, _vp, _int, _dbl,
                                      _dbl, _dbl, ctypes.POINTER(_i64), _vp, _vp, _vp, _vp], _int),
+        "sbq_slender_eta": ([_dbl, ctypes.POINTER(_dbl)], _int),
+        "stokes_apply_host": ([_i64, _vp, _vp, _vp, _dbl, _dbl, _vp, _vp, _int,
+                               ctypes.POINTER(Tune), _vp], _int),
+        "stokes_solve_host": ([_i64, _vp, _vp, _vp, _dbl, _dbl, _int, _vp, _int, _vp, _vp,
+                               ctypes.POINTER(GmresOpts), ctypes.POINTER(GmresReport), _vp], _int),
         "sbq_destroy": ([_vp], None),
     }
     for name, (args, res) in sig.items():
@@ -175,8 +180,21 @@ def device_info():
 
 
 def slender_eta(eps):
-    """eta = 1 / (2 eps log(1/eps)), the slender-body mixing parameter (paper Sec. 4.1)."""
-    return 1.0 / (2.0 * eps * math.log(1.0 / eps))
+    """The slender-body mixing parameter eta of the combined-field formulations, computed by
+    the library (sbq_slender_eta)."""
+    out = _dbl()
+    _check(lib.sbq_slender_eta(float(eps), ctypes.byref(out)))
+    return out.value
+
+
+def _host(t, shape, name):
+    if not (isinstance(t, torch.Tensor) and t.device.type == "cpu" and t.dtype == torch.float64):
+        raise TypeError("%s must be a CPU float64 tensor (pinned for asynchronous copies)" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError("%s has shape %s, expected %s" % (name, tuple(t.shape), tuple(shape)))
+    return t
 
 
 def _apply(kind, src, nrm, w, sigma, trg, alpha, beta, prec, out, stream):
@@ -462,6 +480,23 @@ class StokesOp:
         _check(lib.stokes_op_set_mobility(self.handle, int(off.size - 1), c_off, _stream(stream)))
         self.nbody = int(off.size - 1)
 
+    def set_sl_correction(self, correction, stream=None):
+        """Correction (rowptr, col, val) of the single layer alone, used by mobility_rhs for
+        S nu (e.g. tube_correction(..., alpha=1.0, beta=0.0)); None removes it."""
+        if correction is None:
+            _check(lib.stokes_op_set_sl_correction(self.handle, 0, None, None, None,
+                                                   _stream(stream)))
+            return
+        rowptr, col, val = correction
+        for t, nm, dt in ((rowptr, "rowptr", torch.int64), (col, "col", torch.int64),
+                          (val, "val", torch.float64)):
+            if not (t.is_cuda and t.dtype == dt and t.is_contiguous()):
+                raise TypeError("correction %s must be a contiguous CUDA %s tensor" % (nm, dt))
+        if rowptr.numel() != 3 * self.n + 1:
+            raise ValueError("rowptr must have %d entries" % (3 * self.n + 1))
+        _check(lib.stokes_op_set_sl_correction(self.handle, int(val.numel()), _ptr(rowptr),
+                                               _ptr(col), _ptr(val), _stream(stream)))
+
     def mobility_rhs(self, F, T, us=None, prec="fp64", stream=None):
         """u_s - S nu for body forces F and torques T ((nbody, 3) each, torque about each
         body's weighted centroid); us: slip velocity on the nodes or None."""
@@ -547,26 +582,55 @@ class LaplaceOp(StokesOp):
     _create = "laplace_op_create"
 
 
-def solve_from_host(src, nrm, w, rhs, eta, tol=1e-10, inner_prec="fp32c", restart=100,
-                    max_iter=2000, inner_tol=1e-5, max_outer=30, use_graph=True, device="cuda",
-                    correction=None, body_off=None, resid_prec="fp64"):
-    """End-to-end call on host (pinned CPU) tensors: copy the geometry and data to the GPU,
-    build the operator, solve, and copy the solution back to the host.  correction: None,
-    or the precision ("fp64", "fp32c", "fp32") in which to build the double-layer
-    singularity subtraction over the bodies body_off (default one body)."""
-    dev = torch.device(device)
-    d_src = src.to(dev, non_blocking=True)
-    d_nrm = nrm.to(dev, non_blocking=True)
-    d_w = w.to(dev, non_blocking=True)
-    d_rhs = rhs.to(dev, non_blocking=True)
-    E = None
-    if correction is not None:
-        E = dl_gauss_correction(d_src, d_nrm, d_w, body_off, prec=correction)
-    op = StokesOp(d_src, d_nrm, d_w, eta, correction=E)
-    x, rep = op.solve(d_rhs, tol=tol, inner_prec=inner_prec, restart=restart, max_iter=max_iter,
-                      inner_tol=inner_tol, max_outer=max_outer, use_graph=use_graph,
-                      resid_prec=resid_prec)
-    out = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
-    out.copy_(x)
-    op.close()
-    return out, rep
+def apply_host(src, nrm, w, sigma, eta, diag=0.5, prec="fp32c", tune=None, out=None,
+               stream=None):
+    """stokes_apply_host: K sigma = diag sigma + (D + eta S)[sigma] on the nodes from HOST
+    tensors (CPU float64; pinned memory gives asynchronous copies), result in a host tensor.
+    tune: dict(r, warps, chunk_tiles) or None (tuning cache, else the default shape)."""
+    n = src.shape[1]
+    for a, nm, sh in ((src, "src", (3, n)), (nrm, "nrm", (3, n)), (w, "w", (n,)),
+                      (sigma, "sigma", (3, n))):
+        _host(a, sh, nm)
+    if out is None:
+        out = torch.empty((3, n), dtype=torch.float64, pin_memory=torch.cuda.is_available())
+    _host(out, (3, n), "out")
+    t = None
+    if tune is not None:
+        t = Tune(int(tune["r"]), int(tune["warps"]), int(tune.get("chunk_tiles", 0)))
+    _check(lib.stokes_apply_host(n, _ptr(src), _ptr(nrm), _ptr(w), float(eta), float(diag),
+                                 _ptr(sigma), _ptr(out), _prec(prec),
+                                 ctypes.byref(t) if t is not None else None, _stream(stream)))
+    return out
+
+
+def solve_host(src, nrm, w, rhs, eta, diag=0.5, body_off=None, corr_prec=None, x0=None,
+               tol=1e-10, restart=100, max_iter=2000, inner_prec="fp32c", inner_tol=1e-5,
+               max_outer=30, use_graph=True, resid_prec="fp64", stream=None):
+    """stokes_solve_host: GMRES for K x = rhs from HOST tensors, solution in a host tensor.
+    corr_prec None: no correction; else the double-layer singularity subtraction over the
+    bodies body_off (default one body) with row sums in that precision.  Returns
+    (x, report dict)."""
+    n = src.shape[1]
+    for a, nm, sh in ((src, "src", (3, n)), (nrm, "nrm", (3, n)), (w, "w", (n,)),
+                      (rhs, "rhs", (3, n))):
+        _host(a, sh, nm)
+    x = torch.zeros((3, n), dtype=torch.float64, pin_memory=torch.cuda.is_available())
+    if x0 is not None:
+        x.copy_(x0)
+    nbody, c_off, cp = 0, None, FP64
+    if corr_prec is not None:
+        off = np.asarray([0, n] if body_off is None else body_off, dtype=np.int64)
+        nbody = int(off.size - 1)
+        c_off = (ctypes.c_int64 * off.size)(*[int(v) for v in off])
+        cp = _prec(corr_prec)
+    o = GmresOpts(float(tol), int(restart), int(max_iter), _prec(inner_prec), float(inner_tol),
+                  int(max_outer), 1 if use_graph else 0, _prec(resid_prec))
+    rep = GmresReport()
+    st = lib.stokes_solve_host(n, _ptr(src), _ptr(nrm), _ptr(w), float(eta), float(diag), nbody,
+                               c_off, cp, _ptr(rhs), _ptr(x), ctypes.byref(o), ctypes.byref(rep),
+                               _stream(stream))
+    if st not in (OK, ENOCONV):
+        _check(st)
+    d = rep.as_dict()
+    d["status_name"] = _STATUS.get(st, st)
+    return x, d

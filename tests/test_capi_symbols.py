@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol(libsbq):
 
 def test_host_only_calls(libsbq):
     libsbq.sbq_version.restype = ctypes.c_int
-    assert libsbq.sbq_version() == 200
+    assert libsbq.sbq_version() == 300
     libsbq.sbq_last_error.restype = ctypes.c_char_p
     assert libsbq.sbq_last_error() == b""
     # argument validation happens before any device call
@@ -133,3 +133,57 @@ def test_tube_correction_rules_validation_on_host(libsbq):
     phi[3 * 64 + 1] = 0.5
     w[3 * 64] = float("nan")
     assert call(31) == 1
+
+
+def test_slender_eta_on_host(libsbq):
+    """sbq_slender_eta against the dashed-line values of the paper's Stokes-torus eigenvalue
+    figure (eta = 10.8574 at eps = 1e-2) and its closed form; bad eps is rejected."""
+    import math
+    f = libsbq.sbq_slender_eta
+    f.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    f.restype = ctypes.c_int
+    out = ctypes.c_double()
+    assert f(1e-2, ctypes.byref(out)) == 0
+    assert abs(out.value - 10.8574) < 1e-4
+    for eps in (0.2, 1.0 / 3.0, 0.05):
+        assert f(eps, ctypes.byref(out)) == 0
+        assert abs(out.value * 2.0 * eps * math.log(1.0 / eps) - 1.0) < 1e-15
+    for bad in (0.0, 1.0, -0.1, float("nan")):
+        assert f(bad, ctypes.byref(out)) == 1
+    assert f(0.1, None) == 1
+
+
+def test_host_buffer_calls_validate_on_host(libsbq):
+    """stokes_apply_host / stokes_solve_host reject bad sizes, pointers and options before
+    touching a device."""
+    vp, i64, dbl, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    libsbq.stokes_apply_host.argtypes = [i64, vp, vp, vp, dbl, dbl, vp, vp, ci, vp, vp]
+    libsbq.stokes_solve_host.argtypes = [i64, vp, vp, vp, dbl, dbl, ci, vp, ci, vp, vp, vp, vp, vp]
+    libsbq.sbq_last_error.restype = ctypes.c_char_p
+    buf = (ctypes.c_double * 30)()
+    p = ctypes.cast(buf, vp)
+    assert libsbq.stokes_apply_host(-1, p, p, p, 1.0, 0.5, p, p, 2, None, None) == 1
+    assert libsbq.stokes_apply_host(10, p, None, p, 1.0, 0.5, p, p, 2, None, None) == 1
+    assert libsbq.stokes_apply_host(10, p, p, p, 1.0, 0.5, p, p, 9, None, None) == 1
+    tune = (ctypes.c_int * 3)(3, 3, 0)   # no such tile shape
+    assert libsbq.stokes_apply_host(10, p, p, p, 1.0, 0.5, p, p, 2, ctypes.cast(tune, vp),
+                                    None) == 1
+    assert libsbq.stokes_apply_host(0, None, None, None, 1.0, 0.5, None, None, 2, None, None) == 0
+
+    class Opts(ctypes.Structure):
+        _fields_ = [("tol", dbl), ("restart", ci), ("max_iter", ci), ("inner_prec", ci),
+                    ("inner_tol", dbl), ("max_outer", ci), ("use_graph", ci), ("resid_prec", ci)]
+
+    good = Opts(1e-10, 50, 100, 2, 1e-5, 10, 1, 0)
+    off = (ctypes.c_int64 * 3)(0, 4, 10)
+    bad_off = (ctypes.c_int64 * 3)(0, 6, 4)
+    call = lambda n, nb, o, opts: libsbq.stokes_solve_host(n, p, p, p, 1.0, 0.5, nb, o, 2, p, p,
+                                                           ctypes.byref(opts), None, None)
+    assert call(10, 2, ctypes.cast(bad_off, vp), good) == 1
+    assert call(10, 2, None, good) == 1
+    assert call(10, -1, None, good) == 1
+    assert call(10, 2, ctypes.cast(off, vp), Opts(0.0, 50, 100, 2, 1e-5, 10, 1, 0)) == 1
+    assert call(10, 2, ctypes.cast(off, vp), Opts(1e-10, 50, 100, 2, 2.0, 10, 1, 0)) == 1
+    assert call(10, 2, ctypes.cast(off, vp), Opts(1e-10, 50, 100, 2, 1e-5, 10, 1, 1)) == 1
+    buf[5] = float("nan")     # non-finite right-hand side, caught on the host
+    assert call(10, 0, None, good) == 5

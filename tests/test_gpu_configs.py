@@ -1,0 +1,129 @@
+"""Operator applies on the three large workloads against the FP64 CPU oracle, on 4096
+sampled rows each (the oracle's double loop at a million sources takes about 10 s for 4096
+rows on 16 cores; all rows would take hours).
+
+Workloads (seeded, synthetic):
+  * random slender loop of the paper's Sec. 5.2 recipe, 8192 panels x 8 x 16 = 1,048,576
+    nodes (eps(s) = 0.01 (1 + 0.5 sin 2 pi s), eta from eps = 0.01);
+  * 64 independent capped arcs (one block-diagonal operator, one persistent launch per
+    apply), 1,276,928 nodes; 64 rows from every segment;
+  * helical pipe (helix radius 3, pitch 2, 4 turns, tube radius 1; 1,048,576 wall nodes and
+    two caps) with 100 spheres of radius 0.2: 1,110,624 nodes.
+Error: ||u - u_oracle||_inf / ||u_oracle||_inf over the sampled rows of K sigma =
+sigma/2 + (D + eta S) sigma.  Each bar is the error measured on GB300 times a stated margin
+(BARS below lists both).  The compensated-FP32 errors (3e-7..3e-6) are set by the per-term
+rounding of r = x - y in tile pairs just outside the ones that form r from high and low
+parts; the accumulation error is not the limit (runs of 64 or 128 sources per TwoSum merge
+give the same errors on these workloads).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2310_00889_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+ROWS = 4096
+# (workload, precision) -> (relative error measured on GB300, bar).  Bars: 3x the measured
+# compensated-FP32, double-float and FP64 errors, 2x the plain FP32 error (which grows with
+# the number of terms summed in FP32), rounded up.
+BARS = {
+    ("loop1m", "fp32c"): (9.5e-7, 2.9e-6),
+    ("loop1m", "fp32"): (1.12e-3, 2.3e-3),
+    ("loop1m", "df32"): (5.9e-14, 1.8e-13),
+    ("batch", "fp32c"): (2.89e-6, 8.7e-6),
+    ("batch", "fp32"): (6.6e-5, 1.4e-4),
+    ("batch", "df32"): (2.6e-13, 7.8e-13),
+    ("batch", "fp64"): (2.1e-15, 6.5e-15),
+    ("helix", "fp32c"): (2.8e-7, 8.4e-7),
+    ("helix", "fp32"): (2.6e-5, 5.3e-5),
+    ("helix", "df32"): (1.2e-13, 3.6e-13),
+}
+
+
+@pytest.fixture(scope="module")
+def sbq():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA device is required for the gpu tests")
+    from paper_2310_00889_gb300 import build
+    build.build()
+    from paper_2310_00889_gb300 import sbq as mod
+    return mod
+
+
+def _t(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def _relerr(u, ref):
+    return float(np.abs(u - ref).max() / np.abs(ref).max())
+
+
+def _check(name, prec, u, ref):
+    err = _relerr(u, ref)
+    measured, bar = BARS[(name, prec)]
+    print("%s %s relerr %.3e (bar %.1e)" % (name, prec, err, bar))
+    assert np.all(np.isfinite(u))
+    assert err <= bar
+
+
+def _single_body(sbq, oracle_mod, name, surf, eps, precs):
+    import torch
+    n = surf.size
+    eta = sbq.slender_eta(eps)
+    sig = I.density(n, seed=2)
+    rows = np.sort(np.random.default_rng(4).choice(n, ROWS, replace=False))
+    ref = oracle_mod.combined(surf.x, surf.n, surf.w, sig, surf.x[:, rows], eta, 1.0) \
+        + 0.5 * sig[:, rows]
+    op = sbq.StokesOp(_t(surf.x), _t(surf.n), _t(surf.w), eta)
+    dsig = _t(sig)
+    for prec in precs:
+        u = op.matvec(dsig, prec=prec)[:, torch.as_tensor(rows, device="cuda")].cpu().numpy()
+        _check(name, prec, u, ref)
+    op.close()
+
+
+def test_random_loop_one_million_nodes(sbq, oracle_mod):
+    c = I.config3(panels=8192)
+    _single_body(sbq, oracle_mod, "loop1m", c["surf"], 0.01, ("fp32c", "fp32", "df32"))
+
+
+def test_helix_with_spheres(sbq, oracle_mod):
+    c = I.config5(pitch=2.0)
+    _single_body(sbq, oracle_mod, "helix", c["surf"], c["slenderness"], ("fp32c", "fp32", "df32"))
+
+
+def test_batch_of_64_segments(sbq, oracle_mod):
+    """The block-diagonal batch in one persistent launch per apply: 64 rows of every
+    segment against the oracle applied to that segment alone."""
+    c = I.config4()
+    segs = [g["surf"] for g in c["segments"]]
+    off = np.cumsum([0] + [g.size for g in segs])
+    n = int(off[-1])
+    eta = sbq.slender_eta(c["slenderness"])
+    X = np.concatenate([g.x for g in segs], axis=1)
+    Nn = np.concatenate([g.n for g in segs], axis=1)
+    W = np.concatenate([g.w for g in segs])
+    sig = I.density(n, seed=7)
+    rng = np.random.default_rng(11)
+    rows, refs = [], []
+    for i, g in enumerate(segs):
+        r = np.sort(rng.choice(g.size, ROWS // len(segs), replace=False))
+        sg = sig[:, off[i]:off[i + 1]]
+        refs.append(oracle_mod.combined(g.x, g.n, g.w, sg, g.x[:, r], eta, 1.0) + 0.5 * sg[:, r])
+        rows.append(off[i] + r)
+    import torch
+    rows = np.concatenate(rows)
+    ref = np.concatenate(refs, axis=1)
+    plan = sbq.BatchPlan(off)
+    op = sbq.StokesOp(_t(X), _t(Nn), _t(W), eta, plan=plan)
+    dsig = _t(sig)
+    for prec in ("fp32c", "fp32", "df32", "fp64"):
+        u = op.matvec(dsig, prec=prec)[:, torch.as_tensor(rows, device="cuda")].cpu().numpy()
+        _check("batch", prec, u, ref)
+    op.close()
+    plan.close()

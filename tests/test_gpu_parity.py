@@ -5,9 +5,11 @@ components (all errors in the paper are relative).  Bars:
   * FP64 paths: 1e-10;
   * double-float paths (FP64-class results from FP32 arithmetic): TOL_DF = 1e-11, below the
     FP64 bar (per pair a few 2^-46 of the term, against about 2^-52 for FP64);
-  * FP32 and compensated FP32 paths: TOL_F32 below, a bound measured on GB300 (the
-    FP32 unit roundoff is 6e-8; per-term rounding of r = x - y near the surface and the
-    cancellation in the sum put the observed errors at 1e-7..1e-6).
+  * FP32 and compensated FP32 paths: per case, from the error measured on GB300 (MEASURED
+    below, the largest over the kinds and shapes the case runs): the bar is 3x the measured
+    compensated-FP32 error and 2x the measured plain-FP32 error (rounded up to two digits).
+    The compensated error is the per-term rounding of r = x - y and of the products
+    (1e-7..5e-7 here); the plain FP32 error adds the FP32 accumulation over the sources.
 """
 import math
 
@@ -20,11 +22,42 @@ pytestmark = pytest.mark.gpu
 
 TOL_F64 = 1e-10
 TOL_DF = 1e-11
-TOL_F32 = {"fp32": 2e-5, "fp32c": 2e-5}
+
+# (case, prec) -> relative error measured on GB300 (compensated runs of 128 sources)
+MEASURED = {
+    ("apply_config1_sl", "fp32c"): 2.10e-7, ("apply_config1_sl", "fp32"): 7.8e-7,
+    ("apply_config1_dl", "fp32c"): 5.9e-8, ("apply_config1_dl", "fp32"): 4.8e-6,
+    ("apply_config1_cf", "fp32c"): 6.7e-8, ("apply_config1_cf", "fp32"): 4.9e-6,
+    ("apply_ragged_sl", "fp32c"): 2.1e-7, ("apply_ragged_sl", "fp32"): 1.3e-6,
+    ("apply_ragged_dl", "fp32c"): 3.5e-7, ("apply_ragged_dl", "fp32"): 9.0e-6,
+    ("apply_ragged_cf", "fp32c"): 4.0e-7, ("apply_ragged_cf", "fp32"): 9.3e-6,
+    ("sizes_tails", "fp32c"): 3.8e-7,
+    ("misaligned", "fp32c"): 3.6e-7, ("misaligned", "fp32"): 5.9e-6,
+    ("small_operator", "fp32c"): 1.94e-7, ("small_operator", "fp32"): 2.06e-6,
+    ("config2_sampled", "fp32c"): 4.6e-7, ("config2_sampled", "fp32"): 8.2e-6,
+    ("random_loop", "fp32c"): 2.9e-7, ("random_loop", "fp32"): 6.1e-5,
+    ("gauss_correction", "fp32c"): 4.1e-7, ("gauss_correction", "fp32"): 6.4e-6,
+    ("gauss_operator", "fp32c"): 2.3e-7,
+    ("shuffled", "fp32c"): 1.23e-7,
+    ("laplace_config1", "fp32c"): 4.8e-7, ("laplace_config1", "fp32"): 6.2e-6,
+    ("laplace_ragged", "fp32c"): 4.1e-7, ("laplace_ragged", "fp32"): 8.9e-6,
+    ("laplace_operator", "fp32c"): 1.8e-8,
+    ("mobility_operator", "fp32c"): 6.9e-8,
+}
+
+
+def _bar(case, prec):
+    """Bar of a reduced-precision case: 3x (compensated) or 2x (plain) its measured error."""
+    if prec == "fp64":
+        return TOL_F64
+    if prec == "df32":
+        return TOL_DF
+    m = MEASURED[(case, prec)]
+    return float("%.2g" % ((3.0 if prec == "fp32c" else 2.0) * m))
 
 
 def _tol(prec):
-    return {"fp64": TOL_F64, "df32": TOL_DF}.get(prec) or TOL_F32[prec]
+    return {"fp64": TOL_F64, "df32": TOL_DF}[prec]
 
 
 @pytest.fixture(scope="module")
@@ -96,9 +129,8 @@ def test_apply_parity(sbq, oracle_mod, case, kind, prec):
     ref = _oracle(oracle_mod, kind, src, nrm, w, sig, trg)
     assert np.all(np.isfinite(u))
     err = _relerr(u, ref)
-    tol = _tol(prec)
     print("apply %s %s %s relerr %.3e" % (case, kind, prec, err))
-    assert err <= tol
+    assert err <= _bar("apply_%s_%s" % (case, kind), prec)
 
 
 @pytest.mark.parametrize("ns,nt", [(1, 1), (1, 300), (255, 1), (256, 256), (257, 513),
@@ -114,8 +146,9 @@ def test_apply_sizes_and_tails(sbq, oracle_mod, ns, nt, prec):
     trg = rng.standard_normal((3, nt)) * 1.5
     u = _apply(sbq, "cf", src, nrm, w, sig, trg, prec, 0.7, 1.0)
     ref = _oracle(oracle_mod, "cf", src, nrm, w, sig, trg, 0.7, 1.0)
-    tol = 1e-4 if prec == "fp32c" else _tol(prec)
-    assert _relerr(u, ref) <= tol
+    err = _relerr(u, ref)
+    print("sizes %d %d %s relerr %.3e" % (ns, nt, prec, err))
+    assert err <= _bar("sizes_tails", prec)
 
 
 @pytest.mark.parametrize("kind", ["sl", "dl", "cf"])
@@ -133,14 +166,15 @@ def test_coincident_targets_in_misaligned_tiles(sbq, oracle_mod, kind, prec):
         assert np.all(np.isfinite(u))
         err = _relerr(u, ref)
         print("misaligned %s %s relerr %.3e" % (kind, prec, err))
-        assert err <= _tol(prec)
+        assert err <= _bar("misaligned", prec)
 
 
-_SHAPES = {"fp32": {(2, 4), (4, 4), (8, 4), (4, 8), (4, 2), (8, 2)},
+_SHAPES = {"fp32": {(1, 4), (1, 8), (2, 4), (4, 4), (8, 4), (4, 8), (4, 2), (8, 2)},
            "fp64": {(1, 4), (2, 4)}, "df32": {(1, 4), (2, 4), (4, 4), (2, 8)}}
 
 
-@pytest.mark.parametrize("shape", [(2, 4), (4, 4), (8, 4), (4, 8), (4, 2), (8, 2), (1, 4), (2, 8)])
+@pytest.mark.parametrize("shape", [(2, 4), (4, 4), (8, 4), (4, 8), (4, 2), (8, 2), (1, 4), (2, 8),
+                                   (1, 8)])
 @pytest.mark.parametrize("chunk", [0, 3])
 def test_operator_matvec_every_tile_shape(sbq, oracle_mod, shape, chunk):
     """Each supported tile shape (targets per CTA 256..1024, tiles not aligned with the
@@ -156,7 +190,7 @@ def test_operator_matvec_every_tile_shape(sbq, oracle_mod, shape, chunk):
         out = _np(op.matvec(_t(sig), prec=prec))
         err = _relerr(out, ref)
         print("shape %s chunk %d %s relerr %.3e" % (shape, chunk, prec, err))
-        assert err <= _tol(prec)
+        assert err <= _bar("small_operator", prec)
     op.close()
 
 
@@ -221,7 +255,7 @@ def test_operator_matvec_parity(sbq, oracle_mod, prec, with_csr):
     ref = oracle_mod.matvec(s.x, s.n, s.w, eta, sig, 0.5, E)
     err = _relerr(out, ref)
     print("matvec %s csr=%s relerr %.3e tune %s" % (prec, with_csr, err, op.tune(prec)))
-    assert err <= _tol(prec)
+    assert err <= _bar("small_operator", prec)
     st = op.stats(prec)
     assert st["pairs_per_matvec"] == float(s.size) ** 2
     op.close()
@@ -252,6 +286,25 @@ def small_solve(sbq, oracle_mod):
     return s, rhs, eta, x_ref.reshape(3, -1)
 
 
+@pytest.fixture(scope="module")
+def small_solve_K(oracle_mod, small_solve):
+    """The dense K of small_solve (3072 x 3072, from the oracle) and its smallest singular
+    value and condition number."""
+    s, rhs, eta, x_ref = small_solve
+    K = oracle_mod.dense_operator(s.x, s.n, s.w, s.x, eta, 1.0) + 0.5 * np.eye(3 * s.size)
+    sv = np.linalg.svd(K, compute_uv=False)
+    return K, sv[-1], sv[0] / sv[-1]
+
+
+def _solution_bound(small_solve_K, rhs, x, x_ref):
+    """A posteriori bound on ||x - x_ref||_2 / ||x_ref||_2 for two approximate solutions of
+    K x = rhs: (||r(x)||_2 + ||r(x_ref)||_2) / (sigma_min(K) ||x_ref||_2), residuals formed
+    with the oracle's dense K."""
+    K, smin, _ = small_solve_K
+    res = lambda v: np.linalg.norm(rhs.reshape(-1) - K @ v.reshape(-1))
+    return (res(x) + res(x_ref)) / (smin * np.linalg.norm(x_ref))
+
+
 @pytest.mark.parametrize("use_graph", [True, False])
 @pytest.mark.parametrize("prec", ["fp64", "df32"])
 def test_gmres_fp64_matches_oracle(sbq, oracle_mod, small_solve, use_graph, prec):
@@ -270,7 +323,8 @@ def test_gmres_fp64_matches_oracle(sbq, oracle_mod, small_solve, use_graph, prec
 
 
 @pytest.mark.parametrize("inner,resid", [("fp32c", "fp64"), ("fp32", "fp64"), ("fp32c", "df32")])
-def test_gmres_mixed_refinement_reaches_fp64_tolerance(sbq, oracle_mod, small_solve, inner, resid):
+def test_gmres_mixed_refinement_reaches_fp64_tolerance(sbq, oracle_mod, small_solve, small_solve_K,
+                                                      inner, resid):
     s, rhs, eta, x_ref = small_solve
     op = sbq.StokesOp(_t(s.x), _t(s.n), _t(s.w), eta)
     x, rep = op.solve(_t(rhs), tol=1e-10, restart=100, inner_prec=inner, inner_tol=1e-5,
@@ -280,11 +334,16 @@ def test_gmres_mixed_refinement_reaches_fp64_tolerance(sbq, oracle_mod, small_so
     assert rep["status"] == 0 and rep["rel_res"] <= 1e-10
     assert rep["matvecs_low"] > rep["matvecs_fp64"]
     # the oracle's FP64 residual of the returned x meets the tolerance; x itself agrees with
-    # the oracle's solution to within the conditioning of K times the tolerance
+    # the oracle's solution within the a posteriori bound that the residuals and the
+    # smallest singular value of K give
     xs = _np(x)
     kx = oracle_mod.matvec(s.x, s.n, s.w, eta, xs)
     assert np.linalg.norm(rhs - kx) / np.linalg.norm(rhs) <= 1.05e-10
-    assert _relerr(xs, x_ref) <= 1e-6
+    bound = _solution_bound(small_solve_K, rhs, xs, x_ref)
+    err = float(np.linalg.norm(xs - x_ref) / np.linalg.norm(x_ref))
+    print("mixed %s/%s: x error %.3e, bound %.3e (sigma_min %.3e, cond %.3e)"
+          % (inner, resid, err, bound, small_solve_K[1], small_solve_K[2]))
+    assert err <= bound
     op.close()
 
 
@@ -359,7 +418,7 @@ def test_config2_full_size_sampled_rows(sbq, oracle_mod, prec):
     ref = oracle_mod.combined(s.x, s.n, s.w, sig, s.x[:, rows], eta, 1.0) + 0.5 * sig[:, rows]
     err = _relerr(out[:, rows], ref)
     print("config2 sampled %s relerr %.3e tune %s" % (prec, err, op.tune(prec)))
-    assert err <= _tol(prec)
+    assert err <= _bar("config2_sampled", prec)
     op.close()
 
 
@@ -464,7 +523,8 @@ def test_compensation_helps_on_a_random_loop(sbq, oracle_mod):
     e = {p: _relerr(_np(op.matvec(_t(sig), prec=p)), ref) for p in ("fp32", "fp32c", "fp64")}
     print("random loop errors", e)
     assert e["fp64"] <= TOL_F64
-    assert e["fp32c"] <= TOL_F32["fp32c"] and e["fp32c"] <= e["fp32"] and e["fp32"] <= 5e-4
+    assert e["fp32c"] <= _bar("random_loop", "fp32c") and e["fp32c"] <= e["fp32"]
+    assert e["fp32"] <= _bar("random_loop", "fp32")
     op.close()
 
 
@@ -496,7 +556,7 @@ def test_gauss_correction_matches_oracle(sbq, oracle_mod, prec):
     assert np.array_equal(_np(col), ref.col)
     err = np.abs(_np(val) - ref.val).max() / np.abs(ref.val).max()
     print("gauss correction", prec, err)
-    assert err <= _tol(prec)
+    assert err <= _bar("gauss_correction", prec)
 
 
 def test_gauss_correction_operator_and_solve(sbq, oracle_mod):
@@ -511,7 +571,9 @@ def test_gauss_correction_operator_and_solve(sbq, oracle_mod):
     sig = I.density(s.size, seed=31)
     ref = oracle_mod.matvec(s.x, s.n, s.w, eta, sig, E=E)
     assert _relerr(_np(op.matvec(_t(sig), prec="fp64")), ref) <= TOL_F64
-    assert _relerr(_np(op.matvec(_t(sig), prec="fp32c")), ref) <= TOL_F32["fp32c"]
+    err = _relerr(_np(op.matvec(_t(sig), prec="fp32c")), ref)
+    print("gauss operator fp32c relerr %.3e" % err)
+    assert err <= _bar("gauss_operator", "fp32c")
     b = I.density(s.size, seed=32)
     for inner in ("fp64", "fp32c"):
         x, rep = op.solve(_t(b), tol=1e-10, restart=100, inner_prec=inner)
@@ -633,7 +695,7 @@ def test_node_order_is_invisible(sbq, prec):
     ub = _np(b.matvec(_t(sig[:, p]), prec=prec))
     err = _relerr(ub, ua[:, p])
     print("shuffled %s relerr %.3e" % (prec, err))
-    assert err <= {"fp64": 1e-13, "df32": 1e-11, "fp32c": 2e-6}[prec]
+    assert err <= {"fp64": 1e-13, "df32": 1e-11, "fp32c": _bar("shuffled", "fp32c")}[prec]
     a.close()
     b.close()
 
@@ -667,20 +729,39 @@ def test_batch_with_empty_segment(sbq, oracle_mod):
     op.close()
 
 
-def test_solve_from_host_with_correction(sbq, oracle_mod):
-    """End-to-end call from pinned host tensors (copies, correction, operator, solve, copy
-    back): the returned x meets the tolerance against the oracle operator."""
+def test_solve_host_with_correction(sbq, oracle_mod):
+    """End-to-end C-ABI call on pinned host buffers (stokes_solve_host: copies, correction,
+    operator, solve, copy back): the returned x meets the tolerance against the oracle
+    operator."""
     import torch
     c = I.config2(panels=2, nth=32, nr=8)
     s = c["surf"]
     eta = sbq.slender_eta(0.2)
     h = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
-    x, rep = sbq.solve_from_host(h(s.x), h(s.n), h(s.w), h(c["rhs"]), eta, tol=1e-10,
-                                 correction="df32", resid_prec="df32")
+    x, rep = sbq.solve_host(h(s.x), h(s.n), h(s.w), h(c["rhs"]), eta, tol=1e-10,
+                            corr_prec="df32", resid_prec="df32")
     assert not x.is_cuda and rep["status"] == 0
     E = oracle_mod.dl_gauss_correction(s.x, s.n, s.w)
     r = c["rhs"] - oracle_mod.matvec(s.x, s.n, s.w, eta, x.numpy(), E=E)
     assert np.linalg.norm(r) / np.linalg.norm(c["rhs"]) <= 1.05e-10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_apply_host_matches_oracle(sbq, oracle_mod, prec):
+    """stokes_apply_host (geometry, density and result in pinned host buffers) against the
+    oracle's K sigma = sigma/2 + (D + eta S) sigma on the curved pipe of 4,608 nodes."""
+    import torch
+    c = I.config2(panels=8)
+    s = c["surf"]
+    eta = sbq.slender_eta(0.2)
+    sig = I.density(s.size, seed=31)
+    h = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
+    out = sbq.apply_host(h(s.x), h(s.n), h(s.w), h(sig), eta, prec=prec)
+    assert not out.is_cuda
+    ref = oracle_mod.matvec(s.x, s.n, s.w, eta, sig)
+    err = _relerr(out.numpy(), ref)
+    print("apply_host %s relerr %.3e" % (prec, err))
+    assert err <= (TOL_F64 if prec == "fp64" else 1e-6)
 
 
 # ---------------------------------------------------------------------------
@@ -707,7 +788,7 @@ def test_laplace_apply_parity(sbq, oracle_mod, case, kind, prec):
     assert u.shape == ref.shape and np.all(np.isfinite(u))
     err = _relerr(u, ref)
     print("laplace %s %s %s relerr %.3e" % (case, kind, prec, err))
-    assert err <= _tol(prec)
+    assert err <= _bar("laplace_%s" % case, prec)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "df32"])
@@ -743,7 +824,7 @@ def test_laplace_operator_matvec_parity(sbq, oracle_mod, prec):
     assert out.shape == (t.size,)
     err = _relerr(out, ref)
     print("laplace op %s relerr %.3e" % (prec, err))
-    assert err <= _tol(prec)
+    assert err <= _bar("laplace_operator", prec)
     op.close()
 
 
@@ -818,7 +899,7 @@ def test_mobility_operator_matvec_parity(sbq, oracle_mod):
     for prec in ("fp64", "df32", "fp32c"):
         err = _relerr(_np(op.matvec(_t(sig), prec=prec)), ref)
         print("mobility matvec %s relerr %.3e" % (prec, err))
-        assert err <= _tol(prec)
+        assert err <= _bar("mobility_operator", prec)
     op.close()
 
 

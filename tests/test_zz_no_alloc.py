@@ -1,12 +1,16 @@
-"""The allocation-free single-layer apply agrees with the regular one, call after call.
+"""The allocation-free single-layer apply, called twice in a row, against the regular one and
+against the FP64 oracle.
 
 stokes_sl_apply_noalloc serves callers that cannot allocate GPU memory at the moment they
-need the sum (fixed memory budgets, pools reserved at start-up, loops that must not enter
-an allocator).  It keeps its scratch in one fixed array inside the library instead of
-taking it from the stream-ordered pool as stokes_sl_apply does.  These tests call both
-entry points through the C ABI on the same inputs, several calls in a row with inputs of
-different sizes in between (the shared array keeps the previous call's contents), and
-compare the outputs within the tolerances the parity tests use.
+need the sum: code under a fixed memory budget or a pool reserved at start-up, real-time
+loops that must not enter an allocator, hosts that forbid cudaMalloc after initialisation.
+It keeps its scratch in one fixed array inside the library instead of taking it from the
+stream-ordered pool as stokes_sl_apply does.  These tests call both entry points through the
+C ABI on the same inputs, several calls in a row with inputs of different sizes in between
+(the shared array keeps the previous call's contents), and compare the outputs with each
+other and with the oracle within the bars the parity tests use (3x the compensated-FP32
+error and 2x the plain-FP32 error measured on GB300 for the single layer); the largest
+problem the fixed array admits (131072 sources and targets) runs as well.
 
 The file name makes pytest collect it last.
 """
@@ -19,8 +23,15 @@ from paper_2310_00889_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-10, "fp32": 2e-5, "fp32c": 2e-5}
 PREC = {"fp64": 0, "fp32": 1, "fp32c": 2}
+# measured single-layer errors against the oracle on these cases (GB300), per precision
+MEASURED = {"fp32c": 2.1e-7, "fp32": 4.7e-6}
+
+
+def _bar(prec):
+    if prec == "fp64":
+        return 1e-10
+    return (3.0 if prec == "fp32c" else 2.0) * MEASURED[prec]
 
 
 @pytest.fixture(scope="module")
@@ -51,7 +62,7 @@ def _run(lib, fn, src, w, sig, trg, prec):
     st = getattr(lib, fn)(src.shape[1], p(src), p(w), p(sig), trg.shape[1], p(trg), p(out),
                           PREC[prec], stream)
     assert st == 0, lib.sbq_last_error()
-    torch.cuda.synchronize()
+    assert lib.sbq_check_device(stream) == 0, lib.sbq_last_error()
     return out.cpu().numpy()
 
 
@@ -64,20 +75,47 @@ def _cases():
     return [(s1.x, s1.w, c1["sigma"], c1["trg"]), (s2.x, s2.w, sig2, s2.x[:, ::3])]
 
 
+def _relerr(u, ref):
+    return float(np.abs(u - ref).max() / np.abs(ref).max())
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32c", "fp32"])
-def test_noalloc_matches_regular_apply_on_consecutive_calls(lib, prec):
-    cases = [tuple(_t(a) for a in case) for case in _cases()]
+def test_noalloc_matches_regular_apply_and_oracle_on_consecutive_calls(lib, oracle_mod, prec):
+    host = _cases()
+    refs = [oracle_mod.sl(src, w, sig, trg) for src, w, sig, trg in host]
+    cases = [tuple(_t(a) for a in case) for case in host]
     first = None
     for k, (src, w, sig, trg) in enumerate(cases + cases[:1]):
-        ref = _run(lib, "stokes_sl_apply", src, w, sig, trg, prec)
+        ref_oracle = refs[k % len(cases)]
+        regular = _run(lib, "stokes_sl_apply", src, w, sig, trg, prec)
         got = _run(lib, "stokes_sl_apply_noalloc", src, w, sig, trg, prec)
         assert np.all(np.isfinite(got))
-        err = float(np.abs(got - ref).max() / np.abs(ref).max())
-        assert err <= TOL[prec], (k, err)
+        e_reg = _relerr(got, regular)
+        e_orc = _relerr(got, ref_oracle)
+        print("noalloc call %d %s: vs regular %.3e, vs oracle %.3e" % (k, prec, e_reg, e_orc))
+        assert e_reg <= _bar(prec), (k, e_reg)
+        assert e_orc <= _bar(prec), (k, e_orc)
         if k == 0:
             first = got
     # the third call repeats the first inputs after a larger call: same bits
     assert np.array_equal(got, first)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_noalloc_at_its_maximum_size(lib, oracle_mod, prec):
+    """131072 sources and 131072 targets (the limit of the fixed array): status 0, no device
+    error, sampled rows within the bar of the oracle."""
+    s = I.random_loop(seed=1, panels=1024, ns=8, nth=16)
+    assert s.size == 131072
+    sig = I.density(s.size, seed=23)
+    got = _run(lib, "stokes_sl_apply_noalloc", _t(s.x), _t(s.w), _t(sig), _t(s.x), prec)
+    rows = np.sort(np.random.default_rng(29).choice(s.size, 256, replace=False))
+    ref = oracle_mod.sl(s.x, s.w, sig, s.x[:, rows])
+    err = _relerr(got[:, rows], ref)
+    print("noalloc max size %s relerr %.3e" % (prec, err))
+    assert np.all(np.isfinite(got))
+    # measured on GB300: 3.0e-14 (FP64), 2.7e-7 (compensated FP32); bar 3x the latter
+    assert err <= (1e-10 if prec == "fp64" else 8e-7)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(lib):
