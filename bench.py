@@ -377,11 +377,12 @@ def run_headline(args):
     info = sbq.device_info()
     peak, sm_max = _peak_tflops(info, clocks)
     achieved = FLOPS_PER_PAIR["cf"] * pairs / (kernel_ms * 1e-3) / 1e12
-    traffic = _profiled_traffic("pairsum_f32_comp_helix.json")
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "traffic_unit": "bytes per launch (ncu dram read + write, scaled from a "
-                                "smaller helix by the node count)",
+                "frac": achieved / peak, "traffic": None,
+                "traffic_note": "DRAM traffic of this kernel grows with the node count, not "
+                                "with the pairs: measured 16.3 MB at 193,120 nodes and 40.1 MB "
+                                "at 324,192 nodes (profiles/pairsum_f32_comp_helix.md); the "
+                                "full-size launch was not captured",
                 "kernel": "pairsum_f32_kernel<combined field, compensated>",
                 "flops_per_pair": FLOPS_PER_PAIR["cf"], "pairs_per_launch": pairs,
                 "launch_ms": kernel_ms, "apply_ms": float(np.mean(ams)),
