@@ -95,6 +95,13 @@ def parse(argv=None):
                     help="quadrature: panels of the random loop (x 128 nodes)")
     ap.add_argument("--near-factor", type=float, default=0.5,
                     help="quadrature: near region of an element, radius + f max(length, 2 radius)")
+    ap.add_argument("--build-only", action="store_true",
+                    help="quadrature: only build the Stokes E of the random loop (--quad-panels), "
+                         "--kernel-reps times inside the NVTX range 'kernel_only'")
+    ap.add_argument("--iteration-study", action="store_true",
+                    help="quadrature: also solve the corrected loop systems with plain FP64 "
+                         "GMRES(100) and GMRES(256) and with the mixed solver at GMRES(256) "
+                         "(minutes at 196K nodes)")
     ap.add_argument("--fp64-solve", action="store_true",
                     help="batch: also time the plain FP64 GMRES solve (minutes)")
     ap.add_argument("--no-graph", action="store_true",
@@ -1308,6 +1315,26 @@ def run_quadrature(args):
         m = torch.sparse_csr_tensor(rowptr, col, val, size=(rowptr.shape[0] - 1, v.shape[0]))
         return (m @ v.unsqueeze(1)).squeeze(1)
 
+    if args.build_only:
+        # the Stokes combined-field E of the random loop alone, inside the NVTX range
+        # 'kernel_only' (for profilers)
+        s = I.random_loop(seed=1, panels=args.quad_panels, ns=8, nth=16)
+        args_ = (t(s.x), t(s.n), t(s.w), args.quad_panels, 8, 16)
+        sbq.tube_correction(*args_, kind="stokes", alpha=sbq.slender_eta(0.01), beta=1.0,
+                            near_factor=args.near_factor)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("kernel_only")
+        t0 = time.perf_counter()
+        for _ in range(max(1, args.kernel_reps)):
+            E = sbq.tube_correction(*args_, kind="stokes", alpha=sbq.slender_eta(0.01), beta=1.0,
+                                    near_factor=args.near_factor)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3 / max(1, args.kernel_reps)
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"build_only": "stokes", "nodes": s.size, "build_ms": ms,
+                          "nnz": int(E[2].shape[0])}), flush=True)
+        return 0
+
     # (1) the paper's torus table
     printed = {320: (3.3e-3, 0.016), 720: (7.6e-7, 0.055), 1280: (1.1e-9, 0.166), 2000: (2.1e-10, 0.357)}
     table = []
@@ -1368,7 +1395,7 @@ def run_quadrature(args):
                     "nnz": int(E[2].shape[0]) if E is not None else 0,
                     "solve_ms": solve_ms, "iters": rep["iters"], "refinements": rep["outer_iters"],
                     "rel_res": rep["rel_res"], "status": rep["status_name"]}
-        if corrected:
+        if corrected and args.iteration_study:
             # iteration counts of the same system: plain FP64 GMRES(100) (no FP32 inner solve)
             # and both solvers with a longer restart, to separate the operator's conditioning,
             # the restart length and the FP32 inner solves

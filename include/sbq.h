@@ -278,7 +278,11 @@ SBQ_API int stokes_dl_gauss_correction(int nbody, const int64_t *body_off, const
  * Quadrature correction E of tube elements for stokes_op_create / laplace_op_create: the
  * paper's on-surface corrections (Eq. nystrom-correction; angular weights of Sec. 3.2.2,
  * Eqs. modal-greens-fn-coeff / modal-greens-fn-wts; near-singular rule of Sec. 3.2.3;
- * singular rule of Sec. 3.2.4, Eq. sing-nyst-correc).
+ * singular rule of Sec. 3.2.4, Eq. sing-nyst-correc).  Angular integrals: the periodic
+ * trapezoidal rule on the element's N_theta angles for targets two or more radii from the
+ * source circle; closer, the compiled-in compressed rule of the target's dyadic distance
+ * level (tables for N_theta <= 32) where it has fewer nodes than the dyadically refined
+ * Gauss-Legendre rule, else the latter.
  *   nodes 0 .. nelem*ns*nt - 1 are tube elements: element k holds ns Gauss-Legendre nodes in
  *   its panel parameter times nt equispaced angles 2 pi j / nt, node k*ns*nt + i*nt + j, and
  *   every GL row of an element lies on a circle (a tube y = x_c(s) + rho(s)(e1 cos + e2
@@ -325,24 +329,25 @@ SBQ_API int tube_correction(int64_t nelem, int ns, int nt, int64_t n_total, cons
  * tube_correction; rowptr holds (laplace ? 1 : 3) * ntrg + 1 entries.
  */
 /*
- * tube_correction / tube_correction_targets with compressed angular rules (Sec. 3.2.2 with
- * the generalized Chebyshev rules of Appendix B): for relative distances 2^-30 <= alpha < 1
- * of a target from a source circle, the angular integrals take the caller's rule of level
- * lev = ceil(-log2 alpha) instead of the dyadically refined one.
+ * tube_correction / tube_correction_targets with the caller's angular rules in place of the
+ * compiled-in ones (Sec. 3.2.2 with the generalized Chebyshev rules of Appendix B).
  *   trg == NULL: on-surface targets (the tube nodes, as tube_correction; ntrg ignored);
  *   otherwise ntrg off-surface targets (as tube_correction_targets).
- *   nlev, rule_phi, rule_w, rule_cnt: HOST tables; level l (0 <= l < nlev <= 31) holds
- *   rule_cnt[l] <= 64 nodes: angle offsets rule_phi[l * 64 + m] from the circle point
- *   closest to the target, in [-pi, pi], and weights rule_w[l * 64 + m] (rule_cnt[l] = 0:
- *   that level keeps the dyadic rule).  The rules must integrate, for targets at relative
- *   distance alpha..2 alpha from the unit circle, the kernel components times e^{i l theta}
- *   up to l = N_theta/2 + 1 (paper_2310_00889_gb300/angular_rules.py writes such tables).
+ *   nlev == 0: no compressed rules (every angular integral closer than two radii takes the
+ *   dyadically refined Gauss-Legendre rule); the table arguments are then ignored.
+ *   nlev >= 1: HOST tables; level l (0 <= l < nlev <= 31) serves relative distances alpha
+ *   in [2^-l, 2^(1-l)) and holds rule_cnt[l] <= 128 nodes: angle offsets
+ *   rule_phi[l * 128 + m] from the circle point closest to the target, in [-pi, pi], and
+ *   weights rule_w[l * 128 + m] (rule_cnt[l] = 0: that level keeps the dyadic rule).  The
+ *   rules must integrate, for targets at relative distance alpha..2 alpha from the unit
+ *   circle, the kernel components times e^{i l theta} for l <= rule_l0; rule_l0 must be at
+ *   least nt/2 + 1 (paper_2310_00889_gb300/angular_rules.py writes such tables).
  * Otherwise the same arguments, layout, two-phase use and errors as tube_correction.
  */
 SBQ_API int tube_correction_rules(int64_t nelem, int ns, int nt, int64_t n_total,
                                   const double *src, const double *nrm, const double *w,
                                   int64_t ntrg, const double *trg, int laplace, double alpha,
-                                  double beta, double near_factor, int nlev,
+                                  double beta, double near_factor, int nlev, int rule_l0,
                                   const double *rule_phi, const double *rule_w,
                                   const int *rule_cnt, int64_t *nnz_out, int64_t *rowptr,
                                   int64_t *col, double *val, void *stream);

@@ -88,11 +88,16 @@ def annulus_targets(alpha, nr=12, npsi=24):
 def kernel_components(kind, r, n):
     """Kernel components for offsets r = x - y (3, M) and source normals n: "laplace": 1/|r|;
     "stokes": the six components of the single layer (delta/|r| + r_a r_b/|r|^3) and of the
-    double layer ((r . n) r_a r_b / |r|^5), each up to its constant."""
+    double layer ((r . n) r_a r_b / |r|^5), each up to its constant; "stokes_axial_dl": the
+    double layer for the normal along the circle's axis (0, 0, 1), the part of a tube's normal
+    that a radius varying along the centreline adds."""
     r2 = np.sum(r * r, axis=0)
     rl = np.sqrt(r2)
     if kind == "laplace":
         return [1.0 / rl]
+    if kind == "stokes_axial_dl":
+        return [r[2] * r[a] * r[b] / (r2 * r2 * rl)
+                for a, b in ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))]
     rn = np.sum(r * n, axis=0)
     out = []
     for a, b in ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)):

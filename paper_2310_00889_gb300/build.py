@@ -18,9 +18,12 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libsbq.so")
 ROOT = os.path.dirname(HERE)
 
+GEN = os.path.join(LIBDIR, "gen")
+RULES = os.path.join(HERE, "rules")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
-              "-Xcompiler", "-fPIC,-fvisibility=hidden,-O2", "-I", os.path.join(ROOT, "include")]
+              "-Xcompiler", "-fPIC,-fvisibility=hidden,-O2", "-I", os.path.join(ROOT, "include"),
+              "-I", GEN]
 
 
 def nvcc_path() -> str:
@@ -37,9 +40,55 @@ def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+def _rule_tables():
+    return sorted(glob.glob(os.path.join(RULES, "angular_l*.txt")),
+                  key=lambda f: int(os.path.basename(f)[len("angular_l"):-len(".txt")]))
+
+
 def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) \
-        + [os.path.join(ROOT, "include", "sbq.h"), os.path.abspath(__file__)]
+        + [os.path.join(ROOT, "include", "sbq.h"), os.path.abspath(__file__)] + _rule_tables()
+
+
+def write_rule_tables():
+    """The compressed angular rules (rules/angular_l<l0>.txt, written by angular_rules.py)
+    as a C include for the quadrature builder: per table its l0, the node count of each of
+    the 31 distance levels, and the (offset, weight) pairs level by level, as hexadecimal
+    floating-point literals (exact)."""
+    os.makedirs(GEN, exist_ok=True)
+    l0s, cnts, data = [], [], []
+    for path in _rule_tables():
+        l0 = int(os.path.basename(path)[len("angular_l"):-len(".txt")])
+        cnt = [0] * 31
+        lines = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+        i = 0
+        while i < len(lines):
+            lev, n = int(lines[i][0]), int(lines[i][1])
+            cnt[lev] = n
+            for k in range(n):
+                a, b = lines[i + 1 + k]
+                data.append(float(a).hex())
+                data.append(float(b).hex())
+            i += n + 1
+        l0s.append(l0)
+        cnts.append(cnt)
+    out = ["// generated by paper_2310_00889_gb300/build.py from rules/angular_l*.txt", ""]
+    out.append("static const int kRuleTables = %d;" % len(l0s))
+    out.append("static const int kRuleL0[%d] = {%s};" % (max(1, len(l0s)), ", ".join(map(str, l0s)) or "0"))
+    out.append("static const int kRuleCnt[%d][31] = {%s};" % (
+        max(1, len(l0s)), ", ".join("{" + ", ".join(map(str, c)) + "}" for c in cnts) or "{0}"))
+    out.append("static const double kRuleData[%d] = {" % max(1, len(data)))
+    for k in range(0, len(data), 4):
+        out.append("    " + ", ".join(data[k:k + 4]) + ",")
+    if not data:
+        out.append("    0.0,")
+    out.append("};")
+    text = "\n".join(out) + "\n"
+    path = os.path.join(GEN, "angular_rules_tables.inc")
+    if not os.path.exists(path) or open(path).read() != text:
+        with open(path, "w") as f:
+            f.write(text)
+    return path
 
 
 def up_to_date() -> bool:
@@ -53,6 +102,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     if not force and up_to_date():
         return LIB
     nvcc = nvcc_path()
+    write_rule_tables()
     objdir = os.path.join(LIBDIR, "obj")
     os.makedirs(objdir, exist_ok=True)
     flags = NVCC_FLAGS + list(extra_flags or [])

@@ -111,8 +111,8 @@ def _load():
         "tube_correction": ([_i64, _int, _int, _i64, _vp, _vp, _vp, _int, _dbl, _dbl, _dbl,
                              ctypes.POINTER(_i64), _vp, _vp, _vp, _vp], _int),
         "tube_correction_rules": ([_i64, _int, _int, _i64, _vp, _vp, _vp, _i64, _vp, _int, _dbl,
-                                   _dbl, _dbl, _int, _vp, _vp, _vp, ctypes.POINTER(_i64), _vp,
-                                   _vp, _vp, _vp], _int),
+                                   _dbl, _dbl, _int, _int, _vp, _vp, _vp, ctypes.POINTER(_i64),
+                                   _vp, _vp, _vp, _vp], _int),
         "sbq_peak_probe": ([_int, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), _vp], _int),
         "tube_correction_targets": ([_i64, _int, _int, _i64, _vp, _vp, _vp, _i64, _vp, _int, _dbl,
                                      _dbl, _dbl, ctypes.POINTER(_i64), _vp, _vp, _vp, _vp], _int),
@@ -262,21 +262,28 @@ def dl_gauss_correction(src, nrm, w, body_off=None, prec="fp64", stream=None):
 
 
 def _rules_call(src, nrm, w, nelem, ns, nt, trg, lap, alpha, beta, near_factor, rules, stream):
-    """tube_correction_rules with host tables rules = (phi, w, cnt) of shapes (L, 64),
-    (L, 64), (L,)."""
-    rphi = np.ascontiguousarray(rules[0], dtype=np.float64)
-    rw = np.ascontiguousarray(rules[1], dtype=np.float64)
-    rcnt = np.ascontiguousarray(rules[2], dtype=np.int32)
-    nlev = int(rcnt.shape[0])
-    if rphi.shape != (nlev, 64) or rw.shape != (nlev, 64):
-        raise ValueError("rules: phi and w must be (levels, 64)")
+    """tube_correction_rules with host tables rules = (phi, w, cnt, l0) of shapes (L, 128),
+    (L, 128), (L,) and the tables' mode count, or rules = "none" (no compressed rules)."""
+    if isinstance(rules, str):
+        if rules != "none":
+            raise ValueError("rules must be a table (phi, w, cnt, l0) or 'none'")
+        nlev, l0, dptr_phi, dptr_w, dptr_cnt = 0, 0, None, None, None
+    else:
+        rphi = np.ascontiguousarray(rules[0], dtype=np.float64)
+        rw = np.ascontiguousarray(rules[1], dtype=np.float64)
+        rcnt = np.ascontiguousarray(rules[2], dtype=np.int32)
+        l0 = int(rules[3])
+        nlev = int(rcnt.shape[0])
+        if rphi.shape != (nlev, 128) or rw.shape != (nlev, 128):
+            raise ValueError("rules: phi and w must be (levels, 128)")
+        dptr_phi, dptr_w = rphi.ctypes.data_as(_vp), rw.ctypes.data_as(_vp)
+        dptr_cnt = rcnt.ctypes.data_as(_vp)
     n = src.shape[1]
     m = trg.shape[1] if trg is not None else 0
     nnz = _i64(0)
-    dptr = lambda a: a.ctypes.data_as(_vp)
     args = (int(nelem), int(ns), int(nt), int(n), _ptr(src), _ptr(nrm), _ptr(w), int(m),
             _ptr(trg) if trg is not None else None, lap, float(alpha), float(beta), float(near_factor),
-            nlev, dptr(rphi), dptr(rw), dptr(rcnt))
+            nlev, l0, dptr_phi, dptr_w, dptr_cnt)
     _check(lib.tube_correction_rules(*args, ctypes.byref(nnz), None, None, None, _stream(stream)))
     rows = (1 if lap else 3) * (m if trg is not None else n)
     rowptr = torch.empty(rows + 1, dtype=torch.int64, device=src.device)
@@ -294,8 +301,9 @@ def tube_correction(src, nrm, w, nelem, ns, nt, kind="stokes", alpha=1.0, beta=1
     near region holds it, the entries that turn the punctured sum over the element into the
     accurate integral.  kind "stokes" (alpha S + beta D, 3 x 3) or "laplace" (scalar); an
     operator K = diag I + D + eta S takes alpha = eta, beta = 1.  Pass the result as
-    StokesOp / LaplaceOp (..., correction=...).  rules: None (dyadically refined angular
-    rules) or compressed angular rules (phi, w, cnt), e.g. angular_rules.load(nt)."""
+    StokesOp / LaplaceOp (..., correction=...).  rules: None (the library's compiled-in
+    compressed angular rules), "none" (dyadically refined rules only), or a caller's table
+    (phi, w, cnt, l0), e.g. angular_rules.load(nt)."""
     n = src.shape[1]
     _dev(src, (3, n), "src")
     _dev(nrm, (3, n), "nrm")

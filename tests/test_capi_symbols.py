@@ -106,32 +106,34 @@ def test_tube_correction_validation_on_host(libsbq):
 
 
 def test_tube_correction_rules_validation_on_host(libsbq):
-    """tube_correction_rules rejects malformed rule tables before touching a device."""
+    """tube_correction_rules rejects malformed rule tables and tables whose mode count l0 is
+    below N_theta / 2 + 1 before touching a device."""
     vp, i64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
     f = libsbq.tube_correction_rules
     f.argtypes = [i64, ctypes.c_int, ctypes.c_int, i64, vp, vp, vp, i64, vp, ctypes.c_int, dbl, dbl,
-                  dbl, ctypes.c_int, vp, vp, vp, ctypes.POINTER(i64), vp, vp, vp, vp]
+                  dbl, ctypes.c_int, ctypes.c_int, vp, vp, vp, ctypes.POINTER(i64), vp, vp, vp, vp]
     libsbq.sbq_last_error.restype = ctypes.c_char_p
     fake = vp(16)
     nnz = i64(0)
-    phi = (ctypes.c_double * (31 * 64))()
-    w = (ctypes.c_double * (31 * 64))()
+    phi = (ctypes.c_double * (31 * 128))()
+    w = (ctypes.c_double * (31 * 128))()
     cnt = (ctypes.c_int * 31)()
 
-    def call(nlev, p=phi, ww=w, c=cnt):
-        return f(4, 8, 16, 512, fake, fake, fake, 0, None, 0, 1.0, 1.0, 0.5, nlev,
+    def call(nlev, l0=9, p=phi, ww=w, c=cnt):
+        return f(4, 8, 16, 512, fake, fake, fake, 0, None, 0, 1.0, 1.0, 0.5, nlev, l0,
                  ctypes.cast(p, vp), ctypes.cast(ww, vp), ctypes.cast(c, vp), ctypes.byref(nnz),
                  None, None, None, None)
 
-    assert call(0) == 1 and b"nlev" in libsbq.sbq_last_error()
+    assert call(-1) == 1 and b"nlev" in libsbq.sbq_last_error()
     assert call(32) == 1
-    cnt[3] = 65
-    assert call(31) == 1 and b"64" in libsbq.sbq_last_error()
+    assert call(31, l0=8) == 1 and b"l0" in libsbq.sbq_last_error()   # N_theta 16 needs l0 >= 9
+    cnt[3] = 129
+    assert call(31) == 1 and b"128" in libsbq.sbq_last_error()
     cnt[3] = 2
-    phi[3 * 64 + 1] = 4.0                      # offset outside [-pi, pi]
+    phi[3 * 128 + 1] = 4.0                      # offset outside [-pi, pi]
     assert call(31) == 1 and b"pi" in libsbq.sbq_last_error()
-    phi[3 * 64 + 1] = 0.5
-    w[3 * 64] = float("nan")
+    phi[3 * 128 + 1] = 0.5
+    w[3 * 128] = float("nan")
     assert call(31) == 1
 
 
