@@ -181,13 +181,35 @@ def helix_pipe(a=3.0, pitch=2.0, turns=4.0, R=1.0, panels=2048, ns=8, nth=64) ->
     return _tube(s, ws, c, dc, ddc, np.full(m, R), np.zeros(m), e1, de1, nth, "helix_wall")
 
 
+def _loop_radius(s):
+    """Tube radius of the random loop: 0.01 (1 + 0.5 sin 2 pi s), in [0.005, 0.015]."""
+    return 0.01 * (1.0 + 0.5 * np.sin(2.0 * np.pi * s))
+
+
+def _loop_max_curvature_radius(k, A, B, n=20000):
+    """max over the centreline of kappa(s) * radius(s) (on n equispaced samples)."""
+    s = np.arange(n) / n
+    _, dc, ddc = _loop_eval(s, k, A, B)
+    sp = np.linalg.norm(dc, axis=0)
+    kappa = np.linalg.norm(_cross(dc, ddc), axis=0) / sp ** 3
+    return float(np.max(kappa * _loop_radius(s)))
+
+
+MAX_KAPPA_RHO = 0.5
+
+
 def _loop_coeffs(seed, kmax=10):
+    """Fourier coefficients of the centreline: successive draws from the generator seeded with
+    `seed` until the tube is a valid slender body, kappa * radius <= MAX_KAPPA_RHO everywhere
+    (a draw with kappa * radius >= 1 somewhere folds the tube's inner side over itself)."""
     rng = np.random.default_rng(seed)
     k = np.arange(1, kmax + 1)
     sd = 1.0 / (1.0 + k / 3.0)
-    A = rng.standard_normal((3, kmax)) * sd[None, :]
-    B = rng.standard_normal((3, kmax)) * sd[None, :]
-    return k, A, B
+    while True:
+        A = rng.standard_normal((3, kmax)) * sd[None, :]
+        B = rng.standard_normal((3, kmax)) * sd[None, :]
+        if _loop_max_curvature_radius(k, A, B) <= MAX_KAPPA_RHO:
+            return k, A, B
 
 
 def _loop_eval(s, k, A, B):
@@ -247,8 +269,9 @@ def _transport_frame(s_out, k, A, B, substeps=8):
 
 def random_loop(seed=1, panels=512, ns=8, nth=16, substeps=2) -> Surface:
     """Closed random slender loop of paper Sec. 5.2: Fourier centreline, k = 1..10,
-    iid normal coefficients with standard deviation 1/(1 + k/3); radius
-    0.01 (1 + 0.5 sin 2 pi s), in [0.005, 0.015]."""
+    iid normal coefficients with standard deviation 1/(1 + k/3) (the first draw whose
+    curvature times radius stays <= MAX_KAPPA_RHO); radius 0.01 (1 + 0.5 sin 2 pi s), in
+    [0.005, 0.015]."""
     k, A, B = _loop_coeffs(seed)
     s, ws = _panel_nodes(np.linspace(0.0, 1.0, panels + 1), ns)
     c, dc, ddc = _loop_eval(s, k, A, B)
@@ -256,7 +279,7 @@ def random_loop(seed=1, panels=512, ns=8, nth=16, substeps=2) -> Surface:
     t = _unit(dc)
     e1 = _unit(e1 - np.sum(e1 * t, axis=0) * t)                 # re-orthonormalise (Sec. 3.1.1)
     de1 = _frame_rhs(e1, dc, ddc)
-    eps = 0.01 * (1.0 + 0.5 * np.sin(2.0 * np.pi * s))
+    eps = _loop_radius(s)
     deps = 0.01 * 0.5 * 2.0 * np.pi * np.cos(2.0 * np.pi * s)
     return _tube(s, ws, c, dc, ddc, eps, deps, e1, de1, nth, "random_loop")
 

@@ -148,9 +148,8 @@ def test_csr_layout_and_two_phase_count(sbq):
 X0 = np.zeros(3)
 
 
-def _laplace_identity_error(sbq, S, panels, ns, nt, nf):
+def _laplace_identity_error(sbq, S, panels, ns, nt, nf, x0=X0):
     n = S.size
-    x0 = X0
     d = S.x - x0[:, None]
     r = np.linalg.norm(d, axis=0)
     u, dudn = 1.0 / r, -np.sum(d * S.n, axis=0) / r ** 3
@@ -175,29 +174,50 @@ def test_laplace_green_identity_all_nodes(sbq):
     assert corr < 1e-10
 
 
-def test_stokes_green_identity_all_nodes(sbq):
-    """u / 2 = S[f] - D[u] at every node for the flow of an exterior point force (Appendix A
-    representation, on-surface limit), with the GPU-built Stokes corrections."""
-    S = I.torus(R0=1.0, eps=0.25, panels=16, ns=8, nth=32)
+def _stokes_identity_error(sbq, S, panels, ns, nt, nf, x0=X0):
     n = S.size
-    x0, F = X0, np.array([0.5, -1.0, 0.7])
+    F = np.array([0.5, -1.0, 0.7])
     r = S.x - x0[:, None]
     rl = np.linalg.norm(r, axis=0)
     rf = F @ r
     u = (F[:, None] / rl + r * rf / rl ** 3) / (8.0 * np.pi)
     trac = -(3.0 / (4.0 * np.pi)) * r * rf * np.sum(r * S.n, axis=0) / rl ** 5
-    ES = _csr_host(sbq.tube_correction(_t(S.x), _t(S.n), _t(S.w), 16, 8, 32, kind="stokes",
-                                       alpha=1.0, beta=0.0, near_factor=0.5), 3 * n, 3 * n)
-    ED = _csr_host(sbq.tube_correction(_t(S.x), _t(S.n), _t(S.w), 16, 8, 32, kind="stokes",
-                                       alpha=0.0, beta=1.0, near_factor=0.5), 3 * n, 3 * n)
+    ES = _csr_host(sbq.tube_correction(_t(S.x), _t(S.n), _t(S.w), panels, ns, nt, kind="stokes",
+                                       alpha=1.0, beta=0.0, near_factor=nf), 3 * n, 3 * n)
+    ED = _csr_host(sbq.tube_correction(_t(S.x), _t(S.n), _t(S.w), panels, ns, nt, kind="stokes",
+                                       alpha=0.0, beta=1.0, near_factor=nf), 3 * n, 3 * n)
     Sp = _np(sbq.sl_apply(_t(S.x), _t(S.w), _t(trac), _t(S.x), prec="fp64"))
     Dp = _np(sbq.dl_apply(_t(S.x), _t(S.n), _t(S.w), _t(u), _t(S.x), prec="fp64"))
     lhs = Sp + (ES @ trac.reshape(-1)).reshape(3, n) - Dp - (ED @ u.reshape(-1)).reshape(3, n)
     corr = np.abs(lhs - 0.5 * u).max() / np.abs(u).max()
     punct = np.abs(Sp - Dp - 0.5 * u).max() / np.abs(u).max()
+    return corr, punct
+
+
+def test_stokes_green_identity_all_nodes(sbq):
+    """u / 2 = S[f] - D[u] at every node for the flow of an exterior point force (Appendix A
+    representation, on-surface limit), with the GPU-built Stokes corrections."""
+    S = I.torus(R0=1.0, eps=0.25, panels=16, ns=8, nth=32)
+    corr, punct = _stokes_identity_error(sbq, S, 16, 8, 32, 0.5)
     print("stokes identity: corrected %.3e punctured %.3e" % (corr, punct))
     assert punct > 1e-3
     assert corr < 1e-10
+
+
+def test_green_identities_on_slender_random_loop_all_nodes(sbq):
+    """Both Green's identities at EVERY node of the slender random loop of Sec. 5.2 (256
+    panels x 8 x 16 = 32,768 nodes; element aspect ~20), with the GPU-built E in its default
+    configuration (trapezoidal, compressed and dyadic angular rules chosen per s-node): a check
+    of the builder's rules against the mathematics rather than against the oracle.  Source
+    point / point force at the loop's centroid, 0.49 from the tube."""
+    S = I.random_loop(seed=1, panels=256, ns=8, nth=16)
+    x0 = S.x.mean(axis=1)
+    lap, lap_p = _laplace_identity_error(sbq, S, 256, 8, 16, 0.5, x0=x0)
+    sto, sto_p = _stokes_identity_error(sbq, S, 256, 8, 16, 0.5, x0=x0)
+    print("slender loop identities, every node: laplace %.3e (punctured %.3e), stokes %.3e "
+          "(punctured %.3e)" % (lap, lap_p, sto, sto_p))
+    assert lap_p > 1e-2 and sto_p > 1e-2
+    assert lap < 1e-9 and sto < 1e-9
 
 
 def test_laplace_exterior_solve_with_quadrature_correction(sbq):

@@ -284,3 +284,35 @@ def test_on_element_stokes_layers_match_nested_adaptive_integral(alpha, beta):
     scale = np.abs(exact).max()
     assert np.abs(u - exact).max() < 1e-11 * scale
     assert np.abs(up - exact).max() > 1e-2 * scale
+
+
+def test_laplace_green_identity_on_slender_random_loop():
+    """Green's identity u / 2 = S[du/dn] - D[u] on the slender random loop of Sec. 5.2 (256
+    panels x 8 x 16, radius 0.005..0.015, length ~58: element aspect ~20), for u = 1/|x - x0|
+    with x0 at the loop's centroid (0.49 from the tube), at random nodes and at nodes of the
+    first element (the own-element rule next to the loop's parameter seam).  Measured
+    <= 4.4e-11 of max |u| (punctured sums: 7e-4..0.2)."""
+    panels, ns, nt = 256, 8, 16
+    S = I.random_loop(seed=1, panels=panels, ns=ns, nth=nt)
+    n = S.size
+    x0 = S.x.mean(axis=1)
+    d = S.x - x0[:, None]
+    r = np.linalg.norm(d, axis=0)
+    assert r.min() > 0.4
+    u, dudn = 1.0 / r, -np.sum(d * S.n, axis=0) / r ** 3
+    per = ns * nt
+    tg = list(np.random.default_rng(3).choice(n, 4, replace=False)) + [3 * nt + 5, 7 * nt + 2, 5 * per + 1]
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        rS = T.correction_dense_rows(T.correction_rows(S.x, S.n, S.w, panels, ns, nt, "laplace", 1.0, 0.0,
+                                                       0.5, tg), n, "laplace")
+        rD = T.correction_dense_rows(T.correction_rows(S.x, S.n, S.w, panels, ns, nt, "laplace", 0.0, 1.0,
+                                                       0.5, tg), n, "laplace")
+    Sp = oracle.laplace(S.x, S.n, S.w, dudn, S.x[:, tg], 1.0, 0.0)
+    Dp = oracle.laplace(S.x, S.n, S.w, u, S.x[:, tg], 0.0, 1.0)
+    scale = np.max(np.abs(u))
+    err = max(abs(Sp[k] + rS[t] @ dudn - Dp[k] - rD[t] @ u - 0.5 * u[t]) for k, t in enumerate(tg))
+    punct = min(abs(Sp[k] - Dp[k] - 0.5 * u[t]) for k, t in enumerate(tg))
+    print("slender loop identity (oracle): %.3e" % (err / scale))
+    assert punct > 1e-4 * scale
+    assert err < 1e-9 * scale, err / scale
