@@ -93,7 +93,7 @@ def parse(argv=None):
                          "apart, which the punctured sums cannot resolve)")
     ap.add_argument("--quad-panels", type=int, default=512,
                     help="quadrature: panels of the random loop (x 128 nodes)")
-    ap.add_argument("--near-factor", type=float, default=0.5,
+    ap.add_argument("--near-factor", type=float, default=1.0,
                     help="quadrature: near region of an element, radius + f max(length, 2 radius)")
     ap.add_argument("--build-only", action="store_true",
                     help="quadrature: only build the Stokes E of the random loop (--quad-panels), "

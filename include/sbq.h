@@ -278,11 +278,17 @@ SBQ_API int stokes_dl_gauss_correction(int nbody, const int64_t *body_off, const
  * Quadrature correction E of tube elements for stokes_op_create / laplace_op_create: the
  * paper's on-surface corrections (Eq. nystrom-correction; angular weights of Sec. 3.2.2,
  * Eqs. modal-greens-fn-coeff / modal-greens-fn-wts; near-singular rule of Sec. 3.2.3;
- * singular rule of Sec. 3.2.4, Eq. sing-nyst-correc).  Angular integrals: the periodic
- * trapezoidal rule on the element's N_theta angles for targets two or more radii from the
- * source circle; closer, the compiled-in compressed rule of the target's dyadic distance
- * level (tables for N_theta <= 32) where it has fewer nodes than the dyadically refined
- * Gauss-Legendre rule, else the latter.
+ * singular rule of Sec. 3.2.4, Eq. sing-nyst-correc).  Angular integrals, per s-node, the
+ * rule with the fewest nodes among: the periodic trapezoidal rule on k N_theta angles (k <=
+ * 8, k from its aliasing bound for the target's relative distance), the compiled-in
+ * compressed rule of the distance's dyadic level (App. B; levels down to 2^-52, tables for
+ * N_theta <= 32), and the dyadically refined Gauss-Legendre rule; the first two only where
+ * the area element is resolved by a few modes beyond N_theta / 2 (a bound on the zeros of
+ * |y_theta x y_t|^2).  Outer rule in the panel parameter: for a target on the element
+ * itself, the compiled-in whole-element singular rule of Sec. 3.2.4 (App. B; ns = 8,
+ * N_theta <= 16, element length / radius at the target in [1/4, 8192)), else dyadic panels
+ * towards the target with a graded panel next to it; for other targets dyadic panels
+ * towards the nearest parameter.
  *   nodes 0 .. nelem*ns*nt - 1 are tube elements: element k holds ns Gauss-Legendre nodes in
  *   its panel parameter times nt equispaced angles 2 pi j / nt, node k*ns*nt + i*nt + j, and
  *   every GL row of an element lies on a circle (a tube y = x_c(s) + rho(s)(e1 cos + e2
@@ -333,9 +339,12 @@ SBQ_API int tube_correction(int64_t nelem, int ns, int nt, int64_t n_total, cons
  * compiled-in ones (Sec. 3.2.2 with the generalized Chebyshev rules of Appendix B).
  *   trg == NULL: on-surface targets (the tube nodes, as tube_correction; ntrg ignored);
  *   otherwise ntrg off-surface targets (as tube_correction_targets).
- *   nlev == 0: no compressed rules (every angular integral closer than two radii takes the
- *   dyadically refined Gauss-Legendre rule); the table arguments are then ignored.
- *   nlev >= 1: HOST tables; level l (0 <= l < nlev <= 31) serves relative distances alpha
+ *   nlev == 0: no compressed rules: neither the angular tables (every angular integral
+ *   that the trapezoidal rule does not take goes to the dyadically refined Gauss-Legendre
+ *   rule) nor the whole-element singular rules (own-element targets take dyadic panels and
+ *   the graded panel next to t0); the table arguments are then ignored.
+ *   nlev >= 1: HOST angular tables (the compiled-in singular rules stay on); level l
+ *   (0 <= l < nlev <= 53) serves relative distances alpha
  *   in [2^-l, 2^(1-l)) and holds rule_cnt[l] <= 128 nodes: angle offsets
  *   rule_phi[l * 128 + m] from the circle point closest to the target, in [-pi, pi], and
  *   weights rule_w[l * 128 + m] (rule_cnt[l] = 0: that level keeps the dyadic rule).  The

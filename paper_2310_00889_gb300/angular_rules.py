@@ -4,7 +4,7 @@ compiles in.
 
 Run once per mode count:  python -m paper_2310_00889_gb300.angular_rules 12
 It writes paper_2310_00889_gb300/rules/angular_l12.txt: for every distance level
-lev = 0..30 (relative distance alpha of the target from the source circle in
+lev = 0..52 (relative distance alpha of the target from the source circle in
 [2^-lev, 2^(1-lev)), level 0 being [1, 2)) the nodes (angle offsets from the circle point
 closest to the target) and weights of a rule that integrates G(x, y(theta)) e^{i l theta},
 l <= l0, for every target of the annulus, G running over the components of the Stokes single
@@ -37,7 +37,7 @@ import sys
 
 import numpy as np
 
-LEVELS = 30       # levels 0 .. LEVELS
+LEVELS = 52       # levels 0 .. LEVELS: alpha down to 2^-52
 NMAX = 128        # nodes per level the builder reserves
 EPS = 1e-11
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -111,21 +111,35 @@ def table_path(l0):
 
 
 def generate(l0):
+    """Write the table of l0, keeping the levels an existing table already holds."""
     os.makedirs(os.path.join(HERE, "rules"), exist_ok=True)
     path = table_path(l0)
+    have = {}
+    if os.path.exists(path):
+        lines = [l for l in open(path) if not l.startswith("#")]
+        i = 0
+        while i < len(lines):
+            lev, n = (int(v) for v in lines[i].split())
+            have[lev] = [tuple(float(v) for v in lines[i + 1 + k].split()) for k in range(n)]
+            i += n + 1
     tmp = path + ".partial"
     with open(tmp, "w") as f:
         f.write("# compressed angular rules, l0 = %d (N_theta <= %d), eps = %g; written by "
                 "python -m paper_2310_00889_gb300.angular_rules %d\n" % (l0, 2 * (l0 - 1), EPS, l0))
         f.write("# per level: 'level n' then n lines 'offset weight'\n")
         for lev in range(0, LEVELS + 1):
-            y, om = level_rule(lev, l0)
-            if len(y) > NMAX:
-                raise RuntimeError("level %d needs %d nodes (> %d)" % (lev, len(y), NMAX))
-            f.write("%d %d\n" % (lev, len(y)))
-            for a, b in zip(y, om):
+            if lev in have:
+                rows = have[lev]
+            else:
+                y, om = level_rule(lev, l0)
+                rows = list(zip(y, om))
+                print("l0 %d level %d: %d nodes" % (l0, lev, len(rows)), flush=True)
+            if len(rows) > NMAX:
+                raise RuntimeError("level %d needs %d nodes (> %d)" % (lev, len(rows), NMAX))
+            f.write("%d %d\n" % (lev, len(rows)))
+            for a, b in rows:
                 f.write("%.17e %.17e\n" % (a, b))
-            print("l0 %d level %d: %d nodes" % (l0, lev, len(y)), flush=True)
+            f.flush()
     os.replace(tmp, path)
     return path
 

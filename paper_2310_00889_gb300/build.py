@@ -47,19 +47,28 @@ def _rule_tables():
 
 def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) \
-        + [os.path.join(ROOT, "include", "sbq.h"), os.path.abspath(__file__)] + _rule_tables()
+        + [os.path.join(ROOT, "include", "sbq.h"), os.path.abspath(__file__),
+           os.path.join(os.path.dirname(os.path.abspath(__file__)), "angular_rules.py")] + _rule_tables() + _singular_tables()
+
+
+def _rule_levels():
+    """LEVELS + 1 of angular_rules.py, read from its source (the build imports no package code)."""
+    import re
+    src = open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "angular_rules.py")).read()
+    return int(re.search(r"^LEVELS = (\d+)", src, re.M).group(1)) + 1
 
 
 def write_rule_tables():
     """The compressed angular rules (rules/angular_l<l0>.txt, written by angular_rules.py)
     as a C include for the quadrature builder: per table its l0, the node count of each of
-    the 31 distance levels, and the (offset, weight) pairs level by level, as hexadecimal
+    the LEVELS + 1 distance levels, and the (offset, weight) pairs level by level, as hexadecimal
     floating-point literals (exact)."""
     os.makedirs(GEN, exist_ok=True)
+    nlev = _rule_levels()
     l0s, cnts, data = [], [], []
     for path in _rule_tables():
         l0 = int(os.path.basename(path)[len("angular_l"):-len(".txt")])
-        cnt = [0] * 31
+        cnt = [0] * nlev
         lines = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
         i = 0
         while i < len(lines):
@@ -75,8 +84,9 @@ def write_rule_tables():
     out = ["// generated by paper_2310_00889_gb300/build.py from rules/angular_l*.txt", ""]
     out.append("static const int kRuleTables = %d;" % len(l0s))
     out.append("static const int kRuleL0[%d] = {%s};" % (max(1, len(l0s)), ", ".join(map(str, l0s)) or "0"))
-    out.append("static const int kRuleCnt[%d][31] = {%s};" % (
-        max(1, len(l0s)), ", ".join("{" + ", ".join(map(str, c)) + "}" for c in cnts) or "{0}"))
+    out.append("static const int kRuleLevels = %d;" % nlev)
+    out.append("static const int kRuleCnt[%d][%d] = {%s};" % (
+        max(1, len(l0s)), nlev, ", ".join("{" + ", ".join(map(str, c)) + "}" for c in cnts) or "{0}"))
     out.append("static const double kRuleData[%d] = {" % max(1, len(data)))
     for k in range(0, len(data), 4):
         out.append("    " + ", ".join(data[k:k + 4]) + ",")
@@ -85,6 +95,61 @@ def write_rule_tables():
     out.append("};")
     text = "\n".join(out) + "\n"
     path = os.path.join(GEN, "angular_rules_tables.inc")
+    if not os.path.exists(path) or open(path).read() != text:
+        with open(path, "w") as f:
+            f.write(text)
+    return path
+
+
+def _singular_tables():
+    return sorted(glob.glob(os.path.join(RULES, "singular_ns*_l*.txt")))
+
+
+def write_singular_tables():
+    """The whole-element singular rules (rules/singular_ns<ns>_l<l0>.txt, written by
+    singular_rules.py) as a C include: the table's ns, l0 and aspect levels, per (level, i0)
+    the node count and the offset of its first node, and the (offset, weight) pairs, as
+    hexadecimal floating-point literals (exact).  At most one table; none: kSingTables = 0."""
+    os.makedirs(GEN, exist_ok=True)
+    out = ["// generated by paper_2310_00889_gb300/build.py from rules/singular_ns*_l*.txt", ""]
+    paths = _singular_tables()
+    if paths:
+        path = paths[0]
+        base = os.path.basename(path)[len("singular_ns"):-len(".txt")]
+        ns, l0 = int(base.split("_l")[0]), int(base.split("_l")[1])
+        lines = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+        rules, i = {}, 0
+        while i < len(lines):
+            lev, i0, n = (int(v) for v in lines[i])
+            rules[(lev, i0)] = lines[i + 1:i + 1 + n]
+            i += n + 1
+        lo = min(k[0] for k in rules)
+        hi = max(k[0] for k in rules)
+        cnt, off, data = [], [], []
+        for lev in range(lo, hi + 1):
+            for i0 in range(ns):
+                r = rules.get((lev, i0), [])
+                off.append(len(data) // 2)
+                cnt.append(len(r))
+                for a, b in r:
+                    data.append(float(a).hex())
+                    data.append(float(b).hex())
+        out.append("static const int kSingTables = 1;")
+        out.append("static const int kSingNs = %d, kSingL0 = %d, kSingLo = %d, kSingHi = %d;" % (ns, l0, lo, hi))
+    else:
+        cnt, off, data = [0], [0], []
+        out.append("static const int kSingTables = 0;")
+        out.append("static const int kSingNs = 0, kSingL0 = 0, kSingLo = 0, kSingHi = -1;")
+    out.append("static const int kSingCnt[%d] = {%s};" % (len(cnt), ", ".join(map(str, cnt))))
+    out.append("static const int kSingOff[%d] = {%s};" % (len(off), ", ".join(map(str, off))))
+    out.append("static const double kSingData[%d] = {" % max(1, len(data)))
+    for k in range(0, len(data), 4):
+        out.append("    " + ", ".join(data[k:k + 4]) + ",")
+    if not data:
+        out.append("    0.0,")
+    out.append("};")
+    text = "\n".join(out) + "\n"
+    path = os.path.join(GEN, "singular_rules_tables.inc")
     if not os.path.exists(path) or open(path).read() != text:
         with open(path, "w") as f:
             f.write(text)
@@ -103,6 +168,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
         return LIB
     nvcc = nvcc_path()
     write_rule_tables()
+    write_singular_tables()
     objdir = os.path.join(LIBDIR, "obj")
     os.makedirs(objdir, exist_ok=True)
     flags = NVCC_FLAGS + list(extra_flags or [])

@@ -41,6 +41,9 @@
 // compressed angular rules compiled in from rules/angular_l*.txt (kRuleTables, kRuleL0,
 // kRuleCnt, kRuleData), written by build.py
 #include "angular_rules_tables.inc"
+// whole-element singular rules compiled in from rules/singular_ns*_l*.txt (kSingTables, kSingNs,
+// kSingL0, kSingLo, kSingHi, kSingCnt, kSingOff, kSingData), written by build.py
+#include "singular_rules_tables.inc"
 
 #include <algorithm>
 #include <cmath>
@@ -55,11 +58,15 @@ constexpr int TQ_THREADS = 128;
 constexpr int TQ_Q = 16;           // GL nodes per panel (angular and outer rules)
 constexpr int TQ_SING_N = 24;      // log-singular rule: GL in u after t = u^6
 constexpr int TQ_SING_G = 6;
+constexpr double TQ_SING_TURN = 0.2;  // largest tangent turning (rad) of an element that
+                                      // takes a whole-element singular rule
 constexpr int TQ_LMAX = 60;        // deepest dyadic level
 constexpr int TQ_NS_MAX = 16;
-constexpr int TQ_REFINE = 3;       // rounds of 128-point refinement of t*
+constexpr int TQ_REFINE = 3;       // rounds of 128-point refinement of t*: bracket ~2e-7
+constexpr int TQ_PARAB = 3;        // then parabolic rounds on the squared distance
 constexpr int TQ_RULE_SLOT = 128;  // nodes reserved per level of a compressed angular rule
-constexpr int TQ_RULE_MAXLEV = 30; // compressed rules serve levels 0..30: 2^-30 <= alpha < 2
+constexpr int TQ_RULE_MAXLEV = 52; // compressed rules serve levels 0..52: 2^-52 <= alpha < 2
+static_assert(kRuleLevels == TQ_RULE_MAXLEV + 1, "compiled-in rule tables and TQ_RULE_MAXLEV disagree");
 constexpr int TQ_SB = 64;          // s-nodes per batch
 constexpr int TQ_TRAP_KMAX = 8;    // trapezoidal angular rules of k N_theta nodes, k <= 8
 // aliasing bound of the trapezoidal rule: its error on G e^{i l theta} decays like
@@ -91,6 +98,9 @@ struct ElemGeo {
     double cl[3][TQ_NS_MAX + 2];   // centreline samples: c_i and C(-1), C(+1)
     double rho_max, speed_max, sgn, pad;
     double ag[33];                 // strip width a_g of J^2's zeros at t = -1 + q / 16
+    double spd[TQ_NS_MAX];         // |C'(t_i)|: the centreline's speed at the GL nodes
+    double rho[TQ_NS_MAX];         // radius of row i
+    double turn;                   // turning angle of the centreline's tangent over [-1, 1]
 };
 constexpr int TQ_AG_N = 33;
 
@@ -113,6 +123,13 @@ struct TQParams {
     // dtab[N_theta k (k - 1) / 2 + q], q < k N_theta
     const double *dtab;
     int kmax;
+    // whole-element singular rules (Sec. 3.2.4) for own-element targets: for aspect level
+    // b (2 |C'(t_i0)| / radius_i0 in [2^b, 2^(b+1)), slo <= b <= shi) and position i0, scnt[(b -
+    // slo) ns + i0] nodes from soff[...]: offsets sdel (t - t_i0) and weights swt; scnt null:
+    // none (dyadic panels and the graded panel next to t0 instead)
+    const int *scnt, *soff;
+    const double *sdel, *swt;
+    int slo, shi;
 };
 
 struct Item {
@@ -233,8 +250,32 @@ __global__ void k_elem_setup(long long nelem, TQParams p, const double *__restri
             for (int d = 0; d < 3; ++d)
                 v[d] += dl * g.c[d][m];
         }
-        speed = fmax(speed, sqrt(dot3(v, v)));
+        g.spd[i] = sqrt(dot3(v, v));
+        g.rho[i] = sqrt(0.5 * (g.a[0][i] * g.a[0][i] + g.a[1][i] * g.a[1][i] + g.a[2][i] * g.a[2][i]
+                               + g.b[0][i] * g.b[0][i] + g.b[1][i] * g.b[1][i] + g.b[2][i] * g.b[2][i]));
+        speed = fmax(speed, g.spd[i]);
     }
+    // tangent turning between consecutive GL nodes, scaled from [t_0, t_ns-1] to [-1, 1]
+    double turn = 0.0, tprev[3] = {0, 0, 0};
+    for (int i = 0; i < ns; ++i) {
+        double v[3] = {0, 0, 0};
+        for (int m = 0; m < ns; ++m) {
+            const double dl = dlag(p.tn, ns, m, p.tn[i]);
+            for (int d = 0; d < 3; ++d)
+                v[d] += dl * g.c[d][m];
+        }
+        const double inv = 1.0 / sqrt(dot3(v, v));
+        for (int d = 0; d < 3; ++d)
+            v[d] *= inv;
+        if (i > 0) {
+            const double cr[3] = {tprev[1] * v[2] - tprev[2] * v[1], tprev[2] * v[0] - tprev[0] * v[2],
+                                  tprev[0] * v[1] - tprev[1] * v[0]};
+            turn += atan2(sqrt(dot3(cr, cr)), dot3(tprev, v));
+        }
+        for (int d = 0; d < 3; ++d)
+            tprev[d] = v[d];
+    }
+    g.turn = turn * 2.0 / (p.tn[ns - 1] - p.tn[0]);
     // orientation: sign of (y_theta x y_t) . n at node (0, 0): y_theta = b_0, y_t = C'(t_0) + A'(t_0)
     double yt[3] = {0, 0, 0}, yth[3];
     for (int m = 0; m < ns; ++m) {
@@ -778,48 +819,54 @@ k_tube_items(TQParams p, const Item *__restrict__ items, const ElemGeo *__restri
     sincospi(2.0 * j0 / nt, &sj0, &cj0);
     __syncthreads();
 
-    // ---- nearest parameter t* of an element that does not hold x (sampling + refinement)
+    // ---- nearest parameter t* of an element that does not hold x: sampling, grid refinement,
+    // then parabolic refinement of the squared distance (smooth at its minimum even where
+    // the distance itself is not)
     double t0 = own ? p.tn[i0] : 0.0, dstar = 0.0;
     if (!own) {
+        // distance from x to the circle at parameter tt (closest angle by Newton)
+        auto dist_at = [&](double tt) {
+            double C[3] = {0, 0, 0}, A[3] = {0, 0, 0}, B[3] = {0, 0, 0};
+            for (int i = 0; i < ns; ++i) {
+                const double l = lag_fast(p, ns, i, tt);
+                for (int d = 0; d < 3; ++d) {
+                    C[d] += l * s.sc[d * ns + i];
+                    A[d] += l * s.sa[d * ns + i];
+                    B[d] += l * s.sb[d * ns + i];
+                }
+            }
+            const double dx[3] = {x[0] - C[0], x[1] - C[1], x[2] - C[2]};
+            double th = atan2(dot3(dx, B), dot3(dx, A));
+            for (int itn = 0; itn < 3; ++itn) {
+                double sn, cs;
+                sincos(th, &sn, &cs);
+                double ymx[3], yth[3], ythth[3];
+                for (int d = 0; d < 3; ++d) {
+                    ymx[d] = C[d] + A[d] * cs + B[d] * sn - x[d];
+                    yth[d] = -A[d] * sn + B[d] * cs;
+                    ythth[d] = -A[d] * cs - B[d] * sn;
+                }
+                const double fp = dot3(yth, yth) + dot3(ymx, ythth);
+                if (fp <= 0.0)
+                    break;
+                th -= dot3(ymx, yth) / fp;
+            }
+            double sn, cs;
+            sincos(th, &sn, &cs);
+            double r2 = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                const double v = C[d] + A[d] * cs + B[d] * sn - x[d];
+                r2 += v * v;
+            }
+            return sqrt(r2);
+        };
         double lo = -1.0, hi = 1.0, best_t = 0.0, best_d = 1e300;
         for (int round = 0; round <= TQ_REFINE; ++round) {
             const int np = round == 0 ? 65 : 128;
             double dist = 1e300, tt = 0.0;
             if (tid < np) {
                 tt = round == 0 ? -1.0 + 2.0 * tid / 64.0 : lo + (hi - lo) * tid / 127.0;
-                double C[3] = {0, 0, 0}, A[3] = {0, 0, 0}, B[3] = {0, 0, 0};
-                for (int i = 0; i < ns; ++i) {
-                    const double l = lag_fast(p, ns, i, tt);
-                    for (int d = 0; d < 3; ++d) {
-                        C[d] += l * s.sc[d * ns + i];
-                        A[d] += l * s.sa[d * ns + i];
-                        B[d] += l * s.sb[d * ns + i];
-                    }
-                }
-                const double dx[3] = {x[0] - C[0], x[1] - C[1], x[2] - C[2]};
-                double th = atan2(dot3(dx, B), dot3(dx, A));
-                for (int itn = 0; itn < 3; ++itn) {
-                    double sn, cs;
-                    sincos(th, &sn, &cs);
-                    double ymx[3], yth[3], ythth[3];
-                    for (int d = 0; d < 3; ++d) {
-                        ymx[d] = C[d] + A[d] * cs + B[d] * sn - x[d];
-                        yth[d] = -A[d] * sn + B[d] * cs;
-                        ythth[d] = -A[d] * cs - B[d] * sn;
-                    }
-                    const double fp = dot3(yth, yth) + dot3(ymx, ythth);
-                    if (fp <= 0.0)
-                        break;
-                    th -= dot3(ymx, yth) / fp;
-                }
-                double sn, cs;
-                sincos(th, &sn, &cs);
-                double r2 = 0.0;
-                for (int d = 0; d < 3; ++d) {
-                    const double v = C[d] + A[d] * cs + B[d] * sn - x[d];
-                    r2 += v * v;
-                }
-                dist = sqrt(r2);
+                dist = dist_at(tt);
             }
             s.SD[tid] = dist;
             s.RED[tid] = tt;
@@ -837,6 +884,43 @@ k_tube_items(TQParams p, const Item *__restrict__ items, const ElemGeo *__restri
             hi = nhi;
             __syncthreads();
         }
+        // parabolas through d^2 at best_t - h, best_t, best_t + h: the bracket of ~2e-7 shrinks
+        // to ~1e-13 in TQ_PARAB rounds of three evaluations
+        double h = 0.25 * (hi - lo);
+        for (int pr = 0; pr < TQ_PARAB && h > 0.0; ++pr) {
+            if (tid < 3) {
+                const double tt = fmin(1.0, fmax(-1.0, best_t + (tid - 1) * h));
+                const double dd = dist_at(tt);
+                s.SD[tid] = dd;
+                s.RED[tid] = tt;
+            }
+            __syncthreads();
+            const double f0 = s.SD[0] * s.SD[0], f1 = s.SD[1] * s.SD[1], f2 = s.SD[2] * s.SD[2];
+            // a clamped end point (t* at the element's end): no parabola
+            const bool clamped = s.RED[0] != s.RED[1] - h || s.RED[2] != s.RED[1] + h;
+            for (int q = 0; q < 3; ++q)
+                if (s.SD[q] < best_d) {
+                    best_d = s.SD[q];
+                    best_t = s.RED[q];
+                }
+            __syncthreads();
+            const double curv = f2 - 2.0 * f1 + f0;
+            if (!(curv > 0.0) || clamped)
+                break;
+            const double tv = s.RED[1] - h * fmin(1.0, fmax(-1.0, 0.5 * (f2 - f0) / curv));
+            if (tid == 0) {
+                const double tt = fmin(1.0, fmax(-1.0, tv));
+                s.SD[0] = dist_at(tt);
+                s.RED[0] = tt;
+            }
+            __syncthreads();
+            if (s.SD[0] < best_d) {
+                best_d = s.SD[0];
+                best_t = s.RED[0];
+            }
+            __syncthreads();
+            h *= 1.0 / 64.0;
+        }
         t0 = best_t;
         dstar = best_d;
     }
@@ -851,7 +935,25 @@ k_tube_items(TQParams p, const Item *__restrict__ items, const ElemGeo *__restri
         lev[side] = dyadic_levels(fabs(ell[side]) * speed, own ? rho_max : dstar);
         nside[side] = ell[side] == 0.0 ? 0 : (lev[side] + 1) * TQ_Q + (own ? TQ_SING_N - TQ_Q : 0);
     }
-    const int nsn = nside[0] + nside[1];
+    // own element: the whole-element singular rule of the element's local aspect ratio at
+    // t0, when one is compiled in for it and the element is nearly straight (the rules come
+    // from straight cylinders: within 7e-11 of the dyadic rule on slender-loop elements
+    // turning up to 0.15 rad, but 1e-8..3e-6 off on elements turning 0.4..1.3 rad)
+    int srule = -1, scount = 0;
+    if (own && p.scnt && g.turn <= TQ_SING_TURN) {
+        const double asp = 2.0 * g.spd[i0] / g.rho[i0];
+        if (asp > 0.0 && isfinite(asp)) {
+            const int b = static_cast<int>(floor(log2(asp)));
+            if (b >= p.slo && b <= p.shi) {
+                const int r = (b - p.slo) * ns + i0;
+                if (p.scnt[r] > 0) {
+                    srule = p.soff[r];
+                    scount = p.scnt[r];
+                }
+            }
+        }
+    }
+    const int nsn = srule >= 0 ? scount : nside[0] + nside[1];
     const int nb = max(2, (nt + 7) / 8);
     const double lb = PI_ / nb;
     const int NO = NC * MO;
@@ -886,8 +988,10 @@ k_tube_items(TQParams p, const Item *__restrict__ items, const ElemGeo *__restri
                 phi_ = ldexp(el, -kk);
             }
             const bool sing = own && pan == 0;
-            const double delta = sing ? phi_ * p.sx[q] : plo + (phi_ - plo) * p.gx[q];
-            const double wt = sing ? fabs(phi_) * p.sw[q] : fabs(phi_ - plo) * p.gw[q];
+            const double delta = srule >= 0 ? p.sdel[srule + gidx]
+                                 : sing ? phi_ * p.sx[q] : plo + (phi_ - plo) * p.gx[q];
+            const double wt = srule >= 0 ? p.swt[srule + gidx]
+                              : sing ? fabs(phi_) * p.sw[q] : fabs(phi_ - plo) * p.gw[q];
             const double t = t0 + delta;
             double L[TQ_NS_MAX], dL[TQ_NS_MAX];
             basis_at(p, ns, t, own, i0, delta, L, dL);
@@ -1369,6 +1473,10 @@ int build_tube_correction(long long nelem, int ns, int nt, long long ntot, const
     p.nt = nt;
     p.per = static_cast<int>(per);
     p.rphi = p.rw = nullptr;
+    p.scnt = p.soff = nullptr;
+    p.sdel = p.swt = nullptr;
+    p.slo = 0;
+    p.shi = -1;
     p.rcnt = nullptr;
     p.rnlev = 0;
     // weights of the trapezoidal rules of k N_theta nodes: D_k[q] = (1/N)(1 + 2 sum_{l=1}^{N/2-1}
@@ -1564,6 +1672,34 @@ int build_tube_correction(long long nelem, int ns, int nt, long long ntot, const
             rules_w = b_w.data();
             rules_cnt = b_cnt.data();
         }
+    }
+    // whole-element singular rules for own-element targets: the compiled-in table when it
+    // serves this ns and mode count (l0 >= nt / 2 + 4) and compressed rules are on
+    DevBuf d_scnt, d_soff, d_sdat;
+    std::vector<double> h_sdel, h_swt;
+    if (rules_nlev >= 0 && kSingTables && ns == kSingNs && nt / 2 + 4 <= kSingL0) {
+        const int nr = (kSingHi - kSingLo + 1) * kSingNs;
+        int tot = 0;
+        for (int r = 0; r < nr; ++r)
+            tot = std::max(tot, kSingOff[r] + kSingCnt[r]);
+        h_sdel.resize(2 * static_cast<size_t>(tot));
+        for (int m = 0; m < tot; ++m) {
+            h_sdel[m] = kSingData[2 * m];
+            h_sdel[tot + m] = kSingData[2 * m + 1];
+        }
+        SBQ_TRY(d_scnt.alloc(nr * sizeof(int)));
+        SBQ_TRY(d_soff.alloc(nr * sizeof(int)));
+        SBQ_TRY(d_sdat.alloc(2 * static_cast<size_t>(tot) * sizeof(double)));
+        SBQ_CUDA(cudaMemcpyAsync(d_scnt.p, kSingCnt, nr * sizeof(int), cudaMemcpyHostToDevice, s));
+        SBQ_CUDA(cudaMemcpyAsync(d_soff.p, kSingOff, nr * sizeof(int), cudaMemcpyHostToDevice, s));
+        SBQ_CUDA(cudaMemcpyAsync(d_sdat.p, h_sdel.data(), 2 * static_cast<size_t>(tot) * sizeof(double),
+                                 cudaMemcpyHostToDevice, s));
+        p.scnt = d_scnt.as<int>();
+        p.soff = d_soff.as<int>();
+        p.sdel = d_sdat.as<double>();
+        p.swt = d_sdat.as<double>() + tot;
+        p.slo = kSingLo;
+        p.shi = kSingHi;
     }
     DevBuf d_rphi, d_rw, d_rcnt;
     if (rules_nlev > 0) {

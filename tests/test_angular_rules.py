@@ -17,9 +17,11 @@ def test_table_layout():
     assert tab is not None
     phi, w, cnt, l0 = tab
     assert l0 >= 9
-    assert phi.shape == (31, 128) and w.shape == (31, 128) and cnt.shape == (31,)
+    nl = angular_rules.LEVELS + 1
+    assert nl == 53
+    assert phi.shape == (nl, 128) and w.shape == (nl, 128) and cnt.shape == (nl,)
     assert np.all(cnt > 0) and np.all(cnt <= 128)
-    for lev in range(0, 31):
+    for lev in range(0, nl):
         n = cnt[lev]
         assert np.all(np.abs(phi[lev, :n]) <= math.pi) and np.all(np.isfinite(w[lev, :n]))
     # the rules integrate the kernel times e^{i l theta}, not functions without the kernel's
@@ -28,7 +30,7 @@ def test_table_layout():
         assert abs(w[lev, :cnt[lev]].sum() - 2 * math.pi) < 1e-9
 
 
-@pytest.mark.parametrize("lev", [0, 1, 8, 12, 16, 19, 24, 30])
+@pytest.mark.parametrize("lev", [0, 1, 8, 12, 16, 19, 24, 30, 36, 44, 52])
 def test_table_integrates_the_stokes_family(lev):
     """Unseen annulus targets at relative distance 2^-lev..2^(1-lev): every Stokes single- and
     double-layer component (normals along the circle's radius and along its axis) times

@@ -115,9 +115,9 @@ def test_tube_correction_rules_validation_on_host(libsbq):
     libsbq.sbq_last_error.restype = ctypes.c_char_p
     fake = vp(16)
     nnz = i64(0)
-    phi = (ctypes.c_double * (31 * 128))()
-    w = (ctypes.c_double * (31 * 128))()
-    cnt = (ctypes.c_int * 31)()
+    phi = (ctypes.c_double * (53 * 128))()
+    w = (ctypes.c_double * (53 * 128))()
+    cnt = (ctypes.c_int * 53)()
 
     def call(nlev, l0=9, p=phi, ww=w, c=cnt):
         return f(4, 8, 16, 512, fake, fake, fake, 0, None, 0, 1.0, 1.0, 0.5, nlev, l0,
@@ -125,16 +125,16 @@ def test_tube_correction_rules_validation_on_host(libsbq):
                  None, None, None, None)
 
     assert call(-1) == 1 and b"nlev" in libsbq.sbq_last_error()
-    assert call(32) == 1
-    assert call(31, l0=8) == 1 and b"l0" in libsbq.sbq_last_error()   # N_theta 16 needs l0 >= 9
+    assert call(54) == 1
+    assert call(53, l0=8) == 1 and b"l0" in libsbq.sbq_last_error()   # N_theta 16 needs l0 >= 9
     cnt[3] = 129
-    assert call(31) == 1 and b"128" in libsbq.sbq_last_error()
+    assert call(53) == 1 and b"128" in libsbq.sbq_last_error()
     cnt[3] = 2
     phi[3 * 128 + 1] = 4.0                      # offset outside [-pi, pi]
-    assert call(31) == 1 and b"pi" in libsbq.sbq_last_error()
+    assert call(53) == 1 and b"pi" in libsbq.sbq_last_error()
     phi[3 * 128 + 1] = 0.5
     w[3 * 128] = float("nan")
-    assert call(31) == 1
+    assert call(53) == 1
 
 
 def test_slender_eta_on_host(libsbq):
