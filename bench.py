@@ -1441,7 +1441,7 @@ def run_quadrature(args):
                       "items_per_s": items / (ms * 1e-3),
                       "unknowns_per_s": 3 * s.size / (ms * 1e-3),
                       "roofline": {"bound": "fp64", "profile":
-                                   "profiles/tube_correction_stokes_random_loop_8192.md"},
+                                   "profiles/tube_correction_stokes_random_loop_32768.md"},
                       "cpu_baseline": {"kind": "oracle", "value": o_items / sec,
                                        "unit": "(target, element) items/s", "cores": 1,
                                        "sample": "%d targets, %d items of the same E in %.1f s "
