@@ -102,3 +102,20 @@ def test_random_loop_is_a_valid_slender_body():
     A0 = rng.standard_normal((3, 10)) * sd[None, :]
     B0 = rng.standard_normal((3, 10)) * sd[None, :]
     assert I._loop_max_curvature_radius(k, A0, B0) > 1.0
+
+
+def test_helix_pitch_two_turns_overlap():
+    """The helix wall of the benchmark (radius 3, pitch 2, tube radius 1): the centrelines of
+    adjacent turns are about pitch x cos(helix angle) = 1.989 apart, less than the tube diameter, so
+    at pitch 2 the turns interpenetrate (the solve workload runs at pitch 3, 2.98 apart)."""
+    a, R = 3.0, 1.0
+    for pitch, overlap in ((2.0, True), (3.0, False)):
+        b = pitch / (2.0 * np.pi)
+        p = np.linspace(0.0, 8.0 * np.pi, 80001)
+        c = np.stack([a * np.cos(p), a * np.sin(p), b * p])
+        p0 = 4.0 * np.pi
+        x0 = np.array([a * np.cos(p0), a * np.sin(p0), b * p0])
+        far = np.abs(p - p0) > np.pi
+        dmin = np.linalg.norm(c[:, far] - x0[:, None], axis=0).min()
+        assert abs(dmin - pitch * math.cos(math.atan(pitch / (2.0 * math.pi * a)))) < 1e-4
+        assert (dmin < 2.0 * R) == overlap
