@@ -76,7 +76,7 @@ def parse(argv=None):
                          "subtraction)")
     ap.add_argument("--workload", default="headline",
                     choices=["headline", "curved_pipe", "precision_sweep", "batch", "helix",
-                             "laplace", "mobility", "quadrature", "peaks"],
+                             "laplace", "mobility", "quadrature", "peaks", "tree"],
                     help="headline: the benchmark line (default, helix apply); curved_pipe: "
                          "GMRES-IR solves as the step; precision_sweep: FP32 vs compensated "
                          "FP32 vs FP64 pair sums on random loops of 64K/256K/1M nodes; batch: "
@@ -1478,6 +1478,64 @@ def run_peaks(args):
     return 0
 
 
+def run_tree(args):
+    """Far-field acceleration: the treecode for the single-layer sum (stokes_sl_tree_*) on the
+    slender random loop at 1,048,576 and 4,194,304 nodes (Sec. 5.2 recipe), against the plain
+    FP32 direct sum: apply times (CUDA events, median of the repetitions), kernel evaluations
+    per apply, and the error of each on 2,048 sampled rows against the FP64 direct sum."""
+    import torch
+    import numpy as np
+    from paper_2310_00889_gb300 import build as b
+    b.build()
+    from paper_2310_00889_gb300 import sbq, inputs as I
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(7)
+
+    def t(a):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+    def timed(fn, reps):
+        out, ms = None, []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return out, float(np.median(ms))
+
+    rows = []
+    for panels in (8192, 32768):
+        s = I.random_loop(seed=1, panels=panels, ns=8, nth=16)
+        n = s.size
+        src, w = t(s.x), t(s.w)
+        sig = t(rng.standard_normal((3, n)))
+        sub = np.sort(rng.choice(n, 2048, replace=False))
+        ref = sbq.sl_apply(src, w, sig, t(s.x[:, sub]), prec="fp64").cpu().numpy()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tree = sbq.SlTree(src, w, theta=0.5, order=8)
+        torch.cuda.synchronize()
+        setup_ms = (time.perf_counter() - t0) * 1e3
+        u, tree_ms = timed(lambda: tree.apply(sig), 5)
+        err_tree = float(np.abs(u.cpu().numpy()[:, sub] - ref).max() / np.abs(ref).max())
+        st = tree.stats()
+        tree.close()
+        ud, direct_ms = timed(lambda: sbq.sl_apply(src, w, sig, src, prec="fp32"), 2 if n <= 2 ** 21 else 1)
+        err_direct = float(np.abs(ud.cpu().numpy()[:, sub] - ref).max() / np.abs(ref).max())
+        del ud, u
+        torch.cuda.empty_cache()
+        rows.append({"nodes": n, "theta": 0.5, "order": 8, "setup_ms": setup_ms, "apply_ms": tree_ms,
+                     "kernel_evaluations": st["pairs"], "direct_pairs": float(n) * n,
+                     "cells": st["cells"], "proxies": st["proxies"], "list_entries": st["entries"],
+                     "err_vs_fp64": err_tree, "direct_fp32_ms": direct_ms,
+                     "direct_fp32_err_vs_fp64": err_direct, "speedup": direct_ms / tree_ms})
+    print(json.dumps({"workload": "treecode_single_layer_random_loop", "rows": rows}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1498,6 +1556,8 @@ def main():
         return run_peaks(args)
     if args.workload == "curved_pipe":
         return run_curved_pipe(args)
+    if args.workload == "tree":
+        return run_tree(args)
     return run_headline(args)
 
 

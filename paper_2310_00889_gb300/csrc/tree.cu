@@ -1,0 +1,691 @@
+// Far-field acceleration of the Stokes single-layer sum for large N (the paper evaluates its
+// far field with an FMM, Sec. 3.2, and states the O(N^2) direct cost it replaces, Sec. 3.4):
+// a barycentric Lagrange treecode on the GPU.
+//
+// Setup (host, once per geometry): an octree over the sources (Morton order, tight boxes,
+// leaves of at most TR_LEAF sources) and one over the targets (the same tree when the
+// targets are the sources); every cell gets a tensor grid of Chebyshev points of the second
+// kind on its box, n_d points along dimension d with n_d ~ order * (h_d / h_max)^(1/3) (a
+// slender cell needs few points across); targets in blocks of up to 128 consecutive points
+// in Morton order inside one cell of at most 512 targets, and for every block a list: the proxy grid of every cell that is far
+// (acceptance: distance between the centres minus the block's radius >= cell radius /
+// theta, and the cell holds more sources than proxies) and the sources of every leaf it
+// reaches.
+// Apply (GPU, per density): charges q_k = w_k sigma_k; proxy charges of every cell,
+// q_m = sum_k L_m(y_k) q_k with L_m the tensor Lagrange basis of the grid (barycentric
+// form); then one CTA per target block sums the Stokeslet over its list, each list entry in
+// FP32 and the entries' sums in FP64.  Positions are kept in FP32 relative to the centre of
+// their leaf (sources), block (targets) or cell (proxies), and each entry carries the offset
+// between its frame and the target block's, so that near pairs lose no digits to large
+// absolute coordinates.
+#include "engine.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+struct sbq_tree_s {
+    uint32_t magic = 0x53425454u;   // "SBTT"
+    int device = 0;
+    long long ns = 0, nt = 0;
+    bool same = false;              // targets are the sources (one tree, self pairs excluded)
+    double theta = 0.0;
+    int order = 0;
+    long long n_cells = 0, n_proxies = 0, n_entries = 0, n_tleaves = 0;
+    double pairs = 0.0;             // kernel evaluations per apply
+    int max_level = 0;
+    // device data
+    sbq::DevBuf perm_s, perm_t;     // sorted position -> original index
+    sbq::DevBuf w_sorted;           // FP64 weights, sorted order
+    sbq::DevBuf src_loc;            // float4: source - its leaf centre (sorted order)
+    sbq::DevBuf src_abs;            // double: absolute source positions (3 x ns, sorted)
+    sbq::DevBuf trg_loc;            // float4: target - its leaf centre (sorted order)
+    sbq::DevBuf q;                  // float4 charges, sorted order
+    sbq::DevBuf cells;              // TrCellDev per cell
+    sbq::DevBuf prox_loc;           // float4: proxy - its cell centre
+    sbq::DevBuf prox_q;             // float4 proxy charges
+    sbq::DevBuf chunks;             // int4 (cell, first source, count, 0): P2M work items
+    long long n_chunks = 0;
+    sbq::DevBuf tleaf;              // int4 (first target, count, first entry, entry count)
+    sbq::DevBuf entries;            // TrEntry
+};
+
+namespace sbq {
+
+namespace {
+
+constexpr int TR_LEAF = 128;       // sources (targets) per leaf at most
+constexpr int TR_NMAX = 16;        // proxy points per dimension at most
+constexpr int TR_THREADS = 128;
+constexpr int TR_CHUNK = 512;      // sources per P2M work item
+constexpr int TR_BLOCKCELL = 512;  // target blocks: runs of TR_THREADS inside cells this small
+constexpr int TR_MAXLEV = 21;
+constexpr double TR_PI = 3.14159265358979323846;
+
+struct TrCellDev {
+    double c[3], h[3];
+    int n[3], pfirst;
+};
+
+struct TrEntry {
+    int first, count, kind, pad;   // kind 0: sources [first, first + count); 1: proxies
+    float dx, dy, dz, pad2;        // block frame centre minus target leaf centre
+};
+
+struct HostCell {
+    double c[3], h[3], rad;
+    int first, count, level;
+    int child[8], nchild;
+    int n[3], pfirst, nprox;
+};
+
+struct HostTree {
+    std::vector<int> perm;          // sorted position -> original index
+    std::vector<HostCell> cells;    // cells[0] is the root
+    std::vector<int> leaf_of;       // sorted position -> leaf cell
+    std::vector<int> leaves;        // leaf cells in sorted order
+};
+
+inline uint64_t spread21(uint64_t v)
+{
+    v &= 0x1fffffULL;
+    v = (v | (v << 32)) & 0x1f00000000ffffULL;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffULL;
+    v = (v | (v << 8)) & 0x100f00f00f00f00fULL;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ULL;
+    v = (v | (v << 2)) & 0x1249249249249249ULL;
+    return v;
+}
+
+// Octree over n points (SoA x, y, z): Morton sort, then cells split by the next three key
+// bits until at most `leaf` points remain; tight boxes.
+void build_host_tree(const std::vector<double> &x, long long n, int leaf, HostTree &T)
+{
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (long long k = 0; k < n; ++k)
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = std::min(lo[d], x[d * n + k]);
+            hi[d] = std::max(hi[d], x[d * n + k]);
+        }
+    double ext = 0.0;
+    for (int d = 0; d < 3; ++d)
+        ext = std::max(ext, hi[d] - lo[d]);
+    ext = ext > 0.0 ? ext * (1.0 + 1e-9) : 1.0;
+    std::vector<uint64_t> key(n);
+    for (long long k = 0; k < n; ++k) {
+        uint64_t kk = 0;
+        for (int d = 0; d < 3; ++d) {
+            double u = (x[d * n + k] - lo[d]) / ext * 2097152.0;
+            uint64_t q = static_cast<uint64_t>(std::min(std::max(u, 0.0), 2097151.0));
+            kk |= spread21(q) << (2 - d);
+        }
+        key[k] = kk;
+    }
+    T.perm.resize(n);
+    std::iota(T.perm.begin(), T.perm.end(), 0);
+    std::sort(T.perm.begin(), T.perm.end(), [&](int a, int b) {
+        return key[a] < key[b] || (key[a] == key[b] && a < b);
+    });
+    T.cells.clear();
+    T.leaves.clear();
+    T.leaf_of.assign(n, -1);
+    // iterative build: (cell index) work stack
+    HostCell root{};
+    root.first = 0;
+    root.count = static_cast<int>(n);
+    root.level = 0;
+    T.cells.push_back(root);
+    std::vector<int> stack{0};
+    while (!stack.empty()) {
+        const int ci = stack.back();
+        stack.pop_back();
+        HostCell c = T.cells[ci];
+        double blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int k = c.first; k < c.first + c.count; ++k)
+            for (int d = 0; d < 3; ++d) {
+                const double v = x[d * n + T.perm[k]];
+                blo[d] = std::min(blo[d], v);
+                bhi[d] = std::max(bhi[d], v);
+            }
+        double r2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            c.c[d] = 0.5 * (blo[d] + bhi[d]);
+            c.h[d] = 0.5 * (bhi[d] - blo[d]);
+            r2 += c.h[d] * c.h[d];
+        }
+        c.rad = std::sqrt(r2);
+        c.nchild = 0;
+        if (c.count > leaf && c.level < TR_MAXLEV) {
+            const int shift = 3 * (TR_MAXLEV - 1 - c.level);
+            int b = c.first;
+            while (b < c.first + c.count) {
+                const uint64_t oct = (key[T.perm[b]] >> shift) & 7ULL;
+                int e = b;
+                while (e < c.first + c.count && ((key[T.perm[e]] >> shift) & 7ULL) == oct)
+                    ++e;
+                HostCell ch{};
+                ch.first = b;
+                ch.count = e - b;
+                ch.level = c.level + 1;
+                c.child[c.nchild++] = static_cast<int>(T.cells.size());
+                T.cells.push_back(ch);
+                b = e;
+            }
+            // a cell whose points share one octant keeps splitting through its child
+        }
+        T.cells[ci] = c;
+        if (c.nchild == 0) {
+            T.leaves.push_back(ci);
+            for (int k = c.first; k < c.first + c.count; ++k)
+                T.leaf_of[k] = ci;
+        } else {
+            for (int k = c.nchild - 1; k >= 0; --k)
+                stack.push_back(c.child[k]);
+        }
+    }
+    std::sort(T.leaves.begin(), T.leaves.end(),
+              [&](int a, int b) { return T.cells[a].first < T.cells[b].first; });
+}
+
+// ---------------------------------------------------------------------------------------
+// device kernels
+
+// Chebyshev point j of n (second kind) on [-1, 1]; barycentric weight
+__device__ __forceinline__ double cheb_pt(int j, int n)
+{
+    return n > 1 ? cospi(static_cast<double>(j) / (n - 1)) : 0.0;
+}
+
+__device__ __forceinline__ double cheb_w(int j, int n)
+{
+    double w = (j & 1) ? -1.0 : 1.0;
+    if (j == 0 || j == n - 1)
+        w *= 0.5;
+    return w;
+}
+
+// 1D Lagrange basis values of the n-point grid at xi (barycentric form; exact at nodes)
+__device__ void lagrange_1d(double xi, int n, float *out)
+{
+    if (n == 1) {
+        out[0] = 1.0f;
+        return;
+    }
+    double den = 0.0;
+    int hit = -1;
+    double t[TR_NMAX];
+    for (int j = 0; j < n; ++j) {
+        const double d = xi - cheb_pt(j, n);
+        if (d == 0.0) {
+            hit = j;
+            break;
+        }
+        t[j] = cheb_w(j, n) / d;
+        den += t[j];
+    }
+    for (int j = 0; j < n; ++j)
+        out[j] = hit >= 0 ? (j == hit ? 1.0f : 0.0f) : static_cast<float>(t[j] / den);
+}
+
+// q_k = w_k sigma_k (FP32), sorted order
+__global__ void k_tree_charges(long long ns, const int *__restrict__ perm, const double *__restrict__ w,
+                               const double *__restrict__ sigma, float4 *q)
+{
+    const long long k = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (k >= ns)
+        return;
+    const long long o = perm[k];
+    const double ww = w[k];
+    q[k] = make_float4(static_cast<float>(ww * sigma[o]), static_cast<float>(ww * sigma[ns + o]),
+                       static_cast<float>(ww * sigma[2 * ns + o]), 0.0f);
+}
+
+// proxy charges of one cell from one chunk of its sources (atomically accumulated)
+__global__ void __launch_bounds__(TR_THREADS)
+k_tree_p2m(const int4 *__restrict__ chunks, const TrCellDev *__restrict__ cells,
+           const double *__restrict__ src_abs, long long ns, const float4 *__restrict__ q,
+           float4 *prox_q)
+{
+    __shared__ float Lx[TR_THREADS][TR_NMAX], Ly[TR_THREADS][TR_NMAX], Lz[TR_THREADS][TR_NMAX];
+    __shared__ float4 sq[TR_THREADS];
+    const int4 ck = chunks[blockIdx.x];
+    const TrCellDev c = cells[ck.x];
+    const int np = c.n[0] * c.n[1] * c.n[2];
+    float acc[8][3];
+    constexpr int MPT = 8;   // proxies per thread: 8 x 128 = 1024 >= 10^3, the largest grid
+    for (int m = 0; m < MPT; ++m)
+        acc[m][0] = acc[m][1] = acc[m][2] = 0.0f;
+    for (int base = 0; base < ck.z; base += TR_THREADS) {
+        const int k = base + threadIdx.x;
+        if (k < ck.z) {
+            const long long s = ck.y + k;
+            double xi[3];
+            for (int d = 0; d < 3; ++d)
+                xi[d] = c.h[d] > 0.0 ? (src_abs[d * ns + s] - c.c[d]) / c.h[d] : 0.0;
+            lagrange_1d(xi[0], c.n[0], Lx[threadIdx.x]);
+            lagrange_1d(xi[1], c.n[1], Ly[threadIdx.x]);
+            lagrange_1d(xi[2], c.n[2], Lz[threadIdx.x]);
+            sq[threadIdx.x] = q[s];
+        } else {
+            sq[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int j = 0; j < TR_NMAX; ++j)
+                Lx[threadIdx.x][j] = Ly[threadIdx.x][j] = Lz[threadIdx.x][j] = 0.0f;
+        }
+        __syncthreads();
+        const int cnt = min(TR_THREADS, ck.z - base);
+        for (int m = 0; m < MPT; ++m) {
+            const int pm = threadIdx.x + m * TR_THREADS;
+            if (pm >= np)
+                break;
+            const int a = pm / (c.n[1] * c.n[2]), b = (pm / c.n[2]) % c.n[1], cc = pm % c.n[2];
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+            for (int kk = 0; kk < cnt; ++kk) {
+                const float l = Lx[kk][a] * Ly[kk][b] * Lz[kk][cc];
+                const float4 qq = sq[kk];
+                s0 = fmaf(l, qq.x, s0);
+                s1 = fmaf(l, qq.y, s1);
+                s2 = fmaf(l, qq.z, s2);
+            }
+            acc[m][0] += s0;
+            acc[m][1] += s1;
+            acc[m][2] += s2;
+        }
+        __syncthreads();
+    }
+    for (int m = 0; m < MPT; ++m) {
+        const int pm = threadIdx.x + m * TR_THREADS;
+        if (pm >= np)
+            break;
+        float4 *dst = prox_q + c.pfirst + pm;
+        atomicAdd(&dst->x, acc[m][0]);
+        atomicAdd(&dst->y, acc[m][1]);
+        atomicAdd(&dst->z, acc[m][2]);
+    }
+}
+
+// Stokeslet sums: one CTA per target block, one thread per target; list entries staged in
+// shared memory 128 points at a time
+__global__ void __launch_bounds__(TR_THREADS)
+k_tree_eval(const int4 *__restrict__ tleaf, const TrEntry *__restrict__ entries,
+            const float4 *__restrict__ trg_loc, const float4 *__restrict__ src_loc,
+            const float4 *__restrict__ q, const float4 *__restrict__ prox_loc,
+            const float4 *__restrict__ prox_q, const int *__restrict__ perm_t, long long nt,
+            int same, double *u)
+{
+    __shared__ float4 sp[TR_THREADS], sq[TR_THREADS];
+    const int4 tl = tleaf[blockIdx.x];
+    const int t = threadIdx.x;
+    const bool live = t < tl.y;
+    const float4 x = live ? trg_loc[tl.x + t] : make_float4(0.f, 0.f, 0.f, 0.f);
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+    for (int e = 0; e < tl.w; ++e) {
+        float u0 = 0.f, u1 = 0.f, u2 = 0.f;   // this block's sum in FP32, the total in FP64
+        const TrEntry en = entries[tl.z + e];
+        const float4 *P = en.kind ? prox_loc : src_loc;
+        const float4 *Q = en.kind ? prox_q : q;
+        // target in the block's frame
+        const float xx = x.x - en.dx, xy = x.y - en.dy, xz = x.z - en.dz;
+        for (int base = 0; base < en.count; base += TR_THREADS) {
+            const int k = base + t;
+            if (k < en.count) {
+                sp[t] = P[en.first + k];
+                sq[t] = Q[en.first + k];
+            }
+            __syncthreads();
+            const int cnt = min(TR_THREADS, en.count - base);
+            // the target's own node (same tree, a source block): its sorted index
+            const int self = (same && en.kind == 0) ? tl.x + t - en.first - base : -1;
+            for (int kk = 0; kk < cnt; ++kk) {
+                const float4 y = sp[kk], qq = sq[kk];
+                const float r0 = xx - y.x, r1 = xy - y.y, r2 = xz - y.z;
+                const float rr = fmaf(r0, r0, fmaf(r1, r1, r2 * r2));
+                if (kk != self && rr > 0.0f) {
+                    const float ri = rsqrtf(rr);
+                    const float ri3 = ri * ri * ri;
+                    const float rq = fmaf(r0, qq.x, fmaf(r1, qq.y, r2 * qq.z)) * ri3;
+                    u0 = fmaf(qq.x, ri, fmaf(r0, rq, u0));
+                    u1 = fmaf(qq.y, ri, fmaf(r1, rq, u1));
+                    u2 = fmaf(qq.z, ri, fmaf(r2, rq, u2));
+                }
+            }
+            __syncthreads();
+        }
+        v0 += u0;
+        v1 += u1;
+        v2 += u2;
+    }
+    if (live) {
+        const long long o = perm_t[tl.x + t];
+        const double f = 1.0 / (8.0 * TR_PI);
+        u[o] = f * v0;
+        u[nt + o] = f * v1;
+        u[2 * nt + o] = f * v2;
+    }
+}
+
+int proxies_per_dim(const HostCell &c, int order, int n[3])
+{
+    const double hm = std::max(c.h[0], std::max(c.h[1], c.h[2]));
+    for (int d = 0; d < 3; ++d) {
+        if (c.h[d] <= 0.0 || hm <= 0.0) {
+            n[d] = 1;
+            continue;
+        }
+        const int v = static_cast<int>(std::ceil(order * std::cbrt(c.h[d] / hm)));
+        n[d] = std::max(2, std::min(order, v));
+    }
+    return n[0] * n[1] * n[2];
+}
+
+}  // namespace
+
+static int tree_create_impl(long long ns, const double *src, const double *w, long long nt,
+                            const double *trg, double theta, int order, sbq_tree_s *T,
+                            cudaStream_t s)
+{
+    T->ns = ns;
+    T->nt = nt;
+    T->same = trg == src && nt == ns;
+    T->theta = theta;
+    T->order = order;
+    std::vector<double> hs(3 * ns), hw(ns), ht;
+    SBQ_CUDA(cudaMemcpyAsync(hs.data(), src, 3 * ns * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SBQ_CUDA(cudaMemcpyAsync(hw.data(), w, ns * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (!T->same) {
+        ht.resize(3 * nt);
+        SBQ_CUDA(cudaMemcpyAsync(ht.data(), trg, 3 * nt * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    SBQ_CUDA(cudaStreamSynchronize(s));
+    HostTree S, TT;
+    build_host_tree(hs, ns, TR_LEAF, S);
+    if (!T->same)
+        build_host_tree(ht, nt, TR_LEAF, TT);
+    const HostTree &Tt = T->same ? S : TT;
+    const std::vector<double> &xt = T->same ? hs : ht;
+
+    // proxies of every cell
+    long long np = 0;
+    for (HostCell &c : S.cells) {
+        c.nprox = proxies_per_dim(c, order, c.n);
+        c.pfirst = static_cast<int>(np);
+        np += c.nprox;
+        T->max_level = std::max(T->max_level, c.level);
+    }
+    if (np > 0x7fffffffLL) {
+        set_error("stokes_sl_tree_create: too many proxy points");
+        return SBQ_EINVAL;
+    }
+    std::vector<float4> h_ploc(np);
+    std::vector<TrCellDev> h_cells(S.cells.size());
+    for (size_t ci = 0; ci < S.cells.size(); ++ci) {
+        const HostCell &c = S.cells[ci];
+        TrCellDev &dc = h_cells[ci];
+        for (int d = 0; d < 3; ++d) {
+            dc.c[d] = c.c[d];
+            dc.h[d] = c.h[d];
+            dc.n[d] = c.n[d];
+        }
+        dc.pfirst = c.pfirst;
+        for (int a = 0; a < c.n[0]; ++a)
+            for (int b = 0; b < c.n[1]; ++b)
+                for (int e = 0; e < c.n[2]; ++e) {
+                    const int m = (a * c.n[1] + b) * c.n[2] + e;
+                    auto pt = [](int j, int n) {
+                        return n > 1 ? std::cos(TR_PI * j / (n - 1)) : 0.0;
+                    };
+                    h_ploc[c.pfirst + m] = make_float4(static_cast<float>(c.h[0] * pt(a, c.n[0])),
+                                                       static_cast<float>(c.h[1] * pt(b, c.n[1])),
+                                                       static_cast<float>(c.h[2] * pt(e, c.n[2])), 0.0f);
+                }
+    }
+    // sources: FP32 offsets from their leaf's centre, FP64 absolute positions, weights
+    std::vector<float4> h_sloc(ns);
+    std::vector<double> h_sabs(3 * ns), h_ws(ns);
+    for (long long k = 0; k < ns; ++k) {
+        const int o = S.perm[k];
+        const HostCell &L = S.cells[S.leaf_of[k]];
+        h_sloc[k] = make_float4(static_cast<float>(hs[o] - L.c[0]), static_cast<float>(hs[ns + o] - L.c[1]),
+                                static_cast<float>(hs[2 * ns + o] - L.c[2]), 0.0f);
+        for (int d = 0; d < 3; ++d)
+            h_sabs[d * ns + k] = hs[d * ns + o];
+        h_ws[k] = hw[o];
+    }
+    // target blocks: runs of TR_THREADS consecutive targets in Morton order, each with its
+    // own tight box; target positions in FP32 relative to their block's centre
+    struct TBlock {
+        double c[3], rad;
+        int first, count;
+    };
+    // (runs never leave a cell of at most TR_BLOCKCELL targets, so that a block is as compact
+    // as such a cell: a run across a jump of the Morton order would be spread over the domain
+    // and its FP32 offsets would lose the digits the near pairs need)
+    std::vector<TBlock> tb;
+    std::vector<float4> h_tloc(nt);
+    std::vector<std::pair<int, int>> runs;
+    {
+        std::vector<int> st{0};
+        while (!st.empty()) {
+            const HostCell &C = Tt.cells[st.back()];
+            st.pop_back();
+            if (C.count <= TR_BLOCKCELL || C.nchild == 0) {
+                for (int b = 0; b < C.count; b += TR_THREADS)
+                    runs.emplace_back(C.first + b, std::min(TR_THREADS, C.count - b));
+            } else {
+                for (int k = C.nchild - 1; k >= 0; --k)
+                    st.push_back(C.child[k]);
+            }
+        }
+    }
+    for (const auto &run : runs) {
+        TBlock B{};
+        B.first = run.first;
+        B.count = run.second;
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int k = B.first; k < B.first + B.count; ++k)
+            for (int d = 0; d < 3; ++d) {
+                const double v = xt[d * nt + Tt.perm[k]];
+                lo[d] = std::min(lo[d], v);
+                hi[d] = std::max(hi[d], v);
+            }
+        double r2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            B.c[d] = 0.5 * (lo[d] + hi[d]);
+            r2 += 0.25 * (hi[d] - lo[d]) * (hi[d] - lo[d]);
+        }
+        B.rad = std::sqrt(r2);
+        for (int k = B.first; k < B.first + B.count; ++k) {
+            const int o = Tt.perm[k];
+            h_tloc[k] = make_float4(static_cast<float>(xt[o] - B.c[0]), static_cast<float>(xt[nt + o] - B.c[1]),
+                                    static_cast<float>(xt[2 * nt + o] - B.c[2]), 0.0f);
+        }
+        tb.push_back(B);
+    }
+    // P2M work items: every cell, its sources in chunks
+    std::vector<int4> h_chunks;
+    for (size_t ci = 0; ci < S.cells.size(); ++ci) {
+        const HostCell &c = S.cells[ci];
+        for (int b = 0; b < c.count; b += TR_CHUNK)
+            h_chunks.push_back(make_int4(static_cast<int>(ci), c.first + b, std::min(TR_CHUNK, c.count - b), 0));
+    }
+    // lists: per target block, a traversal of the source tree
+    std::vector<int4> h_tleaf;
+    std::vector<TrEntry> h_ent;
+    double pairs = 0.0;
+    std::vector<int> stack;
+    for (const TBlock &L : tb) {
+        const int e0 = static_cast<int>(h_ent.size());
+        stack.assign(1, 0);
+        while (!stack.empty()) {
+            const HostCell &C = S.cells[stack.back()];
+            stack.pop_back();
+            double d2 = 0.0;
+            for (int d = 0; d < 3; ++d)
+                d2 += (C.c[d] - L.c[d]) * (C.c[d] - L.c[d]);
+            const double dist = std::sqrt(d2) - L.rad;
+            if (dist * theta >= C.rad && C.count > C.nprox) {
+                TrEntry en{C.pfirst, C.nprox, 1, 0, static_cast<float>(C.c[0] - L.c[0]),
+                           static_cast<float>(C.c[1] - L.c[1]), static_cast<float>(C.c[2] - L.c[2]), 0.f};
+                h_ent.push_back(en);
+                pairs += static_cast<double>(C.nprox) * L.count;
+            } else if (C.nchild == 0) {
+                TrEntry en{C.first, C.count, 0, 0, static_cast<float>(C.c[0] - L.c[0]),
+                           static_cast<float>(C.c[1] - L.c[1]), static_cast<float>(C.c[2] - L.c[2]), 0.f};
+                h_ent.push_back(en);
+                pairs += static_cast<double>(C.count) * L.count;
+            } else {
+                for (int k = C.nchild - 1; k >= 0; --k)
+                    stack.push_back(C.child[k]);
+            }
+        }
+        h_tleaf.push_back(make_int4(L.first, L.count, e0, static_cast<int>(h_ent.size()) - e0));
+    }
+    T->n_cells = static_cast<long long>(S.cells.size());
+    T->n_proxies = np;
+    T->n_entries = static_cast<long long>(h_ent.size());
+    T->n_tleaves = static_cast<long long>(h_tleaf.size());
+    T->n_chunks = static_cast<long long>(h_chunks.size());
+    T->pairs = pairs;
+
+    SBQ_TRY(T->perm_s.alloc(ns * sizeof(int)));
+    SBQ_TRY(T->perm_t.alloc(nt * sizeof(int)));
+    SBQ_TRY(T->w_sorted.alloc(ns * sizeof(double)));
+    SBQ_TRY(T->src_loc.alloc(ns * sizeof(float4)));
+    SBQ_TRY(T->src_abs.alloc(3 * ns * sizeof(double)));
+    SBQ_TRY(T->trg_loc.alloc(nt * sizeof(float4)));
+    SBQ_TRY(T->q.alloc(ns * sizeof(float4)));
+    SBQ_TRY(T->cells.alloc(h_cells.size() * sizeof(TrCellDev)));
+    SBQ_TRY(T->prox_loc.alloc(std::max<long long>(np, 1) * sizeof(float4)));
+    SBQ_TRY(T->prox_q.alloc(std::max<long long>(np, 1) * sizeof(float4)));
+    SBQ_TRY(T->chunks.alloc(std::max<size_t>(h_chunks.size(), 1) * sizeof(int4)));
+    SBQ_TRY(T->tleaf.alloc(std::max<size_t>(h_tleaf.size(), 1) * sizeof(int4)));
+    SBQ_TRY(T->entries.alloc(std::max<size_t>(h_ent.size(), 1) * sizeof(TrEntry)));
+    SBQ_CUDA(cudaMemcpyAsync(T->perm_s.p, S.perm.data(), ns * sizeof(int), cudaMemcpyHostToDevice, s));
+    SBQ_CUDA(cudaMemcpyAsync(T->perm_t.p, Tt.perm.data(), nt * sizeof(int), cudaMemcpyHostToDevice, s));
+    SBQ_CUDA(cudaMemcpyAsync(T->w_sorted.p, h_ws.data(), ns * sizeof(double), cudaMemcpyHostToDevice, s));
+    SBQ_CUDA(cudaMemcpyAsync(T->src_loc.p, h_sloc.data(), ns * sizeof(float4), cudaMemcpyHostToDevice, s));
+    SBQ_CUDA(cudaMemcpyAsync(T->src_abs.p, h_sabs.data(), 3 * ns * sizeof(double), cudaMemcpyHostToDevice, s));
+    SBQ_CUDA(cudaMemcpyAsync(T->trg_loc.p, h_tloc.data(), nt * sizeof(float4), cudaMemcpyHostToDevice, s));
+    SBQ_CUDA(cudaMemcpyAsync(T->cells.p, h_cells.data(), h_cells.size() * sizeof(TrCellDev),
+                             cudaMemcpyHostToDevice, s));
+    if (np > 0)
+        SBQ_CUDA(cudaMemcpyAsync(T->prox_loc.p, h_ploc.data(), np * sizeof(float4), cudaMemcpyHostToDevice, s));
+    if (!h_chunks.empty())
+        SBQ_CUDA(cudaMemcpyAsync(T->chunks.p, h_chunks.data(), h_chunks.size() * sizeof(int4),
+                                 cudaMemcpyHostToDevice, s));
+    if (!h_tleaf.empty())
+        SBQ_CUDA(cudaMemcpyAsync(T->tleaf.p, h_tleaf.data(), h_tleaf.size() * sizeof(int4),
+                                 cudaMemcpyHostToDevice, s));
+    if (!h_ent.empty())
+        SBQ_CUDA(cudaMemcpyAsync(T->entries.p, h_ent.data(), h_ent.size() * sizeof(TrEntry),
+                                 cudaMemcpyHostToDevice, s));
+    SBQ_CUDA(cudaStreamSynchronize(s));
+    return SBQ_OK;
+}
+
+static int tree_apply_impl(sbq_tree_s *T, const double *sigma, double *u, cudaStream_t s)
+{
+    if (T->ns == 0 || T->nt == 0) {
+        if (T->nt > 0)
+            SBQ_CUDA(cudaMemsetAsync(u, 0, 3 * T->nt * sizeof(double), s));
+        return SBQ_OK;
+    }
+    const unsigned g = static_cast<unsigned>((T->ns + 255) / 256);
+    k_tree_charges<<<g, 256, 0, s>>>(T->ns, T->perm_s.as<int>(), T->w_sorted.as<double>(), sigma,
+                                     T->q.as<float4>());
+    SBQ_CUDA(cudaGetLastError());
+    SBQ_CUDA(cudaMemsetAsync(T->prox_q.p, 0, std::max<long long>(T->n_proxies, 1) * sizeof(float4), s));
+    if (T->n_chunks > 0) {
+        k_tree_p2m<<<static_cast<unsigned>(T->n_chunks), TR_THREADS, 0, s>>>(
+            T->chunks.as<int4>(), T->cells.as<TrCellDev>(), T->src_abs.as<double>(), T->ns,
+            T->q.as<float4>(), T->prox_q.as<float4>());
+        SBQ_CUDA(cudaGetLastError());
+    }
+    k_tree_eval<<<static_cast<unsigned>(T->n_tleaves), TR_THREADS, 0, s>>>(
+        T->tleaf.as<int4>(), T->entries.as<TrEntry>(), T->trg_loc.as<float4>(), T->src_loc.as<float4>(),
+        T->q.as<float4>(), T->prox_loc.as<float4>(), T->prox_q.as<float4>(), T->perm_t.as<int>(), T->nt,
+        T->same ? 1 : 0, u);
+    SBQ_CUDA(cudaGetLastError());
+    return SBQ_OK;
+}
+
+}  // namespace sbq
+
+namespace {
+int tree_fail(int code, const char *msg)
+{
+    sbq::set_error(msg);
+    return code;
+}
+}  // namespace
+
+extern "C" __attribute__((visibility("default"))) int stokes_sl_tree_create(
+    int64_t ns, const double *src, const double *w, int64_t nt, const double *trg, double theta,
+    int order, sbq_tree_s **out, void *stream)
+{
+    sbq::clear_error();
+    if (!out)
+        return tree_fail(SBQ_EINVAL, "stokes_sl_tree_create: null out");
+    *out = nullptr;
+    if (ns < 0 || nt < 0 || ns > 0x3fffffffLL || nt > 0x3fffffffLL)
+        return tree_fail(SBQ_EINVAL, "stokes_sl_tree_create: sizes must be in 0..2^30 - 1");
+    if ((ns > 0 && (!src || !w)) || (nt > 0 && !trg))
+        return tree_fail(SBQ_EINVAL, "stokes_sl_tree_create: null pointer");
+    if (!(theta > 0.0 && theta < 1.0))
+        return tree_fail(SBQ_EINVAL, "stokes_sl_tree_create: theta must be in (0, 1)");
+    if (order < 2 || order > 10)
+        return tree_fail(SBQ_EINVAL, "stokes_sl_tree_create: order must be in 2..10");
+    sbq_tree_s *T = new sbq_tree_s();
+    cudaGetDevice(&T->device);
+    const int st = sbq::tree_create_impl(ns, src, w, nt, trg, theta, order, T,
+                                         static_cast<cudaStream_t>(stream));
+    if (st != SBQ_OK) {
+        delete T;
+        return st;
+    }
+    *out = T;
+    return SBQ_OK;
+}
+
+extern "C" __attribute__((visibility("default"))) int stokes_sl_tree_apply(sbq_tree_s *T,
+                                                                           const double *sigma,
+                                                                           double *u, void *stream)
+{
+    sbq::clear_error();
+    if (!T || T->magic != 0x53425454u)
+        return tree_fail(SBQ_EINVAL, "stokes_sl_tree_apply: not a tree handle");
+    if ((T->ns > 0 && !sigma) || (T->nt > 0 && !u))
+        return tree_fail(SBQ_EINVAL, "stokes_sl_tree_apply: null pointer");
+    return sbq::tree_apply_impl(T, sigma, u, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" __attribute__((visibility("default"))) int stokes_sl_tree_stats(const sbq_tree_s *T,
+                                                                           double *pairs,
+                                                                           int64_t *counts)
+{
+    sbq::clear_error();
+    if (!T || T->magic != 0x53425454u)
+        return tree_fail(SBQ_EINVAL, "stokes_sl_tree_stats: not a tree handle");
+    if (pairs)
+        *pairs = T->pairs;
+    if (counts) {
+        counts[0] = T->n_cells;
+        counts[1] = T->n_proxies;
+        counts[2] = T->n_entries;
+        counts[3] = T->n_tleaves;
+    }
+    return SBQ_OK;
+}
+
+extern "C" __attribute__((visibility("default"))) int stokes_sl_tree_destroy(sbq_tree_s *T)
+{
+    sbq::clear_error();
+    if (!T)
+        return SBQ_OK;
+    if (T->magic != 0x53425454u)
+        return tree_fail(SBQ_EINVAL, "stokes_sl_tree_destroy: not a tree handle");
+    T->magic = 0;
+    delete T;
+    return SBQ_OK;
+}
