@@ -181,35 +181,39 @@ SBQ_API int stokes_sl_apply_noalloc(int64_t ns, const double *src, const double 
                                     int prec, void *stream);
 
 /*
- * Far-field acceleration of the single-layer sum (the paper's fast route for large N:
- * an FMM for the far field, Sec. 3.2; direct sums cost O(N^2), Sec. 3.4): a barycentric
- * Lagrange treecode.  Approximates stokes_sl_apply (the same sum, the same self-pair
- * exclusion when trg == src) to a relative accuracy set by theta and order, in FP32
- * arithmetic: about 1e-6 at theta = 0.5, order = 10.
- *   stokes_sl_tree_create: ns sources src[3*ns], weights w[ns], nt targets trg[3*nt]
- *     (DEVICE arrays; pass trg == src for the on-surface sum, which then excludes each
- *     node's own term; with distinct arrays no target may coincide with a source: its
- *     term would be unbounded).  theta in (0, 1): a cell of radius r acts through its proxies on target
- *     leaves farther than r / theta; order in 2..10: Chebyshev points along the cell's
- *     longest side (fewer across thin sides).  Copies the geometry to the host, builds
- *     both octrees and the interaction lists there (the setup, once per geometry) and
- *     uploads them; the handle owns its device memory (about 100 bytes per node plus
- *     32 bytes per proxy point and per list entry).  *out receives the handle.
- *   stokes_sl_tree_apply: u[3*nt] (DEVICE, overwritten) from sigma[3*ns] (DEVICE) on
- *     `stream`: source charges, proxy charges of every cell, one CTA per target leaf.
- *   stokes_sl_tree_stats: *pairs = kernel evaluations per apply; counts[0..3] = cells,
- *     proxy points, list entries, target-leaf work items.
- *   stokes_sl_tree_destroy: frees the handle (NULL is accepted).
- * Errors: SBQ_EINVAL for sizes outside 0..2^30-1, null pointers, theta or order out of
- * range, or a handle that is not a tree; SBQ_ECUDA / SBQ_ENOMEM from the runtime.
+ * Far-field acceleration of the layer sums (the paper's fast route for large N: an FMM for
+ * the far field, Sec. 3.2; direct sums cost O(N^2), Sec. 3.4): a barycentric Lagrange
+ * treecode for u = sum_s [alpha S + beta D](x_t - y_s) w_s sigma_s, the sum of
+ * stokes_combined_apply (the same self-pair exclusion when trg == src), to a relative
+ * accuracy set by theta and order, in FP32 arithmetic with FP64 sums of its list entries:
+ * about 2e-6 at theta = 0.5, order = 8.
+ *   stokes_tree_create: ns sources src[3*ns], unit normals nrm[3*ns] (may be NULL when
+ *     beta == 0), weights w[ns], nt targets trg[3*nt] (DEVICE arrays; pass trg == src for
+ *     the on-surface sum, which then excludes each node's own term; with distinct arrays no
+ *     target may coincide with a source: its term would be unbounded); alpha, beta as
+ *     stokes_combined_apply.  theta in (0, 1): a cell of radius r acts through its proxy
+ *     points on target blocks farther than r / theta; order in 2..10: Chebyshev points
+ *     along the cell's longest side (fewer across thin sides).  Copies the geometry to the
+ *     host, builds both octrees and the interaction lists there (the setup, once per
+ *     geometry and coefficient pair) and uploads them; the handle owns its device memory
+ *     (about 100 bytes per node plus 32 bytes per list entry and 16 (single layer) or 48
+ *     bytes per proxy point).  *out receives the handle.
+ *   stokes_tree_apply: u[3*nt] (DEVICE, overwritten) from sigma[3*ns] (DEVICE) on
+ *     `stream`: source charges, proxy charges of every cell, one CTA per target block.
+ *   stokes_tree_stats: *pairs = kernel evaluations per apply; counts[0..3] = cells, proxy
+ *     points, list entries, target blocks.
+ *   stokes_tree_destroy: frees the handle (NULL is accepted).
+ * Errors: SBQ_EINVAL for sizes outside 0..2^30-1, null pointers, non-finite alpha or beta,
+ * theta or order out of range, or a handle that is not a tree; SBQ_ECUDA / SBQ_ENOMEM from
+ * the runtime.
  */
 typedef struct sbq_tree_s sbq_tree;
-SBQ_API int stokes_sl_tree_create(int64_t ns, const double *src, const double *w, int64_t nt,
-                                  const double *trg, double theta, int order, sbq_tree **out,
-                                  void *stream);
-SBQ_API int stokes_sl_tree_apply(sbq_tree *tree, const double *sigma, double *u, void *stream);
-SBQ_API int stokes_sl_tree_stats(const sbq_tree *tree, double *pairs, int64_t *counts);
-SBQ_API int stokes_sl_tree_destroy(sbq_tree *tree);
+SBQ_API int stokes_tree_create(int64_t ns, const double *src, const double *nrm, const double *w,
+                               int64_t nt, const double *trg, double alpha, double beta,
+                               double theta, int order, sbq_tree **out, void *stream);
+SBQ_API int stokes_tree_apply(sbq_tree *tree, const double *sigma, double *u, void *stream);
+SBQ_API int stokes_tree_stats(const sbq_tree *tree, double *pairs, int64_t *counts);
+SBQ_API int stokes_tree_destroy(sbq_tree *tree);
 
 /* Double-layer velocity u = sum D(x_t - y_s; n_s) w_s sigma_s (Eq. stokes-dl), nrm[3*ns]
  * unit outward normals.  Other arguments and errors as stokes_sl_apply. */

@@ -39,13 +39,17 @@ struct sbq_tree_s {
     // device data
     sbq::DevBuf perm_s, perm_t;     // sorted position -> original index
     sbq::DevBuf w_sorted;           // FP64 weights, sorted order
+    sbq::DevBuf n_sorted;           // FP64 normals (3 x ns, sorted), double layer only
+    double alpha = 1.0, beta = 0.0; // u = alpha S + beta D
+    int nq = 1;                     // float4 charge records per point: 1 (S), 3 (S and D)
     sbq::DevBuf src_loc;            // float4: source - its leaf centre (sorted order)
     sbq::DevBuf src_abs;            // double: absolute source positions (3 x ns, sorted)
-    sbq::DevBuf trg_loc;            // float4: target - its leaf centre (sorted order)
-    sbq::DevBuf q;                  // float4 charges, sorted order
+    sbq::DevBuf trg_loc;            // float4: target - its block centre (sorted order)
+    sbq::DevBuf trg_lo, src_lo;     // float4: rounding residuals of trg_loc and src_loc
+    sbq::DevBuf q;                  // nq float4 charge records per source, sorted order
     sbq::DevBuf cells;              // TrCellDev per cell
     sbq::DevBuf prox_loc;           // float4: proxy - its cell centre
-    sbq::DevBuf prox_q;             // float4 proxy charges
+    sbq::DevBuf prox_q;             // nq float4 charge records per proxy
     sbq::DevBuf chunks;             // int4 (cell, first source, count, 0): P2M work items
     long long n_chunks = 0;
     sbq::DevBuf tleaf;              // int4 (first target, count, first entry, entry count)
@@ -71,8 +75,36 @@ struct TrCellDev {
 
 struct TrEntry {
     int first, count, kind, pad;   // kind 0: sources [first, first + count); 1: proxies
-    float dx, dy, dz, pad2;        // block frame centre minus target leaf centre
+    float dx, dy, dz, pad2;        // block frame centre minus target block centre (FP32)
+    float lx, ly, lz, pad3;        // and the rounding residual of that offset
 };
+
+inline TrEntry make_entry(int first, int count, int kind, const double *cb, const double *ct)
+{
+    TrEntry e{};
+    e.first = first;
+    e.count = count;
+    e.kind = kind;
+    const double d[3] = {cb[0] - ct[0], cb[1] - ct[1], cb[2] - ct[2]};
+    e.dx = static_cast<float>(d[0]);
+    e.dy = static_cast<float>(d[1]);
+    e.dz = static_cast<float>(d[2]);
+    e.lx = static_cast<float>(d[0] - e.dx);
+    e.ly = static_cast<float>(d[1] - e.dy);
+    e.lz = static_cast<float>(d[2] - e.dz);
+    return e;
+}
+
+// a float and its rounding residual (the pair holds a double to ~48 bits)
+inline float4 hi4(double x, double y, double z)
+{
+    return make_float4(static_cast<float>(x), static_cast<float>(y), static_cast<float>(z), 0.0f);
+}
+inline float4 lo4(double x, double y, double z)
+{
+    return make_float4(static_cast<float>(x - static_cast<float>(x)), static_cast<float>(y - static_cast<float>(y)),
+                       static_cast<float>(z - static_cast<float>(z)), 0.0f);
+}
 
 struct HostCell {
     double c[3], h[3], rad;
@@ -229,34 +261,50 @@ __device__ void lagrange_1d(double xi, int n, float *out)
         out[j] = hit >= 0 ? (j == hit ? 1.0f : 0.0f) : static_cast<float>(t[j] / den);
 }
 
-// q_k = w_k sigma_k (FP32), sorted order
+// charge records of source k (sorted order): q = w sigma scaled by alpha / (8 pi) and, for
+// the double layer, the tensor d_jl = (w sigma)_j n_l scaled by 3 beta / (4 pi):
+// record 0 (q_x, q_y, q_z, d00), record 1 (d01, d02, d10, d11), record 2 (d12, d20, d21, d22)
+template <int NQ>
 __global__ void k_tree_charges(long long ns, const int *__restrict__ perm, const double *__restrict__ w,
-                               const double *__restrict__ sigma, float4 *q)
+                               const double *__restrict__ nrm, const double *__restrict__ sigma,
+                               double a, double b, float4 *q)
 {
     const long long k = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
     if (k >= ns)
         return;
     const long long o = perm[k];
     const double ww = w[k];
-    q[k] = make_float4(static_cast<float>(ww * sigma[o]), static_cast<float>(ww * sigma[ns + o]),
-                       static_cast<float>(ww * sigma[2 * ns + o]), 0.0f);
+    const double s0 = ww * sigma[o], s1 = ww * sigma[ns + o], s2 = ww * sigma[2 * ns + o];
+    if (NQ == 1) {
+        q[k] = make_float4(static_cast<float>(a * s0), static_cast<float>(a * s1), static_cast<float>(a * s2), 0.0f);
+        return;
+    }
+    const double n0 = nrm[k], n1 = nrm[ns + k], n2 = nrm[2 * ns + k];
+    q[3 * k] = make_float4(static_cast<float>(a * s0), static_cast<float>(a * s1), static_cast<float>(a * s2),
+                           static_cast<float>(b * s0 * n0));
+    q[3 * k + 1] = make_float4(static_cast<float>(b * s0 * n1), static_cast<float>(b * s0 * n2),
+                               static_cast<float>(b * s1 * n0), static_cast<float>(b * s1 * n1));
+    q[3 * k + 2] = make_float4(static_cast<float>(b * s1 * n2), static_cast<float>(b * s2 * n0),
+                               static_cast<float>(b * s2 * n1), static_cast<float>(b * s2 * n2));
 }
 
 // proxy charges of one cell from one chunk of its sources (atomically accumulated)
+template <int NQ>
 __global__ void __launch_bounds__(TR_THREADS)
 k_tree_p2m(const int4 *__restrict__ chunks, const TrCellDev *__restrict__ cells,
            const double *__restrict__ src_abs, long long ns, const float4 *__restrict__ q,
            float4 *prox_q)
 {
     __shared__ float Lx[TR_THREADS][TR_NMAX], Ly[TR_THREADS][TR_NMAX], Lz[TR_THREADS][TR_NMAX];
-    __shared__ float4 sq[TR_THREADS];
+    __shared__ float4 sq[TR_THREADS * NQ];
     const int4 ck = chunks[blockIdx.x];
     const TrCellDev c = cells[ck.x];
     const int np = c.n[0] * c.n[1] * c.n[2];
-    float acc[8][3];
     constexpr int MPT = 8;   // proxies per thread: 8 x 128 = 1024 >= 10^3, the largest grid
+    float acc[MPT][4 * NQ];
     for (int m = 0; m < MPT; ++m)
-        acc[m][0] = acc[m][1] = acc[m][2] = 0.0f;
+        for (int v = 0; v < 4 * NQ; ++v)
+            acc[m][v] = 0.0f;
     for (int base = 0; base < ck.z; base += TR_THREADS) {
         const int k = base + threadIdx.x;
         if (k < ck.z) {
@@ -267,58 +315,77 @@ k_tree_p2m(const int4 *__restrict__ chunks, const TrCellDev *__restrict__ cells,
             lagrange_1d(xi[0], c.n[0], Lx[threadIdx.x]);
             lagrange_1d(xi[1], c.n[1], Ly[threadIdx.x]);
             lagrange_1d(xi[2], c.n[2], Lz[threadIdx.x]);
-            sq[threadIdx.x] = q[s];
+            for (int r = 0; r < NQ; ++r)
+                sq[threadIdx.x * NQ + r] = q[s * NQ + r];
         } else {
-            sq[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int r = 0; r < NQ; ++r)
+                sq[threadIdx.x * NQ + r] = make_float4(0.f, 0.f, 0.f, 0.f);
             for (int j = 0; j < TR_NMAX; ++j)
                 Lx[threadIdx.x][j] = Ly[threadIdx.x][j] = Lz[threadIdx.x][j] = 0.0f;
         }
         __syncthreads();
         const int cnt = min(TR_THREADS, ck.z - base);
+#pragma unroll
         for (int m = 0; m < MPT; ++m) {
             const int pm = threadIdx.x + m * TR_THREADS;
-            if (pm >= np)
-                break;
-            const int a = pm / (c.n[1] * c.n[2]), b = (pm / c.n[2]) % c.n[1], cc = pm % c.n[2];
-            float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-            for (int kk = 0; kk < cnt; ++kk) {
-                const float l = Lx[kk][a] * Ly[kk][b] * Lz[kk][cc];
-                const float4 qq = sq[kk];
-                s0 = fmaf(l, qq.x, s0);
-                s1 = fmaf(l, qq.y, s1);
-                s2 = fmaf(l, qq.z, s2);
+            if (pm < np) {
+                const int a = pm / (c.n[1] * c.n[2]), b = (pm / c.n[2]) % c.n[1], cc = pm % c.n[2];
+                for (int kk = 0; kk < cnt; ++kk) {
+                    const float l = Lx[kk][a] * Ly[kk][b] * Lz[kk][cc];
+#pragma unroll
+                    for (int r = 0; r < NQ; ++r) {
+                        const float4 qq = sq[kk * NQ + r];
+                        acc[m][4 * r] = fmaf(l, qq.x, acc[m][4 * r]);
+                        acc[m][4 * r + 1] = fmaf(l, qq.y, acc[m][4 * r + 1]);
+                        acc[m][4 * r + 2] = fmaf(l, qq.z, acc[m][4 * r + 2]);
+                        acc[m][4 * r + 3] = fmaf(l, qq.w, acc[m][4 * r + 3]);
+                    }
+                }
             }
-            acc[m][0] += s0;
-            acc[m][1] += s1;
-            acc[m][2] += s2;
         }
         __syncthreads();
     }
+#pragma unroll
     for (int m = 0; m < MPT; ++m) {
         const int pm = threadIdx.x + m * TR_THREADS;
-        if (pm >= np)
-            break;
-        float4 *dst = prox_q + c.pfirst + pm;
-        atomicAdd(&dst->x, acc[m][0]);
-        atomicAdd(&dst->y, acc[m][1]);
-        atomicAdd(&dst->z, acc[m][2]);
+        if (pm < np) {
+            float *dst = reinterpret_cast<float *>(prox_q + static_cast<size_t>(c.pfirst + pm) * NQ);
+#pragma unroll
+            for (int v = 0; v < 4 * NQ; ++v)
+                if (NQ > 1 || v < 3)
+                    atomicAdd(dst + v, acc[m][v]);
+        }
     }
+}
+
+// (a - b) - c + lo with the rounding errors of both differences kept (Knuth's TwoSum)
+__device__ __forceinline__ float two_diff3(float a, float b, float c, float lo)
+{
+    const float s1 = a - b;
+    const float bb = s1 - a;
+    const float e1 = (a - (s1 - bb)) - (b + bb);
+    const float s2 = s1 - c;
+    const float cc = s2 - s1;
+    const float e2 = (s1 - (s2 - cc)) - (c + cc);
+    return s2 + ((e1 + e2) + lo);
 }
 
 // Stokeslet sums: one CTA per target block, one thread per target; list entries staged in
 // shared memory 128 points at a time
+template <int NQ>
 __global__ void __launch_bounds__(TR_THREADS)
 k_tree_eval(const int4 *__restrict__ tleaf, const TrEntry *__restrict__ entries,
             const float4 *__restrict__ trg_loc, const float4 *__restrict__ src_loc,
             const float4 *__restrict__ q, const float4 *__restrict__ prox_loc,
             const float4 *__restrict__ prox_q, const int *__restrict__ perm_t, long long nt,
-            int same, double *u)
+            int same, const float4 *__restrict__ trg_lo, const float4 *__restrict__ src_lo, double *u)
 {
-    __shared__ float4 sp[TR_THREADS], sq[TR_THREADS];
+    __shared__ float4 sp[TR_THREADS], sq[TR_THREADS * NQ], sl[NQ == 3 ? TR_THREADS : 1];
     const int4 tl = tleaf[blockIdx.x];
     const int t = threadIdx.x;
     const bool live = t < tl.y;
     const float4 x = live ? trg_loc[tl.x + t] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 xl = (NQ == 3 && live) ? trg_lo[tl.x + t] : make_float4(0.f, 0.f, 0.f, 0.f);
     double v0 = 0.0, v1 = 0.0, v2 = 0.0;
     for (int e = 0; e < tl.w; ++e) {
         float u0 = 0.f, u1 = 0.f, u2 = 0.f;   // this block's sum in FP32, the total in FP64
@@ -327,24 +394,46 @@ k_tree_eval(const int4 *__restrict__ tleaf, const TrEntry *__restrict__ entries,
         const float4 *Q = en.kind ? prox_q : q;
         // target in the block's frame
         const float xx = x.x - en.dx, xy = x.y - en.dy, xz = x.z - en.dz;
+        // the double layer's r . n = O(|r|^2) on the surface: near source blocks form r from
+        // high and low parts with exact (TwoSum) differences, ~2^-48 of the frame offsets
+        const bool hilo = NQ == 3 && en.kind == 0;
         for (int base = 0; base < en.count; base += TR_THREADS) {
             const int k = base + t;
             if (k < en.count) {
                 sp[t] = P[en.first + k];
-                sq[t] = Q[en.first + k];
+                for (int r = 0; r < NQ; ++r)
+                    sq[t * NQ + r] = Q[static_cast<size_t>(en.first + k) * NQ + r];
+                if (hilo)
+                    sl[t] = src_lo[en.first + k];
             }
             __syncthreads();
             const int cnt = min(TR_THREADS, en.count - base);
             // the target's own node (same tree, a source block): its sorted index
             const int self = (same && en.kind == 0) ? tl.x + t - en.first - base : -1;
             for (int kk = 0; kk < cnt; ++kk) {
-                const float4 y = sp[kk], qq = sq[kk];
-                const float r0 = xx - y.x, r1 = xy - y.y, r2 = xz - y.z;
+                const float4 y = sp[kk], qq = sq[kk * NQ];
+                float r0 = xx - y.x, r1 = xy - y.y, r2 = xz - y.z;
+                if (hilo) {
+                    const float4 yl = sl[kk];
+                    r0 = two_diff3(x.x, y.x, en.dx, xl.x - yl.x - en.lx);
+                    r1 = two_diff3(x.y, y.y, en.dy, xl.y - yl.y - en.ly);
+                    r2 = two_diff3(x.z, y.z, en.dz, xl.z - yl.z - en.lz);
+                }
                 const float rr = fmaf(r0, r0, fmaf(r1, r1, r2 * r2));
                 if (kk != self && rr > 0.0f) {
                     const float ri = rsqrtf(rr);
-                    const float ri3 = ri * ri * ri;
-                    const float rq = fmaf(r0, qq.x, fmaf(r1, qq.y, r2 * qq.z)) * ri3;
+                    const float ri2 = ri * ri, ri3 = ri * ri2;
+                    // single layer: q / r + r (r . q) / r^3
+                    float rq = fmaf(r0, qq.x, fmaf(r1, qq.y, r2 * qq.z)) * ri3;
+                    if (NQ == 3) {
+                        // double layer: (r^T d r) r / r^5
+                        const float4 d1 = sq[kk * NQ + 1], d2 = sq[kk * NQ + 2];
+                        const float a0 = fmaf(qq.w, r0, fmaf(d1.x, r1, d1.y * r2));
+                        const float a1 = fmaf(d1.z, r0, fmaf(d1.w, r1, d2.x * r2));
+                        const float a2 = fmaf(d2.y, r0, fmaf(d2.z, r1, d2.w * r2));
+                        const float rdr = fmaf(r0, a0, fmaf(r1, a1, r2 * a2));
+                        rq = fmaf(rdr, ri3 * ri2, rq);
+                    }
                     u0 = fmaf(qq.x, ri, fmaf(r0, rq, u0));
                     u1 = fmaf(qq.y, ri, fmaf(r1, rq, u1));
                     u2 = fmaf(qq.z, ri, fmaf(r2, rq, u2));
@@ -358,10 +447,9 @@ k_tree_eval(const int4 *__restrict__ tleaf, const TrEntry *__restrict__ entries,
     }
     if (live) {
         const long long o = perm_t[tl.x + t];
-        const double f = 1.0 / (8.0 * TR_PI);
-        u[o] = f * v0;
-        u[nt + o] = f * v1;
-        u[2 * nt + o] = f * v2;
+        u[o] = v0;
+        u[nt + o] = v1;
+        u[2 * nt + o] = v2;
     }
 }
 
@@ -381,17 +469,24 @@ int proxies_per_dim(const HostCell &c, int order, int n[3])
 
 }  // namespace
 
-static int tree_create_impl(long long ns, const double *src, const double *w, long long nt,
-                            const double *trg, double theta, int order, sbq_tree_s *T,
-                            cudaStream_t s)
+static int tree_create_impl(long long ns, const double *src, const double *nrm, const double *w,
+                            long long nt, const double *trg, double alpha, double beta,
+                            double theta, int order, sbq_tree_s *T, cudaStream_t s)
 {
+    T->alpha = alpha;
+    T->beta = beta;
+    T->nq = beta != 0.0 ? 3 : 1;
     T->ns = ns;
     T->nt = nt;
     T->same = trg == src && nt == ns;
     T->theta = theta;
     T->order = order;
-    std::vector<double> hs(3 * ns), hw(ns), ht;
+    std::vector<double> hs(3 * ns), hw(ns), ht, hn;
     SBQ_CUDA(cudaMemcpyAsync(hs.data(), src, 3 * ns * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (T->nq == 3) {
+        hn.resize(3 * ns);
+        SBQ_CUDA(cudaMemcpyAsync(hn.data(), nrm, 3 * ns * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
     SBQ_CUDA(cudaMemcpyAsync(hw.data(), w, ns * sizeof(double), cudaMemcpyDeviceToHost, s));
     if (!T->same) {
         ht.resize(3 * nt);
@@ -414,7 +509,7 @@ static int tree_create_impl(long long ns, const double *src, const double *w, lo
         T->max_level = std::max(T->max_level, c.level);
     }
     if (np > 0x7fffffffLL) {
-        set_error("stokes_sl_tree_create: too many proxy points");
+        set_error("stokes_tree_create: too many proxy points");
         return SBQ_EINVAL;
     }
     std::vector<float4> h_ploc(np);
@@ -441,15 +536,18 @@ static int tree_create_impl(long long ns, const double *src, const double *w, lo
                 }
     }
     // sources: FP32 offsets from their leaf's centre, FP64 absolute positions, weights
-    std::vector<float4> h_sloc(ns);
-    std::vector<double> h_sabs(3 * ns), h_ws(ns);
+    std::vector<float4> h_sloc(ns), h_slo(ns);
+    std::vector<double> h_sabs(3 * ns), h_ws(ns), h_ns(T->nq == 3 ? 3 * ns : 0);
     for (long long k = 0; k < ns; ++k) {
         const int o = S.perm[k];
         const HostCell &L = S.cells[S.leaf_of[k]];
-        h_sloc[k] = make_float4(static_cast<float>(hs[o] - L.c[0]), static_cast<float>(hs[ns + o] - L.c[1]),
-                                static_cast<float>(hs[2 * ns + o] - L.c[2]), 0.0f);
-        for (int d = 0; d < 3; ++d)
+        h_sloc[k] = hi4(hs[o] - L.c[0], hs[ns + o] - L.c[1], hs[2 * ns + o] - L.c[2]);
+        h_slo[k] = lo4(hs[o] - L.c[0], hs[ns + o] - L.c[1], hs[2 * ns + o] - L.c[2]);
+        for (int d = 0; d < 3; ++d) {
             h_sabs[d * ns + k] = hs[d * ns + o];
+            if (T->nq == 3)
+                h_ns[d * ns + k] = hn[d * ns + o];
+        }
         h_ws[k] = hw[o];
     }
     // target blocks: runs of TR_THREADS consecutive targets in Morton order, each with its
@@ -462,7 +560,7 @@ static int tree_create_impl(long long ns, const double *src, const double *w, lo
     // as such a cell: a run across a jump of the Morton order would be spread over the domain
     // and its FP32 offsets would lose the digits the near pairs need)
     std::vector<TBlock> tb;
-    std::vector<float4> h_tloc(nt);
+    std::vector<float4> h_tloc(nt), h_tlo(nt);
     std::vector<std::pair<int, int>> runs;
     {
         std::vector<int> st{0};
@@ -497,8 +595,8 @@ static int tree_create_impl(long long ns, const double *src, const double *w, lo
         B.rad = std::sqrt(r2);
         for (int k = B.first; k < B.first + B.count; ++k) {
             const int o = Tt.perm[k];
-            h_tloc[k] = make_float4(static_cast<float>(xt[o] - B.c[0]), static_cast<float>(xt[nt + o] - B.c[1]),
-                                    static_cast<float>(xt[2 * nt + o] - B.c[2]), 0.0f);
+            h_tloc[k] = hi4(xt[o] - B.c[0], xt[nt + o] - B.c[1], xt[2 * nt + o] - B.c[2]);
+            h_tlo[k] = lo4(xt[o] - B.c[0], xt[nt + o] - B.c[1], xt[2 * nt + o] - B.c[2]);
         }
         tb.push_back(B);
     }
@@ -525,13 +623,11 @@ static int tree_create_impl(long long ns, const double *src, const double *w, lo
                 d2 += (C.c[d] - L.c[d]) * (C.c[d] - L.c[d]);
             const double dist = std::sqrt(d2) - L.rad;
             if (dist * theta >= C.rad && C.count > C.nprox) {
-                TrEntry en{C.pfirst, C.nprox, 1, 0, static_cast<float>(C.c[0] - L.c[0]),
-                           static_cast<float>(C.c[1] - L.c[1]), static_cast<float>(C.c[2] - L.c[2]), 0.f};
+                const TrEntry en = make_entry(C.pfirst, C.nprox, 1, C.c, L.c);
                 h_ent.push_back(en);
                 pairs += static_cast<double>(C.nprox) * L.count;
             } else if (C.nchild == 0) {
-                TrEntry en{C.first, C.count, 0, 0, static_cast<float>(C.c[0] - L.c[0]),
-                           static_cast<float>(C.c[1] - L.c[1]), static_cast<float>(C.c[2] - L.c[2]), 0.f};
+                const TrEntry en = make_entry(C.first, C.count, 0, C.c, L.c);
                 h_ent.push_back(en);
                 pairs += static_cast<double>(C.count) * L.count;
             } else {
@@ -554,10 +650,18 @@ static int tree_create_impl(long long ns, const double *src, const double *w, lo
     SBQ_TRY(T->src_loc.alloc(ns * sizeof(float4)));
     SBQ_TRY(T->src_abs.alloc(3 * ns * sizeof(double)));
     SBQ_TRY(T->trg_loc.alloc(nt * sizeof(float4)));
-    SBQ_TRY(T->q.alloc(ns * sizeof(float4)));
+    SBQ_TRY(T->trg_lo.alloc(nt * sizeof(float4)));
+    SBQ_TRY(T->src_lo.alloc(ns * sizeof(float4)));
+    SBQ_CUDA(cudaMemcpyAsync(T->trg_lo.p, h_tlo.data(), nt * sizeof(float4), cudaMemcpyHostToDevice, s));
+    SBQ_CUDA(cudaMemcpyAsync(T->src_lo.p, h_slo.data(), ns * sizeof(float4), cudaMemcpyHostToDevice, s));
+    SBQ_TRY(T->q.alloc(ns * T->nq * sizeof(float4)));
+    if (T->nq == 3) {
+        SBQ_TRY(T->n_sorted.alloc(3 * ns * sizeof(double)));
+        SBQ_CUDA(cudaMemcpyAsync(T->n_sorted.p, h_ns.data(), 3 * ns * sizeof(double), cudaMemcpyHostToDevice, s));
+    }
     SBQ_TRY(T->cells.alloc(h_cells.size() * sizeof(TrCellDev)));
     SBQ_TRY(T->prox_loc.alloc(std::max<long long>(np, 1) * sizeof(float4)));
-    SBQ_TRY(T->prox_q.alloc(std::max<long long>(np, 1) * sizeof(float4)));
+    SBQ_TRY(T->prox_q.alloc(std::max<long long>(np, 1) * T->nq * sizeof(float4)));
     SBQ_TRY(T->chunks.alloc(std::max<size_t>(h_chunks.size(), 1) * sizeof(int4)));
     SBQ_TRY(T->tleaf.alloc(std::max<size_t>(h_tleaf.size(), 1) * sizeof(int4)));
     SBQ_TRY(T->entries.alloc(std::max<size_t>(h_ent.size(), 1) * sizeof(TrEntry)));
@@ -584,6 +688,29 @@ static int tree_create_impl(long long ns, const double *src, const double *w, lo
     return SBQ_OK;
 }
 
+template <int NQ>
+static int tree_apply_nq(sbq_tree_s *T, const double *sigma, double *u, cudaStream_t s)
+{
+    const unsigned g = static_cast<unsigned>((T->ns + 255) / 256);
+    k_tree_charges<NQ><<<g, 256, 0, s>>>(T->ns, T->perm_s.as<int>(), T->w_sorted.as<double>(),
+                                         T->n_sorted.as<double>(), sigma, T->alpha / (8.0 * TR_PI),
+                                         3.0 * T->beta / (4.0 * TR_PI), T->q.as<float4>());
+    SBQ_CUDA(cudaGetLastError());
+    SBQ_CUDA(cudaMemsetAsync(T->prox_q.p, 0, std::max<long long>(T->n_proxies, 1) * NQ * sizeof(float4), s));
+    if (T->n_chunks > 0) {
+        k_tree_p2m<NQ><<<static_cast<unsigned>(T->n_chunks), TR_THREADS, 0, s>>>(
+            T->chunks.as<int4>(), T->cells.as<TrCellDev>(), T->src_abs.as<double>(), T->ns,
+            T->q.as<float4>(), T->prox_q.as<float4>());
+        SBQ_CUDA(cudaGetLastError());
+    }
+    k_tree_eval<NQ><<<static_cast<unsigned>(T->n_tleaves), TR_THREADS, 0, s>>>(
+        T->tleaf.as<int4>(), T->entries.as<TrEntry>(), T->trg_loc.as<float4>(), T->src_loc.as<float4>(),
+        T->q.as<float4>(), T->prox_loc.as<float4>(), T->prox_q.as<float4>(), T->perm_t.as<int>(), T->nt,
+        T->same ? 1 : 0, T->trg_lo.as<float4>(), T->src_lo.as<float4>(), u);
+    SBQ_CUDA(cudaGetLastError());
+    return SBQ_OK;
+}
+
 static int tree_apply_impl(sbq_tree_s *T, const double *sigma, double *u, cudaStream_t s)
 {
     if (T->ns == 0 || T->nt == 0) {
@@ -591,23 +718,7 @@ static int tree_apply_impl(sbq_tree_s *T, const double *sigma, double *u, cudaSt
             SBQ_CUDA(cudaMemsetAsync(u, 0, 3 * T->nt * sizeof(double), s));
         return SBQ_OK;
     }
-    const unsigned g = static_cast<unsigned>((T->ns + 255) / 256);
-    k_tree_charges<<<g, 256, 0, s>>>(T->ns, T->perm_s.as<int>(), T->w_sorted.as<double>(), sigma,
-                                     T->q.as<float4>());
-    SBQ_CUDA(cudaGetLastError());
-    SBQ_CUDA(cudaMemsetAsync(T->prox_q.p, 0, std::max<long long>(T->n_proxies, 1) * sizeof(float4), s));
-    if (T->n_chunks > 0) {
-        k_tree_p2m<<<static_cast<unsigned>(T->n_chunks), TR_THREADS, 0, s>>>(
-            T->chunks.as<int4>(), T->cells.as<TrCellDev>(), T->src_abs.as<double>(), T->ns,
-            T->q.as<float4>(), T->prox_q.as<float4>());
-        SBQ_CUDA(cudaGetLastError());
-    }
-    k_tree_eval<<<static_cast<unsigned>(T->n_tleaves), TR_THREADS, 0, s>>>(
-        T->tleaf.as<int4>(), T->entries.as<TrEntry>(), T->trg_loc.as<float4>(), T->src_loc.as<float4>(),
-        T->q.as<float4>(), T->prox_loc.as<float4>(), T->prox_q.as<float4>(), T->perm_t.as<int>(), T->nt,
-        T->same ? 1 : 0, u);
-    SBQ_CUDA(cudaGetLastError());
-    return SBQ_OK;
+    return T->nq == 3 ? tree_apply_nq<3>(T, sigma, u, s) : tree_apply_nq<1>(T, sigma, u, s);
 }
 
 }  // namespace sbq
@@ -620,25 +731,28 @@ int tree_fail(int code, const char *msg)
 }
 }  // namespace
 
-extern "C" __attribute__((visibility("default"))) int stokes_sl_tree_create(
-    int64_t ns, const double *src, const double *w, int64_t nt, const double *trg, double theta,
-    int order, sbq_tree_s **out, void *stream)
+extern "C" __attribute__((visibility("default"))) int stokes_tree_create(
+    int64_t ns, const double *src, const double *nrm, const double *w, int64_t nt,
+    const double *trg, double alpha, double beta, double theta, int order, sbq_tree_s **out,
+    void *stream)
 {
     sbq::clear_error();
     if (!out)
-        return tree_fail(SBQ_EINVAL, "stokes_sl_tree_create: null out");
+        return tree_fail(SBQ_EINVAL, "stokes_tree_create: null out");
     *out = nullptr;
     if (ns < 0 || nt < 0 || ns > 0x3fffffffLL || nt > 0x3fffffffLL)
-        return tree_fail(SBQ_EINVAL, "stokes_sl_tree_create: sizes must be in 0..2^30 - 1");
-    if ((ns > 0 && (!src || !w)) || (nt > 0 && !trg))
-        return tree_fail(SBQ_EINVAL, "stokes_sl_tree_create: null pointer");
+        return tree_fail(SBQ_EINVAL, "stokes_tree_create: sizes must be in 0..2^30 - 1");
+    if ((ns > 0 && (!src || !w)) || (nt > 0 && !trg) || (ns > 0 && beta != 0.0 && !nrm))
+        return tree_fail(SBQ_EINVAL, "stokes_tree_create: null pointer");
+    if (!std::isfinite(alpha) || !std::isfinite(beta))
+        return tree_fail(SBQ_EINVAL, "stokes_tree_create: non-finite alpha or beta");
     if (!(theta > 0.0 && theta < 1.0))
-        return tree_fail(SBQ_EINVAL, "stokes_sl_tree_create: theta must be in (0, 1)");
+        return tree_fail(SBQ_EINVAL, "stokes_tree_create: theta must be in (0, 1)");
     if (order < 2 || order > 10)
-        return tree_fail(SBQ_EINVAL, "stokes_sl_tree_create: order must be in 2..10");
+        return tree_fail(SBQ_EINVAL, "stokes_tree_create: order must be in 2..10");
     sbq_tree_s *T = new sbq_tree_s();
     cudaGetDevice(&T->device);
-    const int st = sbq::tree_create_impl(ns, src, w, nt, trg, theta, order, T,
+    const int st = sbq::tree_create_impl(ns, src, nrm, w, nt, trg, alpha, beta, theta, order, T,
                                          static_cast<cudaStream_t>(stream));
     if (st != SBQ_OK) {
         delete T;
@@ -648,25 +762,25 @@ extern "C" __attribute__((visibility("default"))) int stokes_sl_tree_create(
     return SBQ_OK;
 }
 
-extern "C" __attribute__((visibility("default"))) int stokes_sl_tree_apply(sbq_tree_s *T,
+extern "C" __attribute__((visibility("default"))) int stokes_tree_apply(sbq_tree_s *T,
                                                                            const double *sigma,
                                                                            double *u, void *stream)
 {
     sbq::clear_error();
     if (!T || T->magic != 0x53425454u)
-        return tree_fail(SBQ_EINVAL, "stokes_sl_tree_apply: not a tree handle");
+        return tree_fail(SBQ_EINVAL, "stokes_tree_apply: not a tree handle");
     if ((T->ns > 0 && !sigma) || (T->nt > 0 && !u))
-        return tree_fail(SBQ_EINVAL, "stokes_sl_tree_apply: null pointer");
+        return tree_fail(SBQ_EINVAL, "stokes_tree_apply: null pointer");
     return sbq::tree_apply_impl(T, sigma, u, static_cast<cudaStream_t>(stream));
 }
 
-extern "C" __attribute__((visibility("default"))) int stokes_sl_tree_stats(const sbq_tree_s *T,
+extern "C" __attribute__((visibility("default"))) int stokes_tree_stats(const sbq_tree_s *T,
                                                                            double *pairs,
                                                                            int64_t *counts)
 {
     sbq::clear_error();
     if (!T || T->magic != 0x53425454u)
-        return tree_fail(SBQ_EINVAL, "stokes_sl_tree_stats: not a tree handle");
+        return tree_fail(SBQ_EINVAL, "stokes_tree_stats: not a tree handle");
     if (pairs)
         *pairs = T->pairs;
     if (counts) {
@@ -678,13 +792,13 @@ extern "C" __attribute__((visibility("default"))) int stokes_sl_tree_stats(const
     return SBQ_OK;
 }
 
-extern "C" __attribute__((visibility("default"))) int stokes_sl_tree_destroy(sbq_tree_s *T)
+extern "C" __attribute__((visibility("default"))) int stokes_tree_destroy(sbq_tree_s *T)
 {
     sbq::clear_error();
     if (!T)
         return SBQ_OK;
     if (T->magic != 0x53425454u)
-        return tree_fail(SBQ_EINVAL, "stokes_sl_tree_destroy: not a tree handle");
+        return tree_fail(SBQ_EINVAL, "stokes_tree_destroy: not a tree handle");
     T->magic = 0;
     delete T;
     return SBQ_OK;

@@ -122,11 +122,11 @@ def _load():
         "stokes_solve_host": ([_i64, _vp, _vp, _vp, _dbl, _dbl, _int, _vp, _int, _vp, _vp,
                                ctypes.POINTER(GmresOpts), ctypes.POINTER(GmresReport), _vp], _int),
         "sbq_destroy": ([_vp], None),
-        "stokes_sl_tree_create": ([_i64, _vp, _vp, _i64, _vp, _dbl, _int, ctypes.POINTER(_vp), _vp],
-                                  _int),
-        "stokes_sl_tree_apply": ([_vp, _vp, _vp, _vp], _int),
-        "stokes_sl_tree_stats": ([_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i64)], _int),
-        "stokes_sl_tree_destroy": ([_vp], _int),
+        "stokes_tree_create": ([_i64, _vp, _vp, _vp, _i64, _vp, _dbl, _dbl, _dbl, _int,
+                                ctypes.POINTER(_vp), _vp], _int),
+        "stokes_tree_apply": ([_vp, _vp, _vp, _vp], _int),
+        "stokes_tree_stats": ([_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i64)], _int),
+        "stokes_tree_destroy": ([_vp], _int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -233,24 +233,27 @@ def sl_apply(src, w, sigma, trg, prec="fp32c", out=None, stream=None):
     return _apply("sl", src, None, w, sigma, trg, 1.0, 0.0, prec, out, stream)
 
 
-class SlTree:
-    """Treecode for the single-layer sum (stokes_sl_tree_*): built once per geometry
-    (src, w; trg defaults to src, the on-surface sum without self terms), applied to any
-    number of densities.  theta and order set the accuracy (about 1e-6 at 0.5 and 10)."""
+class StokesTree:
+    """Treecode for the layer sum alpha S + beta D (stokes_tree_*): built once per geometry
+    (src, nrm, w; trg defaults to src, the on-surface sum without self terms), applied to
+    any number of densities.  theta and order set the accuracy (about 2e-6 at 0.5 and 8)."""
 
-    def __init__(self, src, w, trg=None, theta=0.5, order=8, stream=None):
+    def __init__(self, src, w, nrm=None, trg=None, alpha=1.0, beta=0.0, theta=0.5, order=8,
+                 stream=None):
         ns = src.shape[1]
         _dev(src, (3, ns), "src")
         _dev(w, (ns,), "w")
+        _dev(nrm, (3, ns), "nrm")
         if trg is None:
             trg = src
         nt = trg.shape[1]
         _dev(trg, (3, nt), "trg")
         self.ns, self.nt = ns, nt
-        self._keep = (src, w, trg)
+        self._keep = (src, w, nrm, trg)
         h = ctypes.c_void_p()
-        _check(lib.stokes_sl_tree_create(ns, _ptr(src), _ptr(w), nt, _ptr(trg), float(theta),
-                                         int(order), ctypes.byref(h), _stream(stream)))
+        _check(lib.stokes_tree_create(ns, _ptr(src), _ptr(nrm), _ptr(w), nt, _ptr(trg),
+                                      float(alpha), float(beta), float(theta), int(order),
+                                      ctypes.byref(h), _stream(stream)))
         self.h = h
 
     def apply(self, sigma, out=None, stream=None):
@@ -258,19 +261,19 @@ class SlTree:
         if out is None:
             out = torch.empty((3, self.nt), dtype=torch.float64, device=sigma.device)
         _dev(out, (3, self.nt), "out")
-        _check(lib.stokes_sl_tree_apply(self.h, _ptr(sigma), _ptr(out), _stream(stream)))
+        _check(lib.stokes_tree_apply(self.h, _ptr(sigma), _ptr(out), _stream(stream)))
         return out
 
     def stats(self):
         pairs = ctypes.c_double()
         counts = (ctypes.c_int64 * 4)()
-        _check(lib.stokes_sl_tree_stats(self.h, ctypes.byref(pairs), counts))
+        _check(lib.stokes_tree_stats(self.h, ctypes.byref(pairs), counts))
         return {"pairs": pairs.value, "cells": counts[0], "proxies": counts[1],
                 "entries": counts[2], "target_blocks": counts[3]}
 
     def close(self):
         if self.h is not None and self.h.value:
-            _check(lib.stokes_sl_tree_destroy(self.h))
+            _check(lib.stokes_tree_destroy(self.h))
         self.h = None
 
     def __del__(self):
@@ -278,6 +281,13 @@ class SlTree:
             self.close()
         except Exception:
             pass
+
+
+class SlTree(StokesTree):
+    """StokesTree of the single layer alone (alpha = 1, beta = 0)."""
+
+    def __init__(self, src, w, trg=None, theta=0.5, order=8, stream=None):
+        super().__init__(src, w, None, trg, 1.0, 0.0, theta, order, stream)
 
 
 def dl_apply(src, nrm, w, sigma, trg, prec="fp32c", out=None, stream=None):

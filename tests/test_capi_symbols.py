@@ -192,27 +192,30 @@ def test_host_buffer_calls_validate_on_host(libsbq):
 
 
 def test_tree_arguments_rejected_on_host(libsbq):
-    """stokes_sl_tree_create validates sizes, pointers, theta and order before touching a
-    device; apply / stats / destroy reject a handle that is not a tree."""
+    """stokes_tree_create validates sizes, pointers, coefficients, theta and order before
+    touching a device; apply / destroy reject a handle that is not a tree."""
     vp, i64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
-    f = libsbq.stokes_sl_tree_create
-    f.argtypes = [i64, vp, vp, i64, vp, dbl, ctypes.c_int, ctypes.POINTER(vp), vp]
+    f = libsbq.stokes_tree_create
+    f.argtypes = [i64, vp, vp, vp, i64, vp, dbl, dbl, dbl, ctypes.c_int, ctypes.POINTER(vp), vp]
     libsbq.sbq_last_error.restype = ctypes.c_char_p
     fake = vp(16)
     h = vp()
-    assert f(10, fake, fake, 10, fake, 0.5, 8, None, None) == 1
-    assert f(-1, fake, fake, 10, fake, 0.5, 8, ctypes.byref(h), None) == 1
-    assert f(10, None, fake, 10, fake, 0.5, 8, ctypes.byref(h), None) == 1
+    assert f(10, fake, None, fake, 10, fake, 1.0, 0.0, 0.5, 8, None, None) == 1
+    assert f(-1, fake, None, fake, 10, fake, 1.0, 0.0, 0.5, 8, ctypes.byref(h), None) == 1
+    assert f(10, None, None, fake, 10, fake, 1.0, 0.0, 0.5, 8, ctypes.byref(h), None) == 1
+    # the double layer needs normals
+    assert f(10, fake, None, fake, 10, fake, 1.0, 1.0, 0.5, 8, ctypes.byref(h), None) == 1
+    assert f(10, fake, fake, fake, 10, fake, float("inf"), 1.0, 0.5, 8, ctypes.byref(h), None) == 1
     for theta in (0.0, 1.0, float("nan")):
-        assert f(10, fake, fake, 10, fake, theta, 8, ctypes.byref(h), None) == 1
+        assert f(10, fake, None, fake, 10, fake, 1.0, 0.0, theta, 8, ctypes.byref(h), None) == 1
         assert b"theta" in libsbq.sbq_last_error()
     for order in (1, 11):
-        assert f(10, fake, fake, 10, fake, 0.5, order, ctypes.byref(h), None) == 1
+        assert f(10, fake, None, fake, 10, fake, 1.0, 0.0, 0.5, order, ctypes.byref(h), None) == 1
         assert b"order" in libsbq.sbq_last_error()
     assert h.value is None
-    libsbq.stokes_sl_tree_destroy.argtypes = [vp]
-    assert libsbq.stokes_sl_tree_destroy(None) == 0
+    libsbq.stokes_tree_destroy.argtypes = [vp]
+    assert libsbq.stokes_tree_destroy(None) == 0
     bogus = (ctypes.c_uint32 * 8)()
-    libsbq.stokes_sl_tree_apply.argtypes = [vp, vp, vp, vp]
-    assert libsbq.stokes_sl_tree_apply(ctypes.cast(bogus, vp), fake, fake, None) == 1
+    libsbq.stokes_tree_apply.argtypes = [vp, vp, vp, vp]
+    assert libsbq.stokes_tree_apply(ctypes.cast(bogus, vp), fake, fake, None) == 1
     assert b"tree" in libsbq.sbq_last_error()
