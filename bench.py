@@ -95,6 +95,8 @@ def parse(argv=None):
                     help="quadrature: panels of the random loop (x 128 nodes)")
     ap.add_argument("--near-factor", type=float, default=1.0,
                     help="quadrature: near region of an element, radius + f max(length, 2 radius)")
+    ap.add_argument("--tree-panels", default="8192,32768",
+                    help="tree: loop panel counts (8 x 16 nodes each), comma separated")
     ap.add_argument("--build-only", action="store_true",
                     help="quadrature: only build the Stokes E of the random loop (--quad-panels), "
                          "--kernel-reps times inside the NVTX range 'kernel_only'")
@@ -1508,7 +1510,7 @@ def run_tree(args):
         return out, float(np.median(ms))
 
     rows = []
-    for panels in (8192, 32768):
+    for panels in [int(v) for v in args.tree_panels.split(",")]:
         s = I.random_loop(seed=1, panels=panels, ns=8, nth=16)
         n = s.size
         src, w = t(s.x), t(s.w)
