@@ -24,6 +24,7 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <unordered_map>
 #include <vector>
 
 struct sbq_tree_s {
@@ -502,7 +503,10 @@ static int tree_create_impl(long long ns, const double *src, const double *nrm, 
 
     // proxies of every cell
     long long np = 0;
-    for (HostCell &c : S.cells) {
+    std::unordered_map<int, int> cell_of_proxy;
+    for (size_t ci = 0; ci < S.cells.size(); ++ci) {
+        HostCell &c = S.cells[ci];
+        cell_of_proxy[static_cast<int>(np)] = static_cast<int>(ci);
         c.nprox = proxies_per_dim(c, order, c.n);
         c.pfirst = static_cast<int>(np);
         np += c.nprox;
@@ -600,13 +604,6 @@ static int tree_create_impl(long long ns, const double *src, const double *nrm, 
         }
         tb.push_back(B);
     }
-    // P2M work items: every cell, its sources in chunks
-    std::vector<int4> h_chunks;
-    for (size_t ci = 0; ci < S.cells.size(); ++ci) {
-        const HostCell &c = S.cells[ci];
-        for (int b = 0; b < c.count; b += TR_CHUNK)
-            h_chunks.push_back(make_int4(static_cast<int>(ci), c.first + b, std::min(TR_CHUNK, c.count - b), 0));
-    }
     // lists: per target block, a traversal of the source tree
     std::vector<int4> h_tleaf;
     std::vector<TrEntry> h_ent;
@@ -636,6 +633,20 @@ static int tree_create_impl(long long ns, const double *src, const double *nrm, 
             }
         }
         h_tleaf.push_back(make_int4(L.first, L.count, e0, static_cast<int>(h_ent.size()) - e0));
+    }
+    // P2M work items: the cells some list takes as far (the others need no proxy charges),
+    // their sources in chunks
+    std::vector<char> used(S.cells.size(), 0);
+    for (const TrEntry &en : h_ent)
+        if (en.kind == 1)
+            used[cell_of_proxy[en.first]] = 1;
+    std::vector<int4> h_chunks;
+    for (size_t ci = 0; ci < S.cells.size(); ++ci) {
+        if (!used[ci])
+            continue;
+        const HostCell &c = S.cells[ci];
+        for (int b = 0; b < c.count; b += TR_CHUNK)
+            h_chunks.push_back(make_int4(static_cast<int>(ci), c.first + b, std::min(TR_CHUNK, c.count - b), 0));
     }
     T->n_cells = static_cast<long long>(S.cells.size());
     T->n_proxies = np;
