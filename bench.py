@@ -97,6 +97,8 @@ def parse(argv=None):
                     help="quadrature: near region of an element, radius + f max(length, 2 radius)")
     ap.add_argument("--tree-panels", default="8192,32768",
                     help="tree: loop panel counts (8 x 16 nodes each), comma separated")
+    ap.add_argument("--tree-solve-panels", type=int, default=2048,
+                    help="tree: loop panels of the GMRES-IR solve with treecode inner solves (0: none)")
     ap.add_argument("--build-only", action="store_true",
                     help="quadrature: only build the Stokes E of the random loop (--quad-panels), "
                          "--kernel-reps times inside the NVTX range 'kernel_only'")
@@ -1553,7 +1555,39 @@ def run_tree(args):
                      "cells": st["cells"], "proxies": st["proxies"], "list_entries": st["entries"],
                      "err_vs_fp64": err_tree, "direct_fp32_ms": direct_ms,
                      "direct_fp32_err_vs_fp64": err_direct, "speedup": direct_ms / tree_ms})
-    print(json.dumps({"workload": "treecode_random_loop", "rows": rows}), flush=True)
+    solve = None
+    if args.tree_solve_panels > 0:
+        # GMRES-IR for K = I/2 + D + eta S + E (tube correction, near factor 0.5) with FP64
+        # residuals: treecode inner solves against compensated-FP32 direct ones
+        P = args.tree_solve_panels
+        s = I.random_loop(seed=1, panels=P, ns=8, nth=16)
+        n = s.size
+        src, nrm, w = t(s.x), t(s.n), t(s.w)
+        eta = sbq.slender_eta(0.01)
+        E = sbq.tube_correction(src, nrm, w, P, 8, 16, kind="stokes", alpha=eta, beta=1.0,
+                                near_factor=0.5)
+        op = sbq.StokesOp(src, nrm, w, eta, correction=E)
+        rhs = t(rng.standard_normal((3, n)))
+        res = {}
+        for name, inner in (("treecode_inner", "fp32"), ("compensated_fp32_inner", "fp32c")):
+            if inner == "fp32":
+                op.set_tree(0.5, 8)
+            else:
+                op.set_tree(0.0)
+                op.autotune("fp32c")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            x, rep = op.solve(rhs, tol=1e-10, inner_prec=inner, inner_tol=1e-5, resid_prec="fp64")
+            torch.cuda.synchronize()
+            res[name] = {"ms": (time.perf_counter() - t0) * 1e3, "iters": rep["iters"],
+                         "refinements": rep["outer_iters"], "rel_res": rep["rel_res"],
+                         "status": rep["status_name"]}
+            res[name + "_x"] = x
+        res["solution_rel_diff"] = float((res.pop("treecode_inner_x") - res["compensated_fp32_inner_x"]).abs().max().item()
+                                         / res.pop("compensated_fp32_inner_x").abs().max().item())
+        op.close()
+        solve = {"nodes": n, "eta": eta, "near_factor": 0.5, "tol": 1e-10, **res}
+    print(json.dumps({"workload": "treecode_random_loop", "rows": rows, "solve": solve}), flush=True)
     return 0
 
 

@@ -444,6 +444,15 @@ SBQ_API int laplace_op_create(int64_t n, const double *src, const double *nrm, c
  * tensor, or a handle without the mobility set-up.
  */
 SBQ_API int stokes_op_set_mobility(void *op, int nbody, const int64_t *body_off, void *stream);
+/* Far-field acceleration inside the operator: after stokes_op_set_tree(op, theta, order)
+ * every apply of the operator in SBQ_FP32 (the plain FP32 pair sum; the inner solves of
+ * gmres_solve with inner_prec = SBQ_FP32) evaluates eta S + D with the treecode of
+ * stokes_tree_create (theta, order as there) and adds the correction E and the diagonal as
+ * before; the other precisions keep the direct sums.  Builds the trees from the operator's
+ * geometry (host set-up, once); theta <= 0 removes the treecode.  Synchronises the stream.
+ * Errors: SBQ_EINVAL for a Laplace or batched operator, theta >= 1 or order outside
+ * 2..10. */
+SBQ_API int stokes_op_set_tree(void *op, double theta, int order, void *stream);
 /* Correction of the single layer alone for stokes_mobility_rhs: S nu is then the punctured
  * sum plus this E times nu (Eq. nystrom-correction with the kernel S; e.g. tube_correction
  * with alpha = 1, beta = 0).  CSR over the operator's nodes as for stokes_op_create (device

@@ -593,6 +593,21 @@ SBQ_API int stokes_op_set_mobility(void *oph, int nbody, const int64_t *body_off
     return mob_setup(op, nbody, body_off, static_cast<cudaStream_t>(stream));
 }
 
+SBQ_API int stokes_op_set_tree(void *oph, double theta, int order, void *stream)
+{
+    clear_error();
+    Op *op = as_op(oph);
+    if (!op)
+        return fail(SBQ_EINVAL, "not an operator handle");
+    if (!std::isfinite(theta))
+        return fail(SBQ_EINVAL, "stokes_op_set_tree: non-finite theta");
+    std::lock_guard<std::mutex> lk(op->mu);
+    const int st = tree_op_attach(op, theta, order, static_cast<cudaStream_t>(stream));
+    if (st == SBQ_OK)
+        SBQ_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    return st;
+}
+
 SBQ_API int stokes_op_set_sl_correction(void *oph, int64_t nnz, const int64_t *rowptr,
                                         const int64_t *col, const double *val, void *stream)
 {

@@ -124,6 +124,7 @@ Op::~Op()
 {
     if (gm)
         gmres_destroy(gm);
+    tree_op_free(this);
 }
 
 // ---------------------------------------------------------------------------
@@ -729,7 +730,10 @@ int op_autotune(Op *op, int prec, cudaStream_t s)
 
 int op_matvec(Op *op, const double *sigma, double *out, int prec, cudaStream_t s, double *bound)
 {
-    SBQ_TRY(op_ensure_tuned(op, prec, s));
+    // an attached treecode takes the plain FP32 applies (inner solves)
+    const bool tree = prec == SBQ_FP32 && op->tree != nullptr && bound == nullptr;
+    if (!tree)
+        SBQ_TRY(op_ensure_tuned(op, prec, s));
     int kind;
     double scale, kappa;
     op_kind(op, &kind, &scale, &kappa);
@@ -743,9 +747,12 @@ int op_matvec(Op *op, const double *sigma, double *out, int prec, cudaStream_t s
         SBQ_TRY(mob_field(op, sigma, -1.0, op->mob->y.as<double>(), s));
         y = op->mob->y.as<double>();
     }
-    SBQ_TRY(run_pairsum(kind, prec, op_srcpack(op, prec), *op->ts[prec], op->w.as<double>(), y,
-                        n, op->src.as<double>(), n, out, scale, kappa, op->diag, y, s,
-                        bound, op->perm.as<int>()));
+    if (tree)
+        SBQ_TRY(tree_op_apply(op, y, out, s));
+    else
+        SBQ_TRY(run_pairsum(kind, prec, op_srcpack(op, prec), *op->ts[prec], op->w.as<double>(), y,
+                            n, op->src.as<double>(), n, out, scale, kappa, op->diag, y, s,
+                            bound, op->perm.as<int>()));
     if (op->nnz > 0)
         SBQ_CUDA(launch_csr_apply(op->ncomp * n, op->rowptr.as<int64_t>(), op->col.as<int64_t>(),
                                   op->val.as<double>(), y, out, s));

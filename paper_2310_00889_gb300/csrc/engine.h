@@ -75,6 +75,11 @@ struct MobState {
     DevBuf x, w, body_of, blk, bodyblk, cen, area, iinv, part, rigid, y, r;
 };
 
+// treecode (tree.cu) attached to an operator: replaces its plain FP32 pair sum
+int tree_op_attach(struct Op *op, double theta, int order, cudaStream_t s);
+int tree_op_apply(struct Op *op, const double *y, double *out, cudaStream_t s);
+void tree_op_free(struct Op *op);
+
 struct Op {
     uint32_t magic = OP_MAGIC;
     int device = 0;
@@ -95,6 +100,7 @@ struct Op {
     std::mutex mu;
     struct GmresWS *gm = nullptr;      // solver workspace (gmres.cu)
     std::unique_ptr<MobState> mob;     // set: the operator is K (I - L) + L (mobility)
+    void *tree = nullptr;              // treecode (tree.cu) for applies in SBQ_FP32, or null
     ~Op();
 };
 

@@ -885,7 +885,7 @@ int gmres_solve_impl(Op *op, const double *b, double *x, const sbq_gmres_opts &o
         return SBQ_ENOMEM;
     }
     SBQ_TRY(op_ensure_tuned(op, hp, s));
-    if (mixed)
+    if (mixed && !(low == SBQ_FP32 && op->tree))   // an attached treecode needs no tile shape
         SBQ_TRY(op_ensure_tuned(op, low, s));
 
     std::vector<double> bnorm, res, tol_abs(nseg);

@@ -732,6 +732,94 @@ static int tree_apply_impl(sbq_tree_s *T, const double *sigma, double *u, cudaSt
     return T->nq == 3 ? tree_apply_nq<3>(T, sigma, u, s) : tree_apply_nq<1>(T, sigma, u, s);
 }
 
+// ---- a treecode attached to an operator (engine.h): the operator's K = diag I + D + eta S
+// with the pair sum by the treecode, in the caller's node order
+
+__global__ void k_tree_unperm(long long n, const int *__restrict__ perm, const double *__restrict__ in,
+                              double *out)
+{
+    const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (i >= n)
+        return;
+    const long long o = perm[i];
+    for (int d = 0; d < 3; ++d)
+        out[d * n + o] = in[d * n + i];
+}
+
+__global__ void k_tree_add_diag(long long m, double diag, const double *__restrict__ y, double *out)
+{
+    const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (i < m)
+        out[i] += diag * y[i];
+}
+
+void tree_op_free(Op *op)
+{
+    delete static_cast<sbq_tree_s *>(op->tree);
+    op->tree = nullptr;
+}
+
+int tree_op_attach(Op *op, double theta, int order, cudaStream_t s)
+{
+    tree_op_free(op);
+    if (theta <= 0.0)
+        return SBQ_OK;
+    if (op->laplace) {
+        set_error("stokes_op_set_tree: the treecode serves the Stokes operator");
+        return SBQ_EINVAL;
+    }
+    if (op->plan.nseg > 1) {
+        set_error("stokes_op_set_tree: a batched operator (independent segments) takes no treecode");
+        return SBQ_EINVAL;
+    }
+    if (!(theta < 1.0) || order < 2 || order > 10) {
+        set_error("stokes_op_set_tree: theta must be in (0, 1) and order in 2..10");
+        return SBQ_EINVAL;
+    }
+    const long long n = op->n;
+    DevBuf src, nrm, w;
+    SBQ_TRY(src.alloc(3 * std::max<long long>(n, 1) * sizeof(double)));
+    SBQ_TRY(nrm.alloc(3 * std::max<long long>(n, 1) * sizeof(double)));
+    SBQ_TRY(w.alloc(std::max<long long>(n, 1) * sizeof(double)));
+    if (n > 0) {
+        const unsigned g = static_cast<unsigned>((n + 255) / 256);
+        k_tree_unperm<<<g, 256, 0, s>>>(n, op->perm.as<int>(), op->src.as<double>(), src.as<double>());
+        k_tree_unperm<<<g, 256, 0, s>>>(n, op->perm.as<int>(), op->nrm.as<double>(), nrm.as<double>());
+        SBQ_CUDA(cudaGetLastError());
+        // weights: one component
+        std::vector<int> hp(n);
+        std::vector<double> hw(n), hwo(n);
+        SBQ_CUDA(cudaMemcpyAsync(hp.data(), op->perm.p, n * sizeof(int), cudaMemcpyDeviceToHost, s));
+        SBQ_CUDA(cudaMemcpyAsync(hw.data(), op->w.p, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        SBQ_CUDA(cudaStreamSynchronize(s));
+        for (long long i = 0; i < n; ++i)
+            hwo[hp[i]] = hw[i];
+        SBQ_CUDA(cudaMemcpyAsync(w.p, hwo.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+    sbq_tree_s *T = new sbq_tree_s();
+    cudaGetDevice(&T->device);
+    const int st = tree_create_impl(n, src.as<double>(), nrm.as<double>(), w.as<double>(), n,
+                                    src.as<double>(), op->eta, 1.0, theta, order, T, s);
+    if (st != SBQ_OK) {
+        delete T;
+        return st;
+    }
+    op->tree = T;
+    return SBQ_OK;
+}
+
+int tree_op_apply(Op *op, const double *y, double *out, cudaStream_t s)
+{
+    sbq_tree_s *T = static_cast<sbq_tree_s *>(op->tree);
+    SBQ_TRY(tree_apply_impl(T, y, out, s));
+    const long long m = 3 * op->n;
+    if (m > 0 && op->diag != 0.0) {
+        k_tree_add_diag<<<static_cast<unsigned>((m + 255) / 256), 256, 0, s>>>(m, op->diag, y, out);
+        SBQ_CUDA(cudaGetLastError());
+    }
+    return SBQ_OK;
+}
+
 }  // namespace sbq
 
 namespace {

@@ -96,6 +96,7 @@ def _load():
         "stokes_op_set_mobility": ([_vp, _int, _vp, _vp], _int),
         "stokes_mobility_rhs": ([_vp, _vp, _vp, _vp, _int, _vp], _int),
         "stokes_op_set_sl_correction": ([_vp, _i64, _vp, _vp, _vp, _vp], _int),
+        "stokes_op_set_tree": ([_vp, _dbl, _int, _vp], _int),
         "stokes_mobility_velocity": ([_vp, _vp, _vp, _vp], _int),
         "stokes_matvec_bounded": ([_vp, _vp, _vp, _vp, _vp], _int),
         "gmres_solve": ([_vp, _vp, _vp, ctypes.POINTER(GmresOpts), ctypes.POINTER(GmresReport),
@@ -549,6 +550,11 @@ class StokesOp:
         c_off = (ctypes.c_int64 * off.size)(*[int(v) for v in off])
         _check(lib.stokes_op_set_mobility(self.handle, int(off.size - 1), c_off, _stream(stream)))
         self.nbody = int(off.size - 1)
+
+    def set_tree(self, theta=0.5, order=8, stream=None):
+        """Applies in "fp32" (and inner solves with inner_prec="fp32") then take the treecode
+        (stokes_op_set_tree); theta <= 0 removes it."""
+        _check(lib.stokes_op_set_tree(self.handle, float(theta), int(order), _stream(stream)))
 
     def set_sl_correction(self, correction, stream=None):
         """Correction (rowptr, col, val) of the single layer alone, used by mobility_rhs for

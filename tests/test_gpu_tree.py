@@ -140,3 +140,38 @@ def test_tree_double_layer_alone(sbq, oracle_mod):
     err = _rel(u[:, sub], ref)
     print("treecode, double layer, torus: %.3e" % err)
     assert err < 1e-5
+
+
+def test_tree_as_inner_operator_of_gmres_ir(sbq, oracle_mod):
+    """The treecode attached to the operator K = I/2 + D + eta S + E (tube correction of the
+    slender loop, 65,536 nodes): the FP32 matvec agrees with the FP64 one, and GMRES-IR with
+    treecode inner solves and FP64 residuals reaches the same 1e-10 solution as with
+    compensated-FP32 inner solves."""
+    import torch
+    S = I.random_loop(seed=1, panels=512, ns=8, nth=16)
+    n = S.size
+    src, nrm, w = _t(S.x), _t(S.n), _t(S.w)
+    eta = sbq.slender_eta(0.01)
+    E = sbq.tube_correction(src, nrm, w, 512, 8, 16, kind="stokes", alpha=eta, beta=1.0,
+                            near_factor=0.5)
+    op = sbq.StokesOp(src, nrm, w, eta, correction=E)
+    rng = np.random.default_rng(47)
+    x = _t(rng.standard_normal((3, n)))
+    k64 = op.matvec(x, prec="fp64").cpu().numpy()
+    op.set_tree(0.5, 8)
+    kt = op.matvec(x, prec="fp32").cpu().numpy()
+    err = _rel(kt, k64)
+    print("operator with treecode, fp32 matvec against fp64: %.3e" % err)
+    assert err < 1e-5
+    rhs = _t(rng.standard_normal((3, n)))
+    xt, rt = op.solve(rhs, tol=1e-10, inner_prec="fp32", inner_tol=1e-5, resid_prec="fp64")
+    op.set_tree(0.0)
+    xc, rc = op.solve(rhs, tol=1e-10, inner_prec="fp32c", inner_tol=1e-5, resid_prec="fp64")
+    op.close()
+    diff = (xt - xc).abs().max().item() / xc.abs().max().item()
+    print("GMRES-IR, treecode inner: %d iterations, %d refinements, rel res %.2e; compensated "
+          "FP32 inner: %d iterations; solutions differ by %.2e"
+          % (rt["iters"], rt["outer_iters"], rt["rel_res"], rc["iters"], diff))
+    assert rt["status"] == 0 and rc["status"] == 0
+    assert rt["rel_res"] <= 1e-10
+    assert diff < 1e-8
