@@ -30,8 +30,8 @@ ROWS = 4096
 # compensated-FP32, double-float and FP64 errors, 2x the plain FP32 error (which grows with
 # the number of terms summed in FP32), rounded up.
 BARS = {
-    ("loop1m", "fp32c"): (9.5e-7, 2.9e-6),
-    ("loop1m", "fp32"): (1.12e-3, 2.3e-3),
+    ("loop1m", "fp32c"): (7.3e-7, 2.2e-6),
+    ("loop1m", "fp32"): (3.34e-4, 6.7e-4),
     ("loop1m", "df32"): (5.9e-14, 1.8e-13),
     ("batch", "fp32c"): (2.89e-6, 8.7e-6),
     ("batch", "fp32"): (6.6e-5, 1.4e-4),
