@@ -411,6 +411,7 @@ k_tree_eval(const int4 *__restrict__ tleaf, const TrEntry *__restrict__ entries,
             const int cnt = min(TR_THREADS, en.count - base);
             // the target's own node (same tree, a source block): its sorted index
             const int self = (same && en.kind == 0) ? tl.x + t - en.first - base : -1;
+#pragma unroll 4
             for (int kk = 0; kk < cnt; ++kk) {
                 const float4 y = sp[kk], qq = sq[kk * NQ];
                 float r0 = xx - y.x, r1 = xy - y.y, r2 = xz - y.z;
@@ -421,8 +422,10 @@ k_tree_eval(const int4 *__restrict__ tleaf, const TrEntry *__restrict__ entries,
                     r2 = two_diff3(x.z, y.z, en.dz, xl.z - yl.z - en.lz);
                 }
                 const float rr = fmaf(r0, r0, fmaf(r1, r1, r2 * r2));
-                if (kk != self && rr > 0.0f) {
-                    const float ri = rsqrtf(rr);
+                {
+                    // the target's own node and a source on the target itself add nothing
+                    // (selects, no branch)
+                    const float ri = (kk == self || !(rr > 0.0f)) ? 0.0f : rsqrtf(rr);
                     const float ri2 = ri * ri, ri3 = ri * ri2;
                     // single layer: q / r + r (r . q) / r^3
                     float rq = fmaf(r0, qq.x, fmaf(r1, qq.y, r2 * qq.z)) * ri3;
