@@ -1,23 +1,26 @@
-// Far-field acceleration of the Stokes single-layer sum for large N (the paper evaluates its
-// far field with an FMM, Sec. 3.2, and states the O(N^2) direct cost it replaces, Sec. 3.4):
-// a barycentric Lagrange treecode on the GPU.
+// Far-field acceleration of the layer sums alpha S + beta D for large N (the paper evaluates
+// its far field with an FMM, Sec. 3.2, and states the O(N^2) direct cost it replaces,
+// Sec. 3.4): a barycentric Lagrange treecode on the GPU.
 //
 // Setup (host, once per geometry): an octree over the sources (Morton order, tight boxes,
 // leaves of at most TR_LEAF sources) and one over the targets (the same tree when the
 // targets are the sources); every cell gets a tensor grid of Chebyshev points of the second
 // kind on its box, n_d points along dimension d with n_d ~ order * (h_d / h_max)^(1/3) (a
 // slender cell needs few points across); targets in blocks of up to 128 consecutive points
-// in Morton order inside one cell of at most 512 targets, and for every block a list: the proxy grid of every cell that is far
-// (acceptance: distance between the centres minus the block's radius >= cell radius /
-// theta, and the cell holds more sources than proxies) and the sources of every leaf it
-// reaches.
-// Apply (GPU, per density): charges q_k = w_k sigma_k; proxy charges of every cell,
-// q_m = sum_k L_m(y_k) q_k with L_m the tensor Lagrange basis of the grid (barycentric
-// form); then one CTA per target block sums the Stokeslet over its list, each list entry in
-// FP32 and the entries' sums in FP64.  Positions are kept in FP32 relative to the centre of
-// their leaf (sources), block (targets) or cell (proxies), and each entry carries the offset
-// between its frame and the target block's, so that near pairs lose no digits to large
-// absolute coordinates.
+// in Morton order inside one cell of at most 512 targets, and for every block a list: the
+// proxy grid of every cell that is far (acceptance: distance between the centres minus the
+// block's radius >= cell radius / theta, and the cell holds more sources than proxies) and
+// the sources of every leaf it reaches.
+// Apply (GPU, per density): charge records of the sources (q = w sigma scaled for the single
+// layer and, with the double layer, the tensor q n^T); proxy charges q_m = sum_k L_m(y_k)
+// q_k, L_m the tensor Lagrange basis of the grid (barycentric form), for the cells some list
+// takes as far; then one CTA per target block sums the kernel over its list, each list
+// entry in FP32 and the entries' sums in FP64.  Positions are kept in FP32 relative to the
+// centre of their leaf (sources), block (targets) or cell (proxies), and each entry carries
+// the offset between its frame and the target block's, so that near pairs lose no digits to
+// large absolute coordinates; with the double layer, near source blocks also take the
+// rounding residuals of those offsets (exact differences), since on the surface r . n is
+// O(|r|^2).
 #include "engine.h"
 
 #include <algorithm>
@@ -36,7 +39,6 @@ struct sbq_tree_s {
     int order = 0;
     long long n_cells = 0, n_proxies = 0, n_entries = 0, n_tleaves = 0;
     double pairs = 0.0;             // kernel evaluations per apply
-    int max_level = 0;
     // device data
     sbq::DevBuf perm_s, perm_t;     // sorted position -> original index
     sbq::DevBuf w_sorted;           // FP64 weights, sorted order
@@ -513,7 +515,6 @@ static int tree_create_impl(long long ns, const double *src, const double *nrm, 
         c.nprox = proxies_per_dim(c, order, c.n);
         c.pfirst = static_cast<int>(np);
         np += c.nprox;
-        T->max_level = std::max(T->max_level, c.level);
     }
     if (np > 0x7fffffffLL) {
         set_error("stokes_tree_create: too many proxy points");
