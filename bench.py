@@ -1555,6 +1555,31 @@ def run_tree(args):
                      "cells": st["cells"], "proxies": st["proxies"], "list_entries": st["entries"],
                      "err_vs_fp64": err_tree, "direct_fp32_ms": direct_ms,
                      "direct_fp32_err_vs_fp64": err_direct, "speedup": direct_ms / tree_ms})
+    # the headline geometry (helix wall, caps, 100 spheres; 1.1M nodes): the operator's
+    # combined field by the treecode against the compensated-FP32 direct sum the benchmark
+    # line times
+    hs, heps, hsig = headline_inputs(args.helix_panels)
+    hsrc, hnrm, hw, hs_sig = t(hs.x), t(hs.n), t(hs.w), t(hsig)
+    heta = sbq.slender_eta(heps)
+    hsub = np.sort(rng.choice(hs.size, 2048, replace=False))
+    href = sbq.combined_apply(hsrc, hnrm, hw, hs_sig, t(hs.x[:, hsub]), heta, 1.0, prec="fp64").cpu().numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    htree = sbq.StokesTree(hsrc, hw, nrm=hnrm, alpha=heta, beta=1.0, theta=0.5, order=8)
+    torch.cuda.synchronize()
+    hsetup = (time.perf_counter() - t0) * 1e3
+    hu, hms = timed(lambda: htree.apply(hs_sig), 5)
+    herr = float(np.abs(hu.cpu().numpy()[:, hsub] - href).max() / np.abs(href).max())
+    hst = htree.stats()
+    htree.close()
+    del hu
+    hd, hdms = timed(lambda: sbq.combined_apply(hsrc, hnrm, hw, hs_sig, hsrc, heta, 1.0, prec="fp32c"), 1)
+    hderr = float(np.abs(hd.cpu().numpy()[:, hsub] - href).max() / np.abs(href).max())
+    del hd
+    torch.cuda.empty_cache()
+    helix = {"nodes": hs.size, "eta": heta, "setup_ms": hsetup, "apply_ms": hms, "err_vs_fp64": herr,
+             "kernel_evaluations": hst["pairs"], "direct_pairs": float(hs.size) ** 2,
+             "direct_fp32c_ms": hdms, "direct_fp32c_err_vs_fp64": hderr, "speedup": hdms / hms}
     solve = None
     if args.tree_solve_panels > 0:
         # GMRES-IR for K = I/2 + D + eta S + E (tube correction, near factor 0.5) with FP64
@@ -1587,7 +1612,8 @@ def run_tree(args):
                                          / res.pop("compensated_fp32_inner_x").abs().max().item())
         op.close()
         solve = {"nodes": n, "eta": eta, "near_factor": 0.5, "tol": 1e-10, **res}
-    print(json.dumps({"workload": "treecode_random_loop", "rows": rows, "solve": solve}), flush=True)
+    print(json.dumps({"workload": "treecode_random_loop", "rows": rows, "headline_geometry": helix,
+                      "solve": solve}), flush=True)
     return 0
 
 
