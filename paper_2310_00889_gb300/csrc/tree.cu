@@ -373,8 +373,53 @@ __device__ __forceinline__ float two_diff3(float a, float b, float c, float lo)
     return s2 + ((e1 + e2) + lo);
 }
 
-// Stokeslet sums: one CTA per target block, one thread per target; list entries staged in
-// shared memory 128 points at a time
+// Packed FP32 pairs: one 64-bit register holds the values of two sources; the f32x2
+// instructions process both in one issue slot.
+using tf2 = unsigned long long;
+
+__device__ __forceinline__ tf2 tf2_fma(tf2 a, tf2 b, tf2 c)
+{
+    tf2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ tf2 tf2_mul(tf2 a, tf2 b)
+{
+    tf2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ tf2 tf2_sub(tf2 a, tf2 b)
+{
+    tf2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ tf2 tf2_pack(float lo, float hi)
+{
+    tf2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void tf2_unpack(tf2 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+// Shared-memory tile of TR_THREADS points as packed pairs: field f of points 2m and 2m + 1
+// at f2 index f * (TR_THREADS / 2) + m.  Fields: 0..2 position, 3..5 single-layer charge,
+// then (NQ == 3) 6..14 the double layer's tensor d_jl and 15..17 the position residuals.
+constexpr int TR_HALF = TR_THREADS / 2;
+
+template <int NQ>
+__host__ __device__ constexpr int tree_fields()
+{
+    return NQ == 3 ? 18 : 6;
+}
+
+// Sums over the list of a target block: one CTA per block, one thread per target; list
+// entries staged in shared memory TR_THREADS points at a time, two sources per packed
+// FP32x2 operation; each entry summed in FP32, the entries' sums in FP64.
 template <int NQ>
 __global__ void __launch_bounds__(TR_THREADS)
 k_tree_eval(const int4 *__restrict__ tleaf, const TrEntry *__restrict__ entries,
@@ -383,73 +428,125 @@ k_tree_eval(const int4 *__restrict__ tleaf, const TrEntry *__restrict__ entries,
             const float4 *__restrict__ prox_q, const int *__restrict__ perm_t, long long nt,
             int same, const float4 *__restrict__ trg_lo, const float4 *__restrict__ src_lo, double *u)
 {
-    __shared__ float4 sp[TR_THREADS], sq[TR_THREADS * NQ], sl[NQ == 3 ? TR_THREADS : 1];
+    constexpr int NF = tree_fields<NQ>();
+    __shared__ __align__(16) float sf[NF * TR_THREADS];
     const int4 tl = tleaf[blockIdx.x];
     const int t = threadIdx.x;
     const bool live = t < tl.y;
     const float4 x = live ? trg_loc[tl.x + t] : make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 xl = (NQ == 3 && live) ? trg_lo[tl.x + t] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const tf2 *F = reinterpret_cast<const tf2 *>(sf);
     double v0 = 0.0, v1 = 0.0, v2 = 0.0;
     for (int e = 0; e < tl.w; ++e) {
-        float u0 = 0.f, u1 = 0.f, u2 = 0.f;   // this block's sum in FP32, the total in FP64
         const TrEntry en = entries[tl.z + e];
         const float4 *P = en.kind ? prox_loc : src_loc;
         const float4 *Q = en.kind ? prox_q : q;
         // target in the block's frame
         const float xx = x.x - en.dx, xy = x.y - en.dy, xz = x.z - en.dz;
+        const tf2 X2 = tf2_pack(xx, xx), Y2 = tf2_pack(xy, xy), Z2 = tf2_pack(xz, xz);
         // the double layer's r . n = O(|r|^2) on the surface: near source blocks form r from
         // high and low parts with exact (TwoSum) differences, ~2^-48 of the frame offsets
         const bool hilo = NQ == 3 && en.kind == 0;
+        tf2 ax = 0ull, ay = 0ull, az = 0ull;   // packed (0.f, 0.f)
         for (int base = 0; base < en.count; base += TR_THREADS) {
             const int k = base + t;
+            // stage point t (a point past the block's end: zero charge, far away)
+            float4 pp = make_float4(1e15f, 1e15f, 1e15f, 0.f), q0 = make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 q1 = q0, q2 = q0, pl = q0;
             if (k < en.count) {
-                sp[t] = P[en.first + k];
-                for (int r = 0; r < NQ; ++r)
-                    sq[t * NQ + r] = Q[static_cast<size_t>(en.first + k) * NQ + r];
-                if (hilo)
-                    sl[t] = src_lo[en.first + k];
+                pp = P[en.first + k];
+                q0 = Q[static_cast<size_t>(en.first + k) * NQ];
+                if (NQ == 3) {
+                    q1 = Q[static_cast<size_t>(en.first + k) * NQ + 1];
+                    q2 = Q[static_cast<size_t>(en.first + k) * NQ + 2];
+                    if (hilo)
+                        pl = src_lo[en.first + k];
+                }
+            }
+            sf[0 * TR_THREADS + t] = pp.x;
+            sf[1 * TR_THREADS + t] = pp.y;
+            sf[2 * TR_THREADS + t] = pp.z;
+            sf[3 * TR_THREADS + t] = q0.x;
+            sf[4 * TR_THREADS + t] = q0.y;
+            sf[5 * TR_THREADS + t] = q0.z;
+            if (NQ == 3) {
+                sf[6 * TR_THREADS + t] = q0.w;    // d00
+                sf[7 * TR_THREADS + t] = q1.x;    // d01
+                sf[8 * TR_THREADS + t] = q1.y;    // d02
+                sf[9 * TR_THREADS + t] = q1.z;    // d10
+                sf[10 * TR_THREADS + t] = q1.w;   // d11
+                sf[11 * TR_THREADS + t] = q2.x;   // d12
+                sf[12 * TR_THREADS + t] = q2.y;   // d20
+                sf[13 * TR_THREADS + t] = q2.z;   // d21
+                sf[14 * TR_THREADS + t] = q2.w;   // d22
+                sf[15 * TR_THREADS + t] = pl.x;
+                sf[16 * TR_THREADS + t] = pl.y;
+                sf[17 * TR_THREADS + t] = pl.z;
             }
             __syncthreads();
-            const int cnt = min(TR_THREADS, en.count - base);
-            // the target's own node (same tree, a source block): its sorted index
+            const int cnt2 = (min(TR_THREADS, en.count - base) + 1) / 2;
+            // the target's own node (same tree, a source block): its index in this tile
             const int self = (same && en.kind == 0) ? tl.x + t - en.first - base : -1;
-#pragma unroll 4
-            for (int kk = 0; kk < cnt; ++kk) {
-                const float4 y = sp[kk], qq = sq[kk * NQ];
-                float r0 = xx - y.x, r1 = xy - y.y, r2 = xz - y.z;
+#pragma unroll 2
+            for (int m = 0; m < cnt2; ++m) {
+                tf2 dx, dy, dz;
                 if (hilo) {
-                    const float4 yl = sl[kk];
-                    r0 = two_diff3(x.x, y.x, en.dx, xl.x - yl.x - en.lx);
-                    r1 = two_diff3(x.y, y.y, en.dy, xl.y - yl.y - en.ly);
-                    r2 = two_diff3(x.z, y.z, en.dz, xl.z - yl.z - en.lz);
-                }
-                const float rr = fmaf(r0, r0, fmaf(r1, r1, r2 * r2));
-                {
-                    // the target's own node and a source on the target itself add nothing
-                    // (selects, no branch)
-                    const float ri = (kk == self || !(rr > 0.0f)) ? 0.0f : rsqrtf(rr);
-                    const float ri2 = ri * ri, ri3 = ri * ri2;
-                    // single layer: q / r + r (r . q) / r^3
-                    float rq = fmaf(r0, qq.x, fmaf(r1, qq.y, r2 * qq.z)) * ri3;
-                    if (NQ == 3) {
-                        // double layer: (r^T d r) r / r^5
-                        const float4 d1 = sq[kk * NQ + 1], d2 = sq[kk * NQ + 2];
-                        const float a0 = fmaf(qq.w, r0, fmaf(d1.x, r1, d1.y * r2));
-                        const float a1 = fmaf(d1.z, r0, fmaf(d1.w, r1, d2.x * r2));
-                        const float a2 = fmaf(d2.y, r0, fmaf(d2.z, r1, d2.w * r2));
-                        const float rdr = fmaf(r0, a0, fmaf(r1, a1, r2 * a2));
-                        rq = fmaf(rdr, ri3 * ri2, rq);
+                    float ya, yb, la, lb;
+                    float r[6];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const float xd = d == 0 ? x.x : (d == 1 ? x.y : x.z);
+                        const float ed = d == 0 ? en.dx : (d == 1 ? en.dy : en.dz);
+                        const float xld = d == 0 ? xl.x : (d == 1 ? xl.y : xl.z);
+                        const float eld = d == 0 ? en.lx : (d == 1 ? en.ly : en.lz);
+                        tf2_unpack(F[d * TR_HALF + m], ya, yb);
+                        tf2_unpack(F[(15 + d) * TR_HALF + m], la, lb);
+                        r[2 * d] = two_diff3(xd, ya, ed, xld - la - eld);
+                        r[2 * d + 1] = two_diff3(xd, yb, ed, xld - lb - eld);
                     }
-                    u0 = fmaf(qq.x, ri, fmaf(r0, rq, u0));
-                    u1 = fmaf(qq.y, ri, fmaf(r1, rq, u1));
-                    u2 = fmaf(qq.z, ri, fmaf(r2, rq, u2));
+                    dx = tf2_pack(r[0], r[1]);
+                    dy = tf2_pack(r[2], r[3]);
+                    dz = tf2_pack(r[4], r[5]);
+                } else {
+                    dx = tf2_sub(X2, F[0 * TR_HALF + m]);
+                    dy = tf2_sub(Y2, F[1 * TR_HALF + m]);
+                    dz = tf2_sub(Z2, F[2 * TR_HALF + m]);
                 }
+                const tf2 QX = F[3 * TR_HALF + m], QY = F[4 * TR_HALF + m], QZ = F[5 * TR_HALF + m];
+                const tf2 r2 = tf2_fma(dx, dx, tf2_fma(dy, dy, tf2_mul(dz, dz)));
+                float r2a, r2b;
+                tf2_unpack(r2, r2a, r2b);
+                // the target's own node and a point on the target itself add nothing
+                const float ra = (2 * m == self || !(r2a > 0.0f)) ? 0.0f : rsqrtf(r2a);
+                const float rb = (2 * m + 1 == self || !(r2b > 0.0f)) ? 0.0f : rsqrtf(r2b);
+                const tf2 ri = tf2_pack(ra, rb);
+                const tf2 ri2 = tf2_mul(ri, ri);
+                const tf2 rq = tf2_fma(dx, QX, tf2_fma(dy, QY, tf2_mul(dz, QZ)));
+                // u = ri (q + r [(r . q) ri^2 + (r^T d r) ri^4])
+                tf2 bq = tf2_mul(rq, ri2);
+                if (NQ == 3) {
+                    const tf2 a0 = tf2_fma(F[6 * TR_HALF + m], dx, tf2_fma(F[7 * TR_HALF + m], dy,
+                                                                           tf2_mul(F[8 * TR_HALF + m], dz)));
+                    const tf2 a1 = tf2_fma(F[9 * TR_HALF + m], dx, tf2_fma(F[10 * TR_HALF + m], dy,
+                                                                           tf2_mul(F[11 * TR_HALF + m], dz)));
+                    const tf2 a2 = tf2_fma(F[12 * TR_HALF + m], dx, tf2_fma(F[13 * TR_HALF + m], dy,
+                                                                            tf2_mul(F[14 * TR_HALF + m], dz)));
+                    const tf2 rdr = tf2_fma(dx, a0, tf2_fma(dy, a1, tf2_mul(dz, a2)));
+                    bq = tf2_fma(rdr, tf2_mul(ri2, ri2), bq);
+                }
+                ax = tf2_fma(ri, tf2_fma(bq, dx, QX), ax);
+                ay = tf2_fma(ri, tf2_fma(bq, dy, QY), ay);
+                az = tf2_fma(ri, tf2_fma(bq, dz, QZ), az);
             }
             __syncthreads();
         }
-        v0 += u0;
-        v1 += u1;
-        v2 += u2;
+        float a0, a1;
+        tf2_unpack(ax, a0, a1);
+        v0 += static_cast<double>(a0) + static_cast<double>(a1);
+        tf2_unpack(ay, a0, a1);
+        v1 += static_cast<double>(a0) + static_cast<double>(a1);
+        tf2_unpack(az, a0, a1);
+        v2 += static_cast<double>(a0) + static_cast<double>(a1);
     }
     if (live) {
         const long long o = perm_t[tl.x + t];
