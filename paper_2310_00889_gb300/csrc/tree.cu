@@ -227,41 +227,32 @@ void build_host_tree(const std::vector<double> &x, long long n, int leaf, HostTr
 // ---------------------------------------------------------------------------------------
 // device kernels
 
-// Chebyshev point j of n (second kind) on [-1, 1]; barycentric weight
-__device__ __forceinline__ double cheb_pt(int j, int n)
-{
-    return n > 1 ? cospi(static_cast<double>(j) / (n - 1)) : 0.0;
-}
+// Chebyshev points of the second kind, cos(pi j / (n - 1)), for n = 2..TR_NMAX (row n)
+__constant__ float c_cheb[TR_NMAX + 1][TR_NMAX];
 
-__device__ __forceinline__ double cheb_w(int j, int n)
-{
-    double w = (j & 1) ? -1.0 : 1.0;
-    if (j == 0 || j == n - 1)
-        w *= 0.5;
-    return w;
-}
-
-// 1D Lagrange basis values of the n-point grid at xi (barycentric form; exact at nodes)
-__device__ void lagrange_1d(double xi, int n, float *out)
+// 1D Lagrange basis values of the n-point grid at xi (barycentric form in FP32: the proxy
+// charges need ~1e-7, and the FP64 form's divisions made this the apply's second kernel)
+__device__ void lagrange_1d(float xi, int n, float *out)
 {
     if (n == 1) {
         out[0] = 1.0f;
         return;
     }
-    double den = 0.0;
+    float den = 0.0f;
     int hit = -1;
-    double t[TR_NMAX];
     for (int j = 0; j < n; ++j) {
-        const double d = xi - cheb_pt(j, n);
-        if (d == 0.0) {
+        const float d = xi - c_cheb[n][j];
+        if (d == 0.0f)
             hit = j;
-            break;
-        }
-        t[j] = cheb_w(j, n) / d;
-        den += t[j];
+        float w = (j & 1) ? -1.0f : 1.0f;
+        if (j == 0 || j == n - 1)
+            w *= 0.5f;
+        out[j] = w / d;
+        den += out[j];
     }
+    const float inv = 1.0f / den;
     for (int j = 0; j < n; ++j)
-        out[j] = hit >= 0 ? (j == hit ? 1.0f : 0.0f) : static_cast<float>(t[j] / den);
+        out[j] = hit >= 0 ? (j == hit ? 1.0f : 0.0f) : out[j] * inv;
 }
 
 // charge records of source k (sorted order): q = w sigma scaled by alpha / (8 pi) and, for
@@ -303,6 +294,9 @@ k_tree_p2m(const int4 *__restrict__ chunks, const TrCellDev *__restrict__ cells,
     const int4 ck = chunks[blockIdx.x];
     const TrCellDev c = cells[ck.x];
     const int np = c.n[0] * c.n[1] * c.n[2];
+    double ih[3];   // the cell's offset from its centre in half-widths (0 on a flat axis)
+    for (int d = 0; d < 3; ++d)
+        ih[d] = c.h[d] > 0.0 ? 1.0 / c.h[d] : 0.0;
     constexpr int MPT = 8;   // proxies per thread: 8 x 128 = 1024 >= 10^3, the largest grid
     float acc[MPT][4 * NQ];
     for (int m = 0; m < MPT; ++m)
@@ -312,9 +306,9 @@ k_tree_p2m(const int4 *__restrict__ chunks, const TrCellDev *__restrict__ cells,
         const int k = base + threadIdx.x;
         if (k < ck.z) {
             const long long s = ck.y + k;
-            double xi[3];
+            float xi[3];
             for (int d = 0; d < 3; ++d)
-                xi[d] = c.h[d] > 0.0 ? (src_abs[d * ns + s] - c.c[d]) / c.h[d] : 0.0;
+                xi[d] = static_cast<float>((src_abs[d * ns + s] - c.c[d]) * ih[d]);
             lagrange_1d(xi[0], c.n[0], Lx[threadIdx.x]);
             lagrange_1d(xi[1], c.n[1], Ly[threadIdx.x]);
             lagrange_1d(xi[2], c.n[2], Lz[threadIdx.x]);
@@ -603,6 +597,14 @@ static int tree_create_impl(long long ns, const double *src, const double *nrm, 
     const HostTree &Tt = T->same ? S : TT;
     const std::vector<double> &xt = T->same ? hs : ht;
 
+    // Chebyshev points for the proxy-charge kernel (the same values on every call)
+    {
+        float tab[TR_NMAX + 1][TR_NMAX] = {};
+        for (int n = 2; n <= TR_NMAX; ++n)
+            for (int j = 0; j < n; ++j)
+                tab[n][j] = static_cast<float>(std::cos(TR_PI * j / (n - 1)));
+        SBQ_CUDA(cudaMemcpyToSymbolAsync(c_cheb, tab, sizeof(tab), 0, cudaMemcpyHostToDevice, s));
+    }
     // proxies of every cell
     long long np = 0;
     std::unordered_map<int, int> cell_of_proxy;
