@@ -9,7 +9,8 @@
 // slender cell needs few points across); targets in blocks of up to 128 consecutive points
 // in Morton order inside one cell of at most 512 targets, and for every block a list: the
 // proxy grid of every cell that is far (acceptance: distance between the centres minus the
-// block's radius >= cell radius / theta, and the cell holds more sources than proxies) and
+// block's radius positive and >= cell radius / theta, and the cell holds more sources than
+// proxies) and
 // the sources of every leaf it reaches.
 // Apply (GPU, per density): charge records of the sources (q = w sigma scaled for the single
 // layer and, with the double layer, the tensor q n^T); proxy charges q_m = sum_k L_m(y_k)
@@ -76,11 +77,12 @@ struct TrCellDev {
     int n[3], pfirst;
 };
 
-struct TrEntry {
+struct alignas(16) TrEntry {
     int first, count, kind, pad;   // kind 0: sources [first, first + count); 1: proxies
     float dx, dy, dz, pad2;        // block frame centre minus target block centre (FP32)
     float lx, ly, lz, pad3;        // and the rounding residual of that offset
 };
+static_assert(sizeof(TrEntry) % sizeof(int4) == 0, "entries are read as int4 heads");
 
 inline TrEntry make_entry(int first, int count, int kind, const double *cb, const double *ct)
 {
@@ -411,9 +413,138 @@ __host__ __device__ constexpr int tree_fields()
     return NQ == 3 ? 18 : 6;
 }
 
-// Sums over the list of a target block: one CTA per block, one thread per target; list
-// entries staged in shared memory TR_THREADS points at a time, two sources per packed
-// FP32x2 operation; each entry summed in FP32, the entries' sums in FP64.
+// 1/sqrt(x) on the SFU, denormals flushed (callers pass squared distances of at least
+// FLT_MIN, or select the result away)
+__device__ __forceinline__ float tr_rsqrt(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// 4-byte asynchronous copy global -> shared (no register holds the value on its way)
+__device__ __forceinline__ void cp_async4(float *dst, const float *src)
+{
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Stage point k of a list entry (first, count, kind) = en into column t of the shared tile:
+// position, charge records and (double layer, source leaves) the position's rounding
+// residual, copied asynchronously; a point past the entry's end is written directly (zero
+// charge, far away).
+template <int NQ>
+__device__ __forceinline__ void tr_stage(float *sf, int t, const int4 &en, int k,
+                                         const float4 *__restrict__ src_loc, const float4 *__restrict__ q,
+                                         const float4 *__restrict__ prox_loc,
+                                         const float4 *__restrict__ prox_q, const float4 *__restrict__ src_lo)
+{
+    constexpr int NF = tree_fields<NQ>();
+    if (k < en.y) {
+        const float *P = reinterpret_cast<const float *>((en.z ? prox_loc : src_loc) + en.x + k);
+        const float *Q = reinterpret_cast<const float *>((en.z ? prox_q : q) +
+                                                         static_cast<size_t>(en.x + k) * NQ);
+        for (int f = 0; f < 3; ++f)
+            cp_async4(sf + f * TR_THREADS + t, P + f);
+        // fields 3..5: q; 6..14 (double layer): d00 d01 d02 d10 d11 d12 d20 d21 d22, the
+        // records' floats 3..11 in order
+        for (int f = 3; f < (NQ == 3 ? 15 : 6); ++f)
+            cp_async4(sf + f * TR_THREADS + t, Q + (NQ == 3 ? f - 3 : (f - 3)));
+        if (NQ == 3 && en.z == 0) {
+            const float *L = reinterpret_cast<const float *>(src_lo + en.x + k);
+            for (int f = 15; f < 18; ++f)
+                cp_async4(sf + f * TR_THREADS + t, L + (f - 15));
+        }
+    } else {
+        for (int f = 0; f < NF; ++f)
+            sf[f * TR_THREADS + t] = f < 3 ? 1e15f : 0.0f;
+    }
+}
+
+// The staged points 0 .. 2 cnt2 - 1 of one entry against the thread's target, two per packed
+// operation.  NEAR (a source leaf): the target's own node (index self) and points closer than
+// FLT_MIN add nothing, and with the double layer r is formed from high and low parts with
+// exact (TwoSum) differences, since on the surface r . n = O(|r|^2).  Far entries (proxy grids)
+// need neither: with d > 0 the distance between the centres less the block's radius, their
+// acceptance (d theta >= cell radius) keeps every target at least (1 - theta) d from every
+// proxy point.
+template <int NQ, bool NEAR>
+__device__ __forceinline__ void tr_tile(const tf2 *__restrict__ F, int cnt2, int self, const float4 &x,
+                                        const float4 &xl, const TrEntry &en, tf2 &ax, tf2 &ay, tf2 &az)
+{
+    const float xx = x.x - en.dx, xy = x.y - en.dy, xz = x.z - en.dz;
+    const tf2 X2 = tf2_pack(xx, xx), Y2 = tf2_pack(xy, xy), Z2 = tf2_pack(xz, xz);
+    constexpr float R2MIN = 1.17549435e-38f;
+    // unrolled twice for the single layer; the double layer's loop holds enough registers
+    constexpr int UNROLL = NQ == 3 ? 1 : 2;
+#pragma unroll UNROLL
+    for (int m = 0; m < cnt2; ++m) {
+        tf2 dx, dy, dz;
+        if (NEAR && NQ == 3) {
+            float ya, yb, la, lb;
+            float r[6];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const float xd = d == 0 ? x.x : (d == 1 ? x.y : x.z);
+                const float ed = d == 0 ? en.dx : (d == 1 ? en.dy : en.dz);
+                const float xld = d == 0 ? xl.x : (d == 1 ? xl.y : xl.z);
+                const float eld = d == 0 ? en.lx : (d == 1 ? en.ly : en.lz);
+                tf2_unpack(F[d * TR_HALF + m], ya, yb);
+                tf2_unpack(F[(15 + d) * TR_HALF + m], la, lb);
+                r[2 * d] = two_diff3(xd, ya, ed, xld - la - eld);
+                r[2 * d + 1] = two_diff3(xd, yb, ed, xld - lb - eld);
+            }
+            dx = tf2_pack(r[0], r[1]);
+            dy = tf2_pack(r[2], r[3]);
+            dz = tf2_pack(r[4], r[5]);
+        } else {
+            dx = tf2_sub(X2, F[0 * TR_HALF + m]);
+            dy = tf2_sub(Y2, F[1 * TR_HALF + m]);
+            dz = tf2_sub(Z2, F[2 * TR_HALF + m]);
+        }
+        const tf2 QX = F[3 * TR_HALF + m], QY = F[4 * TR_HALF + m], QZ = F[5 * TR_HALF + m];
+        const tf2 r2 = tf2_fma(dx, dx, tf2_fma(dy, dy, tf2_mul(dz, dz)));
+        float r2a, r2b;
+        tf2_unpack(r2, r2a, r2b);
+        float ra = tr_rsqrt(r2a), rb = tr_rsqrt(r2b);
+        if (NEAR) {
+            ra = (2 * m == self || !(r2a >= R2MIN)) ? 0.0f : ra;
+            rb = (2 * m + 1 == self || !(r2b >= R2MIN)) ? 0.0f : rb;
+        }
+        const tf2 ri = tf2_pack(ra, rb);
+        const tf2 ri2 = tf2_mul(ri, ri);
+        const tf2 rq = tf2_fma(dx, QX, tf2_fma(dy, QY, tf2_mul(dz, QZ)));
+        // u = ri (q + r [(r . q) ri^2 + (r^T d r) ri^4])
+        tf2 bq = tf2_mul(rq, ri2);
+        if (NQ == 3) {
+            const tf2 a0 = tf2_fma(F[6 * TR_HALF + m], dx, tf2_fma(F[7 * TR_HALF + m], dy,
+                                                                   tf2_mul(F[8 * TR_HALF + m], dz)));
+            const tf2 a1 = tf2_fma(F[9 * TR_HALF + m], dx, tf2_fma(F[10 * TR_HALF + m], dy,
+                                                                   tf2_mul(F[11 * TR_HALF + m], dz)));
+            const tf2 a2 = tf2_fma(F[12 * TR_HALF + m], dx, tf2_fma(F[13 * TR_HALF + m], dy,
+                                                                    tf2_mul(F[14 * TR_HALF + m], dz)));
+            const tf2 rdr = tf2_fma(dx, a0, tf2_fma(dy, a1, tf2_mul(dz, a2)));
+            bq = tf2_fma(rdr, tf2_mul(ri2, ri2), bq);
+        }
+        ax = tf2_fma(ri, tf2_fma(bq, dx, QX), ax);
+        ay = tf2_fma(ri, tf2_fma(bq, dy, QY), ay);
+        az = tf2_fma(ri, tf2_fma(bq, dz, QZ), az);
+    }
+}
+
+// Sums over the list of a target block: one CTA per block, one thread per target.  The list
+// is walked in chunks of up to TR_THREADS points of one entry; chunks alternate between two
+// shared-memory buffers, and every thread's asynchronous copies of its point of the next
+// chunk are in flight while the current one is summed (one barrier per chunk).  Each entry is summed in FP32, two
+// sources per packed FP32x2 operation, and the entries' sums are added in FP64.
 template <int NQ>
 __global__ void __launch_bounds__(TR_THREADS)
 k_tree_eval(const int4 *__restrict__ tleaf, const TrEntry *__restrict__ entries,
@@ -423,124 +554,67 @@ k_tree_eval(const int4 *__restrict__ tleaf, const TrEntry *__restrict__ entries,
             int same, const float4 *__restrict__ trg_lo, const float4 *__restrict__ src_lo, double *u)
 {
     constexpr int NF = tree_fields<NQ>();
-    __shared__ __align__(16) float sf[NF * TR_THREADS];
+    __shared__ __align__(16) float sf[2][NF * TR_THREADS];
     const int4 tl = tleaf[blockIdx.x];
     const int t = threadIdx.x;
     const bool live = t < tl.y;
     const float4 x = live ? trg_loc[tl.x + t] : make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 xl = (NQ == 3 && live) ? trg_lo[tl.x + t] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const tf2 *F = reinterpret_cast<const tf2 *>(sf);
     double v0 = 0.0, v1 = 0.0, v2 = 0.0;
-    for (int e = 0; e < tl.w; ++e) {
-        const TrEntry en = entries[tl.z + e];
-        const float4 *P = en.kind ? prox_loc : src_loc;
-        const float4 *Q = en.kind ? prox_q : q;
-        // target in the block's frame
-        const float xx = x.x - en.dx, xy = x.y - en.dy, xz = x.z - en.dz;
-        const tf2 X2 = tf2_pack(xx, xx), Y2 = tf2_pack(xy, xy), Z2 = tf2_pack(xz, xz);
-        // the double layer's r . n = O(|r|^2) on the surface: near source blocks form r from
-        // high and low parts with exact (TwoSum) differences, ~2^-48 of the frame offsets
-        const bool hilo = NQ == 3 && en.kind == 0;
+    if (tl.w > 0) {
+        // (first, count, kind): the leading fields of an entry, all the staging needs
+        const int4 *ehead = reinterpret_cast<const int4 *>(entries + tl.z);
+        constexpr int ESTRIDE = sizeof(TrEntry) / sizeof(int4);
+        int e = 0, base = 0, buf = 0;
+        TrEntry en = entries[tl.z];
+        tr_stage<NQ>(sf[0], t, make_int4(en.first, en.count, en.kind, 0), t, src_loc, q, prox_loc,
+                     prox_q, src_lo);
+        cp_async_commit();
         tf2 ax = 0ull, ay = 0ull, az = 0ull;   // packed (0.f, 0.f)
-        for (int base = 0; base < en.count; base += TR_THREADS) {
-            const int k = base + t;
-            // stage point t (a point past the block's end: zero charge, far away)
-            float4 pp = make_float4(1e15f, 1e15f, 1e15f, 0.f), q0 = make_float4(0.f, 0.f, 0.f, 0.f);
-            float4 q1 = q0, q2 = q0, pl = q0;
-            if (k < en.count) {
-                pp = P[en.first + k];
-                q0 = Q[static_cast<size_t>(en.first + k) * NQ];
-                if (NQ == 3) {
-                    q1 = Q[static_cast<size_t>(en.first + k) * NQ + 1];
-                    q2 = Q[static_cast<size_t>(en.first + k) * NQ + 2];
-                    if (hilo)
-                        pl = src_lo[en.first + k];
-                }
+        for (;;) {
+            cp_async_wait_all();
+            __syncthreads();   // chunk in sf[buf] complete; sf[buf ^ 1] free (its sums are done)
+            // the next chunk: the rest of this entry, else the next entry's first points
+            int e_n = e, base_n = base + TR_THREADS;
+            int4 hn = make_int4(en.first, en.count, en.kind, 0);
+            if (base_n >= en.count) {
+                e_n = e + 1;
+                base_n = 0;
+                if (e_n < tl.w)
+                    hn = ehead[e_n * ESTRIDE];
             }
-            sf[0 * TR_THREADS + t] = pp.x;
-            sf[1 * TR_THREADS + t] = pp.y;
-            sf[2 * TR_THREADS + t] = pp.z;
-            sf[3 * TR_THREADS + t] = q0.x;
-            sf[4 * TR_THREADS + t] = q0.y;
-            sf[5 * TR_THREADS + t] = q0.z;
-            if (NQ == 3) {
-                sf[6 * TR_THREADS + t] = q0.w;    // d00
-                sf[7 * TR_THREADS + t] = q1.x;    // d01
-                sf[8 * TR_THREADS + t] = q1.y;    // d02
-                sf[9 * TR_THREADS + t] = q1.z;    // d10
-                sf[10 * TR_THREADS + t] = q1.w;   // d11
-                sf[11 * TR_THREADS + t] = q2.x;   // d12
-                sf[12 * TR_THREADS + t] = q2.y;   // d20
-                sf[13 * TR_THREADS + t] = q2.z;   // d21
-                sf[14 * TR_THREADS + t] = q2.w;   // d22
-                sf[15 * TR_THREADS + t] = pl.x;
-                sf[16 * TR_THREADS + t] = pl.y;
-                sf[17 * TR_THREADS + t] = pl.z;
+            const bool more = e_n < tl.w;
+            if (more) {
+                tr_stage<NQ>(sf[buf ^ 1], t, hn, base_n + t, src_loc, q, prox_loc, prox_q, src_lo);
+                cp_async_commit();
             }
-            __syncthreads();
+            const tf2 *F = reinterpret_cast<const tf2 *>(sf[buf]);
             const int cnt2 = (min(TR_THREADS, en.count - base) + 1) / 2;
-            // the target's own node (same tree, a source block): its index in this tile
-            const int self = (same && en.kind == 0) ? tl.x + t - en.first - base : -1;
-#pragma unroll 2
-            for (int m = 0; m < cnt2; ++m) {
-                tf2 dx, dy, dz;
-                if (hilo) {
-                    float ya, yb, la, lb;
-                    float r[6];
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        const float xd = d == 0 ? x.x : (d == 1 ? x.y : x.z);
-                        const float ed = d == 0 ? en.dx : (d == 1 ? en.dy : en.dz);
-                        const float xld = d == 0 ? xl.x : (d == 1 ? xl.y : xl.z);
-                        const float eld = d == 0 ? en.lx : (d == 1 ? en.ly : en.lz);
-                        tf2_unpack(F[d * TR_HALF + m], ya, yb);
-                        tf2_unpack(F[(15 + d) * TR_HALF + m], la, lb);
-                        r[2 * d] = two_diff3(xd, ya, ed, xld - la - eld);
-                        r[2 * d + 1] = two_diff3(xd, yb, ed, xld - lb - eld);
-                    }
-                    dx = tf2_pack(r[0], r[1]);
-                    dy = tf2_pack(r[2], r[3]);
-                    dz = tf2_pack(r[4], r[5]);
-                } else {
-                    dx = tf2_sub(X2, F[0 * TR_HALF + m]);
-                    dy = tf2_sub(Y2, F[1 * TR_HALF + m]);
-                    dz = tf2_sub(Z2, F[2 * TR_HALF + m]);
-                }
-                const tf2 QX = F[3 * TR_HALF + m], QY = F[4 * TR_HALF + m], QZ = F[5 * TR_HALF + m];
-                const tf2 r2 = tf2_fma(dx, dx, tf2_fma(dy, dy, tf2_mul(dz, dz)));
-                float r2a, r2b;
-                tf2_unpack(r2, r2a, r2b);
-                // the target's own node and a point on the target itself add nothing
-                const float ra = (2 * m == self || !(r2a > 0.0f)) ? 0.0f : rsqrtf(r2a);
-                const float rb = (2 * m + 1 == self || !(r2b > 0.0f)) ? 0.0f : rsqrtf(r2b);
-                const tf2 ri = tf2_pack(ra, rb);
-                const tf2 ri2 = tf2_mul(ri, ri);
-                const tf2 rq = tf2_fma(dx, QX, tf2_fma(dy, QY, tf2_mul(dz, QZ)));
-                // u = ri (q + r [(r . q) ri^2 + (r^T d r) ri^4])
-                tf2 bq = tf2_mul(rq, ri2);
-                if (NQ == 3) {
-                    const tf2 a0 = tf2_fma(F[6 * TR_HALF + m], dx, tf2_fma(F[7 * TR_HALF + m], dy,
-                                                                           tf2_mul(F[8 * TR_HALF + m], dz)));
-                    const tf2 a1 = tf2_fma(F[9 * TR_HALF + m], dx, tf2_fma(F[10 * TR_HALF + m], dy,
-                                                                           tf2_mul(F[11 * TR_HALF + m], dz)));
-                    const tf2 a2 = tf2_fma(F[12 * TR_HALF + m], dx, tf2_fma(F[13 * TR_HALF + m], dy,
-                                                                            tf2_mul(F[14 * TR_HALF + m], dz)));
-                    const tf2 rdr = tf2_fma(dx, a0, tf2_fma(dy, a1, tf2_mul(dz, a2)));
-                    bq = tf2_fma(rdr, tf2_mul(ri2, ri2), bq);
-                }
-                ax = tf2_fma(ri, tf2_fma(bq, dx, QX), ax);
-                ay = tf2_fma(ri, tf2_fma(bq, dy, QY), ay);
-                az = tf2_fma(ri, tf2_fma(bq, dz, QZ), az);
+            if (en.kind == 0) {
+                // the target's own node (same tree): its index in this chunk
+                const int self = same ? tl.x + t - en.first - base : -1;
+                tr_tile<NQ, true>(F, cnt2, self, x, xl, en, ax, ay, az);
+            } else {
+                tr_tile<NQ, false>(F, cnt2, -1, x, xl, en, ax, ay, az);
             }
-            __syncthreads();
+            if (e_n != e) {   // the entry is complete: its FP32 sum into the FP64 total
+                float a0, a1;
+                tf2_unpack(ax, a0, a1);
+                v0 += static_cast<double>(a0) + static_cast<double>(a1);
+                tf2_unpack(ay, a0, a1);
+                v1 += static_cast<double>(a0) + static_cast<double>(a1);
+                tf2_unpack(az, a0, a1);
+                v2 += static_cast<double>(a0) + static_cast<double>(a1);
+                ax = ay = az = 0ull;
+            }
+            if (!more)
+                break;
+            if (e_n != e)
+                en = entries[tl.z + e_n];
+            e = e_n;
+            base = base_n;
+            buf ^= 1;
         }
-        float a0, a1;
-        tf2_unpack(ax, a0, a1);
-        v0 += static_cast<double>(a0) + static_cast<double>(a1);
-        tf2_unpack(ay, a0, a1);
-        v1 += static_cast<double>(a0) + static_cast<double>(a1);
-        tf2_unpack(az, a0, a1);
-        v2 += static_cast<double>(a0) + static_cast<double>(a1);
     }
     if (live) {
         const long long o = perm_t[tl.x + t];
@@ -722,7 +796,7 @@ static int tree_create_impl(long long ns, const double *src, const double *nrm, 
             for (int d = 0; d < 3; ++d)
                 d2 += (C.c[d] - L.c[d]) * (C.c[d] - L.c[d]);
             const double dist = std::sqrt(d2) - L.rad;
-            if (dist * theta >= C.rad && C.count > C.nprox) {
+            if (dist > 0.0 && dist * theta >= C.rad && C.count > C.nprox) {
                 const TrEntry en = make_entry(C.pfirst, C.nprox, 1, C.c, L.c);
                 h_ent.push_back(en);
                 pairs += static_cast<double>(C.nprox) * L.count;

@@ -50,8 +50,8 @@ def test_tree_cloud_matches_oracle(sbq, oracle_mod):
 @pytest.mark.parametrize("panels,bar", [(512, 3e-6), (8192, 1e-5)])
 def test_tree_slender_loop_matches_oracle(sbq, oracle_mod, panels, bar):
     """The slender random loop (Sec. 5.2 recipe), on-surface sum without self terms, 2,048
-    sampled rows against the oracle: measured 7e-7 at 65,536 nodes and 2.2e-6 at 1,048,576
-    (the plain FP32 direct sum: 2.5e-6 and 5.5e-6)."""
+    sampled rows against the oracle: measured 1.2e-6 at 65,536 nodes and 1.7e-6 at 1,048,576
+    (the plain FP32 direct sum at 1,048,576: 5.1e-6)."""
     rng = np.random.default_rng(42)
     S = I.random_loop(seed=1, panels=panels, ns=8, nth=16)
     n = S.size
