@@ -184,22 +184,24 @@ SBQ_API int stokes_sl_apply_noalloc(int64_t ns, const double *src, const double 
  * Far-field acceleration of the layer sums (the paper's fast route for large N: an FMM for
  * the far field, Sec. 3.2; direct sums cost O(N^2), Sec. 3.4): a barycentric Lagrange
  * treecode for u = sum_s [alpha S + beta D](x_t - y_s) w_s sigma_s, the sum of
- * stokes_combined_apply (the same self-pair exclusion when trg == src), to a relative
- * accuracy set by theta and order, in FP32 arithmetic with FP64 sums of its list entries:
- * about 2e-6 at theta = 0.5, order = 8.
+ * stokes_combined_apply, to a relative accuracy set by theta and order, in FP32 arithmetic
+ * with FP64 sums of its list entries: about 2e-6 at theta = 0.5, order = 8.  Pairs closer
+ * than 4e-6 times the sum of the radii of the source leaf and the target block holding
+ * them are skipped (the FP32 paths' coincidence rule; on the surface it removes each
+ * node's own term, and distinct points must be farther apart than that).
  *   stokes_tree_create: ns sources src[3*ns], unit normals nrm[3*ns] (may be NULL when
  *     beta == 0), weights w[ns], nt targets trg[3*nt] (DEVICE arrays; pass trg == src for
- *     the on-surface sum, which then excludes each node's own term; with distinct arrays no
- *     target may coincide with a source: its term would be unbounded); alpha, beta as
+ *     the on-surface sum: one tree then serves both); alpha, beta as
  *     stokes_combined_apply.  theta in (0, 1): a cell of radius r acts through its proxy
  *     points on target blocks farther than r / theta; order in 2..10: Chebyshev points
  *     along the cell's longest side (fewer across thin sides).  Copies the geometry to the
  *     host, builds both octrees and the interaction lists there (the setup, once per
  *     geometry and coefficient pair) and uploads them; the handle owns its device memory
- *     (about 100 bytes per node plus 32 bytes per list entry and 16 (single layer) or 48
+ *     (about 100 bytes per node plus 48 bytes per list entry and 16 (single layer) or 48
  *     bytes per proxy point).  *out receives the handle.
  *   stokes_tree_apply: u[3*nt] (DEVICE, overwritten) from sigma[3*ns] (DEVICE) on
- *     `stream`: source charges, proxy charges of every cell, one CTA per target block.
+ *     `stream`: source charges, proxy charges of the cells some list takes as far, one CTA
+ *     per target block.
  *   stokes_tree_stats: *pairs = kernel evaluations per apply; counts[0..3] = cells, proxy
  *     points, list entries, target blocks.
  *   stokes_tree_destroy: frees the handle (NULL is accepted).

@@ -13,15 +13,17 @@
 // proxies) and
 // the sources of every leaf it reaches.
 // Apply (GPU, per density): charge records of the sources (q = w sigma scaled for the single
-// layer and, with the double layer, the tensor q n^T); proxy charges q_m = sum_k L_m(y_k)
-// q_k, L_m the tensor Lagrange basis of the grid (barycentric form), for the cells some list
-// takes as far; then one CTA per target block sums the kernel over its list, each list
-// entry in FP32 and the entries' sums in FP64.  Positions are kept in FP32 relative to the
-// centre of their leaf (sources), block (targets) or cell (proxies), and each entry carries
-// the offset between its frame and the target block's, so that near pairs lose no digits to
-// large absolute coordinates; with the double layer, near source blocks also take the
-// rounding residuals of those offsets (exact differences), since on the surface r . n is
-// O(|r|^2).
+// layer and, with the double layer, the tensor (w sigma) n^T); proxy charges q_m = sum_k
+// L_m(y_k) q_k, L_m the tensor Lagrange basis of the grid (barycentric form), for the cells
+// some list takes as far; then one CTA per target block sums the kernel over its list, each
+// list entry in FP32 and the entries' sums in FP64.  Positions are kept in FP32 relative to
+// the centre of their leaf (sources), block (targets) or cell (proxies), and each entry
+// carries the offset between its frame and the target block's, so that near pairs lose no
+// digits to large absolute coordinates; with the double layer, source leaves also take the
+// rounding residuals of the positions and of the offsets, so that r keeps its FP32 accuracy
+// relative to |r| itself, since on the surface r . n is O(|r|^2).  Pairs of a leaf and a
+// block closer than 4e-6 x the sum of their radii count as coincident and are skipped, as
+// in the direct FP32 sums.
 #include "engine.h"
 
 #include <algorithm>
@@ -35,7 +37,7 @@ struct sbq_tree_s {
     uint32_t magic = 0x53425454u;   // "SBTT"
     int device = 0;
     long long ns = 0, nt = 0;
-    bool same = false;              // targets are the sources (one tree, self pairs excluded)
+    bool same = false;              // targets are the sources (one tree)
     double theta = 0.0;
     int order = 0;
     long long n_cells = 0, n_proxies = 0, n_entries = 0, n_tleaves = 0;
@@ -71,6 +73,12 @@ constexpr int TR_CHUNK = 512;      // sources per P2M work item
 constexpr int TR_BLOCKCELL = 512;  // target blocks: runs of TR_THREADS inside cells this small
 constexpr int TR_MAXLEV = 21;
 constexpr double TR_PI = 3.14159265358979323846;
+// Pairs of a source leaf and a target block closer than this fraction of the sum of their
+// radii count as coincident and are skipped (the direct FP32 sums' rule): the rounding of
+// the FP32 frame coordinates moves a coincident pair (a node and itself on the surface) by
+// a few ulps of that sum, far below it.
+constexpr double TR_COINCIDENT_REL = 4.0e-6;
+constexpr float TR_R2MIN = 1.17549435e-38f;   // FLT_MIN: the SFU rsqrt flushes below it
 
 struct TrCellDev {
     double c[3], h[3];
@@ -79,12 +87,14 @@ struct TrCellDev {
 
 struct alignas(16) TrEntry {
     int first, count, kind, pad;   // kind 0: sources [first, first + count); 1: proxies
-    float dx, dy, dz, pad2;        // block frame centre minus target block centre (FP32)
+    float dx, dy, dz;              // block frame centre minus target block centre (FP32)
+    float thr2;                    // kind 0: squared distance below which a pair is skipped
     float lx, ly, lz, pad3;        // and the rounding residual of that offset
 };
 static_assert(sizeof(TrEntry) % sizeof(int4) == 0, "entries are read as int4 heads");
 
-inline TrEntry make_entry(int first, int count, int kind, const double *cb, const double *ct)
+// thr: pairs of a source leaf closer than this count as coincident (skipped)
+inline TrEntry make_entry(int first, int count, int kind, double thr, const double *cb, const double *ct)
 {
     TrEntry e{};
     e.first = first;
@@ -97,6 +107,7 @@ inline TrEntry make_entry(int first, int count, int kind, const double *cb, cons
     e.lx = static_cast<float>(d[0] - e.dx);
     e.ly = static_cast<float>(d[1] - e.dy);
     e.lz = static_cast<float>(d[2] - e.dz);
+    e.thr2 = std::max(static_cast<float>(thr * thr), TR_R2MIN);
     return e;
 }
 
@@ -258,8 +269,10 @@ __device__ void lagrange_1d(float xi, int n, float *out)
 }
 
 // charge records of source k (sorted order): q = w sigma scaled by alpha / (8 pi) and, for
-// the double layer, the tensor d_jl = (w sigma)_j n_l scaled by 3 beta / (4 pi):
-// record 0 (q_x, q_y, q_z, d00), record 1 (d01, d02, d10, d11), record 2 (d12, d20, d21, d22)
+// the double layer, the tensor d = m n^T, m = w sigma scaled by 3 beta / (4 pi): record 0
+// (q_x, q_y, q_z, d00), record 1 (d01, d02, d10, d11), record 2 (d12, d20, d21, d22), each
+// product formed in FP64 and rounded once.  (The near sums in the rank-one form (r . m)(r . n)
+// from FP32 m and n were tried: twice the error of the combined field at 1M nodes.)
 template <int NQ>
 __global__ void k_tree_charges(long long ns, const int *__restrict__ perm, const double *__restrict__ w,
                                const double *__restrict__ nrm, const double *__restrict__ sigma,
@@ -276,12 +289,13 @@ __global__ void k_tree_charges(long long ns, const int *__restrict__ perm, const
         return;
     }
     const double n0 = nrm[k], n1 = nrm[ns + k], n2 = nrm[2 * ns + k];
+    const double m0 = b * s0, m1 = b * s1, m2 = b * s2;
     q[3 * k] = make_float4(static_cast<float>(a * s0), static_cast<float>(a * s1), static_cast<float>(a * s2),
-                           static_cast<float>(b * s0 * n0));
-    q[3 * k + 1] = make_float4(static_cast<float>(b * s0 * n1), static_cast<float>(b * s0 * n2),
-                               static_cast<float>(b * s1 * n0), static_cast<float>(b * s1 * n1));
-    q[3 * k + 2] = make_float4(static_cast<float>(b * s1 * n2), static_cast<float>(b * s2 * n0),
-                               static_cast<float>(b * s2 * n1), static_cast<float>(b * s2 * n2));
+                           static_cast<float>(m0 * n0));
+    q[3 * k + 1] = make_float4(static_cast<float>(m0 * n1), static_cast<float>(m0 * n2),
+                               static_cast<float>(m1 * n0), static_cast<float>(m1 * n1));
+    q[3 * k + 2] = make_float4(static_cast<float>(m1 * n2), static_cast<float>(m2 * n0),
+                               static_cast<float>(m2 * n1), static_cast<float>(m2 * n2));
 }
 
 // proxy charges of one cell from one chunk of its sources (atomically accumulated)
@@ -357,18 +371,6 @@ k_tree_p2m(const int4 *__restrict__ chunks, const TrCellDev *__restrict__ cells,
     }
 }
 
-// (a - b) - c + lo with the rounding errors of both differences kept (Knuth's TwoSum)
-__device__ __forceinline__ float two_diff3(float a, float b, float c, float lo)
-{
-    const float s1 = a - b;
-    const float bb = s1 - a;
-    const float e1 = (a - (s1 - bb)) - (b + bb);
-    const float s2 = s1 - c;
-    const float cc = s2 - s1;
-    const float e2 = (s1 - (s2 - cc)) - (c + cc);
-    return s2 + ((e1 + e2) + lo);
-}
-
 // Packed FP32 pairs: one 64-bit register holds the values of two sources; the f32x2
 // instructions process both in one issue slot.
 using tf2 = unsigned long long;
@@ -389,6 +391,12 @@ __device__ __forceinline__ tf2 tf2_sub(tf2 a, tf2 b)
 {
     tf2 d;
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ tf2 tf2_add(tf2 a, tf2 b)
+{
+    tf2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
 __device__ __forceinline__ tf2 tf2_pack(float lo, float hi)
@@ -437,10 +445,12 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// Stage point k of a list entry (first, count, kind) = en into column t of the shared tile:
-// position, charge records and (double layer, source leaves) the position's rounding
-// residual, copied asynchronously; a point past the entry's end is written directly (zero
-// charge, far away).
+// Stage point k of a list entry, head en = (first, count, kind), into column t of the
+// shared tile, copied asynchronously; a point past the entry's end is written directly
+// (zero charge, far away).  Fields: 0..2 position, 3..5 single-layer charge q; with the
+// double layer, the tensor d in 6..14 (d00 d01 d02 d10 d11 d12 d20 d21 d22, the records'
+// floats 3..11 in order) and, for a source leaf, the position's rounding residual in
+// 15..17.
 template <int NQ>
 __device__ __forceinline__ void tr_stage(float *sf, int t, const int4 &en, int k,
                                          const float4 *__restrict__ src_loc, const float4 *__restrict__ q,
@@ -454,10 +464,8 @@ __device__ __forceinline__ void tr_stage(float *sf, int t, const int4 &en, int k
                                                          static_cast<size_t>(en.x + k) * NQ);
         for (int f = 0; f < 3; ++f)
             cp_async4(sf + f * TR_THREADS + t, P + f);
-        // fields 3..5: q; 6..14 (double layer): d00 d01 d02 d10 d11 d12 d20 d21 d22, the
-        // records' floats 3..11 in order
-        for (int f = 3; f < (NQ == 3 ? 15 : 6); ++f)
-            cp_async4(sf + f * TR_THREADS + t, Q + (NQ == 3 ? f - 3 : (f - 3)));
+        for (int f = 0; f < 3 * NQ + (NQ == 3 ? 3 : 0); ++f)
+            cp_async4(sf + (3 + f) * TR_THREADS + t, Q + f);
         if (NQ == 3 && en.z == 0) {
             const float *L = reinterpret_cast<const float *>(src_lo + en.x + k);
             for (int f = 15; f < 18; ++f)
@@ -470,45 +478,52 @@ __device__ __forceinline__ void tr_stage(float *sf, int t, const int4 &en, int k
 }
 
 // The staged points 0 .. 2 cnt2 - 1 of one entry against the thread's target, two per packed
-// operation.  NEAR (a source leaf): the target's own node (index self) and points closer than
-// FLT_MIN add nothing, and with the double layer r is formed from high and low parts with
-// exact (TwoSum) differences, since on the surface r . n = O(|r|^2).  Far entries (proxy grids)
-// need neither: with d > 0 the distance between the centres less the block's radius, their
-// acceptance (d theta >= cell radius) keeps every target at least (1 - theta) d from every
-// proxy point.
+// operation.  NEAR (a source leaf): pairs closer than the entry's coincidence distance (the
+// target's own node on the surface among them) add nothing; with the double layer, r is
+// formed from high and low parts, since on the surface r . n = O(|r|^2): the target in the
+// leaf's frame as an exact (hi, lo)
+// pair (TwoSum, once per entry), then r = (x_hi - y_hi) + (x_lo - y_lo), accurate to an ulp
+// of r itself rather than of the frames.  Far entries (proxy grids) need neither: with d > 0
+// the distance between the centres less the block's radius, their acceptance (d theta >=
+// cell radius) keeps every target at least (1 - theta) d from every proxy point.
 template <int NQ, bool NEAR>
-__device__ __forceinline__ void tr_tile(const tf2 *__restrict__ F, int cnt2, int self, const float4 &x,
+__device__ __forceinline__ void tr_tile(const tf2 *__restrict__ F, int cnt2, const float4 &x,
                                         const float4 &xl, const TrEntry &en, tf2 &ax, tf2 &ay, tf2 &az)
 {
-    const float xx = x.x - en.dx, xy = x.y - en.dy, xz = x.z - en.dz;
-    const tf2 X2 = tf2_pack(xx, xx), Y2 = tf2_pack(xy, xy), Z2 = tf2_pack(xz, xz);
-    constexpr float R2MIN = 1.17549435e-38f;
+    constexpr bool HILO = NEAR && NQ == 3;
+    const float thr2 = en.thr2;
+    float xh[3], xo[3];
+    {
+        const float xv[3] = {x.x, x.y, x.z}, xlv[3] = {xl.x, xl.y, xl.z};
+        const float ev[3] = {en.dx, en.dy, en.dz}, elv[3] = {en.lx, en.ly, en.lz};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            xh[d] = xv[d] - ev[d];
+            if (HILO) {   // x - e = xh + err exactly
+                const float bb = xh[d] - xv[d];
+                const float err = (xv[d] - (xh[d] - bb)) - (ev[d] + bb);
+                xo[d] = (xlv[d] - elv[d]) + err;
+            }
+        }
+    }
+    const tf2 X2 = tf2_pack(xh[0], xh[0]), Y2 = tf2_pack(xh[1], xh[1]), Z2 = tf2_pack(xh[2], xh[2]);
+    tf2 XL2 = 0ull, YL2 = 0ull, ZL2 = 0ull;
+    if (HILO) {
+        XL2 = tf2_pack(xo[0], xo[0]);
+        YL2 = tf2_pack(xo[1], xo[1]);
+        ZL2 = tf2_pack(xo[2], xo[2]);
+    }
     // unrolled twice for the single layer; the double layer's loop holds enough registers
     constexpr int UNROLL = NQ == 3 ? 1 : 2;
 #pragma unroll UNROLL
     for (int m = 0; m < cnt2; ++m) {
-        tf2 dx, dy, dz;
-        if (NEAR && NQ == 3) {
-            float ya, yb, la, lb;
-            float r[6];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const float xd = d == 0 ? x.x : (d == 1 ? x.y : x.z);
-                const float ed = d == 0 ? en.dx : (d == 1 ? en.dy : en.dz);
-                const float xld = d == 0 ? xl.x : (d == 1 ? xl.y : xl.z);
-                const float eld = d == 0 ? en.lx : (d == 1 ? en.ly : en.lz);
-                tf2_unpack(F[d * TR_HALF + m], ya, yb);
-                tf2_unpack(F[(15 + d) * TR_HALF + m], la, lb);
-                r[2 * d] = two_diff3(xd, ya, ed, xld - la - eld);
-                r[2 * d + 1] = two_diff3(xd, yb, ed, xld - lb - eld);
-            }
-            dx = tf2_pack(r[0], r[1]);
-            dy = tf2_pack(r[2], r[3]);
-            dz = tf2_pack(r[4], r[5]);
-        } else {
-            dx = tf2_sub(X2, F[0 * TR_HALF + m]);
-            dy = tf2_sub(Y2, F[1 * TR_HALF + m]);
-            dz = tf2_sub(Z2, F[2 * TR_HALF + m]);
+        tf2 dx = tf2_sub(X2, F[0 * TR_HALF + m]);
+        tf2 dy = tf2_sub(Y2, F[1 * TR_HALF + m]);
+        tf2 dz = tf2_sub(Z2, F[2 * TR_HALF + m]);
+        if (HILO) {
+            dx = tf2_add(dx, tf2_sub(XL2, F[15 * TR_HALF + m]));
+            dy = tf2_add(dy, tf2_sub(YL2, F[16 * TR_HALF + m]));
+            dz = tf2_add(dz, tf2_sub(ZL2, F[17 * TR_HALF + m]));
         }
         const tf2 QX = F[3 * TR_HALF + m], QY = F[4 * TR_HALF + m], QZ = F[5 * TR_HALF + m];
         const tf2 r2 = tf2_fma(dx, dx, tf2_fma(dy, dy, tf2_mul(dz, dz)));
@@ -516,8 +531,8 @@ __device__ __forceinline__ void tr_tile(const tf2 *__restrict__ F, int cnt2, int
         tf2_unpack(r2, r2a, r2b);
         float ra = tr_rsqrt(r2a), rb = tr_rsqrt(r2b);
         if (NEAR) {
-            ra = (2 * m == self || !(r2a >= R2MIN)) ? 0.0f : ra;
-            rb = (2 * m + 1 == self || !(r2b >= R2MIN)) ? 0.0f : rb;
+            ra = r2a >= thr2 ? ra : 0.0f;
+            rb = r2b >= thr2 ? rb : 0.0f;
         }
         const tf2 ri = tf2_pack(ra, rb);
         const tf2 ri2 = tf2_mul(ri, ri);
@@ -551,7 +566,7 @@ k_tree_eval(const int4 *__restrict__ tleaf, const TrEntry *__restrict__ entries,
             const float4 *__restrict__ trg_loc, const float4 *__restrict__ src_loc,
             const float4 *__restrict__ q, const float4 *__restrict__ prox_loc,
             const float4 *__restrict__ prox_q, const int *__restrict__ perm_t, long long nt,
-            int same, const float4 *__restrict__ trg_lo, const float4 *__restrict__ src_lo, double *u)
+            const float4 *__restrict__ trg_lo, const float4 *__restrict__ src_lo, double *u)
 {
     constexpr int NF = tree_fields<NQ>();
     __shared__ __align__(16) float sf[2][NF * TR_THREADS];
@@ -590,13 +605,10 @@ k_tree_eval(const int4 *__restrict__ tleaf, const TrEntry *__restrict__ entries,
             }
             const tf2 *F = reinterpret_cast<const tf2 *>(sf[buf]);
             const int cnt2 = (min(TR_THREADS, en.count - base) + 1) / 2;
-            if (en.kind == 0) {
-                // the target's own node (same tree): its index in this chunk
-                const int self = same ? tl.x + t - en.first - base : -1;
-                tr_tile<NQ, true>(F, cnt2, self, x, xl, en, ax, ay, az);
-            } else {
-                tr_tile<NQ, false>(F, cnt2, -1, x, xl, en, ax, ay, az);
-            }
+            if (en.kind == 0)
+                tr_tile<NQ, true>(F, cnt2, x, xl, en, ax, ay, az);
+            else
+                tr_tile<NQ, false>(F, cnt2, x, xl, en, ax, ay, az);
             if (e_n != e) {   // the entry is complete: its FP32 sum into the FP64 total
                 float a0, a1;
                 tf2_unpack(ax, a0, a1);
@@ -797,11 +809,12 @@ static int tree_create_impl(long long ns, const double *src, const double *nrm, 
                 d2 += (C.c[d] - L.c[d]) * (C.c[d] - L.c[d]);
             const double dist = std::sqrt(d2) - L.rad;
             if (dist > 0.0 && dist * theta >= C.rad && C.count > C.nprox) {
-                const TrEntry en = make_entry(C.pfirst, C.nprox, 1, C.c, L.c);
+                const TrEntry en = make_entry(C.pfirst, C.nprox, 1, 0.0, C.c, L.c);
                 h_ent.push_back(en);
                 pairs += static_cast<double>(C.nprox) * L.count;
             } else if (C.nchild == 0) {
-                const TrEntry en = make_entry(C.first, C.count, 0, C.c, L.c);
+                const TrEntry en = make_entry(C.first, C.count, 0, TR_COINCIDENT_REL * (L.rad + C.rad),
+                                              C.c, L.c);
                 h_ent.push_back(en);
                 pairs += static_cast<double>(C.count) * L.count;
             } else {
@@ -894,7 +907,7 @@ static int tree_apply_nq(sbq_tree_s *T, const double *sigma, double *u, cudaStre
     k_tree_eval<NQ><<<static_cast<unsigned>(T->n_tleaves), TR_THREADS, 0, s>>>(
         T->tleaf.as<int4>(), T->entries.as<TrEntry>(), T->trg_loc.as<float4>(), T->src_loc.as<float4>(),
         T->q.as<float4>(), T->prox_loc.as<float4>(), T->prox_q.as<float4>(), T->perm_t.as<int>(), T->nt,
-        T->same ? 1 : 0, T->trg_lo.as<float4>(), T->src_lo.as<float4>(), u);
+        T->trg_lo.as<float4>(), T->src_lo.as<float4>(), u);
     SBQ_CUDA(cudaGetLastError());
     return SBQ_OK;
 }

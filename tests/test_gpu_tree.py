@@ -175,3 +175,29 @@ def test_tree_as_inner_operator_of_gmres_ir(sbq, oracle_mod):
     assert rt["status"] == 0 and rc["status"] == 0
     assert rt["rel_res"] <= 1e-10
     assert diff < 1e-8
+
+
+def test_tree_coincident_nodes(sbq, oracle_mod):
+    """A 3D cloud in which 500 nodes repeat others exactly, on-surface sum (targets = sources)
+    of the combined field with random unit normals: a coincident pair adds nothing, whether
+    the two copies share a leaf or not (the punctured sum the oracle takes), and no output is
+    non-finite; 600 rows against the oracle, the repeated nodes and their originals among
+    them."""
+    rng = np.random.default_rng(48)
+    n0 = 6000
+    x0 = rng.standard_normal((3, n0))
+    dup = rng.choice(n0, 500, replace=False)
+    x = np.concatenate([x0, x0[:, dup]], axis=1)
+    n = x.shape[1]
+    w, sig = rng.random(n), rng.standard_normal((3, n))
+    nrm = rng.standard_normal((3, n))
+    nrm /= np.linalg.norm(nrm, axis=0)
+    T = sbq.StokesTree(_t(x), _t(w), nrm=_t(nrm), alpha=1.0, beta=1.0)
+    u = T.apply(_t(sig)).cpu().numpy()
+    T.close()
+    assert np.isfinite(u).all()
+    sub = np.unique(np.concatenate([dup[:200], n0 + np.arange(200), rng.choice(n, 200, replace=False)]))
+    ref = oracle_mod.combined(x, nrm, w, sig, x[:, sub], 1.0, 1.0)
+    err = _rel(u[:, sub], ref)
+    print("treecode, cloud with coincident nodes: %.3e" % err)
+    assert err < 1e-5
