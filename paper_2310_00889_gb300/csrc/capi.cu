@@ -7,6 +7,7 @@
 #include <utility>
 #include <vector>
 #include <new>
+#include <thread>
 
 namespace sbq {
 const char *last_error_cstr();
@@ -78,8 +79,11 @@ int apply_generic(int64_t ns, const double *src, const double *nrm, const double
 
 // Recursive coordinate bisection of the nodes [b, e): split at the median of the longest
 // bounding-box axis, at a multiple of 256 nodes (128 at the last level), so that every
-// aligned block of 128 or 256 nodes is one subtree: a compact patch of the surface.
-static void rcb_order(const std::vector<double> &hx, long long n, int *b, int *e)
+// aligned block of 128 or 256 nodes is one subtree: a compact patch of the surface.  hx
+// holds the coordinates component-major (x of all n nodes, then y, then z).  The two halves
+// of a large range are ordered by two threads while `par` > 1 (the result does not depend
+// on it: the halves are disjoint).
+static void rcb_order(const double *hx, long long n, int *b, int *e, int par)
 {
     const long long m = e - b;
     if (m <= 128)
@@ -105,14 +109,28 @@ static void rcb_order(const std::vector<double> &hx, long long n, int *b, int *e
         half = m - unit;
     std::nth_element(b, b + half, e,
                      [&](int i, int j) { return hx[ax * n + i] < hx[ax * n + j]; });
-    rcb_order(hx, n, b, b + half);
-    rcb_order(hx, n, b + half, e);
+    if (par > 1 && m >= 65536) {
+        bool spawned = false;
+        std::thread th;
+        try {
+            th = std::thread([=] { rcb_order(hx, n, b, b + half, par / 2); });
+            spawned = true;
+        } catch (...) {
+        }
+        if (!spawned)
+            rcb_order(hx, n, b, b + half, 1);
+        rcb_order(hx, n, b + half, e, par - par / 2);
+        if (spawned)
+            th.join();
+        return;
+    }
+    rcb_order(hx, n, b, b + half, 1);
+    rcb_order(hx, n, b + half, e, 1);
 }
 
 // Mean bounding radius (about the bounding-box midpoint) of the blocks of 256 consecutive
 // nodes of order[a..b).
-static double mean_tile_radius(const std::vector<double> &hx, long long n, const int *order,
-                               long long cnt)
+static double mean_tile_radius(const double *hx, long long n, const int *order, long long cnt)
 {
     double sum = 0.0;
     long long tiles = 0;
@@ -139,6 +157,18 @@ static double mean_tile_radius(const std::vector<double> &hx, long long n, const
     return tiles ? sum / tiles : 0.0;
 }
 
+// out[c n + k] = in[c n + perm[k]] for the ncomp components of n nodes
+__global__ void k_gather_nodes(const double *__restrict__ in, const int *__restrict__ perm, long long n,
+                               int ncomp, double *__restrict__ out)
+{
+    const long long k = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (k >= n)
+        return;
+    const long long u = perm[k];
+    for (int c = 0; c < ncomp; ++c)
+        out[c * n + k] = in[c * n + u];
+}
+
 // Internal node order of an operator: within each segment, either the caller's order or a
 // recursive coordinate bisection of the nodes, whichever makes the smaller tiles (mean
 // bounding radius of blocks of 256).  Consecutive caller nodes are often compact already
@@ -148,29 +178,27 @@ static double mean_tile_radius(const std::vector<double> &hx, long long n, const
 // exact differences).  The operator keeps its geometry in the internal order and
 // perm[k] = the caller's index of internal node k; the density pack gathers through perm
 // and the reductions scatter through it, so callers never see the internal order.
-// host_geom: src, nrm, w are host arrays (else device arrays, read back here).
+// host_geom: src, nrm, w are host arrays (else device arrays; only the coordinates are read
+// back).  The order is computed on the host from the coordinates; the geometry is gathered
+// into it on the device (host arrays are uploaded as they are, then gathered).
 static int internal_order(Op *op, const double *src, const double *nrm, const double *w,
                           bool host_geom)
 {
     const long long n = op->n;
-    std::vector<double> hx(3 * n), hn(3 * n), hw(n);
+    std::vector<double> hbuf;
+    const double *hx = src;
     cudaError_t e = cudaSuccess;
-    if (host_geom) {
-        std::copy(src, src + 3 * n, hx.begin());
-        std::copy(nrm, nrm + 3 * n, hn.begin());
-        std::copy(w, w + n, hw.begin());
-    } else {
-        e = cudaMemcpy(hx.data(), src, 3 * n * sizeof(double), cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(hn.data(), nrm, 3 * n * sizeof(double), cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(hw.data(), w, n * sizeof(double), cudaMemcpyDeviceToHost);
+    if (!host_geom) {
+        hbuf.resize(3 * n);
+        e = cudaMemcpy(hbuf.data(), src, 3 * n * sizeof(double), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess)
             return cuda_status(e, "cudaMemcpy (operator geometry)");
+        hx = hbuf.data();
     }
-    for (double v : hx)
-        if (!std::isfinite(v))
+    for (long long k = 0; k < 3 * n; ++k)
+        if (!std::isfinite(hx[k]))
             return fail(SBQ_EINVAL, "non-finite source coordinate");
+    const int par = static_cast<int>(std::max(1u, std::min(16u, std::thread::hardware_concurrency())));
     std::vector<int> perm(n), alt;
     for (long long k = 0; k < n; ++k)
         perm[k] = static_cast<int>(k);
@@ -179,29 +207,41 @@ static int internal_order(Op *op, const double *src, const double *nrm, const do
         if (b - a <= 256)
             continue;
         alt.assign(perm.begin() + a, perm.begin() + b);
-        rcb_order(hx, n, alt.data(), alt.data() + alt.size());
+        rcb_order(hx, n, alt.data(), alt.data() + alt.size(), par);
         if (mean_tile_radius(hx, n, alt.data(), b - a) <
             mean_tile_radius(hx, n, perm.data() + a, b - a))
             std::copy(alt.begin(), alt.end(), perm.begin() + a);
     }
-    std::vector<double> px(3 * n), pn(3 * n), pw(n);
-    for (long long k = 0; k < n; ++k) {
-        const long long u = perm[k];
-        for (int c = 0; c < 3; ++c) {
-            px[c * n + k] = hx[c * n + u];
-            pn[c * n + k] = hn[c * n + u];
-        }
-        pw[k] = hw[u];
-    }
-    e = cudaMemcpy(op->src.p, px.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(op->nrm.p, pn.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(op->w.p, pw.data(), n * sizeof(double), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(op->perm.p, perm.data(), n * sizeof(int), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(op->perm.p, perm.data(), n * sizeof(int), cudaMemcpyHostToDevice);
     if (e != cudaSuccess)
-        return cuda_status(e, "cudaMemcpy (operator geometry)");
+        return cuda_status(e, "cudaMemcpy (operator node order)");
+    const unsigned grid = static_cast<unsigned>((n + 255) / 256);
+    struct Arr {
+        const double *in;
+        int ncomp;
+        DevBuf *out;
+    };
+    const Arr arrs[3] = {{src, 3, &op->src}, {nrm, 3, &op->nrm}, {w, 1, &op->w}};
+    DevBuf tmp;
+    if (host_geom)
+        SBQ_TRY(tmp.alloc(3 * static_cast<size_t>(n) * sizeof(double)));
+    for (const Arr &ar : arrs) {
+        const double *in = ar.in;
+        if (host_geom) {
+            // the legacy stream orders this copy after the previous gather out of tmp
+            e = cudaMemcpy(tmp.p, ar.in, ar.ncomp * n * sizeof(double), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess)
+                return cuda_status(e, "cudaMemcpy (operator geometry)");
+            in = tmp.as<double>();
+        }
+        k_gather_nodes<<<grid, 256>>>(in, op->perm.as<int>(), n, ar.ncomp, ar.out->as<double>());
+        e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return cuda_status(e, "k_gather_nodes");
+    }
+    e = cudaStreamSynchronize(nullptr);
+    if (e != cudaSuccess)
+        return cuda_status(e, "operator geometry gather");
     return SBQ_OK;
 }
 
