@@ -30,7 +30,8 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
-#include <unordered_map>
+#include <thread>
+#include <utility>
 #include <vector>
 
 struct sbq_tree_s {
@@ -86,7 +87,8 @@ struct TrCellDev {
 };
 
 struct alignas(16) TrEntry {
-    int first, count, kind, pad;   // kind 0: sources [first, first + count); 1: proxies
+    int first, count, kind;        // kind 0: sources [first, first + count); 1: proxies
+    int cell;                      // the source cell (set up on the host; unused on the device)
     float dx, dy, dz;              // block frame centre minus target block centre (FP32)
     float thr2;                    // kind 0: squared distance below which a pair is skipped
     float lx, ly, lz, pad3;        // and the rounding residual of that offset
@@ -147,8 +149,37 @@ inline uint64_t spread21(uint64_t v)
     return v;
 }
 
+// fn(lo, hi) over [0, count) split into contiguous ranges of at least `grain` items run by
+// up to 16 host threads (in the calling thread alone when threads cannot be started); fn
+// writes disjoint outputs
+template <class Fn>
+void host_parallel(long long count, long long grain, Fn fn)
+{
+    const long long hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const int nth = static_cast<int>(std::max(1LL, std::min(hw, count / std::max(1LL, grain))));
+    const long long per = (count + nth - 1) / nth;
+    std::vector<std::thread> th;
+    long long done_to = 0;   // ranges below this were handed to threads
+    try {
+        for (int i = 1; i < nth && i * per < count; ++i) {
+            const long long lo = i * per, hi = std::min(count, lo + per);
+            th.emplace_back([=, &fn] { fn(lo, hi); });
+            done_to = hi;
+        }
+    } catch (...) {
+    }
+    fn(0, std::min(count, per));
+    if (done_to < count)   // ranges no thread took
+        for (long long lo = std::max(per, done_to); lo < count; lo += per)
+            fn(lo, std::min(count, lo + per));
+    for (std::thread &t : th)
+        t.join();
+}
+
 // Octree over n points (SoA x, y, z): Morton sort, then cells split by the next three key
-// bits until at most `leaf` points remain; tight boxes.
+// bits until at most `leaf` points remain; tight boxes.  The topology comes from the sorted
+// keys alone (octant boundaries by binary search), the boxes bottom-up: leaves from their
+// points, every other cell from its children.
 void build_host_tree(const std::vector<double> &x, long long n, int leaf, HostTree &T)
 {
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -161,25 +192,48 @@ void build_host_tree(const std::vector<double> &x, long long n, int leaf, HostTr
     for (int d = 0; d < 3; ++d)
         ext = std::max(ext, hi[d] - lo[d]);
     ext = ext > 0.0 ? ext * (1.0 + 1e-9) : 1.0;
-    std::vector<uint64_t> key(n);
-    for (long long k = 0; k < n; ++k) {
-        uint64_t kk = 0;
-        for (int d = 0; d < 3; ++d) {
-            double u = (x[d * n + k] - lo[d]) / ext * 2097152.0;
-            uint64_t q = static_cast<uint64_t>(std::min(std::max(u, 0.0), 2097151.0));
-            kk |= spread21(q) << (2 - d);
+    // sort (key, index) pairs: chunks in parallel, then pairwise merges (the order is the
+    // total order of the pairs, whatever the chunking)
+    std::vector<std::pair<uint64_t, int>> kp(n);
+    constexpr long long PGRAIN = 32768;   // points per thread at least
+    host_parallel(n, PGRAIN, [&](long long b, long long e) {
+        for (long long k = b; k < e; ++k) {
+            uint64_t kk = 0;
+            for (int d = 0; d < 3; ++d) {
+                double u = (x[d * n + k] - lo[d]) / ext * 2097152.0;
+                uint64_t q = static_cast<uint64_t>(std::min(std::max(u, 0.0), 2097151.0));
+                kk |= spread21(q) << (2 - d);
+            }
+            kp[k] = {kk, static_cast<int>(k)};
         }
-        key[k] = kk;
-    }
-    T.perm.resize(n);
-    std::iota(T.perm.begin(), T.perm.end(), 0);
-    std::sort(T.perm.begin(), T.perm.end(), [&](int a, int b) {
-        return key[a] < key[b] || (key[a] == key[b] && a < b);
     });
+    const long long nchunk = n >= 16 * PGRAIN ? 16 : 1, per = std::max(1LL, (n + nchunk - 1) / nchunk);
+    host_parallel(nchunk, 1, [&](long long b, long long e) {
+        for (long long c = b; c < e; ++c)
+            std::sort(kp.begin() + std::min(n, c * per), kp.begin() + std::min(n, (c + 1) * per));
+    });
+    for (long long w = per; w < n; w *= 2)
+        host_parallel((n + 2 * w - 1) / (2 * w), 1, [&](long long b, long long e) {
+            for (long long c = b; c < e; ++c) {
+                const long long a0 = c * 2 * w, m = std::min(n, a0 + w), b0 = std::min(n, a0 + 2 * w);
+                std::inplace_merge(kp.begin() + a0, kp.begin() + m, kp.begin() + b0);
+            }
+        });
+    T.perm.resize(n);
+    std::vector<uint64_t> ks(n);
+    std::vector<double> xs(3 * n);   // coordinates in sorted order
+    host_parallel(n, PGRAIN, [&](long long b, long long e) {
+        for (long long k = b; k < e; ++k) {
+            T.perm[k] = kp[k].second;
+            ks[k] = kp[k].first;
+            for (int d = 0; d < 3; ++d)
+                xs[d * n + k] = x[d * n + kp[k].second];
+        }
+    });
+    // topology, depth first (cell indices in creation order: children after their parent)
     T.cells.clear();
     T.leaves.clear();
     T.leaf_of.assign(n, -1);
-    // iterative build: (cell index) work stack
     HostCell root{};
     root.first = 0;
     root.count = static_cast<int>(n);
@@ -190,36 +244,23 @@ void build_host_tree(const std::vector<double> &x, long long n, int leaf, HostTr
         const int ci = stack.back();
         stack.pop_back();
         HostCell c = T.cells[ci];
-        double blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
-        for (int k = c.first; k < c.first + c.count; ++k)
-            for (int d = 0; d < 3; ++d) {
-                const double v = x[d * n + T.perm[k]];
-                blo[d] = std::min(blo[d], v);
-                bhi[d] = std::max(bhi[d], v);
-            }
-        double r2 = 0.0;
-        for (int d = 0; d < 3; ++d) {
-            c.c[d] = 0.5 * (blo[d] + bhi[d]);
-            c.h[d] = 0.5 * (bhi[d] - blo[d]);
-            r2 += c.h[d] * c.h[d];
-        }
-        c.rad = std::sqrt(r2);
         c.nchild = 0;
         if (c.count > leaf && c.level < TR_MAXLEV) {
             const int shift = 3 * (TR_MAXLEV - 1 - c.level);
-            int b = c.first;
-            while (b < c.first + c.count) {
-                const uint64_t oct = (key[T.perm[b]] >> shift) & 7ULL;
-                int e = b;
-                while (e < c.first + c.count && ((key[T.perm[e]] >> shift) & 7ULL) == oct)
-                    ++e;
+            // the keys of a cell share their bits above `shift + 3`, so the octant is
+            // non-decreasing along the cell's sorted range
+            const auto beg = ks.begin() + c.first, end = beg + c.count;
+            auto it = beg;
+            while (it != end) {
+                const uint64_t oct = (*it >> shift) & 7ULL;
+                const auto nx = std::partition_point(it, end, [&](uint64_t v) { return ((v >> shift) & 7ULL) <= oct; });
                 HostCell ch{};
-                ch.first = b;
-                ch.count = e - b;
+                ch.first = static_cast<int>(it - ks.begin());
+                ch.count = static_cast<int>(nx - it);
                 ch.level = c.level + 1;
                 c.child[c.nchild++] = static_cast<int>(T.cells.size());
                 T.cells.push_back(ch);
-                b = e;
+                it = nx;
             }
             // a cell whose points share one octant keeps splitting through its child
         }
@@ -232,6 +273,36 @@ void build_host_tree(const std::vector<double> &x, long long n, int leaf, HostTr
             for (int k = c.nchild - 1; k >= 0; --k)
                 stack.push_back(c.child[k]);
         }
+    }
+    // tight boxes: leaves from their points (in parallel), then every other cell from its
+    // children, in reverse creation order
+    const long long nc = static_cast<long long>(T.cells.size());
+    std::vector<double> blo(3 * nc, INFINITY), bhi(3 * nc, -INFINITY);
+    host_parallel(static_cast<long long>(T.leaves.size()), PGRAIN / TR_LEAF, [&](long long b, long long e) {
+        for (long long li = b; li < e; ++li) {
+            const HostCell &c = T.cells[T.leaves[li]];
+            double *l = &blo[3 * T.leaves[li]], *h = &bhi[3 * T.leaves[li]];
+            for (int k = c.first; k < c.first + c.count; ++k)
+                for (int d = 0; d < 3; ++d) {
+                    l[d] = std::min(l[d], xs[d * n + k]);
+                    h[d] = std::max(h[d], xs[d * n + k]);
+                }
+        }
+    });
+    for (long long ci = nc - 1; ci >= 0; --ci) {
+        HostCell &c = T.cells[ci];
+        for (int j = 0; j < c.nchild; ++j)
+            for (int d = 0; d < 3; ++d) {
+                blo[3 * ci + d] = std::min(blo[3 * ci + d], blo[3 * c.child[j] + d]);
+                bhi[3 * ci + d] = std::max(bhi[3 * ci + d], bhi[3 * c.child[j] + d]);
+            }
+        double r2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            c.c[d] = 0.5 * (blo[3 * ci + d] + bhi[3 * ci + d]);
+            c.h[d] = 0.5 * (bhi[3 * ci + d] - blo[3 * ci + d]);
+            r2 += c.h[d] * c.h[d];
+        }
+        c.rad = std::sqrt(r2);
     }
     std::sort(T.leaves.begin(), T.leaves.end(),
               [&](int a, int b) { return T.cells[a].first < T.cells[b].first; });
@@ -693,10 +764,8 @@ static int tree_create_impl(long long ns, const double *src, const double *nrm, 
     }
     // proxies of every cell
     long long np = 0;
-    std::unordered_map<int, int> cell_of_proxy;
     for (size_t ci = 0; ci < S.cells.size(); ++ci) {
         HostCell &c = S.cells[ci];
-        cell_of_proxy[static_cast<int>(np)] = static_cast<int>(ci);
         c.nprox = proxies_per_dim(c, order, c.n);
         c.pfirst = static_cast<int>(np);
         np += c.nprox;
@@ -705,44 +774,51 @@ static int tree_create_impl(long long ns, const double *src, const double *nrm, 
         set_error("stokes_tree_create: too many proxy points");
         return SBQ_EINVAL;
     }
+    // Chebyshev points of the second kind, cos(pi j / (n - 1)), row n
+    double cheb[TR_NMAX + 1][TR_NMAX] = {};
+    for (int m = 2; m <= TR_NMAX; ++m)
+        for (int j = 0; j < m; ++j)
+            cheb[m][j] = std::cos(TR_PI * j / (m - 1));
     std::vector<float4> h_ploc(np);
     std::vector<TrCellDev> h_cells(S.cells.size());
-    for (size_t ci = 0; ci < S.cells.size(); ++ci) {
-        const HostCell &c = S.cells[ci];
-        TrCellDev &dc = h_cells[ci];
-        for (int d = 0; d < 3; ++d) {
-            dc.c[d] = c.c[d];
-            dc.h[d] = c.h[d];
-            dc.n[d] = c.n[d];
+    host_parallel(static_cast<long long>(S.cells.size()), 256, [&](long long cb, long long ce) {
+        for (long long ci = cb; ci < ce; ++ci) {
+            const HostCell &c = S.cells[ci];
+            TrCellDev &dc = h_cells[ci];
+            for (int d = 0; d < 3; ++d) {
+                dc.c[d] = c.c[d];
+                dc.h[d] = c.h[d];
+                dc.n[d] = c.n[d];
+            }
+            dc.pfirst = c.pfirst;
+            auto pt = [&](int j, int m) { return m > 1 ? cheb[m][j] : 0.0; };
+            for (int a = 0; a < c.n[0]; ++a)
+                for (int b = 0; b < c.n[1]; ++b)
+                    for (int e = 0; e < c.n[2]; ++e) {
+                        const int m = (a * c.n[1] + b) * c.n[2] + e;
+                        h_ploc[c.pfirst + m] = make_float4(static_cast<float>(c.h[0] * pt(a, c.n[0])),
+                                                           static_cast<float>(c.h[1] * pt(b, c.n[1])),
+                                                           static_cast<float>(c.h[2] * pt(e, c.n[2])), 0.0f);
+                    }
         }
-        dc.pfirst = c.pfirst;
-        for (int a = 0; a < c.n[0]; ++a)
-            for (int b = 0; b < c.n[1]; ++b)
-                for (int e = 0; e < c.n[2]; ++e) {
-                    const int m = (a * c.n[1] + b) * c.n[2] + e;
-                    auto pt = [](int j, int n) {
-                        return n > 1 ? std::cos(TR_PI * j / (n - 1)) : 0.0;
-                    };
-                    h_ploc[c.pfirst + m] = make_float4(static_cast<float>(c.h[0] * pt(a, c.n[0])),
-                                                       static_cast<float>(c.h[1] * pt(b, c.n[1])),
-                                                       static_cast<float>(c.h[2] * pt(e, c.n[2])), 0.0f);
-                }
-    }
+    });
     // sources: FP32 offsets from their leaf's centre, FP64 absolute positions, weights
     std::vector<float4> h_sloc(ns), h_slo(ns);
     std::vector<double> h_sabs(3 * ns), h_ws(ns), h_ns(T->nq == 3 ? 3 * ns : 0);
-    for (long long k = 0; k < ns; ++k) {
-        const int o = S.perm[k];
-        const HostCell &L = S.cells[S.leaf_of[k]];
-        h_sloc[k] = hi4(hs[o] - L.c[0], hs[ns + o] - L.c[1], hs[2 * ns + o] - L.c[2]);
-        h_slo[k] = lo4(hs[o] - L.c[0], hs[ns + o] - L.c[1], hs[2 * ns + o] - L.c[2]);
-        for (int d = 0; d < 3; ++d) {
-            h_sabs[d * ns + k] = hs[d * ns + o];
-            if (T->nq == 3)
-                h_ns[d * ns + k] = hn[d * ns + o];
+    host_parallel(ns, 32768, [&](long long kb, long long ke) {
+        for (long long k = kb; k < ke; ++k) {
+            const int o = S.perm[k];
+            const HostCell &L = S.cells[S.leaf_of[k]];
+            h_sloc[k] = hi4(hs[o] - L.c[0], hs[ns + o] - L.c[1], hs[2 * ns + o] - L.c[2]);
+            h_slo[k] = lo4(hs[o] - L.c[0], hs[ns + o] - L.c[1], hs[2 * ns + o] - L.c[2]);
+            for (int d = 0; d < 3; ++d) {
+                h_sabs[d * ns + k] = hs[d * ns + o];
+                if (T->nq == 3)
+                    h_ns[d * ns + k] = hn[d * ns + o];
+            }
+            h_ws[k] = hw[o];
         }
-        h_ws[k] = hw[o];
-    }
+    });
     // target blocks: runs of TR_THREADS consecutive targets in Morton order, each with its
     // own tight box; target positions in FP32 relative to their block's centre
     struct TBlock {
@@ -769,67 +845,98 @@ static int tree_create_impl(long long ns, const double *src, const double *nrm, 
             }
         }
     }
-    for (const auto &run : runs) {
-        TBlock B{};
-        B.first = run.first;
-        B.count = run.second;
-        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-        for (int k = B.first; k < B.first + B.count; ++k)
+    tb.resize(runs.size());
+    host_parallel(static_cast<long long>(runs.size()), 256, [&](long long rb, long long re) {
+        for (long long ri = rb; ri < re; ++ri) {
+            TBlock &B = tb[ri];
+            B.first = runs[ri].first;
+            B.count = runs[ri].second;
+            double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+            for (int k = B.first; k < B.first + B.count; ++k)
+                for (int d = 0; d < 3; ++d) {
+                    const double v = xt[d * nt + Tt.perm[k]];
+                    lo[d] = std::min(lo[d], v);
+                    hi[d] = std::max(hi[d], v);
+                }
+            double r2 = 0.0;
             for (int d = 0; d < 3; ++d) {
-                const double v = xt[d * nt + Tt.perm[k]];
-                lo[d] = std::min(lo[d], v);
-                hi[d] = std::max(hi[d], v);
+                B.c[d] = 0.5 * (lo[d] + hi[d]);
+                r2 += 0.25 * (hi[d] - lo[d]) * (hi[d] - lo[d]);
             }
-        double r2 = 0.0;
-        for (int d = 0; d < 3; ++d) {
-            B.c[d] = 0.5 * (lo[d] + hi[d]);
-            r2 += 0.25 * (hi[d] - lo[d]) * (hi[d] - lo[d]);
+            B.rad = std::sqrt(r2);
+            for (int k = B.first; k < B.first + B.count; ++k) {
+                const int o = Tt.perm[k];
+                h_tloc[k] = hi4(xt[o] - B.c[0], xt[nt + o] - B.c[1], xt[2 * nt + o] - B.c[2]);
+                h_tlo[k] = lo4(xt[o] - B.c[0], xt[nt + o] - B.c[1], xt[2 * nt + o] - B.c[2]);
+            }
         }
-        B.rad = std::sqrt(r2);
-        for (int k = B.first; k < B.first + B.count; ++k) {
-            const int o = Tt.perm[k];
-            h_tloc[k] = hi4(xt[o] - B.c[0], xt[nt + o] - B.c[1], xt[2 * nt + o] - B.c[2]);
-            h_tlo[k] = lo4(xt[o] - B.c[0], xt[nt + o] - B.c[1], xt[2 * nt + o] - B.c[2]);
+    });
+    // lists: per target block, a traversal of the source tree (blocks in parallel ranges,
+    // each range's entries concatenated in block order)
+    const long long nblk = static_cast<long long>(tb.size());
+    const long long nrange = std::min<long long>(64, std::max<long long>(1, nblk));
+    const long long bper = (nblk + nrange - 1) / nrange;
+    std::vector<std::vector<TrEntry>> rent(nrange);
+    std::vector<int> rcount(nblk, 0);
+    std::vector<double> rpairs(nrange, 0.0);
+    host_parallel(nrange, nblk >= 256 ? 1 : nrange, [&](long long rlo, long long rhi) {
+        std::vector<int> stack;
+        for (long long r = rlo; r < rhi; ++r) {
+            std::vector<TrEntry> &ent = rent[r];
+            for (long long bi = r * bper; bi < std::min(nblk, (r + 1) * bper); ++bi) {
+                const TBlock &L = tb[bi];
+                const size_t e0 = ent.size();
+                stack.assign(1, 0);
+                while (!stack.empty()) {
+                    const int cidx = stack.back();
+                    const HostCell &C = S.cells[cidx];
+                    stack.pop_back();
+                    double d2 = 0.0;
+                    for (int d = 0; d < 3; ++d)
+                        d2 += (C.c[d] - L.c[d]) * (C.c[d] - L.c[d]);
+                    const double dist = std::sqrt(d2) - L.rad;
+                    if (dist > 0.0 && dist * theta >= C.rad && C.count > C.nprox) {
+                        ent.push_back(make_entry(C.pfirst, C.nprox, 1, 0.0, C.c, L.c));
+                        ent.back().cell = cidx;
+                        rpairs[r] += static_cast<double>(C.nprox) * L.count;
+                    } else if (C.nchild == 0) {
+                        ent.push_back(make_entry(C.first, C.count, 0, TR_COINCIDENT_REL * (L.rad + C.rad),
+                                                 C.c, L.c));
+                        ent.back().cell = cidx;
+                        rpairs[r] += static_cast<double>(C.count) * L.count;
+                    } else {
+                        for (int k = C.nchild - 1; k >= 0; --k)
+                            stack.push_back(C.child[k]);
+                    }
+                }
+                rcount[bi] = static_cast<int>(ent.size() - e0);
+            }
         }
-        tb.push_back(B);
-    }
-    // lists: per target block, a traversal of the source tree
+    });
     std::vector<int4> h_tleaf;
     std::vector<TrEntry> h_ent;
     double pairs = 0.0;
-    std::vector<int> stack;
-    for (const TBlock &L : tb) {
-        const int e0 = static_cast<int>(h_ent.size());
-        stack.assign(1, 0);
-        while (!stack.empty()) {
-            const HostCell &C = S.cells[stack.back()];
-            stack.pop_back();
-            double d2 = 0.0;
-            for (int d = 0; d < 3; ++d)
-                d2 += (C.c[d] - L.c[d]) * (C.c[d] - L.c[d]);
-            const double dist = std::sqrt(d2) - L.rad;
-            if (dist > 0.0 && dist * theta >= C.rad && C.count > C.nprox) {
-                const TrEntry en = make_entry(C.pfirst, C.nprox, 1, 0.0, C.c, L.c);
-                h_ent.push_back(en);
-                pairs += static_cast<double>(C.nprox) * L.count;
-            } else if (C.nchild == 0) {
-                const TrEntry en = make_entry(C.first, C.count, 0, TR_COINCIDENT_REL * (L.rad + C.rad),
-                                              C.c, L.c);
-                h_ent.push_back(en);
-                pairs += static_cast<double>(C.count) * L.count;
-            } else {
-                for (int k = C.nchild - 1; k >= 0; --k)
-                    stack.push_back(C.child[k]);
-            }
+    for (long long r = 0; r < nrange; ++r) {
+        h_ent.insert(h_ent.end(), rent[r].begin(), rent[r].end());
+        pairs += rpairs[r];
+    }
+    if (h_ent.size() > 0x7fffffffULL) {
+        set_error("stokes_tree_create: too many list entries");
+        return SBQ_EINVAL;
+    }
+    {
+        long long e0 = 0;
+        for (long long bi = 0; bi < nblk; ++bi) {
+            h_tleaf.push_back(make_int4(tb[bi].first, tb[bi].count, static_cast<int>(e0), rcount[bi]));
+            e0 += rcount[bi];
         }
-        h_tleaf.push_back(make_int4(L.first, L.count, e0, static_cast<int>(h_ent.size()) - e0));
     }
     // P2M work items: the cells some list takes as far (the others need no proxy charges),
     // their sources in chunks
     std::vector<char> used(S.cells.size(), 0);
     for (const TrEntry &en : h_ent)
         if (en.kind == 1)
-            used[cell_of_proxy[en.first]] = 1;
+            used[en.cell] = 1;
     std::vector<int4> h_chunks;
     for (size_t ci = 0; ci < S.cells.size(); ++ci) {
         if (!used[ci])
