@@ -746,16 +746,19 @@ def test_solve_host_with_correction(sbq, oracle_mod):
     assert np.linalg.norm(r) / np.linalg.norm(c["rhs"]) <= 1.05e-10
 
 
+@pytest.mark.parametrize("pinned", [True, False])
 @pytest.mark.parametrize("prec", ["fp64", "fp32c"])
-def test_apply_host_matches_oracle(sbq, oracle_mod, prec):
-    """stokes_apply_host (geometry, density and result in pinned host buffers) against the
-    oracle's K sigma = sigma/2 + (D + eta S) sigma on the curved pipe of 4,608 nodes."""
+def test_apply_host_matches_oracle(sbq, oracle_mod, prec, pinned):
+    """stokes_apply_host (geometry, density and result in pinned or pageable host buffers)
+    against the oracle's K sigma = sigma/2 + (D + eta S) sigma on the curved pipe of 4,608
+    nodes."""
     import torch
     c = I.config2(panels=8)
     s = c["surf"]
     eta = sbq.slender_eta(0.2)
     sig = I.density(s.size, seed=31)
-    h = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
+    h = lambda a: (torch.as_tensor(np.ascontiguousarray(a)).pin_memory() if pinned
+                   else torch.as_tensor(np.ascontiguousarray(a)).clone())
     out = sbq.apply_host(h(s.x), h(s.n), h(s.w), h(sig), eta, prec=prec)
     assert not out.is_cuda
     ref = oracle_mod.matvec(s.x, s.n, s.w, eta, sig)
