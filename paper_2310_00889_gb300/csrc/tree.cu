@@ -29,6 +29,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <new>
 #include <numeric>
 #include <thread>
 #include <utility>
@@ -735,6 +736,8 @@ static int tree_create_impl(long long ns, const double *src, const double *nrm, 
     T->same = trg == src && nt == ns;
     T->theta = theta;
     T->order = order;
+    if (ns == 0 || nt == 0)
+        return SBQ_OK;   // nothing to build: the apply writes zeros (no sources) or nothing
     std::vector<double> hs(3 * ns), hw(ns), ht, hn;
     SBQ_CUDA(cudaMemcpyAsync(hs.data(), src, 3 * ns * sizeof(double), cudaMemcpyDeviceToHost, s));
     if (T->nq == 3) {
@@ -1056,7 +1059,7 @@ void tree_op_free(Op *op)
     op->tree = nullptr;
 }
 
-int tree_op_attach(Op *op, double theta, int order, cudaStream_t s)
+static int tree_op_attach_impl(Op *op, double theta, int order, cudaStream_t s)
 {
     tree_op_free(op);
     if (theta <= 0.0)
@@ -1095,14 +1098,30 @@ int tree_op_attach(Op *op, double theta, int order, cudaStream_t s)
     }
     sbq_tree_s *T = new sbq_tree_s();
     cudaGetDevice(&T->device);
-    const int st = tree_create_impl(n, src.as<double>(), nrm.as<double>(), w.as<double>(), n,
-                                    src.as<double>(), op->eta, 1.0, theta, order, T, s);
+    int st;
+    try {
+        st = tree_create_impl(n, src.as<double>(), nrm.as<double>(), w.as<double>(), n,
+                              src.as<double>(), op->eta, 1.0, theta, order, T, s);
+    } catch (...) {
+        delete T;
+        throw;
+    }
     if (st != SBQ_OK) {
         delete T;
         return st;
     }
     op->tree = T;
     return SBQ_OK;
+}
+
+int tree_op_attach(Op *op, double theta, int order, cudaStream_t s)
+{
+    try {   // the host build allocates; nothing may be thrown across the C ABI
+        return tree_op_attach_impl(op, theta, order, s);
+    } catch (const std::bad_alloc &) {
+        set_error("stokes_op_set_tree: out of host memory");
+        return SBQ_ENOMEM;
+    }
 }
 
 int tree_op_apply(Op *op, const double *y, double *out, cudaStream_t s)
@@ -1146,10 +1165,17 @@ extern "C" __attribute__((visibility("default"))) int stokes_tree_create(
         return tree_fail(SBQ_EINVAL, "stokes_tree_create: theta must be in (0, 1)");
     if (order < 2 || order > 10)
         return tree_fail(SBQ_EINVAL, "stokes_tree_create: order must be in 2..10");
-    sbq_tree_s *T = new sbq_tree_s();
+    sbq_tree_s *T = new (std::nothrow) sbq_tree_s();
+    if (!T)
+        return tree_fail(SBQ_ENOMEM, "stokes_tree_create: out of host memory");
     cudaGetDevice(&T->device);
-    const int st = sbq::tree_create_impl(ns, src, nrm, w, nt, trg, alpha, beta, theta, order, T,
-                                         static_cast<cudaStream_t>(stream));
+    int st;
+    try {   // the host build allocates; nothing may be thrown across the C ABI
+        st = sbq::tree_create_impl(ns, src, nrm, w, nt, trg, alpha, beta, theta, order, T,
+                                   static_cast<cudaStream_t>(stream));
+    } catch (const std::bad_alloc &) {
+        st = tree_fail(SBQ_ENOMEM, "stokes_tree_create: out of host memory");
+    }
     if (st != SBQ_OK) {
         delete T;
         return st;

@@ -201,3 +201,42 @@ def test_tree_coincident_nodes(sbq, oracle_mod):
     err = _rel(u[:, sub], ref)
     print("treecode, cloud with coincident nodes: %.3e" % err)
     assert err < 1e-5
+
+
+@pytest.mark.parametrize("n", [1, 2, 127, 128, 129, 600])
+def test_tree_small_sizes(sbq, oracle_mod, n):
+    """Sizes around one leaf and one target block (1 to 600 nodes of a 3D cloud), on-surface
+    sums of the single layer and of the combined field against the oracle on every row; a
+    single node has nothing to sum."""
+    rng = np.random.default_rng(50 + n)
+    x, w, sig = rng.standard_normal((3, n)), rng.random(n), rng.standard_normal((3, n))
+    nrm = rng.standard_normal((3, n))
+    nrm /= np.linalg.norm(nrm, axis=0)
+    T = sbq.SlTree(_t(x), _t(w))
+    u = T.apply(_t(sig)).cpu().numpy()
+    T.close()
+    C = sbq.StokesTree(_t(x), _t(w), nrm=_t(nrm), alpha=0.7, beta=1.0)
+    uc = C.apply(_t(sig)).cpu().numpy()
+    C.close()
+    if n == 1:
+        assert np.all(u == 0.0) and np.all(uc == 0.0)
+        return
+    assert _rel(u, oracle_mod.sl(x, w, sig, x)) < 1e-5
+    assert _rel(uc, oracle_mod.combined(x, nrm, w, sig, x, 0.7, 1.0)) < 1e-5
+
+
+def test_tree_empty(sbq):
+    """No targets: an empty result; no sources: zeros at every target."""
+    import torch
+    rng = np.random.default_rng(57)
+    x, w = _t(rng.standard_normal((3, 50))), _t(rng.random(50))
+    T = sbq.SlTree(x, w, trg=_t(np.zeros((3, 0))))
+    u = T.apply(_t(rng.standard_normal((3, 50))))
+    T.close()
+    assert tuple(u.shape) == (3, 0)
+    T = sbq.SlTree(_t(np.zeros((3, 0))), _t(np.zeros(0)), trg=x)
+    u = T.apply(_t(np.zeros((3, 0))), out=torch.full((3, 50), 7.0, dtype=torch.float64, device="cuda"))
+    st = T.stats()
+    T.close()
+    assert tuple(u.shape) == (3, 50) and bool((u == 0.0).all())
+    assert st["pairs"] == 0.0 and st["entries"] == 0
