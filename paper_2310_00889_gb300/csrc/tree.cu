@@ -553,11 +553,11 @@ __device__ __forceinline__ void tr_stage(float *sf, int t, const int4 &en, int k
 // operation.  NEAR (a source leaf): pairs closer than the entry's coincidence distance (the
 // target's own node on the surface among them) add nothing; with the double layer, r is
 // formed from high and low parts, since on the surface r . n = O(|r|^2): the target in the
-// leaf's frame as an exact (hi, lo)
-// pair (TwoSum, once per entry), then r = (x_hi - y_hi) + (x_lo - y_lo), accurate to an ulp
-// of r itself rather than of the frames.  Far entries (proxy grids) need neither: with d > 0
-// the distance between the centres less the block's radius, their acceptance (d theta >=
-// cell radius) keeps every target at least (1 - theta) d from every proxy point.
+// leaf's frame as an exact (hi, lo) pair (TwoSum, once per entry), then r = (x_hi - y_hi) +
+// (x_lo - y_lo), accurate to an ulp of r itself rather than of the frames.  Far entries
+// (proxy grids) need neither: with d > 0 the distance between the centres less the block's
+// radius, their acceptance (d theta >= cell radius) keeps every target at least
+// (1 - theta) d from every proxy point.
 template <int NQ, bool NEAR>
 __device__ __forceinline__ void tr_tile(const tf2 *__restrict__ F, int cnt2, const float4 &x,
                                         const float4 &xl, const TrEntry &en, tf2 &ax, tf2 &ay, tf2 &az)
