@@ -389,11 +389,13 @@ def run_headline(args):
     peak, sm_max = _peak_tflops(info, clocks)
     achieved = FLOPS_PER_PAIR["cf"] * pairs / (kernel_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "traffic_note": "DRAM traffic of this kernel grows with the node count, not "
-                                "with the pairs: measured 16.3 MB at 193,120 nodes and 40.1 MB "
-                                "at 324,192 nodes (profiles/pairsum_f32_comp_helix.md); the "
-                                "full-size launch was not captured",
+                "frac": achieved / peak,
+                "traffic": _profiled_traffic("pairsum_f32_comp_helix_1110624.json"),
+                "traffic_unit": "bytes per launch (ncu dram read + write, one-pass capture of "
+                                "this launch, profiles/pairsum_f32_comp_helix_1110624.json)",
+                "traffic_note": "the kernel is ALU-bound: 182 MB per 842 ms launch; reads are "
+                                "1.4 x the packed sources and targets (88.8 MB), writes the "
+                                "chunk partial sums that leave L2",
                 "kernel": "pairsum_f32_kernel<combined field, compensated>",
                 "flops_per_pair": FLOPS_PER_PAIR["cf"], "pairs_per_launch": pairs,
                 "launch_ms": kernel_ms, "apply_ms": float(np.mean(ams)),
